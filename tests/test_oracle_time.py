@@ -1,0 +1,110 @@
+"""Pins of the oracle's time integrators: textbook Adams-Bashforth weights (Sec. 3.1), the
+minimum-norm property of the extended-history weights (Sec. 3.2), the AB3 real stability
+bound 6/11, the identity MRAB(SR=1) == single-rate AB (Sec. 5.2), MRAB design order on a
+two-component linear ODE (Sec. 3.3), and the performance model of Sec. 6.1."""
+import math
+
+import numpy as np
+import scipy.linalg
+
+import workloads as W
+from conftest import golden
+from oracle import OracleSystem, ab_coefficients, mrab_macro_step, rk3_heun_step, srab_step
+
+
+def test_ab_textbook():
+    n3 = np.arange(-2, 1.0)
+    assert np.allclose(ab_coefficients(n3, 0, 1, 3), np.array([5, -16, 23]) / 12, atol=1e-15)
+    n4 = np.arange(-3, 1.0)
+    assert np.allclose(ab_coefficients(n4, 0, 1, 4), np.array([-9, 37, -59, 55]) / 24, atol=1e-14)
+    # scale invariance: nodes and interval in another unit
+    assert np.allclose(ab_coefficients(0.1 * n3, 0, 0.1, 3), 0.1 * np.array([5, -16, 23]) / 12, atol=1e-15)
+
+
+def test_extended_history_min_norm():
+    nodes = np.arange(-3, 1.0)
+    a = ab_coefficients(nodes, 0, 1, 3)
+    # moment conditions hold
+    for i in range(3):
+        assert abs(np.sum(a * nodes ** i) - 1.0 / (i + 1)) < 1e-14
+    # minimum norm <=> orthogonal to the null space of V^T, spanned here by the third
+    # difference (-1, 3, -3, 1) (which annihilates quadratics)
+    z = np.array([-1.0, 3.0, -3.0, 1.0])
+    assert abs(a @ z) < 1e-14
+    assert abs(np.sum(z * nodes ** 2)) < 1e-14
+
+
+def _max_root(alpha, z):
+    # y_{n+1} = y_n + z sum_k alpha_k y_{n-m+1+k}; characteristic polynomial in zeta
+    m = len(alpha)
+    c = np.zeros(m + 1)
+    c[0] = 1.0
+    c[1] = -1.0
+    for k in range(m):
+        c[m - k] -= z * alpha[k]
+    return np.abs(np.roots(c)).max()
+
+
+def test_ab3_real_stability_bound():
+    a = ab_coefficients(np.arange(-2, 1.0), 0, 1, 3)
+    assert abs(_max_root(a, -6.0 / 11.0) - 1.0) < 1e-9
+    assert _max_root(a, -0.54) < 1.0
+    assert _max_root(a, -0.55) > 1.0
+    # extended history stretches the negative-real bound (Sec. 3.2)
+    a34 = ab_coefficients(np.arange(-3, 1.0), 0, 1, 3)
+    assert _max_root(a34, -0.85) < 1.0
+
+
+def test_mrab_sr1_equals_srab():
+    wl = W.vortex_box_in_box(seed=4, n_bg=32, n_fine=21, step_ratio=1)
+    S = OracleSystem(wl)
+    H = S.macro_step_size(wl["q0"])
+    y, hf, hs = S.bootstrap(wl["q0"], H)
+    out, _, _ = S.mrab(y, hf, hs, H, 3)
+    hist = [[hs[k], hf[k]] for k in range(3)]
+    z = [y[0], y[1]]
+    for _ in range(3):
+        z, hist = srab_step(z, hist, H, 3, S.rhs_all)
+    assert np.array_equal(out[0], z[0]) and np.array_equal(out[1], z[1])
+
+
+def test_mrab_order_linear_ode():
+    lf, ls, c = 10.0, 1.0, 0.5
+    A = np.array([[-lf, c], [c, -ls]])
+    y0 = np.array([1.0, 0.5])
+    T = 1.0
+    errs = []
+    for n in (80, 160, 320):
+        H = T / n
+        sr = 3
+        h = H / sr
+        # exact histories at t = 0: fast at -2h,-h,0, slow at -2H,-H,0
+        ex = lambda t: scipy.linalg.expm(A * t) @ y0
+        hf = [A[0] @ ex(-k * h) for k in (2, 1, 0)]
+        hs = [A[1] @ ex(-k * H) for k in (2, 1, 0)]
+        f, s = y0[0], y0[1]
+        for _ in range(n):
+            f, s, hf, hs = mrab_macro_step(f, s, hf, hs, H, sr, 3,
+                                           rhs_fast=lambda ff, ss: A[0, 0] * ff + A[0, 1] * ss,
+                                           rhs_slow=lambda ss, ff: A[1, 0] * ff + A[1, 1] * ss)
+        e = ex(T)
+        errs.append(math.hypot(f - e[0], s - e[1]))
+    eocs = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(2.9 < e < 3.15 for e in eocs), eocs
+
+
+def test_rk3_order():
+    lam = -1.3
+    errs = []
+    for n in (20, 40):
+        y = [np.array(1.0)]
+        for _ in range(n):
+            y, _ = rk3_heun_step(y, 1.0 / n, lambda z: [lam * z[0]])
+        errs.append(abs(float(y[0]) - math.exp(lam)))
+    assert 2.9 < math.log2(errs[0] / errs[1]) < 3.1
+
+
+def test_performance_model_rk4_total():
+    g = {r[0]: int(r[1]) for r in golden("perf_model.txt")}
+    # eq. (perf_RK4) with t = dt_RK4
+    assert 4 * (g["n_fast"] + g["n_slow"]) == g["rk4_total"]
