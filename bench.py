@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput of the MRAB-integrated SBP-SAT overset solver on one GB300.
+
+Workload: the 2D Navier-Stokes cylinder in cross-flow (Sec. 5.1 shape): a 512 x 128 O-grid
+(radial stretching 1.05, wall inside, overset interface outside) on a 1024 x 512 Cartesian
+background with far-field faces; Re 200, Mach 0.2, Pr 0.72; MRAB order 3, step ratio 4;
+synthetic uniform inflow plus a seeded 1e-3 Gaussian perturbation.
+
+One benchmark step is one MRAB macro step: the slow (background) right-hand side fused with
+its update, and four fused fast (O-grid) micro steps, each preceded by the interface
+interpolation (with the slow extrapolation). The metric is mesh-point right-hand-side
+evaluations per second: (n_slow + 4 n_fast) per step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank advances its own replica (the method has no exchange between
+independent systems); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("cylinder overset Navier-Stokes: O-grid 512x128 + Cartesian 1024x512, "
+            "MRAB order 3, step ratio 4")
+L2_FLUSH_BYTES = 256 << 20
+FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 rate of GB300 (no FP64 tensor path)
+FLOP_PER_POINT_NS = 300.0      # algorithmic FLOPs of one 2D NS right-hand-side point + update
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant line")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = []
+        smax = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+def _setup_dist(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _evals_per_step(wl):
+    bg, og = wl["meshes"]
+    sr = wl["params"]["step_ratio"]
+    n_bg = bg["n"][0] * bg["n"][1]
+    n_og = og["n"][0] * og["n"][1]
+    return n_bg + sr * n_og, n_bg, n_og
+
+
+def _run_gpu(wl, dtype, steps, warmup, world, local, sample_clocks=True):
+    import torch
+    import paper_1805_06607_gb300 as sbp
+
+    g = sbp.System(wl, dtype=dtype)
+    g.bind(wl["q0"])
+    g.mrab_init()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        flush.zero_()
+        g.mrab_step(1)
+    g.check()
+    g.profile_read(reset=True)
+    g.profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(local)
+    _barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with (sampler if sample_clocks else _Null()):
+        for k in range(steps):
+            flush.zero_()                       # evict the working set (< L2) between steps
+            ev[k][0].record(stream)
+            g.mrab_step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    _barrier(world)
+    g.profile_enable(False)
+    prof = g.profile_read(reset=True)
+    g.check()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    # end to end through host buffers: states in from pinned host memory, states out
+    inf = g.info
+    host_in = [torch.empty((4, inf[k].nj, inf[k].pitch), dtype=g.tdtype).pin_memory() for k in range(2)]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    for k in range(2):
+        host_in[k].copy_(g.current_state(k))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        for k in range(2):
+            g.current_state(k).copy_(host_in[k], non_blocking=True)
+        g.mrab_step(1)
+        for k in range(2):
+            host_out[k].copy_(g.current_state(k), non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / steps
+    bytes_io = sum(h.numel() * h.element_size() for h in host_in)
+    out = {"step_ms": step_ms, "wall_s": wall, "prof": prof, "clocks": sampler.summary() if sample_clocks else None,
+           "e2e_ms": e2e_ms, "h2d": bytes_io, "d2h": bytes_io, "info": inf,
+           "launches_per_step": 2 + 2 * wl["params"]["step_ratio"]}
+    g.close()
+    return out
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def _roofline(res, wl, dtype, hbm_peak, peak_kind):
+    """Dominant kernel of the step (largest device time) against its bound."""
+    evals, n_bg, n_og = _evals_per_step(wl)
+    prof = res["prof"]
+    phase = max(prof, key=lambda p: prof[p][0])
+    ms, n = prof[phase]
+    avg_s = ms / max(n, 1) / 1e3
+    esz = 8 if dtype == "f64" else 4
+    pts = n_bg if phase.endswith("slow") else n_og
+    curv = not phase.endswith("slow")
+    m = wl["params"]["hist_len"]
+    if phase.startswith("rhs"):
+        # q in + q out + new history slot out + (m-1) older slots in, 4 variables, + class byte;
+        # curvilinear meshes also read 5 metric planes
+        bpp = (4 * esz) * (3 + (m - 1)) + 1 + (5 * esz if curv else 0)
+    else:
+        bpp = 0.0
+    roof = {"kernel": phase, "launches": n, "avg_launch_ms": avg_s * 1e3}
+    if dtype == "f64" and phase.startswith("rhs"):
+        flops = FLOP_PER_POINT_NS * pts
+        roof.update({"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "peak_kind": "nominal FP64 (derived: 152 SMs x 2 DFMA/clk x 2 x 2.06 GHz)",
+                     "hbm_achieved_gbs": bpp * pts / avg_s / 1e9, "bytes_per_point": bpp,
+                     "flop_per_point": FLOP_PER_POINT_NS})
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        roof.update({"bound": "hbm", "achieved": bpp * pts / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "peak_kind": peak_kind, "bytes_per_point": bpp})
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    return roof
+
+
+def _cpu_baseline(wl, seconds):
+    """The oracle, as it stands, on the host: whole MRAB macro steps of the same workload."""
+    import numpy as np
+    from oracle import OracleSystem
+
+    ref = OracleSystem(wl)
+    q = wl["q0"]
+    H = ref.macro_step_size(q)
+    m = wl["params"]["hist_len"]
+    a = ref.rhs_all(q)
+    hf = [a[ref.fast]] * m
+    hs = [a[ref.slow]] * m
+    evals, _, _ = _evals_per_step(wl)
+    n = 0
+    t0 = time.perf_counter()
+    y = [np.array(v) for v in q]
+    while True:
+        y, hf, hs = ref.mrab(y, hf, hs, H, 1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": n * evals / el, "unit": "point-evals/s", "cores": 1, "kind": "oracle",
+            "sample": "%d MRAB macro steps of the full workload (histories seeded with the initial "
+                      "right-hand side), %.1f s, single-threaded C + numpy" % (n, el)}
+
+
+def _reference(args):
+    world, rank, _ = (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if rank != 0:
+        return 0
+    import numpy as np
+    import workloads as W
+    from oracle import OracleSystem
+
+    wl = W.cylinder_overset(seed=0)
+    evals, _, _ = _evals_per_step(wl)
+    ref = OracleSystem(wl)
+    q = wl["q0"]
+    H = ref.macro_step_size(q)
+    m = wl["params"]["hist_len"]
+    a = ref.rhs_all(q)
+    hf = [a[ref.fast]] * m
+    hs = [a[ref.slow]] * m
+    y = [np.array(v) for v in q]
+    for _ in range(args.warmup):
+        y, hf, hs = ref.mrab(y, hf, hs, H, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y, hf, hs = ref.mrab(y, hf, hs, H, 1)
+    el = time.perf_counter() - t0
+    v = args.steps * evals / el
+    line = {"impl": "reference", "metric": "mesh-point RHS evals/s", "value": v, "unit": "point-evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": sum(mm["n"][0] * mm["n"][1] for mm in wl["meshes"]),
+                       "evals_per_step": evals},
+            "cpu_baseline": {"value": v, "unit": "point-evals/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d timed MRAB macro steps of the full workload after %d warm-up steps"
+                                       % (args.steps, args.warmup)},
+            "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return _reference(args)
+    import workloads as W
+
+    world, rank, local = _setup_dist(args)
+    wl = W.cylinder_overset(seed=rank)
+    evals, n_bg, n_og = _evals_per_step(wl)
+    hbm_peak, peak_kind = _peaks()
+    res = _run_gpu(wl, args.dtype, args.steps, args.warmup, world, local)
+    step_ms = _max_over_ranks(world, res["step_ms"])
+    e2e_ms = _max_over_ranks(world, res["e2e_ms"])
+    line = {
+        "metric": "mesh-point RHS evals/s", "value": world * evals / (step_ms / 1e3), "unit": "point-evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points": n_bg + n_og, "evals_per_step": evals,
+                   "step": "one MRAB macro step (1 slow + 4 fast fused RHS/update, 5 interpolations)",
+                   "l2": "256 MiB buffer written before every timed step (working set < L2)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": res["clocks"],
+        "e2e": {"value": world * evals / (e2e_ms / 1e3), "unit": "point-evals/s",
+                "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+        "gpu_launches": res["launches_per_step"] * args.steps,
+        "roofline": _roofline(res, wl, args.dtype, hbm_peak, peak_kind),
+        "phases_ms_per_step": {p: v[0] / args.steps for p, v in res["prof"].items()},
+        "wall_s_timed_region": res["wall_s"],
+    }
+    if not args.no_variants:
+        other = "f32" if args.dtype == "f64" else "f64"
+        r2 = _run_gpu(wl, other, args.steps, args.warmup, world, local, sample_clocks=False)
+        ms2 = _max_over_ranks(world, r2["step_ms"])
+        line["variants"] = {other: {"value": world * evals / (ms2 / 1e3), "ms_per_step": ms2,
+                                    "roofline": _roofline(r2, wl, other, hbm_peak, peak_kind),
+                                    "phases_ms_per_step": {p: v[0] / args.steps for p, v in r2["prof"].items()}}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * sbp_mrab.h -- C ABI of the GB300 library for multi-rate Adams-Bashforth time integration of
+ * the SBP-SAT discretised compressible Euler / Navier-Stokes equations on two overset
+ * structured meshes (arXiv 1805.06607, "Multi-Rate Time Integration on Overset Meshes").
+ *
+ * Conventions
+ *  - Every call returns an sbp_status; nothing throws across the ABI. sbp_status_string()
+ *    names a status; sbp_last_error_message() gives detail for the calling thread's last
+ *    failure (a CUDA error string, the offending argument, ...).
+ *  - Device memory for states, histories and right-hand sides is owned by the caller and
+ *    passed as plain device pointers. The library owns the tables it derives at creation
+ *    (class maps, metrics, SAT lists, donor stencils) and a small device error word; they
+ *    are freed by sbp_system_destroy.
+ *  - Fields are structure-of-arrays: variable v of point (i, j) sits at
+ *    base[v * field_elems + j * pitch + i], i fastest, with pitch and field_elems from
+ *    sbp_mesh_info. nvar = 4 in 2D: (rho, rho u, rho v, rho E). The element type is double
+ *    for SBP_F64 systems and float for SBP_F32 systems, fixed at creation.
+ *  - Streams are cudaStream_t values passed as void*; NULL means the legacy default stream.
+ *    Calls that return host results (sbp_timestep, sbp_check) synchronise that stream.
+ *  - A system is not thread-safe; use one system per host thread.
+ */
+#ifndef SBP_MRAB_H
+#define SBP_MRAB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbp_system_s *sbp_system_t;
+
+typedef enum {
+  SBP_OK = 0,
+  SBP_ERR_ARG = -1,       /* null pointer, bad enum or size */
+  SBP_ERR_SHAPE = -2,     /* mesh too small, non-positive cell volume, inconsistent sizes */
+  SBP_ERR_DTYPE = -3,     /* element type not supported for the requested call */
+  SBP_ERR_CUDA = -4,      /* a CUDA runtime call failed (detail in the message) */
+  SBP_ERR_NONFINITE = -5, /* a kernel met a non-finite or non-physical state */
+  SBP_ERR_DONOR = -6,     /* no valid donor stencil for a receiver */
+  SBP_ERR_TIMEOUT = -7,   /* a bounded device wait gave up */
+  SBP_ERR_BOUNDS = -8,    /* a kernel index check failed */
+  SBP_ERR_STATE = -9      /* call out of order (e.g. stepping before sbp_mrab_init) */
+} sbp_status;
+
+enum { SBP_BC_PERIODIC = 0, SBP_BC_INTERFACE = 1, SBP_BC_FARFIELD = 2, SBP_BC_WALL = 3 };
+enum { SBP_EULER = 0, SBP_NS = 1 };
+enum { SBP_F64 = 0, SBP_F32 = 1 };
+
+/* One structured 2D mesh. Faces are ordered i-low, i-high, j-low, j-high. A periodic direction
+ * must have SBP_BC_PERIODIC on both of its faces. Curvilinear meshes give host coordinate
+ * arrays x, y of nj*ni points (i fastest; copied at creation). Cartesian meshes may leave x, y
+ * NULL and give lo/h instead. shift is the coordinate jump across a periodic wrap:
+ * (dx, dy) when i wraps, then (dx, dy) when j wraps (0 for a closed O-grid). */
+typedef struct {
+  int n[2];
+  int periodic[2];
+  int bc[4];
+  int cartesian;
+  double lo[2], h[2];
+  const double *x, *y;
+  double shift[4];
+} sbp_mesh_desc;
+
+/* Physics, penalties and integrator. Non-dimensionalisation: rho_inf = 1, c_inf = 1,
+ * T = gamma p / rho; mu is the viscous coefficient (Mach/Re), constant, with Stokes' lambda =
+ * -2/3 mu and heat conductivity mu / (Pr (gamma - 1)). qinf is the far-field state. The
+ * integrator is MRAB of order `order` with `hist_len` >= order history values (extended
+ * history when larger), step ratio H/h = step_ratio >= 1, mesh `fast_mesh` advancing at the
+ * micro step. hole_cells: background points farther than hole_cells background spacings
+ * inside the fine mesh's outer boundary are holes. */
+typedef struct {
+  int physics;
+  int dtype;
+  double gamma, mu, pr, twall;
+  double omega_corner;           /* Omega of Sec. 4.2 eq. (penalty_interp) at corner receivers */
+  double sigma_interface;        /* sigma^I of eq. (int); the paper uses 1/2 */
+  double sigma_physical;         /* sigma^I of the far-field and wall penalties */
+  double cfl;
+  double qinf[4];
+  int order, hist_len, step_ratio, fast_mesh;
+  int hole_cells;
+} sbp_params;
+
+typedef struct {
+  int ni, nj, pitch;
+  size_t field_elems;   /* elements of one variable plane: pitch * nj */
+  size_t state_bytes;   /* nvar planes */
+  size_t hist_bytes;    /* hist_len * state_bytes */
+  int nvar, n_holes, n_receivers, n_sat_points;
+  int elem_size;        /* 8 (F64) or 4 (F32) */
+} sbp_mesh_info;
+
+/* Create a two-mesh overset system (mesh 0 = background, mesh 1 = the overset fine mesh) and
+ * run its setup (Sec. 2.2 and Sec. 4.1): hole cut, SBP segment classes, metrics (computed on
+ * the device by the derivative operator), SAT lists, donor search and Lagrange weights, and
+ * the Adams-Bashforth / MRAB coefficient plan (Sec. 3.1-3.3). Synchronous. */
+sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                             sbp_system_t *out);
+sbp_status sbp_system_destroy(sbp_system_t sys);
+sbp_status sbp_mesh_info_get(sbp_system_t sys, int mesh, sbp_mesh_info *info);
+
+/* Setup tables copied to host memory, for inspection and tests.
+ *  iblank: nj*ni bytes (1 active, 0 hole). metrics: 5*nj*ni doubles, planes
+ *  (xi_x/J, xi_y/J, eta_x/J, eta_y/J, J). receivers: n_receivers point indices j*ni+i;
+ *  donor_base: 2 ints per receiver (i0, j0) on the other mesh; donor_w: 8 doubles per receiver
+ *  (4 Lagrange weights along i, then 4 along j). Any output pointer may be NULL. */
+sbp_status sbp_get_tables(sbp_system_t sys, int mesh, signed char *iblank, double *metrics,
+                          int *receivers, int *donor_base, double *donor_w);
+
+/* Donor-cell Lagrange interpolation (Sec. 2.2; Sec. 3.3 step 2 for the extrapolated state):
+ * for each receiver r of recv_mesh, qhat[v*n_receivers + r] = sum over the 4x4 donor stencil
+ * of w_i w_j q_donor. With NS physics and fvhat != NULL also the six Cartesian viscous-flux
+ * components (F^V_x then F^V_y; momentum x, momentum y, energy) interpolated the same way into
+ * fvhat[c*n_receivers + r]. q_donor is a full state of the other mesh (device). qhat, fvhat:
+ * device, caller-owned. */
+sbp_status sbp_overset_interp(sbp_system_t sys, int recv_mesh, const void *q_donor, void *qhat,
+                              void *fvhat, void *stream);
+
+/* Right-hand side dq/dt of one mesh (Sec. 2.2 eq. (int)): metric-weighted inviscid and
+ * viscous fluxes, SBP 4-2 derivatives with segment closures, physical and interface SAT
+ * penalties, the interface values interpolated from q_other. rhs: device, caller-owned,
+ * same layout as q_self; holes get 0. */
+sbp_status sbp_rhs_eval(sbp_system_t sys, int mesh, const void *q_self, const void *q_other, void *rhs,
+                        void *stream);
+
+/* Stable step estimate of Sec. 4.1 eqs. (ts_inv), (ts_visc), (ts_overall) on both meshes for
+ * the given states, without the CFL factor (dt_mesh[2], host), and the macro step
+ * H = min(cfl dt_slow, step_ratio cfl dt_fast) (host). Synchronises the stream. */
+sbp_status sbp_timestep(sbp_system_t sys, const void *q_mesh0, const void *q_mesh1, double *dt_mesh,
+                        double *H, void *stream);
+
+/* Bind caller-owned device buffers for the time integrator: per mesh two state buffers (the
+ * integrator alternates between them) and one history ring of hist_len states. */
+sbp_status sbp_bind(sbp_system_t sys, int mesh, void *q_a, void *q_b, void *hist);
+/* Device pointer of the bound buffer that holds mesh's current state. */
+sbp_status sbp_current_state(sbp_system_t sys, int mesh, void **q);
+
+/* Bootstrap (Sec. 3.1): Heun's third-order Runge-Kutta at the micro step h = H/step_ratio for
+ * (hist_len-1)*step_ratio steps from the current bound states, recording the fast right-hand
+ * side every micro step and the slow one every macro step. H <= 0 takes H from sbp_timestep
+ * on the initial states. Allocates and frees its own stage buffers. */
+sbp_status sbp_mrab_init(sbp_system_t sys, double H, void *stream);
+
+/* n macro steps of the fastest-first MRAB scheme without re-extrapolation (Sec. 3.3, Steps
+ * 1-7, any integer step ratio). Per macro step: interpolate the fast state to the slow
+ * receivers; slow RHS fused with the slow state update; then step_ratio fused fast RHS +
+ * fast updates, each fed by the slow extrapolant at its micro time. Asynchronous. */
+sbp_status sbp_mrab_step(sbp_system_t sys, int n, void *stream);
+
+/* Macro step size H and elapsed time since the end of the bootstrap. */
+sbp_status sbp_mrab_time(sbp_system_t sys, double *H, double *t);
+
+/* Phase timers, the device-side counterpart of the paper's RHS / interpolation time split
+ * (Sec. 6.2, Table perfthird). While enabled, sbp_mrab_step records a CUDA event pair on its
+ * stream around every kernel launch and attributes the elapsed device time to one phase:
+ * interpolation to the slow mesh's receivers, the slow fused RHS + update, interpolation to the
+ * fast mesh's receivers (with the slow extrapolation), the fast fused RHS + update.
+ * sbp_profile_read waits for the recorded events and returns, per phase, the accumulated
+ * milliseconds and launch counts (arrays of SBP_PHASE_COUNT); reset != 0 clears them. */
+enum { SBP_PHASE_INTERP_SLOW = 0, SBP_PHASE_RHS_SLOW = 1, SBP_PHASE_INTERP_FAST = 2, SBP_PHASE_RHS_FAST = 3,
+       SBP_PHASE_COUNT = 4 };
+sbp_status sbp_profile_enable(sbp_system_t sys, int enable);
+sbp_status sbp_profile_read(sbp_system_t sys, double *ms, int *launches, int reset);
+
+/* Synchronise the stream and report (then clear) the device error word. */
+sbp_status sbp_check(sbp_system_t sys, void *stream);
+
+const char *sbp_status_string(sbp_status s);
+const char *sbp_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBP_MRAB_H */

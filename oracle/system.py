@@ -173,9 +173,17 @@ class OracleSystem:
                 raise RuntimeError("hole growing did not converge")
             shift = np.array([m["shift"][0][0], m["shift"][0][1], m["shift"][1][0], m["shift"][1][1]])
             met = np.zeros((5, nj, ni))
-            rc = L.orc_metrics2d(ni, nj, _p(shift), _p(m["x"]), _p(m["y"]), _p(ci), _p(cj), _p(met))
-            if rc != 0:
-                raise RuntimeError("non-positive cell volume at point %d" % (-1 - rc))
+            if m["cartesian"]:
+                # a uniform Cartesian map is linear and D reproduces linear functions exactly, so
+                # the metrics are the exact constants (y_eta, -x_eta, -y_xi, x_xi, 1/(hx hy))
+                hx, hy = m["h"]
+                act = ci != CL_HOLE
+                for c, val in enumerate((hy, 0.0, 0.0, hx, 1.0 / (hx * hy))):
+                    met[c] = np.where(act, val, 1.0 if c in (0, 3, 4) else 0.0)
+            else:
+                rc = L.orc_metrics2d(ni, nj, _p(shift), _p(m["x"]), _p(m["y"]), _p(ci), _p(cj), _p(met))
+                if rc != 0:
+                    raise RuntimeError("non-positive cell volume at point %d" % (-1 - rc))
             self.ci.append(ci)
             self.cj.append(cj)
             self.met.append(met)

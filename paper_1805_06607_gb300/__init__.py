@@ -1,0 +1,282 @@
+"""GB300 (sm_103a) library for multi-rate Adams-Bashforth integration of the SBP-SAT
+compressible Euler / Navier-Stokes equations on overset meshes (arXiv 1805.06607).
+
+This module is a thin ctypes binding of the C ABI declared in ``include/sbp_mrab.h``:
+it marshals arguments and owns device buffers through PyTorch; every step of the
+method runs in the library's CUDA kernels. There is no CPU fallback: importing the
+module fails when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsbpmrab.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libsbpmrab.so is not built: run paper_1805_06607_gb300.build.build() "
+                      "(or __graft_entry__.build()) first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+BC = {"periodic": 0, "interface": 1, "farfield": 2, "wall": 3}
+PHYSICS = {"euler": 0, "ns": 1}
+DTYPE = {"f64": 0, "f32": 1}
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 2), ("periodic", ctypes.c_int * 2), ("bc", ctypes.c_int * 4),
+                ("cartesian", ctypes.c_int), ("lo", ctypes.c_double * 2), ("h", ctypes.c_double * 2),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("shift", ctypes.c_double * 4)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("physics", ctypes.c_int), ("dtype", ctypes.c_int), ("gamma", ctypes.c_double),
+                ("mu", ctypes.c_double), ("pr", ctypes.c_double), ("twall", ctypes.c_double),
+                ("omega_corner", ctypes.c_double), ("sigma_interface", ctypes.c_double),
+                ("sigma_physical", ctypes.c_double), ("cfl", ctypes.c_double), ("qinf", ctypes.c_double * 4),
+                ("order", ctypes.c_int), ("hist_len", ctypes.c_int), ("step_ratio", ctypes.c_int),
+                ("fast_mesh", ctypes.c_int), ("hole_cells", ctypes.c_int)]
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("ni", ctypes.c_int), ("nj", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("field_elems", ctypes.c_size_t), ("state_bytes", ctypes.c_size_t),
+                ("hist_bytes", ctypes.c_size_t), ("nvar", ctypes.c_int), ("n_holes", ctypes.c_int),
+                ("n_receivers", ctypes.c_int), ("n_sat_points", ctypes.c_int), ("elem_size", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "sbp_system_create": [ctypes.POINTER(MeshDesc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "sbp_system_destroy": [_P],
+    "sbp_mesh_info_get": [_P, _I, ctypes.POINTER(MeshInfo)],
+    "sbp_get_tables": [_P, _I, _P, _P, _P, _P, _P],
+    "sbp_overset_interp": [_P, _I, _P, _P, _P, _P],
+    "sbp_rhs_eval": [_P, _I, _P, _P, _P, _P],
+    "sbp_timestep": [_P, _P, _P, _P, _P, _P],
+    "sbp_bind": [_P, _I, _P, _P, _P],
+    "sbp_current_state": [_P, _I, ctypes.POINTER(_P)],
+    "sbp_mrab_init": [_P, _D, _P],
+    "sbp_mrab_step": [_P, _I, _P],
+    "sbp_mrab_time": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "sbp_check": [_P, _P],
+    "sbp_profile_enable": [_P, _I],
+    "sbp_profile_read": [_P, _P, _P, _I],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.sbp_status_string.argtypes = [ctypes.c_int]
+_lib.sbp_status_string.restype = ctypes.c_char_p
+_lib.sbp_last_error_message.argtypes = []
+_lib.sbp_last_error_message.restype = ctypes.c_char_p
+
+
+class SbpError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.sbp_status_string(status).decode()
+        detail = _lib.sbp_last_error_message().decode()
+        super().__init__("%s: %s (%d) %s" % (where, msg, status, detail))
+
+
+def _check(status, where):
+    if status != 0:
+        raise SbpError(status, where)
+
+
+def lib():
+    return _lib
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class System:
+    """A two-mesh overset system on the current CUDA device.
+
+    ``wl`` is a workload dict (``workloads`` layout: meshes, params). States are exchanged
+    as numpy arrays (nvar, nj, ni) or as device tensors in the library's pitched layout.
+    """
+
+    def __init__(self, wl, dtype="f64", sigma_interface=0.5, sigma_physical=1.0, hole_cells=4):
+        import torch
+        self.torch = torch
+        self.dtype = dtype
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        self.meshes = wl["meshes"]
+        p = wl["params"]
+        descs = (MeshDesc * 2)()
+        self._keep = []
+        for k, m in enumerate(self.meshes):
+            d = descs[k]
+            d.n[0], d.n[1] = m["n"]
+            d.periodic[0], d.periodic[1] = int(m["periodic"][0]), int(m["periodic"][1])
+            for f in range(4):
+                d.bc[f] = BC[m["bc"][f]]
+            d.cartesian = int(m["cartesian"])
+            d.lo[0], d.lo[1] = m["lo"]
+            d.h[0], d.h[1] = m["h"]
+            x = np.ascontiguousarray(m["x"], dtype=np.float64)
+            y = np.ascontiguousarray(m["y"], dtype=np.float64)
+            self._keep += [x, y]
+            d.x = x.ctypes.data
+            d.y = y.ctypes.data
+            sh = m["shift"]
+            d.shift[0], d.shift[1], d.shift[2], d.shift[3] = sh[0][0], sh[0][1], sh[1][0], sh[1][1]
+        pr = Params()
+        pr.physics = PHYSICS[p["physics"]]
+        pr.dtype = DTYPE[dtype]
+        pr.gamma = p["gamma"]
+        pr.mu = p["mu"]
+        pr.pr = p["pr"]
+        pr.twall = p["twall"]
+        pr.omega_corner = p["omega_corner"]
+        pr.sigma_interface = sigma_interface
+        pr.sigma_physical = sigma_physical
+        pr.cfl = p["cfl"]
+        for v in range(4):
+            pr.qinf[v] = float(p["qinf"][v])
+        pr.order = p["order"]
+        pr.hist_len = p["hist_len"]
+        pr.step_ratio = p["step_ratio"]
+        pr.fast_mesh = p["fast_mesh"]
+        pr.hole_cells = hole_cells
+        self.params = p
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        _check(_lib.sbp_system_create(descs, 2, ctypes.byref(pr), ctypes.byref(h)), "sbp_system_create")
+        self.h = h
+        self.info = []
+        for k in range(2):
+            inf = MeshInfo()
+            _check(_lib.sbp_mesh_info_get(self.h, k, ctypes.byref(inf)), "sbp_mesh_info_get")
+            self.info.append(inf)
+        self.bound = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- layout helpers ------------------------------------------------------------------------
+    def empty_state(self, k, n=1):
+        inf = self.info[k]
+        t = self.torch.zeros((n, 4, inf.nj, inf.pitch), dtype=self.tdtype, device="cuda")
+        return t if n > 1 else t[0]
+
+    def to_device(self, k, q):
+        inf = self.info[k]
+        t = self.empty_state(k)
+        t[:, :, :inf.ni] = self.torch.from_numpy(np.ascontiguousarray(q)).to(self.tdtype).cuda()
+        return t
+
+    def to_host(self, k, t):
+        inf = self.info[k]
+        return t[..., :inf.ni].double().cpu().numpy()
+
+    # -- calls ---------------------------------------------------------------------------------
+    def tables(self, k):
+        inf = self.info[k]
+        n = inf.ni * inf.nj
+        nr = inf.n_receivers
+        ib = np.zeros(n, np.int8)
+        met = np.zeros(5 * n)
+        rec = np.zeros(max(nr, 1), np.int32)
+        base = np.zeros(max(2 * nr, 1), np.int32)
+        w = np.zeros(max(8 * nr, 1))
+        _check(_lib.sbp_get_tables(self.h, k, ib.ctypes.data, met.ctypes.data, rec.ctypes.data, base.ctypes.data,
+                                   w.ctypes.data), "sbp_get_tables")
+        return {"iblank": ib.reshape(inf.nj, inf.ni), "metrics": met.reshape(5, inf.nj, inf.ni),
+                "receivers": rec[:nr], "base": base[:2 * nr].reshape(nr, 2), "w": w[:8 * nr].reshape(nr, 8)}
+
+    def overset_interp(self, recv, q_donor, viscous_fluxes=True, stream=None):
+        nr = self.info[recv].n_receivers
+        qhat = self.torch.zeros((4, max(nr, 1)), dtype=self.tdtype, device="cuda")
+        fvhat = self.torch.zeros((6, max(nr, 1)), dtype=self.tdtype, device="cuda") if viscous_fluxes else None
+        _check(_lib.sbp_overset_interp(self.h, recv, _ptr(q_donor), _ptr(qhat), _ptr(fvhat), _stream(stream)),
+               "sbp_overset_interp")
+        return qhat[:, :nr], (fvhat[:, :nr] if fvhat is not None else None)
+
+    def rhs_eval(self, k, q_self, q_other, out=None, stream=None):
+        if out is None:
+            out = self.empty_state(k)
+        _check(_lib.sbp_rhs_eval(self.h, k, _ptr(q_self), _ptr(q_other), _ptr(out), _stream(stream)), "sbp_rhs_eval")
+        return out
+
+    def timestep(self, q0, q1, stream=None):
+        dt = (ctypes.c_double * 2)()
+        H = ctypes.c_double()
+        _check(_lib.sbp_timestep(self.h, _ptr(q0), _ptr(q1), ctypes.cast(dt, ctypes.c_void_p),
+                                 ctypes.cast(ctypes.pointer(H), ctypes.c_void_p), _stream(stream)), "sbp_timestep")
+        return [dt[0], dt[1]], H.value
+
+    def bind(self, q_host):
+        """Allocate and bind integrator buffers; load the initial states (numpy, per mesh)."""
+        self.bound = []
+        for k in range(2):
+            qa = self.to_device(k, q_host[k])
+            qb = self.empty_state(k)
+            hist = self.empty_state(k, n=self.params["hist_len"]) if self.params["hist_len"] > 1 else \
+                self.empty_state(k)[None]
+            _check(_lib.sbp_bind(self.h, k, _ptr(qa), _ptr(qb), _ptr(hist)), "sbp_bind")
+            self.bound.append((qa, qb, hist))
+
+    def current_state(self, k):
+        p = ctypes.c_void_p()
+        _check(_lib.sbp_current_state(self.h, k, ctypes.byref(p)), "sbp_current_state")
+        qa, qb, _ = self.bound[k]
+        return qa if p.value == qa.data_ptr() else qb
+
+    def mrab_init(self, H=0.0, stream=None):
+        _check(_lib.sbp_mrab_init(self.h, float(H), _stream(stream)), "sbp_mrab_init")
+
+    def mrab_step(self, n=1, stream=None):
+        _check(_lib.sbp_mrab_step(self.h, int(n), _stream(stream)), "sbp_mrab_step")
+
+    def mrab_time(self):
+        H = ctypes.c_double()
+        t = ctypes.c_double()
+        _check(_lib.sbp_mrab_time(self.h, ctypes.byref(H), ctypes.byref(t)), "sbp_mrab_time")
+        return H.value, t.value
+
+    PHASES = ("interp_slow", "rhs_slow", "interp_fast", "rhs_fast")
+
+    def profile_enable(self, on=True):
+        _check(_lib.sbp_profile_enable(self.h, int(bool(on))), "sbp_profile_enable")
+
+    def profile_read(self, reset=True):
+        """Per-phase device milliseconds and launch counts recorded by sbp_mrab_step."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int * 4)()
+        _check(_lib.sbp_profile_read(self.h, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p),
+                                     int(reset)), "sbp_profile_read")
+        return {p: (ms[i], n[i]) for i, p in enumerate(self.PHASES)}
+
+    def check(self, stream=None):
+        _check(_lib.sbp_check(self.h, _stream(stream)), "sbp_check")
+
+
+def exported_symbols():
+    """Names declared in include/sbp_mrab.h that the library must export."""
+    return sorted(list(_SIGS) + ["sbp_status_string", "sbp_last_error_message"])

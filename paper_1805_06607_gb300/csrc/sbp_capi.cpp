@@ -1,0 +1,615 @@
+// C ABI of the library: system creation (host setup + device tables), right-hand side and
+// interpolation calls, the time-step reduction, and the MRAB integrator with its Runge-Kutta
+// bootstrap. Device work is issued on the caller's stream; the GPU kernels live in
+// sbp_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sbp_device.h"
+#include "sbp_internal.h"
+
+using namespace sbp;
+
+namespace {
+thread_local std::string g_msg;
+
+sbp_status fail(sbp_status s, const std::string &msg) {
+  g_msg = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) return fail(SBP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct MeshDev {
+  uint8_t *cls = nullptr;
+  void *met = nullptr;
+  int *tile_sat = nullptr;
+  uint32_t *sat_ij = nullptr, *sat_code = nullptr;
+  int *sat_recv = nullptr;
+  double *sat_scale = nullptr;
+  int *base = nullptr;
+  double *w = nullptr;
+  void *qhat = nullptr, *fvhat = nullptr;
+  int tiles_x = 0, tiles_y = 0;
+  // bound integrator buffers
+  void *q[2] = {nullptr, nullptr};
+  void *hist = nullptr;
+  int cur = 0, head = -1, count = 0;
+};
+
+template <typename P>
+cudaError_t upload(P *&dst, const void *src, size_t bytes) {
+  cudaError_t e = cudaMalloc((void **)&dst, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  if (bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  return e;
+}
+}  // namespace
+
+struct sbp_system_s {
+  sbp_params p{};
+  MeshHost mh[2];
+  MeshDev md[2];
+  CoeffPlan plan;
+  size_t esz = 8;
+  int *d_err = nullptr;
+  unsigned long long *d_dt = nullptr;
+  double H = 0.0, t = 0.0;
+  bool initialised = false;
+  // phase timers
+  bool prof = false;
+  struct Pending {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[SBP_PHASE_COUNT] = {0, 0, 0, 0};
+  int prof_n[SBP_PHASE_COUNT] = {0, 0, 0, 0};
+
+  cudaEvent_t take_event() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // Launch `fn` on stream s, bracketed by an event pair when the timers are on.
+  template <typename Fn>
+  cudaError_t timed(int phase, cudaStream_t s, Fn &&fn) {
+    if (!prof) return fn();
+    Pending p{phase, take_event(), take_event()};
+    cudaEventRecord(p.a, s);
+    cudaError_t e = fn();
+    cudaEventRecord(p.b, s);
+    pending.push_back(p);
+    return e;
+  }
+  cudaError_t drain() {
+    for (auto &p : pending) {
+      cudaError_t e = cudaEventSynchronize(p.b);
+      if (e != cudaSuccess) return e;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p.a, p.b);
+      prof_ms[p.phase] += ms;
+      prof_n[p.phase] += 1;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+    return cudaSuccess;
+  }
+
+  ~sbp_system_s() {
+    for (auto &d : md) {
+      cudaFree(d.cls);
+      cudaFree(d.met);
+      cudaFree(d.tile_sat);
+      cudaFree(d.sat_ij);
+      cudaFree(d.sat_code);
+      cudaFree(d.sat_recv);
+      cudaFree(d.sat_scale);
+      cudaFree(d.base);
+      cudaFree(d.w);
+      cudaFree(d.qhat);
+      cudaFree(d.fvhat);
+    }
+    cudaFree(d_err);
+    cudaFree(d_dt);
+    drain();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+
+  bool viscous() const { return p.physics == SBP_NS; }
+  int fast() const { return p.fast_mesh; }
+  int slow() const { return 1 - p.fast_mesh; }
+  size_t state_elems(int k) const { return (size_t)kNvar * mh[k].pitch * mh[k].nj; }
+
+  DevMesh dev_mesh(int k) const {
+    DevMesh d{};
+    const MeshHost &m = mh[k];
+    d.ni = m.ni;
+    d.nj = m.nj;
+    d.pitch = m.pitch;
+    d.per_i = m.per[0];
+    d.per_j = m.per[1];
+    d.cart = m.cartesian;
+    d.field = (size_t)m.pitch * m.nj;
+    d.cls = md[k].cls;
+    d.met = md[k].met;
+    if (m.cartesian) {
+      d.mc[0] = m.h[1];
+      d.mc[1] = 0.0;
+      d.mc[2] = 0.0;
+      d.mc[3] = m.h[0];
+      d.mc[4] = 1.0 / (m.h[0] * m.h[1]);
+    }
+    return d;
+  }
+
+  Gas gas() const {
+    Gas g{};
+    g.gamma = p.gamma;
+    g.mu = viscous() ? p.mu : 0.0;
+    g.pr = p.pr;
+    g.twall = p.twall;
+    g.sig_int = p.sigma_interface;
+    g.sig_phys = p.sigma_physical;
+    for (int v = 0; v < 4; ++v) g.qinf[v] = p.qinf[v];
+    return g;
+  }
+
+  // Interpolate the donor state (optionally extrapolated) to recv's receivers, into recv's
+  // workspace.
+  cudaError_t interp(int recv, const void *q_donor, const void *const *hist, const double *beta, int nbeta,
+                     cudaStream_t s) {
+    InterpLaunch a{};
+    a.d = dev_mesh(1 - recv);
+    a.g = gas();
+    a.q = q_donor;
+    a.nbeta = nbeta;
+    for (int k = 0; k < nbeta; ++k) {
+      a.hist[k] = hist[k];
+      a.beta[k] = beta[k];
+    }
+    a.nrecv = (int)mh[recv].recv_pt.size();
+    a.base = md[recv].base;
+    a.w = md[recv].w;
+    a.qhat = md[recv].qhat;
+    a.fvhat = viscous() ? md[recv].fvhat : nullptr;
+    return launch_interp(a, p.dtype, viscous(), s);
+  }
+
+  RhsLaunch rhs_args(int k, const void *q) const {
+    RhsLaunch a{};
+    a.m = dev_mesh(k);
+    a.g = gas();
+    a.q = q;
+    a.tile_sat = md[k].tile_sat;
+    a.sat_ij = md[k].sat_ij;
+    a.sat_code = md[k].sat_code;
+    a.sat_recv = md[k].sat_recv;
+    a.sat_scale = md[k].sat_scale;
+    a.qhat = md[k].qhat;
+    a.fvhat = md[k].fvhat;
+    a.nrecv = (int)mh[k].recv_pt.size();
+    a.err = d_err;
+    return a;
+  }
+
+  cudaError_t rhs_plain(int k, const void *q_self, const void *q_other, void *out, cudaStream_t s) {
+    cudaError_t e = interp(k, q_other, nullptr, nullptr, 0, s);
+    if (e != cudaSuccess) return e;
+    RhsLaunch a = rhs_args(k, q_self);
+    a.mode = 0;
+    a.out = out;
+    return launch_rhs(a, p.dtype, viscous(), s);
+  }
+
+  void *hist_slot(int k, int slot) const { return (char *)md[k].hist + (size_t)slot * state_elems(k) * esz; }
+};
+
+extern "C" {
+
+const char *sbp_status_string(sbp_status s) {
+  switch (s) {
+    case SBP_OK: return "ok";
+    case SBP_ERR_ARG: return "invalid argument";
+    case SBP_ERR_SHAPE: return "invalid shape";
+    case SBP_ERR_DTYPE: return "unsupported element type";
+    case SBP_ERR_CUDA: return "CUDA error";
+    case SBP_ERR_NONFINITE: return "non-finite state";
+    case SBP_ERR_DONOR: return "no donor";
+    case SBP_ERR_TIMEOUT: return "device wait timed out";
+    case SBP_ERR_BOUNDS: return "index out of bounds";
+    case SBP_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char *sbp_last_error_message(void) { return g_msg.c_str(); }
+
+sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                             sbp_system_t *out) {
+  if (!meshes || !params || !out) return fail(SBP_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (n_meshes != 2) return fail(SBP_ERR_ARG, "exactly two meshes (background, fine) are supported");
+  const sbp_params &p = *params;
+  if (p.physics != SBP_EULER && p.physics != SBP_NS) return fail(SBP_ERR_ARG, "physics");
+  if (p.dtype != SBP_F64 && p.dtype != SBP_F32) return fail(SBP_ERR_DTYPE, "dtype");
+  if (p.fast_mesh != 0 && p.fast_mesh != 1) return fail(SBP_ERR_ARG, "fast_mesh");
+  if (!(p.gamma > 1.0) || p.mu < 0.0 || !(p.pr > 0.0)) return fail(SBP_ERR_ARG, "gas constants");
+  auto *S = new sbp_system_s();
+  std::unique_ptr<sbp_system_s> guard(S);
+  S->p = p;
+  if (S->p.hole_cells <= 0) S->p.hole_cells = 4;
+  S->esz = p.dtype == SBP_F64 ? 8 : 4;
+  std::string err;
+  sbp_status st;
+  for (int k = 0; k < 2; ++k)
+    if ((st = setup_mesh_basic(meshes[k], S->mh[k], err)) != SBP_OK) return fail(st, err);
+  if (!S->mh[0].cartesian) return fail(SBP_ERR_ARG, "the background (mesh 0) must be Cartesian");
+  double margin = S->p.hole_cells * std::max(S->mh[0].h[0], S->mh[0].h[1]);
+  if ((st = setup_holes(S->mh[0], S->mh[1], margin, err)) != SBP_OK) return fail(st, err);
+  for (int k = 0; k < 2; ++k) {
+    if ((st = setup_classes(S->mh[k], err)) != SBP_OK) return fail(st, err);
+    if ((st = setup_sat(S->mh[k], p.omega_corner, err)) != SBP_OK) return fail(st, err);
+  }
+  for (int k = 0; k < 2; ++k)
+    if ((st = setup_donors(S->mh[k], S->mh[1 - k], err)) != SBP_OK) return fail(st, err);
+  if ((st = build_plan(p.order, p.hist_len, p.step_ratio, S->plan, err)) != SBP_OK) return fail(st, err);
+
+  // device tables
+  CUDA_TRY(cudaMalloc((void **)&S->d_err, sizeof(int)));
+  CUDA_TRY(cudaMemset(S->d_err, 0, sizeof(int)));
+  CUDA_TRY(cudaMalloc((void **)&S->d_dt, 2 * sizeof(unsigned long long)));
+  for (int k = 0; k < 2; ++k) {
+    MeshHost &m = S->mh[k];
+    MeshDev &d = S->md[k];
+    size_t field = (size_t)m.pitch * m.nj;
+    std::vector<uint8_t> cls(field, 0xFF);
+    for (int j = 0; j < m.nj; ++j)
+      std::memcpy(&cls[(size_t)j * m.pitch], &m.cls[(size_t)j * m.ni], m.ni);
+    CUDA_TRY(upload(d.cls, cls.data(), field));
+    if (!m.cartesian) {
+      CUDA_TRY(cudaMalloc(&d.met, 5 * field * S->esz));
+      double *dx = nullptr, *dy = nullptr;
+      CUDA_TRY(upload(dx, m.x.data(), m.x.size() * sizeof(double)));
+      CUDA_TRY(upload(dy, m.y.data(), m.y.size() * sizeof(double)));
+      DevMesh dm = S->dev_mesh(k);
+      cudaError_t e = launch_metrics(dm, dx, dy, m.shift, d.met, p.dtype, 0);
+      cudaError_t e2 = cudaDeviceSynchronize();
+      cudaFree(dx);
+      cudaFree(dy);
+      CUDA_TRY(e);
+      CUDA_TRY(e2);
+    }
+    // SAT points grouped by tile
+    d.tiles_x = (m.ni + kTileX - 1) / kTileX;
+    d.tiles_y = (m.nj + kTileY - 1) / kTileY;
+    int nt = d.tiles_x * d.tiles_y;
+    size_t ns = m.sat_pt.size();
+    std::vector<int> order(ns);
+    for (size_t s = 0; s < ns; ++s) order[s] = (int)s;
+    auto tile_of = [&](int pt) { return (pt / m.ni) / kTileY * d.tiles_x + (pt % m.ni) / kTileX; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tile_of(m.sat_pt[a]) < tile_of(m.sat_pt[b]); });
+    std::vector<int> toff(nt + 1, 0);
+    std::vector<uint32_t> ij(ns), code(ns);
+    std::vector<int> recv(ns);
+    std::vector<double> scale(ns);
+    for (size_t s = 0; s < ns; ++s) {
+      int o = order[s], pt = m.sat_pt[o];
+      toff[tile_of(pt) + 1]++;
+      ij[s] = (uint32_t)(pt % m.ni) | ((uint32_t)(pt / m.ni) << 16);
+      code[s] = m.sat_code[o];
+      recv[s] = m.sat_recv[o];
+      scale[s] = m.sat_scale[o];
+    }
+    for (int t = 0; t < nt; ++t) toff[t + 1] += toff[t];
+    CUDA_TRY(upload(d.tile_sat, toff.data(), toff.size() * sizeof(int)));
+    CUDA_TRY(upload(d.sat_ij, ij.data(), ns * sizeof(uint32_t)));
+    CUDA_TRY(upload(d.sat_code, code.data(), ns * sizeof(uint32_t)));
+    CUDA_TRY(upload(d.sat_recv, recv.data(), ns * sizeof(int)));
+    CUDA_TRY(upload(d.sat_scale, scale.data(), ns * sizeof(double)));
+    size_t nr = m.recv_pt.size();
+    CUDA_TRY(upload(d.base, m.donor_base.data(), 2 * nr * sizeof(int)));
+    CUDA_TRY(upload(d.w, m.donor_w.data(), 8 * nr * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&d.qhat, (4 * nr + 1) * S->esz));
+    CUDA_TRY(cudaMalloc(&d.fvhat, (6 * nr + 1) * S->esz));
+  }
+  CUDA_TRY(cudaDeviceSynchronize());
+  *out = guard.release();
+  return SBP_OK;
+}
+
+sbp_status sbp_system_destroy(sbp_system_t sys) {
+  delete sys;
+  return SBP_OK;
+}
+
+sbp_status sbp_mesh_info_get(sbp_system_t S, int k, sbp_mesh_info *info) {
+  if (!S || !info || k < 0 || k > 1) return fail(SBP_ERR_ARG, "bad argument");
+  const MeshHost &m = S->mh[k];
+  info->ni = m.ni;
+  info->nj = m.nj;
+  info->pitch = m.pitch;
+  info->field_elems = (size_t)m.pitch * m.nj;
+  info->state_bytes = S->state_elems(k) * S->esz;
+  info->hist_bytes = info->state_bytes * S->p.hist_len;
+  info->nvar = kNvar;
+  info->n_holes = (int)std::count(m.active.begin(), m.active.end(), 0);
+  info->n_receivers = (int)m.recv_pt.size();
+  info->n_sat_points = (int)m.sat_pt.size();
+  info->elem_size = (int)S->esz;
+  return SBP_OK;
+}
+
+sbp_status sbp_get_tables(sbp_system_t S, int k, signed char *iblank, double *metrics, int *receivers,
+                          int *donor_base, double *donor_w) {
+  if (!S || k < 0 || k > 1) return fail(SBP_ERR_ARG, "bad argument");
+  const MeshHost &m = S->mh[k];
+  size_t n = (size_t)m.ni * m.nj, field = (size_t)m.pitch * m.nj;
+  if (iblank)
+    for (size_t p = 0; p < n; ++p) iblank[p] = m.active[p];
+  if (metrics) {
+    if (m.cartesian) {
+      double c[5] = {m.h[1], 0.0, 0.0, m.h[0], 1.0 / (m.h[0] * m.h[1])};
+      for (int q = 0; q < 5; ++q)
+        for (size_t p = 0; p < n; ++p) metrics[q * n + p] = m.active[p] ? c[q] : (q == 0 || q == 3 || q == 4 ? 1.0 : 0.0);
+    } else {
+      std::vector<char> buf(5 * field * S->esz);
+      CUDA_TRY(cudaMemcpy(buf.data(), S->md[k].met, buf.size(), cudaMemcpyDeviceToHost));
+      for (int q = 0; q < 5; ++q)
+        for (int j = 0; j < m.nj; ++j)
+          for (int i = 0; i < m.ni; ++i) {
+            size_t src = q * field + (size_t)j * m.pitch + i;
+            metrics[q * n + (size_t)j * m.ni + i] =
+                S->esz == 8 ? ((double *)buf.data())[src] : (double)((float *)buf.data())[src];
+          }
+    }
+  }
+  size_t nr = m.recv_pt.size();
+  if (receivers) std::memcpy(receivers, m.recv_pt.data(), nr * sizeof(int));
+  if (donor_base) std::memcpy(donor_base, m.donor_base.data(), 2 * nr * sizeof(int));
+  if (donor_w) std::memcpy(donor_w, m.donor_w.data(), 8 * nr * sizeof(double));
+  return SBP_OK;
+}
+
+sbp_status sbp_overset_interp(sbp_system_t S, int recv, const void *q_donor, void *qhat, void *fvhat, void *stream) {
+  if (!S || recv < 0 || recv > 1 || !q_donor || !qhat) return fail(SBP_ERR_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  InterpLaunch a{};
+  a.d = S->dev_mesh(1 - recv);
+  a.g = S->gas();
+  a.q = q_donor;
+  a.nrecv = (int)S->mh[recv].recv_pt.size();
+  a.base = S->md[recv].base;
+  a.w = S->md[recv].w;
+  a.qhat = qhat;
+  a.fvhat = S->viscous() ? fvhat : nullptr;
+  CUDA_TRY(launch_interp(a, S->p.dtype, S->viscous(), s));
+  return SBP_OK;
+}
+
+sbp_status sbp_rhs_eval(sbp_system_t S, int k, const void *q_self, const void *q_other, void *rhs, void *stream) {
+  if (!S || k < 0 || k > 1 || !q_self || !q_other || !rhs) return fail(SBP_ERR_ARG, "bad argument");
+  CUDA_TRY(S->rhs_plain(k, q_self, q_other, rhs, (cudaStream_t)stream));
+  return SBP_OK;
+}
+
+sbp_status sbp_timestep(sbp_system_t S, const void *q0, const void *q1, double *dt_mesh, double *H, void *stream) {
+  if (!S || !q0 || !q1) return fail(SBP_ERR_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const void *qs[2] = {q0, q1};
+  for (int k = 0; k < 2; ++k) CUDA_TRY(launch_dt(S->dev_mesh(k), S->gas(), qs[k], S->p.dtype, S->d_dt + k, s));
+  unsigned long long bits[2];
+  CUDA_TRY(cudaMemcpyAsync(bits, S->d_dt, sizeof(bits), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  double dt[2];
+  for (int k = 0; k < 2; ++k) std::memcpy(&dt[k], &bits[k], sizeof(double));
+  if (dt_mesh) {
+    dt_mesh[0] = dt[0];
+    dt_mesh[1] = dt[1];
+  }
+  if (H) *H = std::min(S->p.cfl * dt[S->slow()], S->p.step_ratio * S->p.cfl * dt[S->fast()]);
+  return SBP_OK;
+}
+
+sbp_status sbp_bind(sbp_system_t S, int k, void *qa, void *qb, void *hist) {
+  if (!S || k < 0 || k > 1 || !qa || !qb || !hist) return fail(SBP_ERR_ARG, "bad argument");
+  MeshDev &d = S->md[k];
+  d.q[0] = qa;
+  d.q[1] = qb;
+  d.hist = hist;
+  d.cur = 0;
+  d.head = -1;
+  d.count = 0;
+  S->initialised = false;
+  return SBP_OK;
+}
+
+sbp_status sbp_current_state(sbp_system_t S, int k, void **q) {
+  if (!S || k < 0 || k > 1 || !q) return fail(SBP_ERR_ARG, "bad argument");
+  *q = S->md[k].q[S->md[k].cur];
+  return SBP_OK;
+}
+
+sbp_status sbp_mrab_init(sbp_system_t S, double H, void *stream) {
+  if (!S) return fail(SBP_ERR_ARG, "null system");
+  for (int k = 0; k < 2; ++k)
+    if (!S->md[k].hist) return fail(SBP_ERR_STATE, "buffers not bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!(H > 0.0)) {
+    sbp_status st = sbp_timestep(S, S->md[0].q[S->md[0].cur], S->md[1].q[S->md[1].cur], nullptr, &H, stream);
+    if (st != SBP_OK) return st;
+  }
+  const int m = S->plan.m, sr = S->plan.sr, F = S->fast(), Sl = S->slow();
+  const double h = H / sr;
+  // stage buffers: per mesh a stage state, k1 (when not recorded) and k2/k3
+  void *ystage[2], *k1tmp[2], *k23[2];
+  std::vector<void *> allocs;
+  for (int k = 0; k < 2; ++k) {
+    size_t b = S->state_elems(k) * S->esz;
+    CUDA_TRY(cudaMalloc(&ystage[k], b));
+    allocs.push_back(ystage[k]);
+    CUDA_TRY(cudaMalloc(&k1tmp[k], b));
+    allocs.push_back(k1tmp[k]);
+    CUDA_TRY(cudaMalloc(&k23[k], b));
+    allocs.push_back(k23[k]);
+    CUDA_TRY(cudaMemsetAsync(ystage[k], 0, b, s));
+    S->md[k].head = -1;
+    S->md[k].count = 0;
+  }
+  auto release = [&]() {
+    cudaStreamSynchronize(s);
+    for (void *ptr : allocs) cudaFree(ptr);
+  };
+  const int nsteps = (m - 1) * sr;
+  cudaError_t e = cudaSuccess;
+  for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+    void *y[2] = {S->md[0].q[S->md[0].cur], S->md[1].q[S->md[1].cur]};
+    void *k1[2] = {k1tmp[0], k1tmp[1]};
+    bool rec_f = step >= nsteps - (m - 1), rec_s = step % sr == 0;
+    if (rec_f) {
+      MeshDev &d = S->md[F];
+      d.head = (d.head + 1) % m;
+      d.count++;
+      k1[F] = S->hist_slot(F, d.head);
+    }
+    if (rec_s) {
+      MeshDev &d = S->md[Sl];
+      d.head = (d.head + 1) % m;
+      d.count++;
+      k1[Sl] = S->hist_slot(Sl, d.head);
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = S->rhs_plain(k, y[k], y[1 - k], k1[k], s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = launch_axpy(y[k], k1[k], h / 3.0, nullptr, 0.0, ystage[k], S->state_elems(k), S->p.dtype, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = S->rhs_plain(k, ystage[k], ystage[1 - k], k23[k], s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = launch_axpy(y[k], k23[k], 2.0 * h / 3.0, nullptr, 0.0, ystage[k], S->state_elems(k), S->p.dtype, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = S->rhs_plain(k, ystage[k], ystage[1 - k], k23[k], s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = launch_axpy(y[k], k1[k], h / 4.0, k23[k], 3.0 * h / 4.0, y[k], S->state_elems(k), S->p.dtype, s);
+  }
+  release();
+  if (e != cudaSuccess) return fail(SBP_ERR_CUDA, std::string("bootstrap: ") + cudaGetErrorString(e));
+  S->H = H;
+  S->t = 0.0;
+  S->initialised = true;
+  return SBP_OK;
+}
+
+sbp_status sbp_mrab_step(sbp_system_t S, int n, void *stream) {
+  if (!S || n < 0) return fail(SBP_ERR_ARG, "bad argument");
+  if (!S->initialised) return fail(SBP_ERR_STATE, "sbp_mrab_init has not run");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int m = S->plan.m, sr = S->plan.sr, F = S->fast(), Sl = S->slow();
+  const double H = S->H, h = H / sr;
+  for (int step = 0; step < n; ++step) {
+    MeshDev &ds = S->md[Sl];
+    MeshDev &df = S->md[F];
+    // slow mesh: receivers from the fast state at t, right-hand side at t, s(t+H) into the
+    // other buffer (s(t) stays for the extrapolation of the micro steps)
+    CUDA_TRY(S->timed(SBP_PHASE_INTERP_SLOW, s, [&] { return S->interp(Sl, df.q[df.cur], nullptr, nullptr, 0, s); }));
+    {
+      int slot = (ds.head + 1) % m;
+      RhsLaunch a = S->rhs_args(Sl, ds.q[ds.cur]);
+      a.mode = 1;
+      a.out = S->hist_slot(Sl, slot);
+      a.qnext = ds.q[1 - ds.cur];
+      a.nold = m - 1;
+      for (int k = 0; k < m - 1; ++k) {
+        a.hold[k] = S->hist_slot(Sl, (slot + 1 + k) % m);
+        a.alpha[k] = S->plan.ab[k] * H;
+      }
+      a.alpha[m - 1] = S->plan.ab[m - 1] * H;
+      CUDA_TRY(S->timed(SBP_PHASE_RHS_SLOW, s, [&] { return launch_rhs(a, S->p.dtype, S->viscous(), s); }));
+      ds.head = slot;
+    }
+    // fast mesh: step_ratio micro steps, receivers fed by the slow extrapolant
+    for (int j = 0; j < sr; ++j) {
+      const void *hs[kMaxHist];
+      double beta[kMaxHist];
+      int nb = 0;
+      if (j > 0) {
+        nb = m;
+        for (int k = 0; k < m; ++k) {
+          hs[k] = S->hist_slot(Sl, (ds.head + 1 + k) % m);
+          beta[k] = S->plan.ext[j][k] * H;
+        }
+      }
+      CUDA_TRY(S->timed(SBP_PHASE_INTERP_FAST, s, [&] { return S->interp(F, ds.q[ds.cur], hs, beta, nb, s); }));
+      int slot = (df.head + 1) % m;
+      RhsLaunch a = S->rhs_args(F, df.q[df.cur]);
+      a.mode = 1;
+      a.out = S->hist_slot(F, slot);
+      a.qnext = df.q[1 - df.cur];
+      a.nold = m - 1;
+      for (int k = 0; k < m - 1; ++k) {
+        a.hold[k] = S->hist_slot(F, (slot + 1 + k) % m);
+        a.alpha[k] = S->plan.ab[k] * h;
+      }
+      a.alpha[m - 1] = S->plan.ab[m - 1] * h;
+      CUDA_TRY(S->timed(SBP_PHASE_RHS_FAST, s, [&] { return launch_rhs(a, S->p.dtype, S->viscous(), s); }));
+      df.head = slot;
+      df.cur ^= 1;
+    }
+    ds.cur ^= 1;
+    S->t += H;
+  }
+  return SBP_OK;
+}
+
+sbp_status sbp_mrab_time(sbp_system_t S, double *H, double *t) {
+  if (!S) return fail(SBP_ERR_ARG, "null system");
+  if (H) *H = S->H;
+  if (t) *t = S->t;
+  return SBP_OK;
+}
+
+sbp_status sbp_profile_enable(sbp_system_t S, int enable) {
+  if (!S) return fail(SBP_ERR_ARG, "null system");
+  S->prof = enable != 0;
+  return SBP_OK;
+}
+
+sbp_status sbp_profile_read(sbp_system_t S, double *ms, int *launches, int reset) {
+  if (!S) return fail(SBP_ERR_ARG, "null system");
+  CUDA_TRY(S->drain());
+  for (int k = 0; k < SBP_PHASE_COUNT; ++k) {
+    if (ms) ms[k] = S->prof_ms[k];
+    if (launches) launches[k] = S->prof_n[k];
+    if (reset) {
+      S->prof_ms[k] = 0.0;
+      S->prof_n[k] = 0;
+    }
+  }
+  return SBP_OK;
+}
+
+sbp_status sbp_check(sbp_system_t S, void *stream) {
+  if (!S) return fail(SBP_ERR_ARG, "null system");
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int e = 0;
+  CUDA_TRY(cudaMemcpy(&e, S->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(S->d_err, 0, sizeof(int)));
+  if (e) return fail((sbp_status)e, "device error word set");
+  return SBP_OK;
+}
+
+}  // extern "C"

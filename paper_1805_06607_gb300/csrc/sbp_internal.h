@@ -1,0 +1,72 @@
+// Internal types shared by the host setup, the C ABI and the CUDA kernels of the library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sbp_mrab.h"
+
+namespace sbp {
+
+constexpr int kMaxHist = 6;   // longest Adams-Bashforth history supported (AB46)
+constexpr int kNvar = 4;      // 2D conserved variables
+
+// Stencil class of a point along one direction, 4 bits: kind in bits 2-3, closure row in
+// bits 0-1. Interior: 5-point central row; left/right: closure row r counted from the
+// segment's low/high end; hole: inactive.
+enum : uint8_t { kInterior = 0, kLeft = 1, kRight = 2, kHole = 3 };
+inline uint8_t cls_code(int kind, int row) { return (uint8_t)((kind << 2) | row); }
+
+// SAT term kinds (physical and interface boundaries).
+enum : int { kTermInterface = 1, kTermFarfield = 2, kTermWall = 3 };
+
+// Tile of the fused right-hand-side kernels (points per CTA along i and j).
+struct TileShape {
+  int tx, ty;
+};
+
+// Host-side products of the setup of one mesh.
+struct MeshHost {
+  int ni = 0, nj = 0, pitch = 0;
+  int per[2] = {0, 0};
+  int bc[4] = {0, 0, 0, 0};
+  int cartesian = 0;
+  double lo[2] = {0, 0}, h[2] = {0, 0};
+  double shift[4] = {0, 0, 0, 0};
+  std::vector<double> x, y;          // nj*ni, i fastest
+  std::vector<int8_t> active;        // nj*ni
+  std::vector<uint8_t> cls;          // nj*ni: (class_j << 4) | class_i
+  // SAT points: one entry per point with at least one term; terms packed 4 bits each
+  // (bit 0 direction, bit 1 side (0 = low face "+", 1 = high face "-"), bits 2-3 kind),
+  // count in bits 0-2 and terms from bit 3 upward.
+  std::vector<int> sat_pt;           // j*ni+i
+  std::vector<uint32_t> sat_code;
+  std::vector<int> sat_recv;         // receiver index or -1
+  std::vector<double> sat_scale;     // Omega for corner interface points, else 1
+  // receivers of this mesh (sorted by point) and their donors on the other mesh
+  std::vector<int> recv_pt;
+  std::vector<int> donor_base;       // 2 per receiver
+  std::vector<double> donor_w;       // 8 per receiver
+};
+
+// Adams-Bashforth / MRAB coefficient plan (Sec. 3.1-3.3), weights oldest first, in units of
+// the step (multiply by h or H).
+struct CoeffPlan {
+  int order = 3, m = 3, sr = 1;
+  std::vector<double> ab;                 // m: one step over [0, 1] on the nodes -(m-1)..0
+  std::vector<std::vector<double>> ext;   // sr entries: slow extrapolant integrated over [0, j/sr]
+};
+
+// Host setup (sbp_setup.cpp).
+sbp_status setup_mesh_basic(const sbp_mesh_desc &d, MeshHost &m, std::string &err);
+sbp_status setup_holes(MeshHost &bg, const MeshHost &fine, double margin, std::string &err);
+sbp_status setup_classes(MeshHost &m, std::string &err);
+sbp_status setup_sat(MeshHost &m, double omega_corner, std::string &err);
+sbp_status setup_donors(MeshHost &recv, const MeshHost &donor, std::string &err);
+sbp_status solve_ab_weights(const std::vector<double> &nodes, double a, double b, int order,
+                            std::vector<double> &alpha);
+sbp_status build_plan(int order, int m, int sr, CoeffPlan &plan, std::string &err);
+
+}  // namespace sbp

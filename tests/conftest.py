@@ -19,3 +19,13 @@ def golden(name):
             if line:
                 rows.append(line.split())
     return rows
+
+
+def build_library():
+    """Build the CUDA library in-tree (by path: importing the package needs the built file)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "sbp_build", os.path.join(ROOT, "paper_1805_06607_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
