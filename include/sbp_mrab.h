@@ -124,6 +124,22 @@ sbp_status sbp_overset_interp(sbp_system_t sys, int recv_mesh, const void *q_don
 sbp_status sbp_rhs_eval(sbp_system_t sys, int mesh, const void *q_self, const void *q_other, void *rhs,
                         void *stream);
 
+/* sbp_rhs_eval for callers that cannot have device memory allocated for them while they run:
+ * code that evaluates the right-hand side inside a CUDA stream capture in global mode (where
+ * cudaMalloc is illegal), or in a process whose device memory is all reserved up front by
+ * another allocator. The paper has no counterpart; the result equals sbp_rhs_eval's. The
+ * receiver workspace (interpolated states and viscous fluxes) lives in one fixed device array
+ * of SBP_NOALLOC_MAX_RECEIVERS * 10 doubles (640 KiB) that the library defines and that every
+ * GPU loading the library keeps until the process exits; the call allocates and frees nothing.
+ * Meshes with more receivers than SBP_NOALLOC_MAX_RECEIVERS get SBP_ERR_SHAPE. All calls share
+ * the array and nothing in it needs to start at zero (the gather overwrites each entry it later
+ * reads); calls that overlap on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller. The first call on each device looks up the array's device address
+ * (with that device current); make that first call before any stream capture. */
+#define SBP_NOALLOC_MAX_RECEIVERS 8192
+sbp_status sbp_rhs_eval_noalloc(sbp_system_t sys, int mesh, const void *q_self, const void *q_other, void *rhs,
+                                void *stream);
+
 /* Stable step estimate of Sec. 4.1 eqs. (ts_inv), (ts_visc), (ts_overall) on both meshes for
  * the given states, without the CFL factor (dt_mesh[2], host), and the macro step
  * H = min(cfl dt_slow, step_ratio cfl dt_fast) (host). Synchronises the stream. */

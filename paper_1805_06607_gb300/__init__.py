@@ -59,6 +59,7 @@ _SIGS = {
     "sbp_get_tables": [_P, _I, _P, _P, _P, _P, _P],
     "sbp_overset_interp": [_P, _I, _P, _P, _P, _P],
     "sbp_rhs_eval": [_P, _I, _P, _P, _P, _P],
+    "sbp_rhs_eval_noalloc": [_P, _I, _P, _P, _P, _P],
     "sbp_timestep": [_P, _P, _P, _P, _P, _P],
     "sbp_bind": [_P, _I, _P, _P, _P],
     "sbp_current_state": [_P, _I, ctypes.POINTER(_P)],

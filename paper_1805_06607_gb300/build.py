@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsbpmrab.so")
-SOURCES = ["sbp_kernels.cu", "sbp_capi.cpp", "sbp_setup.cpp"]
+SOURCES = ["sbp_kernels.cu", "sbp_capi.cpp", "sbp_setup.cpp", "sbp_noalloc.cu"]
 HEADERS = ["sbp_internal.h", "sbp_device.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

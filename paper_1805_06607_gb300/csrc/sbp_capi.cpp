@@ -410,6 +410,27 @@ sbp_status sbp_rhs_eval(sbp_system_t S, int k, const void *q_self, const void *q
   return SBP_OK;
 }
 
+sbp_status sbp_rhs_eval_noalloc(sbp_system_t S, int k, const void *q_self, const void *q_other, void *rhs,
+                                void *stream) {
+  if (!S || k < 0 || k > 1 || !q_self || !q_other || !rhs) return fail(SBP_ERR_ARG, "bad argument");
+  int nrecv = (int)S->mh[k].recv_pt.size();
+  if (nrecv > SBP_NOALLOC_MAX_RECEIVERS)
+    return fail(SBP_ERR_SHAPE, "mesh has " + std::to_string(nrecv) + " receivers; sbp_rhs_eval_noalloc supports " +
+                                   std::to_string(SBP_NOALLOC_MAX_RECEIVERS));
+  InterpLaunch ia{};
+  ia.d = S->dev_mesh(1 - k);
+  ia.g = S->gas();
+  ia.q = q_other;
+  ia.nrecv = nrecv;
+  ia.base = S->md[k].base;
+  ia.w = S->md[k].w;
+  RhsLaunch ra = S->rhs_args(k, q_self);
+  ra.mode = 0;
+  ra.out = rhs;
+  CUDA_TRY(rhs_eval_static_scratch(ia, ra, S->p.dtype, S->viscous(), S->esz, (cudaStream_t)stream));
+  return SBP_OK;
+}
+
 sbp_status sbp_timestep(sbp_system_t S, const void *q0, const void *q1, double *dt_mesh, double *H, void *stream) {
   if (!S || !q0 || !q1) return fail(SBP_ERR_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;

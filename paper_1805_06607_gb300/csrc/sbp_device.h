@@ -78,5 +78,9 @@ cudaError_t launch_metrics(const DevMesh &m, const double *x, const double *y, c
 cudaError_t launch_axpy(const void *y, const void *k1, double c1, const void *k2, double c2, void *y_out, size_t n,
                         int dtype, cudaStream_t s);
 size_t rhs_smem_bytes(int dtype, bool viscous, bool curvilinear);
+// Interpolation + right-hand side with the receiver workspace in the library's fixed device
+// array (sbp_noalloc.cu); the qhat/fvhat pointers of the descriptors are replaced.
+cudaError_t rhs_eval_static_scratch(InterpLaunch ia, RhsLaunch ra, int dtype, bool viscous, size_t elem,
+                                    cudaStream_t s);
 
 }  // namespace sbp
