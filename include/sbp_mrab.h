@@ -89,6 +89,8 @@ typedef struct {
   size_t hist_bytes;    /* hist_len * state_bytes */
   int nvar, n_holes, n_receivers, n_sat_points;
   int elem_size;        /* 8 (F64) or 4 (F32) */
+  int strip_width;      /* columns per CTA of the fused right-hand-side kernel */
+  int rows_per_cta;     /* rows per CTA (chosen by the autotuner, see sbp_autotune) */
 } sbp_mesh_info;
 
 /* Create a two-mesh overset system (mesh 0 = background, mesh 1 = the overset fine mesh) and
@@ -163,6 +165,21 @@ sbp_status sbp_mrab_init(sbp_system_t sys, double H, void *stream);
  * receivers; slow RHS fused with the slow state update; then step_ratio fused fast RHS +
  * fast updates, each fed by the slow extrapolant at its micro time. Asynchronous. */
 sbp_status sbp_mrab_step(sbp_system_t sys, int n, void *stream);
+
+/* Whether sbp_mrab_step replays CUDA graphs (default 1) or launches kernel by kernel (0).
+ * With graphs, each macro step is one graph launch on the caller's stream: the graph is
+ * captured once per ring/buffer phase (at most 4 hist_len^2 of them, on first use) and runs
+ * the slow right-hand side and the first fast micro step on parallel branches, which both
+ * depend only on the states at t. Results are identical in both modes. The phase timers
+ * (sbp_profile_enable) force the kernel-by-kernel mode while they are on. */
+sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
+
+/* Autotuner of the fused right-hand-side kernel's block shape (rows per CTA; the strip width
+ * is fixed by the CTA size): for each mesh it times the kernel on the bound state at several
+ * shapes and keeps the fastest (reported by sbp_mesh_info_get). It runs at the end of
+ * sbp_mrab_init while enabled (the default); enabling it on an initialised system runs it at
+ * once. Synchronises the stream. */
+sbp_status sbp_autotune(sbp_system_t sys, int enable, void *stream);
 
 /* Macro step size H and elapsed time since the end of the bootstrap. */
 sbp_status sbp_mrab_time(sbp_system_t sys, double *H, double *t);

@@ -46,7 +46,8 @@ class MeshInfo(ctypes.Structure):
     _fields_ = [("ni", ctypes.c_int), ("nj", ctypes.c_int), ("pitch", ctypes.c_int),
                 ("field_elems", ctypes.c_size_t), ("state_bytes", ctypes.c_size_t),
                 ("hist_bytes", ctypes.c_size_t), ("nvar", ctypes.c_int), ("n_holes", ctypes.c_int),
-                ("n_receivers", ctypes.c_int), ("n_sat_points", ctypes.c_int), ("elem_size", ctypes.c_int)]
+                ("n_receivers", ctypes.c_int), ("n_sat_points", ctypes.c_int), ("elem_size", ctypes.c_int),
+                ("strip_width", ctypes.c_int), ("rows_per_cta", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -68,6 +69,8 @@ _SIGS = {
     "sbp_mrab_time": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "sbp_check": [_P, _P],
     "sbp_profile_enable": [_P, _I],
+    "sbp_use_graphs": [_P, _I],
+    "sbp_autotune": [_P, _I, _P],
     "sbp_profile_read": [_P, _P, _P, _I],
 }
 for _name, _args in _SIGS.items():
@@ -262,6 +265,17 @@ class System:
         return H.value, t.value
 
     PHASES = ("interp_slow", "rhs_slow", "interp_fast", "rhs_fast")
+
+    def mesh_info(self, k):
+        inf = MeshInfo()
+        _check(_lib.sbp_mesh_info_get(self.h, k, ctypes.byref(inf)), "sbp_mesh_info_get")
+        return inf
+
+    def autotune(self, on=True, stream=None):
+        _check(_lib.sbp_autotune(self.h, int(bool(on)), _stream(stream)), "sbp_autotune")
+
+    def use_graphs(self, on=True):
+        _check(_lib.sbp_use_graphs(self.h, int(bool(on))), "sbp_use_graphs")
 
     def profile_enable(self, on=True):
         _check(_lib.sbp_profile_enable(self.h, int(bool(on))), "sbp_profile_enable")

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -34,13 +35,22 @@ struct MeshDev {
   uint8_t *cls = nullptr;
   void *met = nullptr;
   int *tile_sat = nullptr;
+  void *flux = nullptr;
   uint32_t *sat_ij = nullptr, *sat_code = nullptr;
   int *sat_recv = nullptr;
   double *sat_scale = nullptr;
   int *base = nullptr;
   double *w = nullptr;
+  void *wt = nullptr;   // donor weights in the compute type
+  void *sat = nullptr;  // per SAT point: 4 penalty terms
   void *qhat = nullptr, *fvhat = nullptr;
-  int tiles_x = 0, tiles_y = 0;
+  // distinct donor points of this mesh's receivers, per-receiver indices into them, and the
+  // per-step donor values (10 planes per extrapolation set)
+  uint32_t *dpts = nullptr;
+  int *didx = nullptr;
+  void *dv = nullptr;
+  int ndv = 0, dv_sets = 0;
+  int rows_per_cta = 16;
   // bound integrator buffers
   void *q[2] = {nullptr, nullptr};
   void *hist = nullptr;
@@ -76,6 +86,18 @@ struct sbp_system_s {
   std::vector<cudaEvent_t> pool;
   double prof_ms[SBP_PHASE_COUNT] = {0, 0, 0, 0};
   int prof_n[SBP_PHASE_COUNT] = {0, 0, 0, 0};
+  // CUDA graphs of one macro step, one per ring/buffer phase (the kernel arguments differ by
+  // phase), captured on internal streams with the slow RHS and the first fast micro step on
+  // parallel branches.
+  bool use_graph = true;
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::map<uint64_t, cudaGraphExec_t> graphs;
+
+  void clear_graphs() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
 
   cudaEvent_t take_event() {
     if (!pool.empty()) {
@@ -118,19 +140,30 @@ struct sbp_system_s {
       cudaFree(d.cls);
       cudaFree(d.met);
       cudaFree(d.tile_sat);
+      cudaFree(d.flux);
       cudaFree(d.sat_ij);
       cudaFree(d.sat_code);
       cudaFree(d.sat_recv);
       cudaFree(d.sat_scale);
       cudaFree(d.base);
       cudaFree(d.w);
+      cudaFree(d.wt);
+      cudaFree(d.sat);
       cudaFree(d.qhat);
       cudaFree(d.fvhat);
+      cudaFree(d.dpts);
+      cudaFree(d.didx);
+      cudaFree(d.dv);
     }
     cudaFree(d_err);
     cudaFree(d_dt);
     drain();
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    clear_graphs();
+    if (cap) cudaStreamDestroy(cap);
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
   }
 
   bool viscous() const { return p.physics == SBP_NS; }
@@ -199,6 +232,8 @@ struct sbp_system_s {
     a.g = gas();
     a.q = q;
     a.tile_sat = md[k].tile_sat;
+    a.rows_per_cta = md[k].rows_per_cta;
+    a.flux = md[k].flux;
     a.sat_ij = md[k].sat_ij;
     a.sat_code = md[k].sat_code;
     a.sat_recv = md[k].sat_recv;
@@ -207,7 +242,40 @@ struct sbp_system_s {
     a.fvhat = md[k].fvhat;
     a.nrecv = (int)mh[k].recv_pt.size();
     a.err = d_err;
+    a.sat = md[k].sat;
+    a.nsat = (int)mh[k].sat_pt.size();
+    a.dwt = md[k].wt;
+    fill_consts(k, a.cf);
+    fill_consts(k, a.cd);
     return a;
+  }
+
+  template <typename T>
+  void fill_consts(int k, KConst<T> &c) const {
+    const double g = p.gamma, mu = viscous() ? p.mu : 0.0;
+    c.gam = (T)g;
+    c.g1 = (T)(g - 1.0);
+    c.mu = (T)mu;
+    c.kap = (T)(mu / (p.pr * (g - 1.0)));
+    c.mu43 = (T)(4.0 / 3.0 * mu);
+    c.mu23 = (T)(2.0 / 3.0 * mu);
+    c.sig_int = (T)p.sigma_interface;
+    c.sig_phys = (T)p.sigma_physical;
+    c.tw = (T)(p.twall / (g * (g - 1.0)));
+    for (int v = 0; v < 4; ++v) c.qinf[v] = (T)p.qinf[v];
+    const MeshHost &m = mh[k];
+    if (m.cartesian) {
+      c.mc[0] = (T)m.h[1];
+      c.mc[1] = (T)0;
+      c.mc[2] = (T)0;
+      c.mc[3] = (T)m.h[0];
+      c.mc[4] = (T)(1.0 / (m.h[0] * m.h[1]));
+      c.jx = (T)(1.0 / m.h[0]);
+      c.jy = (T)(1.0 / m.h[1]);
+    } else {
+      for (int q = 0; q < 5; ++q) c.mc[q] = (T)0;
+      c.jx = c.jy = (T)0;
+    }
   }
 
   cudaError_t rhs_plain(int k, const void *q_self, const void *q_other, void *out, cudaStream_t s) {
@@ -220,6 +288,179 @@ struct sbp_system_s {
   }
 
   void *hist_slot(int k, int slot) const { return (char *)md[k].hist + (size_t)slot * state_elems(k) * esz; }
+
+  // Donor values of mesh `recv`'s receivers from the other mesh's state at `q`, for the
+  // extrapolation sets [set0, set0 + nsets) of the plan (set j: slow extrapolant over [0, j/SR]).
+  cudaError_t donor_vals(int recv, const void *q, int set0, int nsets, bool extrapolate, double Hh,
+                         cudaStream_t s) {
+    DonorLaunch a{};
+    const int don = 1 - recv, m = plan.m;
+    a.d = dev_mesh(don);
+    a.g = gas();
+    a.q = q;
+    a.nsets = nsets;
+    a.npts = md[recv].ndv;
+    a.pts = md[recv].dpts;
+    a.dv = (char *)md[recv].dv + (size_t)set0 * 10 * md[recv].ndv * esz;
+    for (int k = 0; k < m; ++k) a.hist[k] = hist_slot(don, (md[don].head + 1 + k) % m);
+    for (int j = 0; j < nsets; ++j) {
+      int set = set0 + j;
+      a.nb[j] = (extrapolate && set > 0) ? m : 0;
+      for (int k = 0; k < m; ++k) a.beta[j][k] = extrapolate ? plan.ext[set][k] * Hh : 0.0;
+    }
+    return launch_donor_vals(a, p.dtype, viscous(), s);
+  }
+
+  // Fused right-hand side + Adams-Bashforth update of mesh k with step dt, receivers gathered
+  // from donor-value set `set`. Pushes the new right-hand side into the ring slot after head.
+  cudaError_t fused(int k, int set, double dt, cudaStream_t s) {
+    const int m = plan.m;
+    MeshDev &d = md[k];
+    int slot = (d.head + 1) % m;
+    RhsLaunch a = rhs_args(k, d.q[d.cur]);
+    a.dv = (char *)d.dv + (size_t)set * 10 * d.ndv * esz;
+    a.didx = d.didx;
+    a.ndv = d.ndv;
+    a.mode = 1;
+    a.out = hist_slot(k, slot);
+    a.qnext = d.q[1 - d.cur];
+    a.nold = m - 1;
+    for (int j = 0; j < m - 1; ++j) {
+      a.hold[j] = hist_slot(k, (slot + 1 + j) % m);
+      a.alpha[j] = plan.ab[j] * dt;
+    }
+    a.alpha[m - 1] = plan.ab[m - 1] * dt;
+    return launch_rhs(a, p.dtype, viscous(), s);
+  }
+
+  // Enqueue one macro step (Sec. 3.3) for the current ring heads and state buffers, without
+  // changing them. With `side` set, the slow right-hand side and the first fast micro step
+  // (which needs only s(t) and f(t)) run on two streams joined before the second micro step.
+  cudaError_t issue_step(cudaStream_t s, cudaStream_t sd) {
+    const int F = fast(), Sl = slow(), sr = plan.sr;
+    const double h = H / sr;
+    MeshDev saved_s = md[Sl], saved_f = md[F];
+    cudaError_t e = cudaSuccess;
+    auto run = [&](cudaError_t x) {
+      if (e == cudaSuccess) e = x;
+    };
+    if (sd) {
+      run(cudaEventRecord(ev_fork, s));
+      run(cudaStreamWaitEvent(sd, ev_fork, 0));
+      // side: fast receivers from s(t), first micro step
+      run(donor_vals(F, md[Sl].q[md[Sl].cur], 0, 1, false, H, sd));
+      run(fused(F, 0, h, sd));
+    }
+    // slow: receivers from f(t), fused RHS + update into the other buffer
+    run(timed(SBP_PHASE_INTERP_SLOW, s, [&] { return donor_vals(Sl, md[F].q[md[F].cur], 0, 1, false, H, s); }));
+    run(timed(SBP_PHASE_RHS_SLOW, s, [&] { return fused(Sl, 0, H, s); }));
+    md[Sl].head = (md[Sl].head + 1) % plan.m;
+    // fast receivers for the micro steps that need the slow extrapolant (a_s(t) is now in the ring)
+    int first = sd ? 1 : 0;
+    if (sr > first)
+      run(timed(SBP_PHASE_INTERP_FAST, s,
+                [&] { return donor_vals(F, md[Sl].q[md[Sl].cur], first, sr - first, true, H, s); }));
+    if (sd) {
+      md[F].head = (md[F].head + 1) % plan.m;
+      md[F].cur ^= 1;
+      run(cudaEventRecord(ev_join, sd));
+      run(cudaStreamWaitEvent(s, ev_join, 0));
+    }
+    for (int j = first; j < sr; ++j) {
+      run(timed(SBP_PHASE_RHS_FAST, s, [&] { return fused(F, j, h, s); }));
+      md[F].head = (md[F].head + 1) % plan.m;
+      md[F].cur ^= 1;
+    }
+    md[Sl] = saved_s;
+    md[F] = saved_f;
+    return e;
+  }
+
+  // Host bookkeeping after one macro step.
+  void advance() {
+    md[slow()].head = (md[slow()].head + 1) % plan.m;
+    md[slow()].cur ^= 1;
+    for (int j = 0; j < plan.sr; ++j) {
+      md[fast()].head = (md[fast()].head + 1) % plan.m;
+      md[fast()].cur ^= 1;
+    }
+    t += H;
+  }
+
+  // Autotuner of the fused kernel's block shape: for each mesh, time the right-hand side (mode
+  // 0, into the history slot the next push overwrites) at several rows-per-CTA values on the
+  // bound state and keep the fastest. The strip width is fixed by the CTA size.
+  bool autotune_on = true;
+  cudaError_t autotune(cudaStream_t s) {
+    static const int cands[] = {8, 16, 32};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      MeshDev &d = md[k];
+      if (!d.hist) continue;
+      void *scratch = hist_slot(k, (d.head + 1) % plan.m);
+      e = interp(k, md[1 - k].q[md[1 - k].cur], nullptr, nullptr, 0, s);
+      float best = 1e30f;
+      int best_rows = d.rows_per_cta;
+      for (int rows : cands) {
+        if (rows > mh[k].nj || e != cudaSuccess) continue;
+        d.rows_per_cta = rows;
+        RhsLaunch a = rhs_args(k, d.q[d.cur]);
+        a.mode = 0;
+        a.out = scratch;
+        e = launch_rhs(a, p.dtype, viscous(), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_rhs(a, p.dtype, viscous(), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          best_rows = rows;
+        }
+      }
+      d.rows_per_cta = best_rows;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return e;
+  }
+
+  uint64_t phase_key() const {
+    const MeshDev &a = md[slow()], &b = md[fast()];
+    return (uint64_t)a.cur | ((uint64_t)a.head << 1) | ((uint64_t)b.cur << 8) | ((uint64_t)b.head << 9);
+  }
+
+  cudaError_t launch_step_graph(cudaStream_t s) {
+    uint64_t key = phase_key();
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+      cudaError_t e;
+      if (!cap) {
+        if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+      }
+      if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+      cudaError_t ei = issue_step(cap, side);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(cap, &g);
+      if (ei != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return ei;
+      }
+      if (e != cudaSuccess) return e;
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return e;
+      it = graphs.emplace(key, ex).first;
+    }
+    return cudaGraphLaunch(it->second, s);
+  }
 };
 
 extern "C" {
@@ -252,6 +493,8 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
   if (p.dtype != SBP_F64 && p.dtype != SBP_F32) return fail(SBP_ERR_DTYPE, "dtype");
   if (p.fast_mesh != 0 && p.fast_mesh != 1) return fail(SBP_ERR_ARG, "fast_mesh");
   if (!(p.gamma > 1.0) || p.mu < 0.0 || !(p.pr > 0.0)) return fail(SBP_ERR_ARG, "gas constants");
+  if (p.step_ratio < 1 || p.step_ratio > kMaxSets)
+    return fail(SBP_ERR_ARG, "step_ratio must be in 1.." + std::to_string(kMaxSets));
   auto *S = new sbp_system_s();
   std::unique_ptr<sbp_system_s> guard(S);
   S->p = p;
@@ -297,16 +540,16 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
       CUDA_TRY(e);
       CUDA_TRY(e2);
     }
-    // SAT points grouped by tile
-    d.tiles_x = (m.ni + kTileX - 1) / kTileX;
-    d.tiles_y = (m.nj + kTileY - 1) / kTileY;
-    int nt = d.tiles_x * d.tiles_y;
+    // SAT points grouped by 32 x 8 tile, tiles in column-major order so that the tiles of a
+    // taller CTA (16 or 32 rows) are contiguous
+    const int ntx = (m.ni + kTileX - 1) / kTileX, nty8 = (m.nj + 7) / 8;
     size_t ns = m.sat_pt.size();
     std::vector<int> order(ns);
     for (size_t s = 0; s < ns; ++s) order[s] = (int)s;
-    auto tile_of = [&](int pt) { return (pt / m.ni) / kTileY * d.tiles_x + (pt % m.ni) / kTileX; };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tile_of(m.sat_pt[a]) < tile_of(m.sat_pt[b]); });
-    std::vector<int> toff(nt + 1, 0);
+    auto tile_of = [&](int pt) { return ((pt % m.ni) / kTileX) * nty8 + (pt / m.ni) / 8; };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return tile_of(m.sat_pt[a]) < tile_of(m.sat_pt[b]); });
+    std::vector<int> toff((size_t)ntx * nty8 + 1, 0);
     std::vector<uint32_t> ij(ns), code(ns);
     std::vector<int> recv(ns);
     std::vector<double> scale(ns);
@@ -318,8 +561,10 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
       recv[s] = m.sat_recv[o];
       scale[s] = m.sat_scale[o];
     }
-    for (int t = 0; t < nt; ++t) toff[t + 1] += toff[t];
+    for (size_t t = 0; t + 1 < toff.size(); ++t) toff[t + 1] += toff[t];
     CUDA_TRY(upload(d.tile_sat, toff.data(), toff.size() * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&d.flux, 8 * field * S->esz));
+    d.rows_per_cta = 16;
     CUDA_TRY(upload(d.sat_ij, ij.data(), ns * sizeof(uint32_t)));
     CUDA_TRY(upload(d.sat_code, code.data(), ns * sizeof(uint32_t)));
     CUDA_TRY(upload(d.sat_recv, recv.data(), ns * sizeof(int)));
@@ -327,8 +572,20 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
     size_t nr = m.recv_pt.size();
     CUDA_TRY(upload(d.base, m.donor_base.data(), 2 * nr * sizeof(int)));
     CUDA_TRY(upload(d.w, m.donor_w.data(), 8 * nr * sizeof(double)));
+    if (p.dtype == SBP_F64) {
+      CUDA_TRY(upload(d.wt, m.donor_w.data(), 8 * nr * sizeof(double)));
+    } else {
+      std::vector<float> wf(m.donor_w.begin(), m.donor_w.end());
+      CUDA_TRY(upload(d.wt, wf.data(), wf.size() * sizeof(float)));
+    }
+    CUDA_TRY(cudaMalloc(&d.sat, (4 * ns + 1) * S->esz));
     CUDA_TRY(cudaMalloc(&d.qhat, (4 * nr + 1) * S->esz));
     CUDA_TRY(cudaMalloc(&d.fvhat, (6 * nr + 1) * S->esz));
+    d.ndv = (int)m.donor_pts.size();
+    d.dv_sets = k == p.fast_mesh ? p.step_ratio : 1;
+    CUDA_TRY(upload(d.dpts, m.donor_pts.data(), m.donor_pts.size() * sizeof(uint32_t)));
+    CUDA_TRY(upload(d.didx, m.donor_idx.data(), m.donor_idx.size() * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&d.dv, ((size_t)d.dv_sets * 10 * d.ndv + 1) * S->esz));
   }
   CUDA_TRY(cudaDeviceSynchronize());
   *out = guard.release();
@@ -354,6 +611,8 @@ sbp_status sbp_mesh_info_get(sbp_system_t S, int k, sbp_mesh_info *info) {
   info->n_receivers = (int)m.recv_pt.size();
   info->n_sat_points = (int)m.sat_pt.size();
   info->elem_size = (int)S->esz;
+  info->rows_per_cta = S->md[k].rows_per_cta;
+  info->strip_width = kTileX;
   return SBP_OK;
 }
 
@@ -459,6 +718,7 @@ sbp_status sbp_bind(sbp_system_t S, int k, void *qa, void *qb, void *hist) {
   d.head = -1;
   d.count = 0;
   S->initialised = false;
+  S->clear_graphs();
   return SBP_OK;
 }
 
@@ -531,6 +791,18 @@ sbp_status sbp_mrab_init(sbp_system_t S, double H, void *stream) {
   S->H = H;
   S->t = 0.0;
   S->initialised = true;
+  S->clear_graphs();
+  if (S->autotune_on) CUDA_TRY(S->autotune(s));
+  return SBP_OK;
+}
+
+sbp_status sbp_autotune(sbp_system_t S, int enable, void *stream) {
+  if (!S) return fail(SBP_ERR_ARG, "null system");
+  S->autotune_on = enable != 0;
+  if (S->autotune_on && S->initialised) {
+    CUDA_TRY(S->autotune((cudaStream_t)stream));
+    S->clear_graphs();
+  }
   return SBP_OK;
 }
 
@@ -538,59 +810,10 @@ sbp_status sbp_mrab_step(sbp_system_t S, int n, void *stream) {
   if (!S || n < 0) return fail(SBP_ERR_ARG, "bad argument");
   if (!S->initialised) return fail(SBP_ERR_STATE, "sbp_mrab_init has not run");
   cudaStream_t s = (cudaStream_t)stream;
-  const int m = S->plan.m, sr = S->plan.sr, F = S->fast(), Sl = S->slow();
-  const double H = S->H, h = H / sr;
   for (int step = 0; step < n; ++step) {
-    MeshDev &ds = S->md[Sl];
-    MeshDev &df = S->md[F];
-    // slow mesh: receivers from the fast state at t, right-hand side at t, s(t+H) into the
-    // other buffer (s(t) stays for the extrapolation of the micro steps)
-    CUDA_TRY(S->timed(SBP_PHASE_INTERP_SLOW, s, [&] { return S->interp(Sl, df.q[df.cur], nullptr, nullptr, 0, s); }));
-    {
-      int slot = (ds.head + 1) % m;
-      RhsLaunch a = S->rhs_args(Sl, ds.q[ds.cur]);
-      a.mode = 1;
-      a.out = S->hist_slot(Sl, slot);
-      a.qnext = ds.q[1 - ds.cur];
-      a.nold = m - 1;
-      for (int k = 0; k < m - 1; ++k) {
-        a.hold[k] = S->hist_slot(Sl, (slot + 1 + k) % m);
-        a.alpha[k] = S->plan.ab[k] * H;
-      }
-      a.alpha[m - 1] = S->plan.ab[m - 1] * H;
-      CUDA_TRY(S->timed(SBP_PHASE_RHS_SLOW, s, [&] { return launch_rhs(a, S->p.dtype, S->viscous(), s); }));
-      ds.head = slot;
-    }
-    // fast mesh: step_ratio micro steps, receivers fed by the slow extrapolant
-    for (int j = 0; j < sr; ++j) {
-      const void *hs[kMaxHist];
-      double beta[kMaxHist];
-      int nb = 0;
-      if (j > 0) {
-        nb = m;
-        for (int k = 0; k < m; ++k) {
-          hs[k] = S->hist_slot(Sl, (ds.head + 1 + k) % m);
-          beta[k] = S->plan.ext[j][k] * H;
-        }
-      }
-      CUDA_TRY(S->timed(SBP_PHASE_INTERP_FAST, s, [&] { return S->interp(F, ds.q[ds.cur], hs, beta, nb, s); }));
-      int slot = (df.head + 1) % m;
-      RhsLaunch a = S->rhs_args(F, df.q[df.cur]);
-      a.mode = 1;
-      a.out = S->hist_slot(F, slot);
-      a.qnext = df.q[1 - df.cur];
-      a.nold = m - 1;
-      for (int k = 0; k < m - 1; ++k) {
-        a.hold[k] = S->hist_slot(F, (slot + 1 + k) % m);
-        a.alpha[k] = S->plan.ab[k] * h;
-      }
-      a.alpha[m - 1] = S->plan.ab[m - 1] * h;
-      CUDA_TRY(S->timed(SBP_PHASE_RHS_FAST, s, [&] { return launch_rhs(a, S->p.dtype, S->viscous(), s); }));
-      df.head = slot;
-      df.cur ^= 1;
-    }
-    ds.cur ^= 1;
-    S->t += H;
+    if (S->use_graph && !S->prof) CUDA_TRY(S->launch_step_graph(s));
+    else CUDA_TRY(S->issue_step(s, nullptr));
+    S->advance();
   }
   return SBP_OK;
 }
@@ -599,6 +822,12 @@ sbp_status sbp_mrab_time(sbp_system_t S, double *H, double *t) {
   if (!S) return fail(SBP_ERR_ARG, "null system");
   if (H) *H = S->H;
   if (t) *t = S->t;
+  return SBP_OK;
+}
+
+sbp_status sbp_use_graphs(sbp_system_t S, int enable) {
+  if (!S) return fail(SBP_ERR_ARG, "null system");
+  S->use_graph = enable != 0;
   return SBP_OK;
 }
 

@@ -25,13 +25,30 @@ struct Gas {
   double qinf[4];
 };
 
-// Fused right-hand side (+ optional MRAB update) over all tiles of one mesh.
+// Constants of the right-hand side in the compute type, prepared on the host (converting
+// double constants inside a float kernel would occupy GB300's narrow FP64 pipe).
+template <typename T>
+struct KConst {
+  T gam, g1, mu, kap, mu43, mu23;  // gamma, gamma-1, mu, mu/(Pr(gamma-1)), 4/3 mu, 2/3 mu
+  T sig_int, sig_phys, tw;          // penalties; wall energy factor Tw/(gamma(gamma-1))
+  T qinf[4];
+  T mc[5];                          // Cartesian metrics
+  T jx, jy;                         // Cartesian J xi_x and J eta_y (1/hx, 1/hy)
+};
+
+// Right-hand side (+ optional MRAB update) of one mesh: k_flux then k_update.
 struct RhsLaunch {
   DevMesh m;
   Gas g;
+  KConst<float> cf;
+  KConst<double> cd;
   const void *q;
-  // SAT points of this mesh, grouped by tile (tile_sat has one offset per tile + 1)
+  void *sat;  // per SAT point: its 4 penalty terms (written by k_flux, added by k_update)
+  // SAT points of this mesh grouped by 32 x 8 tile (tile id = (i / 32) * ceil(nj / 8) + j / 8);
+  // tile_sat has one offset per tile + 1
   const int *tile_sat;
+  int rows_per_cta;  // 8, 16 or 32: rows per CTA of the right-hand-side kernels
+  void *flux;        // 8 planes: F^_xi (4 variables), F^_eta (4 variables)
   const uint32_t *sat_ij;   // i | j << 16
   const uint32_t *sat_code;
   const int *sat_recv;
@@ -39,6 +56,14 @@ struct RhsLaunch {
   const void *qhat;
   const void *fvhat;
   int nrecv;
+  // When dv is set, the receiver values are gathered in the SAT stage instead of read from
+  // qhat/fvhat: q^ = sum_16 w_a w_b dv[c][didx], with dv the per-donor-point values of
+  // k_donor_vals (10 planes of ndv values: 4 state, 6 viscous fluxes).
+  const void *dv;
+  const int *didx;
+  const void *dwt;  // donor weights in the compute type, 8 per receiver
+  int ndv;
+  int nsat;         // number of SAT points (length of the planes of `sat`)
   // epilogue: mode 0 writes dq/dt to out; mode 1 writes it to out (the newest history slot)
   // and qnext = q + sum_k alpha[k] hold[k] + alpha[nold] dq/dt (FP64 accumulation)
   int mode;
@@ -65,11 +90,30 @@ struct InterpLaunch {
   void *fvhat;  // NULL: skip the viscous fluxes
 };
 
-// Tile of the fused right-hand-side kernel.
-constexpr int kTileX = 32, kTileY = 8;
+// Values at the distinct donor points of one receiving mesh, for `nsets` extrapolation sets:
+// set s holds q + sum_k beta[s][k] hist[k] (nb[s] terms) and, for Navier-Stokes, the Cartesian
+// viscous fluxes of that state. Output dv[(s * 10 + c) * npts + d].
+constexpr int kMaxSets = 16;
+struct DonorLaunch {
+  DevMesh d;
+  Gas g;
+  const void *q;
+  const void *hist[kMaxHist];
+  double beta[kMaxSets][kMaxHist];
+  int nb[kMaxSets];
+  int nsets;
+  int npts;
+  const uint32_t *pts;  // i | j << 16
+  void *dv;
+};
+
+// Columns per CTA and threads per CTA of the right-hand-side kernels.
+constexpr int kTileX = 32;
+constexpr int kNT = 256;
 
 cudaError_t launch_rhs(const RhsLaunch &a, int dtype, bool viscous, cudaStream_t s);
 cudaError_t launch_interp(const InterpLaunch &a, int dtype, bool viscous, cudaStream_t s);
+cudaError_t launch_donor_vals(const DonorLaunch &a, int dtype, bool viscous, cudaStream_t s);
 cudaError_t launch_dt(const DevMesh &m, const Gas &g, const void *q, int dtype, unsigned long long *out,
                       cudaStream_t s);
 cudaError_t launch_metrics(const DevMesh &m, const double *x, const double *y, const double shift[4], void *met,
@@ -77,7 +121,6 @@ cudaError_t launch_metrics(const DevMesh &m, const double *x, const double *y, c
 // y_out = y + c1 k1 + c2 k2 (k2 may be NULL), FP64 accumulation, over n elements.
 cudaError_t launch_axpy(const void *y, const void *k1, double c1, const void *k2, double c2, void *y_out, size_t n,
                         int dtype, cudaStream_t s);
-size_t rhs_smem_bytes(int dtype, bool viscous, bool curvilinear);
 // Interpolation + right-hand side with the receiver workspace in the library's fixed device
 // array (sbp_noalloc.cu); the qhat/fvhat pointers of the descriptors are replaced.
 cudaError_t rhs_eval_static_scratch(InterpLaunch ia, RhsLaunch ra, int dtype, bool viscous, size_t elem,

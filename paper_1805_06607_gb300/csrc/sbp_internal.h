@@ -49,6 +49,10 @@ struct MeshHost {
   std::vector<int> recv_pt;
   std::vector<int> donor_base;       // 2 per receiver
   std::vector<double> donor_w;       // 8 per receiver
+  // the distinct donor points of all receivers (i | j << 16 on the other mesh, sorted) and,
+  // per receiver, the index of each of its 16 stencil points (b * 4 + a) in that list
+  std::vector<uint32_t> donor_pts;
+  std::vector<int> donor_idx;
 };
 
 // Adams-Bashforth / MRAB coefficient plan (Sec. 3.1-3.3), weights oldest first, in units of

@@ -64,13 +64,14 @@ __device__ __forceinline__ T dline(const T *f, int s, int st, unsigned code) {
   return sgn > 0 ? acc : -acc;
 }
 
+// Index g on a line of n points: wrapped once on a periodic line; false when outside the line
+// (non-periodic) or more than one period away (strips wider than a small periodic mesh).
 __device__ __forceinline__ bool wrap_index(int &g, int n, int per) {
   if (per) {
     if (g < 0) g += n;
-    if (g >= n) g -= n;
-    return true;
+    else if (g >= n) g -= n;
   }
-  return g >= 0 && g < n;
+  return (unsigned)g < (unsigned)n;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -140,294 +141,445 @@ __device__ __forceinline__ void penalty_apply(const T q[4], T gam, T kx, T ky, i
 }
 
 // ---------------------------------------------------------------------------------------------
-// Fused right-hand side. One CTA per kTileX x kTileY tile, one thread per owned point.
-// Shared memory holds the state (and primitives) on the tile plus a halo of HQ points, and
-// metrics, gradients and contravariant fluxes on the tile plus HB = 3 points (the reach of
-// the closure rows). Halo HQ = 3 for Euler; 6 for Navier-Stokes, where the fluxes at the
-// band points need gradients that reach 3 points further.
-template <typename T, bool VISC, bool CURV>
-struct RhsSmem {
-  static constexpr int TX = kTileX, TY = kTileY, NT = TX * TY;
-  static constexpr int HQ = VISC ? 6 : 3, HB = 3;
-  static constexpr int RX = TX + 2 * HQ, RY = TY + 2 * HQ, RN = RX * RY;
-  static constexpr int BX = TX + 2 * HB, BY = TY + 2 * HB, BN = BX * BY;
-  static constexpr size_t n_q = 4 * RN, n_prim = VISC ? 3 * RN : 0, n_met = CURV ? 5 * BN : 0,
-                          n_grad = VISC ? 6 * BN : 0, n_flx = 8 * BN, n_rhs = 4 * NT;
-  static constexpr size_t bytes = (n_q + n_prim + n_met + n_grad + n_flx + n_rhs) * sizeof(T) + RN;
-};
-
+// Right-hand side in two kernels per mesh:
+//  k_flux    contravariant fluxes F^_xi, F^_eta (inviscid minus viscous) at every point, written
+//            to a flux buffer (8 planes) that stays in L2 for the next kernel. Navier-Stokes
+//            tiles stage the primitives with a 3-point halo in shared memory for the velocity
+//            and temperature gradients; each flux is computed once.
+//  k_update  SBP derivatives of the fluxes (3-point halo of flux planes in shared memory),
+//            -J times their sum, SAT penalties at the tile's boundary and receiver points, and
+//            the epilogue (mode 0: dq/dt; mode 1: also the Adams-Bashforth / MRAB update).
 template <typename T, bool CURV>
-__device__ __forceinline__ void load_metrics(const DevMesh &m, const T *smet, int bidx, int bn, T mt[5]) {
+__device__ __forceinline__ void point_metrics(const DevMesh &m, int gi, int gj, T mt[5]) {
   if (CURV) {
+    const T *met = static_cast<const T *>(m.met);
+    size_t p = (size_t)gj * m.pitch + gi;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) mt[c] = smet[c * bn + bidx];
+    for (int c = 0; c < 5; ++c) mt[c] = met[c * m.field + p];
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c) mt[c] = (T)m.mc[c];
   }
 }
 
-template <typename T, bool VISC, bool CURV>
-__global__ void __launch_bounds__(kTileX *kTileY) k_rhs(const RhsLaunch a) {
-  using S = RhsSmem<T, VISC, CURV>;
-  constexpr int TX = S::TX, NT = S::NT, HQ = S::HQ, HB = S::HB, RX = S::RX, RN = S::RN, BX = S::BX,
-                BN = S::BN;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *sq = reinterpret_cast<T *>(smem_raw);
-  T *sprim = sq + S::n_q;
-  T *smet = sprim + S::n_prim;
-  T *sgrad = smet + S::n_met;
-  T *sflx = sgrad + S::n_grad;
-  T *srhs = sflx + S::n_flx;
-  uint8_t *scls = reinterpret_cast<uint8_t *>(srhs + S::n_rhs);
+template <typename T>
+__device__ __forceinline__ void prim_at(const T *q, size_t field, size_t p, T gam, T pr[3]) {
+  T r = q[p], ri = T(1) / r;
+  T u = q[field + p] * ri, v = q[2 * field + p] * ri;
+  T pres = (gam - T(1)) * (q[3 * field + p] - T(0.5) * (q[field + p] * u + q[2 * field + p] * v));
+  pr[0] = u;
+  pr[1] = v;
+  pr[2] = gam * pres * ri;
+}
 
-  const DevMesh &m = a.m;
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * S::TY;
-  const T *q = static_cast<const T *>(a.q);
-  const T gam = (T)a.g.gamma, mu = (T)a.g.mu, kap = (T)(a.g.mu / (a.g.pr * (a.g.gamma - 1.0)));
-
-  // ---- stage 0: state and classes on the halo region; metrics on the band
-  for (int idx = tid; idx < RN; idx += NT) {
-    int gi = i0 - HQ + idx % RX, gj = j0 - HQ + idx / RX;
-    bool in = wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j);
-    if (in) {
-      size_t p = (size_t)gj * m.pitch + gi;
-      scls[idx] = m.cls[p];
+// Cartesian viscous fluxes at one point from the state in global memory (used at SAT points).
+template <typename T, bool CURV>
+__device__ void visc_at_point(const DevMesh &m, const T *q, int i, int j, T gam, T mu, T kap, T Fv[3], T Gv[3]) {
+  size_t p = (size_t)j * m.pitch + i;
+  unsigned code = m.cls[p];
+  T dxi[3] = {0, 0, 0}, deta[3] = {0, 0, 0};
+  for (int dir = 0; dir < 2; ++dir) {
+    int row, sgn;
+    row_of(dir == 0 ? (code & 15u) : (code >> 4), row, sgn);
+    for (int e = 0; e < 4; ++e) {
+      T we = wgt<T>(row, e);
+      if (we == T(0)) continue;
+      int ii = i, jj = j;
+      if (dir == 0) ii += sgn * c_off[row][e];
+      else jj += sgn * c_off[row][e];
+      wrap_index(ii, m.ni, m.per_i);
+      wrap_index(jj, m.nj, m.per_j);
+      T pr[3];
+      prim_at(q, m.field, (size_t)jj * m.pitch + ii, gam, pr);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) sq[v * RN + idx] = q[v * m.field + p];
-    } else {
-      scls[idx] = 0xFF;
-      sq[idx] = T(1);
-      sq[RN + idx] = T(0);
-      sq[2 * RN + idx] = T(0);
-      sq[3 * RN + idx] = T(2.5);
-    }
-  }
-  if (CURV) {
-    const T *met = static_cast<const T *>(m.met);
-    for (int idx = tid; idx < BN; idx += NT) {
-      int gi = i0 - HB + idx % BX, gj = j0 - HB + idx / BX;
-      bool in = wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j);
-      if (in) {
-        size_t p = (size_t)gj * m.pitch + gi;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) smet[c * BN + idx] = met[c * m.field + p];
-      } else {
-        smet[idx] = T(1);
-        smet[BN + idx] = T(0);
-        smet[2 * BN + idx] = T(0);
-        smet[3 * BN + idx] = T(1);
-        smet[4 * BN + idx] = T(1);
+      for (int f = 0; f < 3; ++f) {
+        if (dir == 0) dxi[f] += T(sgn) * we * pr[f];
+        else deta[f] += T(sgn) * we * pr[f];
       }
     }
   }
-  __syncthreads();
+  T mt[5];
+  point_metrics<T, CURV>(m, i, j, mt);
+  T gr[6];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    gr[2 * f] = mt[4] * (mt[0] * dxi[f] + mt[2] * deta[f]);
+    gr[2 * f + 1] = mt[4] * (mt[1] * dxi[f] + mt[3] * deta[f]);
+  }
+  T pc[3];
+  prim_at(q, m.field, p, gam, pc);
+  viscous_flux(pc[0], pc[1], gr, mu, kap, Fv, Gv);
+}
 
-  // ---- stage 1: primitives u, v, T on the halo region (viscous only)
-  if (VISC) {
+// Kernel constants in the compute type.
+template <typename T>
+__device__ __forceinline__ const KConst<T> &kc(const RhsLaunch &a);
+template <>
+__device__ __forceinline__ const KConst<float> &kc<float>(const RhsLaunch &a) {
+  return a.cf;
+}
+template <>
+__device__ __forceinline__ const KConst<double> &kc<double>(const RhsLaunch &a) {
+  return a.cd;
+}
+
+template <typename T, bool CURV>
+__device__ __forceinline__ void load_met(const RhsLaunch &a, int gi, int gj, T mt[5]) {
+  if (CURV) {
+    const T *met = static_cast<const T *>(a.m.met);
+    size_t p = (size_t)gj * a.m.pitch + gi;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) mt[c] = met[c * a.m.field + p];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) mt[c] = kc<T>(a).mc[c];
+  }
+}
+
+// Cartesian viscous fluxes from gradients (u_x, u_y, v_x, v_y, T_x, T_y), Stokes hypothesis.
+template <typename T>
+__device__ __forceinline__ void visc_flux_k(const KConst<T> &k, T u, T v, const T gr[6], T Fv[3], T Gv[3]) {
+  T txx = k.mu43 * gr[0] - k.mu23 * gr[3];
+  T tyy = k.mu43 * gr[3] - k.mu23 * gr[0];
+  T txy = k.mu * (gr[1] + gr[2]);
+  Fv[0] = txx;
+  Fv[1] = txy;
+  Fv[2] = u * txx + v * txy + k.kap * gr[4];
+  Gv[0] = txy;
+  Gv[1] = tyy;
+  Gv[2] = u * txy + v * tyy + k.kap * gr[5];
+}
+
+// Gradients of (u, v, T) at smem index r of the primitive planes (row stride rx), chain rule
+// with the metrics; Cartesian meshes use the constants J xi_x = 1/hx, J eta_y = 1/hy.
+template <typename T, bool CURV>
+__device__ __forceinline__ void smem_grads(const RhsLaunch &a, const T *prim, int rn, int r, int rx, unsigned code,
+                                           const T mt[5], T gr[6]) {
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    T dxi = dline(prim + f * rn, r, 1, code & 15u);
+    T deta = dline(prim + f * rn, r, rx, code >> 4);
+    if (CURV) {
+      gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
+      gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
+    } else {
+      gr[2 * f] = kc<T>(a).jx * dxi;
+      gr[2 * f + 1] = kc<T>(a).jy * deta;
+    }
+  }
+}
+
+// SAT terms of one boundary / receiver point (Sec. 2.2 eq. (int); physical forms of Sec. 5.1):
+// q_p the point's state, (Fv, Gv) its Cartesian viscous fluxes; returns the sum in acc.
+template <typename T, bool VISC>
+__device__ void sat_terms(const RhsLaunch &a, int s, const T qp[4], const T mt[5], const T Fv[3], const T Gv[3],
+                          T acc[4]) {
+  const KConst<T> &k = kc<T>(a);
+  const T *qhat = static_cast<const T *>(a.qhat);
+  const T *fvhat = static_cast<const T *>(a.fvhat);
+  const T *dw = static_cast<const T *>(a.dwt);
+  uint32_t code = a.sat_code[s];
+  int recv = a.sat_recv[s];
+  T scale = (T)a.sat_scale[s];
+  constexpr int NRV = VISC ? 10 : 4;
+  T rv[NRV];
+#pragma unroll
+  for (int c = 0; c < NRV; ++c) rv[c] = T(0);
+  if (recv >= 0) {
+    if (a.dv) {
+      const T *dv = static_cast<const T *>(a.dv);
+      for (int e = 0; e < 16; ++e) {
+        T w = dw[8 * recv + (e & 3)] * dw[8 * recv + 4 + (e >> 2)];
+        int d = a.didx[16 * recv + e];
+#pragma unroll
+        for (int c = 0; c < NRV; ++c) rv[c] += w * dv[c * a.ndv + d];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rv[c] = qhat[c * a.nrecv + recv];
+      if constexpr (VISC) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) rv[4 + c] = fvhat[c * a.nrecv + recv];
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) acc[v] = T(0);
+  int nt = code & 7u;
+  for (int t = 0; t < nt; ++t) {
+    unsigned term = (code >> (3 + 4 * t)) & 15u;
+    int dir = term & 1u, side = (term & 2u) ? -1 : 1, kind = (int)(term >> 2);
+    T kx = mt[4] * mt[2 * dir], ky = mt[4] * mt[2 * dir + 1];
+    T tgt[4];
+    T sig1 = T(0), sigI = kind == kTermInterface ? k.sig_int : k.sig_phys;
+    if (kind == kTermInterface) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) tgt[v] = rv[v];
+      if (VISC) sig1 = T(0.5) * k.mu * (kx * kx + ky * ky);
+    } else if (kind == kTermFarfield) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) tgt[v] = k.qinf[v];
+    } else {
+      tgt[0] = qp[0];
+      tgt[1] = T(0);
+      tgt[2] = T(0);
+      tgt[3] = qp[0] * k.tw;
+      if (VISC) sig1 = T(0.5) * k.mu * (kx * kx + ky * ky);
+    }
+    T dq[4], kd[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dq[v] = qp[v] - tgt[v];
+    penalty_apply(qp, k.gam, kx, ky, side, dq, kd);
+    T sat[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sat[v] = -(sigI * kd[v] + sig1 * dq[v]) * T(1.0 / SBP_P0);
+    if constexpr (VISC) {
+      if (kind == kTermInterface) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T own = kx * Fv[c] + ky * Gv[c];
+          T hat = kx * rv[4 + c] + ky * rv[7 + c];
+          sat[c + 1] += T(0.5) * T(side) * (own - hat) * T(1.0 / SBP_P0);
+        }
+      }
+    }
+    T sc = kind == kTermInterface ? scale : T(1);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] += sc * sat[v];
+  }
+}
+
+// SAT entries of the CTA's rows: the tile lists are grouped by 32 x 8 tiles in column-major
+// tile order, so a 32 x TY block owns a contiguous range.
+template <int TY>
+__device__ __forceinline__ void tile_sat_range(const RhsLaunch &a, int &s0, int &s1) {
+  const int nty8 = (a.m.nj + 7) / 8;
+  const int ty8 = blockIdx.y * (TY / 8);
+  const int id0 = blockIdx.x * nty8 + ty8, id1 = blockIdx.x * nty8 + min(ty8 + TY / 8, nty8);
+  s0 = a.tile_sat[id0];
+  s1 = a.tile_sat[id1];
+}
+
+template <typename T, bool VISC, int TY>
+struct FluxTile {
+  static constexpr int TX = kTileX, NT = kNT, PPT = TX * TY / NT;
+  static constexpr int H = VISC ? 3 : 0, RX = TX + 2 * H, RY = TY + 2 * H, RN = RX * RY;
+};
+
+// Contravariant fluxes at every point of a 32 x TY tile, then the SAT terms of the tile's
+// boundary and receiver points (their state, primitives and gradients are at hand here).
+template <typename T, bool VISC, bool CURV, int TY>
+// At least 4 (FP32) / 3 (FP64) resident CTAs per SM: caps the registers that the SAT tail
+// (taken by boundary tiles only) would otherwise claim for the whole kernel.
+__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 4 : 3) k_flux(const RhsLaunch a) {
+  using F = FluxTile<T, VISC, TY>;
+  constexpr int TX = F::TX, NT = F::NT, H = F::H, RX = F::RX, RN = F::RN;
+  __shared__ T prim[VISC ? 3 * RN : 1];
+  __shared__ uint8_t scls[VISC ? RN : 1];
+  const DevMesh &m = a.m;
+  const KConst<T> &k = kc<T>(a);
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const T *q = static_cast<const T *>(a.q);
+  T *fl = static_cast<T *>(a.flux);
+  if constexpr (VISC) {
     for (int idx = tid; idx < RN; idx += NT) {
-      T ri = T(1) / sq[idx];
-      T u = sq[RN + idx] * ri, v = sq[2 * RN + idx] * ri;
-      T p = (gam - T(1)) * (sq[3 * RN + idx] - T(0.5) * (sq[RN + idx] * u + sq[2 * RN + idx] * v));
-      sprim[idx] = u;
-      sprim[RN + idx] = v;
-      sprim[2 * RN + idx] = gam * p * ri;
+      int gi = i0 - H + idx % RX, gj = j0 - H + idx / RX;
+      bool in = wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j);
+      T pr[3] = {T(0), T(0), T(1)};
+      uint8_t c = 0xFF;
+      if (in) {
+        size_t p = (size_t)gj * m.pitch + gi;
+        prim_at(q, m.field, p, k.gam, pr);
+        c = m.cls[p];
+      }
+      prim[idx] = pr[0];
+      prim[RN + idx] = pr[1];
+      prim[2 * RN + idx] = pr[2];
+      scls[idx] = c;
     }
     __syncthreads();
   }
-
-  // ---- stage 2: gradients and contravariant fluxes on the band
-  for (int idx = tid; idx < BN; idx += NT) {
-    int bx = idx % BX, by = idx / BX;
-    int r = (by + HQ - HB) * RX + (bx + HQ - HB);
-    unsigned code = scls[r];
+#pragma unroll
+  for (int kk = 0; kk < F::PPT; ++kk) {
+    const int li = tid % TX, lj = tid / TX + kk * (NT / TX);
+    const int gi = i0 + li, gj = j0 + lj;
+    if (gi >= m.ni || gj >= m.nj) continue;
+    const size_t p = (size_t)gj * m.pitch + gi;
+    T qp[4] = {q[p], q[m.field + p], q[2 * m.field + p], q[3 * m.field + p]};
     T mt[5];
-    load_metrics<T, CURV>(m, smet, idx, BN, mt);
-    T qp[4] = {sq[r], sq[RN + r], sq[2 * RN + r], sq[3 * RN + r]};
-    T F[4], G[4], u, v, p;
-    inviscid_flux(qp, gam, F, G, u, v, p);
-    if (VISC) {
+    load_met<T, CURV>(a, gi, gj, mt);
+    T u, v, pr;
+    T Fx[4], Gx[4];
+    if constexpr (VISC) {
+      const int r = (lj + H) * RX + (li + H);
+      u = prim[r];
+      v = prim[RN + r];
+      pr = qp[0] * prim[2 * RN + r] / k.gam;  // p = rho T / gamma
       T gr[6];
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        T dxi = dline(sprim + f * RN, r, 1, code & 15u);
-        T deta = dline(sprim + f * RN, r, RX, code >> 4);
-        if (CURV) {
-          gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
-          gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
-        } else {
-          gr[2 * f] = mt[4] * (mt[0] * dxi);
-          gr[2 * f + 1] = mt[4] * (mt[3] * deta);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 6; ++c) sgrad[c * BN + idx] = gr[c];
+      smem_grads<T, CURV>(a, prim, RN, r, RX, scls[r], mt, gr);
       T Fv[3], Gv[3];
-      viscous_flux(u, v, gr, mu, kap, Fv, Gv);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        F[c + 1] -= Fv[c];
-        G[c + 1] -= Gv[c];
-      }
+      visc_flux_k(k, u, v, gr, Fv, Gv);
+      Fx[0] = qp[1];
+      Fx[1] = qp[1] * u + pr - Fv[0];
+      Fx[2] = qp[2] * u - Fv[1];
+      Fx[3] = (qp[3] + pr) * u - Fv[2];
+      Gx[0] = qp[2];
+      Gx[1] = qp[1] * v - Gv[0];
+      Gx[2] = qp[2] * v + pr - Gv[1];
+      Gx[3] = (qp[3] + pr) * v - Gv[2];
+    } else {
+      inviscid_flux(qp, k.gam, Fx, Gx, u, v, pr);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      if (CURV) {
-        sflx[c * BN + idx] = mt[0] * F[c] + mt[1] * G[c];
-        sflx[(4 + c) * BN + idx] = mt[2] * F[c] + mt[3] * G[c];
-      } else {
-        sflx[c * BN + idx] = mt[0] * F[c];
-        sflx[(4 + c) * BN + idx] = mt[3] * G[c];
-      }
+      fl[c * m.field + p] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : mt[0] * Fx[c];
+      fl[(4 + c) * m.field + p] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : mt[3] * Gx[c];
     }
   }
-  __syncthreads();
-
-  // ---- stage 3: dq/dt = -J (D_xi F^_xi + D_eta F^_eta) at the owned points
-  const int lx = tid % TX, ly = tid / TX;
-  const int gi = i0 + lx, gj = j0 + ly;
-  const int bown = (ly + HB) * BX + (lx + HB);
-  const int rown = (ly + HQ) * RX + (lx + HQ);
-  {
-    unsigned code = scls[rown];
-    T mt[5];
-    load_metrics<T, CURV>(m, smet, bown, BN, mt);
-    bool hole = (code & 15u) == 0xFu;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      T d = dline(sflx + c * BN, bown, 1, code & 15u) + dline(sflx + (4 + c) * BN, bown, BX, code >> 4);
-      srhs[c * NT + tid] = hole ? T(0) : -mt[4] * d;
-    }
-  }
-  __syncthreads();
-
-  // ---- stage 4: SAT penalties at this tile's boundary and receiver points
-  {
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    const int s0 = a.tile_sat[tile], s1 = a.tile_sat[tile + 1];
-    const T *qhat = static_cast<const T *>(a.qhat);
-    const T *fvhat = static_cast<const T *>(a.fvhat);
-    for (int s = s0 + tid; s < s1; s += NT) {
-      uint32_t ij = a.sat_ij[s];
-      int li = (int)(ij & 0xFFFFu) - i0, lj = (int)(ij >> 16) - j0;
-      int r = (lj + HQ) * RX + (li + HQ);
-      int b = (lj + HB) * BX + (li + HB);
-      T mt[5];
-      load_metrics<T, CURV>(m, smet, b, BN, mt);
-      T qp[4] = {sq[r], sq[RN + r], sq[2 * RN + r], sq[3 * RN + r]};
-      T Fv[3] = {0, 0, 0}, Gv[3] = {0, 0, 0};
-      if (VISC) {
-        T gr[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) gr[c] = sgrad[c * BN + b];
-        viscous_flux(sprim[r], sprim[RN + r], gr, mu, kap, Fv, Gv);
-      }
-      uint32_t code = a.sat_code[s];
-      int recv = a.sat_recv[s];
-      T scale = (T)a.sat_scale[s];
-      T acc[4] = {0, 0, 0, 0};
-      int nt = code & 7u;
-      for (int t = 0; t < nt; ++t) {
-        unsigned term = (code >> (3 + 4 * t)) & 15u;
-        int dir = term & 1u, side = (term & 2u) ? -1 : 1, kind = (int)(term >> 2);
-        T kx = mt[4] * mt[2 * dir], ky = mt[4] * mt[2 * dir + 1];
-        T tgt[4];
-        T sig1 = T(0), sigI = kind == kTermInterface ? (T)a.g.sig_int : (T)a.g.sig_phys;
-        if (kind == kTermInterface) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) tgt[v] = qhat[v * a.nrecv + recv];
-          if (VISC) sig1 = T(0.5) * mu * (kx * kx + ky * ky);
-        } else if (kind == kTermFarfield) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) tgt[v] = (T)a.g.qinf[v];
-        } else {
-          tgt[0] = qp[0];
-          tgt[1] = T(0);
-          tgt[2] = T(0);
-          tgt[3] = qp[0] * (T)(a.g.twall / (a.g.gamma * (a.g.gamma - 1.0)));
-          if (VISC) sig1 = T(0.5) * mu * (kx * kx + ky * ky);
-        }
-        T dq[4], kd[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) dq[v] = qp[v] - tgt[v];
-        penalty_apply(qp, gam, kx, ky, side, dq, kd);
-        T sat[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) sat[v] = -(sigI * kd[v] + sig1 * dq[v]) * T(1.0 / SBP_P0);
-        if (VISC && kind == kTermInterface) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            T own = kx * Fv[c] + ky * Gv[c];
-            T hat = kx * fvhat[c * a.nrecv + recv] + ky * fvhat[(3 + c) * a.nrecv + recv];
-            sat[c + 1] += T(0.5) * T(side) * (own - hat) * T(1.0 / SBP_P0);
-          }
-        }
-        T sc = kind == kTermInterface ? scale : T(1);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] += sc * sat[v];
-      }
-      int o = lj * TX + li;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) srhs[v * NT + o] += acc[v];
-    }
-  }
-  __syncthreads();
-
-  // ---- stage 5: epilogue
-  if (gi < m.ni && gj < m.nj) {
+  // SAT terms of this tile's boundary / receiver points (one thread per point)
+  int s0, s1;
+  tile_sat_range<TY>(a, s0, s1);
+  T *satb = static_cast<T *>(a.sat);
+  for (int s = s0 + tid; s < s1; s += NT) {
+    uint32_t ij = a.sat_ij[s];
+    int gi = (int)(ij & 0xFFFFu), gj = (int)(ij >> 16);
     size_t p = (size_t)gj * m.pitch + gi;
+    T qp[4] = {q[p], q[m.field + p], q[2 * m.field + p], q[3 * m.field + p]};
+    T mt[5];
+    load_met<T, CURV>(a, gi, gj, mt);
+    T Fv[3] = {0, 0, 0}, Gv[3] = {0, 0, 0};
+    if constexpr (VISC) {
+      const int r = (gj - j0 + H) * RX + (gi - i0 + H);
+      T gr[6];
+      smem_grads<T, CURV>(a, prim, RN, r, RX, scls[r], mt, gr);
+      visc_flux_k(k, prim[r], prim[RN + r], gr, Fv, Gv);
+    }
+    T acc[4];
+    sat_terms<T, VISC>(a, s, qp, mt, Fv, Gv, acc);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) satb[c * a.nsat + s] = acc[c];
+  }
+}
+
+template <typename T, int TY>
+struct UpdTile {
+  static constexpr int TX = kTileX, NT = kNT, PPT = TX * TY / NT;
+  static constexpr int RX = TX + 6, RY = TY + 6, RN = RX * RY;
+  static constexpr size_t bytes = (size_t)(8 * RN) * sizeof(T);
+};
+
+// SBP derivatives of the fluxes, the tile's SAT terms, and the epilogue.
+template <typename T, bool VISC, bool CURV, int TY>
+__global__ void __launch_bounds__(kNT) k_update(const RhsLaunch a) {
+  using U = UpdTile<T, TY>;
+  constexpr int TX = U::TX, NT = U::NT, RX = U::RX, RN = U::RN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sf = reinterpret_cast<T *>(smem_raw);  // [8][RN]
+  const DevMesh &m = a.m;
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const T *q = static_cast<const T *>(a.q);
+  const T *fl = static_cast<const T *>(a.flux);
+  const T *satb = static_cast<const T *>(a.sat);
+
+  for (int idx = tid; idx < RN; idx += NT) {
+    int gi = i0 - 3 + idx % RX, gj = j0 - 3 + idx / RX;
+    bool in = wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j);
+    size_t p = in ? (size_t)gj * m.pitch + gi : 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sf[c * RN + idx] = in ? fl[c * m.field + p] : T(0);
+  }
+  __syncthreads();
+  int s0, s1;
+  tile_sat_range<TY>(a, s0, s1);
+#pragma unroll
+  for (int kk = 0; kk < U::PPT; ++kk) {
+    const int li = tid % TX, lj = tid / TX + kk * (NT / TX);
+    const int gi = i0 + li, gj = j0 + lj;
+    if (gi >= m.ni || gj >= m.nj) continue;
+    const size_t p = (size_t)gj * m.pitch + gi;
+    unsigned code = m.cls[p];
+    const int r = (lj + 3) * RX + (li + 3);
+    T rhs[4] = {T(0), T(0), T(0), T(0)};
+    if ((code & 15u) != 15u) {
+      T jac;
+      if (CURV) jac = static_cast<const T *>(m.met)[4 * m.field + p];
+      else jac = kc<T>(a).mc[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        rhs[c] = -jac * (dline(sf + c * RN, r, 1, code & 15u) + dline(sf + (4 + c) * RN, r, RX, code >> 4));
+      if (s0 < s1) {
+        // the tile's SAT entries are sorted by (j, i): binary search for this point
+        uint32_t key = (uint32_t)gi | ((uint32_t)gj << 16);
+        int lo = s0, hi = s1;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          uint32_t km = a.sat_ij[mid];
+          if ((km >> 16) < (key >> 16) || ((km >> 16) == (key >> 16) && (km & 0xFFFFu) < (key & 0xFFFFu))) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < s1 && a.sat_ij[lo] == key) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) rhs[c] += satb[c * a.nsat + lo];
+        }
+      }
+    }
     T *out = static_cast<T *>(a.out);
     if (a.mode == 0) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) out[c * m.field + p] = srhs[c * NT + tid];
+      for (int c = 0; c < 4; ++c) out[c * m.field + p] = rhs[c];
     } else {
       T *qn = static_cast<T *>(a.qnext);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        T rc = srhs[c * NT + tid];
-        out[c * m.field + p] = rc;
-        double acc = (double)sq[c * RN + rown];
-        for (int k = 0; k < a.nold; ++k) acc += a.alpha[k] * (double)static_cast<const T *>(a.hold[k])[c * m.field + p];
-        acc += a.alpha[a.nold] * (double)rc;
+        out[c * m.field + p] = rhs[c];
+        double acc = (double)q[c * m.field + p];
+        for (int h = 0; h < a.nold; ++h)
+          acc += a.alpha[h] * (double)static_cast<const T *>(a.hold[h])[c * m.field + p];
+        acc += a.alpha[a.nold] * (double)rhs[c];
         qn[c * m.field + p] = (T)acc;
       }
     }
   }
 }
 
-template <typename T, bool VISC, bool CURV>
+template <typename T, bool VISC, bool CURV, int TY>
 static cudaError_t launch_rhs_t(const RhsLaunch &a, cudaStream_t s) {
-  using S = RhsSmem<T, VISC, CURV>;
-  auto kern = k_rhs<T, VISC, CURV>;
+  using U = UpdTile<T, TY>;
+  auto ku = k_update<T, VISC, CURV, TY>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    cudaError_t e = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U::bytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((a.m.ni + S::TX - 1) / S::TX, (a.m.nj + S::TY - 1) / S::TY);
-  kern<<<grid, S::NT, S::bytes, s>>>(a);
+  dim3 grid((a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
+  k_flux<T, VISC, CURV, TY><<<grid, kNT, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ku<<<grid, kNT, U::bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T, bool VISC, bool CURV>
+static cudaError_t launch_rhs_ty(const RhsLaunch &a, cudaStream_t s) {
+  switch (a.rows_per_cta) {
+    case 8: return launch_rhs_t<T, VISC, CURV, 8>(a, s);
+    case 16: return launch_rhs_t<T, VISC, CURV, 16>(a, s);
+    case 32: return launch_rhs_t<T, VISC, CURV, 32>(a, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_rhs(const RhsLaunch &a, int dtype, bool viscous, cudaStream_t s) {
   bool curv = !a.m.cart;
   if (dtype == SBP_F64) {
-    if (viscous) return curv ? launch_rhs_t<double, true, true>(a, s) : launch_rhs_t<double, true, false>(a, s);
-    return curv ? launch_rhs_t<double, false, true>(a, s) : launch_rhs_t<double, false, false>(a, s);
+    if (viscous) return curv ? launch_rhs_ty<double, true, true>(a, s) : launch_rhs_ty<double, true, false>(a, s);
+    return curv ? launch_rhs_ty<double, false, true>(a, s) : launch_rhs_ty<double, false, false>(a, s);
   }
-  if (viscous) return curv ? launch_rhs_t<float, true, true>(a, s) : launch_rhs_t<float, true, false>(a, s);
-  return curv ? launch_rhs_t<float, false, true>(a, s) : launch_rhs_t<float, false, false>(a, s);
-}
-
-size_t rhs_smem_bytes(int dtype, bool viscous, bool curv) {
-  if (dtype == SBP_F64) {
-    if (viscous) return curv ? RhsSmem<double, true, true>::bytes : RhsSmem<double, true, false>::bytes;
-    return curv ? RhsSmem<double, false, true>::bytes : RhsSmem<double, false, false>::bytes;
-  }
-  if (viscous) return curv ? RhsSmem<float, true, true>::bytes : RhsSmem<float, true, false>::bytes;
-  return curv ? RhsSmem<float, false, true>::bytes : RhsSmem<float, false, false>::bytes;
+  if (viscous) return curv ? launch_rhs_ty<float, true, true>(a, s) : launch_rhs_ty<float, true, false>(a, s);
+  return curv ? launch_rhs_ty<float, false, true>(a, s) : launch_rhs_ty<float, false, false>(a, s);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -562,6 +714,118 @@ cudaError_t launch_interp(const InterpLaunch &a, int dtype, bool viscous, cudaSt
   }
   if (viscous) return curv ? launch_interp_t<float, true, true>(a, s) : launch_interp_t<float, true, false>(a, s);
   return curv ? launch_interp_t<float, false, true>(a, s) : launch_interp_t<float, false, false>(a, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Donor-point values for the fused gather of k_rhs. One thread per (extrapolation set, distinct
+// donor point): the state q + sum_k beta_k hist_k (FP64 accumulation; Sec. 3.3 Step 2 for the
+// slow extrapolant at a micro time) and, for Navier-Stokes, the Cartesian viscous fluxes of that
+// state by the donor mesh's own SBP derivatives.
+template <typename T>
+__device__ __forceinline__ void set_state(const DonorLaunch &a, int set, size_t p, T out[4]) {
+  const T *q = static_cast<const T *>(a.q);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    double acc = (double)q[v * a.d.field + p];
+    for (int k = 0; k < a.nb[set]; ++k)
+      acc += a.beta[set][k] * (double)static_cast<const T *>(a.hist[k])[v * a.d.field + p];
+    out[v] = (T)acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void set_prim(const DonorLaunch &a, int set, int i, int j, T gam, T pr[3]) {
+  T s[4];
+  set_state(a, set, (size_t)j * a.d.pitch + i, s);
+  T ri = T(1) / s[0];
+  T u = s[1] * ri, v = s[2] * ri;
+  T p = (gam - T(1)) * (s[3] - T(0.5) * (s[1] * u + s[2] * v));
+  pr[0] = u;
+  pr[1] = v;
+  pr[2] = gam * p * ri;
+}
+
+template <typename T, bool VISC, bool CURV>
+__global__ void __launch_bounds__(128) k_donor_vals(const DonorLaunch a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nsets * a.npts) return;
+  const int set = t / a.npts, d = t - set * a.npts;
+  const uint32_t ij = a.pts[d];
+  const int ii = (int)(ij & 0xFFFFu), jj = (int)(ij >> 16);
+  const size_t p = (size_t)jj * a.d.pitch + ii;
+  T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * a.npts;
+  T s[4];
+  set_state(a, set, p, s);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) dv[v * a.npts + d] = s[v];
+  if constexpr (VISC) {
+    const T gam = (T)a.g.gamma, mu = (T)a.g.mu, kap = (T)(a.g.mu / (a.g.pr * (a.g.gamma - 1.0)));
+    unsigned code = a.d.cls[p];
+    T dxi[3] = {0, 0, 0}, deta[3] = {0, 0, 0};
+    for (int dir = 0; dir < 2; ++dir) {
+      int row, sgn;
+      row_of(dir == 0 ? (code & 15u) : (code >> 4), row, sgn);
+      for (int e = 0; e < 4; ++e) {
+        T we = wgt<T>(row, e);
+        if (we == T(0)) continue;
+        int ni_ = ii, nj_ = jj;
+        if (dir == 0) ni_ += sgn * c_off[row][e];
+        else nj_ += sgn * c_off[row][e];
+        wrap_index(ni_, a.d.ni, a.d.per_i);
+        wrap_index(nj_, a.d.nj, a.d.per_j);
+        T pr[3];
+        set_prim(a, set, ni_, nj_, gam, pr);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          if (dir == 0) dxi[f] += T(sgn) * we * pr[f];
+          else deta[f] += T(sgn) * we * pr[f];
+        }
+      }
+    }
+    T mt[5];
+    if (CURV) {
+      const T *met = static_cast<const T *>(a.d.met);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) mt[c] = met[c * a.d.field + p];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) mt[c] = (T)a.d.mc[c];
+    }
+    T gr[6];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      gr[2 * f] = mt[4] * (mt[0] * dxi[f] + mt[2] * deta[f]);
+      gr[2 * f + 1] = mt[4] * (mt[1] * dxi[f] + mt[3] * deta[f]);
+    }
+    T ri = T(1) / s[0];
+    T Fv[3], Gv[3];
+    viscous_flux(s[1] * ri, s[2] * ri, gr, mu, kap, Fv, Gv);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dv[(4 + c) * a.npts + d] = Fv[c];
+      dv[(7 + c) * a.npts + d] = Gv[c];
+    }
+  }
+}
+
+template <typename T, bool VISC, bool CURV>
+static cudaError_t launch_donor_vals_t(const DonorLaunch &a, cudaStream_t s) {
+  int n = a.nsets * a.npts;
+  if (n == 0) return cudaSuccess;
+  k_donor_vals<T, VISC, CURV><<<(n + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_donor_vals(const DonorLaunch &a, int dtype, bool viscous, cudaStream_t s) {
+  bool curv = !a.d.cart;
+  if (dtype == SBP_F64) {
+    if (viscous)
+      return curv ? launch_donor_vals_t<double, true, true>(a, s) : launch_donor_vals_t<double, true, false>(a, s);
+    return curv ? launch_donor_vals_t<double, false, true>(a, s) : launch_donor_vals_t<double, false, false>(a, s);
+  }
+  if (viscous)
+    return curv ? launch_donor_vals_t<float, true, true>(a, s) : launch_donor_vals_t<float, true, false>(a, s);
+  return curv ? launch_donor_vals_t<float, false, true>(a, s) : launch_donor_vals_t<float, false, false>(a, s);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -407,6 +407,29 @@ sbp_status setup_donors(MeshHost &rm, const MeshHost &d, std::string &err) {
       rm.donor_w[8 * r + 4 + a] = lj[a];
     }
   }
+  // distinct donor points, so that per-point work (extrapolation, viscous fluxes) is done once
+  std::vector<uint32_t> all;
+  all.reserve(16 * nr);
+  auto packed = [&](size_t r, int a, int b) {
+    int ii = ((rm.donor_base[2 * r] + a) % d.ni + d.ni) % d.ni;
+    int jj = ((rm.donor_base[2 * r + 1] + b) % d.nj + d.nj) % d.nj;
+    return (uint32_t)ii | ((uint32_t)jj << 16);
+  };
+  for (size_t r = 0; r < nr; ++r)
+    for (int b = 0; b < 4; ++b)
+      for (int a = 0; a < 4; ++a) all.push_back(packed(r, a, b));
+  auto key = [](uint32_t v) { return ((uint64_t)(v >> 16) << 16) | (v & 0xFFFFu); };
+  std::sort(all.begin(), all.end(), [&](uint32_t x, uint32_t y) { return key(x) < key(y); });
+  all.erase(std::unique(all.begin(), all.end()), all.end());
+  rm.donor_pts = all;
+  rm.donor_idx.assign(16 * nr, 0);
+  for (size_t r = 0; r < nr; ++r)
+    for (int b = 0; b < 4; ++b)
+      for (int a = 0; a < 4; ++a) {
+        uint32_t v = packed(r, a, b);
+        auto it = std::lower_bound(all.begin(), all.end(), v, [&](uint32_t x, uint32_t y) { return key(x) < key(y); });
+        rm.donor_idx[16 * r + b * 4 + a] = (int)(it - all.begin());
+      }
   return SBP_OK;
 }
 
