@@ -747,72 +747,103 @@ __device__ __forceinline__ void set_prim(const DonorLaunch &a, int set, int i, i
 
 template <typename T, bool VISC, bool CURV>
 __global__ void __launch_bounds__(128) k_donor_vals(const DonorLaunch a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.nsets * a.npts) return;
-  const int set = t / a.npts, d = t - set * a.npts;
-  const uint32_t ij = a.pts[d];
-  const int ii = (int)(ij & 0xFFFFu), jj = (int)(ij >> 16);
-  const size_t p = (size_t)jj * a.d.pitch + ii;
-  T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * a.npts;
-  T s[4];
-  set_state(a, set, p, s);
+  const int n = a.nsets * a.npts;
+  if constexpr (!VISC) {
+    // Euler: one thread per (set, donor point)
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int set = t / a.npts, d = t - set * a.npts;
+    const uint32_t ij = a.pts[d];
+    const size_t p = (size_t)(ij >> 16) * a.d.pitch + (ij & 0xFFFFu);
+    T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * a.npts;
+    T s[4];
+    set_state(a, set, p, s);
 #pragma unroll
-  for (int v = 0; v < 4; ++v) dv[v * a.npts + d] = s[v];
-  if constexpr (VISC) {
-    const T gam = (T)a.g.gamma, mu = (T)a.g.mu, kap = (T)(a.g.mu / (a.g.pr * (a.g.gamma - 1.0)));
-    unsigned code = a.d.cls[p];
-    T dxi[3] = {0, 0, 0}, deta[3] = {0, 0, 0};
-    for (int dir = 0; dir < 2; ++dir) {
+    for (int v = 0; v < 4; ++v) dv[v * a.npts + d] = s[v];
+  } else {
+    // Navier-Stokes: a 16-lane group per (set, donor point). Lane 0 holds the point itself,
+    // lanes 1-4 the xi-stencil and lanes 5-8 the eta-stencil points of its derivative classes;
+    // every lane evaluates the extrapolated state and primitives of its point, and the
+    // stencil-weighted primitives are summed over the group with shuffles.
+    const int l = threadIdx.x & 15;
+    const int pair = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    const bool valid = pair < n;
+    const int set = valid ? pair / a.npts : 0, d = valid ? pair - set * a.npts : 0;
+    const uint32_t ij = valid ? a.pts[d] : 0u;
+    const int ii = (int)(ij & 0xFFFFu), jj = (int)(ij >> 16);
+    const size_t p = (size_t)jj * a.d.pitch + ii;
+    const unsigned code = valid ? a.d.cls[p] : 0xFFu;
+    const T gam = (T)a.g.gamma;
+    int pi = ii, pj = jj, dir = 2;
+    T w = T(0);
+    if (l >= 1 && l <= 8) {
+      dir = l <= 4 ? 0 : 1;
       int row, sgn;
       row_of(dir == 0 ? (code & 15u) : (code >> 4), row, sgn);
-      for (int e = 0; e < 4; ++e) {
-        T we = wgt<T>(row, e);
-        if (we == T(0)) continue;
-        int ni_ = ii, nj_ = jj;
-        if (dir == 0) ni_ += sgn * c_off[row][e];
-        else nj_ += sgn * c_off[row][e];
-        wrap_index(ni_, a.d.ni, a.d.per_i);
-        wrap_index(nj_, a.d.nj, a.d.per_j);
-        T pr[3];
-        set_prim(a, set, ni_, nj_, gam, pr);
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-          if (dir == 0) dxi[f] += T(sgn) * we * pr[f];
-          else deta[f] += T(sgn) * we * pr[f];
-        }
-      }
+      const int e = (l - 1) & 3;
+      w = T(sgn) * wgt<T>(row, e);
+      const int off = sgn * c_off[row][e];
+      if (dir == 0) pi += off;
+      else pj += off;
+      wrap_index(pi, a.d.ni, a.d.per_i);
+      wrap_index(pj, a.d.nj, a.d.per_j);
     }
-    T mt[5];
-    if (CURV) {
-      const T *met = static_cast<const T *>(a.d.met);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) mt[c] = met[c * a.d.field + p];
-    } else {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) mt[c] = (T)a.d.mc[c];
-    }
-    T gr[6];
+    const bool act = valid && (l == 0 || w != T(0));
+    T s[4] = {T(1), T(0), T(0), T(2.5)};
+    if (act) set_state(a, set, (size_t)pj * a.d.pitch + pi, s);
+    const T ri = T(1) / s[0];
+    const T pr[3] = {s[1] * ri, s[2] * ri, gam * (gam - T(1)) * (s[3] - T(0.5) * (s[1] * s[1] + s[2] * s[2]) * ri) * ri};
+    T cx[3], cy[3];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      gr[2 * f] = mt[4] * (mt[0] * dxi[f] + mt[2] * deta[f]);
-      gr[2 * f + 1] = mt[4] * (mt[1] * dxi[f] + mt[3] * deta[f]);
+      cx[f] = (act && dir == 0) ? w * pr[f] : T(0);
+      cy[f] = (act && dir == 1) ? w * pr[f] : T(0);
     }
-    T ri = T(1) / s[0];
-    T Fv[3], Gv[3];
-    viscous_flux(s[1] * ri, s[2] * ri, gr, mu, kap, Fv, Gv);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      dv[(4 + c) * a.npts + d] = Fv[c];
-      dv[(7 + c) * a.npts + d] = Gv[c];
+    for (int o = 8; o > 0; o >>= 1) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        cx[f] += __shfl_xor_sync(0xffffffffu, cx[f], o);
+        cy[f] += __shfl_xor_sync(0xffffffffu, cy[f], o);
+      }
+    }
+    if (valid && l == 0) {
+      T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * a.npts;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dv[v * a.npts + d] = s[v];
+      const T mu = (T)a.g.mu, kap = (T)(a.g.mu / (a.g.pr * (a.g.gamma - 1.0)));
+      T mt[5];
+      if (CURV) {
+        const T *met = static_cast<const T *>(a.d.met);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) mt[c] = met[c * a.d.field + p];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) mt[c] = (T)a.d.mc[c];
+      }
+      T gr[6];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        gr[2 * f] = mt[4] * (mt[0] * cx[f] + mt[2] * cy[f]);
+        gr[2 * f + 1] = mt[4] * (mt[1] * cx[f] + mt[3] * cy[f]);
+      }
+      T Fv[3], Gv[3];
+      viscous_flux(pr[0], pr[1], gr, mu, kap, Fv, Gv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dv[(4 + c) * a.npts + d] = Fv[c];
+        dv[(7 + c) * a.npts + d] = Gv[c];
+      }
     }
   }
 }
 
 template <typename T, bool VISC, bool CURV>
 static cudaError_t launch_donor_vals_t(const DonorLaunch &a, cudaStream_t s) {
-  int n = a.nsets * a.npts;
+  long n = (long)a.nsets * a.npts;
   if (n == 0) return cudaSuccess;
-  k_donor_vals<T, VISC, CURV><<<(n + 127) / 128, 128, 0, s>>>(a);
+  long threads = VISC ? 16 * n : n;
+  k_donor_vals<T, VISC, CURV><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
