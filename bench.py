@@ -46,6 +46,7 @@ def _args():
     ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batched workload")
     return ap.parse_args()
 
 
@@ -264,6 +265,50 @@ def _roofline(res, wl, dtype, hbm_peak, peak_kind):
     return roof
 
 
+def _run_batch(dtype, steps, warmup, seed=0):
+    """64 independent 2D Euler vortex systems (backgrounds 128^2..512^2, fine patches at ratio
+    2, 4 or 8 = their MRAB step ratio), one cooperative persistent launch per micro step."""
+    import torch
+    import paper_1805_06607_gb300 as sbp
+    import workloads as W
+
+    wls = W.batched_vortices(seed=seed)
+    t0 = time.perf_counter()
+    members = []
+    for wl in wls:
+        g = sbp.System(wl, dtype=dtype)
+        g.autotune(False)
+        g.bind(wl["q0"])
+        g.mrab_init()
+        members.append(g)
+    b = sbp.Batch(members, autotune=True)
+    setup_s = time.perf_counter() - t0
+    evals = sum(wl["meshes"][0]["n"][0] * wl["meshes"][0]["n"][1]
+                + wl["params"]["step_ratio"] * wl["meshes"][1]["n"][0] * wl["meshes"][1]["n"][1] for wl in wls)
+    points = sum(m["n"][0] * m["n"][1] for wl in wls for m in wl["meshes"])
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        b.step(1)
+    b.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.check()
+    ms = e0.elapsed_time(e1) / steps
+    info = b.info()
+    b.close()
+    for g in members:
+        g.close()
+    return {"value": evals / (ms / 1e3), "unit": "point-evals/s", "ms_per_step": ms, "dtype": dtype,
+            "systems": len(wls), "points": points, "evals_per_step": evals,
+            "step": "one macro step of every member = max(step ratio) cooperative launches (CUDA graph)",
+            "l2": "working set (%.1f GB) larger than L2" % (points * 4 * (8 if dtype == "f64" else 4) * 5 / 1e9),
+            "rows_per_cta": info["rows_per_cta"], "grid": info["grid"], "setup_s": setup_s}
+
+
 def _cpu_baseline(wl, seconds):
     """The oracle, as it stands, on the host: whole MRAB macro steps of the same workload."""
     import numpy as np
@@ -369,6 +414,8 @@ def main():
                                     "roofline": _roofline(r2, wl, other, hbm_peak, peak_kind),
                                     "autotuned_blocks": r2["tuning"],
                                     "phases_ms_per_step": {p: v[0] / args.steps for p, v in r2["prof"].items()}}}
+    if not args.no_batch:
+        line["batched"] = {dt: _run_batch(dt, args.steps, args.warmup, seed=rank) for dt in ("f64", "f32")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:

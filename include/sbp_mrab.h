@@ -196,6 +196,29 @@ enum { SBP_PHASE_INTERP_SLOW = 0, SBP_PHASE_RHS_SLOW = 1, SBP_PHASE_INTERP_FAST 
 sbp_status sbp_profile_enable(sbp_system_t sys, int enable);
 sbp_status sbp_profile_read(sbp_system_t sys, double *ms, int *launches, int reset);
 
+/* ---- Batches of overset systems --------------------------------------------------------------
+ * Many independent two-mesh systems (for example many small problems of different sizes and
+ * step ratios) advanced together: every MRAB micro step (Sec. 3.3) of every member is ONE
+ * cooperative persistent launch with three phases separated by grid barriers: donor values of
+ * all receiving meshes, contravariant fluxes of all tiles, then SBP derivatives + SAT + update
+ * of all tiles. A macro step is max(step_ratio) such launches, replayed as a CUDA graph per
+ * ring phase. The grid barrier's spin is bounded (about a second); on expiry the kernel records
+ * SBP_ERR_TIMEOUT in the batch's error word (sbp_batch_check) and returns.
+ * Members must be initialised (sbp_mrab_init), share element type, physics and fine-mesh kind
+ * (all Cartesian or all curvilinear) and have a Cartesian slow mesh; they stay usable on their
+ * own (their states and ring positions follow the batch). The results equal stepping each
+ * member alone. autotune != 0 picks the tile height (8 or 16 rows) by timing two macro steps
+ * per candidate on a snapshot of every member's buffers (restored afterwards). */
+typedef struct sbp_batch_s *sbp_batch_t;
+sbp_status sbp_batch_create(const sbp_system_t *systems, int n, int autotune, void *stream, sbp_batch_t *out);
+sbp_status sbp_batch_destroy(sbp_batch_t batch);
+/* n macro steps of every member (asynchronous). */
+sbp_status sbp_batch_step(sbp_batch_t batch, int n, void *stream);
+/* members, tile rows per CTA, cooperative grid size, number of ring phases (graphs). */
+sbp_status sbp_batch_info(sbp_batch_t batch, int *members, int *rows_per_cta, int *grid, int *period);
+/* Synchronise the stream and report (then clear) the batch's device error word. */
+sbp_status sbp_batch_check(sbp_batch_t batch, void *stream);
+
 /* Synchronise the stream and report (then clear) the device error word. */
 sbp_status sbp_check(sbp_system_t sys, void *stream);
 

@@ -73,6 +73,13 @@ _SIGS = {
     "sbp_autotune": [_P, _I, _P],
     "sbp_profile_read": [_P, _P, _P, _I],
 }
+_SIGS.update({
+    "sbp_batch_create": [ctypes.POINTER(_P), _I, _I, _P, ctypes.POINTER(_P)],
+    "sbp_batch_destroy": [_P],
+    "sbp_batch_step": [_P, _I, _P],
+    "sbp_batch_info": [_P, _P, _P, _P, _P],
+    "sbp_batch_check": [_P, _P],
+})
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
@@ -290,6 +297,42 @@ class System:
 
     def check(self, stream=None):
         _check(_lib.sbp_check(self.h, _stream(stream)), "sbp_check")
+
+
+class Batch:
+    """Member systems (already bound and initialised) advanced together, one cooperative
+    persistent launch per micro step (C ABI: sbp_batch_*)."""
+
+    def __init__(self, systems, autotune=True, stream=None):
+        self.systems = list(systems)
+        arr = (ctypes.c_void_p * len(self.systems))(*[g.h.value for g in self.systems])
+        h = ctypes.c_void_p()
+        _check(_lib.sbp_batch_create(arr, len(self.systems), int(bool(autotune)), _stream(stream), ctypes.byref(h)),
+               "sbp_batch_create")
+        self.h = h
+
+    def step(self, n=1, stream=None):
+        _check(_lib.sbp_batch_step(self.h, int(n), _stream(stream)), "sbp_batch_step")
+
+    def info(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(_lib.sbp_batch_info(self.h, *[ctypes.cast(ctypes.pointer(x), ctypes.c_void_p) for x in v]),
+               "sbp_batch_info")
+        return {"members": v[0].value, "rows_per_cta": v[1].value, "grid": v[2].value, "period": v[3].value}
+
+    def check(self, stream=None):
+        _check(_lib.sbp_batch_check(self.h, _stream(stream)), "sbp_batch_check")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def exported_symbols():

@@ -291,8 +291,7 @@ struct sbp_system_s {
 
   // Donor values of mesh `recv`'s receivers from the other mesh's state at `q`, for the
   // extrapolation sets [set0, set0 + nsets) of the plan (set j: slow extrapolant over [0, j/SR]).
-  cudaError_t donor_vals(int recv, const void *q, int set0, int nsets, bool extrapolate, double Hh,
-                         cudaStream_t s) {
+  DonorLaunch donor_args(int recv, const void *q, int set0, int nsets, bool extrapolate, double Hh) const {
     DonorLaunch a{};
     const int don = 1 - recv, m = plan.m;
     a.d = dev_mesh(don);
@@ -308,14 +307,23 @@ struct sbp_system_s {
       a.nb[j] = (extrapolate && set > 0) ? m : 0;
       for (int k = 0; k < m; ++k) a.beta[j][k] = extrapolate ? plan.ext[set][k] * Hh : 0.0;
     }
-    return launch_donor_vals(a, p.dtype, viscous(), s);
+    return a;
+  }
+
+  cudaError_t donor_vals(int recv, const void *q, int set0, int nsets, bool extrapolate, double Hh,
+                         cudaStream_t s) {
+    return launch_donor_vals(donor_args(recv, q, set0, nsets, extrapolate, Hh), p.dtype, viscous(), s);
   }
 
   // Fused right-hand side + Adams-Bashforth update of mesh k with step dt, receivers gathered
   // from donor-value set `set`. Pushes the new right-hand side into the ring slot after head.
   cudaError_t fused(int k, int set, double dt, cudaStream_t s) {
+    return launch_rhs(fused_args(k, set, dt), p.dtype, viscous(), s);
+  }
+
+  RhsLaunch fused_args(int k, int set, double dt) const {
     const int m = plan.m;
-    MeshDev &d = md[k];
+    const MeshDev &d = md[k];
     int slot = (d.head + 1) % m;
     RhsLaunch a = rhs_args(k, d.q[d.cur]);
     a.dv = (char *)d.dv + (size_t)set * 10 * d.ndv * esz;
@@ -330,7 +338,7 @@ struct sbp_system_s {
       a.alpha[j] = plan.ab[j] * dt;
     }
     a.alpha[m - 1] = plan.ab[m - 1] * dt;
-    return launch_rhs(a, p.dtype, viscous(), s);
+    return a;
   }
 
   // Enqueue one macro step (Sec. 3.3) for the current ring heads and state buffers, without
@@ -859,6 +867,316 @@ sbp_status sbp_check(sbp_system_t S, void *stream) {
   CUDA_TRY(cudaMemcpy(&e, S->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemset(S->d_err, 0, sizeof(int)));
   if (e) return fail((sbp_status)e, "device error word set");
+  return SBP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batches: many independent overset systems advanced together, one cooperative persistent
+// launch per micro step (donor values, fluxes and updates of all members, with grid barriers
+// in between). The member systems keep their own tables and buffers; the batch holds, for each
+// ring/buffer phase of the members, device arrays of launch descriptors and tile work lists.
+namespace {
+int gcd_i(int a, int b) { return b ? gcd_i(b, a % b) : a; }
+
+struct MemberBook {
+  int cur[2], head[2], count[2];
+  double t;
+};
+
+MemberBook save_book(const sbp_system_s *S) {
+  MemberBook b{};
+  for (int k = 0; k < 2; ++k) {
+    b.cur[k] = S->md[k].cur;
+    b.head[k] = S->md[k].head;
+    b.count[k] = S->md[k].count;
+  }
+  b.t = S->t;
+  return b;
+}
+
+void load_book(sbp_system_s *S, const MemberBook &b) {
+  for (int k = 0; k < 2; ++k) {
+    S->md[k].cur = b.cur[k];
+    S->md[k].head = b.head[k];
+    S->md[k].count = b.count[k];
+  }
+  S->t = b.t;
+}
+}  // namespace
+
+struct sbp_batch_s {
+  std::vector<sbp_system_t> mem;
+  int dtype = SBP_F64;
+  bool visc = false, curvf = false;
+  int ty = 16, grid = 0, srmax = 1, period = 1, variant = 0;
+  std::vector<std::vector<BatchSubstep>> subs;  // [period][srmax]
+  std::vector<void *> allocs;
+  unsigned *bar = nullptr;
+  int *err = nullptr;
+  cudaStream_t cap = nullptr;
+  std::map<int, cudaGraphExec_t> graphs;
+
+  void free_plan() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+    subs.clear();
+  }
+  ~sbp_batch_s() {
+    free_plan();
+    cudaFree(bar);
+    cudaFree(err);
+    if (cap) cudaStreamDestroy(cap);
+  }
+
+  template <typename V>
+  cudaError_t up(const std::vector<V> &v, const V *&dst) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(v.size() * sizeof(V), 16));
+    if (e != cudaSuccess) return e;
+    allocs.push_back(p);
+    if (!v.empty()) e = cudaMemcpy(p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice);
+    dst = static_cast<const V *>(p);
+    return e;
+  }
+
+  // Launch descriptors and work lists for `period` consecutive macro steps from the members'
+  // current ring/buffer phase (which they return to after `period` steps).
+  cudaError_t build_plan() {
+    free_plan();
+    std::vector<MemberBook> start;
+    for (auto *S : mem) start.push_back(save_book(S));
+    subs.assign(period, std::vector<BatchSubstep>(srmax));
+    for (int v = 0; v < period; ++v) {
+      std::vector<std::vector<DonorLaunch>> dl(srmax);
+      std::vector<std::vector<RhsLaunch>> rl(srmax);
+      std::vector<std::vector<int4>> items(srmax);
+      auto add_rhs = [&](int j, sbp_system_s *S, int k, RhsLaunch a) {
+        a.rows_per_cta = ty;
+        int r = (int)rl[j].size();
+        rl[j].push_back(a);
+        int ntx = (S->mh[k].ni + kTileX - 1) / kTileX, nty = (S->mh[k].nj + ty - 1) / ty;
+        for (int by = 0; by < nty; ++by)
+          for (int bx = 0; bx < ntx; ++bx) items[j].push_back(make_int4(r, bx, by, S->mh[k].cartesian ? 0 : 1));
+      };
+      for (auto *S : mem) {
+        MemberBook b0 = save_book(S);
+        const int F = S->fast(), Sl = S->slow(), sr = S->plan.sr, m = S->plan.m;
+        const double H = S->H, h = H / sr;
+        dl[0].push_back(S->donor_args(Sl, S->md[F].q[S->md[F].cur], 0, 1, false, H));
+        dl[0].push_back(S->donor_args(F, S->md[Sl].q[S->md[Sl].cur], 0, 1, false, H));
+        add_rhs(0, S, Sl, S->fused_args(Sl, 0, H));
+        S->md[Sl].head = (S->md[Sl].head + 1) % m;
+        for (int j = 0; j < sr; ++j) {
+          if (j > 0) dl[j].push_back(S->donor_args(F, S->md[Sl].q[S->md[Sl].cur], j, 1, true, H));
+          add_rhs(j, S, F, S->fused_args(F, j, h));
+          S->md[F].head = (S->md[F].head + 1) % m;
+          S->md[F].cur ^= 1;
+        }
+        load_book(S, b0);
+        S->advance();
+      }
+      for (int j = 0; j < srmax; ++j) {
+        BatchSubstep &b = subs[v][j];
+        std::vector<int> off(1, 0);
+        for (auto &a : dl[j]) off.push_back(off.back() + a.nsets * a.npts);
+        cudaError_t e;
+        const DonorLaunch *ddl;
+        const RhsLaunch *drl;
+        if ((e = up(dl[j], ddl)) != cudaSuccess) return e;
+        if ((e = up(off, b.dl_off)) != cudaSuccess) return e;
+        if ((e = up(rl[j], drl)) != cudaSuccess) return e;
+        if ((e = up(items[j], b.items)) != cudaSuccess) return e;
+        b.dl = ddl;
+        b.rl = drl;
+        b.n_dl = (int)dl[j].size();
+        b.n_items = (int)items[j].size();
+        b.bar_count = bar;
+        b.bar_gen = bar + 1;
+        b.err = err;
+      }
+    }
+    for (size_t i = 0; i < mem.size(); ++i) load_book(mem[i], start[i]);
+    variant = 0;
+    return batch_grid_size(dtype, visc, curvf, ty, &grid);
+  }
+
+  cudaError_t launch_variant(cudaStream_t s) {
+    auto it = graphs.find(variant);
+    if (it == graphs.end()) {
+      cudaError_t e;
+      if (!cap && (e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+      if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+      cudaError_t ei = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), cap);
+      for (int j = 0; j < srmax && ei == cudaSuccess; ++j)
+        ei = launch_batch_substep(subs[variant][j], grid, dtype, visc, curvf, ty, cap);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(cap, &g);
+      if (ei != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return ei;
+      }
+      if (e != cudaSuccess) return e;
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return e;
+      it = graphs.emplace(variant, ex).first;
+    }
+    return cudaGraphLaunch(it->second, s);
+  }
+
+  cudaError_t step(cudaStream_t s) {
+    cudaError_t e = launch_variant(s);
+    if (e != cudaSuccess) return e;
+    for (auto *S : mem) S->advance();
+    variant = (variant + 1) % period;
+    return cudaSuccess;
+  }
+};
+
+extern "C" {
+
+sbp_status sbp_batch_create(const sbp_system_t *systems, int n, int autotune, void *stream, sbp_batch_t *out) {
+  if (!systems || n < 1 || !out) return fail(SBP_ERR_ARG, "bad argument");
+  *out = nullptr;
+  auto *B = new sbp_batch_s();
+  std::unique_ptr<sbp_batch_s> guard(B);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < n; ++i) {
+    sbp_system_s *S = systems[i];
+    if (!S) return fail(SBP_ERR_ARG, "null member");
+    if (!S->initialised) return fail(SBP_ERR_STATE, "member " + std::to_string(i) + " has not run sbp_mrab_init");
+    for (int j = 0; j < i; ++j)
+      if (systems[j] == S) return fail(SBP_ERR_ARG, "a system appears twice in the batch");
+    bool cf = !S->mh[S->fast()].cartesian;
+    if (i == 0) {
+      B->dtype = S->p.dtype;
+      B->visc = S->viscous();
+      B->curvf = cf;
+    } else if (S->p.dtype != B->dtype || S->viscous() != B->visc || cf != B->curvf) {
+      return fail(SBP_ERR_ARG, "batch members must share element type, physics and fine-mesh kind");
+    }
+    if (!S->mh[S->slow()].cartesian) return fail(SBP_ERR_ARG, "batch members need a Cartesian slow mesh");
+    B->srmax = std::max(B->srmax, S->plan.sr);
+    B->mem.push_back(S);
+  }
+  // common period of the members' ring/buffer phases
+  int period = 1;
+  for (auto *S : B->mem) {
+    MemberBook b0 = save_book(S);
+    uint64_t k0 = S->phase_key();
+    int pb = 0;
+    do {
+      S->advance();
+      ++pb;
+    } while (S->phase_key() != k0 && pb < 64);
+    load_book(S, b0);
+    if (pb >= 64) return fail(SBP_ERR_STATE, "ring phase period above 64");
+    period = period / gcd_i(period, pb) * pb;
+    if (period > 64) return fail(SBP_ERR_STATE, "common ring phase period above 64");
+  }
+  B->period = period;
+  CUDA_TRY(cudaMalloc((void **)&B->bar, 2 * sizeof(unsigned)));
+  CUDA_TRY(cudaMemset(B->bar, 0, 2 * sizeof(unsigned)));
+  CUDA_TRY(cudaMalloc((void **)&B->err, sizeof(int)));
+  CUDA_TRY(cudaMemset(B->err, 0, sizeof(int)));
+  if (autotune) {
+    // time two macro steps per tile height on a snapshot of every member, then restore
+    std::vector<void *> snap;
+    std::vector<std::pair<void *, size_t>> bufs;
+    for (auto *S : B->mem)
+      for (int k = 0; k < 2; ++k) {
+        size_t sb = S->state_elems(k) * S->esz;
+        bufs.push_back({S->md[k].q[0], sb});
+        bufs.push_back({S->md[k].q[1], sb});
+        bufs.push_back({S->md[k].hist, sb * S->plan.m});
+      }
+    size_t total = 0;
+    for (auto &b : bufs) total += b.second;
+    void *store = nullptr;
+    CUDA_TRY(cudaMalloc(&store, total));
+    auto copy = [&](bool save) {
+      size_t off = 0;
+      for (auto &b : bufs) {
+        cudaError_t e = save ? cudaMemcpyAsync((char *)store + off, b.first, b.second, cudaMemcpyDeviceToDevice, s)
+                             : cudaMemcpyAsync(b.first, (char *)store + off, b.second, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        off += b.second;
+      }
+      return cudaSuccess;
+    };
+    std::vector<MemberBook> books;
+    for (auto *S : B->mem) books.push_back(save_book(S));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_ty = 16;
+    cudaError_t e = copy(true);
+    for (int ty : {8, 16}) {
+      if (e != cudaSuccess) break;
+      B->ty = ty;
+      if ((e = B->build_plan()) != cudaSuccess) break;
+      if ((e = B->step(s)) != cudaSuccess) break;  // capture + warm-up
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = B->step(s);
+      cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_ty = ty;
+      }
+      if (e == cudaSuccess) e = copy(false);
+      for (size_t i = 0; i < B->mem.size(); ++i) load_book(B->mem[i], books[i]);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(store);
+    CUDA_TRY(e);
+    int flag = 0;
+    CUDA_TRY(cudaMemcpy(&flag, B->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail((sbp_status)flag, "batch autotune step failed");
+    B->ty = best_ty;
+  }
+  CUDA_TRY(B->build_plan());
+  *out = guard.release();
+  return SBP_OK;
+}
+
+sbp_status sbp_batch_destroy(sbp_batch_t B) {
+  delete B;
+  return SBP_OK;
+}
+
+sbp_status sbp_batch_step(sbp_batch_t B, int n, void *stream) {
+  if (!B || n < 0) return fail(SBP_ERR_ARG, "bad argument");
+  for (int i = 0; i < n; ++i) CUDA_TRY(B->step((cudaStream_t)stream));
+  return SBP_OK;
+}
+
+sbp_status sbp_batch_info(sbp_batch_t B, int *members, int *rows_per_cta, int *grid, int *period) {
+  if (!B) return fail(SBP_ERR_ARG, "null batch");
+  if (members) *members = (int)B->mem.size();
+  if (rows_per_cta) *rows_per_cta = B->ty;
+  if (grid) *grid = B->grid;
+  if (period) *period = B->period;
+  return SBP_OK;
+}
+
+sbp_status sbp_batch_check(sbp_batch_t B, void *stream) {
+  if (!B) return fail(SBP_ERR_ARG, "null batch");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int flag = 0;
+  CUDA_TRY(cudaMemcpy(&flag, B->err, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(B->err, 0, sizeof(int)));
+  if (flag) return fail((sbp_status)flag, "batch device error word set");
   return SBP_OK;
 }
 

@@ -1,0 +1,643 @@
+// Device code shared by the library's CUDA translation units (sm_103a): SBP 4-2 derivative
+// rows, pointwise physics, the SAT penalty, and the tile bodies of the right-hand side
+// (flux_tile, update_tile) and of the donor values (donor_group), which the single-system
+// kernels and the batched persistent kernel both call.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+#include <cstring>
+
+#include "sbp_device.h"
+
+namespace sbp {
+
+// ---------------------------------------------------------------------------------------------
+// SBP 4-2 first derivative, every class written as four (offset, weight) pairs applied with a
+// direction sign: rows 0..3 are the boundary closures of the diagonal-norm operator with norm
+// H = diag(17/48, 59/48, 43/48, 49/48, 1, ...), row 4 the interior fourth-order central row,
+// row 5 a hole (all zero). A closure counted from a segment's high end uses the same row with
+// the offsets and the result negated.
+static __constant__ int8_t c_off[6][4] = {{0, 1, 2, 3}, {-1, 1, 0, 0}, {-2, -1, 1, 2}, {-3, -1, 1, 2}, {-2, -1, 1, 2},
+                                   {0, 0, 0, 0}};
+static __constant__ double c_w64[6][4] = {{-24.0 / 17.0, 59.0 / 34.0, -4.0 / 17.0, -3.0 / 34.0},
+                                   {-0.5, 0.5, 0.0, 0.0},
+                                   {4.0 / 43.0, -59.0 / 86.0, 59.0 / 86.0, -4.0 / 43.0},
+                                   {3.0 / 98.0, -59.0 / 98.0, 32.0 / 49.0, -4.0 / 49.0},
+                                   {1.0 / 12.0, -2.0 / 3.0, 2.0 / 3.0, -1.0 / 12.0},
+                                   {0.0, 0.0, 0.0, 0.0}};
+static __constant__ float c_w32[6][4] = {{-24.0f / 17.0f, 59.0f / 34.0f, -4.0f / 17.0f, -3.0f / 34.0f},
+                                  {-0.5f, 0.5f, 0.0f, 0.0f},
+                                  {4.0f / 43.0f, -59.0f / 86.0f, 59.0f / 86.0f, -4.0f / 43.0f},
+                                  {3.0f / 98.0f, -59.0f / 98.0f, 32.0f / 49.0f, -4.0f / 49.0f},
+                                  {1.0f / 12.0f, -2.0f / 3.0f, 2.0f / 3.0f, -1.0f / 12.0f},
+                                  {0.0f, 0.0f, 0.0f, 0.0f}};
+// p0 of eq. (int): first entry of the norm H (unit index spacing).
+#define SBP_P0 (17.0 / 48.0)
+
+template <typename T> __device__ __forceinline__ T wgt(int r, int e);
+template <> __device__ __forceinline__ double wgt<double>(int r, int e) { return c_w64[r][e]; }
+template <> __device__ __forceinline__ float wgt<float>(int r, int e) { return c_w32[r][e]; }
+
+// (row, sign) of a 4-bit class code (kind << 2 | closure row).
+__device__ __forceinline__ void row_of(unsigned code, int &row, int &sgn) {
+  unsigned kind = code >> 2;
+  row = kind == kInterior ? 4 : kind == kHole ? 5 : (int)(code & 3u);
+  sgn = kind == kRight ? -1 : 1;
+}
+
+// Derivative along a direction with element stride st at position s of array f.
+template <typename T>
+__device__ __forceinline__ T dline(const T *f, int s, int st, unsigned code) {
+  int row, sgn;
+  row_of(code, row, sgn);
+  T acc = T(0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc += wgt<T>(row, e) * f[s + sgn * c_off[row][e] * st];
+  return sgn > 0 ? acc : -acc;
+}
+
+// Index g on a line of n points: wrapped once on a periodic line; false when outside the line
+// (non-periodic) or more than one period away (strips wider than a small periodic mesh).
+__device__ __forceinline__ bool wrap_index(int &g, int n, int per) {
+  if (per) {
+    if (g < 0) g += n;
+    else if (g >= n) g -= n;
+  }
+  return (unsigned)g < (unsigned)n;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pointwise physics. q = (rho, rho u, rho v, rho E), p = (gamma-1)(rho E - rho |u|^2/2),
+// T = gamma p / rho.
+template <typename T>
+__device__ __forceinline__ void inviscid_flux(const T q[4], T gam, T F[4], T G[4], T &u, T &v, T &p) {
+  T ri = T(1) / q[0];
+  u = q[1] * ri;
+  v = q[2] * ri;
+  p = (gam - T(1)) * (q[3] - T(0.5) * (q[1] * u + q[2] * v));
+  F[0] = q[1];
+  F[1] = q[1] * u + p;
+  F[2] = q[2] * u;
+  F[3] = (q[3] + p) * u;
+  G[0] = q[2];
+  G[1] = q[1] * v;
+  G[2] = q[2] * v + p;
+  G[3] = (q[3] + p) * v;
+}
+
+// Cartesian viscous fluxes (momentum x, momentum y, energy of F^V and of G^V) from the
+// velocity and temperature gradients: Stokes hypothesis, constant mu, Fourier heat flux.
+template <typename T>
+__device__ __forceinline__ void viscous_flux(T u, T v, const T gr[6], T mu, T kap, T Fv[3], T Gv[3]) {
+  // gr = (u_x, u_y, v_x, v_y, T_x, T_y)
+  T div = gr[0] + gr[3];
+  T txx = mu * (T(2) * gr[0]) - T(2.0 / 3.0) * mu * div;
+  T tyy = mu * (T(2) * gr[3]) - T(2.0 / 3.0) * mu * div;
+  T txy = mu * (gr[1] + gr[2]);
+  Fv[0] = txx;
+  Fv[1] = txy;
+  Fv[2] = u * txx + v * txy + kap * gr[4];
+  Gv[0] = txy;
+  Gv[1] = tyy;
+  Gv[2] = u * txy + v * tyy + kap * gr[5];
+}
+
+// K^{+/-}_k (q - target) of eq. (int), applied through the eigen-decomposition of the flux
+// Jacobian in direction k at state q: the acoustic waves U +/- c|k| with strengths
+// (dp +/- rho c dUn) / (2 c^2), and the entropy and shear waves at U. side = +1 keeps the
+// positive eigenvalues ((|L| + L)/2), side = -1 the magnitude of the negative ones.
+template <typename T>
+__device__ __forceinline__ void penalty_apply(const T q[4], T gam, T kx, T ky, int side, const T dq[4], T out[4]) {
+  T rho = q[0], ri = T(1) / rho, u = q[1] * ri, v = q[2] * ri;
+  T k2 = u * u + v * v;
+  T p = (gam - T(1)) * (q[3] - T(0.5) * rho * k2);
+  T c2 = gam * p * ri, c = sqrt(c2);
+  T H = (q[3] + p) * ri;
+  T kn = sqrt(kx * kx + ky * ky), kinv = T(1) / kn;
+  T nx = kx * kinv, ny = ky * kinv;
+  T U = kx * u + ky * v, Un = U * kinv;
+  T du = (dq[1] - u * dq[0]) * ri, dv = (dq[2] - v * dq[0]) * ri;
+  T dp = (gam - T(1)) * (dq[3] - u * dq[1] - v * dq[2] + T(0.5) * k2 * dq[0]);
+  T dUn = nx * du + ny * dv;
+  T ap = (dp + rho * c * dUn) / (T(2) * c2), am = (dp - rho * c * dUn) / (T(2) * c2);
+  T a0 = dq[0] - dp / c2;
+  T dut = du - nx * dUn, dvt = dv - ny * dUn;
+  T l0 = U, lp = U + c * kn, lm = U - c * kn;
+  T f0 = side > 0 ? fmax(l0, T(0)) : fmax(-l0, T(0));
+  T fp = side > 0 ? fmax(lp, T(0)) : fmax(-lp, T(0));
+  T fm = side > 0 ? fmax(lm, T(0)) : fmax(-lm, T(0));
+  out[0] = f0 * a0 + fp * ap + fm * am;
+  out[1] = f0 * (a0 * u + rho * dut) + fp * ap * (u + c * nx) + fm * am * (u - c * nx);
+  out[2] = f0 * (a0 * v + rho * dvt) + fp * ap * (v + c * ny) + fm * am * (v - c * ny);
+  out[3] = f0 * (a0 * T(0.5) * k2 + rho * (u * dut + v * dvt)) + fp * ap * (H + c * Un) + fm * am * (H - c * Un);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Right-hand side in two kernels per mesh:
+//  k_flux    contravariant fluxes F^_xi, F^_eta (inviscid minus viscous) at every point, written
+//            to a flux buffer (8 planes) that stays in L2 for the next kernel. Navier-Stokes
+//            tiles stage the primitives with a 3-point halo in shared memory for the velocity
+//            and temperature gradients; each flux is computed once.
+//  k_update  SBP derivatives of the fluxes (3-point halo of flux planes in shared memory),
+//            -J times their sum, SAT penalties at the tile's boundary and receiver points, and
+//            the epilogue (mode 0: dq/dt; mode 1: also the Adams-Bashforth / MRAB update).
+template <typename T, bool CURV>
+__device__ __forceinline__ void point_metrics(const DevMesh &m, int gi, int gj, T mt[5]) {
+  if (CURV) {
+    const T *met = static_cast<const T *>(m.met);
+    size_t p = (size_t)gj * m.pitch + gi;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) mt[c] = met[c * m.field + p];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) mt[c] = (T)m.mc[c];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void prim_at(const T *q, size_t field, size_t p, T gam, T pr[3]) {
+  T r = q[p], ri = T(1) / r;
+  T u = q[field + p] * ri, v = q[2 * field + p] * ri;
+  T pres = (gam - T(1)) * (q[3 * field + p] - T(0.5) * (q[field + p] * u + q[2 * field + p] * v));
+  pr[0] = u;
+  pr[1] = v;
+  pr[2] = gam * pres * ri;
+}
+
+// Cartesian viscous fluxes at one point from the state in global memory (used at SAT points).
+template <typename T, bool CURV>
+__device__ void visc_at_point(const DevMesh &m, const T *q, int i, int j, T gam, T mu, T kap, T Fv[3], T Gv[3]) {
+  size_t p = (size_t)j * m.pitch + i;
+  unsigned code = m.cls[p];
+  T dxi[3] = {0, 0, 0}, deta[3] = {0, 0, 0};
+  for (int dir = 0; dir < 2; ++dir) {
+    int row, sgn;
+    row_of(dir == 0 ? (code & 15u) : (code >> 4), row, sgn);
+    for (int e = 0; e < 4; ++e) {
+      T we = wgt<T>(row, e);
+      if (we == T(0)) continue;
+      int ii = i, jj = j;
+      if (dir == 0) ii += sgn * c_off[row][e];
+      else jj += sgn * c_off[row][e];
+      wrap_index(ii, m.ni, m.per_i);
+      wrap_index(jj, m.nj, m.per_j);
+      T pr[3];
+      prim_at(q, m.field, (size_t)jj * m.pitch + ii, gam, pr);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        if (dir == 0) dxi[f] += T(sgn) * we * pr[f];
+        else deta[f] += T(sgn) * we * pr[f];
+      }
+    }
+  }
+  T mt[5];
+  point_metrics<T, CURV>(m, i, j, mt);
+  T gr[6];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    gr[2 * f] = mt[4] * (mt[0] * dxi[f] + mt[2] * deta[f]);
+    gr[2 * f + 1] = mt[4] * (mt[1] * dxi[f] + mt[3] * deta[f]);
+  }
+  T pc[3];
+  prim_at(q, m.field, p, gam, pc);
+  viscous_flux(pc[0], pc[1], gr, mu, kap, Fv, Gv);
+}
+
+// Kernel constants in the compute type.
+template <typename T>
+__device__ __forceinline__ const KConst<T> &kc(const RhsLaunch &a);
+template <>
+__device__ __forceinline__ const KConst<float> &kc<float>(const RhsLaunch &a) {
+  return a.cf;
+}
+template <>
+__device__ __forceinline__ const KConst<double> &kc<double>(const RhsLaunch &a) {
+  return a.cd;
+}
+
+template <typename T, bool CURV>
+__device__ __forceinline__ void load_met(const RhsLaunch &a, int gi, int gj, T mt[5]) {
+  if (CURV) {
+    const T *met = static_cast<const T *>(a.m.met);
+    size_t p = (size_t)gj * a.m.pitch + gi;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) mt[c] = met[c * a.m.field + p];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) mt[c] = kc<T>(a).mc[c];
+  }
+}
+
+// Cartesian viscous fluxes from gradients (u_x, u_y, v_x, v_y, T_x, T_y), Stokes hypothesis.
+template <typename T>
+__device__ __forceinline__ void visc_flux_k(const KConst<T> &k, T u, T v, const T gr[6], T Fv[3], T Gv[3]) {
+  T txx = k.mu43 * gr[0] - k.mu23 * gr[3];
+  T tyy = k.mu43 * gr[3] - k.mu23 * gr[0];
+  T txy = k.mu * (gr[1] + gr[2]);
+  Fv[0] = txx;
+  Fv[1] = txy;
+  Fv[2] = u * txx + v * txy + k.kap * gr[4];
+  Gv[0] = txy;
+  Gv[1] = tyy;
+  Gv[2] = u * txy + v * tyy + k.kap * gr[5];
+}
+
+// Gradients of (u, v, T) at smem index r of the primitive planes (row stride rx), chain rule
+// with the metrics; Cartesian meshes use the constants J xi_x = 1/hx, J eta_y = 1/hy.
+template <typename T, bool CURV>
+__device__ __forceinline__ void smem_grads(const RhsLaunch &a, const T *prim, int rn, int r, int rx, unsigned code,
+                                           const T mt[5], T gr[6]) {
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    T dxi = dline(prim + f * rn, r, 1, code & 15u);
+    T deta = dline(prim + f * rn, r, rx, code >> 4);
+    if (CURV) {
+      gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
+      gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
+    } else {
+      gr[2 * f] = kc<T>(a).jx * dxi;
+      gr[2 * f + 1] = kc<T>(a).jy * deta;
+    }
+  }
+}
+
+// SAT terms of one boundary / receiver point (Sec. 2.2 eq. (int); physical forms of Sec. 5.1):
+// q_p the point's state, (Fv, Gv) its Cartesian viscous fluxes; returns the sum in acc.
+template <typename T, bool VISC>
+__device__ void sat_terms(const RhsLaunch &a, int s, const T qp[4], const T mt[5], const T Fv[3], const T Gv[3],
+                          T acc[4]) {
+  const KConst<T> &k = kc<T>(a);
+  const T *qhat = static_cast<const T *>(a.qhat);
+  const T *fvhat = static_cast<const T *>(a.fvhat);
+  const T *dw = static_cast<const T *>(a.dwt);
+  uint32_t code = a.sat_code[s];
+  int recv = a.sat_recv[s];
+  T scale = (T)a.sat_scale[s];
+  constexpr int NRV = VISC ? 10 : 4;
+  T rv[NRV];
+#pragma unroll
+  for (int c = 0; c < NRV; ++c) rv[c] = T(0);
+  if (recv >= 0) {
+    if (a.dv) {
+      const T *dv = static_cast<const T *>(a.dv);
+      for (int e = 0; e < 16; ++e) {
+        T w = dw[8 * recv + (e & 3)] * dw[8 * recv + 4 + (e >> 2)];
+        int d = a.didx[16 * recv + e];
+#pragma unroll
+        for (int c = 0; c < NRV; ++c) rv[c] += w * dv[c * a.ndv + d];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rv[c] = qhat[c * a.nrecv + recv];
+      if constexpr (VISC) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) rv[4 + c] = fvhat[c * a.nrecv + recv];
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) acc[v] = T(0);
+  int nt = code & 7u;
+  for (int t = 0; t < nt; ++t) {
+    unsigned term = (code >> (3 + 4 * t)) & 15u;
+    int dir = term & 1u, side = (term & 2u) ? -1 : 1, kind = (int)(term >> 2);
+    T kx = mt[4] * mt[2 * dir], ky = mt[4] * mt[2 * dir + 1];
+    T tgt[4];
+    T sig1 = T(0), sigI = kind == kTermInterface ? k.sig_int : k.sig_phys;
+    if (kind == kTermInterface) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) tgt[v] = rv[v];
+      if (VISC) sig1 = T(0.5) * k.mu * (kx * kx + ky * ky);
+    } else if (kind == kTermFarfield) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) tgt[v] = k.qinf[v];
+    } else {
+      tgt[0] = qp[0];
+      tgt[1] = T(0);
+      tgt[2] = T(0);
+      tgt[3] = qp[0] * k.tw;
+      if (VISC) sig1 = T(0.5) * k.mu * (kx * kx + ky * ky);
+    }
+    T dq[4], kd[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dq[v] = qp[v] - tgt[v];
+    penalty_apply(qp, k.gam, kx, ky, side, dq, kd);
+    T sat[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sat[v] = -(sigI * kd[v] + sig1 * dq[v]) * T(1.0 / SBP_P0);
+    if constexpr (VISC) {
+      if (kind == kTermInterface) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T own = kx * Fv[c] + ky * Gv[c];
+          T hat = kx * rv[4 + c] + ky * rv[7 + c];
+          sat[c + 1] += T(0.5) * T(side) * (own - hat) * T(1.0 / SBP_P0);
+        }
+      }
+    }
+    T sc = kind == kTermInterface ? scale : T(1);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] += sc * sat[v];
+  }
+}
+
+// SAT entries of the CTA's rows: the tile lists are grouped by 32 x 8 tiles in column-major
+// tile order, so a 32 x TY block owns a contiguous range.
+template <int TY>
+__device__ __forceinline__ void tile_sat_range(const RhsLaunch &a, int bx, int by, int &s0, int &s1) {
+  const int nty8 = (a.m.nj + 7) / 8;
+  const int ty8 = by * (TY / 8);
+  const int id0 = bx * nty8 + ty8, id1 = bx * nty8 + min(ty8 + TY / 8, nty8);
+  s0 = a.tile_sat[id0];
+  s1 = a.tile_sat[id1];
+}
+
+template <typename T, bool VISC, int TY>
+struct FluxTile {
+  static constexpr int TX = kTileX, NT = kNT, PPT = TX * TY / NT;
+  static constexpr int H = VISC ? 3 : 0, RX = TX + 2 * H, RY = TY + 2 * H, RN = RX * RY;
+};
+
+// Contravariant fluxes at every point of a 32 x TY tile, then the SAT terms of the tile's
+// boundary and receiver points (their state, primitives and gradients are at hand here).
+template <typename T, bool VISC, bool CURV, int TY>
+__device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T *prim, uint8_t *scls) {
+  using F = FluxTile<T, VISC, TY>;
+  constexpr int TX = F::TX, NT = F::NT, H = F::H, RX = F::RX, RN = F::RN;
+  const DevMesh &m = a.m;
+  const KConst<T> &k = kc<T>(a);
+  const int tid = threadIdx.x;
+  const int i0 = bx * TX, j0 = by * TY;
+  const T *q = static_cast<const T *>(a.q);
+  T *fl = static_cast<T *>(a.flux);
+  if constexpr (VISC) {
+    for (int idx = tid; idx < RN; idx += NT) {
+      int gi = i0 - H + idx % RX, gj = j0 - H + idx / RX;
+      bool in = wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j);
+      T pr[3] = {T(0), T(0), T(1)};
+      uint8_t c = 0xFF;
+      if (in) {
+        size_t p = (size_t)gj * m.pitch + gi;
+        prim_at(q, m.field, p, k.gam, pr);
+        c = m.cls[p];
+      }
+      prim[idx] = pr[0];
+      prim[RN + idx] = pr[1];
+      prim[2 * RN + idx] = pr[2];
+      scls[idx] = c;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int kk = 0; kk < F::PPT; ++kk) {
+    const int li = tid % TX, lj = tid / TX + kk * (NT / TX);
+    const int gi = i0 + li, gj = j0 + lj;
+    if (gi >= m.ni || gj >= m.nj) continue;
+    const size_t p = (size_t)gj * m.pitch + gi;
+    T qp[4] = {q[p], q[m.field + p], q[2 * m.field + p], q[3 * m.field + p]};
+    T mt[5];
+    load_met<T, CURV>(a, gi, gj, mt);
+    T u, v, pr;
+    T Fx[4], Gx[4];
+    if constexpr (VISC) {
+      const int r = (lj + H) * RX + (li + H);
+      u = prim[r];
+      v = prim[RN + r];
+      pr = qp[0] * prim[2 * RN + r] / k.gam;  // p = rho T / gamma
+      T gr[6];
+      smem_grads<T, CURV>(a, prim, RN, r, RX, scls[r], mt, gr);
+      T Fv[3], Gv[3];
+      visc_flux_k(k, u, v, gr, Fv, Gv);
+      Fx[0] = qp[1];
+      Fx[1] = qp[1] * u + pr - Fv[0];
+      Fx[2] = qp[2] * u - Fv[1];
+      Fx[3] = (qp[3] + pr) * u - Fv[2];
+      Gx[0] = qp[2];
+      Gx[1] = qp[1] * v - Gv[0];
+      Gx[2] = qp[2] * v + pr - Gv[1];
+      Gx[3] = (qp[3] + pr) * v - Gv[2];
+    } else {
+      inviscid_flux(qp, k.gam, Fx, Gx, u, v, pr);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      fl[c * m.field + p] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : mt[0] * Fx[c];
+      fl[(4 + c) * m.field + p] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : mt[3] * Gx[c];
+    }
+  }
+  // SAT terms of this tile's boundary / receiver points (one thread per point)
+  int s0, s1;
+  tile_sat_range<TY>(a, bx, by, s0, s1);
+  T *satb = static_cast<T *>(a.sat);
+  for (int s = s0 + tid; s < s1; s += NT) {
+    uint32_t ij = a.sat_ij[s];
+    int gi = (int)(ij & 0xFFFFu), gj = (int)(ij >> 16);
+    size_t p = (size_t)gj * m.pitch + gi;
+    T qp[4] = {q[p], q[m.field + p], q[2 * m.field + p], q[3 * m.field + p]};
+    T mt[5];
+    load_met<T, CURV>(a, gi, gj, mt);
+    T Fv[3] = {0, 0, 0}, Gv[3] = {0, 0, 0};
+    if constexpr (VISC) {
+      const int r = (gj - j0 + H) * RX + (gi - i0 + H);
+      T gr[6];
+      smem_grads<T, CURV>(a, prim, RN, r, RX, scls[r], mt, gr);
+      visc_flux_k(k, prim[r], prim[RN + r], gr, Fv, Gv);
+    }
+    T acc[4];
+    sat_terms<T, VISC>(a, s, qp, mt, Fv, Gv, acc);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) satb[c * a.nsat + s] = acc[c];
+  }
+}
+
+template <typename T, int TY>
+struct UpdTile {
+  static constexpr int TX = kTileX, NT = kNT, PPT = TX * TY / NT;
+  static constexpr int RX = TX + 6, RY = TY + 6, RN = RX * RY;
+  static constexpr size_t bytes = (size_t)(8 * RN) * sizeof(T);
+};
+
+// SBP derivatives of the fluxes, the tile's SAT terms, and the epilogue.
+template <typename T, bool VISC, bool CURV, int TY>
+__device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, T *sf) {
+  using U = UpdTile<T, TY>;
+  constexpr int TX = U::TX, NT = U::NT, RX = U::RX, RN = U::RN;
+  const DevMesh &m = a.m;
+  const int tid = threadIdx.x;
+  const int i0 = bx * TX, j0 = by * TY;
+  const T *q = static_cast<const T *>(a.q);
+  const T *fl = static_cast<const T *>(a.flux);
+  const T *satb = static_cast<const T *>(a.sat);
+
+  for (int idx = tid; idx < RN; idx += NT) {
+    int gi = i0 - 3 + idx % RX, gj = j0 - 3 + idx / RX;
+    bool in = wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j);
+    size_t p = in ? (size_t)gj * m.pitch + gi : 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sf[c * RN + idx] = in ? fl[c * m.field + p] : T(0);
+  }
+  __syncthreads();
+  int s0, s1;
+  tile_sat_range<TY>(a, bx, by, s0, s1);
+#pragma unroll
+  for (int kk = 0; kk < U::PPT; ++kk) {
+    const int li = tid % TX, lj = tid / TX + kk * (NT / TX);
+    const int gi = i0 + li, gj = j0 + lj;
+    if (gi >= m.ni || gj >= m.nj) continue;
+    const size_t p = (size_t)gj * m.pitch + gi;
+    unsigned code = m.cls[p];
+    const int r = (lj + 3) * RX + (li + 3);
+    T rhs[4] = {T(0), T(0), T(0), T(0)};
+    if ((code & 15u) != 15u) {
+      T jac;
+      if (CURV) jac = static_cast<const T *>(m.met)[4 * m.field + p];
+      else jac = kc<T>(a).mc[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        rhs[c] = -jac * (dline(sf + c * RN, r, 1, code & 15u) + dline(sf + (4 + c) * RN, r, RX, code >> 4));
+      if (s0 < s1) {
+        // the tile's SAT entries are sorted by (j, i): binary search for this point
+        uint32_t key = (uint32_t)gi | ((uint32_t)gj << 16);
+        int lo = s0, hi = s1;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          uint32_t km = a.sat_ij[mid];
+          if ((km >> 16) < (key >> 16) || ((km >> 16) == (key >> 16) && (km & 0xFFFFu) < (key & 0xFFFFu))) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < s1 && a.sat_ij[lo] == key) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) rhs[c] += satb[c * a.nsat + lo];
+        }
+      }
+    }
+    T *out = static_cast<T *>(a.out);
+    if (a.mode == 0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) out[c * m.field + p] = rhs[c];
+    } else {
+      T *qn = static_cast<T *>(a.qnext);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        out[c * m.field + p] = rhs[c];
+        double acc = (double)q[c * m.field + p];
+        for (int h = 0; h < a.nold; ++h)
+          acc += a.alpha[h] * (double)static_cast<const T *>(a.hold[h])[c * m.field + p];
+        acc += a.alpha[a.nold] * (double)rhs[c];
+        qn[c * m.field + p] = (T)acc;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Donor-point values for the fused gather of k_rhs. One thread per (extrapolation set, distinct
+// donor point): the state q + sum_k beta_k hist_k (FP64 accumulation; Sec. 3.3 Step 2 for the
+// slow extrapolant at a micro time) and, for Navier-Stokes, the Cartesian viscous fluxes of that
+// state by the donor mesh's own SBP derivatives.
+template <typename T>
+__device__ __forceinline__ void set_state(const DonorLaunch &a, int set, size_t p, T out[4]) {
+  const T *q = static_cast<const T *>(a.q);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    double acc = (double)q[v * a.d.field + p];
+    for (int k = 0; k < a.nb[set]; ++k)
+      acc += a.beta[set][k] * (double)static_cast<const T *>(a.hist[k])[v * a.d.field + p];
+    out[v] = (T)acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void set_prim(const DonorLaunch &a, int set, int i, int j, T gam, T pr[3]) {
+  T s[4];
+  set_state(a, set, (size_t)j * a.d.pitch + i, s);
+  T ri = T(1) / s[0];
+  T u = s[1] * ri, v = s[2] * ri;
+  T p = (gam - T(1)) * (s[3] - T(0.5) * (s[1] * u + s[2] * v));
+  pr[0] = u;
+  pr[1] = v;
+  pr[2] = gam * p * ri;
+}
+
+// Navier-Stokes donor values of one (set, donor point) pair by a 16-lane group; every lane of
+// the warp must call this (shuffles), with valid = false for lanes past the end.
+template <typename T, bool CURV>
+__device__ __forceinline__ void donor_group(const DonorLaunch &a, int pair, bool valid);
+
+template <typename T, bool CURV>
+__device__ __forceinline__ void donor_group(const DonorLaunch &a, int pair, bool valid) {
+  {
+    const int l = threadIdx.x & 15;
+    const int set = valid ? pair / a.npts : 0, d = valid ? pair - set * a.npts : 0;
+    const uint32_t ij = valid ? a.pts[d] : 0u;
+    const int ii = (int)(ij & 0xFFFFu), jj = (int)(ij >> 16);
+    const size_t p = (size_t)jj * a.d.pitch + ii;
+    const unsigned code = valid ? a.d.cls[p] : 0xFFu;
+    const T gam = (T)a.g.gamma;
+    int pi = ii, pj = jj, dir = 2;
+    T w = T(0);
+    if (l >= 1 && l <= 8) {
+      dir = l <= 4 ? 0 : 1;
+      int row, sgn;
+      row_of(dir == 0 ? (code & 15u) : (code >> 4), row, sgn);
+      const int e = (l - 1) & 3;
+      w = T(sgn) * wgt<T>(row, e);
+      const int off = sgn * c_off[row][e];
+      if (dir == 0) pi += off;
+      else pj += off;
+      wrap_index(pi, a.d.ni, a.d.per_i);
+      wrap_index(pj, a.d.nj, a.d.per_j);
+    }
+    const bool act = valid && (l == 0 || w != T(0));
+    T s[4] = {T(1), T(0), T(0), T(2.5)};
+    if (act) set_state(a, set, (size_t)pj * a.d.pitch + pi, s);
+    const T ri = T(1) / s[0];
+    const T pr[3] = {s[1] * ri, s[2] * ri, gam * (gam - T(1)) * (s[3] - T(0.5) * (s[1] * s[1] + s[2] * s[2]) * ri) * ri};
+    T cx[3], cy[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      cx[f] = (act && dir == 0) ? w * pr[f] : T(0);
+      cy[f] = (act && dir == 1) ? w * pr[f] : T(0);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        cx[f] += __shfl_xor_sync(0xffffffffu, cx[f], o);
+        cy[f] += __shfl_xor_sync(0xffffffffu, cy[f], o);
+      }
+    }
+    if (valid && l == 0) {
+      T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * a.npts;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dv[v * a.npts + d] = s[v];
+      const T mu = (T)a.g.mu, kap = (T)(a.g.mu / (a.g.pr * (a.g.gamma - 1.0)));
+      T mt[5];
+      if (CURV) {
+        const T *met = static_cast<const T *>(a.d.met);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) mt[c] = met[c * a.d.field + p];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) mt[c] = (T)a.d.mc[c];
+      }
+      T gr[6];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        gr[2 * f] = mt[4] * (mt[0] * cx[f] + mt[2] * cy[f]);
+        gr[2 * f + 1] = mt[4] * (mt[1] * cx[f] + mt[3] * cy[f]);
+      }
+      T Fv[3], Gv[3];
+      viscous_flux(pr[0], pr[1], gr, mu, kap, Fv, Gv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dv[(4 + c) * a.npts + d] = Fv[c];
+        dv[(7 + c) * a.npts + d] = Gv[c];
+      }
+    }
+  }
+}
+
+}  // namespace sbp

@@ -111,6 +111,24 @@ struct DonorLaunch {
 constexpr int kTileX = 32;
 constexpr int kNT = 256;
 
+// One micro step of a batch of systems (a cooperative launch): donor values of the listed
+// receiving meshes, then fluxes and updates of the listed tiles. items: (descriptor, tile x,
+// tile y, 1 if the mesh is curvilinear).
+struct BatchSubstep {
+  const void *dl;     // DonorLaunch[n_dl] in device memory
+  const int *dl_off;  // n_dl + 1 prefix sums of the (set, point) pairs per descriptor
+  int n_dl;
+  const void *rl;     // RhsLaunch[] in device memory
+  const int4 *items;
+  int n_items;
+  unsigned *bar_count;
+  unsigned *bar_gen;
+  int *err;
+};
+cudaError_t launch_batch_substep(const BatchSubstep &b, int grid, int dtype, bool viscous, bool curv_fine, int ty,
+                                 cudaStream_t s);
+cudaError_t batch_grid_size(int dtype, bool viscous, bool curv_fine, int ty, int *grid);
+
 cudaError_t launch_rhs(const RhsLaunch &a, int dtype, bool viscous, cudaStream_t s);
 cudaError_t launch_interp(const InterpLaunch &a, int dtype, bool viscous, cudaStream_t s);
 cudaError_t launch_donor_vals(const DonorLaunch &a, int dtype, bool viscous, cudaStream_t s);

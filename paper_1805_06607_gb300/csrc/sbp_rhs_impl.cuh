@@ -1,0 +1,66 @@
+// Right-hand-side kernels of one mesh, k_flux then k_update (tile bodies in sbp_dev.cuh); included
+// once per element type by sbp_rhs_f32.cu and sbp_rhs_f64.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+#include <cstring>
+
+#include "sbp_dev.cuh"
+
+namespace sbp {
+
+// At least 4 (FP32) / 3 (FP64) resident CTAs per SM: caps the registers that the SAT tail
+// (taken by boundary tiles only) would otherwise claim for the whole kernel.
+template <typename T, bool VISC, bool CURV, int TY>
+__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 4 : 3) k_flux(const RhsLaunch a) {
+  using F = FluxTile<T, VISC, TY>;
+  __shared__ T prim[VISC ? 3 * F::RN : 1];
+  __shared__ uint8_t scls[VISC ? F::RN : 1];
+  flux_tile<T, VISC, CURV, TY>(a, blockIdx.x, blockIdx.y, prim, scls);
+}
+
+template <typename T, bool VISC, bool CURV, int TY>
+__global__ void __launch_bounds__(kNT) k_update(const RhsLaunch a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  update_tile<T, VISC, CURV, TY>(a, blockIdx.x, blockIdx.y, reinterpret_cast<T *>(smem_raw));
+}
+
+template <typename T, bool VISC, bool CURV, int TY>
+static cudaError_t launch_rhs_t(const RhsLaunch &a, cudaStream_t s) {
+  using U = UpdTile<T, TY>;
+  auto ku = k_update<T, VISC, CURV, TY>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U::bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
+  k_flux<T, VISC, CURV, TY><<<grid, kNT, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ku<<<grid, kNT, U::bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, bool VISC, bool CURV>
+static cudaError_t launch_rhs_ty(const RhsLaunch &a, cudaStream_t s) {
+  switch (a.rows_per_cta) {
+    case 8: return launch_rhs_t<T, VISC, CURV, 8>(a, s);
+    case 16: return launch_rhs_t<T, VISC, CURV, 16>(a, s);
+    case 32: return launch_rhs_t<T, VISC, CURV, 32>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Launch for one element type T, dispatched on physics and metric kind.
+template <typename T>
+cudaError_t launch_rhs_typed(const RhsLaunch &a, bool viscous, cudaStream_t s) {
+  bool curv = !a.m.cart;
+  if (viscous) return curv ? launch_rhs_ty<T, true, true>(a, s) : launch_rhs_ty<T, true, false>(a, s);
+  return curv ? launch_rhs_ty<T, false, true>(a, s) : launch_rhs_ty<T, false, false>(a, s);
+}
+
+}  // namespace sbp

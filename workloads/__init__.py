@@ -178,3 +178,23 @@ def mms_box_in_box(n, kind="inviscid", gamma=GAMMA, mu=1.0):
                   fast_mesh=1, cfl=0.5, qinf=np.array([1.0, 0.0, 0.0, 1.0 / (gamma * (gamma - 1.0))]),
                   twall=1.0, omega_corner=1.0)
     return {"meshes": [bg, fine], "q0": qs, "params": params}
+
+
+def batched_vortices(seed=0, n_systems=64, n_range=(128, 512), ratios=(2, 4, 8), bg_half=5.0, omega=5.0,
+                     mach=0.5, order=3, cfl=0.5):
+    """Many independent 2D Euler vortex systems: background N x N periodic on [-bg_half, bg_half]^2
+    with N ~ U{n_range}, one fine patch of 1/8 of the background side whose spacing is the
+    background spacing / r, r drawn from `ratios` and used as the MRAB step ratio; vortex centres
+    seeded near the patch."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(n_systems):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        r = int(rng.choice(ratios))
+        fine_half = bg_half / 8.0
+        n_fine = int(round(n * r / 8.0)) + 1
+        wl = vortex_box_in_box(seed=int(rng.integers(1 << 30)), n_bg=n, n_fine=n_fine, bg_half=bg_half,
+                               fine_half=fine_half, omega=omega, phi=1.0, mach=mach, order=order,
+                               step_ratio=r, cfl=cfl, jitter=0.5 * fine_half)
+        out.append(wl)
+    return out
