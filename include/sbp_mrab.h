@@ -219,6 +219,74 @@ sbp_status sbp_batch_info(sbp_batch_t batch, int *members, int *rows_per_cta, in
 /* Synchronise the stream and report (then clear) the batch's device error word. */
 sbp_status sbp_batch_check(sbp_batch_t batch, void *stream);
 
+/* ---- Discrete adjoint (SBP_F64 systems only) --------------------------------------------------
+ * Exact derivatives of the discrete operators above (not of the continuous equations): the
+ * right-hand side of Sec. 2.2 eq. (int) with its SBP closures, SAT penalties and interface
+ * values, the donor-cell interpolation of Sec. 2.2, the Runge-Kutta bootstrap of Sec. 3.1 and
+ * the MRAB macro step of Sec. 3.3 (fastest-first, no re-extrapolation). The paper does not
+ * derive an adjoint; these calls differentiate the method as implemented. Local Jacobians are
+ * exact (forward-mode dual numbers on the same point-wise formulas); the derivative stencils
+ * enter through their transposes, including the closure rows; every sum is a fixed-order
+ * gather, so repeated calls give identical bits. Characteristic splittings (the sign of a
+ * wave speed in K+/-) are differentiated on the branch the state selects. Buffers are device
+ * memory in the state layout unless stated; the library allocates its FP64 workspace (about 17
+ * planes per mesh plus 30 doubles per receiver) on the first call and keeps it until
+ * sbp_system_destroy. All of these return SBP_ERR_DTYPE on SBP_F32 systems. */
+
+/* Replace the far-field state qinf[4] (host) of the system (Sec. 4.1 far-field SAT target). */
+sbp_status sbp_set_freestream(sbp_system_t sys, const double *qinf);
+
+/* Vector-Jacobian product of sbp_rhs_eval(mesh, q_self, q_other): with R = dq/dt of `mesh`,
+ * writes lq_self = (dR/dq_self)^T lam and lq_other = (dR/dq_other)^T lam (through the receivers'
+ * interpolated states and viscous fluxes), and, when lqinf != NULL, lqinf[4] (host) =
+ * (dR/dqinf)^T lam (synchronises the stream). lam has the layout of q_self; its values at holes
+ * are ignored. Outputs are overwritten, pad columns included. */
+sbp_status sbp_rhs_eval_vjp(sbp_system_t sys, int mesh, const void *q_self, const void *q_other, const void *lam,
+                            void *lq_self, void *lq_other, double *lqinf, void *stream);
+
+/* Jacobian-vector product of sbp_rhs_eval: drhs = (dR/dq_self) dq_self + (dR/dq_other) dq_other +
+ * (dR/dqinf) dqinf (dqinf: host, 4 values, or NULL for zero). drhs is 0 at holes. */
+sbp_status sbp_rhs_eval_jvp(sbp_system_t sys, int mesh, const void *q_self, const void *q_other,
+                            const void *dq_self, const void *dq_other, const double *dqinf, void *drhs,
+                            void *stream);
+
+/* Vector-Jacobian product of sbp_overset_interp(recv_mesh, q_donor): lq_donor (state layout of the
+ * donor mesh, overwritten) = adjoint of q_donor for receiver-value adjoints lqhat (4 x
+ * n_receivers) and lfvhat (6 x n_receivers, NULL for zero; ignored for Euler). */
+sbp_status sbp_overset_interp_vjp(sbp_system_t sys, int recv_mesh, const void *q_donor, const void *lqhat,
+                                  const void *lfvhat, void *lq_donor, void *stream);
+
+/* Probe-pressure objective of a whole run and its gradient. From the initial states q0 (device,
+ * state layout) the run is the bootstrap of sbp_mrab_init followed by n_steps macro steps of
+ * sbp_mrab_step, all with macro step H (the eager kernel sequence; identical results to the
+ * graphs). The objective is
+ *   J = H * sum over macro steps n = 1..n_steps of sum over probes p of p_p(t_n)^2,
+ * with p_p the pressure interpolated at probe p from the background (mesh 0) state after step n
+ * through the 4x4 Lagrange stencil of the interface interpolation (Sec. 2.2) on the
+ * background's nodes. probe_xy: host, 2 per probe; every stencil point must be active.
+ * Outputs (any may be NULL): J (host), probe_p (host, n_steps x n_probes pressures), the
+ * gradients dJ/dq0 of both meshes (device, state layout; both or neither) and dJ/dqinf[4]
+ * (host; the far-field state enters through the far-field SAT only; the viscous coefficient,
+ * H and the initial states are held fixed), forward_steps (host: macro steps run, recomputation
+ * included). Without gradient outputs only the forward runs.
+ * The reverse sweep recomputes forward steps from checkpoints: n_snapshots device snapshots
+ * (each a state and a history ring per mesh) besides the initial one, placed by binomial
+ * checkpointing (Griewank): every macro step is recomputed at most r times, r the least integer
+ * with C(n_snapshots + r, r) >= n_steps. n_snapshots >= n_steps - 1 stores every step (one
+ * recomputation each). Workspace (snapshots, bootstrap stage states, adjoint rings) is allocated
+ * for the call and freed before it returns; the system's bound buffers and ring positions are
+ * left unchanged. Synchronises the stream. */
+typedef struct {
+  int n_steps;
+  int n_snapshots;
+  int n_probes;
+  const double *probe_xy;
+  double H;
+} sbp_adjoint_desc;
+sbp_status sbp_adjoint_probe(sbp_system_t sys, const sbp_adjoint_desc *desc, const void *q0_mesh0,
+                             const void *q0_mesh1, double *J, double *probe_p, void *dJ_dq0_mesh0,
+                             void *dJ_dq0_mesh1, double *dJ_dqinf, long *forward_steps, void *stream);
+
 /* Synchronise the stream and report (then clear) the device error word. */
 sbp_status sbp_check(sbp_system_t sys, void *stream);
 

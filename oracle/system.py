@@ -378,3 +378,61 @@ class OracleSystem:
     def cell_sizes(self):
         """Cell size per point for eq. (l2error): J^-1 (= dx dy on Cartesian meshes), holes 0."""
         return [np.where(self.iblank[k] != 0, 1.0 / self.met[k][4], 0.0) for k in range(2)]
+
+
+# ---------------------------------------------------------------------------------------------
+# Probe-pressure objective (the objective of the discrete adjoint; the paper has none)
+# ---------------------------------------------------------------------------------------------
+def probe_stencil(mesh, xy):
+    """4 x 4 Lagrange stencil of point xy on a Cartesian mesh, the stencil kind of Sec. 2.2's
+    interpolation: nodes i0..i0+3 along each direction with i0 = floor(xi) - 1 (the point in
+    the middle cell), shifted inward at non-periodic edges; weights are the Lagrange basis
+    polynomials of those nodes at the point. Returns ((i0, j0), (w_i[4], w_j[4]))."""
+    base, ws = [], []
+    for d in range(2):
+        xi = (xy[d] - mesh["lo"][d]) / mesh["h"][d]
+        n = mesh["n"][d]
+        i0 = int(np.floor(xi)) - 1
+        if not mesh["periodic"][d]:
+            if xi < 0.0 or xi > n - 1:
+                raise ValueError("probe outside the mesh")
+            i0 = max(0, min(n - 4, i0))
+        t = xi - i0
+        w = []
+        for a in range(4):
+            others = [b for b in range(4) if b != a]
+            w.append(np.prod([(t - b) / (a - b) for b in others]))
+        base.append(i0)
+        ws.append(np.array(w))
+    return tuple(base), tuple(ws)
+
+
+def probe_pressure(mesh, q, stencil, gamma):
+    """Pressure interpolated at a probe: sum over the 4 x 4 nodes of w_a w_b p(q)."""
+    (i0, j0), (wi, wj) = stencil
+    ni, nj = mesh["n"]
+    acc = 0.0
+    for b in range(4):
+        for a in range(4):
+            i, j = (i0 + a) % ni, (j0 + b) % nj
+            rho, mx, my, E = q[:, j, i]
+            p = (gamma - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho)
+            acc += wi[a] * wj[b] * p
+    return acc
+
+
+def probe_objective(osys, q0, probe_xy, n_steps, H):
+    """J = H sum_{n=1..n_steps} sum_p p_p(t_n)^2 over the bootstrap + n_steps MRAB macro steps
+    (Sec. 3.1, Sec. 3.3) from the initial states q0, probes on the background (mesh 0).
+    Returns (J, pressures[n_steps, n_probes])."""
+    bg = osys.meshes[0]
+    st = [probe_stencil(bg, xy) for xy in np.asarray(probe_xy, dtype=np.float64).reshape(-1, 2)]
+    qs, hf, hs = osys.bootstrap([np.array(q, dtype=np.float64) for q in q0], H)
+    pr = np.zeros((n_steps, len(st)))
+    J = 0.0
+    for n in range(n_steps):
+        qs, hf, hs = osys.mrab(qs, hf, hs, H, 1)
+        for p, s in enumerate(st):
+            pr[n, p] = probe_pressure(bg, qs[0], s, osys.gamma)
+        J += H * float(np.sum(pr[n] ** 2))
+    return J, pr

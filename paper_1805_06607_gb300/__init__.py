@@ -50,6 +50,11 @@ class MeshInfo(ctypes.Structure):
                 ("strip_width", ctypes.c_int), ("rows_per_cta", ctypes.c_int)]
 
 
+class AdjointDesc(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int), ("n_snapshots", ctypes.c_int), ("n_probes", ctypes.c_int),
+                ("probe_xy", ctypes.c_void_p), ("H", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -79,6 +84,13 @@ _SIGS.update({
     "sbp_batch_step": [_P, _I, _P],
     "sbp_batch_info": [_P, _P, _P, _P, _P],
     "sbp_batch_check": [_P, _P],
+})
+_SIGS.update({
+    "sbp_set_freestream": [_P, _P],
+    "sbp_rhs_eval_vjp": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
+    "sbp_rhs_eval_jvp": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
+    "sbp_overset_interp_vjp": [_P, _I, _P, _P, _P, _P, _P],
+    "sbp_adjoint_probe": [_P, ctypes.POINTER(AdjointDesc), _P, _P, _P, _P, _P, _P, _P, _P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -297,6 +309,70 @@ class System:
 
     def check(self, stream=None):
         _check(_lib.sbp_check(self.h, _stream(stream)), "sbp_check")
+
+    # -- discrete adjoint (FP64 systems) -------------------------------------------------------
+    def set_freestream(self, qinf):
+        arr = (ctypes.c_double * 4)(*[float(v) for v in qinf])
+        _check(_lib.sbp_set_freestream(self.h, ctypes.cast(arr, ctypes.c_void_p)), "sbp_set_freestream")
+
+    def rhs_eval_vjp(self, k, q_self, q_other, lam, stream=None):
+        """((dR_k/dq_self)^T lam, (dR_k/dq_other)^T lam, (dR_k/dqinf)^T lam as numpy[4])."""
+        lq_s = self.empty_state(k)
+        lq_o = self.empty_state(1 - k)
+        lqinf = (ctypes.c_double * 4)()
+        _check(_lib.sbp_rhs_eval_vjp(self.h, k, _ptr(q_self), _ptr(q_other), _ptr(lam), _ptr(lq_s), _ptr(lq_o),
+                                     ctypes.cast(lqinf, ctypes.c_void_p), _stream(stream)), "sbp_rhs_eval_vjp")
+        return lq_s, lq_o, np.array(lqinf[:])
+
+    def rhs_eval_jvp(self, k, q_self, q_other, dq_self, dq_other, dqinf=None, stream=None):
+        out = self.empty_state(k)
+        arr = (ctypes.c_double * 4)(*[float(v) for v in dqinf]) if dqinf is not None else None
+        _check(_lib.sbp_rhs_eval_jvp(self.h, k, _ptr(q_self), _ptr(q_other), _ptr(dq_self), _ptr(dq_other),
+                                     ctypes.cast(arr, ctypes.c_void_p) if arr is not None else None, _ptr(out),
+                                     _stream(stream)), "sbp_rhs_eval_jvp")
+        return out
+
+    def overset_interp_vjp(self, recv, q_donor, lqhat, lfvhat=None, stream=None):
+        nr = self.info[recv].n_receivers
+        lq = self.empty_state(1 - recv)
+        lqh = self.torch.zeros((4, max(nr, 1)), dtype=self.torch.float64, device="cuda")
+        lqh[:, :nr] = lqhat
+        lfv = None
+        if lfvhat is not None:
+            lfv = self.torch.zeros((6, max(nr, 1)), dtype=self.torch.float64, device="cuda")
+            lfv[:, :nr] = lfvhat
+        if nr:
+            lqh = lqh[:, :nr].contiguous()
+            lfv = lfv[:, :nr].contiguous() if lfv is not None else None
+        _check(_lib.sbp_overset_interp_vjp(self.h, recv, _ptr(q_donor), _ptr(lqh), _ptr(lfv), _ptr(lq),
+                                           _stream(stream)), "sbp_overset_interp_vjp")
+        return lq
+
+    def adjoint_probe(self, q0, probe_xy, n_steps, H, n_snapshots=None, grad=True, stream=None):
+        """Probe objective J of a run from device states q0 = (mesh 0, mesh 1) and, with grad,
+        its gradients w.r.t. q0 (device tensors) and the far-field state (numpy[4])."""
+        xy = np.ascontiguousarray(probe_xy, dtype=np.float64).reshape(-1, 2)
+        d = AdjointDesc()
+        d.n_steps = int(n_steps)
+        d.n_snapshots = int(n_steps if n_snapshots is None else n_snapshots)
+        d.n_probes = xy.shape[0]
+        d.probe_xy = xy.ctypes.data
+        d.H = float(H)
+        J = ctypes.c_double()
+        pp = np.zeros(max(int(n_steps) * xy.shape[0], 1))
+        fwd = ctypes.c_long()
+        g = [self.empty_state(0), self.empty_state(1)] if grad else [None, None]
+        gq = (ctypes.c_double * 4)()
+        _check(_lib.sbp_adjoint_probe(self.h, ctypes.byref(d), _ptr(q0[0]), _ptr(q0[1]),
+                                      ctypes.cast(ctypes.pointer(J), ctypes.c_void_p), pp.ctypes.data,
+                                      _ptr(g[0]), _ptr(g[1]), ctypes.cast(gq, ctypes.c_void_p) if grad else None,
+                                      ctypes.cast(ctypes.pointer(fwd), ctypes.c_void_p), _stream(stream)),
+               "sbp_adjoint_probe")
+        out = {"J": J.value, "p": pp[:int(n_steps) * xy.shape[0]].reshape(int(n_steps), xy.shape[0]),
+               "forward_steps": fwd.value}
+        if grad:
+            out.update({"dq0": g, "dqinf": np.array(gq[:])})
+        return out
 
 
 class Batch:

@@ -129,6 +129,91 @@ cudaError_t launch_batch_substep(const BatchSubstep &b, int grid, int dtype, boo
                                  cudaStream_t s);
 cudaError_t batch_grid_size(int dtype, bool viscous, bool curv_fine, int ty, int *grid);
 
+// Discrete adjoint of one mesh's right-hand side (FP64): given lam = adjoint of dq/dt at the
+// state q, accumulate lq += (dR/dq)^T lam, write the adjoint of the receiver values
+// (lrv, 10 per receiver: state then viscous fluxes) and of the far-field state (lqinf, 4 per
+// SAT point). Scratch: mu (8 planes), ld (6 planes), lp (3 planes).
+struct AdjLaunch {
+  DevMesh m;
+  KConst<double> k;
+  bool viscous;
+  const double *q, *lam;
+  double *lq, *mu, *ld, *lp;
+  int nsat;
+  const uint32_t *sat_ij, *sat_code;
+  const int *sat_recv;
+  const double *sat_scale;
+  const double *rv;  // receiver values used by the forward evaluation (10 x nrecv)
+  int nrecv;
+  double *lrv;
+  double *lqinf;
+};
+// Adjoint of the receiver values back to the donor mesh: per distinct donor point d,
+// ldv(d) = sum over (receiver, stencil slot) using d of w lrv (inverse lists inv_off/inv_re,
+// entries r * 16 + slot), then through the donor values (state shat and its viscous fluxes)
+// into lshat (4 planes on the donor mesh, accumulated). Scratch on the donor mesh: ld (6
+// planes, cleared here), lp (3 planes).
+struct AdjDonorLaunch {
+  DevMesh d;
+  KConst<double> k;
+  bool viscous;
+  const double *shat;  // donor state the receiver values were taken from
+  int npts;
+  const uint32_t *pts;
+  const int *inv_off, *inv_re;
+  const double *w;     // 8 per receiver
+  const double *lrv;   // 10 x nrecv
+  int nrecv;
+  double *ldv;         // scratch 10 x npts
+  double *lshat, *ld, *lp;
+};
+cudaError_t launch_rhs_adjoint(const AdjLaunch &a, cudaStream_t s);
+cudaError_t launch_donor_adjoint(const AdjDonorLaunch &a, cudaStream_t s);
+// Probe pressures p_p = sum_d w_d p(q_d) (8 weights per probe, base (i0, j0)) and the adjoint
+// seed lq(d) += scale * 2 p_p w_d dp/dq(q_d); probes are applied one after another.
+cudaError_t launch_probe(const DevMesh &m, const double *q, int nprobe, const int *base, const double *w,
+                         double *pout, double *lq, double scale, double gamma, cudaStream_t s);
+
+// Tangent (Jacobian-vector product) of one mesh's right-hand side (FP64): out = (dR/dq) qd +
+// (dR/drv) rvd + (dR/dqinf) qinfd, with rvd the tangent of the receiver values from the donor
+// state's tangent (TlDonorLaunch, run first). Scratch: pd (3 planes), fd (8 planes) on the mesh;
+// the donor side's pd on the donor mesh.
+struct TlLaunch {
+  DevMesh m;
+  KConst<double> k;
+  bool viscous;
+  const double *q, *qd;
+  double *pd, *fd, *out;
+  int nsat;
+  const uint32_t *sat_ij, *sat_code;
+  const int *sat_recv;
+  const double *sat_scale;
+  const double *rv, *rvd;
+  int nrecv;
+  double qinfd[4];
+};
+struct TlDonorLaunch {
+  DevMesh d;
+  KConst<double> k;
+  bool viscous;
+  const double *q, *qd;  // donor state and its tangent
+  double *pd;            // scratch: 3 planes on the donor mesh
+  int nrecv;
+  const int *base;
+  const double *w;
+  double *rvd;           // 10 x nrecv
+};
+cudaError_t launch_rhs_tangent(const TlLaunch &a, const TlDonorLaunch &dn, cudaStream_t s);
+
+// FP64 linear combinations and reductions used by the adjoint driver.
+constexpr int kMaxLin = 8;
+struct LinComb {
+  double c[kMaxLin];
+  const double *x[kMaxLin];
+};
+cudaError_t launch_lincomb(double *out, const double *base, const LinComb &lc, int nx, size_t n, cudaStream_t s);
+cudaError_t launch_sum4(const double *x, int n, double *acc, cudaStream_t s);
+
 cudaError_t launch_rhs(const RhsLaunch &a, int dtype, bool viscous, cudaStream_t s);
 cudaError_t launch_interp(const InterpLaunch &a, int dtype, bool viscous, cudaStream_t s);
 cudaError_t launch_donor_vals(const DonorLaunch &a, int dtype, bool viscous, cudaStream_t s);

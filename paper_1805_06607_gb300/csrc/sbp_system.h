@@ -1,0 +1,550 @@
+// The system object behind sbp_system_t: host setup products, device tables, integrator
+// bookkeeping, CUDA graphs and phase timers. Shared by the C ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sbp_device.h"
+#include "sbp_internal.h"
+
+using namespace sbp;
+
+namespace sbp {
+inline thread_local std::string g_msg;
+
+inline sbp_status fail(sbp_status s, const std::string &msg) {
+  g_msg = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) return fail(SBP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct MeshDev {
+  uint8_t *cls = nullptr;
+  void *met = nullptr;
+  int *tile_sat = nullptr;
+  void *flux = nullptr;
+  uint32_t *sat_ij = nullptr, *sat_code = nullptr;
+  int *sat_recv = nullptr;
+  double *sat_scale = nullptr;
+  int *base = nullptr;
+  double *w = nullptr;
+  void *wt = nullptr;   // donor weights in the compute type
+  void *sat = nullptr;  // per SAT point: 4 penalty terms
+  void *qhat = nullptr, *fvhat = nullptr;
+  // distinct donor points of this mesh's receivers, per-receiver indices into them, and the
+  // per-step donor values (10 planes per extrapolation set)
+  uint32_t *dpts = nullptr;
+  int *didx = nullptr;
+  void *dv = nullptr;
+  int ndv = 0, dv_sets = 0;
+  // inverse donor lists for the adjoint (built on first use): per distinct donor point, the
+  // (receiver * 16 + stencil slot) entries that read it
+  int *inv_off = nullptr, *inv_re = nullptr;
+  int rows_per_cta = 16;
+  // bound integrator buffers
+  void *q[2] = {nullptr, nullptr};
+  void *hist = nullptr;
+  int cur = 0, head = -1, count = 0;
+};
+
+template <typename P>
+inline cudaError_t upload(P *&dst, const void *src, size_t bytes) {
+  cudaError_t e = cudaMalloc((void **)&dst, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  if (bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  return e;
+}
+}  // namespace sbp
+
+struct sbp_system_s {
+  sbp_params p{};
+  MeshHost mh[2];
+  MeshDev md[2];
+  CoeffPlan plan;
+  size_t esz = 8;
+  int *d_err = nullptr;
+  unsigned long long *d_dt = nullptr;
+  double H = 0.0, t = 0.0;
+  bool initialised = false;
+  // phase timers
+  bool prof = false;
+  struct Pending {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[SBP_PHASE_COUNT] = {0, 0, 0, 0};
+  int prof_n[SBP_PHASE_COUNT] = {0, 0, 0, 0};
+  // CUDA graphs of one macro step, one per ring/buffer phase (the kernel arguments differ by
+  // phase), captured on internal streams with the slow RHS and the first fast micro step on
+  // parallel branches.
+  bool use_graph = true;
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::map<uint64_t, cudaGraphExec_t> graphs;
+  // FP64 workspace of the adjoint and tangent calls, per mesh (allocated on first use):
+  // mu 8 planes, ld 6 planes, lp 3 planes, receiver values rv and their adjoint lrv (10 per
+  // receiver), far-field adjoint per SAT point (4), donor-point adjoint ldv (10 per point)
+  struct AdjWs {
+    double *mu = nullptr, *ld = nullptr, *lp = nullptr, *rv = nullptr, *lrv = nullptr, *lqinf = nullptr,
+           *ldv = nullptr;
+  } aws[2];
+  double *d_qinf_acc = nullptr;  // 4 doubles: accumulated far-field adjoint
+  bool aws_ready = false;
+  std::vector<void *> adj_allocs;
+
+  void clear_graphs() {
+    for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+
+  cudaEvent_t take_event() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // Launch `fn` on stream s, bracketed by an event pair when the timers are on.
+  template <typename Fn>
+  cudaError_t timed(int phase, cudaStream_t s, Fn &&fn) {
+    if (!prof) return fn();
+    Pending p{phase, take_event(), take_event()};
+    cudaEventRecord(p.a, s);
+    cudaError_t e = fn();
+    cudaEventRecord(p.b, s);
+    pending.push_back(p);
+    return e;
+  }
+  cudaError_t drain() {
+    for (auto &p : pending) {
+      cudaError_t e = cudaEventSynchronize(p.b);
+      if (e != cudaSuccess) return e;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p.a, p.b);
+      prof_ms[p.phase] += ms;
+      prof_n[p.phase] += 1;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+    return cudaSuccess;
+  }
+
+  ~sbp_system_s() {
+    for (auto &d : md) {
+      cudaFree(d.cls);
+      cudaFree(d.met);
+      cudaFree(d.tile_sat);
+      cudaFree(d.flux);
+      cudaFree(d.sat_ij);
+      cudaFree(d.sat_code);
+      cudaFree(d.sat_recv);
+      cudaFree(d.sat_scale);
+      cudaFree(d.base);
+      cudaFree(d.w);
+      cudaFree(d.wt);
+      cudaFree(d.sat);
+      cudaFree(d.qhat);
+      cudaFree(d.fvhat);
+      cudaFree(d.dpts);
+      cudaFree(d.didx);
+      cudaFree(d.dv);
+      cudaFree(d.inv_off);
+      cudaFree(d.inv_re);
+    }
+    cudaFree(d_err);
+    cudaFree(d_dt);
+    for (void *ptr : adj_allocs) cudaFree(ptr);
+    drain();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    clear_graphs();
+    if (cap) cudaStreamDestroy(cap);
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+  }
+
+  bool viscous() const { return p.physics == SBP_NS; }
+  int fast() const { return p.fast_mesh; }
+  int slow() const { return 1 - p.fast_mesh; }
+  size_t state_elems(int k) const { return (size_t)kNvar * mh[k].pitch * mh[k].nj; }
+
+  DevMesh dev_mesh(int k) const {
+    DevMesh d{};
+    const MeshHost &m = mh[k];
+    d.ni = m.ni;
+    d.nj = m.nj;
+    d.pitch = m.pitch;
+    d.per_i = m.per[0];
+    d.per_j = m.per[1];
+    d.cart = m.cartesian;
+    d.field = (size_t)m.pitch * m.nj;
+    d.cls = md[k].cls;
+    d.met = md[k].met;
+    if (m.cartesian) {
+      d.mc[0] = m.h[1];
+      d.mc[1] = 0.0;
+      d.mc[2] = 0.0;
+      d.mc[3] = m.h[0];
+      d.mc[4] = 1.0 / (m.h[0] * m.h[1]);
+    }
+    return d;
+  }
+
+  Gas gas() const {
+    Gas g{};
+    g.gamma = p.gamma;
+    g.mu = viscous() ? p.mu : 0.0;
+    g.pr = p.pr;
+    g.twall = p.twall;
+    g.sig_int = p.sigma_interface;
+    g.sig_phys = p.sigma_physical;
+    for (int v = 0; v < 4; ++v) g.qinf[v] = p.qinf[v];
+    return g;
+  }
+
+  // Interpolate the donor state (optionally extrapolated) to recv's receivers, into recv's
+  // workspace.
+  cudaError_t interp(int recv, const void *q_donor, const void *const *hist, const double *beta, int nbeta,
+                     cudaStream_t s) {
+    InterpLaunch a{};
+    a.d = dev_mesh(1 - recv);
+    a.g = gas();
+    a.q = q_donor;
+    a.nbeta = nbeta;
+    for (int k = 0; k < nbeta; ++k) {
+      a.hist[k] = hist[k];
+      a.beta[k] = beta[k];
+    }
+    a.nrecv = (int)mh[recv].recv_pt.size();
+    a.base = md[recv].base;
+    a.w = md[recv].w;
+    a.qhat = md[recv].qhat;
+    a.fvhat = viscous() ? md[recv].fvhat : nullptr;
+    return launch_interp(a, p.dtype, viscous(), s);
+  }
+
+  RhsLaunch rhs_args(int k, const void *q) const {
+    RhsLaunch a{};
+    a.m = dev_mesh(k);
+    a.g = gas();
+    a.q = q;
+    a.tile_sat = md[k].tile_sat;
+    a.rows_per_cta = md[k].rows_per_cta;
+    a.flux = md[k].flux;
+    a.sat_ij = md[k].sat_ij;
+    a.sat_code = md[k].sat_code;
+    a.sat_recv = md[k].sat_recv;
+    a.sat_scale = md[k].sat_scale;
+    a.qhat = md[k].qhat;
+    a.fvhat = md[k].fvhat;
+    a.nrecv = (int)mh[k].recv_pt.size();
+    a.err = d_err;
+    a.sat = md[k].sat;
+    a.nsat = (int)mh[k].sat_pt.size();
+    a.dwt = md[k].wt;
+    fill_consts(k, a.cf);
+    fill_consts(k, a.cd);
+    return a;
+  }
+
+  template <typename T>
+  void fill_consts(int k, KConst<T> &c) const {
+    const double g = p.gamma, mu = viscous() ? p.mu : 0.0;
+    c.gam = (T)g;
+    c.g1 = (T)(g - 1.0);
+    c.mu = (T)mu;
+    c.kap = (T)(mu / (p.pr * (g - 1.0)));
+    c.mu43 = (T)(4.0 / 3.0 * mu);
+    c.mu23 = (T)(2.0 / 3.0 * mu);
+    c.sig_int = (T)p.sigma_interface;
+    c.sig_phys = (T)p.sigma_physical;
+    c.tw = (T)(p.twall / (g * (g - 1.0)));
+    for (int v = 0; v < 4; ++v) c.qinf[v] = (T)p.qinf[v];
+    const MeshHost &m = mh[k];
+    if (m.cartesian) {
+      c.mc[0] = (T)m.h[1];
+      c.mc[1] = (T)0;
+      c.mc[2] = (T)0;
+      c.mc[3] = (T)m.h[0];
+      c.mc[4] = (T)(1.0 / (m.h[0] * m.h[1]));
+      c.jx = (T)(1.0 / m.h[0]);
+      c.jy = (T)(1.0 / m.h[1]);
+    } else {
+      for (int q = 0; q < 5; ++q) c.mc[q] = (T)0;
+      c.jx = c.jy = (T)0;
+    }
+  }
+
+  cudaError_t rhs_plain(int k, const void *q_self, const void *q_other, void *out, cudaStream_t s) {
+    cudaError_t e = interp(k, q_other, nullptr, nullptr, 0, s);
+    if (e != cudaSuccess) return e;
+    RhsLaunch a = rhs_args(k, q_self);
+    a.mode = 0;
+    a.out = out;
+    return launch_rhs(a, p.dtype, viscous(), s);
+  }
+
+  void *hist_slot(int k, int slot) const { return (char *)md[k].hist + (size_t)slot * state_elems(k) * esz; }
+
+  // Donor values of mesh `recv`'s receivers from the other mesh's state at `q`, for the
+  // extrapolation sets [set0, set0 + nsets) of the plan (set j: slow extrapolant over [0, j/SR]).
+  DonorLaunch donor_args(int recv, const void *q, int set0, int nsets, bool extrapolate, double Hh) const {
+    DonorLaunch a{};
+    const int don = 1 - recv, m = plan.m;
+    a.d = dev_mesh(don);
+    a.g = gas();
+    a.q = q;
+    a.nsets = nsets;
+    a.npts = md[recv].ndv;
+    a.pts = md[recv].dpts;
+    a.dv = (char *)md[recv].dv + (size_t)set0 * 10 * md[recv].ndv * esz;
+    for (int k = 0; k < m; ++k) a.hist[k] = hist_slot(don, (md[don].head + 1 + k) % m);
+    for (int j = 0; j < nsets; ++j) {
+      int set = set0 + j;
+      a.nb[j] = (extrapolate && set > 0) ? m : 0;
+      for (int k = 0; k < m; ++k) a.beta[j][k] = extrapolate ? plan.ext[set][k] * Hh : 0.0;
+    }
+    return a;
+  }
+
+  cudaError_t donor_vals(int recv, const void *q, int set0, int nsets, bool extrapolate, double Hh,
+                         cudaStream_t s) {
+    return launch_donor_vals(donor_args(recv, q, set0, nsets, extrapolate, Hh), p.dtype, viscous(), s);
+  }
+
+  // Fused right-hand side + Adams-Bashforth update of mesh k with step dt, receivers gathered
+  // from donor-value set `set`. Pushes the new right-hand side into the ring slot after head.
+  cudaError_t fused(int k, int set, double dt, cudaStream_t s) {
+    return launch_rhs(fused_args(k, set, dt), p.dtype, viscous(), s);
+  }
+
+  RhsLaunch fused_args(int k, int set, double dt) const {
+    const int m = plan.m;
+    const MeshDev &d = md[k];
+    int slot = (d.head + 1) % m;
+    RhsLaunch a = rhs_args(k, d.q[d.cur]);
+    a.dv = (char *)d.dv + (size_t)set * 10 * d.ndv * esz;
+    a.didx = d.didx;
+    a.ndv = d.ndv;
+    a.mode = 1;
+    a.out = hist_slot(k, slot);
+    a.qnext = d.q[1 - d.cur];
+    a.nold = m - 1;
+    for (int j = 0; j < m - 1; ++j) {
+      a.hold[j] = hist_slot(k, (slot + 1 + j) % m);
+      a.alpha[j] = plan.ab[j] * dt;
+    }
+    a.alpha[m - 1] = plan.ab[m - 1] * dt;
+    return a;
+  }
+
+  // Enqueue one macro step (Sec. 3.3) for the current ring heads and state buffers, without
+  // changing them. With `side` set, the slow right-hand side and the first fast micro step
+  // (which needs only s(t) and f(t)) run on two streams joined before the second micro step.
+  // frec (eager mode only): the fast state before micro step j is copied to frec[j].
+  cudaError_t issue_step(cudaStream_t s, cudaStream_t sd, void *const *frec = nullptr) {
+    const int F = fast(), Sl = slow(), sr = plan.sr;
+    const double h = H / sr;
+    MeshDev saved_s = md[Sl], saved_f = md[F];
+    cudaError_t e = cudaSuccess;
+    auto run = [&](cudaError_t x) {
+      if (e == cudaSuccess) e = x;
+    };
+    if (sd) {
+      run(cudaEventRecord(ev_fork, s));
+      run(cudaStreamWaitEvent(sd, ev_fork, 0));
+      // side: fast receivers from s(t), first micro step
+      run(donor_vals(F, md[Sl].q[md[Sl].cur], 0, 1, false, H, sd));
+      run(fused(F, 0, h, sd));
+    }
+    // slow: receivers from f(t), fused RHS + update into the other buffer
+    run(timed(SBP_PHASE_INTERP_SLOW, s, [&] { return donor_vals(Sl, md[F].q[md[F].cur], 0, 1, false, H, s); }));
+    run(timed(SBP_PHASE_RHS_SLOW, s, [&] { return fused(Sl, 0, H, s); }));
+    md[Sl].head = (md[Sl].head + 1) % plan.m;
+    // fast receivers for the micro steps that need the slow extrapolant (a_s(t) is now in the ring)
+    int first = sd ? 1 : 0;
+    if (sr > first)
+      run(timed(SBP_PHASE_INTERP_FAST, s,
+                [&] { return donor_vals(F, md[Sl].q[md[Sl].cur], first, sr - first, true, H, s); }));
+    if (sd) {
+      md[F].head = (md[F].head + 1) % plan.m;
+      md[F].cur ^= 1;
+      run(cudaEventRecord(ev_join, sd));
+      run(cudaStreamWaitEvent(s, ev_join, 0));
+    }
+    for (int j = first; j < sr; ++j) {
+      if (frec)
+        run(cudaMemcpyAsync(frec[j], md[F].q[md[F].cur], state_elems(F) * esz, cudaMemcpyDeviceToDevice, s));
+      run(timed(SBP_PHASE_RHS_FAST, s, [&] { return fused(F, j, h, s); }));
+      md[F].head = (md[F].head + 1) % plan.m;
+      md[F].cur ^= 1;
+    }
+    md[Sl] = saved_s;
+    md[F] = saved_f;
+    return e;
+  }
+
+  // Host bookkeeping after one macro step.
+  void advance() {
+    md[slow()].head = (md[slow()].head + 1) % plan.m;
+    md[slow()].cur ^= 1;
+    for (int j = 0; j < plan.sr; ++j) {
+      md[fast()].head = (md[fast()].head + 1) % plan.m;
+      md[fast()].cur ^= 1;
+    }
+    t += H;
+  }
+
+  // Autotuner of the fused kernel's block shape: for each mesh, time the right-hand side (mode
+  // 0, into the history slot the next push overwrites) at several rows-per-CTA values on the
+  // bound state and keep the fastest. The strip width is fixed by the CTA size.
+  bool autotune_on = true;
+  cudaError_t autotune(cudaStream_t s) {
+    static const int cands[] = {8, 16, 32};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      MeshDev &d = md[k];
+      if (!d.hist) continue;
+      void *scratch = hist_slot(k, (d.head + 1) % plan.m);
+      e = interp(k, md[1 - k].q[md[1 - k].cur], nullptr, nullptr, 0, s);
+      float best = 1e30f;
+      int best_rows = d.rows_per_cta;
+      for (int rows : cands) {
+        if (rows > mh[k].nj || e != cudaSuccess) continue;
+        d.rows_per_cta = rows;
+        RhsLaunch a = rhs_args(k, d.q[d.cur]);
+        a.mode = 0;
+        a.out = scratch;
+        e = launch_rhs(a, p.dtype, viscous(), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_rhs(a, p.dtype, viscous(), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          best_rows = rows;
+        }
+      }
+      d.rows_per_cta = best_rows;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return e;
+  }
+
+  // Bootstrap of Sec. 3.1 on the bound buffers: Heun's third-order Runge-Kutta at the micro
+  // step h = H / SR for (m - 1) SR steps on both meshes, recording the fast right-hand side of
+  // the last m - 1 steps and the slow one every SR steps into the rings. With ystore set, the
+  // state of mesh k before step n is copied to ystore[k] + n * state size first.
+  cudaError_t bootstrap(double Hm, cudaStream_t s, void *const *ystore) {
+    const int m = plan.m, sr = plan.sr, F = fast(), Sl = slow();
+    const double h = Hm / sr;
+    void *ystage[2] = {nullptr, nullptr}, *k1tmp[2] = {nullptr, nullptr}, *k23[2] = {nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+      size_t b = state_elems(k) * esz;
+      if (e == cudaSuccess) e = cudaMalloc(&ystage[k], b);
+      if (e == cudaSuccess) e = cudaMalloc(&k1tmp[k], b);
+      if (e == cudaSuccess) e = cudaMalloc(&k23[k], b);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ystage[k], 0, b, s);
+      md[k].head = -1;
+      md[k].count = 0;
+    }
+    const int nsteps = (m - 1) * sr;
+    for (int step = 0; step < nsteps && e == cudaSuccess; ++step) {
+      void *y[2] = {md[0].q[md[0].cur], md[1].q[md[1].cur]};
+      void *k1[2] = {k1tmp[0], k1tmp[1]};
+      if (ystore)
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+          size_t b = state_elems(k) * esz;
+          e = cudaMemcpyAsync((char *)ystore[k] + (size_t)step * b, y[k], b, cudaMemcpyDeviceToDevice, s);
+        }
+      bool rec_f = step >= nsteps - (m - 1), rec_s = step % sr == 0;
+      if (rec_f) {
+        MeshDev &d = md[F];
+        d.head = (d.head + 1) % m;
+        d.count++;
+        k1[F] = hist_slot(F, d.head);
+      }
+      if (rec_s) {
+        MeshDev &d = md[Sl];
+        d.head = (d.head + 1) % m;
+        d.count++;
+        k1[Sl] = hist_slot(Sl, d.head);
+      }
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = rhs_plain(k, y[k], y[1 - k], k1[k], s);
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = launch_axpy(y[k], k1[k], h / 3.0, nullptr, 0.0, ystage[k], state_elems(k), p.dtype, s);
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = rhs_plain(k, ystage[k], ystage[1 - k], k23[k], s);
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = launch_axpy(y[k], k23[k], 2.0 * h / 3.0, nullptr, 0.0, ystage[k], state_elems(k), p.dtype, s);
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = rhs_plain(k, ystage[k], ystage[1 - k], k23[k], s);
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = launch_axpy(y[k], k1[k], h / 4.0, k23[k], 3.0 * h / 4.0, y[k], state_elems(k), p.dtype, s);
+    }
+    cudaError_t es = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = es;
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(ystage[k]);
+      cudaFree(k1tmp[k]);
+      cudaFree(k23[k]);
+    }
+    return e;
+  }
+
+  uint64_t phase_key() const {
+    const MeshDev &a = md[slow()], &b = md[fast()];
+    return (uint64_t)a.cur | ((uint64_t)a.head << 1) | ((uint64_t)b.cur << 8) | ((uint64_t)b.head << 9);
+  }
+
+  cudaError_t launch_step_graph(cudaStream_t s) {
+    uint64_t key = phase_key();
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+      cudaError_t e;
+      if (!cap) {
+        if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+      }
+      if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+      cudaError_t ei = issue_step(cap, side);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(cap, &g);
+      if (ei != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return ei;
+      }
+      if (e != cudaSuccess) return e;
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return e;
+      it = graphs.emplace(key, ex).first;
+    }
+    return cudaGraphLaunch(it->second, s);
+  }
+};

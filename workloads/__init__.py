@@ -198,3 +198,19 @@ def batched_vortices(seed=0, n_systems=64, n_range=(128, 512), ratios=(2, 4, 8),
                                step_ratio=r, cfl=cfl, jitter=0.5 * fine_half)
         out.append(wl)
     return out
+
+
+def wake_probes(seed=0, n=8, x_range=(1.8, 3.5), y_range=(-0.6, 0.6)):
+    """n probe points (x, y) drawn uniformly in a box behind the cylinder (the wake region)."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(x_range[0], x_range[1], n), rng.uniform(y_range[0], y_range[1], n)], axis=1)
+
+
+def cylinder_adjoint(seed=0, **kw):
+    """The adjoint workload: the cylinder geometry at half resolution (O-grid 256 x 64 on a
+    512 x 256 background of spacing 0.1), step ratio 4, with 8 wake probes."""
+    args = dict(n_theta=256, n_r=64, s_bg=0.1, bg_n=(512, 256), bg_lo=(-12.8, -12.8), step_ratio=4)
+    args.update(kw)
+    wl = cylinder_overset(seed=seed, **args)
+    wl["probes"] = wake_probes(seed + 1, 8, x_range=(3.0, 6.0), y_range=(-1.0, 1.0))
+    return wl
