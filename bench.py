@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batched workload")
+    ap.add_argument("--no-rate-compare", action="store_true", help="skip MRAB vs single-rate at equal error")
     return ap.parse_args()
 
 
@@ -309,6 +310,88 @@ def _run_batch(dtype, steps, warmup, seed=0):
             "rows_per_cta": info["rows_per_cta"], "grid": info["grid"], "setup_s": setup_s}
 
 
+def _l2_error(g, qs, ref):
+    """Eq. (l2error): sqrt of the sum over both meshes' active points of the squared error
+    (all variables) times the cell size 1/J."""
+    import numpy as np
+    tot = 0.0
+    for k in range(2):
+        t = g.tables(k)
+        vol = np.where(t["iblank"] != 0, 1.0 / t["metrics"][4], 0.0)
+        e = np.asarray(qs[k]) - np.asarray(ref[k])
+        tot += float(np.sum((e * e).sum(axis=0) * vol))
+    return float(np.sqrt(tot))
+
+
+def _time_slow_steps(g, n_slow, per_slow):
+    """Median device time of one slow step (per_slow library steps, CUDA-graph replay)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_slow)]
+    for k in range(n_slow):
+        ev[k][0].record(stream)
+        g.mrab_step(per_slow)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    g.check()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def _mrab_vs_single_rate(name, wl, k_slow, exact=None, ref_factor=8):
+    """MRAB (step ratio SR, macro step H) against single-rate AB (SR = 1) at the micro step
+    h = H / SR on both meshes, both from their own Runge-Kutta bootstraps (Sec. 3.1) and compared
+    at the same physical time T = (m - 1) H + k_slow H: seconds per slow step H and the L2 error
+    of eq. (l2error) against `exact` (the analytic solution, a function of T) or, without one,
+    against single-rate AB at h / ref_factor."""
+    import torch
+    import paper_1805_06607_gb300 as sbp
+
+    p = wl["params"]
+    sr, m = int(p["step_ratio"]), int(p["hist_len"])
+    ga = sbp.System(wl, dtype="f64")
+    ga.bind(wl["q0"])
+    qd = [ga.current_state(k) for k in range(2)]
+    _, H = ga.timestep(qd[0], qd[1])
+    h = H / sr
+    T = (m - 1) * H + k_slow * H
+    ga.mrab_init(H)
+    t_mrab = _time_slow_steps(ga, k_slow, 1)
+    q_mrab = [ga.to_host(k, ga.current_state(k)) for k in range(2)]
+    wl1 = dict(wl, params=dict(p, step_ratio=1))
+    gb = sbp.System(wl1, dtype="f64")
+    gb.bind(wl["q0"])
+    gb.mrab_init(h)
+    gb.mrab_step((m - 1) * (sr - 1))  # its bootstrap covered (m - 1) h of the (m - 1) H
+    t_srab = _time_slow_steps(gb, k_slow, sr)
+    q_srab = [gb.to_host(k, gb.current_state(k)) for k in range(2)]
+    if exact is not None:
+        ref = exact(T)
+        ref_kind = "analytic solution"
+    else:
+        gr = sbp.System(wl1, dtype="f64")
+        gr.bind(wl["q0"])
+        hr = h / ref_factor
+        gr.mrab_init(hr)
+        gr.mrab_step(int(round(T / hr)) - (m - 1))
+        torch.cuda.synchronize()
+        gr.check()
+        ref = [gr.to_host(k, gr.current_state(k)) for k in range(2)]
+        ref_kind = "single-rate AB%d at h/%d (same discretisation)" % (int(p["order"]), ref_factor)
+        gr.close()
+    e_m, e_s = _l2_error(ga, q_mrab, ref), _l2_error(gb, q_srab, ref)
+    n_s = wl["meshes"][1 - p["fast_mesh"]]["n"][0] * wl["meshes"][1 - p["fast_mesh"]]["n"][1]
+    n_f = wl["meshes"][p["fast_mesh"]]["n"][0] * wl["meshes"][p["fast_mesh"]]["n"][1]
+    ga.close()
+    gb.close()
+    return {"workload": name, "step_ratio": sr, "order": int(p["order"]), "H": H, "slow_steps": k_slow, "T": T,
+            "s_per_slow_step_mrab": t_mrab / 1e3, "s_per_slow_step_single_rate": t_srab / 1e3,
+            "speedup": t_srab / t_mrab, "l2_mrab": e_m, "l2_single_rate": e_s, "l2_reference": ref_kind,
+            "equal_error": bool(e_m <= 1.1 * e_s),
+            "model_ratio_eq_perf_AB": (sr * n_f + n_s) / (sr * (n_f + n_s)),
+            "timing": "median over the slow steps of CUDA-event device time, CUDA-graph replay (the first steps "
+                      "of each ring phase include its capture), FP64"}
+
+
 def _cpu_baseline(wl, seconds):
     """The oracle, as it stands, on the host: whole MRAB macro steps of the same workload."""
     import numpy as np
@@ -414,6 +497,16 @@ def main():
                                     "roofline": _roofline(r2, wl, other, hbm_peak, peak_kind),
                                     "autotuned_blocks": r2["tuning"],
                                     "phases_ms_per_step": {p: v[0] / args.steps for p, v in r2["prof"].items()}}}
+    if not args.no_rate_compare and rank == 0:
+        import workloads as W2
+        c1 = W2.vortex_box_in_box(seed=0)
+        vort = c1["vortex"]
+        exact = lambda T: [W2.vortex_state(mm["x"], mm["y"], T, **vort) for mm in c1["meshes"]]
+        line["mrab_vs_single_rate"] = {
+            "vortex_box_in_box": _mrab_vs_single_rate("2D Euler vortex: periodic 64x64 + 41x41 patch, SR 2",
+                                                      c1, 100, exact=exact),
+            "cylinder": _mrab_vs_single_rate(WORKLOAD, W2.cylinder_overset(seed=0), 20),
+        }
     if not args.no_batch:
         line["batched"] = {dt: _run_batch(dt, args.steps, args.warmup, seed=rank) for dt in ("f64", "f32")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
