@@ -89,8 +89,10 @@ typedef struct {
   size_t hist_bytes;    /* hist_len * state_bytes */
   int nvar, n_holes, n_receivers, n_sat_points;
   int elem_size;        /* 8 (F64) or 4 (F32) */
-  int strip_width;      /* columns per CTA of the fused right-hand-side kernel */
+  int strip_width;      /* columns per CTA of the right-hand-side kernel */
   int rows_per_cta;     /* rows per CTA (chosen by the autotuner, see sbp_autotune) */
+  int single_pass;      /* 1: the single-pass marching kernel (rows_per_cta = its chunk of rows);
+                           0: the flux + derivative kernel pair */
 } sbp_mesh_info;
 
 /* Create a two-mesh overset system (mesh 0 = background, mesh 1 = the overset fine mesh) and
@@ -174,12 +176,24 @@ sbp_status sbp_mrab_step(sbp_system_t sys, int n, void *stream);
  * (sbp_profile_enable) force the kernel-by-kernel mode while they are on. */
 sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
 
-/* Autotuner of the fused right-hand-side kernel's block shape (rows per CTA; the strip width
- * is fixed by the CTA size): for each mesh it times the kernel on the bound state at several
- * shapes and keeps the fastest (reported by sbp_mesh_info_get). It runs at the end of
- * sbp_mrab_init while enabled (the default); enabling it on an initialised system runs it at
- * once. Synchronises the stream. */
+/* Autotuner of the right-hand side's kernel and block shape. Two kernel designs compute the
+ * same bits: a pair (contravariant fluxes of a 32 x rows tile with a halo-3 primitive tile in
+ * shared memory, then derivatives + SAT + update from a halo-3 flux tile; 8, 16 or 32 rows per
+ * CTA), and a single pass that marches a strip of 64 columns up a chunk of 16, 32, 64 or 128
+ * rows, 4 rows per step, with 16-row ring buffers of state, metrics, class bytes (copied one
+ * step ahead with cp.async), primitives and fluxes in shared memory (state, metrics and result
+ * cross HBM once). For each mesh the autotuner times every candidate on the bound state
+ * and keeps the fastest (reported by sbp_mesh_info_get). It runs at the end of sbp_mrab_init
+ * while enabled (the default); enabling it on an initialised system runs it at once.
+ * Synchronises the stream. */
 sbp_status sbp_autotune(sbp_system_t sys, int enable, void *stream);
+
+/* Choose the right-hand-side kernel of `mesh` by hand (the autotuner's choice otherwise): strip
+ * = 0 selects the kernel pair with rows = 8, 16 or 32 rows per CTA; strip = 64 the single-pass
+ * marching kernel with chunks of `rows` rows (1..65535). Both give the same bits.
+ * Later autotuner runs (sbp_mrab_init, sbp_autotune) override the choice; disable the
+ * autotuner (sbp_autotune(sys, 0, stream)) to keep it. */
+sbp_status sbp_set_rhs_shape(sbp_system_t sys, int mesh, int strip, int rows);
 
 /* Macro step size H and elapsed time since the end of the bootstrap. */
 sbp_status sbp_mrab_time(sbp_system_t sys, double *H, double *t);

@@ -47,7 +47,7 @@ class MeshInfo(ctypes.Structure):
                 ("field_elems", ctypes.c_size_t), ("state_bytes", ctypes.c_size_t),
                 ("hist_bytes", ctypes.c_size_t), ("nvar", ctypes.c_int), ("n_holes", ctypes.c_int),
                 ("n_receivers", ctypes.c_int), ("n_sat_points", ctypes.c_int), ("elem_size", ctypes.c_int),
-                ("strip_width", ctypes.c_int), ("rows_per_cta", ctypes.c_int)]
+                ("strip_width", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("single_pass", ctypes.c_int)]
 
 
 class AdjointDesc(ctypes.Structure):
@@ -77,6 +77,7 @@ _SIGS = {
     "sbp_use_graphs": [_P, _I],
     "sbp_autotune": [_P, _I, _P],
     "sbp_profile_read": [_P, _P, _P, _I],
+    "sbp_set_rhs_shape": [_P, _I, _I, _I],
 }
 _SIGS.update({
     "sbp_batch_create": [ctypes.POINTER(_P), _I, _I, _P, ctypes.POINTER(_P)],
@@ -292,6 +293,11 @@ class System:
 
     def autotune(self, on=True, stream=None):
         _check(_lib.sbp_autotune(self.h, int(bool(on)), _stream(stream)), "sbp_autotune")
+
+    def set_rhs_shape(self, k, strip, rows):
+        """strip 0: kernel pair with `rows` rows per CTA; 64: marching kernel, chunks of `rows`."""
+        _check(_lib.sbp_set_rhs_shape(self.h, k, int(strip), int(rows)), "sbp_set_rhs_shape")
+        self.info[k] = self.mesh_info(k)
 
     def use_graphs(self, on=True):
         _check(_lib.sbp_use_graphs(self.h, int(bool(on))), "sbp_use_graphs")

@@ -153,8 +153,9 @@ sbp_status sbp_mesh_info_get(sbp_system_t S, int k, sbp_mesh_info *info) {
   info->n_receivers = (int)m.recv_pt.size();
   info->n_sat_points = (int)m.sat_pt.size();
   info->elem_size = (int)S->esz;
-  info->rows_per_cta = S->md[k].rows_per_cta;
-  info->strip_width = kTileX;
+  info->rows_per_cta = S->md[k].strip ? S->md[k].chunk : S->md[k].rows_per_cta;
+  info->strip_width = S->md[k].strip ? S->md[k].strip : kTileX;
+  info->single_pass = S->md[k].strip ? 1 : 0;
   return SBP_OK;
 }
 
@@ -296,6 +297,23 @@ sbp_status sbp_autotune(sbp_system_t S, int enable, void *stream) {
     CUDA_TRY(S->autotune((cudaStream_t)stream));
     S->clear_graphs();
   }
+  return SBP_OK;
+}
+
+sbp_status sbp_set_rhs_shape(sbp_system_t S, int k, int strip, int rows) {
+  if (!S || k < 0 || k > 1) return fail(SBP_ERR_ARG, "bad argument");
+  MeshDev &d = S->md[k];
+  if (strip == 0) {
+    if (rows != 8 && rows != 16 && rows != 32) return fail(SBP_ERR_ARG, "split kernels take 8, 16 or 32 rows per CTA");
+    d.strip = 0;
+    d.rows_per_cta = rows;
+  } else {
+    if (strip != 64) return fail(SBP_ERR_ARG, "the marching kernel takes strips of 64 columns");
+    if (rows < 1 || rows > 65535) return fail(SBP_ERR_ARG, "chunk rows out of range");
+    d.strip = strip;
+    d.chunk = rows;
+  }
+  S->clear_graphs();
   return SBP_OK;
 }
 

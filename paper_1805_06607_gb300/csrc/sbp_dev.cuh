@@ -58,6 +58,62 @@ __device__ __forceinline__ T dline(const T *f, int s, int st, unsigned code) {
   return sgn > 0 ? acc : -acc;
 }
 
+// A derivative row decoded once per point and direction: tap offsets (times the direction
+// sign), weights, and whether the sum is negated (a closure counted from the segment's high
+// end). row_sum applies it to one plane with dline's operation order, through per-tap pointers
+// shared by all planes (plane c at offset c * plane stride).
+template <typename T>
+struct Row {
+  int off[4];
+  T w[4];
+  bool neg;
+};
+
+template <typename T>
+__device__ __forceinline__ Row<T> decode_row(unsigned code) {
+  Row<T> r;
+  int row, sgn;
+  row_of(code, row, sgn);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    r.off[e] = sgn * c_off[row][e];
+    r.w[e] = wgt<T>(row, e);
+  }
+  r.neg = sgn < 0;
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T row_sum(const Row<T> &r, const T *const p[4], int plane) {
+  T acc = T(0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc += r.w[e] * p[e][plane];
+  return r.neg ? -acc : acc;
+}
+
+// The interior row (row 4) with its weights as compile-time constants: the same values and
+// operation order as row_sum on a decoded interior row, with the taps at fixed offsets.
+template <typename T>
+struct CentralRow;
+template <>
+struct CentralRow<float> {
+  static constexpr float w0 = 1.0f / 12.0f, w1 = -2.0f / 3.0f, w2 = 2.0f / 3.0f, w3 = -1.0f / 12.0f;
+};
+template <>
+struct CentralRow<double> {
+  static constexpr double w0 = 1.0 / 12.0, w1 = -2.0 / 3.0, w2 = 2.0 / 3.0, w3 = -1.0 / 12.0;
+};
+
+template <typename T>
+__device__ __forceinline__ T central_sum(const T *const p[4], int plane) {
+  T acc = T(0);
+  acc += CentralRow<T>::w0 * p[0][plane];
+  acc += CentralRow<T>::w1 * p[1][plane];
+  acc += CentralRow<T>::w2 * p[2][plane];
+  acc += CentralRow<T>::w3 * p[3][plane];
+  return acc;
+}
+
 // Index g on a line of n points: wrapped once on a periodic line; false when outside the line
 // (non-periodic) or more than one period away (strips wider than a small periodic mesh).
 __device__ __forceinline__ bool wrap_index(int &g, int n, int per) {
@@ -68,6 +124,21 @@ __device__ __forceinline__ bool wrap_index(int &g, int n, int per) {
   return (unsigned)g < (unsigned)n;
 }
 
+// Products and fused multiply-adds with a fixed rounding (never re-associated or contracted
+// differently by the compiler), for expressions that several kernels must evaluate to the
+// same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// p = (gamma - 1)(rho E - (rho u u + rho v v) / 2).
+template <typename T>
+__device__ __forceinline__ T pressure_of(T gam, T rE, T ru, T rv, T u, T v) {
+  const T ke = fma_rn(ru, u, mul_rn(rv, v));
+  return mul_rn(gam - T(1), fma_rn(T(-0.5), ke, rE));
+}
+
 // ---------------------------------------------------------------------------------------------
 // Pointwise physics. q = (rho, rho u, rho v, rho E), p = (gamma-1)(rho E - rho |u|^2/2),
 // T = gamma p / rho.
@@ -76,7 +147,7 @@ __device__ __forceinline__ void inviscid_flux(const T q[4], T gam, T F[4], T G[4
   T ri = T(1) / q[0];
   u = q[1] * ri;
   v = q[2] * ri;
-  p = (gam - T(1)) * (q[3] - T(0.5) * (q[1] * u + q[2] * v));
+  p = pressure_of(gam, q[3], q[1], q[2], u, v);
   F[0] = q[1];
   F[1] = q[1] * u + p;
   F[2] = q[2] * u;
@@ -156,14 +227,20 @@ __device__ __forceinline__ void point_metrics(const DevMesh &m, int gi, int gj, 
   }
 }
 
+// Primitives (u, v, T) of the conserved state (q0, q1, q2, q3).
 template <typename T>
-__device__ __forceinline__ void prim_at(const T *q, size_t field, size_t p, T gam, T pr[3]) {
-  T r = q[p], ri = T(1) / r;
-  T u = q[field + p] * ri, v = q[2 * field + p] * ri;
-  T pres = (gam - T(1)) * (q[3 * field + p] - T(0.5) * (q[field + p] * u + q[2 * field + p] * v));
+__device__ __forceinline__ void prim4(T q0, T q1, T q2, T q3, T gam, T pr[3]) {
+  T ri = T(1) / q0;
+  T u = q1 * ri, v = q2 * ri;
+  T pres = pressure_of(gam, q3, q1, q2, u, v);
   pr[0] = u;
   pr[1] = v;
   pr[2] = gam * pres * ri;
+}
+
+template <typename T>
+__device__ __forceinline__ void prim_at(const T *q, size_t field, size_t p, T gam, T pr[3]) {
+  prim4(q[p], q[field + p], q[2 * field + p], q[3 * field + p], gam, pr);
 }
 
 // Cartesian viscous fluxes at one point from the state in global memory (used at SAT points).
@@ -249,10 +326,17 @@ __device__ __forceinline__ void visc_flux_k(const KConst<T> &k, T u, T v, const 
 template <typename T, bool CURV>
 __device__ __forceinline__ void smem_grads(const RhsLaunch &a, const T *prim, int rn, int r, int rx, unsigned code,
                                            const T mt[5], T gr[6]) {
+  const Row<T> ri = decode_row<T>(code & 15u), rj = decode_row<T>(code >> 4);
+  const T *pi[4], *pj[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    pi[e] = prim + r + ri.off[e];
+    pj[e] = prim + r + rj.off[e] * rx;
+  }
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
-    T dxi = dline(prim + f * rn, r, 1, code & 15u);
-    T deta = dline(prim + f * rn, r, rx, code >> 4);
+    T dxi = row_sum(ri, pi, f * rn);
+    T deta = row_sum(rj, pj, f * rn);
     if (CURV) {
       gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
       gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
@@ -405,7 +489,7 @@ __device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T 
       const int r = (lj + H) * RX + (li + H);
       u = prim[r];
       v = prim[RN + r];
-      pr = qp[0] * prim[2 * RN + r] / k.gam;  // p = rho T / gamma
+      pr = pressure_of(k.gam, qp[3], qp[1], qp[2], u, v);  // prim_at's pressure
       T gr[6];
       smem_grads<T, CURV>(a, prim, RN, r, RX, scls[r], mt, gr);
       T Fv[3], Gv[3];
@@ -494,9 +578,15 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
       T jac;
       if (CURV) jac = static_cast<const T *>(m.met)[4 * m.field + p];
       else jac = kc<T>(a).mc[4];
+      const Row<T> ri = decode_row<T>(code & 15u), rj = decode_row<T>(code >> 4);
+      const T *pi[4], *pj[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        rhs[c] = -jac * (dline(sf + c * RN, r, 1, code & 15u) + dline(sf + (4 + c) * RN, r, RX, code >> 4));
+      for (int e = 0; e < 4; ++e) {
+        pi[e] = sf + r + ri.off[e];
+        pj[e] = sf + r + rj.off[e] * RX;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rhs[c] = -jac * (row_sum(ri, pi, c * RN) + row_sum(rj, pj, (4 + c) * RN));
       if (s0 < s1) {
         // the tile's SAT entries are sorted by (j, i): binary search for this point
         uint32_t key = (uint32_t)gi | ((uint32_t)gj << 16);

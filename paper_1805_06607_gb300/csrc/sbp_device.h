@@ -47,7 +47,10 @@ struct RhsLaunch {
   // SAT points of this mesh grouped by 32 x 8 tile (tile id = (i / 32) * ceil(nj / 8) + j / 8);
   // tile_sat has one offset per tile + 1
   const int *tile_sat;
-  int rows_per_cta;  // 8, 16 or 32: rows per CTA of the right-hand-side kernels
+  int rows_per_cta;  // 8, 16 or 32: rows per CTA of the split right-hand-side kernels
+  // strip = 0: split kernels (k_flux, k_update); 64: the single-pass marching kernel (k_march)
+  // with strips of 64 columns and chunks of `chunk` rows per CTA
+  int strip, chunk;
   void *flux;        // 8 planes: F^_xi (4 variables), F^_eta (4 variables)
   const uint32_t *sat_ij;   // i | j << 16
   const uint32_t *sat_code;

@@ -8,6 +8,7 @@
 #include <cstring>
 
 #include "sbp_dev.cuh"
+#include "sbp_march_impl.cuh"
 
 namespace sbp {
 
@@ -59,6 +60,10 @@ static cudaError_t launch_rhs_ty(const RhsLaunch &a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_rhs_typed(const RhsLaunch &a, bool viscous, cudaStream_t s) {
   bool curv = !a.m.cart;
+  if (a.strip) {
+    if (viscous) return curv ? launch_march_w<T, true, true>(a, s) : launch_march_w<T, true, false>(a, s);
+    return curv ? launch_march_w<T, false, true>(a, s) : launch_march_w<T, false, false>(a, s);
+  }
   if (viscous) return curv ? launch_rhs_ty<T, true, true>(a, s) : launch_rhs_ty<T, true, false>(a, s);
   return curv ? launch_rhs_ty<T, false, true>(a, s) : launch_rhs_ty<T, false, false>(a, s);
 }

@@ -53,6 +53,7 @@ struct MeshDev {
   // (receiver * 16 + stencil slot) entries that read it
   int *inv_off = nullptr, *inv_re = nullptr;
   int rows_per_cta = 16;
+  int strip = 0, chunk = 64;  // strip > 0: the single-pass marching kernel (see RhsLaunch)
   // bound integrator buffers
   void *q[2] = {nullptr, nullptr};
   void *hist = nullptr;
@@ -248,6 +249,8 @@ struct sbp_system_s {
     a.q = q;
     a.tile_sat = md[k].tile_sat;
     a.rows_per_cta = md[k].rows_per_cta;
+    a.strip = md[k].strip;
+    a.chunk = md[k].chunk;
     a.flux = md[k].flux;
     a.sat_ij = md[k].sat_ij;
     a.sat_code = md[k].sat_code;
@@ -413,12 +416,16 @@ struct sbp_system_s {
     t += H;
   }
 
-  // Autotuner of the fused kernel's block shape: for each mesh, time the right-hand side (mode
-  // 0, into the history slot the next push overwrites) at several rows-per-CTA values on the
-  // bound state and keep the fastest. The strip width is fixed by the CTA size.
+  // Autotuner of the right-hand side's kernel and block shape: for each mesh, time the
+  // right-hand side (mode 0, into the history slot the next push overwrites) on the bound state
+  // with the split kernels at 8, 16 and 32 rows per CTA and with the marching kernel (strips of
+  // 64 columns) at chunks of 16, 32, 64 and 128 rows, and keep the fastest.
   bool autotune_on = true;
   cudaError_t autotune(cudaStream_t s) {
-    static const int cands[] = {8, 16, 32};
+    struct Cand {
+      int strip, rows;
+    };
+    static const Cand cands[] = {{0, 8}, {0, 16}, {0, 32}, {64, 16}, {64, 32}, {64, 64}, {64, 128}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -428,10 +435,14 @@ struct sbp_system_s {
       void *scratch = hist_slot(k, (d.head + 1) % plan.m);
       e = interp(k, md[1 - k].q[md[1 - k].cur], nullptr, nullptr, 0, s);
       float best = 1e30f;
-      int best_rows = d.rows_per_cta;
-      for (int rows : cands) {
-        if (rows > mh[k].nj || e != cudaSuccess) continue;
-        d.rows_per_cta = rows;
+      Cand best_c{d.strip, d.strip ? d.chunk : d.rows_per_cta};
+      for (const Cand &c : cands) {
+        if (e != cudaSuccess) continue;
+        if (c.strip == 0 && c.rows > mh[k].nj) continue;
+        if (c.strip > 0 && c.rows > 2 * mh[k].nj) continue;
+        d.strip = c.strip;
+        if (c.strip) d.chunk = c.rows;
+        else d.rows_per_cta = c.rows;
         RhsLaunch a = rhs_args(k, d.q[d.cur]);
         a.mode = 0;
         a.out = scratch;
@@ -444,10 +455,12 @@ struct sbp_system_s {
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         if (e == cudaSuccess && ms < best) {
           best = ms;
-          best_rows = rows;
+          best_c = c;
         }
       }
-      d.rows_per_cta = best_rows;
+      d.strip = best_c.strip;
+      if (best_c.strip) d.chunk = best_c.rows;
+      else d.rows_per_cta = best_c.rows;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -1,0 +1,106 @@
+"""The single-pass marching right-hand-side kernel against the kernel pair and the oracle.
+
+Both designs perform the same floating-point operations per point in the same order, so the
+right-hand side and whole MRAB runs must agree bit for bit, for every chunk height (chunks that are
+not a multiple of the rows per tick, chunks taller than the mesh,
+periodic wrap in i and j, holes, ragged edges), in FP64 and FP32; FP64 also matches the oracle
+to the 1e-12 parity bar."""
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import build_library
+from oracle import OracleSystem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sbp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build_library()
+    import paper_1805_06607_gb300 as mod
+    return mod
+
+
+CASES = {
+    "vortex": lambda: W.vortex_box_in_box(seed=31),
+    "cylinder": lambda: W.cylinder_small(seed=32),
+    "mms_viscous": lambda: W.mms_box_in_box(52, "viscous"),
+    "cylinder_ragged": lambda: W.cylinder_small(seed=33, n_theta=72, n_r=20, bg_n=(90, 50), hist_len=4),
+}
+SHAPES = [(64, 7), (64, 32), (64, 1), (64, 24), (64, 128), (64, 1000)]
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_march_rhs_bit_identical(sbp, case, dtype):
+    wl = CASES[case]()
+    g = sbp.System(wl, dtype=dtype)
+    q = [g.to_device(k, wl["q0"][k]) for k in range(2)]
+    for k in range(2):
+        g.set_rhs_shape(k, 0, 16)
+        ref = g.rhs_eval(k, q[k], q[1 - k]).clone()
+        for strip, rows in SHAPES:
+            g.set_rhs_shape(k, strip, rows)
+            info = g.mesh_info(k)
+            assert info.single_pass == 1 and info.strip_width == strip and info.rows_per_cta == rows
+            got = g.rhs_eval(k, q[k], q[1 - k])
+            assert torch.equal(got, ref), (k, strip, rows)
+    if dtype == "f64":
+        o = OracleSystem(wl)
+        for k in range(2):
+            g.set_rhs_shape(k, 64, 24)
+            got = g.to_host(k, g.rhs_eval(k, q[k], q[1 - k]))
+            want = o.coupled_rhs(k, wl["q0"][k], wl["q0"][1 - k])
+            act = o.iblank[k] != 0
+            assert _rel(got[:, act], want[:, act]) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["vortex", "cylinder_ragged"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_march_mrab_bit_identical(sbp, case, dtype):
+    wl = CASES[case]()
+    runs = []
+    for shape in [(0, 8), (64, 40), (64, 16)]:
+        g = sbp.System(wl, dtype=dtype)
+        g.autotune(False)
+        for k in range(2):
+            g.set_rhs_shape(k, *shape)
+        g.bind(wl["q0"])
+        g.mrab_init()
+        g.mrab_step(5)
+        g.check()
+        runs.append([g.current_state(k).clone() for k in range(2)])
+        g.close()
+    for r in runs[1:]:
+        for k in range(2):
+            assert torch.equal(r[k], runs[0][k])
+
+
+def test_autotuner_reports_a_candidate(sbp):
+    wl = W.cylinder_small(seed=34)
+    g = sbp.System(wl, dtype="f32")
+    g.bind(wl["q0"])
+    g.mrab_init()
+    for k in range(2):
+        info = g.mesh_info(k)
+        if info.single_pass:
+            assert info.strip_width == 64 and info.rows_per_cta in (16, 32, 64, 128)
+        else:
+            assert info.strip_width == 32 and info.rows_per_cta in (8, 16, 32)
+
+
+def test_bad_shapes_rejected(sbp):
+    wl = W.vortex_box_in_box(seed=35, n_bg=40, n_fine=25)
+    g = sbp.System(wl)
+    for args in [(0, 12), (48, 32), (32, 32), (64, 0), (64, -3)]:
+        with pytest.raises(sbp.SbpError):
+            g.set_rhs_shape(0, *args)
