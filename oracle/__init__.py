@@ -5,9 +5,10 @@ benchmark's ``cpu_baseline`` / ``--impl reference`` legs use it to check and
 time the GPU library. The GPU library never imports it and shares no code
 with it; the two meet only through the seeded inputs of ``workloads``.
 
-The C part (``orc2d.c``) holds the per-point arithmetic; ``system.py`` holds
-the assembly (hole cut, receivers, donors), the Adams-Bashforth coefficient
-solve and the time integrators, each citing the passage it follows.
+The C part (``orc2d.c``, ``orc3d.c``, ``orc_sbp.h``) holds the per-point
+arithmetic; ``system.py`` (2D) and ``system3d.py`` (3D Cartesian) hold the
+assembly (hole cut, receivers, donors), the Adams-Bashforth coefficient solve
+and the time integrators, each citing the passage it follows.
 """
 from __future__ import annotations
 
@@ -16,14 +17,15 @@ import os
 import subprocess
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "orc2d.c")]
+_SRC = [os.path.join(_HERE, "orc2d.c"), os.path.join(_HERE, "orc3d.c")]
+_DEPS = _SRC + [os.path.join(_HERE, "orc_sbp.h")]
 _SO = os.path.join(_HERE, "_build", "liborc.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle's C part with gcc (no FMA contraction, so x86 and Arm agree)."""
-    newest = max(os.path.getmtime(s) for s in _SRC)
+    newest = max(os.path.getmtime(s) for s in _DEPS)
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
         return _SO
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
@@ -66,12 +68,26 @@ def lib():
     L.orc_dt2d.restype = D
     L.orc_apply_d1.argtypes = [I, P, P, P]
     L.orc_apply_d1.restype = I
+    L.orc_classes3d.argtypes = [I, I, I, I, I, I, P, P, P, P]
+    L.orc_classes3d.restype = I
+    L.orc_viscflux3d.argtypes = [I, I, I, P, P, P, D, D, D, P, D, D, D, P]
+    L.orc_viscflux3d.restype = I
+    L.orc_penalty_matrix3d.argtypes = [P, D, D, D, D, I, P]
+    L.orc_penalty_matrix3d.restype = None
+    L.orc_rhs3d.argtypes = [I, I, I, P, P, P, D, D, D, P, I, D, D, D,
+                            I, P, P, P, P, P, P, I, P, P, P, D, D, P]
+    L.orc_rhs3d.restype = I
+    L.orc_interp3d.argtypes = [I, I, I, I, P, I, P, P, P]
+    L.orc_interp3d.restype = I
+    L.orc_dt3d.argtypes = [I, I, I, P, D, D, D, P, D, D, D]
+    L.orc_dt3d.restype = D
     _lib = L
     return L
 
 
 from .system import (OracleSystem, ab_coefficients, mrab_macro_step, rk3_heun_step,  # noqa: E402
                      srab_step, l2_norm)
+from .system3d import OracleSystem3D  # noqa: E402
 
-__all__ = ["build", "lib", "OracleSystem", "ab_coefficients", "mrab_macro_step", "rk3_heun_step",
+__all__ = ["build", "lib", "OracleSystem", "OracleSystem3D", "ab_coefficients", "mrab_macro_step", "rk3_heun_step",
            "srab_step", "l2_norm"]

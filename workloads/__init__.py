@@ -214,3 +214,97 @@ def cylinder_adjoint(seed=0, **kw):
     wl = cylinder_overset(seed=seed, **args)
     wl["probes"] = wake_probes(seed + 1, 8, x_range=(3.0, 6.0), y_range=(-1.0, 1.0))
     return wl
+
+
+# --------------------------------------------------------------------------------------------
+# 3D Cartesian workloads
+# --------------------------------------------------------------------------------------------
+
+def cartesian_mesh3d(name, n, lo, h, bc, periodic=(False, False, False)):
+    """Uniform 3D Cartesian mesh with n points per direction starting at lo. Faces are ordered
+    i-low, i-high, j-low, j-high, k-low, k-high."""
+    return {"name": name, "dim": 3, "n": tuple(int(v) for v in n), "periodic": tuple(bool(v) for v in periodic),
+            "cartesian": True, "lo": tuple(map(float, lo)), "h": tuple(map(float, h)), "bc": tuple(bc)}
+
+
+def axes3d(m):
+    """Coordinates of a 3D Cartesian mesh as three 1D arrays (x along i, y along j, z along k)."""
+    return [m["lo"][d] + m["h"][d] * np.arange(m["n"][d], dtype=np.float64) for d in range(3)]
+
+
+def freestream3d(mach, gamma=GAMMA):
+    return np.array([1.0, mach, 0.0, 0.0, 1.0 / (gamma * (gamma - 1.0)) + 0.5 * mach * mach])
+
+
+def taylor_green_box(seed=0, n_bg=256, n_fine=192, ratio=4, mach=0.1, re=1600.0, pr=0.72, pulse_amp=1e-3,
+                     pulse_width=4.0, order=3, hist_len=None, step_ratio=4, cfl=0.5, physics="ns"):
+    """3D Taylor-Green vortex on a periodic n_bg^3 background over [0, 2 pi)^3 with an overset
+    n_fine^3 box at 1/ratio of the background spacing centred at (pi, pi, pi) (interface on all
+    six faces), plus a Gaussian pressure pulse of relative amplitude pulse_amp and width
+    pulse_width fine spacings at the box centre jittered by the seed. Velocity
+    u = M sin x cos y cos z, v = -M cos x sin y cos z, w = 0; pressure
+    p = 1/gamma + M^2/16 (cos 2x + cos 2y)(cos 2z + 2); temperature T = gamma p / rho = 1."""
+    rng = np.random.default_rng(seed)
+    h = 2.0 * math.pi / n_bg
+    hf = h / ratio
+    bg = cartesian_mesh3d("background", (n_bg,) * 3, (0.0,) * 3, (h,) * 3, ("periodic",) * 6, (True,) * 3)
+    lo_f = math.pi - 0.5 * (n_fine - 1) * hf
+    fine = cartesian_mesh3d("fine", (n_fine,) * 3, (lo_f,) * 3, (hf,) * 3, ("interface",) * 6)
+    centre = np.full(3, math.pi) + rng.uniform(-1.0, 1.0, 3) * hf
+    qs = []
+    for m in (bg, fine):
+        x, y, z = axes3d(m)
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        u = mach * np.sin(X) * np.cos(Y) * np.cos(Z)
+        v = -mach * np.cos(X) * np.sin(Y) * np.cos(Z)
+        p = 1.0 / GAMMA + mach * mach / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+        r2 = (X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2
+        p = p * (1.0 + pulse_amp * np.exp(-r2 / (pulse_width * hf) ** 2))
+        rho = GAMMA * p
+        E = p / (GAMMA - 1.0) + 0.5 * rho * (u * u + v * v)
+        qs.append(np.stack([rho, rho * u, rho * v, np.zeros_like(rho), E]))
+        del X, Y, Z
+    params = dict(physics=physics, gamma=GAMMA, mu=(mach / re if physics == "ns" else 0.0), pr=pr, order=order,
+                  hist_len=hist_len or order, step_ratio=step_ratio, fast_mesh=1, cfl=cfl,
+                  qinf=freestream3d(0.0), twall=1.0, omega_corner=1.0)
+    return {"meshes": [bg, fine], "q0": qs, "params": params, "seed": seed}
+
+
+def taylor_green_small(seed=0, **kw):
+    """A scaled-down Taylor-Green box for parity tests: 24^3 background, 21^3 box at ratio 2."""
+    args = dict(n_bg=24, n_fine=21, ratio=2, step_ratio=2, pulse_width=2.0, mach=0.3, re=100.0)
+    args.update(kw)
+    return taylor_green_box(seed=seed, **args)
+
+
+def extrude_to_3d(wl, nk, lz, axis=2):
+    """A 2D Cartesian two-mesh workload extruded along a new periodic direction of nk points
+    over length lz: axis = 2 puts the 2D plane in (x, y) and extrudes along z; axis = 1 puts it
+    in (x, z) and extrudes along y. The velocity component along the new direction is 0."""
+    meshes, qs = [], []
+    for m, q in zip(wl["meshes"], wl["q0"]):
+        bc = list(m["bc"])
+        per = list(m["periodic"])
+        if axis == 2:
+            n = (m["n"][0], m["n"][1], nk)
+            lo = (m["lo"][0], m["lo"][1], 0.0)
+            h = (m["h"][0], m["h"][1], lz / nk)
+            bc3 = bc + ["periodic", "periodic"]
+            per3 = (per[0], per[1], True)
+            q3 = np.stack([q[0], q[1], q[2], np.zeros_like(q[0]), q[3]])
+            q3 = np.broadcast_to(q3[:, None], (5, nk) + q.shape[1:]).copy()
+        else:
+            n = (m["n"][0], nk, m["n"][1])
+            lo = (m["lo"][0], 0.0, m["lo"][1])
+            h = (m["h"][0], lz / nk, m["h"][1])
+            bc3 = bc[:2] + ["periodic", "periodic"] + bc[2:]
+            per3 = (per[0], True, per[1])
+            q3 = np.stack([q[0], q[1], np.zeros_like(q[0]), q[2], q[3]])
+            q3 = np.broadcast_to(q3[:, :, None, :], (5, q.shape[1], nk, q.shape[2])).copy()
+        meshes.append(cartesian_mesh3d(m["name"], n, lo, h, bc3, per3))
+        qs.append(q3)
+    p = dict(wl["params"])
+    qi = np.asarray(p["qinf"], dtype=np.float64)
+    p["qinf"] = (np.array([qi[0], qi[1], qi[2], 0.0, qi[3]]) if axis == 2
+                 else np.array([qi[0], qi[1], 0.0, qi[2], qi[3]]))
+    return {"meshes": meshes, "q0": qs, "params": p}
