@@ -79,7 +79,7 @@ typedef struct {
   double cfl;
   double qinf[4];
   int order, hist_len, step_ratio, fast_mesh;
-  int hole_cells;
+  double hole_cells;             /* hole margin in background spacings (<= 0: 4) */
 } sbp_params;
 
 typedef struct {
@@ -300,6 +300,63 @@ typedef struct {
 sbp_status sbp_adjoint_probe(sbp_system_t sys, const sbp_adjoint_desc *desc, const void *q0_mesh0,
                              const void *q0_mesh1, double *J, double *probe_p, void *dJ_dq0_mesh0,
                              void *dJ_dq0_mesh1, double *dJ_dqinf, long *forward_steps, void *stream);
+
+/* ---- 3D Cartesian systems ---------------------------------------------------------------------
+ * Two overset uniform Cartesian 3D meshes (mesh 0 = background, mesh 1 = the fine box): the
+ * compressible Navier-Stokes / Euler equations of App. C.1 in three directions,
+ * dq/dt = -(D_x (F - F^V) + D_y (G - G^V) + D_z (H - H^V)) + SAT with D_x = D_xi / hx etc.
+ * (SBP 4-2, Sec. 2.1), the interface and far-field SAT of Sec. 2.2 eq. (int) with the
+ * characteristic matrices of the 3D flux Jacobian, 4 x 4 x 4 donor-cell Lagrange
+ * interpolation (Sec. 2.2), and the same MRAB integrator (Sec. 3.1-3.3) as the 2D systems.
+ * q = (rho, rho u, rho v, rho w, rho E): nvar = 5 planes; variable v of point (i, j, k) sits at
+ * base[v * field_elems + (k * nj + j) * pitch + i]. Faces are ordered i-low, i-high, j-low,
+ * j-high, k-low, k-high; a periodic direction has SBP_BC_PERIODIC on both faces; the walls of
+ * the 2D systems are not offered in 3D. Hole cut: background points inside the fine box and
+ * more than hole_cells background spacings from each of its non-periodic faces. The sbp_params
+ * fields are read as for 2D systems (qinf takes its first four entries as (rho, rho u, rho v,
+ * rho E) with rho w = 0: use sbp3_set_freestream for a full 5-component state). */
+typedef struct sbp3_system_s *sbp3_system_t;
+typedef struct {
+  int n[3];
+  int periodic[3];
+  int bc[6];
+  double lo[3], h[3];
+} sbp3_mesh_desc;
+typedef struct {
+  int ni, nj, nk, pitch;
+  size_t field_elems;   /* pitch * nj * nk */
+  size_t state_bytes;   /* 5 planes */
+  int nvar, n_holes, n_receivers, n_sat_points, elem_size;
+} sbp3_mesh_info;
+
+sbp_status sbp3_system_create(const sbp3_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                              sbp3_system_t *out);
+sbp_status sbp3_system_destroy(sbp3_system_t sys);
+sbp_status sbp3_mesh_info_get(sbp3_system_t sys, int mesh, sbp3_mesh_info *info);
+/* qinf[5] (host): far-field state of the far-field SAT. */
+sbp_status sbp3_set_freestream(sbp3_system_t sys, const double *qinf);
+/* Setup tables (host, any pointer may be NULL): iblank ni*nj*nk bytes (1 active); receivers
+ * n_receivers linear indices (k*nj + j)*ni + i; donor_base 3 ints and donor_w 12 doubles
+ * (4 Lagrange weights along i, j, k) per receiver. */
+sbp_status sbp3_get_tables(sbp3_system_t sys, int mesh, signed char *iblank, long long *receivers, int *donor_base,
+                           double *donor_w);
+/* Interpolation to recv_mesh's receivers from the other mesh's state (device): qhat 5 x
+ * n_receivers, fvhat 12 x n_receivers (Cartesian viscous fluxes F^V_x, F^V_y, F^V_z, each
+ * momentum x, y, z and energy; NS only, may be NULL). */
+sbp_status sbp3_overset_interp(sbp3_system_t sys, int recv_mesh, const void *q_donor, void *qhat, void *fvhat,
+                               void *stream);
+/* Right-hand side of one mesh with its receivers fed from q_other; holes get 0. */
+sbp_status sbp3_rhs_eval(sbp3_system_t sys, int mesh, const void *q_self, const void *q_other, void *rhs,
+                         void *stream);
+/* Time step of Sec. 4.1 per mesh (without the CFL factor) and the macro step H (host). */
+sbp_status sbp3_timestep(sbp3_system_t sys, const void *q0, const void *q1, double *dt_mesh, double *H,
+                         void *stream);
+/* Integrator buffers, bootstrap and macro steps: as sbp_bind, sbp_mrab_init, sbp_mrab_step. */
+sbp_status sbp3_bind(sbp3_system_t sys, int mesh, void *q_a, void *q_b, void *hist);
+sbp_status sbp3_current_state(sbp3_system_t sys, int mesh, void **q);
+sbp_status sbp3_mrab_init(sbp3_system_t sys, double H, void *stream);
+sbp_status sbp3_mrab_step(sbp3_system_t sys, int n, void *stream);
+sbp_status sbp3_check(sbp3_system_t sys, void *stream);
 
 /* Synchronise the stream and report (then clear) the device error word. */
 sbp_status sbp_check(sbp_system_t sys, void *stream);

@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
                 ("omega_corner", ctypes.c_double), ("sigma_interface", ctypes.c_double),
                 ("sigma_physical", ctypes.c_double), ("cfl", ctypes.c_double), ("qinf", ctypes.c_double * 4),
                 ("order", ctypes.c_int), ("hist_len", ctypes.c_int), ("step_ratio", ctypes.c_int),
-                ("fast_mesh", ctypes.c_int), ("hole_cells", ctypes.c_int)]
+                ("fast_mesh", ctypes.c_int), ("hole_cells", ctypes.c_double)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -48,6 +48,18 @@ class MeshInfo(ctypes.Structure):
                 ("hist_bytes", ctypes.c_size_t), ("nvar", ctypes.c_int), ("n_holes", ctypes.c_int),
                 ("n_receivers", ctypes.c_int), ("n_sat_points", ctypes.c_int), ("elem_size", ctypes.c_int),
                 ("strip_width", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("single_pass", ctypes.c_int)]
+
+
+class Mesh3Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("periodic", ctypes.c_int * 3), ("bc", ctypes.c_int * 6),
+                ("lo", ctypes.c_double * 3), ("h", ctypes.c_double * 3)]
+
+
+class Mesh3Info(ctypes.Structure):
+    _fields_ = [("ni", ctypes.c_int), ("nj", ctypes.c_int), ("nk", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("field_elems", ctypes.c_size_t), ("state_bytes", ctypes.c_size_t), ("nvar", ctypes.c_int),
+                ("n_holes", ctypes.c_int), ("n_receivers", ctypes.c_int), ("n_sat_points", ctypes.c_int),
+                ("elem_size", ctypes.c_int)]
 
 
 class AdjointDesc(ctypes.Structure):
@@ -92,6 +104,21 @@ _SIGS.update({
     "sbp_rhs_eval_jvp": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
     "sbp_overset_interp_vjp": [_P, _I, _P, _P, _P, _P, _P],
     "sbp_adjoint_probe": [_P, ctypes.POINTER(AdjointDesc), _P, _P, _P, _P, _P, _P, _P, _P, _P],
+})
+_SIGS.update({
+    "sbp3_system_create": [ctypes.POINTER(Mesh3Desc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "sbp3_system_destroy": [_P],
+    "sbp3_mesh_info_get": [_P, _I, ctypes.POINTER(Mesh3Info)],
+    "sbp3_set_freestream": [_P, _P],
+    "sbp3_get_tables": [_P, _I, _P, _P, _P, _P],
+    "sbp3_overset_interp": [_P, _I, _P, _P, _P, _P],
+    "sbp3_rhs_eval": [_P, _I, _P, _P, _P, _P],
+    "sbp3_timestep": [_P, _P, _P, _P, _P, _P],
+    "sbp3_bind": [_P, _I, _P, _P, _P],
+    "sbp3_current_state": [_P, _I, ctypes.POINTER(_P)],
+    "sbp3_mrab_init": [_P, _D, _P],
+    "sbp3_mrab_step": [_P, _I, _P],
+    "sbp3_check": [_P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -379,6 +406,149 @@ class System:
         if grad:
             out.update({"dq0": g, "dqinf": np.array(gq[:])})
         return out
+
+
+class System3D:
+    """A two-mesh 3D Cartesian overset system (C ABI sbp3_*). ``wl`` is a 3D workload dict
+    (``workloads.taylor_green_box`` layout). States are numpy arrays (5, nk, nj, ni) or device
+    tensors (5, nk, nj, pitch)."""
+
+    def __init__(self, wl, dtype="f64", sigma_interface=0.5, sigma_physical=1.0, hole_cells=4):
+        import torch
+        self.torch = torch
+        self.dtype = dtype
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        self.meshes = wl["meshes"]
+        p = wl["params"]
+        descs = (Mesh3Desc * 2)()
+        for k, m in enumerate(self.meshes):
+            d = descs[k]
+            for a in range(3):
+                d.n[a] = m["n"][a]
+                d.periodic[a] = int(m["periodic"][a])
+                d.lo[a] = m["lo"][a]
+                d.h[a] = m["h"][a]
+            for f in range(6):
+                d.bc[f] = BC[m["bc"][f]]
+        pr = Params()
+        pr.physics = PHYSICS[p["physics"]]
+        pr.dtype = DTYPE[dtype]
+        pr.gamma = p["gamma"]
+        pr.mu = p["mu"]
+        pr.pr = p["pr"]
+        pr.twall = p["twall"]
+        pr.omega_corner = p["omega_corner"]
+        pr.sigma_interface = sigma_interface
+        pr.sigma_physical = sigma_physical
+        pr.cfl = p["cfl"]
+        qi = np.asarray(p["qinf"], dtype=np.float64)
+        for v, c in enumerate((0, 1, 2, 4)):
+            pr.qinf[v] = float(qi[c])
+        pr.order = p["order"]
+        pr.hist_len = p["hist_len"]
+        pr.step_ratio = p["step_ratio"]
+        pr.fast_mesh = p["fast_mesh"]
+        pr.hole_cells = hole_cells
+        self.params = p
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        _check(_lib.sbp3_system_create(descs, 2, ctypes.byref(pr), ctypes.byref(h)), "sbp3_system_create")
+        self.h = h
+        arr = (ctypes.c_double * 5)(*[float(v) for v in qi])
+        _check(_lib.sbp3_set_freestream(self.h, ctypes.cast(arr, ctypes.c_void_p)), "sbp3_set_freestream")
+        self.info = []
+        for k in range(2):
+            inf = Mesh3Info()
+            _check(_lib.sbp3_mesh_info_get(self.h, k, ctypes.byref(inf)), "sbp3_mesh_info_get")
+            self.info.append(inf)
+        self.bound = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp3_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_state(self, k, n=1):
+        inf = self.info[k]
+        t = self.torch.zeros((n, 5, inf.nk, inf.nj, inf.pitch), dtype=self.tdtype, device="cuda")
+        return t if n > 1 else t[0]
+
+    def to_device(self, k, q):
+        inf = self.info[k]
+        t = self.empty_state(k)
+        t[..., :inf.ni] = self.torch.from_numpy(np.ascontiguousarray(q)).to(self.tdtype).cuda()
+        return t
+
+    def to_host(self, k, t):
+        return t[..., :self.info[k].ni].double().cpu().numpy()
+
+    def tables(self, k):
+        inf = self.info[k]
+        n = inf.ni * inf.nj * inf.nk
+        nr = inf.n_receivers
+        ib = np.zeros(n, np.int8)
+        rec = np.zeros(max(nr, 1), np.int64)
+        base = np.zeros(max(3 * nr, 1), np.int32)
+        w = np.zeros(max(12 * nr, 1))
+        _check(_lib.sbp3_get_tables(self.h, k, ib.ctypes.data, rec.ctypes.data, base.ctypes.data, w.ctypes.data),
+               "sbp3_get_tables")
+        return {"iblank": ib.reshape(inf.nk, inf.nj, inf.ni), "receivers": rec[:nr],
+                "base": base[:3 * nr].reshape(nr, 3), "w": w[:12 * nr].reshape(nr, 12)}
+
+    def overset_interp(self, recv, q_donor, stream=None):
+        nr = self.info[recv].n_receivers
+        qhat = self.torch.zeros((5, max(nr, 1)), dtype=self.tdtype, device="cuda")
+        fvhat = self.torch.zeros((12, max(nr, 1)), dtype=self.tdtype, device="cuda")
+        if nr:
+            qhat, fvhat = qhat[:, :nr].contiguous(), fvhat[:, :nr].contiguous()
+        _check(_lib.sbp3_overset_interp(self.h, recv, _ptr(q_donor), _ptr(qhat), _ptr(fvhat), _stream(stream)),
+               "sbp3_overset_interp")
+        return qhat[:, :nr], fvhat[:, :nr]
+
+    def rhs_eval(self, k, q_self, q_other, out=None, stream=None):
+        if out is None:
+            out = self.empty_state(k)
+        _check(_lib.sbp3_rhs_eval(self.h, k, _ptr(q_self), _ptr(q_other), _ptr(out), _stream(stream)),
+               "sbp3_rhs_eval")
+        return out
+
+    def timestep(self, q0, q1, stream=None):
+        dt = (ctypes.c_double * 2)()
+        H = ctypes.c_double()
+        _check(_lib.sbp3_timestep(self.h, _ptr(q0), _ptr(q1), ctypes.cast(dt, ctypes.c_void_p),
+                                  ctypes.cast(ctypes.pointer(H), ctypes.c_void_p), _stream(stream)), "sbp3_timestep")
+        return [dt[0], dt[1]], H.value
+
+    def bind(self, q_host):
+        self.bound = []
+        for k in range(2):
+            qa = self.to_device(k, q_host[k])
+            qb = self.empty_state(k)
+            hist = self.empty_state(k, n=self.params["hist_len"]) if self.params["hist_len"] > 1 else \
+                self.empty_state(k)[None]
+            _check(_lib.sbp3_bind(self.h, k, _ptr(qa), _ptr(qb), _ptr(hist)), "sbp3_bind")
+            self.bound.append((qa, qb, hist))
+
+    def current_state(self, k):
+        p = ctypes.c_void_p()
+        _check(_lib.sbp3_current_state(self.h, k, ctypes.byref(p)), "sbp3_current_state")
+        qa, qb, _ = self.bound[k]
+        return qa if p.value == qa.data_ptr() else qb
+
+    def mrab_init(self, H=0.0, stream=None):
+        _check(_lib.sbp3_mrab_init(self.h, float(H), _stream(stream)), "sbp3_mrab_init")
+
+    def mrab_step(self, n=1, stream=None):
+        _check(_lib.sbp3_mrab_step(self.h, int(n), _stream(stream)), "sbp3_mrab_step")
+
+    def check(self, stream=None):
+        _check(_lib.sbp3_check(self.h, _stream(stream)), "sbp3_check")
 
 
 class Batch:

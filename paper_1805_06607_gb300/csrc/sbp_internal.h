@@ -72,5 +72,38 @@ sbp_status setup_donors(MeshHost &recv, const MeshHost &donor, std::string &err)
 sbp_status solve_ab_weights(const std::vector<double> &nodes, double a, double b, int order,
                             std::vector<double> &alpha);
 sbp_status build_plan(int order, int m, int sr, CoeffPlan &plan, std::string &err);
+// Maximal runs of active points (a[off + st * k] != 0) on a line of n points: (start, length).
+std::vector<std::pair<int, int>> active_runs(const std::vector<int8_t> &a, size_t off, size_t st, int n, bool per);
+
+// ---------------------------------------------------------------------------------------------
+// 3D Cartesian meshes (sbp3_setup.cpp). Points (i, j, k) have the linear index
+// (k * nj + j) * ni + i on the host; class codes are 4 bits per direction (i, j, k) in a 16-bit
+// word, 0xFFF for a hole. SAT codes: term count in bits 0-1, then per term 4 bits from bit 2:
+// direction (2 bits), side (1 bit: 0 low face "+", 1 high face "-"), kind (1 bit: 0 interface,
+// 1 far field).
+constexpr int kNvar3 = 5;
+struct Mesh3Host {
+  int n[3] = {0, 0, 0}, pitch = 0;
+  int per[3] = {0, 0, 0};
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  double lo[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+  std::vector<int8_t> active;
+  std::vector<uint16_t> cls;
+  std::vector<int64_t> sat_pt;
+  std::vector<uint32_t> sat_code;
+  std::vector<int> sat_recv;
+  std::vector<double> sat_scale;
+  std::vector<int64_t> recv_pt;
+  std::vector<int> donor_base;       // 3 per receiver
+  std::vector<double> donor_w;       // 12 per receiver (i, j, k)
+  std::vector<int64_t> donor_pts;    // distinct donor points (linear index on the donor mesh)
+  std::vector<int> donor_idx;        // 64 per receiver: (c * 4 + b) * 4 + a -> index in donor_pts
+  size_t points() const { return (size_t)n[0] * n[1] * n[2]; }
+};
+sbp_status setup3_mesh(const sbp3_mesh_desc &d, Mesh3Host &m, std::string &err);
+sbp_status setup3_holes(Mesh3Host &bg, const Mesh3Host &fine, double margin, std::string &err);
+sbp_status setup3_classes(Mesh3Host &m, std::string &err);
+sbp_status setup3_sat(Mesh3Host &m, double omega_corner, std::string &err);
+sbp_status setup3_donors(Mesh3Host &rm, const Mesh3Host &d, std::string &err);
 
 }  // namespace sbp

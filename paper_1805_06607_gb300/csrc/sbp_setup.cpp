@@ -135,9 +135,8 @@ sbp_status setup_holes(MeshHost &bg, const MeshHost &fine, double margin, std::s
 // ---------------------------------------------------------------------------------------------
 // SBP segments: every maximal run of active points on a line carries the boundary closures at
 // both ends; runs shorter than 8 points become holes (repeated to a fixed point).
-namespace {
 // Runs of active points on one line; returns (start, length) pairs, start in [0, n).
-std::vector<std::pair<int, int>> runs(const std::vector<int8_t> &a, size_t off, size_t st, int n, bool per) {
+std::vector<std::pair<int, int>> active_runs(const std::vector<int8_t> &a, size_t off, size_t st, int n, bool per) {
   std::vector<std::pair<int, int>> out;
   int first_hole = -1;
   for (int k = 0; k < n; ++k)
@@ -169,6 +168,9 @@ std::vector<std::pair<int, int>> runs(const std::vector<int8_t> &a, size_t off, 
   }
   return out;
 }
+
+namespace {
+auto runs = active_runs;
 }  // namespace
 
 sbp_status setup_classes(MeshHost &m, std::string &err) {
