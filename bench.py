@@ -48,6 +48,9 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-system batched workload")
     ap.add_argument("--no-rate-compare", action="store_true", help="skip MRAB vs single-rate at equal error")
+    ap.add_argument("--no-large", action="store_true", help="skip rhs_eval on meshes larger than L2")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D Taylor-Green workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     return ap.parse_args()
 
 
@@ -392,6 +395,208 @@ def _mrab_vs_single_rate(name, wl, k_slow, exact=None, ref_factor=8):
                       "of each ring phase include its capture), FP64"}
 
 
+def _rhs_eval_large(hbm_peak, peak_kind, reps=10):
+    """sbp_rhs_eval alone on meshes larger than L2 (SURVEY's K2 on enlarged workloads): the
+    cylinder at 4x resolution (Navier-Stokes; O-grid 2048 x 512, background 4096 x 2048) and
+    the vortex pair at 32x resolution (Euler; background 2048^2, patch 821^2), FP32 and FP64,
+    kernel shape from the autotuner. Algorithmic bytes per point: state in + right-hand side out
+    (+ 5 metric planes on curvilinear meshes); L2 flushed before every evaluation."""
+    import torch
+    import paper_1805_06607_gb300 as sbp
+    import workloads as W
+
+    cases = {
+        "cylinder_4x_ns": lambda: W.cylinder_overset(seed=0, n_theta=2048, n_r=512, s_bg=0.0125, bg_n=(4096, 2048),
+                                                    bg_lo=(-12.8, -12.8), stretch=1.05 ** 0.25),
+        "vortex_32x_euler": lambda: W.vortex_box_in_box(seed=0, n_bg=2048, n_fine=821),
+    }
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, mk in cases.items():
+        wl = mk()
+        for dtype in ("f32", "f64"):
+            g = sbp.System(wl, dtype=dtype)
+            g.bind(wl["q0"])
+            g.mrab_init()
+            q = [g.current_state(k) for k in range(2)]
+            res = {}
+            for k, mesh in enumerate(("background", "fine")):
+                inf = g.mesh_info(k)
+                rhs = g.empty_state(k)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+                g.rhs_eval(k, q[k], q[1 - k], rhs)
+                for r in range(reps):
+                    flush.zero_()
+                    ev[r][0].record(stream)
+                    g.rhs_eval(k, q[k], q[1 - k], rhs)
+                    ev[r][1].record(stream)
+                torch.cuda.synchronize()
+                ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+                pts = inf.ni * inf.nj
+                es = inf.elem_size
+                bpp = es * (8 + (0 if wl["meshes"][k]["cartesian"] else 5))
+                gbs = pts * bpp / (ms / 1e3) / 1e9
+                res[mesh] = {"points": pts, "ms": ms, "gpts_per_s": pts / (ms / 1e3) / 1e9, "bytes_per_point": bpp,
+                             "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                             "kernel": ("single pass, 64-column strips, %d-row chunks" % inf.rows_per_cta
+                                        if inf.single_pass else "flux + derivative pair, %d rows" % inf.rows_per_cta)}
+            g.check()
+            g.close()
+            out["%s_%s" % (name, dtype)] = res
+    out["peak"] = {"hbm_gbs": hbm_peak, "kind": peak_kind}
+    return out
+
+
+def _run_3d(steps, warmup, hbm_peak, peak_kind):
+    """The 3D workload: Taylor-Green vortex on a periodic 256^3 background with an overset 192^3
+    box at 1/4 spacing (Re 1600, Mach 0.1, Gaussian pressure pulse in the box), MRAB order 3,
+    step ratio 4; FP32 states with FP64 update arithmetic, and FP64. Per macro step: 256^3 + 4 x
+    192^3 point evaluations. Also sbp3_rhs_eval of the background alone against the HBM
+    roofline (state in + right-hand side out: 40 B/pt FP32, 80 B/pt FP64), and the FP32 run's
+    relative L2 distance from the FP64 run after the timed steps."""
+    import numpy as np
+    import torch
+    import paper_1805_06607_gb300 as sbp
+    import workloads as W
+
+    t0 = time.perf_counter()
+    wl = W.taylor_green_box(seed=0)
+    gen_s = time.perf_counter() - t0
+    nb = int(np.prod(wl["meshes"][0]["n"]))
+    nf = int(np.prod(wl["meshes"][1]["n"]))
+    sr = wl["params"]["step_ratio"]
+    evals = nb + sr * nf
+    stream = torch.cuda.current_stream()
+    out = {"workload": "3D Taylor-Green: periodic 256^3 + overset 192^3 box at 1/4 spacing, MRAB order 3, "
+                       "step ratio 4", "points": nb + nf, "evals_per_step": evals, "input_generation_s": gen_s}
+    finals = {}
+    H = None
+    for dtype in ("f32", "f64"):
+        t0 = time.perf_counter()
+        g = sbp.System3D(wl, dtype=dtype)
+        g.bind(wl["q0"])
+        if H is None:
+            _, H = g.timestep(g.current_state(0), g.current_state(1))
+        g.mrab_init(H)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        for _ in range(warmup):
+            g.mrab_step(1)
+        g.check()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            ev[k][0].record(stream)
+            g.mrab_step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        g.check()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        finals[dtype] = [g.to_host(k, g.current_state(k)) for k in range(2)]
+        # right-hand side of the background alone
+        q = g.current_state(0)
+        rhs = g.empty_state(0)
+        g.rhs_eval(0, q, g.current_state(1), rhs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            g.rhs_eval(0, q, g.current_state(1), rhs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rms = e0.elapsed_time(e1) / 5
+        es = 4 if dtype == "f32" else 8
+        gbs = nb * 10 * es / (rms / 1e3) / 1e9
+        out[dtype] = {"ms_per_step": ms, "value": evals / (ms / 1e3), "unit": "point-evals/s",
+                      "setup_and_bootstrap_s": setup_s,
+                      "rhs_eval_background": {"ms": rms, "gpts_per_s": nb / (rms / 1e3) / 1e9,
+                                              "bytes_per_point": 10 * es, "achieved_gbs": gbs,
+                                              "hbm_frac": gbs / hbm_peak, "peak_kind": peak_kind}}
+        g.close()
+        torch.cuda.empty_cache()
+    num = sum(float(np.sum((finals["f32"][k] - finals["f64"][k]) ** 2)) for k in range(2))
+    den = sum(float(np.sum(finals["f64"][k] ** 2)) for k in range(2))
+    out["fp32_vs_fp64_rel_l2"] = (num / den) ** 0.5
+    out["fp32_vs_fp64_after"] = "bootstrap + %d macro steps" % (warmup + steps)
+    return out
+
+
+def _run_adjoint(n_steps=500, n_snapshots=40):
+    """The adjoint workload: the cylinder at half resolution (O-grid 256 x 64, background
+    512 x 256), MRAB order 3, step ratio 4, FP64; objective J = H sum_n sum_p p_p(t_n)^2 over
+    n_steps macro steps at 8 wake probes; gradient w.r.t. the initial states and the far-field
+    Mach number by the library's checkpointed reverse sweep (n_snapshots snapshots), checked
+    against one central difference (h = 1e-6) along a seeded direction of the initial states and
+    one in the Mach number."""
+    import numpy as np
+    import torch
+    import paper_1805_06607_gb300 as sbp
+    from paper_1805_06607_gb300.adjoint import freestream_state
+    import workloads as W
+
+    wl = W.cylinder_adjoint(seed=0)
+    g = sbp.System(wl, dtype="f64")
+    q0 = [g.to_device(k, wl["q0"][k]) for k in range(2)]
+    _, H = g.timestep(q0[0], q0[1])
+    probes = wl["probes"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fwd = g.adjoint_probe(q0, probes, n_steps, H, grad=False)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = g.adjoint_probe(q0, probes, n_steps, H, n_snapshots=n_snapshots)
+    t_grad = time.perf_counter() - t0
+    rng = np.random.default_rng(1)
+    dirs = [g.to_device(k, rng.standard_normal(np.shape(wl["q0"][k]))) for k in range(2)]
+    h = 1e-6
+    jp = g.adjoint_probe([q0[k] + h * dirs[k] for k in range(2)], probes, n_steps, H, grad=False)["J"]
+    jm = g.adjoint_probe([q0[k] - h * dirs[k] for k in range(2)], probes, n_steps, H, grad=False)["J"]
+    fd = (jp - jm) / (2 * h)
+    ad = sum(float((r["dq0"][k] * dirs[k]).sum()) for k in range(2))
+    # Mach number: through the far-field state alone (initial states fixed), and through the
+    # far-field state and the inflow part of the initial states together (q0 = free stream at M
+    # plus the fixed seeded perturbation: dq0/dM = (0, 1, 0, M) at every point)
+    gam = wl["params"]["gamma"]
+    mach = float(wl["params"]["qinf"][1])
+    dq_dm = np.array([0.0, 1.0, 0.0, mach])
+    ad_far = float(r["dqinf"] @ dq_dm)
+    ad_ic = sum(float((r["dq0"][k][:, :, :g.info[k].ni].sum(dim=(1, 2)).cpu().numpy()) @ dq_dm) for k in range(2))
+    js_far, js_tot = [], []
+    base = freestream_state(mach, gam).numpy()
+    for mm in (mach + h, mach - h):
+        qi = freestream_state(mm, gam).numpy()
+        g.set_freestream(qi)
+        js_far.append(g.adjoint_probe(q0, probes, n_steps, H, grad=False)["J"])
+        shift = torch.tensor(qi - base, dtype=torch.float64, device="cuda")
+        q0m = []
+        for k in range(2):
+            t = q0[k].clone()
+            t[:, :, :g.info[k].ni] += shift[:, None, None]
+            q0m.append(t)
+        js_tot.append(g.adjoint_probe(q0m, probes, n_steps, H, grad=False)["J"])
+    g.set_freestream(np.asarray(wl["params"]["qinf"], dtype=np.float64))
+    fd_far = (js_far[0] - js_far[1]) / (2 * h)
+    fd_tot = (js_tot[0] - js_tot[1]) / (2 * h)
+    g.close()
+
+    # rounding of J (summed in FP64) bounds what a central difference can resolve
+    fd_noise = 4.0 * np.finfo(np.float64).eps * abs(r["J"]) / h
+
+    def cmp(a, f):
+        return {"adjoint": a, "central_difference": f, "abs_diff": abs(a - f),
+                "rel_diff": abs(a - f) / abs(f) if f != 0.0 else None,
+                "within_1e-6_or_fd_rounding": bool(abs(a - f) <= max(1e-6 * abs(f), fd_noise))}
+    return {"workload": "cylinder O-grid 256x64 + background 512x256, MRAB order 3, step ratio 4, FP64, 8 wake probes",
+            "macro_steps": n_steps, "snapshots": n_snapshots, "H": H, "J": r["J"],
+            "forward_s": t_fwd, "gradient_s": t_grad, "gradient_over_forward": t_grad / t_fwd,
+            "forward_steps_with_recompute": r["forward_steps"],
+            "fd_q0": cmp(ad, fd),
+            "fd_mach_far_field_only": cmp(ad_far, fd_far),
+            "fd_mach_far_field_and_initial_state": cmp(ad_far + ad_ic, fd_tot),
+            "fd_step": h, "fd_rounding_bound": fd_noise,
+            "note": "the far field lies 9+ diameters from the probes: over this horizon J does not depend on "
+                    "the far-field state alone"}
+
+
 def _cpu_baseline(wl, seconds):
     """The oracle, as it stands, on the host: whole MRAB macro steps of the same workload."""
     import numpy as np
@@ -497,6 +702,12 @@ def main():
                                     "roofline": _roofline(r2, wl, other, hbm_peak, peak_kind),
                                     "autotuned_blocks": r2["tuning"],
                                     "phases_ms_per_step": {p: v[0] / args.steps for p, v in r2["prof"].items()}}}
+    if not args.no_adjoint and rank == 0:
+        line["adjoint"] = _run_adjoint()
+    if not args.no_3d and rank == 0:
+        line["taylor_green_3d"] = _run_3d(min(args.steps, 10), 2, hbm_peak, peak_kind)
+    if not args.no_large and rank == 0:
+        line["rhs_eval_large"] = _rhs_eval_large(hbm_peak, peak_kind)
     if not args.no_rate_compare and rank == 0:
         import workloads as W2
         c1 = W2.vortex_box_in_box(seed=0)
