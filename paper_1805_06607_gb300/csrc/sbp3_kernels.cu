@@ -194,8 +194,10 @@ __global__ void __launch_bounds__(256) k3_flux(const Rhs3Launch a) {
   }
 }
 
+// One thread per SAT point, launched in 32-thread blocks so that the few hundred points of a
+// background spread over the SMs.
 template <typename T, bool VISC>
-__global__ void __launch_bounds__(128) k3_sat(const Rhs3Launch a) {
+__global__ void __launch_bounds__(32) k3_sat(const Rhs3Launch a) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nsat) return;
   const Dev3Mesh &m = a.m;
@@ -204,11 +206,6 @@ __global__ void __launch_bounds__(128) k3_sat(const Rhs3Launch a) {
   const int i = (int)(pl % m.ni), j = (int)((pl / m.ni) % m.nj), k = (int)(pl / ((int64_t)m.ni * m.nj));
   const size_t p = pidx3(m, i, j, k);
   const T *q = static_cast<const T *>(a.q);
-  T qp[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) qp[v] = q[v * m.field + p];
-  T Fv[3][4] = {};
-  if (VISC) visc3_at(m, kk, static_cast<const T *>(a.prim), i, j, k, Fv);
   constexpr int NRV = VISC ? kRv3 : 5;
   T rv[NRV];
 #pragma unroll
@@ -217,15 +214,19 @@ __global__ void __launch_bounds__(128) k3_sat(const Rhs3Launch a) {
   if (recv >= 0) {
     const T *dv = static_cast<const T *>(a.dv);
     const T *w = static_cast<const T *>(a.dwt) + 12 * recv;
-    for (int c3 = 0; c3 < 4; ++c3)
-      for (int b = 0; b < 4; ++b)
-        for (int e = 0; e < 4; ++e) {
-          const T wt = w[e] * w[4 + b] * w[8 + c3];
-          const int d = a.didx[64 * recv + (c3 * 4 + b) * 4 + e];
+    for (int t = 0; t < 64; ++t) {  // donor point (c3 * 4 + b) * 4 + e
+      const int e = t & 3, b = (t >> 2) & 3, c3 = t >> 4;
+      const T wt = w[e] * w[4 + b] * w[8 + c3];
+      const int d = a.didx[64 * recv + t];
 #pragma unroll
-          for (int c = 0; c < NRV; ++c) rv[c] += wt * dv[c * a.ndv + d];
-        }
+      for (int c = 0; c < NRV; ++c) rv[c] += wt * dv[c * a.ndv + d];
+    }
   }
+  T qp[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qp[v] = q[v * m.field + p];
+  T Fv[3][4] = {};
+  if (VISC) visc3_at(m, kk, static_cast<const T *>(a.prim), i, j, k, Fv);
   const uint32_t code = a.sat_code[s];
   const int nt = code & 3u;
   T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -448,8 +449,9 @@ static cudaError_t launch3_rhs_t(const Rhs3Launch &a, cudaStream_t s) {
   if (a.visc) k3_flux<T, true><<<grid, blk, 0, s>>>(a);
   else k3_flux<T, false><<<grid, blk, 0, s>>>(a);
   if (a.nsat > 0) {
-    if (a.visc) k3_sat<T, true><<<(a.nsat + 127) / 128, 128, 0, s>>>(a);
-    else k3_sat<T, false><<<(a.nsat + 127) / 128, 128, 0, s>>>(a);
+    const int blocks = (a.nsat + 31) / 32;
+    if (a.visc) k3_sat<T, true><<<blocks, 32, 0, s>>>(a);
+    else k3_sat<T, false><<<blocks, 32, 0, s>>>(a);
   }
   k3_update<T><<<grid, blk, 0, s>>>(a);
   return cudaGetLastError();

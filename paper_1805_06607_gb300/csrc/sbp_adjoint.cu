@@ -357,61 +357,70 @@ __global__ void k_adj_point(const AdjLaunch a) {
   }
 }
 
+// SAT adjoint in two passes: one thread per (SAT point, input) evaluates the dual-number
+// derivative of the point's SAT terms along that input (inputs: q 4, g 6, rv 10, qinf 4) and
+// stores lam . dSAT/d(input); then one thread per SAT point applies the 24 values.
 template <bool VISC, bool CURV>
 __global__ void k_adj_sat(const AdjLaunch a) {
   const DevMesh &m = a.m;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.nsat; s += gridDim.x * blockDim.x) {
-    uint32_t ij = a.sat_ij[s];
-    int i = (int)(ij & 0xFFFFu), j = (int)(ij >> 16);
-    size_t p = (size_t)j * m.pitch + i;
-    double mt[5];
-    metrics_at(m, p, mt);
-    double q[4] = {a.q[p], a.q[m.field + p], a.q[2 * m.field + p], a.q[3 * m.field + p]};
-    double g[6] = {0, 0, 0, 0, 0, 0};
-    if (VISC) grads_at(m, a.q, a.k.gam, i, j, g);
-    int recv = a.sat_recv[s];
-    double rv[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (recv >= 0)
-      for (int c = 0; c < 10; ++c) rv[c] = a.rv[(size_t)c * a.nrecv + recv];
-    double lam[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) lam[c] = a.lam[c * m.field + p];
-    uint32_t code = a.sat_code[s];
-    double scale = a.sat_scale[s];
-    // inputs: q (4), g (6), rv (10), qinf (4)
-    double lin[24];
-    for (int in = 0; in < 24; ++in) {
-      lin[in] = 0.0;
-      if (!VISC && in >= 4 && in < 10) continue;
-      if (recv < 0 && in >= 10 && in < 20) continue;
-      Dd qd[4], gd[6], rd[10], fd[4], out[4];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) qd[b] = Dd(q[b], in == b ? 1.0 : 0.0);
-#pragma unroll
-      for (int b = 0; b < 6; ++b) gd[b] = Dd(g[b], in == 4 + b ? 1.0 : 0.0);
-#pragma unroll
-      for (int b = 0; b < 10; ++b) rd[b] = Dd(rv[b], in == 10 + b ? 1.0 : 0.0);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) fd[b] = Dd(a.k.qinf[b], in == 20 + b ? 1.0 : 0.0);
-      sat_of<Dd, VISC>(a.k, mt, code, scale, qd, gd, rd, fd, out);
-      double acc = 0.0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc += out[c].d * lam[c];
-      lin[in] = acc;
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) a.lq[c * m.field + p] += lin[c];
-    if (VISC) {
-      double ldp[6];
-      chain_adjoint(mt, !CURV, lin + 4, ldp);
-#pragma unroll
-      for (int b = 0; b < 6; ++b) a.ld[b * m.field + p] += ldp[b];
-    }
-    if (recv >= 0)
-      for (int c = 0; c < 10; ++c) a.lrv[(size_t)c * a.nrecv + recv] = lin[10 + c];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) a.lqinf[(size_t)4 * s + c] = lin[20 + c];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 24 * a.nsat) return;
+  const int s = t / 24, in = t - 24 * s;
+  const int recv = a.sat_recv[s];
+  if ((!VISC && in >= 4 && in < 10) || (recv < 0 && in >= 10 && in < 20)) {
+    a.satlin[t] = 0.0;
+    return;
   }
+  uint32_t ij = a.sat_ij[s];
+  int i = (int)(ij & 0xFFFFu), j = (int)(ij >> 16);
+  size_t p = (size_t)j * m.pitch + i;
+  double mt[5];
+  metrics_at(m, p, mt);
+  double q[4] = {a.q[p], a.q[m.field + p], a.q[2 * m.field + p], a.q[3 * m.field + p]};
+  double g[6] = {0, 0, 0, 0, 0, 0};
+  if (VISC) grads_at(m, a.q, a.k.gam, i, j, g);
+  double rv[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (recv >= 0)
+    for (int c = 0; c < 10; ++c) rv[c] = a.rv[(size_t)c * a.nrecv + recv];
+  Dd qd[4], gd[6], rd[10], fd[4], out[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) qd[b] = Dd(q[b], in == b ? 1.0 : 0.0);
+#pragma unroll
+  for (int b = 0; b < 6; ++b) gd[b] = Dd(g[b], in == 4 + b ? 1.0 : 0.0);
+#pragma unroll
+  for (int b = 0; b < 10; ++b) rd[b] = Dd(rv[b], in == 10 + b ? 1.0 : 0.0);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) fd[b] = Dd(a.k.qinf[b], in == 20 + b ? 1.0 : 0.0);
+  sat_of<Dd, VISC>(a.k, mt, a.sat_code[s], a.sat_scale[s], qd, gd, rd, fd, out);
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc += out[c].d * a.lam[c * m.field + p];
+  a.satlin[t] = acc;
+}
+
+template <bool CURV>
+__global__ void k_adj_sat_apply(const AdjLaunch a) {
+  const DevMesh &m = a.m;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nsat) return;
+  const double *lin = a.satlin + 24 * (size_t)s;
+  uint32_t ij = a.sat_ij[s];
+  int i = (int)(ij & 0xFFFFu), j = (int)(ij >> 16);
+  size_t p = (size_t)j * m.pitch + i;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) a.lq[c * m.field + p] += lin[c];
+  if (a.viscous) {
+    double mt[5], ldp[6];
+    metrics_at(m, p, mt);
+    chain_adjoint(mt, !CURV, lin + 4, ldp);
+#pragma unroll
+    for (int b = 0; b < 6; ++b) a.ld[b * m.field + p] += ldp[b];
+  }
+  const int recv = a.sat_recv[s];
+  if (recv >= 0)
+    for (int c = 0; c < 10; ++c) a.lrv[(size_t)c * a.nrecv + recv] = lin[10 + c];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) a.lqinf[(size_t)4 * s + c] = lin[20 + c];
 }
 
 // lp (3 planes) = D_xi^T ld(xi) + D_eta^T ld(eta) for u, v, T.
@@ -459,7 +468,7 @@ cudaError_t launch_rhs_adjoint(const AdjLaunch &a, cudaStream_t s) {
     else k_adj_point<false, false><<<blocks, 128, 0, s>>>(a);
   }
   if (a.nsat > 0) {
-    int sb = (a.nsat + 63) / 64;
+    int sb = (24 * a.nsat + 63) / 64;
     if (a.viscous) {
       if (curv) k_adj_sat<true, true><<<sb, 64, 0, s>>>(a);
       else k_adj_sat<true, false><<<sb, 64, 0, s>>>(a);
@@ -467,6 +476,9 @@ cudaError_t launch_rhs_adjoint(const AdjLaunch &a, cudaStream_t s) {
       if (curv) k_adj_sat<false, true><<<sb, 64, 0, s>>>(a);
       else k_adj_sat<false, false><<<sb, 64, 0, s>>>(a);
     }
+    int ab = (a.nsat + 63) / 64;
+    if (curv) k_adj_sat_apply<true><<<ab, 64, 0, s>>>(a);
+    else k_adj_sat_apply<false><<<ab, 64, 0, s>>>(a);
   }
   if (a.viscous) {
     k_adj_dT<<<blocks, 128, 0, s>>>(a.m, a.ld, a.lp);

@@ -35,6 +35,7 @@ cudaError_t ensure_ws(sbp_system_s *S) {
     if (e == cudaSuccess) e = adj_alloc(S, &w.rv, 10 * nr);
     if (e == cudaSuccess) e = adj_alloc(S, &w.lrv, 10 * nr);
     if (e == cudaSuccess) e = adj_alloc(S, &w.lqinf, 4 * ns);
+    if (e == cudaSuccess) e = adj_alloc(S, &w.satlin, 24 * ns);
     if (e == cudaSuccess) e = adj_alloc(S, &w.ldv, 10 * m.donor_pts.size());
     const int nd = (int)m.donor_pts.size();
     std::vector<int> off(nd + 1, 0), ent(m.donor_idx.size());
@@ -122,6 +123,7 @@ cudaError_t rhs_vjp(sbp_system_s *S, int k, const double *q_self, const double *
   a.nrecv = (int)m.recv_pt.size();
   a.lrv = w.lrv;
   a.lqinf = w.lqinf;
+  a.satlin = w.satlin;
   if ((e = launch_rhs_adjoint(a, s)) != cudaSuccess) return e;
   if ((e = launch_sum4(w.lqinf, a.nsat, S->d_qinf_acc, s)) != cudaSuccess) return e;
   if (a.nrecv > 0 && lq_other) e = interp_vjp(S, k, q_other, lq_other, s);

@@ -150,6 +150,7 @@ struct AdjLaunch {
   int nrecv;
   double *lrv;
   double *lqinf;
+  double *satlin;    // scratch: 24 per SAT point
 };
 // Adjoint of the receiver values back to the donor mesh: per distinct donor point d,
 // ldv(d) = sum over (receiver, stencil slot) using d of w lrv (inverse lists inv_off/inv_re,

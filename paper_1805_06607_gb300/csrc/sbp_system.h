@@ -101,7 +101,7 @@ struct sbp_system_s {
   // receiver), far-field adjoint per SAT point (4), donor-point adjoint ldv (10 per point)
   struct AdjWs {
     double *mu = nullptr, *ld = nullptr, *lp = nullptr, *rv = nullptr, *lrv = nullptr, *lqinf = nullptr,
-           *ldv = nullptr;
+           *ldv = nullptr, *satlin = nullptr;
   } aws[2];
   double *d_qinf_acc = nullptr;  // 4 doubles: accumulated far-field adjoint
   bool aws_ready = false;
