@@ -253,61 +253,50 @@ __device__ __forceinline__ void chain_adjoint(const double mt[5], bool cart, con
   }
 }
 
-// Transposed stencil along one direction: sum over the points j within reach 3 of i of the
-// coefficient that j's derivative row gives to i, times x(j).
-__device__ __forceinline__ double dT_at(const DevMesh &m, const double *x, int i, int j, int dir) {
-  double acc = 0.0;
+// Transposed stencil: the coefficient that the derivative row (direction dir) of the point at
+// offset o from (i, j) gives to (i, j), and that point's index pj (0 when out of the mesh or when
+// its row does not reach (i, j)). A non-zero tap has a unique offset, so at most one matches.
+__device__ __forceinline__ double tcoef(const DevMesh &m, int i, int j, int dir, int o, size_t &pj) {
   const int n = dir == 0 ? m.ni : m.nj;
   const int per = dir == 0 ? m.per_i : m.per_j;
-  const int c0 = dir == 0 ? i : j;
-  for (int o = -3; o <= 3; ++o) {
-    int c = c0 + o;
-    if (!wrap_index(c, n, per)) continue;
-    size_t pj = dir == 0 ? (size_t)j * m.pitch + c : (size_t)c * m.pitch + i;
-    unsigned code = m.cls[pj];
-    code = dir == 0 ? (code & 15u) : (code >> 4);
-    int row, sgn;
-    row_of(code, row, sgn);
+  int c = (dir == 0 ? i : j) + o;
+  if (!wrap_index(c, n, per)) return 0.0;
+  pj = dir == 0 ? (size_t)j * m.pitch + c : (size_t)c * m.pitch + i;
+  unsigned code = m.cls[pj];
+  code = dir == 0 ? (code & 15u) : (code >> 4);
+  int row, sgn;
+  row_of(code, row, sgn);
+  double cf = 0.0;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      double we = c_w64[row][e];
-      if (we != 0.0 && sgn * c_off[row][e] == -o) acc += sgn * we * x[pj];
-    }
+  for (int e = 0; e < 4; ++e) {
+    const double we = c_w64[row][e];
+    if (we != 0.0 && sgn * c_off[row][e] == -o) cf = sgn * we;
   }
-  return acc;
+  return cf;
 }
 
-// mu = -D^T (J lam): 8 planes (xi: 4 variables, eta: 4 variables).
+// mu = -D^T (J lam): 8 planes (xi: 4 variables, eta: 4 variables); each neighbour's row is
+// decoded once for all variables.
 __global__ void k_adj_mu(const AdjLaunch a) {
   const DevMesh &m = a.m;
   size_t n = (size_t)m.ni * m.nj;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     int i = (int)(t % m.ni), j = (int)(t / m.ni);
     size_t p = (size_t)j * m.pitch + i;
-    for (int dir = 0; dir < 2; ++dir)
-      for (int c = 0; c < 4; ++c) {
-        // x(j) = J_j lam_c(j): the stencil gather reads it at the neighbours
-        double acc = 0.0;
-        const int nn = dir == 0 ? m.ni : m.nj;
-        const int per = dir == 0 ? m.per_i : m.per_j;
-        const int c0 = dir == 0 ? i : j;
-        for (int o = -3; o <= 3; ++o) {
-          int cc = c0 + o;
-          if (!wrap_index(cc, nn, per)) continue;
-          size_t pj = dir == 0 ? (size_t)j * m.pitch + cc : (size_t)cc * m.pitch + i;
-          unsigned code = m.cls[pj];
-          code = dir == 0 ? (code & 15u) : (code >> 4);
-          int row, sgn;
-          row_of(code, row, sgn);
-          double jac = m.cart ? m.mc[4] : static_cast<const double *>(m.met)[4 * m.field + pj];
+    for (int dir = 0; dir < 2; ++dir) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int o = -3; o <= 3; ++o) {
+        size_t pj = 0;
+        const double cf = tcoef(m, i, j, dir, o, pj);
+        if (cf == 0.0) continue;
+        const double jac = m.cart ? m.mc[4] : static_cast<const double *>(m.met)[4 * m.field + pj];
+        const double x = cf * jac;
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            double we = c_w64[row][e];
-            if (we != 0.0 && sgn * c_off[row][e] == -o) acc += sgn * we * jac * a.lam[c * m.field + pj];
-          }
-        }
-        a.mu[(dir * 4 + c) * m.field + p] = -acc;
+        for (int c = 0; c < 4; ++c) acc[c] += x * a.lam[c * m.field + pj];
       }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a.mu[(dir * 4 + c) * m.field + p] = -acc[c];
+    }
   }
 }
 
@@ -429,9 +418,17 @@ __global__ void k_adj_dT(const DevMesh m, const double *ld, double *lp) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
     int i = (int)(t % m.ni), j = (int)(t / m.ni);
     size_t p = (size_t)j * m.pitch + i;
+    double acc[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    for (int dir = 0; dir < 2; ++dir)
+      for (int o = -3; o <= 3; ++o) {
+        size_t pj = 0;
+        const double cf = tcoef(m, i, j, dir, o, pj);
+        if (cf == 0.0) continue;
 #pragma unroll
-    for (int f = 0; f < 3; ++f)
-      lp[f * m.field + p] = dT_at(m, ld + (2 * f) * m.field, i, j, 0) + dT_at(m, ld + (2 * f + 1) * m.field, i, j, 1);
+        for (int f = 0; f < 3; ++f) acc[f][dir] += cf * ld[(2 * f + dir) * m.field + pj];
+      }
+#pragma unroll
+    for (int f = 0; f < 3; ++f) lp[f * m.field + p] = acc[f][0] + acc[f][1];
   }
 }
 
