@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--no-large", action="store_true", help="skip rhs_eval on meshes larger than L2")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D Taylor-Green workload")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
+    ap.add_argument("--no-stability", action="store_true", help="skip the step-matrix stability study")
     return ap.parse_args()
 
 
@@ -597,6 +598,44 @@ def _run_adjoint(n_steps=500, n_snapshots=40):
                     "the far-field state alone"}
 
 
+def _run_stability(ratios=(1, 2, 3, 4), rel_tol=3e-3):
+    """Step-matrix stability (Sec. 4.3): the largest stable macro step H of MRAB order 3 for
+    several step ratios on the vortex geometry (periodic 64^2 background, 41^2 patch at 1/3.1
+    of its spacing) linearised about the uniform Mach 0.5 flow, by bisection on the spectral
+    radius of G_eps (Arnoldi on GPU steps). r_SRAB = H_max / H_max(SR = 1) and the efficiency
+    r_SRAB / SR mirror the paper's stability table."""
+    import numpy as np
+    import paper_1805_06607_gb300 as sbp
+    from paper_1805_06607_gb300.stability import max_stable_step
+    import workloads as W
+
+    out = {"workload": "vortex box-in-box geometry (64^2 + 41^2), uniform Mach 0.5 flow, MRAB order 3",
+           "rows": []}
+    h1 = None
+    t0 = time.perf_counter()
+    for sr in ratios:
+        wl = W.vortex_box_in_box(seed=0, step_ratio=sr)
+        qinf = np.asarray(wl["params"]["qinf"], dtype=np.float64)
+        uni = [np.broadcast_to(qinf[:, None, None], (4, m["n"][1], m["n"][0])).copy() for m in wl["meshes"]]
+
+        def make():
+            g = sbp.System(wl)
+            g.bind(uni)
+            return g
+
+        g = make()
+        dts, _ = g.timestep(g.current_state(0), g.current_state(1))
+        g.close()
+        Hmax, ev = max_stable_step(make, 0.25 * sr * dts[1], 2.0 * sr * dts[1], rel_tol=rel_tol)
+        if h1 is None:
+            h1 = Hmax
+        out["rows"].append({"step_ratio": sr, "H_max": Hmax, "r_SRAB": Hmax / h1, "efficiency": Hmax / h1 / sr,
+                            "bisection_evaluations": len(ev)})
+    out["dt_fast_estimate_sec41"] = dts[1]
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def _cpu_baseline(wl, seconds):
     """The oracle, as it stands, on the host: whole MRAB macro steps of the same workload."""
     import numpy as np
@@ -702,6 +741,8 @@ def main():
                                     "roofline": _roofline(r2, wl, other, hbm_peak, peak_kind),
                                     "autotuned_blocks": r2["tuning"],
                                     "phases_ms_per_step": {p: v[0] / args.steps for p, v in r2["prof"].items()}}}
+    if not args.no_stability and rank == 0:
+        line["stability"] = _run_stability()
     if not args.no_adjoint and rank == 0:
         line["adjoint"] = _run_adjoint()
     if not args.no_3d and rank == 0:

@@ -195,6 +195,14 @@ sbp_status sbp_autotune(sbp_system_t sys, int enable, void *stream);
  * autotuner (sbp_autotune(sys, 0, stream)) to keep it. */
 sbp_status sbp_set_rhs_shape(sbp_system_t sys, int mesh, int strip, int rows);
 
+/* The integrator state of `mesh` between macro steps (after sbp_mrab_init): its current state
+ * and the hist_len - 1 right-hand-side history entries the next macro step reads, oldest first
+ * (the MRAB stepping vector of Sec. 3.3 / the step matrix of Sec. 4.3). set = 0 copies them to
+ * the caller's device buffers q (state layout) and hist ((hist_len - 1) states, contiguous);
+ * set = 1 copies them from those buffers into the integrator, so a run can be checkpointed and
+ * resumed, or perturbed. Asynchronous on the stream. */
+sbp_status sbp_integrator_state(sbp_system_t sys, int mesh, void *q, void *hist, int set, void *stream);
+
 /* Macro step size H and elapsed time since the end of the bootstrap. */
 sbp_status sbp_mrab_time(sbp_system_t sys, double *H, double *t);
 

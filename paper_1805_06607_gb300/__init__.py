@@ -90,6 +90,7 @@ _SIGS = {
     "sbp_autotune": [_P, _I, _P],
     "sbp_profile_read": [_P, _P, _P, _I],
     "sbp_set_rhs_shape": [_P, _I, _I, _I],
+    "sbp_integrator_state": [_P, _I, _P, _P, _I, _P],
 }
 _SIGS.update({
     "sbp_batch_create": [ctypes.POINTER(_P), _I, _I, _P, ctypes.POINTER(_P)],
@@ -304,6 +305,23 @@ class System:
 
     def mrab_step(self, n=1, stream=None):
         _check(_lib.sbp_mrab_step(self.h, int(n), _stream(stream)), "sbp_mrab_step")
+
+    def get_state(self, stream=None):
+        """Integrator state per mesh: (state, history entries oldest first) device tensors."""
+        out = []
+        m = self.params["hist_len"]
+        for k in range(2):
+            q = self.empty_state(k)
+            h = self.empty_state(k, n=max(m - 1, 1)) if m > 2 else self.empty_state(k)[None]
+            _check(_lib.sbp_integrator_state(self.h, k, _ptr(q), _ptr(h), 0, _stream(stream)), "sbp_integrator_state")
+            out.append((q, h[:m - 1]))
+        return out
+
+    def set_state(self, state, stream=None):
+        for k in range(2):
+            q, h = state[k]
+            _check(_lib.sbp_integrator_state(self.h, k, _ptr(q.contiguous()), _ptr(h.contiguous()), 1,
+                                             _stream(stream)), "sbp_integrator_state")
 
     def mrab_time(self):
         H = ctypes.c_double()

@@ -271,6 +271,26 @@ sbp_status sbp_current_state(sbp_system_t S, int k, void **q) {
   return SBP_OK;
 }
 
+sbp_status sbp_integrator_state(sbp_system_t S, int k, void *q, void *hist, int set, void *stream) {
+  if (!S || k < 0 || k > 1 || !q || !hist || (set != 0 && set != 1)) return fail(SBP_ERR_ARG, "bad argument");
+  if (!S->initialised) return fail(SBP_ERR_STATE, "sbp_mrab_init has not run");
+  cudaStream_t s = (cudaStream_t)stream;
+  const MeshDev &d = S->md[k];
+  const size_t b = S->state_elems(k) * S->esz;
+  const int m = S->plan.m;
+  void *cur = d.q[d.cur];
+  CUDA_TRY(set ? cudaMemcpyAsync(cur, q, b, cudaMemcpyDeviceToDevice, s)
+               : cudaMemcpyAsync(q, cur, b, cudaMemcpyDeviceToDevice, s));
+  // the m - 1 entries the next macro step reads, oldest first: slots head + 2 + j (mod m)
+  for (int j = 0; j < m - 1; ++j) {
+    void *slot = S->hist_slot(k, (d.head + 2 + j) % m);
+    void *user = (char *)hist + (size_t)j * b;
+    CUDA_TRY(set ? cudaMemcpyAsync(slot, user, b, cudaMemcpyDeviceToDevice, s)
+                 : cudaMemcpyAsync(user, slot, b, cudaMemcpyDeviceToDevice, s));
+  }
+  return SBP_OK;
+}
+
 sbp_status sbp_mrab_init(sbp_system_t S, double H, void *stream) {
   if (!S) return fail(SBP_ERR_ARG, "null system");
   for (int k = 0; k < 2; ++k)
