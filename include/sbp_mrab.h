@@ -203,6 +203,18 @@ sbp_status sbp_set_rhs_shape(sbp_system_t sys, int mesh, int strip, int rows);
  * resumed, or perturbed. Asynchronous on the stream. */
 sbp_status sbp_integrator_state(sbp_system_t sys, int mesh, void *q, void *hist, int set, void *stream);
 
+/* n steps of the classical fourth-order Runge-Kutta method at step h on both meshes at one
+ * rate, the single-rate baseline of Sec. 4.4 and 6.1 (eq. (perf_RK4): four right-hand sides
+ * of every point per step). Each stage evaluates both meshes' right-hand sides with the overset
+ * coupling to the other mesh's stage state (sbp_overset_interp + sbp_rhs_eval), then
+ * y <- y + h/6 k1 + h/3 k2 + h/3 k3 + h/6 k4 with FP64 accumulation, in place in the current
+ * state buffers (sbp_bind). Needs h > 0 (SBP_ERR_ARG) and bound buffers (SBP_ERR_STATE).
+ * Allocates five states per mesh of stage storage on first use (kept with the system). A step
+ * is one CUDA graph replay while graphs are on (sbp_use_graphs). Leaves the MRAB history
+ * stale: sbp_mrab_init must run again before sbp_mrab_step. Asynchronous on the stream; the
+ * elapsed time (sbp_mrab_time) advances by n h. */
+sbp_status sbp_rk4_step(sbp_system_t sys, int n, double h, void *stream);
+
 /* Macro step size H and elapsed time since the end of the bootstrap. */
 sbp_status sbp_mrab_time(sbp_system_t sys, double *H, double *t);
 

@@ -86,8 +86,8 @@ def lib():
 
 
 from .system import (OracleSystem, ab_coefficients, mrab_macro_step, rk3_heun_step,  # noqa: E402
-                     srab_step, l2_norm)
+                     rk4_step, srab_step, l2_norm)
 from .system3d import OracleSystem3D  # noqa: E402
 
 __all__ = ["build", "lib", "OracleSystem", "OracleSystem3D", "ab_coefficients", "mrab_macro_step", "rk3_heun_step",
-           "srab_step", "l2_norm"]
+           "rk4_step", "srab_step", "l2_norm"]

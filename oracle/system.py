@@ -56,6 +56,17 @@ def rk3_heun_step(y, h, f):
     return [yi + (h / 4.0) * (a + 3.0 * c) for yi, a, c in zip(y, k1, k3)], k1
 
 
+def rk4_step(y, h, f):
+    """The classical fourth-order Runge-Kutta step, the single-rate baseline integrator of
+    Sec. 4.4 and 6.1: k1 = f(y), k2 = f(y + h/2 k1), k3 = f(y + h/2 k2), k4 = f(y + h k3),
+    y_new = y + h/6 (k1 + 2 k2 + 2 k3 + k4). y is a list of per-component arrays."""
+    k1 = f(y)
+    k2 = f([yi + (h / 2.0) * ki for yi, ki in zip(y, k1)])
+    k3 = f([yi + (h / 2.0) * ki for yi, ki in zip(y, k2)])
+    k4 = f([yi + h * ki for yi, ki in zip(y, k3)])
+    return [yi + (h / 6.0) * (a + 2.0 * b + 2.0 * c + d) for yi, a, b, c, d in zip(y, k1, k2, k3, k4)]
+
+
 def _combine(y, coeffs, hist):
     out = y
     for c, a in zip(coeffs, hist):
@@ -374,6 +385,14 @@ class OracleSystem:
         out = [None, None]
         out[self.fast], out[self.slow] = f, s
         return out, hist_f, hist_s
+
+    def rk4(self, qs, h, n_steps):
+        """n_steps classical Runge-Kutta steps of size h on both meshes at one rate, every stage
+        with the overset coupling (the baseline integrator of Sec. 4.4 and 6.1)."""
+        y = [np.array(q, dtype=np.float64) for q in qs]
+        for _ in range(n_steps):
+            y = rk4_step(y, h, self.rhs_all)
+        return y
 
     def cell_sizes(self):
         """Cell size per point for eq. (l2error): J^-1 (= dx dy on Cartesian meshes), holes 0."""

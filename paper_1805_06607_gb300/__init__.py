@@ -84,6 +84,7 @@ _SIGS = {
     "sbp_mrab_init": [_P, _D, _P],
     "sbp_mrab_step": [_P, _I, _P],
     "sbp_mrab_time": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "sbp_rk4_step": [_P, _I, _D, _P],
     "sbp_check": [_P, _P],
     "sbp_profile_enable": [_P, _I],
     "sbp_use_graphs": [_P, _I],
@@ -305,6 +306,11 @@ class System:
 
     def mrab_step(self, n=1, stream=None):
         _check(_lib.sbp_mrab_step(self.h, int(n), _stream(stream)), "sbp_mrab_step")
+
+    def rk4_step(self, n, h, stream=None):
+        """n classical Runge-Kutta steps of size h on both meshes (single rate), in place on the
+        bound states; the MRAB history must be rebuilt (mrab_init) before the next mrab_step."""
+        _check(_lib.sbp_rk4_step(self.h, int(n), float(h), _stream(stream)), "sbp_rk4_step")
 
     def get_state(self, stream=None):
         """Integrator state per mesh: (state, history entries oldest first) device tensors."""

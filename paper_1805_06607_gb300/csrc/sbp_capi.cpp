@@ -349,6 +349,16 @@ sbp_status sbp_mrab_step(sbp_system_t S, int n, void *stream) {
   return SBP_OK;
 }
 
+sbp_status sbp_rk4_step(sbp_system_t S, int n, double h, void *stream) {
+  if (!S || n < 0 || !(h > 0.0) || !std::isfinite(h)) return fail(SBP_ERR_ARG, "bad argument");
+  for (int k = 0; k < 2; ++k)
+    if (!S->md[k].hist) return fail(SBP_ERR_STATE, "buffers not bound");
+  CUDA_TRY(S->rk4(n, h, (cudaStream_t)stream));
+  S->initialised = false;
+  S->t += n * h;
+  return SBP_OK;
+}
+
 sbp_status sbp_mrab_time(sbp_system_t S, double *H, double *t) {
   if (!S) return fail(SBP_ERR_ARG, "null system");
   if (H) *H = S->H;

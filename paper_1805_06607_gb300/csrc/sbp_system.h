@@ -107,9 +107,19 @@ struct sbp_system_s {
   bool aws_ready = false;
   std::vector<void *> adj_allocs;
 
+  // Classical fourth-order Runge-Kutta, the single-rate baseline integrator (Sec. 4.4, 6.1):
+  // per mesh a stage state and the four stage derivatives (allocated on first use), and the
+  // CUDA graph of one step for the step size and state buffers it was captured with.
+  void *rk_buf[2] = {nullptr, nullptr};
+  cudaGraphExec_t rk_graph = nullptr;
+  double rk_graph_h = 0.0;
+  int rk_graph_cur = -1;
+
   void clear_graphs() {
     for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
+    if (rk_graph) cudaGraphExecDestroy(rk_graph);
+    rk_graph = nullptr;
   }
 
   cudaEvent_t take_event() {
@@ -172,6 +182,7 @@ struct sbp_system_s {
     }
     cudaFree(d_err);
     cudaFree(d_dt);
+    for (void *b : rk_buf) cudaFree(b);
     for (void *ptr : adj_allocs) cudaFree(ptr);
     drain();
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
@@ -523,6 +534,78 @@ struct sbp_system_s {
       cudaFree(ystage[k]);
       cudaFree(k1tmp[k]);
       cudaFree(k23[k]);
+    }
+    return e;
+  }
+
+  // One classical Runge-Kutta step of size h on both meshes, in place on the current state
+  // buffers: k_i = f(y_i) with y_1 = y, y_2 = y + h/2 k_1, y_3 = y + h/2 k_2, y_4 = y + h k_3,
+  // each stage with the overset coupling to the other mesh's stage state, then
+  // y + h/6 k_1 + h/3 k_2 + h/3 k_3 + h/6 k_4 (two FP64-accumulated passes).
+  cudaError_t issue_rk4(double h, cudaStream_t s) {
+    void *y[2], *ys[2], *kk[2][4];
+    for (int k = 0; k < 2; ++k) {
+      const size_t b = state_elems(k) * esz;
+      y[k] = md[k].q[md[k].cur];
+      ys[k] = rk_buf[k];
+      for (int i = 0; i < 4; ++i) kk[k][i] = (char *)rk_buf[k] + (size_t)(1 + i) * b;
+    }
+    cudaError_t e = cudaSuccess;
+    auto stage = [&](void *const *in, int i) {
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = rhs_plain(k, in[k], in[1 - k], kk[k][i], s);
+    };
+    const double c[3] = {0.5 * h, 0.5 * h, h};
+    stage(y, 0);
+    for (int i = 0; i < 3; ++i) {
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = launch_axpy(y[k], kk[k][i], c[i], nullptr, 0.0, ys[k], state_elems(k), p.dtype, s);
+      stage(ys, i + 1);
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = launch_axpy(y[k], kk[k][0], h / 6.0, kk[k][1], h / 3.0, ys[k], state_elems(k), p.dtype, s);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+      e = launch_axpy(ys[k], kk[k][2], h / 3.0, kk[k][3], h / 6.0, y[k], state_elems(k), p.dtype, s);
+    return e;
+  }
+
+  cudaError_t rk4(int n, double h, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      if (rk_buf[k]) continue;
+      const size_t b = 5 * state_elems(k) * esz;
+      e = cudaMalloc(&rk_buf[k], b);
+      if (e == cudaSuccess) e = cudaMemsetAsync(rk_buf[k], 0, b, s);
+    }
+    if (e != cudaSuccess) return e;
+    const int key = md[0].cur | (md[1].cur << 1);
+    if (use_graph && !prof) {
+      if (!rk_graph || rk_graph_h != h || rk_graph_cur != key) {
+        if (rk_graph) cudaGraphExecDestroy(rk_graph);
+        rk_graph = nullptr;
+        if (!cap) {
+          if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+          if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+          if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+          if ((e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        cudaError_t ei = issue_rk4(h, cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        if (ei != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          return ei;
+        }
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&rk_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        rk_graph_h = h;
+        rk_graph_cur = key;
+      }
+      for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaGraphLaunch(rk_graph, s);
+    } else {
+      for (int i = 0; i < n && e == cudaSuccess; ++i) e = issue_rk4(h, s);
     }
     return e;
   }

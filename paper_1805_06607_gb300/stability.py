@@ -20,6 +20,10 @@ values up to about 1 % above 1, while past the stability limit the outliers rise
 (several percent within a few percent of H). The largest stable macro step is found by
 bisection. Every step runs in the library's kernels; only the small
 Krylov algebra runs on the host.
+
+The same analysis applies to the single-rate classical Runge-Kutta baseline (Sec. 4.4), whose
+integrator state is the two meshes' current states alone (``integrator="rk4"``); the ratio of
+the largest stable steps is the r_RK4 of the performance model, eqs. (perf_RK4), (perf_AB).
 """
 from __future__ import annotations
 
@@ -27,17 +31,25 @@ import numpy as np
 
 
 class StepMatrix:
-    """G_eps of one MRAB macro step of ``system`` at macro step H around the state reached by
-    the bootstrap from the bound initial states (``system.bind`` must have run)."""
+    """G_eps of one step of ``system`` at step H (``system.bind`` must have run): an MRAB
+    macro step around the state reached by the bootstrap from the bound initial states, or
+    (integrator="rk4") a classical Runge-Kutta step of both meshes around the bound states."""
 
-    def __init__(self, system, H, eps=1e-7):
+    def __init__(self, system, H, eps=1e-7, integrator="mrab"):
         import torch
+        if integrator not in ("mrab", "rk4"):
+            raise ValueError("integrator must be 'mrab' or 'rk4'")
         self.torch = torch
         self.g = system
+        self.H = H
         self.eps = eps
+        self.integrator = integrator
         system.autotune(False)
-        system.mrab_init(H)
-        self.phi0 = system.get_state()
+        if integrator == "mrab":
+            system.mrab_init(H)
+            self.phi0 = system.get_state()
+        else:
+            self.phi0 = [(system.current_state(k).clone(), None) for k in range(2)]
         self.masks = []
         for k in range(2):
             inf = system.info[k]
@@ -56,7 +68,8 @@ class StepMatrix:
         for k, (q, h) in enumerate(state):
             m = self.masks[k]
             parts.append(q[:, m].reshape(-1))
-            parts.append(h[:, :, m].reshape(-1))
+            if h is not None:
+                parts.append(h[:, :, m].reshape(-1))
         return self.torch.cat(parts).double().cpu().numpy()
 
     def unpack(self, vec):
@@ -65,20 +78,28 @@ class StepMatrix:
         t = self.torch.from_numpy(np.ascontiguousarray(vec)).cuda()
         for k, (q0, h0) in enumerate(self.phi0):
             m = self.masks[k]
-            q, h = q0.clone(), h0.clone()
+            q = q0.clone()
             n = int(m.sum()) * q.shape[0]
             q[:, m] = t[o:o + n].reshape(q.shape[0], -1).to(q.dtype)
             o += n
-            nh = int(m.sum()) * h.shape[0] * h.shape[1]
-            h[:, :, m] = t[o:o + nh].reshape(h.shape[0], h.shape[1], -1).to(h.dtype)
-            o += nh
+            h = None
+            if h0 is not None:
+                h = h0.clone()
+                nh = int(m.sum()) * h.shape[0] * h.shape[1]
+                h[:, :, m] = t[o:o + nh].reshape(h.shape[0], h.shape[1], -1).to(h.dtype)
+                o += nh
             out.append((q, h))
         return out
 
     def _step(self, state):
-        self.g.set_state(state)
-        self.g.mrab_step(1)
-        return self.pack(self.g.get_state())
+        if self.integrator == "mrab":
+            self.g.set_state(state)
+            self.g.mrab_step(1)
+            return self.pack(self.g.get_state())
+        for k in range(2):
+            self.g.current_state(k).copy_(state[k][0])
+        self.g.rk4_step(1, self.H)
+        return self.pack([(self.g.current_state(k), None) for k in range(2)])
 
     def matvec(self, v):
         v = np.asarray(v, dtype=np.float64).reshape(-1)
@@ -95,7 +116,8 @@ class StepMatrix:
 
 def arnoldi_radius(matvec, n, kdim=60, seed=0):
     """Largest modulus of the Ritz values of a kdim-dimensional Krylov space of the operator
-    (Arnoldi, modified Gram-Schmidt applied twice), from a seeded random start vector."""
+    (Arnoldi, modified Gram-Schmidt applied twice), from a seeded random start vector. A step
+    that leaves the finite numbers (a state driven non-physical) counts as unstable: inf."""
     V = np.zeros((kdim + 1, n))
     Hm = np.zeros((kdim + 1, kdim))
     v = np.random.default_rng(seed).standard_normal(n)
@@ -103,6 +125,8 @@ def arnoldi_radius(matvec, n, kdim=60, seed=0):
     k = kdim
     for j in range(kdim):
         w = matvec(V[j])
+        if not np.all(np.isfinite(w)):
+            return float("inf")
         for _ in range(2):
             for i in range(j + 1):
                 c = V[i] @ w
@@ -116,15 +140,26 @@ def arnoldi_radius(matvec, n, kdim=60, seed=0):
     return float(np.abs(np.linalg.eigvals(Hm[:k, :k])).max())
 
 
-def max_stable_step(make_system, H_lo, H_hi, rel_tol=1e-3, slack=0.02, **kw):
+def max_stable_step(make_system, H_lo, H_hi, rel_tol=1e-3, slack=0.02, integrator="mrab", **kw):
     """Largest H in [H_lo, H_hi] with rho(G_eps(H)) <= 1 + slack, by bisection; make_system()
     returns a freshly bound system. H_lo must be stable and H_hi unstable. Returns (H, evaluations)."""
+
+    def radius(H):
+        g = make_system()
+        rho = StepMatrix(g, H, integrator=integrator).spectral_radius(**kw)
+        g.close()
+        return rho
+
+    return bisect_stable_step(radius, H_lo, H_hi, rel_tol=rel_tol, slack=slack)
+
+
+def bisect_stable_step(radius, H_lo, H_hi, rel_tol=1e-3, slack=0.02):
+    """Largest H in [H_lo, H_hi] with radius(H) <= 1 + slack, by bisection on the step, for any
+    spectral-radius estimate radius(H) of a step matrix. Returns (H, [(H, radius), ...])."""
     evals = []
 
     def stable(H):
-        g = make_system()
-        rho = StepMatrix(g, H).spectral_radius(**kw)
-        g.close()
+        rho = radius(H)
         evals.append((H, rho))
         return rho <= 1.0 + slack
 

@@ -38,6 +38,16 @@ CASES = {
     "mms_viscous": lambda: W.mms_box_in_box(52, "viscous"),
 }
 
+# The extended-history Adams-Bashforth family of Sec. 3.2 inside MRAB (order n, history m:
+# ABnm), on small geometries: the interface and operator paths are those of CASES.
+AB_CASES = {
+    "vortex_ab45": lambda: W.vortex_box_in_box(seed=16, n_bg=40, n_fine=25, step_ratio=2, order=4, hist_len=5),
+    "vortex_ab35_sr3": lambda: W.vortex_box_in_box(seed=17, n_bg=40, n_fine=25, step_ratio=3, order=3, hist_len=5),
+    "vortex_ab44_sr4": lambda: W.vortex_box_in_box(seed=18, n_bg=40, n_fine=25, step_ratio=4, order=4, hist_len=4),
+    "cylinder_ab46": lambda: W.cylinder_small(seed=19, n_theta=72, n_r=20, bg_n=(90, 50), order=4, hist_len=6,
+                                              step_ratio=2),
+}
+
 
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_setup_tables(sbp, case):
@@ -92,9 +102,10 @@ def test_interp_and_rhs_fp64(sbp, case):
     g.close()
 
 
-@pytest.mark.parametrize("case", ["vortex", "cylinder", "vortex_sr3_ab34", "cylinder_ab34", "vortex_sr1"])
+@pytest.mark.parametrize("case", ["vortex", "cylinder", "vortex_sr3_ab34", "cylinder_ab34", "vortex_sr1"]
+                         + sorted(AB_CASES))
 def test_mrab_fp64(sbp, case):
-    wl = CASES[case]()
+    wl = {**CASES, **AB_CASES}[case]()
     ref = OracleSystem(wl)
     g = sbp.System(wl)
     qd = [g.to_device(k, wl["q0"][k]) for k in range(2)]

@@ -7,11 +7,15 @@ Sec. 4.1 step estimate. The AB3 bound is computed here from the AB3 weights by t
 locus. MRAB with step ratio 2 on the vortex geometry, where the fine patch sets the limit,
 must reach that bound (the paper's ~100 % efficiency below the spacing ratio).
 """
+import ctypes
+import math
+
 import numpy as np
 
+import oracle
 import workloads as W
 from conftest import golden
-from oracle import OracleSystem, ab_coefficients
+from oracle import OracleSystem, ab_coefficients, rk4_step
 
 
 def _arnoldi_radius(matvec, n, kdim=60, seed=0):
@@ -113,3 +117,67 @@ def test_mrab_uniform_flow_stability_limit_matches_theory():
 
     assert rho(0.95 * f_star * sr * dt_fast) <= 1.0 + 1e-3
     assert rho(1.05 * f_star * sr * dt_fast) > 1.0 + 1e-3
+
+
+def _e2_case():
+    g = {r[0]: float(r[1]) for r in golden("rk4_advection_stability.txt")}
+    n = int(g["n_points"])
+    dx = g["length"] / n  # periodic: the point at x = length is the point at x = 0
+    L = oracle.lib()
+    cls = np.zeros(n, np.int8)  # periodic line: the interior row everywhere
+    D = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        out = np.zeros(n)
+        L.orc_apply_d1(n, ctypes.c_void_p(cls.ctypes.data), ctypes.c_void_p(e.ctypes.data),
+                       ctypes.c_void_p(out.ctypes.data))
+        D[:, k] = out
+    return g, n, dx, D
+
+
+def _step_matrix_radius(step, base, eps=1e-7):
+    """The step matrix of Sec. 4.3 built column by column as the paper does (perturb one entry
+    of the integrator state by eps, eq. (sm_form)), and its spectral radius from a dense
+    eigen-decomposition (in place of SLEPc's Krylov-Schur solver)."""
+    n = base.size
+    y0 = step(base)
+    G = np.empty((n, n))
+    for j in range(n):
+        ph = base.copy()
+        ph[j] += eps
+        G[:, j] = (step(ph) - y0) / eps
+    return float(np.abs(np.linalg.eigvals(G)).max())
+
+
+def test_rk4_advection_step_matrix_reproduces_sec44():
+    """Sec. 4.4: RK4 on 1D periodic advection (61 points on [0, 1.01666]); the step-matrix
+    procedure finds the largest stable step between 0.03 and 0.035, consistent with the
+    estimate (RK4 imaginary-axis bound) / (lambda_max dx) * dx. Here the bound is the exact
+    2 sqrt(2) of the RK4 amplification polynomial and lambda_max is this grid's own largest
+    eigenvalue of D, so the bisection must land on that closed form."""
+    g, n, dx, D = _e2_case()
+    x = np.arange(n) * dx
+    base = np.sin(2.0 * math.pi * x / g["length"]) + 0.3 * np.cos(6.0 * math.pi * x / g["length"])
+
+    def radius(dt):
+        return _step_matrix_radius(lambda u: rk4_step([u], dt, lambda v: [-(D @ v[0]) / dx])[0], base)
+
+    assert radius(g["dt_stable"]) <= 1.0 + 1e-6
+    assert radius(g["dt_unstable"]) > 1.0 + 1e-6
+    lo, hi = g["dt_stable"], g["dt_unstable"]
+    while hi - lo > 1e-7:
+        mid = 0.5 * (lo + hi)
+        if radius(mid) <= 1.0 + 1e-6:
+            lo = mid
+        else:
+            hi = mid
+    lam_dx = float(np.abs(np.linalg.eigvals(D)).max())
+    # 61 discrete wave numbers sample the continuous maximum 1.3722 (1.3705 here)
+    assert abs(lam_dx - float(golden("periodic_spectrum.txt")[0][0])) < 2e-3
+    closed = 2.0 * math.sqrt(2.0) / lam_dx * dx
+    assert abs(lo - closed) < 2e-6 * closed, (lo, closed)
+    # the paper's estimate from its approximate imaginary-axis bound lies in the same bracket
+    est = g["rk4_imag_bound_approx"] / float(golden("periodic_spectrum.txt")[0][0]) * dx
+    assert abs(est - g["dt_estimate"]) < 2e-5
+    assert g["dt_stable"] < est < lo < g["dt_unstable"]

@@ -9,7 +9,7 @@ import scipy.linalg
 
 import workloads as W
 from conftest import golden
-from oracle import OracleSystem, ab_coefficients, mrab_macro_step, rk3_heun_step, srab_step
+from oracle import OracleSystem, ab_coefficients, mrab_macro_step, rk3_heun_step, rk4_step, srab_step
 
 
 def test_ab_textbook():
@@ -102,6 +102,25 @@ def test_rk3_order():
             y, _ = rk3_heun_step(y, 1.0 / n, lambda z: [lam * z[0]])
         errs.append(abs(float(y[0]) - math.exp(lam)))
     assert 2.9 < math.log2(errs[0] / errs[1]) < 3.1
+
+
+def test_rk4_order():
+    lam = -1.3
+    errs = []
+    for n in (10, 20):
+        y = [np.array(1.0)]
+        for _ in range(n):
+            y = rk4_step(y, 1.0 / n, lambda z: [lam * z[0]])
+        errs.append(abs(float(y[0]) - math.exp(lam)))
+    assert 3.9 < math.log2(errs[0] / errs[1]) < 4.1
+
+
+def test_rk4_amplification_is_the_degree_4_taylor_polynomial():
+    """One step on y' = z y multiplies y by 1 + z + z^2/2 + z^3/6 + z^4/24 (complex z): every
+    stage weight and node enters a different power."""
+    for z in (0.3 + 0.0j, -1.7 + 0.4j, 2.1j, -0.5 - 2.6j):
+        y = rk4_step([np.array(1.0 + 0.0j)], 1.0, lambda v, z=z: [z * v[0]])
+        assert abs(complex(y[0]) - (1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24)) < 1e-14
 
 
 def test_performance_model_rk4_total():
