@@ -83,6 +83,21 @@ __device__ __forceinline__ Row<T> decode_row(unsigned code) {
   return r;
 }
 
+// The same with the weights taken from a per-mesh table of scaled rows (tab[row][tap]).
+template <typename T>
+__device__ __forceinline__ Row<T> decode_row_w(unsigned code, const T (*tab)[4]) {
+  Row<T> r;
+  int row, sgn;
+  row_of(code, row, sgn);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    r.off[e] = sgn * c_off[row][e];
+    r.w[e] = tab[row][e];
+  }
+  r.neg = sgn < 0;
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T row_sum(const Row<T> &r, const T *const p[4], int plane) {
   T acc = T(0);
@@ -111,6 +126,16 @@ __device__ __forceinline__ T central_sum(const T *const p[4], int plane) {
   acc += CentralRow<T>::w1 * p[1][plane];
   acc += CentralRow<T>::w2 * p[2][plane];
   acc += CentralRow<T>::w3 * p[3][plane];
+  return acc;
+}
+
+// The interior row with the weights w (a scaled table's row 4), taps at fixed offsets: row_sum's
+// operation order.
+template <typename T>
+__device__ __forceinline__ T central_sum_w(const T *const p[4], int plane, const T w[4]) {
+  T acc = T(0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc += w[e] * p[e][plane];
   return acc;
 }
 
@@ -322,11 +347,12 @@ __device__ __forceinline__ void visc_flux_k(const KConst<T> &k, T u, T v, const 
 }
 
 // Gradients of (u, v, T) at smem index r of the primitive planes (row stride rx), chain rule
-// with the metrics; Cartesian meshes use the constants J xi_x = 1/hx, J eta_y = 1/hy.
+// with the metrics; Cartesian meshes take the rows scaled by 1/hx, 1/hy (d/dx, d/dy directly).
 template <typename T, bool CURV>
 __device__ __forceinline__ void smem_grads(const RhsLaunch &a, const T *prim, int rn, int r, int rx, unsigned code,
                                            const T mt[5], T gr[6]) {
-  const Row<T> ri = decode_row<T>(code & 15u), rj = decode_row<T>(code >> 4);
+  const Row<T> ri = CURV ? decode_row<T>(code & 15u) : decode_row_w<T>(code & 15u, kc<T>(a).wx);
+  const Row<T> rj = CURV ? decode_row<T>(code >> 4) : decode_row_w<T>(code >> 4, kc<T>(a).wy);
   const T *pi[4], *pj[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -341,8 +367,8 @@ __device__ __forceinline__ void smem_grads(const RhsLaunch &a, const T *prim, in
       gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
       gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
     } else {
-      gr[2 * f] = kc<T>(a).jx * dxi;
-      gr[2 * f + 1] = kc<T>(a).jy * deta;
+      gr[2 * f] = dxi;
+      gr[2 * f + 1] = deta;
     }
   }
 }
@@ -505,10 +531,12 @@ __device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T 
     } else {
       inviscid_flux(qp, k.gam, Fx, Gx, u, v, pr);
     }
+    // contravariant fluxes on curvilinear meshes; Cartesian meshes keep F and G (the update's
+    // scaled rows give d/dx, d/dy)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      fl[c * m.field + p] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : mt[0] * Fx[c];
-      fl[(4 + c) * m.field + p] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : mt[3] * Gx[c];
+      fl[c * m.field + p] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : Fx[c];
+      fl[(4 + c) * m.field + p] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : Gx[c];
     }
   }
   // SAT terms of this tile's boundary / receiver points (one thread per point)
@@ -575,18 +603,22 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
     const int r = (lj + 3) * RX + (li + 3);
     T rhs[4] = {T(0), T(0), T(0), T(0)};
     if ((code & 15u) != 15u) {
-      T jac;
-      if (CURV) jac = static_cast<const T *>(m.met)[4 * m.field + p];
-      else jac = kc<T>(a).mc[4];
-      const Row<T> ri = decode_row<T>(code & 15u), rj = decode_row<T>(code >> 4);
+      const Row<T> ri = CURV ? decode_row<T>(code & 15u) : decode_row_w<T>(code & 15u, kc<T>(a).wx);
+      const Row<T> rj = CURV ? decode_row<T>(code >> 4) : decode_row_w<T>(code >> 4, kc<T>(a).wy);
       const T *pi[4], *pj[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         pi[e] = sf + r + ri.off[e];
         pj[e] = sf + r + rj.off[e] * RX;
       }
+      if (CURV) {
+        const T jac = static_cast<const T *>(m.met)[4 * m.field + p];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) rhs[c] = -jac * (row_sum(ri, pi, c * RN) + row_sum(rj, pj, (4 + c) * RN));
+        for (int c = 0; c < 4; ++c) rhs[c] = -jac * (row_sum(ri, pi, c * RN) + row_sum(rj, pj, (4 + c) * RN));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) rhs[c] = -(row_sum(ri, pi, c * RN) + row_sum(rj, pj, (4 + c) * RN));
+      }
       if (s0 < s1) {
         // the tile's SAT entries are sorted by (j, i): binary search for this point
         uint32_t key = (uint32_t)gi | ((uint32_t)gj << 16);
@@ -630,11 +662,21 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
 template <typename T>
 __device__ __forceinline__ void set_state(const DonorLaunch &a, int set, size_t p, T out[4]) {
   const T *q = static_cast<const T *>(a.q);
+  const int nb = a.nb[set];
+  // every load first (one memory latency for the group), then the sums in history order
+  T qv[4], hv[kMaxHist][4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) qv[v] = q[v * a.d.field + p];
+#pragma unroll
+  for (int k = 0; k < kMaxHist; ++k)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) hv[k][v] = k < nb ? static_cast<const T *>(a.hist[k])[v * a.d.field + p] : T(0);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    double acc = (double)q[v * a.d.field + p];
-    for (int k = 0; k < a.nb[set]; ++k)
-      acc += a.beta[set][k] * (double)static_cast<const T *>(a.hist[k])[v * a.d.field + p];
+    double acc = (double)qv[v];
+#pragma unroll
+    for (int k = 0; k < kMaxHist; ++k)
+      if (k < nb) acc += a.beta[set][k] * (double)hv[k][v];
     out[v] = (T)acc;
   }
 }

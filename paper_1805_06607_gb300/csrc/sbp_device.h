@@ -34,6 +34,10 @@ struct KConst {
   T qinf[4];
   T mc[5];                          // Cartesian metrics
   T jx, jy;                         // Cartesian J xi_x and J eta_y (1/hx, 1/hy)
+  // Cartesian meshes: the derivative rows' weights times 1/hx (wx) and 1/hy (wy), so that a
+  // row sum is the physical derivative d/dx or d/dy (rows as in the device table: closures
+  // 0-3, interior 4, hole 5)
+  T wx[6][4], wy[6][4];
 };
 
 // Right-hand side (+ optional MRAB update) of one mesh: k_flux then k_update.

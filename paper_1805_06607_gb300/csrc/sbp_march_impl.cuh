@@ -169,8 +169,8 @@ __device__ __forceinline__ void march_flux_point(const RhsLaunch &a, const T *qr
         pj[e] = prim + ((row + off) & (kRing - 1)) * PW + pc;
       }
     } else {
-      ri = decode_row<T>(code & 15u);
-      rj = decode_row<T>(code >> 4);
+      ri = CURV ? decode_row<T>(code & 15u) : decode_row_w<T>(code & 15u, k.wx);
+      rj = CURV ? decode_row<T>(code >> 4) : decode_row_w<T>(code >> 4, k.wy);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         pi[e] = prim + o + ri.off[e];
@@ -180,14 +180,14 @@ __device__ __forceinline__ void march_flux_point(const RhsLaunch &a, const T *qr
     T gr[6];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      T dxi = INT ? central_sum(pi, f * kRing * PW) : row_sum(ri, pi, f * kRing * PW);
-      T deta = INT ? central_sum(pj, f * kRing * PW) : row_sum(rj, pj, f * kRing * PW);
       if (CURV) {
+        T dxi = INT ? central_sum(pi, f * kRing * PW) : row_sum(ri, pi, f * kRing * PW);
+        T deta = INT ? central_sum(pj, f * kRing * PW) : row_sum(rj, pj, f * kRing * PW);
         gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
         gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
       } else {
-        gr[2 * f] = k.jx * dxi;
-        gr[2 * f + 1] = k.jy * deta;
+        gr[2 * f] = INT ? central_sum_w(pi, f * kRing * PW, k.wx[4]) : row_sum(ri, pi, f * kRing * PW);
+        gr[2 * f + 1] = INT ? central_sum_w(pj, f * kRing * PW, k.wy[4]) : row_sum(rj, pj, f * kRing * PW);
       }
     }
     T Fv[3], Gv[3];
@@ -206,15 +206,16 @@ __device__ __forceinline__ void march_flux_point(const RhsLaunch &a, const T *qr
   const int fo = sl * FW + pc - 3;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    fr[c * kRing * FW + fo] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : mt[0] * Fx[c];
-    fr[(4 + c) * kRing * FW + fo] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : mt[3] * Gx[c];
+    fr[c * kRing * FW + fo] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : Fx[c];
+    fr[(4 + c) * kRing * FW + fo] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : Gx[c];
   }
 }
 
-// -J (D_xi F^_xi + D_eta F^_eta) of one point from the flux ring (flux column fc).
-template <typename T, bool INT>
-__device__ __forceinline__ void march_div_point(const T *fr, int FW, int row, int fc, unsigned code, T jac,
-                                                T rhs[4]) {
+// -J (D_xi F^_xi + D_eta F^_eta) of one point from the flux ring (flux column fc); on Cartesian
+// meshes -(d/dx F + d/dy G) with the scaled rows of k.
+template <typename T, bool CURV, bool INT>
+__device__ __forceinline__ void march_div_point(const KConst<T> &k, const T *fr, int FW, int row, int fc,
+                                                unsigned code, T jac, T rhs[4]) {
   const int sl = row & (kRing - 1), o = sl * FW + fc;
   const T *pi[4], *pj[4];
   Row<T> ri, rj;
@@ -226,8 +227,8 @@ __device__ __forceinline__ void march_div_point(const T *fr, int FW, int row, in
       pj[e] = fr + ((row + off) & (kRing - 1)) * FW + fc;
     }
   } else {
-    ri = decode_row<T>(code & 15u);
-    rj = decode_row<T>(code >> 4);
+    ri = CURV ? decode_row<T>(code & 15u) : decode_row_w<T>(code & 15u, k.wx);
+    rj = CURV ? decode_row<T>(code >> 4) : decode_row_w<T>(code >> 4, k.wy);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       pi[e] = fr + o + ri.off[e];
@@ -236,9 +237,15 @@ __device__ __forceinline__ void march_div_point(const T *fr, int FW, int row, in
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const T di = INT ? central_sum(pi, c * kRing * FW) : row_sum(ri, pi, c * kRing * FW);
-    const T dj = INT ? central_sum(pj, (4 + c) * kRing * FW) : row_sum(rj, pj, (4 + c) * kRing * FW);
-    rhs[c] = -jac * (di + dj);
+    if (CURV) {
+      const T di = INT ? central_sum(pi, c * kRing * FW) : row_sum(ri, pi, c * kRing * FW);
+      const T dj = INT ? central_sum(pj, (4 + c) * kRing * FW) : row_sum(rj, pj, (4 + c) * kRing * FW);
+      rhs[c] = -jac * (di + dj);
+    } else {
+      const T di = INT ? central_sum_w(pi, c * kRing * FW, k.wx[4]) : row_sum(ri, pi, c * kRing * FW);
+      const T dj = INT ? central_sum_w(pj, (4 + c) * kRing * FW, k.wy[4]) : row_sum(rj, pj, (4 + c) * kRing * FW);
+      rhs[c] = -(di + dj);
+    }
   }
 }
 
@@ -317,8 +324,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
           const int tile = (gi / kTileX) * nty8 + gj / 8;
           const int s0 = a.tile_sat[tile], s1 = a.tile_sat[tile + 1];
           const T jac = CURV ? mr[4 * kRing * PW + o] : k.mc[4];
-          if (code == 0u) march_div_point<T, true>(fr, FW, gj, cc + 3, code, jac, rhs);
-          else march_div_point<T, false>(fr, FW, gj, cc + 3, code, jac, rhs);
+          if (code == 0u) march_div_point<T, CURV, true>(k, fr, FW, gj, cc + 3, code, jac, rhs);
+          else march_div_point<T, CURV, false>(k, fr, FW, gj, cc + 3, code, jac, rhs);
           if (s0 < s1) {
             const uint32_t key = (uint32_t)gi | ((uint32_t)gj << 16);
             int lo = s0, hi = s1;

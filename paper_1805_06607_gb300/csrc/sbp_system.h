@@ -30,6 +30,16 @@ inline sbp_status fail(sbp_status s, const std::string &msg) {
     if (e_ != cudaSuccess) return fail(SBP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// Weights of the SBP 4-2 derivative rows in the device table's order and tap order (closure
+// rows 0-3 of the diagonal-norm operator, the interior row, a hole row), for the Cartesian
+// meshes' scaled copies.
+inline constexpr double kSbpRows[6][4] = {{-24.0 / 17.0, 59.0 / 34.0, -4.0 / 17.0, -3.0 / 34.0},
+                                          {-0.5, 0.5, 0.0, 0.0},
+                                          {4.0 / 43.0, -59.0 / 86.0, 59.0 / 86.0, -4.0 / 43.0},
+                                          {3.0 / 98.0, -59.0 / 98.0, 32.0 / 49.0, -4.0 / 49.0},
+                                          {1.0 / 12.0, -2.0 / 3.0, 2.0 / 3.0, -1.0 / 12.0},
+                                          {0.0, 0.0, 0.0, 0.0}};
+
 struct MeshDev {
   uint8_t *cls = nullptr;
   void *met = nullptr;
@@ -301,9 +311,16 @@ struct sbp_system_s {
       c.mc[4] = (T)(1.0 / (m.h[0] * m.h[1]));
       c.jx = (T)(1.0 / m.h[0]);
       c.jy = (T)(1.0 / m.h[1]);
+      for (int r = 0; r < 6; ++r)
+        for (int e = 0; e < 4; ++e) {
+          c.wx[r][e] = (T)(kSbpRows[r][e] / m.h[0]);
+          c.wy[r][e] = (T)(kSbpRows[r][e] / m.h[1]);
+        }
     } else {
       for (int q = 0; q < 5; ++q) c.mc[q] = (T)0;
       c.jx = c.jy = (T)0;
+      for (int r = 0; r < 6; ++r)
+        for (int e = 0; e < 4; ++e) c.wx[r][e] = c.wy[r][e] = (T)0;
     }
   }
 
