@@ -398,6 +398,44 @@ def _mrab_vs_single_rate(name, wl, k_slow, exact=None, ref_factor=10):
                       "of each ring phase include its capture), FP64"}
 
 
+def _mrab_variants(name, wl, k_slow, ref_factor=10):
+    """The MRAB orderings of Sec. 3.3 on the same workload and macro step H: fastest-first (the
+    paper's), slowest-first, slowest-first with re-extrapolation. Seconds per slow step (CUDA-
+    graph replay) and the L2 error of eq. (l2error) at T = (m - 1) H + k_slow H against the
+    classical Runge-Kutta method at h / ref_factor from the same initial state."""
+    import torch
+    import paper_1805_06607_gb300 as sbp
+
+    p = wl["params"]
+    sr, m = int(p["step_ratio"]), int(p["hist_len"])
+    g0 = sbp.System(wl, dtype="f64")
+    g0.bind(wl["q0"])
+    qd = [g0.current_state(k) for k in range(2)]
+    _, H = g0.timestep(qd[0], qd[1])
+    g0.close()
+    T = (m - 1) * H + k_slow * H
+    gr = sbp.System(dict(wl, params=dict(p, step_ratio=1)), dtype="f64")
+    gr.bind(wl["q0"])
+    hr = H / sr / ref_factor
+    gr.rk4_step(int(round(T / hr)), hr)
+    torch.cuda.synchronize()
+    gr.check()
+    ref = [gr.to_host(k, gr.current_state(k)) for k in range(2)]
+    gr.close()
+    rows = []
+    for scheme in ("fastest_first", "slowest_first", "slowest_first_reextrapolate"):
+        g = sbp.System(dict(wl, params=dict(p, scheme=scheme)), dtype="f64")
+        g.bind(wl["q0"])
+        g.mrab_init(H)
+        t_ms = _time_slow_steps(g, k_slow, 1)
+        q = [g.to_host(k, g.current_state(k)) for k in range(2)]
+        rows.append({"scheme": scheme, "s_per_slow_step": t_ms / 1e3, "l2": _l2_error(g, q, ref)})
+        g.close()
+    return {"workload": name, "H": H, "slow_steps": k_slow, "T": T, "rows": rows,
+            "l2_reference": "classical Runge-Kutta at h/%d (same discretisation)" % ref_factor,
+            "timing": "median over the slow steps of CUDA-event device time, CUDA-graph replay, FP64"}
+
+
 def _rhs_eval_large(hbm_peak, peak_kind, reps=10):
     """sbp_rhs_eval alone on meshes larger than L2 (SURVEY's K2 on enlarged workloads): the
     cylinder at 4x resolution (Navier-Stokes; O-grid 2048 x 512, background 4096 x 2048) and
@@ -849,6 +887,7 @@ def main():
                                                       c1, 100, exact=exact),
             "cylinder": _mrab_vs_single_rate(WORKLOAD, W2.cylinder_overset(seed=0), 20),
         }
+        line["mrab_orderings"] = _mrab_variants(WORKLOAD, W2.cylinder_overset(seed=0), 20)
     if not args.no_batch:
         line["batched"] = {dt: _run_batch(dt, args.steps, args.warmup, seed=rank) for dt in ("f64", "f32")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -80,7 +80,24 @@ typedef struct {
   double qinf[4];
   int order, hist_len, step_ratio, fast_mesh;
   double hole_cells;             /* hole margin in background spacings (<= 0: 4) */
+  int scheme;                    /* MRAB ordering, an sbp_mrab_scheme (0: the paper's) */
 } sbp_params;
+
+/* The orderings of a macro step that Sec. 3.3 lists as design choices. The paper's runs use
+ * fastest-first without re-extrapolation (the default): the fast micro steps take the slow
+ * state from the slow extrapolant, and the slow right-hand side at t + H is evaluated with the
+ * fast state reached at t + H. The slowest-first variants advance the slow state first and
+ * evaluate the slow right-hand side at t + H with the fast state extrapolated over the macro
+ * step (fast history ending at t); the fast micro steps then take the slow state from the
+ * slow extrapolant of the history ending at t (SLOWEST_FIRST: the slow right-hand side runs
+ * beside the fast micro steps) or re-extrapolated from the history ending at t + H
+ * (SLOWEST_FIRST_REEXTRAPOLATE). All take one slow and step_ratio fast right-hand sides per
+ * macro step. 3D systems, batches and the adjoint support fastest-first only. */
+typedef enum {
+  SBP_MRAB_FASTEST_FIRST = 0,
+  SBP_MRAB_SLOWEST_FIRST = 1,
+  SBP_MRAB_SLOWEST_FIRST_REEXTRAPOLATE = 2
+} sbp_mrab_scheme;
 
 typedef struct {
   int ni, nj, pitch;
@@ -165,7 +182,12 @@ sbp_status sbp_mrab_init(sbp_system_t sys, double H, void *stream);
 /* n macro steps of the fastest-first MRAB scheme without re-extrapolation (Sec. 3.3, Steps
  * 1-7, any integer step ratio). Per macro step: interpolate the fast state to the slow
  * receivers; slow RHS fused with the slow state update; then step_ratio fused fast RHS +
- * fast updates, each fed by the slow extrapolant at its micro time. Asynchronous. */
+ * fast updates, each fed by the slow extrapolant at its micro time. Asynchronous.
+ * Slowest-first systems (sbp_params.scheme): the slow state update alone (its newest history
+ * value exists), the fast state extrapolated to the slow receivers' donors after the first
+ * micro step has pushed a_f(t), the slow RHS at t + H from them, and the fast micro steps
+ * (beside the slow RHS without re-extrapolation, after it with). sbp_mrab_init ends with the
+ * slow RHS at the bootstrap's end time for these. */
 sbp_status sbp_mrab_step(sbp_system_t sys, int n, void *stream);
 
 /* Whether sbp_mrab_step replays CUDA graphs (default 1) or launches kernel by kernel (0).
@@ -200,7 +222,8 @@ sbp_status sbp_set_rhs_shape(sbp_system_t sys, int mesh, int strip, int rows);
  * (the MRAB stepping vector of Sec. 3.3 / the step matrix of Sec. 4.3). set = 0 copies them to
  * the caller's device buffers q (state layout) and hist ((hist_len - 1) states, contiguous);
  * set = 1 copies them from those buffers into the integrator, so a run can be checkpointed and
- * resumed, or perturbed. Asynchronous on the stream. */
+ * resumed, or perturbed. Asynchronous on the stream. Fastest-first systems only
+ * (SBP_ERR_STATE otherwise). */
 sbp_status sbp_integrator_state(sbp_system_t sys, int mesh, void *q, void *hist, int set, void *stream);
 
 /* n steps of the classical fourth-order Runge-Kutta method at step h on both meshes at one

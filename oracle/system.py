@@ -110,6 +110,44 @@ def mrab_macro_step(f, s, hist_f, hist_s, H, sr, order, rhs_fast, rhs_slow):
     return f, s, hist_f, hist_s
 
 
+def mrab_macro_step_slowest_first(f, s, hist_f, hist_s, H, sr, order, rhs_fast, rhs_slow, reextrapolate=False):
+    """One macro step of the slowest-first MRAB variants, the other ordering of Sec. 3.3's
+    design choices (the paper's runs use fastest-first; the variants follow its description of
+    the alternatives). Entry: histories of m values each, oldest first, ending at t.
+      1. s advances over [t, t+H] by the integral of the slow extrapolant (history ending at t).
+      2. The fast state at t+H is extrapolated: f^ = f(t) + integral of the fast extrapolant
+         over [t, t+H].
+      3. The slow right-hand side at t+H is evaluated with it, a_s(s(t+H), f^), and appended.
+      4. The fast micro steps as in fastest-first; the slow state at the intermediate micro
+         times is s(t) + the integral from t of the slow polynomial through the slow history:
+         without re-extrapolation the one of step 1 (history ending at t), with
+         re-extrapolation the one through the updated history (ending at t+H).
+      5. The fast right-hand side at t+H, a_f(f(t+H), s(t+H)), is appended.
+    """
+    m = len(hist_f)
+    h = H / sr
+    nodes = np.arange(-(m - 1), 1, dtype=np.float64)
+    alpha_f = ab_coefficients(nodes, 0.0, 1.0, order) * h
+    alpha_s = ab_coefficients(nodes, 0.0, 1.0, order) * H
+    s_new = _combine(s, alpha_s, hist_s)
+    f_hat = _combine(f, ab_coefficients(nodes, 0.0, float(sr), order) * h, hist_f)
+    hist_s_new = list(hist_s[1:]) + [rhs_slow(s_new, f_hat)]
+    nodes_new = nodes + 1.0  # the updated slow history, relative to t in units of H
+    hist_f = list(hist_f)
+    for j in range(sr):
+        f = _combine(f, alpha_f, hist_f)
+        if j < sr - 1:
+            if reextrapolate:
+                beta = ab_coefficients(nodes_new, 0.0, (j + 1) / sr, order) * H
+                s_hat = _combine(s, beta, hist_s_new)
+            else:
+                beta = ab_coefficients(nodes, 0.0, (j + 1) / sr, order) * H
+                s_hat = _combine(s, beta, hist_s)
+            hist_f = hist_f[1:] + [rhs_fast(f, s_hat)]
+    hist_f = hist_f[1:] + [rhs_fast(f, s_new)]
+    return f, s_new, hist_f, hist_s_new
+
+
 def srab_step(y, hist, dt, order, rhs):
     """Single-rate Adams-Bashforth step of Sec. 3.1 eq. (ab_general) on the whole system:
     y(t+dt) = y(t) + sum_k alpha_k F_k; then F at t+dt is appended to the history.
@@ -373,15 +411,22 @@ class OracleSystem:
         hist_s.append(a[self.slow])
         return y, hist_f, hist_s
 
-    def mrab(self, qs, hist_f, hist_s, H, n_steps):
+    def mrab(self, qs, hist_f, hist_s, H, n_steps, scheme="fastest_first"):
+        """n_steps MRAB macro steps; scheme "fastest_first" (the paper's), "slowest_first" or
+        "slowest_first_reextrapolate" (Sec. 3.3's alternatives)."""
         f, s = qs[self.fast], qs[self.slow]
         sr = int(self.p["step_ratio"])
         order = int(self.p["order"])
         for _ in range(n_steps):
-            f, s, hist_f, hist_s = mrab_macro_step(
-                f, s, hist_f, hist_s, H, sr, order,
-                rhs_fast=lambda ff, ss: self.coupled_rhs(self.fast, ff, ss),
-                rhs_slow=lambda ss, ff: self.coupled_rhs(self.slow, ss, ff))
+            kw = dict(rhs_fast=lambda ff, ss: self.coupled_rhs(self.fast, ff, ss),
+                      rhs_slow=lambda ss, ff: self.coupled_rhs(self.slow, ss, ff))
+            if scheme == "fastest_first":
+                f, s, hist_f, hist_s = mrab_macro_step(f, s, hist_f, hist_s, H, sr, order, **kw)
+            elif scheme in ("slowest_first", "slowest_first_reextrapolate"):
+                f, s, hist_f, hist_s = mrab_macro_step_slowest_first(
+                    f, s, hist_f, hist_s, H, sr, order, reextrapolate=scheme.endswith("reextrapolate"), **kw)
+            else:
+                raise ValueError("unknown MRAB scheme " + scheme)
         out = [None, None]
         out[self.fast], out[self.slow] = f, s
         return out, hist_f, hist_s

@@ -39,7 +39,10 @@ class Params(ctypes.Structure):
                 ("omega_corner", ctypes.c_double), ("sigma_interface", ctypes.c_double),
                 ("sigma_physical", ctypes.c_double), ("cfl", ctypes.c_double), ("qinf", ctypes.c_double * 4),
                 ("order", ctypes.c_int), ("hist_len", ctypes.c_int), ("step_ratio", ctypes.c_int),
-                ("fast_mesh", ctypes.c_int), ("hole_cells", ctypes.c_double)]
+                ("fast_mesh", ctypes.c_int), ("hole_cells", ctypes.c_double), ("scheme", ctypes.c_int)]
+
+# MRAB orderings of Sec. 3.3 (sbp_mrab_scheme)
+SCHEMES = {"fastest_first": 0, "slowest_first": 1, "slowest_first_reextrapolate": 2}
 
 
 class MeshInfo(ctypes.Structure):
@@ -209,6 +212,7 @@ class System:
         pr.step_ratio = p["step_ratio"]
         pr.fast_mesh = p["fast_mesh"]
         pr.hole_cells = hole_cells
+        pr.scheme = SCHEMES[p.get("scheme", "fastest_first")]
         self.params = p
         h = ctypes.c_void_p()
         torch.cuda.init()

@@ -267,6 +267,7 @@ sbp_status sbp3_system_create(const sbp3_mesh_desc *meshes, int n_meshes, const 
   if (!(p.gamma > 1.0) || p.mu < 0.0 || !(p.pr > 0.0)) return fail(SBP_ERR_ARG, "gas constants");
   if (p.step_ratio < 1 || p.step_ratio > kMaxSets)
     return fail(SBP_ERR_ARG, "step_ratio must be in 1.." + std::to_string(kMaxSets));
+  if (p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_ARG, "3D systems are fastest-first");
   auto *S = new sbp3_system_s();
   std::unique_ptr<sbp3_system_s> guard(S);
   S->p = p;

@@ -516,6 +516,7 @@ sbp_status sbp_adjoint_probe(sbp_system_t S, const sbp_adjoint_desc *desc, const
                              void *dJ_dq0_mesh1, double *dJ_dqinf, long *forward_steps, void *stream) {
   if (!S || !desc || !q0_mesh0 || !q0_mesh1) return fail(SBP_ERR_ARG, "bad argument");
   if (S->p.dtype != SBP_F64) return fail(SBP_ERR_DTYPE, "the adjoint needs an SBP_F64 system");
+  if (S->p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_ARG, "the adjoint needs a fastest-first system");
   if (desc->n_steps < 0 || desc->n_snapshots < 0 || desc->n_probes < 1 || !desc->probe_xy || !(desc->H > 0.0))
     return fail(SBP_ERR_ARG, "descriptor: n_steps >= 0, n_snapshots >= 0, n_probes >= 1, probe_xy, H > 0");
   if (S->plan.m < 2) return fail(SBP_ERR_ARG, "the adjoint needs hist_len >= 2");

@@ -37,6 +37,8 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
   if (!(p.gamma > 1.0) || p.mu < 0.0 || !(p.pr > 0.0)) return fail(SBP_ERR_ARG, "gas constants");
   if (p.step_ratio < 1 || p.step_ratio > kMaxSets)
     return fail(SBP_ERR_ARG, "step_ratio must be in 1.." + std::to_string(kMaxSets));
+  if (p.scheme < SBP_MRAB_FASTEST_FIRST || p.scheme > SBP_MRAB_SLOWEST_FIRST_REEXTRAPOLATE)
+    return fail(SBP_ERR_ARG, "scheme");
   auto *S = new sbp_system_s();
   std::unique_ptr<sbp_system_s> guard(S);
   S->p = p;
@@ -274,6 +276,7 @@ sbp_status sbp_current_state(sbp_system_t S, int k, void **q) {
 sbp_status sbp_integrator_state(sbp_system_t S, int k, void *q, void *hist, int set, void *stream) {
   if (!S || k < 0 || k > 1 || !q || !hist || (set != 0 && set != 1)) return fail(SBP_ERR_ARG, "bad argument");
   if (!S->initialised) return fail(SBP_ERR_STATE, "sbp_mrab_init has not run");
+  if (S->p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_STATE, "fastest-first systems only");
   cudaStream_t s = (cudaStream_t)stream;
   const MeshDev &d = S->md[k];
   const size_t b = S->state_elems(k) * S->esz;
@@ -307,6 +310,9 @@ sbp_status sbp_mrab_init(sbp_system_t S, double H, void *stream) {
   S->initialised = true;
   S->clear_graphs();
   if (S->autotune_on) CUDA_TRY(S->autotune(s));
+  // slowest-first macro steps start with the slow history ending at the current time (after
+  // the autotuner, which uses the slot this push fills as scratch)
+  if (S->p.scheme != SBP_MRAB_FASTEST_FIRST) CUDA_TRY(S->slow_rhs_push(s));
   return SBP_OK;
 }
 
@@ -583,6 +589,7 @@ sbp_status sbp_batch_create(const sbp_system_t *systems, int n, int autotune, vo
     sbp_system_s *S = systems[i];
     if (!S) return fail(SBP_ERR_ARG, "null member");
     if (!S->initialised) return fail(SBP_ERR_STATE, "member " + std::to_string(i) + " has not run sbp_mrab_init");
+    if (S->p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_ARG, "batches need fastest-first members");
     for (int j = 0; j < i; ++j)
       if (systems[j] == S) return fail(SBP_ERR_ARG, "a system appears twice in the batch");
     bool cf = !S->mh[S->fast()].cartesian;

@@ -229,6 +229,13 @@ cudaError_t launch_dt(const DevMesh &m, const Gas &g, const void *q, int dtype, 
                       cudaStream_t s);
 cudaError_t launch_metrics(const DevMesh &m, const double *x, const double *y, const double shift[4], void *met,
                            int dtype, cudaStream_t s);
+// out = q + sum_{k < nh} alpha[k] hist[k] (history order), FP64 accumulation, over n elements.
+struct ABCombine {
+  const void *hist[kMaxHist];
+  double alpha[kMaxHist];
+  int nh;
+};
+cudaError_t launch_ab_combine(const void *q, const ABCombine &c, void *out, size_t n, int dtype, cudaStream_t s);
 // y_out = y + c1 k1 + c2 k2 (k2 may be NULL), FP64 accumulation, over n elements.
 cudaError_t launch_axpy(const void *y, const void *k1, double c1, const void *k2, double c2, void *y_out, size_t n,
                         int dtype, cudaStream_t s);

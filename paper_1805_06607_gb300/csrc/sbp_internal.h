@@ -61,6 +61,11 @@ struct CoeffPlan {
   int order = 3, m = 3, sr = 1;
   std::vector<double> ab;                 // m: one step over [0, 1] on the nodes -(m-1)..0
   std::vector<std::vector<double>> ext;   // sr entries: slow extrapolant integrated over [0, j/sr]
+  // slowest-first variants: the fast extrapolant integrated over a whole macro step [0, sr]
+  // (units of the micro step), and the slow polynomial through the history ending one macro
+  // step later (nodes -(m-2)..1) integrated over [0, j/sr] (re-extrapolation)
+  std::vector<double> fext;
+  std::vector<std::vector<double>> rext;
 };
 
 // Host setup (sbp_setup.cpp).

@@ -385,6 +385,26 @@ cudaError_t launch_axpy(const void *y, const void *k1, double c1, const void *k2
 }
 
 
+// Adams-Bashforth state update without a new right-hand side (the slow step of the
+// slowest-first MRAB variants, whose newest history value already exists):
+// out = q + sum_k alpha_k hist_k in history order, FP64 accumulation.
+template <typename T>
+__global__ void k_ab_combine(const T *q, const ABCombine c, T *out, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    double acc = (double)q[t];
+    for (int k = 0; k < c.nh; ++k) acc += c.alpha[k] * (double)static_cast<const T *>(c.hist[k])[t];
+    out[t] = (T)acc;
+  }
+}
+
+cudaError_t launch_ab_combine(const void *q, const ABCombine &c, void *out, size_t n, int dtype, cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (dtype == SBP_F64) k_ab_combine<double><<<blocks, 256, 0, s>>>((const double *)q, c, (double *)out, n);
+  else k_ab_combine<float><<<blocks, 256, 0, s>>>((const float *)q, c, (float *)out, n);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------------
 // Element-type dispatch of the right-hand-side and batch launchers (instantiated per type in
 // their own translation units so that they compile in parallel).

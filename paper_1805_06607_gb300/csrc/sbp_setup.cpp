@@ -515,6 +515,18 @@ sbp_status build_plan(int order, int m, int sr, CoeffPlan &plan, std::string &er
       err = "singular moment system";
       return SBP_ERR_ARG;
     }
+  if (solve_ab_weights(nodes, 0.0, (double)sr, order, plan.fext) != SBP_OK) {
+    err = "singular moment system";
+    return SBP_ERR_ARG;
+  }
+  std::vector<double> later(m);
+  for (int k = 0; k < m; ++k) later[k] = nodes[k] + 1.0;
+  plan.rext.assign(sr, std::vector<double>(m, 0.0));
+  for (int j = 1; j < sr; ++j)
+    if (solve_ab_weights(later, 0.0, (double)j / sr, order, plan.rext[j]) != SBP_OK) {
+      err = "singular moment system";
+      return SBP_ERR_ARG;
+    }
   return SBP_OK;
 }
 

@@ -104,7 +104,7 @@ struct sbp_system_s {
   // parallel branches.
   bool use_graph = true;
   cudaStream_t cap = nullptr, side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_a = nullptr, ev_b = nullptr;
   std::map<uint64_t, cudaGraphExec_t> graphs;
   // FP64 workspace of the adjoint and tangent calls, per mesh (allocated on first use):
   // mu 8 planes, ld 6 planes, lp 3 planes, receiver values rv and their adjoint lrv (10 per
@@ -201,6 +201,8 @@ struct sbp_system_s {
     if (side) cudaStreamDestroy(side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_a) cudaEventDestroy(ev_a);
+    if (ev_b) cudaEventDestroy(ev_b);
   }
 
   bool viscous() const { return p.physics == SBP_NS; }
@@ -387,11 +389,137 @@ struct sbp_system_s {
     return a;
   }
 
+  cudaError_t ensure_capture_streams() {
+    cudaError_t e = cudaSuccess;
+    if (!cap) {
+      if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+      if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&ev_a, cudaEventDisableTiming)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&ev_b, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    return e;
+  }
+
+  // ---- slowest-first variants (sbp_params.scheme) ----------------------------------------------
+  // The slow right-hand side at the slow mesh's state q with receivers from the donor values in
+  // set 0 of its workspace, into the slow ring slot after head (mode 0; head unchanged).
+  cudaError_t slow_rhs_at(const void *q, cudaStream_t s) {
+    const int Sl = slow();
+    const MeshDev &d = md[Sl];
+    RhsLaunch a = rhs_args(Sl, q);
+    a.dv = d.dv;
+    a.didx = d.didx;
+    a.ndv = d.ndv;
+    a.mode = 0;
+    a.out = hist_slot(Sl, (d.head + 1) % plan.m);
+    return launch_rhs(a, p.dtype, viscous(), s);
+  }
+
+  // a_s at the current states (receivers from the fast mesh's current state), pushed into the
+  // slow ring: the slowest-first variants' first macro step needs the slow history to end at
+  // the current time.
+  cudaError_t slow_rhs_push(cudaStream_t s) {
+    const int Sl = slow(), F = fast();
+    cudaError_t e = donor_vals(Sl, md[F].q[md[F].cur], 0, 1, false, H, s);
+    if (e == cudaSuccess) e = slow_rhs_at(md[Sl].q[md[Sl].cur], s);
+    if (e == cudaSuccess) {
+      md[Sl].head = (md[Sl].head + 1) % plan.m;
+      md[Sl].count++;
+    }
+    return e;
+  }
+
+  // s(t + H) = s(t) + sum_k alpha_k H a_s,k over the m slow history values (oldest first).
+  cudaError_t slow_combine(const void *q_in, void *q_out, cudaStream_t s) {
+    const int Sl = slow(), m = plan.m;
+    ABCombine c{};
+    c.nh = m;
+    for (int k = 0; k < m; ++k) {
+      c.hist[k] = hist_slot(Sl, (md[Sl].head + 1 + k) % m);
+      c.alpha[k] = plan.ab[k] * H;
+    }
+    return launch_ab_combine(q_in, c, q_out, state_elems(Sl), p.dtype, s);
+  }
+
+  // One macro step of the slowest-first variants for the state at entry f(t), s(t), the fast
+  // ring ending at a_f(t - h), the slow ring ending at a_s(t):
+  //  fast chain: receivers' donor values (set 0 = s(t); without re-extrapolation every set from
+  //    the slow extrapolant of the ring ending at a_s(t)), micro step 0 (pushes a_f(t)), and,
+  //    once f^ is taken, micro steps 1..SR-1;
+  //  slow chain: s(t + H) by the slow extrapolant; after micro step 0, f^(t + H) = f(t) + the
+  //    fast extrapolant over the macro step at the slow receivers' donors; a_s(t + H) =
+  //    RHS(s(t + H), f^) pushed into the slow ring; with re-extrapolation, then the fast
+  //    receivers' sets 1..SR-1 from the slow ring ending at a_s(t + H).
+  // With `sd`, the fast chain runs on sd: without re-extrapolation the slow right-hand side
+  // and micro steps 1..SR-1 run side by side.
+  cudaError_t issue_step_sf(cudaStream_t s, cudaStream_t sd) {
+    const int F = fast(), Sl = slow(), sr = plan.sr, m = plan.m;
+    const bool rex = p.scheme == SBP_MRAB_SLOWEST_FIRST_REEXTRAPOLATE;
+    const double h = H / sr;
+    MeshDev saved_s = md[Sl], saved_f = md[F];
+    cudaError_t e = cudaSuccess;
+    auto run = [&](cudaError_t x) {
+      if (e == cudaSuccess) e = x;
+    };
+    cudaStream_t fs = sd ? sd : s;
+    void *s_t = md[Sl].q[md[Sl].cur], *s_new = md[Sl].q[1 - md[Sl].cur];
+    void *f_t = md[F].q[md[F].cur];
+    if (sd) {
+      run(cudaEventRecord(ev_fork, s));
+      run(cudaStreamWaitEvent(sd, ev_fork, 0));
+    }
+    run(timed(SBP_PHASE_INTERP_FAST, fs, [&] { return donor_vals(F, s_t, 0, rex ? 1 : sr, !rex, H, fs); }));
+    run(timed(SBP_PHASE_RHS_FAST, fs, [&] { return fused(F, 0, h, fs); }));
+    md[F].head = (md[F].head + 1) % m;
+    md[F].cur ^= 1;
+    if (sd) run(cudaEventRecord(ev_a, sd));
+    run(timed(SBP_PHASE_RHS_SLOW, s, [&] { return slow_combine(s_t, s_new, s); }));
+    if (sd) run(cudaStreamWaitEvent(s, ev_a, 0));
+    run(timed(SBP_PHASE_INTERP_SLOW, s, [&] {
+      DonorLaunch a = donor_args(Sl, f_t, 0, 1, false, h);
+      a.nb[0] = m;
+      for (int k = 0; k < m; ++k) a.beta[0][k] = plan.fext[k] * h;
+      return launch_donor_vals(a, p.dtype, viscous(), s);
+    }));
+    if (sd && !rex) run(cudaEventRecord(ev_b, s));
+    run(timed(SBP_PHASE_RHS_SLOW, s, [&] { return slow_rhs_at(s_new, s); }));
+    md[Sl].head = (md[Sl].head + 1) % m;
+    md[Sl].cur ^= 1;
+    if (rex && sr > 1)
+      run(timed(SBP_PHASE_INTERP_FAST, s, [&] {
+        DonorLaunch a = donor_args(F, s_t, 1, sr - 1, false, H);
+        for (int j = 0; j < sr - 1; ++j) {
+          a.nb[j] = m;
+          for (int k = 0; k < m; ++k) a.beta[j][k] = plan.rext[1 + j][k] * H;
+        }
+        return launch_donor_vals(a, p.dtype, viscous(), s);
+      }));
+    if (sd) {
+      if (rex) run(cudaEventRecord(ev_b, s));
+      run(cudaStreamWaitEvent(sd, ev_b, 0));
+    }
+    for (int j = 1; j < sr; ++j) {
+      run(timed(SBP_PHASE_RHS_FAST, fs, [&] { return fused(F, j, h, fs); }));
+      md[F].head = (md[F].head + 1) % m;
+      md[F].cur ^= 1;
+    }
+    if (sd) {
+      run(cudaEventRecord(ev_join, sd));
+      run(cudaStreamWaitEvent(s, ev_join, 0));
+    }
+    md[Sl] = saved_s;
+    md[F] = saved_f;
+    return e;
+  }
+
   // Enqueue one macro step (Sec. 3.3) for the current ring heads and state buffers, without
   // changing them. With `side` set, the slow right-hand side and the first fast micro step
   // (which needs only s(t) and f(t)) run on two streams joined before the second micro step.
   // frec (eager mode only): the fast state before micro step j is copied to frec[j].
   cudaError_t issue_step(cudaStream_t s, cudaStream_t sd, void *const *frec = nullptr) {
+    if (p.scheme != SBP_MRAB_FASTEST_FIRST) return issue_step_sf(s, sd);
     const int F = fast(), Sl = slow(), sr = plan.sr;
     const double h = H / sr;
     MeshDev saved_s = md[Sl], saved_f = md[F];
@@ -445,7 +573,7 @@ struct sbp_system_s {
   }
 
   // Autotuner of the right-hand side's kernel and block shape: for each mesh, time the
-  // right-hand side (mode 0, into the history slot the next push overwrites) on the bound state
+  // right-hand side (mode 0, into the state buffer the next step overwrites) on the bound state
   // with the split kernels at 8, 16 and 32 rows per CTA and with the marching kernel (strips of
   // 64 columns) at chunks of 16, 32, 64 and 128 rows, and keep the fastest.
   bool autotune_on = true;
@@ -460,7 +588,7 @@ struct sbp_system_s {
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       MeshDev &d = md[k];
       if (!d.hist) continue;
-      void *scratch = hist_slot(k, (d.head + 1) % plan.m);
+      void *scratch = d.q[1 - d.cur];  // the buffer the next step writes
       e = interp(k, md[1 - k].q[md[1 - k].cur], nullptr, nullptr, 0, s);
       float best = 1e30f;
       Cand best_c{d.strip, d.strip ? d.chunk : d.rows_per_cta};
@@ -599,12 +727,7 @@ struct sbp_system_s {
       if (!rk_graph || rk_graph_h != h || rk_graph_cur != key) {
         if (rk_graph) cudaGraphExecDestroy(rk_graph);
         rk_graph = nullptr;
-        if (!cap) {
-          if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
-          if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) return e;
-          if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
-          if ((e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
-        }
+        if ((e = ensure_capture_streams()) != cudaSuccess) return e;
         if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
         cudaError_t ei = issue_rk4(h, cap);
         cudaGraph_t g = nullptr;
@@ -637,12 +760,7 @@ struct sbp_system_s {
     auto it = graphs.find(key);
     if (it == graphs.end()) {
       cudaError_t e;
-      if (!cap) {
-        if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
-        if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) return e;
-        if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
-        if ((e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
-      }
+      if ((e = ensure_capture_streams()) != cudaSuccess) return e;
       if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
       cudaError_t ei = issue_step(cap, side);
       cudaGraph_t g = nullptr;

@@ -1,0 +1,120 @@
+"""The slowest-first MRAB variants of Sec. 3.3's design choices on the GPU path, against the
+oracle's macro steps (oracle.mrab_macro_step_slowest_first): 1e-12 relative in FP64, 1e-5 in
+FP32; CUDA-graph replay (slow right-hand side and fast micro steps on parallel branches) equal
+to kernel-by-kernel launches; at step ratio 1 every ordering is single-rate AB, bit for bit."""
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import build_library
+from oracle import OracleSystem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SCHEMES = ["slowest_first", "slowest_first_reextrapolate"]
+
+
+@pytest.fixture(scope="module")
+def sbp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build_library()
+    import paper_1805_06607_gb300 as mod
+    return mod
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def with_scheme(wl, scheme):
+    return dict(wl, params=dict(wl["params"], scheme=scheme))
+
+
+CASES = {
+    "vortex": lambda: W.vortex_box_in_box(seed=31),
+    "vortex_sr3_ab34": lambda: W.vortex_box_in_box(seed=32, n_bg=48, n_fine=33, step_ratio=3, hist_len=4),
+    "cylinder": lambda: W.cylinder_small(seed=33),
+}
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_variant_matches_oracle_fp64(sbp, case, scheme):
+    wl = with_scheme(CASES[case](), scheme)
+    ref = OracleSystem(wl)
+    H = ref.macro_step_size(wl["q0"])
+    y, hf, hs = ref.bootstrap(wl["q0"], H)
+    n = 4
+    want, _, _ = ref.mrab(y, hf, hs, H, n, scheme=scheme)
+    g = sbp.System(wl)
+    g.bind(wl["q0"])
+    g.mrab_init(H)
+    g.mrab_step(n)
+    g.check()
+    for k in range(2):
+        got = g.to_host(k, g.current_state(k))
+        e = rel(got, want[k])
+        assert e < 1e-12, (k, e)
+    g.close()
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_variant_fp32(sbp, scheme):
+    wl = with_scheme(CASES["cylinder"](), scheme)
+    ref = OracleSystem(wl)
+    H = ref.macro_step_size(wl["q0"])
+    y, hf, hs = ref.bootstrap(wl["q0"], H)
+    want, _, _ = ref.mrab(y, hf, hs, H, 3, scheme=scheme)
+    g = sbp.System(wl, dtype="f32")
+    g.bind(wl["q0"])
+    g.mrab_init(H)
+    g.mrab_step(3)
+    g.check()
+    for k in range(2):
+        assert rel(g.to_host(k, g.current_state(k)), want[k]) < 1e-5
+    g.close()
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_variant_graph_matches_eager(sbp, scheme):
+    wl = with_scheme(CASES["vortex_sr3_ab34"](), scheme)
+    out = []
+    for graphs in (False, True):
+        g = sbp.System(wl)
+        g.use_graphs(graphs)
+        g.bind(wl["q0"])
+        g.mrab_init()
+        g.mrab_step(9)
+        g.check()
+        out.append([g.to_host(k, g.current_state(k)) for k in range(2)])
+        g.close()
+    for k in range(2):
+        assert np.array_equal(out[0][k], out[1][k])
+
+
+def test_step_ratio_one_orderings_agree(sbp):
+    base = W.vortex_box_in_box(seed=34, n_bg=40, n_fine=25, step_ratio=1)
+    out = {}
+    for scheme in ["fastest_first"] + SCHEMES:
+        g = sbp.System(with_scheme(base, scheme))
+        g.bind(base["q0"])
+        g.mrab_init()
+        g.mrab_step(5)
+        g.check()
+        out[scheme] = [g.to_host(k, g.current_state(k)) for k in range(2)]
+        g.close()
+    for scheme in SCHEMES:
+        for k in range(2):
+            assert np.array_equal(out[scheme][k], out["fastest_first"][k]), scheme
+
+
+def test_variant_state_record_refused(sbp):
+    wl = with_scheme(CASES["vortex"](), "slowest_first")
+    g = sbp.System(wl)
+    g.bind(wl["q0"])
+    g.mrab_init()
+    with pytest.raises(RuntimeError):
+        g.get_state()
+    g.close()

@@ -5,11 +5,13 @@ two-component linear ODE (Sec. 3.3), and the performance model of Sec. 6.1."""
 import math
 
 import numpy as np
+import pytest
 import scipy.linalg
 
 import workloads as W
 from conftest import golden
-from oracle import OracleSystem, ab_coefficients, mrab_macro_step, rk3_heun_step, rk4_step, srab_step
+from oracle import (OracleSystem, ab_coefficients, mrab_macro_step, mrab_macro_step_slowest_first,
+                    rk3_heun_step, rk4_step, srab_step)
 
 
 def test_ab_textbook():
@@ -91,6 +93,78 @@ def test_mrab_order_linear_ode():
         errs.append(math.hypot(f - e[0], s - e[1]))
     eocs = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
     assert all(2.9 < e < 3.15 for e in eocs), eocs
+
+
+@pytest.mark.parametrize("reextrapolate", [False, True])
+def test_slowest_first_sr1_equals_srab(reextrapolate):
+    """At step ratio 1 the extrapolated fast state is the fast update itself, so both
+    slowest-first variants reduce to single-rate AB, bit for bit."""
+    wl = W.vortex_box_in_box(seed=4, n_bg=32, n_fine=21, step_ratio=1)
+    S = OracleSystem(wl)
+    H = S.macro_step_size(wl["q0"])
+    y, hf, hs = S.bootstrap(wl["q0"], H)
+    scheme = "slowest_first_reextrapolate" if reextrapolate else "slowest_first"
+    out, _, _ = S.mrab(y, hf, hs, H, 3, scheme=scheme)
+    hist = [[hs[k], hf[k]] for k in range(3)]
+    z = [y[0], y[1]]
+    for _ in range(3):
+        z, hist = srab_step(z, hist, H, 3, S.rhs_all)
+    assert np.array_equal(out[0], z[0]) and np.array_equal(out[1], z[1])
+
+
+@pytest.mark.parametrize("scheme", ["fastest_first", "slowest_first", "slowest_first_reextrapolate"])
+def test_mrab_variants_exact_on_polynomial_chain(scheme):
+    """A coupled chain whose right-hand sides are polynomials of degree <= 2 in time along the
+    exact solution: s1' = 1, s2' = s1, s4' = s2, f' = s2, s3' = f - s4, from zero (s1 = t,
+    s2 = t^2/2, s4 = f = t^3/6, s3 = 0). Third-order MRAB integrates it exactly in every
+    variant, but only with the right extrapolation weights: the fast micro steps need the slow
+    extrapolant (or re-extrapolant) of s2 at the micro times, and s3 stays 0 only if the
+    extrapolated fast state at t+H (slowest-first) or the fast state itself is exact."""
+    sr, H = 3, 0.1
+    h = H / sr
+    ex_s = lambda t: np.array([t, t * t / 2, 0.0, t ** 3 / 6])  # noqa: E731
+    ex_f = lambda t: np.array([t ** 3 / 6])  # noqa: E731
+    rhs_s = lambda ss, ff: np.array([1.0, ss[0], ff[0] - ss[3], ss[1]])  # noqa: E731
+    rhs_f = lambda ff, ss: np.array([ss[1]])  # noqa: E731
+    t0 = 0.4
+    hf = [rhs_f(ex_f(t0 - k * h), ex_s(t0 - k * h)) for k in (2, 1, 0)]
+    hs = [rhs_s(ex_s(t0 - k * H), ex_f(t0 - k * H)) for k in (2, 1, 0)]
+    f, s = ex_f(t0), ex_s(t0)
+    n = 7
+    for _ in range(n):
+        if scheme == "fastest_first":
+            f, s, hf, hs = mrab_macro_step(f, s, hf, hs, H, sr, 3, rhs_fast=rhs_f, rhs_slow=rhs_s)
+        else:
+            f, s, hf, hs = mrab_macro_step_slowest_first(f, s, hf, hs, H, sr, 3, rhs_fast=rhs_f, rhs_slow=rhs_s,
+                                                         reextrapolate=scheme.endswith("reextrapolate"))
+    T = t0 + n * H
+    assert np.abs(f - ex_f(T)).max() < 1e-13
+    assert np.abs(s - ex_s(T)).max() < 1e-13
+
+
+@pytest.mark.parametrize("reextrapolate", [False, True])
+def test_slowest_first_order_linear_ode(reextrapolate):
+    lf, ls, c = 10.0, 1.0, 0.5
+    A = np.array([[-lf, c], [c, -ls]])
+    y0 = np.array([1.0, 0.5])
+    T = 1.0
+    errs = []
+    for n in (80, 160, 320):
+        H = T / n
+        sr = 3
+        h = H / sr
+        ex = lambda t: scipy.linalg.expm(A * t) @ y0  # noqa: E731
+        hf = [A[0] @ ex(-k * h) for k in (2, 1, 0)]
+        hs = [A[1] @ ex(-k * H) for k in (2, 1, 0)]
+        f, s = y0[0], y0[1]
+        for _ in range(n):
+            f, s, hf, hs = mrab_macro_step_slowest_first(
+                f, s, hf, hs, H, sr, 3, rhs_fast=lambda ff, ss: A[0, 0] * ff + A[0, 1] * ss,
+                rhs_slow=lambda ss, ff: A[1, 0] * ff + A[1, 1] * ss, reextrapolate=reextrapolate)
+        e = ex(T)
+        errs.append(math.hypot(f - e[0], s - e[1]))
+    eocs = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(2.85 < e < 3.2 for e in eocs), eocs
 
 
 def test_rk3_order():
