@@ -190,6 +190,15 @@ sbp_status sbp_mrab_init(sbp_system_t sys, double H, void *stream);
  * slow RHS at the bootstrap's end time for these. */
 sbp_status sbp_mrab_step(sbp_system_t sys, int n, void *stream);
 
+/* Change the macro step to H (> 0) for the following macro steps (Sec. 3.3 Step 1: H_i may
+ * change from one macro step to the next, h_i = H_i / step_ratio). While the histories still
+ * hold values at the old spacing (the next hist_len - 1 macro steps), every Adams-Bashforth
+ * and extrapolation weight is solved on the history's node times (the moment conditions of
+ * Sec. 3.1 with the nodes shifted to the start of the interval and scaled by its step) and the
+ * steps are launched kernel by kernel; then CUDA-graph replay resumes with the plan's weights
+ * times the new H. Fastest-first systems after sbp_mrab_init only (SBP_ERR_STATE). */
+sbp_status sbp_mrab_set_step(sbp_system_t sys, double H);
+
 /* Whether sbp_mrab_step replays CUDA graphs (default 1) or launches kernel by kernel (0).
  * With graphs, each macro step is one graph launch on the caller's stream: the graph is
  * captured once per ring/buffer phase (at most 4 hist_len^2 of them, on first use) and runs

@@ -86,8 +86,9 @@ def lib():
 
 
 from .system import (OracleSystem, ab_coefficients, mrab_macro_step, mrab_macro_step_slowest_first,  # noqa: E402
-                     rk3_heun_step, rk4_step, srab_step, l2_norm)
+                     mrab_macro_step_var, rk3_heun_step, rk4_step, srab_step, l2_norm)
 from .system3d import OracleSystem3D  # noqa: E402
 
 __all__ = ["build", "lib", "OracleSystem", "OracleSystem3D", "ab_coefficients", "mrab_macro_step",
-           "mrab_macro_step_slowest_first", "rk3_heun_step", "rk4_step", "srab_step", "l2_norm"]
+           "mrab_macro_step_slowest_first", "mrab_macro_step_var", "rk3_heun_step", "rk4_step", "srab_step",
+           "l2_norm"]

@@ -110,6 +110,31 @@ def mrab_macro_step(f, s, hist_f, hist_s, H, sr, order, rhs_fast, rhs_slow):
     return f, s, hist_f, hist_s
 
 
+def mrab_macro_step_var(f, s, hist_f, times_f, hist_s, times_s, t, H, sr, order, rhs_fast, rhs_slow):
+    """Fastest-first MRAB macro step [t, t+H] for histories at arbitrary past times (the macro
+    step may change from one macro step to the next, Sec. 3.3 Step 1): every weight solves the
+    moment conditions on the actual node times, shifted to the start of the interval it
+    integrates and scaled by its step, so that uniform histories give mrab_macro_step's
+    weights. times_f, times_s: the node times of hist_f, hist_s (oldest first, ending at t).
+    Returns the states and histories (with their times) at t+H."""
+    h = H / sr
+    tf = np.asarray(times_f, dtype=np.float64)
+    ts = np.asarray(times_s, dtype=np.float64)
+    hist_f = list(hist_f)
+    for j in range(sr):
+        tj = t + j * h
+        f = _combine(f, ab_coefficients((tf - tj) / h, 0.0, 1.0, order) * h, hist_f)
+        if j < sr - 1:
+            beta = ab_coefficients((ts - t) / H, 0.0, (j + 1) / sr, order) * H
+            s_hat = _combine(s, beta, hist_s)
+            hist_f = hist_f[1:] + [rhs_fast(f, s_hat)]
+            tf = np.append(tf[1:], t + (j + 1) * h)
+    s = _combine(s, ab_coefficients((ts - t) / H, 0.0, 1.0, order) * H, hist_s)
+    hist_f = hist_f[1:] + [rhs_fast(f, s)]
+    hist_s = list(hist_s[1:]) + [rhs_slow(s, f)]
+    return f, s, hist_f, np.append(tf[1:], t + H), hist_s, np.append(ts[1:], t + H)
+
+
 def mrab_macro_step_slowest_first(f, s, hist_f, hist_s, H, sr, order, rhs_fast, rhs_slow, reextrapolate=False):
     """One macro step of the slowest-first MRAB variants, the other ordering of Sec. 3.3's
     design choices (the paper's runs use fastest-first; the variants follow its description of
@@ -438,6 +463,27 @@ class OracleSystem:
         for _ in range(n_steps):
             y = rk4_step(y, h, self.rhs_all)
         return y
+
+    def mrab_var(self, qs, hist_f, hist_s, H0, steps):
+        """Fastest-first MRAB with a macro step that changes between macro steps: the
+        histories come from bootstrap(qs, H0) (node times -(m-1)..0 in units of its micro and
+        macro step), then one macro step per entry of `steps`."""
+        sr = int(self.p["step_ratio"])
+        order = int(self.p["order"])
+        m = len(hist_f)
+        h0 = H0 / sr
+        tf = np.array([(k - (m - 1)) * h0 for k in range(m)])
+        ts = np.array([(k - (m - 1)) * H0 for k in range(m)])
+        f, s, t = qs[self.fast], qs[self.slow], 0.0
+        for H in steps:
+            f, s, hist_f, tf, hist_s, ts = mrab_macro_step_var(
+                f, s, hist_f, tf, hist_s, ts, t, H, sr, order,
+                rhs_fast=lambda ff, ss: self.coupled_rhs(self.fast, ff, ss),
+                rhs_slow=lambda ss, ff: self.coupled_rhs(self.slow, ss, ff))
+            t = t + H
+        out = [None, None]
+        out[self.fast], out[self.slow] = f, s
+        return out
 
     def cell_sizes(self):
         """Cell size per point for eq. (l2error): J^-1 (= dx dy on Cartesian meshes), holes 0."""

@@ -88,6 +88,7 @@ _SIGS = {
     "sbp_mrab_step": [_P, _I, _P],
     "sbp_mrab_time": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "sbp_rk4_step": [_P, _I, _D, _P],
+    "sbp_mrab_set_step": [_P, _D],
     "sbp_check": [_P, _P],
     "sbp_profile_enable": [_P, _I],
     "sbp_use_graphs": [_P, _I],
@@ -310,6 +311,11 @@ class System:
 
     def mrab_step(self, n=1, stream=None):
         _check(_lib.sbp_mrab_step(self.h, int(n), _stream(stream)), "sbp_mrab_step")
+
+    def mrab_set_step(self, H):
+        """Macro step H for the following macro steps (weights solved on the history's node
+        times until the histories are uniform in H again)."""
+        _check(_lib.sbp_mrab_set_step(self.h, float(H)), "sbp_mrab_set_step")
 
     def rk4_step(self, n, h, stream=None):
         """n classical Runge-Kutta steps of size h on both meshes (single rate), in place on the

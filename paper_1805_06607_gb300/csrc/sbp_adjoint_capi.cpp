@@ -571,6 +571,7 @@ sbp_status sbp_adjoint_probe(sbp_system_t S, const sbp_adjoint_desc *desc, const
   CUDA_TRY(cudaMemcpyAsync(A.q[1][0], q0_mesh1, A.n[1] * 8, cudaMemcpyDeviceToDevice, s));
   S->H = A.H;
   S->t = 0.0;
+  S->var_left = 0;
   CUDA_TRY(upload(A.d_base, ps.base.data(), ps.base.size() * sizeof(int)));
   A.allocs.push_back(A.d_base);
   CUDA_TRY(upload(A.d_w, ps.w.data(), ps.w.size() * sizeof(double)));

@@ -307,6 +307,7 @@ sbp_status sbp_mrab_init(sbp_system_t S, double H, void *stream) {
   if (e != cudaSuccess) return fail(SBP_ERR_CUDA, std::string("bootstrap: ") + cudaGetErrorString(e));
   S->H = H;
   S->t = 0.0;
+  S->var_left = 0;
   S->initialised = true;
   S->clear_graphs();
   if (S->autotune_on) CUDA_TRY(S->autotune(s));
@@ -348,9 +349,29 @@ sbp_status sbp_mrab_step(sbp_system_t S, int n, void *stream) {
   if (!S->initialised) return fail(SBP_ERR_STATE, "sbp_mrab_init has not run");
   cudaStream_t s = (cudaStream_t)stream;
   for (int step = 0; step < n; ++step) {
-    if (S->use_graph && !S->prof) CUDA_TRY(S->launch_step_graph(s));
-    else CUDA_TRY(S->issue_step(s, nullptr));
+    if (S->var_left > 0) {
+      sbp_system_s::StepCoef c;
+      if (!S->step_coef(c)) return fail(SBP_ERR_ARG, "singular moment system for the history's node times");
+      CUDA_TRY(S->issue_step(s, nullptr, nullptr, &c));
+      S->var_left--;
+    } else if (S->use_graph && !S->prof) {
+      CUDA_TRY(S->launch_step_graph(s));
+    } else {
+      CUDA_TRY(S->issue_step(s, nullptr));
+    }
     S->advance();
+  }
+  return SBP_OK;
+}
+
+sbp_status sbp_mrab_set_step(sbp_system_t S, double H) {
+  if (!S || !(H > 0.0) || !std::isfinite(H)) return fail(SBP_ERR_ARG, "bad argument");
+  if (!S->initialised) return fail(SBP_ERR_STATE, "sbp_mrab_init has not run");
+  if (S->p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_STATE, "fastest-first systems only");
+  if (H != S->H) {
+    S->H = H;
+    S->var_left = S->plan.m - 1;  // until the histories hold m values spaced by the new step
+    S->clear_graphs();
   }
   return SBP_OK;
 }

@@ -89,6 +89,11 @@ struct sbp_system_s {
   unsigned long long *d_dt = nullptr;
   double H = 0.0, t = 0.0;
   bool initialised = false;
+  // Node times of the history entries per mesh and ring slot (time since the end of the
+  // bootstrap), and the number of coming macro steps whose histories are not uniform in the
+  // current H (after sbp_mrab_set_step): those take weights solved on the node times.
+  double tnode[2][kMaxHist] = {};
+  int var_left = 0;
   // phase timers
   bool prof = false;
   struct Pending {
@@ -358,6 +363,45 @@ struct sbp_system_s {
     return a;
   }
 
+  // Adams-Bashforth weights of one fastest-first macro step solved on the history's node times
+  // (macro steps that change H, Sec. 3.3 Step 1), already multiplied by their steps: the slow
+  // update, the slow extrapolation sets, and the update of each fast micro step. The nodes of
+  // each weight set are shifted to the start of the interval it integrates and scaled by its
+  // step, so that a uniform history gives the plan's weights.
+  struct StepCoef {
+    double as[kMaxHist];
+    double ext[kMaxSets][kMaxHist];
+    double af[kMaxSets][kMaxHist];
+  };
+  bool step_coef(StepCoef &c) const {
+    const int F = fast(), Sl = slow(), m = plan.m, sr = plan.sr, n = plan.order;
+    const double h = H / sr;
+    std::vector<double> rel(m), w;
+    const int hs = (md[Sl].head + 1) % m;  // the slot a_s(t) is pushed into
+    for (int k = 0; k < m; ++k) {
+      const int slot = (hs + 1 + k) % m;
+      rel[k] = ((slot == hs ? t : tnode[Sl][slot]) - t) / H;
+    }
+    if (solve_ab_weights(rel, 0.0, 1.0, n, w) != SBP_OK) return false;
+    for (int k = 0; k < m; ++k) c.as[k] = w[k] * H;
+    for (int j = 1; j < sr; ++j) {
+      if (solve_ab_weights(rel, 0.0, (double)j / sr, n, w) != SBP_OK) return false;
+      for (int k = 0; k < m; ++k) c.ext[j][k] = w[k] * H;
+    }
+    double ring[kMaxHist];
+    for (int k = 0; k < m; ++k) ring[k] = tnode[F][k];
+    int hf = md[F].head;
+    for (int j = 0; j < sr; ++j) {
+      const double tj = t + j * h;
+      hf = (hf + 1) % m;
+      ring[hf] = tj;
+      for (int k = 0; k < m; ++k) rel[k] = (ring[(hf + 1 + k) % m] - tj) / h;
+      if (solve_ab_weights(rel, 0.0, 1.0, n, w) != SBP_OK) return false;
+      for (int k = 0; k < m; ++k) c.af[j][k] = w[k] * h;
+    }
+    return true;
+  }
+
   cudaError_t donor_vals(int recv, const void *q, int set0, int nsets, bool extrapolate, double Hh,
                          cudaStream_t s) {
     return launch_donor_vals(donor_args(recv, q, set0, nsets, extrapolate, Hh), p.dtype, viscous(), s);
@@ -365,11 +409,12 @@ struct sbp_system_s {
 
   // Fused right-hand side + Adams-Bashforth update of mesh k with step dt, receivers gathered
   // from donor-value set `set`. Pushes the new right-hand side into the ring slot after head.
-  cudaError_t fused(int k, int set, double dt, cudaStream_t s) {
-    return launch_rhs(fused_args(k, set, dt), p.dtype, viscous(), s);
+  cudaError_t fused(int k, int set, double dt, cudaStream_t s, const double *alpha = nullptr) {
+    return launch_rhs(fused_args(k, set, dt, alpha), p.dtype, viscous(), s);
   }
 
-  RhsLaunch fused_args(int k, int set, double dt) const {
+  // alpha: the m weights (oldest first, multiplied by the step) instead of the plan's
+  RhsLaunch fused_args(int k, int set, double dt, const double *alpha = nullptr) const {
     const int m = plan.m;
     const MeshDev &d = md[k];
     int slot = (d.head + 1) % m;
@@ -383,9 +428,9 @@ struct sbp_system_s {
     a.nold = m - 1;
     for (int j = 0; j < m - 1; ++j) {
       a.hold[j] = hist_slot(k, (slot + 1 + j) % m);
-      a.alpha[j] = plan.ab[j] * dt;
+      a.alpha[j] = alpha ? alpha[j] : plan.ab[j] * dt;
     }
-    a.alpha[m - 1] = plan.ab[m - 1] * dt;
+    a.alpha[m - 1] = alpha ? alpha[m - 1] : plan.ab[m - 1] * dt;
     return a;
   }
 
@@ -427,6 +472,7 @@ struct sbp_system_s {
     if (e == cudaSuccess) {
       md[Sl].head = (md[Sl].head + 1) % plan.m;
       md[Sl].count++;
+      tnode[Sl][md[Sl].head] = t;
     }
     return e;
   }
@@ -518,7 +564,7 @@ struct sbp_system_s {
   // changing them. With `side` set, the slow right-hand side and the first fast micro step
   // (which needs only s(t) and f(t)) run on two streams joined before the second micro step.
   // frec (eager mode only): the fast state before micro step j is copied to frec[j].
-  cudaError_t issue_step(cudaStream_t s, cudaStream_t sd, void *const *frec = nullptr) {
+  cudaError_t issue_step(cudaStream_t s, cudaStream_t sd, void *const *frec = nullptr, const StepCoef *cf = nullptr) {
     if (p.scheme != SBP_MRAB_FASTEST_FIRST) return issue_step_sf(s, sd);
     const int F = fast(), Sl = slow(), sr = plan.sr;
     const double h = H / sr;
@@ -536,13 +582,18 @@ struct sbp_system_s {
     }
     // slow: receivers from f(t), fused RHS + update into the other buffer
     run(timed(SBP_PHASE_INTERP_SLOW, s, [&] { return donor_vals(Sl, md[F].q[md[F].cur], 0, 1, false, H, s); }));
-    run(timed(SBP_PHASE_RHS_SLOW, s, [&] { return fused(Sl, 0, H, s); }));
+    run(timed(SBP_PHASE_RHS_SLOW, s, [&] { return fused(Sl, 0, H, s, cf ? cf->as : nullptr); }));
     md[Sl].head = (md[Sl].head + 1) % plan.m;
     // fast receivers for the micro steps that need the slow extrapolant (a_s(t) is now in the ring)
     int first = sd ? 1 : 0;
     if (sr > first)
-      run(timed(SBP_PHASE_INTERP_FAST, s,
-                [&] { return donor_vals(F, md[Sl].q[md[Sl].cur], first, sr - first, true, H, s); }));
+      run(timed(SBP_PHASE_INTERP_FAST, s, [&] {
+        DonorLaunch a = donor_args(F, md[Sl].q[md[Sl].cur], first, sr - first, true, H);
+        if (cf)
+          for (int j = 0; j < sr - first; ++j)
+            for (int k = 0; k < plan.m; ++k) a.beta[j][k] = cf->ext[first + j][k];
+        return launch_donor_vals(a, p.dtype, viscous(), s);
+      }));
     if (sd) {
       md[F].head = (md[F].head + 1) % plan.m;
       md[F].cur ^= 1;
@@ -552,7 +603,7 @@ struct sbp_system_s {
     for (int j = first; j < sr; ++j) {
       if (frec)
         run(cudaMemcpyAsync(frec[j], md[F].q[md[F].cur], state_elems(F) * esz, cudaMemcpyDeviceToDevice, s));
-      run(timed(SBP_PHASE_RHS_FAST, s, [&] { return fused(F, j, h, s); }));
+      run(timed(SBP_PHASE_RHS_FAST, s, [&] { return fused(F, j, h, s, cf ? cf->af[j] : nullptr); }));
       md[F].head = (md[F].head + 1) % plan.m;
       md[F].cur ^= 1;
     }
@@ -565,9 +616,12 @@ struct sbp_system_s {
   void advance() {
     md[slow()].head = (md[slow()].head + 1) % plan.m;
     md[slow()].cur ^= 1;
+    // a_s(t); the slowest-first orderings push a_s(t + H)
+    tnode[slow()][md[slow()].head] = p.scheme == SBP_MRAB_FASTEST_FIRST ? t : t + H;
     for (int j = 0; j < plan.sr; ++j) {
       md[fast()].head = (md[fast()].head + 1) % plan.m;
       md[fast()].cur ^= 1;
+      tnode[fast()][md[fast()].head] = t + j * (H / plan.sr);
     }
     t += H;
   }
@@ -656,12 +710,14 @@ struct sbp_system_s {
         d.head = (d.head + 1) % m;
         d.count++;
         k1[F] = hist_slot(F, d.head);
+        tnode[F][d.head] = (double)(step - nsteps) * h;
       }
       if (rec_s) {
         MeshDev &d = md[Sl];
         d.head = (d.head + 1) % m;
         d.count++;
         k1[Sl] = hist_slot(Sl, d.head);
+        tnode[Sl][d.head] = (double)((step - nsteps) / sr) * Hm;
       }
       for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = rhs_plain(k, y[k], y[1 - k], k1[k], s);
       for (int k = 0; k < 2 && e == cudaSuccess; ++k)

@@ -118,3 +118,31 @@ def test_variant_state_record_refused(sbp):
     with pytest.raises(RuntimeError):
         g.get_state()
     g.close()
+
+
+@pytest.mark.parametrize("case", ["vortex", "vortex_sr3_ab34", "cylinder"])
+def test_variable_macro_step_matches_oracle(sbp, case):
+    """The macro step changes between macro steps (Sec. 3.3 Step 1): weights solved on the
+    history's node times while it is not uniform, then the plan's weights again."""
+    wl = CASES[case]()
+    ref = OracleSystem(wl)
+    H0 = ref.macro_step_size(wl["q0"])
+    y, hf, hs = ref.bootstrap(wl["q0"], H0)
+    steps = [H0, 0.7 * H0, 0.7 * H0, 1.1 * H0, 1.1 * H0, 1.1 * H0, 1.1 * H0, 1.1 * H0]
+    want = ref.mrab_var(y, hf, hs, H0, steps)
+    fixed, _, _ = ref.mrab(y, hf, hs, H0, len(steps))
+    g = sbp.System(wl)
+    g.bind(wl["q0"])
+    g.mrab_init(H0)
+    for Hi in steps:
+        g.mrab_set_step(Hi)
+        g.mrab_step(1)
+    g.check()
+    Hg, t = g.mrab_time()
+    assert Hg == steps[-1] and t == pytest.approx(sum(steps))
+    for k in range(2):
+        got = g.to_host(k, g.current_state(k))
+        assert rel(got, want[k]) < 1e-12, (k, rel(got, want[k]))
+        # and the run is not the fixed-step one
+        assert rel(want[k], fixed[k]) > 1e-9
+    g.close()

@@ -11,7 +11,7 @@ import scipy.linalg
 import workloads as W
 from conftest import golden
 from oracle import (OracleSystem, ab_coefficients, mrab_macro_step, mrab_macro_step_slowest_first,
-                    rk3_heun_step, rk4_step, srab_step)
+                    mrab_macro_step_var, rk3_heun_step, rk4_step, srab_step)
 
 
 def test_ab_textbook():
@@ -140,6 +140,74 @@ def test_mrab_variants_exact_on_polynomial_chain(scheme):
     T = t0 + n * H
     assert np.abs(f - ex_f(T)).max() < 1e-13
     assert np.abs(s - ex_s(T)).max() < 1e-13
+
+
+def _chain():
+    ex_s = lambda t: np.array([t, t * t / 2, 0.0, t ** 3 / 6])  # noqa: E731
+    ex_f = lambda t: np.array([t ** 3 / 6])  # noqa: E731
+    rhs_s = lambda ss, ff: np.array([1.0, ss[0], ff[0] - ss[3], ss[1]])  # noqa: E731
+    rhs_f = lambda ff, ss: np.array([ss[1]])  # noqa: E731
+    return ex_s, ex_f, rhs_s, rhs_f
+
+
+def test_variable_macro_step_exact_on_polynomial_chain():
+    """Changing H between macro steps (Sec. 3.3 Step 1): with the weights solved on the actual
+    node times, third-order MRAB stays exact on the polynomial chain for any step sequence."""
+    ex_s, ex_f, rhs_s, rhs_f = _chain()
+    sr, H0, t = 3, 0.1, 0.4
+    h0 = H0 / sr
+    tf = np.array([t - 2 * h0, t - h0, t])
+    ts = np.array([t - 2 * H0, t - H0, t])
+    hf = [rhs_f(ex_f(x), ex_s(x)) for x in tf]
+    hs = [rhs_s(ex_s(x), ex_f(x)) for x in ts]
+    f, s = ex_f(t), ex_s(t)
+    for H in (0.1, 0.07, 0.07, 0.13, 0.05, 0.1, 0.1):
+        f, s, hf, tf, hs, ts = mrab_macro_step_var(f, s, hf, tf, hs, ts, t, H, sr, 3, rhs_fast=rhs_f, rhs_slow=rhs_s)
+        t += H
+    assert np.abs(f - ex_f(t)).max() < 1e-13
+    assert np.abs(s - ex_s(t)).max() < 1e-13
+
+
+def test_variable_macro_step_uniform_equals_fixed():
+    """With a constant H the variable-step weights are the fixed-step ones: the same states to
+    rounding of the node offsets."""
+    wl = W.vortex_box_in_box(seed=5, n_bg=32, n_fine=21)
+    S = OracleSystem(wl)
+    H = S.macro_step_size(wl["q0"])
+    y, hf, hs = S.bootstrap(wl["q0"], H)
+    a, _, _ = S.mrab(y, hf, hs, H, 3)
+    b = S.mrab_var(y, hf, hs, H, [H, H, H])
+    for k in range(2):
+        assert np.abs(a[k] - b[k]).max() <= 1e-13 * np.abs(a[k]).max()
+
+
+def test_variable_macro_step_order_linear_ode():
+    """Third order on the two-component linear ODE with macro steps alternating between H and
+    0.6 H."""
+    lf, ls, c = 10.0, 1.0, 0.5
+    A = np.array([[-lf, c], [c, -ls]])
+    y0 = np.array([1.0, 0.5])
+    errs = []
+    for n in (80, 160, 320):
+        H = 1.0 / n
+        sr = 3
+        h = H / sr
+        ex = lambda t: scipy.linalg.expm(A * t) @ y0  # noqa: E731
+        tf = np.array([-2 * h, -h, 0.0])
+        ts = np.array([-2 * H, -H, 0.0])
+        hf = [A[0] @ ex(x) for x in tf]
+        hs = [A[1] @ ex(x) for x in ts]
+        f, s, t = y0[0], y0[1], 0.0
+        for i in range(n):
+            Hi = H if i % 2 == 0 else 0.6 * H
+            f, s, hf, tf, hs, ts = mrab_macro_step_var(
+                f, s, hf, tf, hs, ts, t, Hi, sr, 3, rhs_fast=lambda ff, ss: A[0, 0] * ff + A[0, 1] * ss,
+                rhs_slow=lambda ss, ff: A[1, 0] * ff + A[1, 1] * ss)
+            t += Hi
+        e = ex(t)
+        errs.append(math.hypot(f - e[0], s - e[1]))
+    eocs = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(2.85 < e < 3.2 for e in eocs), eocs
 
 
 @pytest.mark.parametrize("reextrapolate", [False, True])
