@@ -166,7 +166,8 @@ def _run_gpu(wl, dtype, steps, warmup, world, local, sample_clocks=True):
     g.bind(wl["q0"])
     g.mrab_init()
     torch.cuda.synchronize()
-    tuning = {name: {"strip_width": g.mesh_info(k).strip_width, "rows_per_cta": g.mesh_info(k).rows_per_cta}
+    tuning = {name: {"strip_width": g.mesh_info(k).strip_width, "rows_per_cta": g.mesh_info(k).rows_per_cta,
+                     "rows_update": g.mesh_info(k).rows_update}
               for k, name in enumerate(("background", "ogrid"))}
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")

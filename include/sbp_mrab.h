@@ -110,6 +110,7 @@ typedef struct {
   int rows_per_cta;     /* rows per CTA (chosen by the autotuner, see sbp_autotune) */
   int single_pass;      /* 1: the single-pass marching kernel (rows_per_cta = its chunk of rows);
                            0: the flux + derivative kernel pair */
+  int rows_update;      /* kernel pair: rows per CTA of the derivative (update) kernel, 4..32 */
 } sbp_mesh_info;
 
 /* Create a two-mesh overset system (mesh 0 = background, mesh 1 = the overset fine mesh) and
@@ -220,7 +221,8 @@ sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
 sbp_status sbp_autotune(sbp_system_t sys, int enable, void *stream);
 
 /* Choose the right-hand-side kernel of `mesh` by hand (the autotuner's choice otherwise): strip
- * = 0 selects the kernel pair with rows = 8, 16 or 32 rows per CTA; strip = 64 the single-pass
+ * = 0 selects the kernel pair with rows & 0xFF = 8, 16 or 32 rows per CTA of the flux kernel
+ * and rows >> 8 = 4, 8, 16 or 32 rows of the derivative kernel (0: the same); strip = 64 the single-pass
  * marching kernel with chunks of `rows` rows (1..65535). Both give the same bits.
  * Later autotuner runs (sbp_mrab_init, sbp_autotune) override the choice; disable the
  * autotuner (sbp_autotune(sys, 0, stream)) to keep it. */

@@ -50,7 +50,8 @@ class MeshInfo(ctypes.Structure):
                 ("field_elems", ctypes.c_size_t), ("state_bytes", ctypes.c_size_t),
                 ("hist_bytes", ctypes.c_size_t), ("nvar", ctypes.c_int), ("n_holes", ctypes.c_int),
                 ("n_receivers", ctypes.c_int), ("n_sat_points", ctypes.c_int), ("elem_size", ctypes.c_int),
-                ("strip_width", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("single_pass", ctypes.c_int)]
+                ("strip_width", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("single_pass", ctypes.c_int),
+                ("rows_update", ctypes.c_int)]
 
 
 class Mesh3Desc(ctypes.Structure):
@@ -355,9 +356,11 @@ class System:
     def autotune(self, on=True, stream=None):
         _check(_lib.sbp_autotune(self.h, int(bool(on)), _stream(stream)), "sbp_autotune")
 
-    def set_rhs_shape(self, k, strip, rows):
-        """strip 0: kernel pair with `rows` rows per CTA; 64: marching kernel, chunks of `rows`."""
-        _check(_lib.sbp_set_rhs_shape(self.h, k, int(strip), int(rows)), "sbp_set_rhs_shape")
+    def set_rhs_shape(self, k, strip, rows, rows_update=0):
+        """strip 0: kernel pair with `rows` rows per CTA of the flux kernel and `rows_update`
+        (0: the same) of the derivative kernel; 64: marching kernel, chunks of `rows`."""
+        code = int(rows) | (int(rows_update) << 8) if int(strip) == 0 else int(rows)
+        _check(_lib.sbp_set_rhs_shape(self.h, k, int(strip), code), "sbp_set_rhs_shape")
         self.info[k] = self.mesh_info(k)
 
     def use_graphs(self, on=True):

@@ -109,6 +109,10 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
     CUDA_TRY(upload(d.tile_sat, toff.data(), toff.size() * sizeof(int)));
     CUDA_TRY(cudaMalloc(&d.flux, 8 * field * S->esz));
     d.rows_per_cta = 16;
+    if (p.physics == SBP_NS && k == p.fast_mesh) {
+      CUDA_TRY(cudaMalloc(&d.prim, 3 * field * S->esz));
+      CUDA_TRY(cudaMemset(d.prim, 0, 3 * field * S->esz));
+    }
     CUDA_TRY(upload(d.sat_ij, ij.data(), ns * sizeof(uint32_t)));
     CUDA_TRY(upload(d.sat_code, code.data(), ns * sizeof(uint32_t)));
     CUDA_TRY(upload(d.sat_recv, recv.data(), ns * sizeof(int)));
@@ -156,6 +160,7 @@ sbp_status sbp_mesh_info_get(sbp_system_t S, int k, sbp_mesh_info *info) {
   info->n_sat_points = (int)m.sat_pt.size();
   info->elem_size = (int)S->esz;
   info->rows_per_cta = S->md[k].strip ? S->md[k].chunk : S->md[k].rows_per_cta;
+  info->rows_update = S->md[k].strip ? 0 : (S->md[k].rows_upd ? S->md[k].rows_upd : S->md[k].rows_per_cta);
   info->strip_width = S->md[k].strip ? S->md[k].strip : kTileX;
   info->single_pass = S->md[k].strip ? 1 : 0;
   return SBP_OK;
@@ -331,9 +336,13 @@ sbp_status sbp_set_rhs_shape(sbp_system_t S, int k, int strip, int rows) {
   if (!S || k < 0 || k > 1) return fail(SBP_ERR_ARG, "bad argument");
   MeshDev &d = S->md[k];
   if (strip == 0) {
-    if (rows != 8 && rows != 16 && rows != 32) return fail(SBP_ERR_ARG, "split kernels take 8, 16 or 32 rows per CTA");
+    const int rf = rows & 0xFF, ru = rows >> 8;
+    if (rf != 8 && rf != 16 && rf != 32) return fail(SBP_ERR_ARG, "split kernels take 8, 16 or 32 rows per CTA");
+    if (ru != 0 && ru != 4 && ru != 8 && ru != 16 && ru != 32)
+      return fail(SBP_ERR_ARG, "the derivative kernel takes 4, 8, 16 or 32 rows per CTA");
     d.strip = 0;
-    d.rows_per_cta = rows;
+    d.rows_per_cta = rf;
+    d.rows_upd = ru;
   } else {
     if (strip != 64) return fail(SBP_ERR_ARG, "the marching kernel takes strips of 64 columns");
     if (rows < 1 || rows > 65535) return fail(SBP_ERR_ARG, "chunk rows out of range");

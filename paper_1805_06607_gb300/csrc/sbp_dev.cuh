@@ -455,11 +455,12 @@ __device__ void sat_terms(const RhsLaunch &a, int s, const T qp[4], const T mt[5
 
 // SAT entries of the CTA's rows: the tile lists are grouped by 32 x 8 tiles in column-major
 // tile order, so a 32 x TY block owns a contiguous range.
+// A block of fewer than 8 rows gets its 8-row group's range (a superset, searched by key).
 template <int TY>
 __device__ __forceinline__ void tile_sat_range(const RhsLaunch &a, int bx, int by, int &s0, int &s1) {
   const int nty8 = (a.m.nj + 7) / 8;
-  const int ty8 = by * (TY / 8);
-  const int id0 = bx * nty8 + ty8, id1 = bx * nty8 + min(ty8 + TY / 8, nty8);
+  const int ty8 = (by * TY) / 8, ty8e = min(((by + 1) * TY + 7) / 8, nty8);
+  const int id0 = bx * nty8 + ty8, id1 = bx * nty8 + ty8e;
   s0 = a.tile_sat[id0];
   s1 = a.tile_sat[id1];
 }
@@ -483,6 +484,7 @@ __device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T 
   const T *q = static_cast<const T *>(a.q);
   T *fl = static_cast<T *>(a.flux);
   if constexpr (VISC) {
+    const T *pin = static_cast<const T *>(a.prim_in);
     for (int idx = tid; idx < RN; idx += NT) {
       int gi = i0 - H + idx % RX, gj = j0 - H + idx / RX;
       bool in = wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j);
@@ -490,7 +492,13 @@ __device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T 
       uint8_t c = 0xFF;
       if (in) {
         size_t p = (size_t)gj * m.pitch + gi;
-        prim_at(q, m.field, p, k.gam, pr);
+        if (pin) {
+          pr[0] = pin[p];
+          pr[1] = pin[m.field + p];
+          pr[2] = pin[2 * m.field + p];
+        } else {
+          prim_at(q, m.field, p, k.gam, pr);
+        }
         c = m.cls[p];
       }
       prim[idx] = pr[0];
@@ -566,7 +574,7 @@ __device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T 
 
 template <typename T, int TY>
 struct UpdTile {
-  static constexpr int TX = kTileX, NT = kNT, PPT = TX * TY / NT;
+  static constexpr int TX = kTileX, NT = TX * TY < kNT ? TX * TY : kNT, PPT = TX * TY / NT;
   static constexpr int RX = TX + 6, RY = TY + 6, RN = RX * RY;
   static constexpr size_t bytes = (size_t)(8 * RN) * sizeof(T);
 };
@@ -641,6 +649,7 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
       for (int c = 0; c < 4; ++c) out[c * m.field + p] = rhs[c];
     } else {
       T *qn = static_cast<T *>(a.qnext);
+      T qv[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         out[c * m.field + p] = rhs[c];
@@ -648,7 +657,16 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
         for (int h = 0; h < a.nold; ++h)
           acc += a.alpha[h] * (double)static_cast<const T *>(a.hold[h])[c * m.field + p];
         acc += a.alpha[a.nold] * (double)rhs[c];
-        qn[c * m.field + p] = (T)acc;
+        qv[c] = (T)acc;
+        qn[c * m.field + p] = qv[c];
+      }
+      if (VISC && a.prim_out) {
+        // the next right-hand side's primitives of this point (prim_at's arithmetic)
+        T pr[3];
+        prim4(qv[0], qv[1], qv[2], qv[3], kc<T>(a).gam, pr);
+        T *po = static_cast<T *>(a.prim_out);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) po[f * m.field + p] = pr[f];
       }
     }
   }

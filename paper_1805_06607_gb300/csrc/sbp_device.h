@@ -51,11 +51,17 @@ struct RhsLaunch {
   // SAT points of this mesh grouped by 32 x 8 tile (tile id = (i / 32) * ceil(nj / 8) + j / 8);
   // tile_sat has one offset per tile + 1
   const int *tile_sat;
-  int rows_per_cta;  // 8, 16 or 32: rows per CTA of the split right-hand-side kernels
+  int rows_per_cta;  // 8, 16 or 32: rows per CTA of the split kernels' flux kernel
+  int rows_upd;      // 4, 8, 16 or 32: rows per CTA of their update kernel (0: rows_per_cta)
   // strip = 0: split kernels (k_flux, k_update); 64: the single-pass marching kernel (k_march)
   // with strips of 64 columns and chunks of `chunk` rows per CTA
   int strip, chunk;
   void *flux;        // 8 planes: F^_xi (4 variables), F^_eta (4 variables)
+  // Navier-Stokes primitives (u, v, T: 3 planes of the state's layout). prim_in: the flux
+  // kernel reads the primitives of q from here instead of computing them; prim_out: the
+  // update (mode 1) writes the primitives of qnext here. Either may be null.
+  const void *prim_in;
+  void *prim_out;
   const uint32_t *sat_ij;   // i | j << 16
   const uint32_t *sat_code;
   const int *sat_recv;

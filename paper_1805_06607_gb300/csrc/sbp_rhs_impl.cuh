@@ -23,13 +23,20 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 4 : 3) k_flux(const RhsL
 }
 
 template <typename T, bool VISC, bool CURV, int TY>
-__global__ void __launch_bounds__(kNT) k_update(const RhsLaunch a) {
+__global__ void __launch_bounds__(UpdTile<T, TY>::NT) k_update(const RhsLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   update_tile<T, VISC, CURV, TY>(a, blockIdx.x, blockIdx.y, reinterpret_cast<T *>(smem_raw));
 }
 
 template <typename T, bool VISC, bool CURV, int TY>
-static cudaError_t launch_rhs_t(const RhsLaunch &a, cudaStream_t s) {
+static cudaError_t launch_flux_t(const RhsLaunch &a, cudaStream_t s) {
+  dim3 grid((a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
+  k_flux<T, VISC, CURV, TY><<<grid, kNT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, bool VISC, bool CURV, int TY>
+static cudaError_t launch_update_t(const RhsLaunch &a, cudaStream_t s) {
   using U = UpdTile<T, TY>;
   auto ku = k_update<T, VISC, CURV, TY>;
   static bool attr_set = false;
@@ -39,19 +46,26 @@ static cudaError_t launch_rhs_t(const RhsLaunch &a, cudaStream_t s) {
     attr_set = true;
   }
   dim3 grid((a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
-  k_flux<T, VISC, CURV, TY><<<grid, kNT, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  ku<<<grid, kNT, U::bytes, s>>>(a);
+  ku<<<grid, U::NT, U::bytes, s>>>(a);
   return cudaGetLastError();
 }
 
+// The flux kernel with rows_per_cta (8, 16, 32) rows per CTA, then the update kernel with
+// rows_upd (4, 8, 16, 32; 0: the same).
 template <typename T, bool VISC, bool CURV>
 static cudaError_t launch_rhs_ty(const RhsLaunch &a, cudaStream_t s) {
+  cudaError_t e = cudaErrorInvalidValue;
   switch (a.rows_per_cta) {
-    case 8: return launch_rhs_t<T, VISC, CURV, 8>(a, s);
-    case 16: return launch_rhs_t<T, VISC, CURV, 16>(a, s);
-    case 32: return launch_rhs_t<T, VISC, CURV, 32>(a, s);
+    case 8: e = launch_flux_t<T, VISC, CURV, 8>(a, s); break;
+    case 16: e = launch_flux_t<T, VISC, CURV, 16>(a, s); break;
+    case 32: e = launch_flux_t<T, VISC, CURV, 32>(a, s); break;
+  }
+  if (e != cudaSuccess) return e;
+  switch (a.rows_upd ? a.rows_upd : a.rows_per_cta) {
+    case 4: return launch_update_t<T, VISC, CURV, 4>(a, s);
+    case 8: return launch_update_t<T, VISC, CURV, 8>(a, s);
+    case 16: return launch_update_t<T, VISC, CURV, 16>(a, s);
+    case 32: return launch_update_t<T, VISC, CURV, 32>(a, s);
   }
   return cudaErrorInvalidValue;
 }

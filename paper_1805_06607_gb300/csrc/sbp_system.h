@@ -63,7 +63,9 @@ struct MeshDev {
   // (receiver * 16 + stencil slot) entries that read it
   int *inv_off = nullptr, *inv_re = nullptr;
   int rows_per_cta = 16;
+  int rows_upd = 0;           // rows per CTA of the update kernel (0: rows_per_cta)
   int strip = 0, chunk = 64;  // strip > 0: the single-pass marching kernel (see RhsLaunch)
+  void *prim = nullptr;       // Navier-Stokes fast mesh: primitives handed from micro step to micro step
   // bound integrator buffers
   void *q[2] = {nullptr, nullptr};
   void *hist = nullptr;
@@ -194,6 +196,7 @@ struct sbp_system_s {
       cudaFree(d.dv);
       cudaFree(d.inv_off);
       cudaFree(d.inv_re);
+      cudaFree(d.prim);
     }
     cudaFree(d_err);
     cudaFree(d_dt);
@@ -277,6 +280,7 @@ struct sbp_system_s {
     a.q = q;
     a.tile_sat = md[k].tile_sat;
     a.rows_per_cta = md[k].rows_per_cta;
+    a.rows_upd = md[k].rows_upd;
     a.strip = md[k].strip;
     a.chunk = md[k].chunk;
     a.flux = md[k].flux;
@@ -431,6 +435,12 @@ struct sbp_system_s {
       a.alpha[j] = alpha ? alpha[j] : plan.ab[j] * dt;
     }
     a.alpha[m - 1] = alpha ? alpha[m - 1] : plan.ab[m - 1] * dt;
+    // fast micro steps hand the primitives of the state they produce to the next micro step
+    // (the split kernels' flux kernel then loads them instead of computing its halo's)
+    if (k == fast() && d.prim && d.strip == 0) {
+      if (set > 0) a.prim_in = d.prim;
+      if (set < plan.sr - 1) a.prim_out = d.prim;
+    }
     return a;
   }
 
@@ -633,9 +643,10 @@ struct sbp_system_s {
   bool autotune_on = true;
   cudaError_t autotune(cudaStream_t s) {
     struct Cand {
-      int strip, rows;
+      int strip, rows, rows_upd;
     };
-    static const Cand cands[] = {{0, 8}, {0, 16}, {0, 32}, {64, 16}, {64, 32}, {64, 64}, {64, 128}};
+    static const Cand cands[] = {{0, 8, 0},   {0, 8, 4},   {0, 16, 0},  {0, 16, 8},  {0, 16, 4}, {0, 32, 0},
+                                 {0, 32, 16}, {64, 16, 0}, {64, 32, 0}, {64, 64, 0}, {64, 128, 0}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -645,7 +656,7 @@ struct sbp_system_s {
       void *scratch = d.q[1 - d.cur];  // the buffer the next step writes
       e = interp(k, md[1 - k].q[md[1 - k].cur], nullptr, nullptr, 0, s);
       float best = 1e30f;
-      Cand best_c{d.strip, d.strip ? d.chunk : d.rows_per_cta};
+      Cand best_c{d.strip, d.strip ? d.chunk : d.rows_per_cta, d.rows_upd};
       for (const Cand &c : cands) {
         if (e != cudaSuccess) continue;
         if (c.strip == 0 && c.rows > mh[k].nj) continue;
@@ -653,6 +664,7 @@ struct sbp_system_s {
         d.strip = c.strip;
         if (c.strip) d.chunk = c.rows;
         else d.rows_per_cta = c.rows;
+        d.rows_upd = c.rows_upd;
         RhsLaunch a = rhs_args(k, d.q[d.cur]);
         a.mode = 0;
         a.out = scratch;
@@ -671,6 +683,7 @@ struct sbp_system_s {
       d.strip = best_c.strip;
       if (best_c.strip) d.chunk = best_c.rows;
       else d.rows_per_cta = best_c.rows;
+      d.rows_upd = best_c.rows_upd;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
