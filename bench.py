@@ -73,25 +73,32 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, interval_ms=20):
         self.dev = device_index
-        self.rows = []
+        self.interval = interval_ms
+        self.rows = []  # (host time, fields)
         self.proc = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
         return self
 
+    def wait_first(self, timeout=3.0):
+        """Block until nvidia-smi has printed its first sample (it takes a while to start)."""
+        t_end = time.perf_counter() + timeout
+        while self.proc and not self.rows and time.perf_counter() < t_end:
+            time.sleep(0.005)
+
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([c.strip() for c in line.split(",")])
+            self.rows.append((time.perf_counter(), [c.strip() for c in line.split(",")]))
 
     def __exit__(self, *exc):
         if self.proc:
@@ -101,12 +108,21 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None, t_end=None):
+        """Median SM clock and throttle reasons over the samples taken from t0 on (through
+        t_end when given); samples_in_timed_region counts those inside [t0, t1]."""
         sm = []
         smax = None
         reasons = set()
+        inside = 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for ts, r in self.rows:
+            if t0 is not None and ts < t0:
+                continue
+            if t_end is not None and ts > t_end:
+                continue
+            if t0 is not None and t1 is not None and ts <= t1:
+                inside += 1
             try:
                 sm.append(float(r[1]))
                 smax = float(r[2])
@@ -116,7 +132,8 @@ class ClockSampler:
             except (ValueError, IndexError):
                 continue
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_timed_region": inside,
+                "interval_ms": self.interval}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -177,17 +194,31 @@ def _run_gpu(wl, dtype, steps, warmup, world, local, sample_clocks=True):
     g.check()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     sampler = ClockSampler(local)
-    _barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    clk = None
     with (sampler if sample_clocks else _Null()):
+        if sample_clocks:
+            sampler.wait_first()
+        _barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         for k in range(steps):
             flush.zero_()                       # evict the working set (< L2) between steps
             ev[k][0].record(stream)
             g.mrab_step(1)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        if sample_clocks:
+            # the same steps, untimed, for a few more clock samples under this load
+            while time.perf_counter() - t1 < 0.4:
+                for _ in range(32):
+                    flush.zero_()
+                    g.mrab_step(1)
+                torch.cuda.synchronize()
+            clk = sampler.summary(t0, t1, time.perf_counter())
+            clk["note"] = ("samples from the start of the timed steps through 0.4 s of the same steps "
+                           "run untimed right after them")
+    wall = t1 - t0
     _barrier(world)
     g.check()
     step_ms = sum(a.elapsed_time(b) for a, b in ev) / steps
@@ -224,7 +255,7 @@ def _run_gpu(wl, dtype, steps, warmup, world, local, sample_clocks=True):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / steps
     bytes_io = sum(h.numel() * h.element_size() for h in host_in)
-    out = {"step_ms": step_ms, "wall_s": wall, "prof": prof, "clocks": sampler.summary() if sample_clocks else None,
+    out = {"step_ms": step_ms, "wall_s": wall, "prof": prof, "clocks": clk,
            "e2e_ms": e2e_ms, "h2d": bytes_io, "d2h": bytes_io, "info": inf,
            # 3 donor-value launches + (flux, update) per right-hand side (1 slow + SR fast)
            "launches_per_step": 3 + 2 * (1 + wl["params"]["step_ratio"]), "tuning": tuning}
@@ -482,7 +513,8 @@ def _rhs_eval_large(hbm_peak, peak_kind, reps=10):
                 res[mesh] = {"points": pts, "ms": ms, "gpts_per_s": pts / (ms / 1e3) / 1e9, "bytes_per_point": bpp,
                              "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
                              "kernel": ("single pass, 64-column strips, %d-row chunks" % inf.rows_per_cta
-                                        if inf.single_pass else "flux + derivative pair, %d rows" % inf.rows_per_cta)}
+                                        if inf.single_pass else "flux + derivative pair, %d / %d rows"
+                                        % (inf.rows_per_cta, inf.rows_update))}
             g.check()
             g.close()
             out["%s_%s" % (name, dtype)] = res

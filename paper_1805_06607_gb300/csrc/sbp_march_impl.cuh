@@ -88,26 +88,43 @@ __global__ void __launch_bounds__(128) k_sat(const RhsLaunch a) {
   for (int c = 0; c < 4; ++c) satb[c * a.nsat + s] = acc[c];
 }
 
+// A thread's items of a window stage with `width` columns per row (R rows): row in the tick,
+// ring column, and the wrapped mesh column (-1 outside the mesh or past the items). The same
+// every tick, so they are worked out once per CTA.
+struct WinItem {
+  int rr, cc, gi;
+};
+
+template <int R, int NT>
+__device__ __forceinline__ void win_items(const DevMesh &m, int width, int col0, WinItem it[2]) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int idx = threadIdx.x + k * NT;
+    it[k].rr = idx / width;
+    it[k].cc = idx - it[k].rr * width;
+    int gi = col0 + it[k].cc;
+    it[k].gi = (idx < R * width && wrap_index(gi, m.ni, m.per_i)) ? gi : -1;
+  }
+}
+
 // Copies of rows [r0, r0 + R) of the window into the state / metric rings (cp.async) and
 // class bytes into registers (cls[] per item; kNoCls where the point is outside the mesh).
 template <typename T, bool VISC, bool CURV>
-__device__ __forceinline__ void march_fetch(const RhsLaunch &a, int i0, int r0, int rmax, T *qr, T *mr,
-                                            unsigned cls[2]) {
+__device__ __forceinline__ void march_fetch(const RhsLaunch &a, const WinItem wi[2], int r0, int rmax, T *qr,
+                                            T *mr, unsigned cls[2]) {
   using M = March<T, VISC, CURV>;
   constexpr int R = M::R, PW = M::PW, NT = M::NT;
   const DevMesh &m = a.m;
   const T *q = static_cast<const T *>(a.q);
   const T *met = static_cast<const T *>(m.met);
+  static_assert(R * PW <= 2 * NT, "two items per thread");
 #pragma unroll
-  for (int it = 0; it < (R * PW + NT - 1) / NT; ++it) {
-    const int idx = threadIdx.x + it * NT;
+  for (int it = 0; it < 2; ++it) {
     cls[it] = kNoCls;
-    if (idx >= R * PW) continue;
-    const int rr = idx / PW, cc = idx - rr * PW;
-    const int row = r0 + rr;
-    if (row >= rmax) continue;
-    int gi = i0 - 6 + cc, gj = row;
-    if (!(wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j))) continue;
+    const int gi = wi[it].gi, cc = wi[it].cc;
+    const int row = r0 + wi[it].rr;
+    int gj = row;
+    if (gi < 0 || row >= rmax || !wrap_index(gj, m.nj, m.per_j)) continue;
     const size_t p = (size_t)gj * m.pitch + gi;
     const int o = (row & (kRing - 1)) * PW + cc;
 #pragma unroll
@@ -121,15 +138,13 @@ __device__ __forceinline__ void march_fetch(const RhsLaunch &a, int i0, int r0, 
 }
 
 template <typename T, bool VISC, bool CURV>
-__device__ __forceinline__ void march_store_cls(int r0, uint8_t *cr, const unsigned cls[2]) {
+__device__ __forceinline__ void march_store_cls(const WinItem wi[2], int r0, uint8_t *cr, const unsigned cls[2]) {
   using M = March<T, VISC, CURV>;
-  constexpr int R = M::R, PW = M::PW, NT = M::NT;
+  constexpr int PW = M::PW;
 #pragma unroll
-  for (int it = 0; it < (R * PW + NT - 1) / NT; ++it) {
-    const int idx = threadIdx.x + it * NT;
-    if (idx >= R * PW || cls[it] == kNoCls) continue;
-    const int rr = idx / PW, cc = idx - rr * PW;
-    cr[((r0 + rr) & (kRing - 1)) * PW + cc] = (uint8_t)cls[it];
+  for (int it = 0; it < 2; ++it) {
+    if (cls[it] == kNoCls) continue;
+    cr[((r0 + wi[it].rr) & (kRing - 1)) * PW + wi[it].cc] = (uint8_t)cls[it];
   }
 }
 
@@ -269,10 +284,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
   const int nty8 = (m.nj + 7) / 8;
   const int rmax = j1 + 6;  // rows of the window: [j0 - 6, j1 + 6)
 
+  WinItem pw[2], fw[2];  // items of the P-wide (fetch, primitives) and F-wide (fluxes) stages
+  win_items<R, NT>(m, PW, i0 - 6, pw);
+  win_items<R, NT>(m, FW, i0 - 3, fw);
   unsigned cls[2];
-  march_fetch<T, VISC, CURV>(a, i0, j0 - 6, rmax, qr, mr, cls);
+  march_fetch<T, VISC, CURV>(a, pw, j0 - 6, rmax, qr, mr, cls);
   cp_async_commit();
-  march_store_cls<T, VISC, CURV>(j0 - 6, cr, cls);
+  march_store_cls<T, VISC, CURV>(pw, j0 - 6, cr, cls);
 
   for (int b = j0 - 6; b - 6 < j1; b += R) {
     // this tick's rows have landed (issued one tick ago) and every thread is done with the
@@ -280,17 +298,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
     // (their ring slots belong to rows no stage of this tick reads)
     cp_async_wait<0>();
     __syncthreads();
-    march_fetch<T, VISC, CURV>(a, i0, b + R, rmax, qr, mr, cls);
+    march_fetch<T, VISC, CURV>(a, pw, b + R, rmax, qr, mr, cls);
     cp_async_commit();
     if constexpr (VISC) {
       // P: primitives of rows [b, b + R)
-      for (int idx = tid; idx < R * PW; idx += NT) {
-        const int rr = idx / PW, cc = idx - rr * PW;
-        const int row = b + rr;
-        const int o = (row & (kRing - 1)) * PW + cc;
-        if (row >= rmax) continue;
-        int gi = i0 - 6 + cc, gj = row;
-        if (!(wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j))) continue;
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int row = b + pw[it].rr;
+        const int o = (row & (kRing - 1)) * PW + pw[it].cc;
+        int gj = row;
+        if (pw[it].gi < 0 || row >= rmax || !wrap_index(gj, m.nj, m.per_j)) continue;
         T pr[3];
         prim4(qr[o], qr[kRing * PW + o], qr[2 * kRing * PW + o], qr[3 * kRing * PW + o], k.gam, pr);
 #pragma unroll
@@ -299,13 +316,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
       __syncthreads();
     }
     // F: contravariant fluxes of rows [b - 3, b + R - 3), window columns [3, W + 9)
-    for (int idx = tid; idx < R * FW; idx += NT) {
-      const int rr = idx / FW, cc = idx - rr * FW;
-      const int row = b - 3 + rr;
-      if (row < j0 - 3 || row >= j1 + 3) continue;
-      int gi = i0 - 3 + cc, gj = row;
-      if (!(wrap_index(gi, m.ni, m.per_i) & wrap_index(gj, m.nj, m.per_j))) continue;
-      const int pc = cc + 3;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int row = b - 3 + fw[it].rr;
+      int gj = row;
+      if (fw[it].gi < 0 || row < j0 - 3 || row >= j1 + 3 || !wrap_index(gj, m.nj, m.per_j)) continue;
+      const int pc = fw[it].cc + 3;
       const unsigned code = cr[(row & (kRing - 1)) * PW + pc];
       if (code == 0u) march_flux_point<T, VISC, CURV, true>(a, qr, mr, prim, fr, row, pc, code);
       else march_flux_point<T, VISC, CURV, false>(a, qr, mr, prim, fr, row, pc, code);
@@ -321,11 +337,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
         const unsigned code = cr[o];
         T rhs[4] = {T(0), T(0), T(0), T(0)};
         if ((code & 15u) != 15u) {
-          const int tile = (gi / kTileX) * nty8 + gj / 8;
-          const int s0 = a.tile_sat[tile], s1 = a.tile_sat[tile + 1];
           const T jac = CURV ? mr[4 * kRing * PW + o] : k.mc[4];
           if (code == 0u) march_div_point<T, CURV, true>(k, fr, FW, gj, cc + 3, code, jac, rhs);
           else march_div_point<T, CURV, false>(k, fr, FW, gj, cc + 3, code, jac, rhs);
+          // SAT points are boundary or receiver points: a closure row in some direction
+          const int tile = (gi / kTileX) * nty8 + gj / 8;
+          const int s0 = code != 0u ? a.tile_sat[tile] : 0, s1 = code != 0u ? a.tile_sat[tile + 1] : 0;
           if (s0 < s1) {
             const uint32_t key = (uint32_t)gi | ((uint32_t)gj << 16);
             int lo = s0, hi = s1;
@@ -362,7 +379,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
       }
     }
     // class bytes of the prefetched rows; their slots are not read by this tick's stages
-    march_store_cls<T, VISC, CURV>(b + R, cr, cls);
+    march_store_cls<T, VISC, CURV>(pw, b + R, cr, cls);
   }
   cp_async_wait<0>();
 }
