@@ -81,6 +81,13 @@ typedef struct {
   int order, hist_len, step_ratio, fast_mesh;
   double hole_cells;             /* hole margin in background spacings (<= 0: 4) */
   int scheme;                    /* MRAB ordering, an sbp_mrab_scheme (0: the paper's) */
+  /* Sponge layer at far-field faces (Sec. 5.1: sponge boundaries of a given depth in cells;
+   * the form is cited, not printed). Within sponge_cells (0: off, at most 16) points of a
+   * far-field face the right-hand side gains -sigma (q - qinf), sigma = sponge_strength
+   * ((D - d) / D)^2 for the index distance d < D = sponge_cells to the nearest far-field face.
+   * Forward paths only: the adjoint calls reject a system with a sponge. */
+  int sponge_cells;
+  double sponge_strength;
 } sbp_params;
 
 /* The orderings of a macro step that Sec. 3.3 lists as design choices. The paper's runs use

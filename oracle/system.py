@@ -372,6 +372,25 @@ class OracleSystem:
                            _p(out))
         return out
 
+    def sponge_strength(self, k):
+        """Sponge layer of Sec. 5.1 (far-field boundaries with a sponge `sponge_cells` points deep,
+        the form cited to Bodony's sponge analysis, not printed): per point the strength
+        sigma = A ((D - d) / D)^2 for the index distance d < D from a far-field face, the largest
+        over the faces, A = `sponge_strength`; 0 elsewhere, at holes, or with D = 0."""
+        m = self.meshes[k]
+        ni, nj = m["n"]
+        D = int(self.p.get("sponge_cells", 0))
+        sig = np.zeros((nj, ni))
+        if D <= 0:
+            return sig
+        A = float(self.p.get("sponge_strength", 1.0))
+        i = np.arange(ni)[None, :] + 0 * np.arange(nj)[:, None]
+        j = np.arange(nj)[:, None] + 0 * np.arange(ni)[None, :]
+        for face, d in zip(m["bc"], (i, ni - 1 - i, j, nj - 1 - j)):
+            if face == "farfield":
+                sig = np.maximum(sig, np.where(d < D, A * ((D - d) / D) ** 2, 0.0))
+        return np.where(self.iblank[k] != 0, sig, 0.0)
+
     def rhs(self, k, q, qhat, fvhat=None):
         """dq/dt on mesh k given the interpolated donor values at its receivers."""
         L = lib()
@@ -391,6 +410,9 @@ class OracleSystem:
                          float(self.p["twall"]), self.sig_int, self.sig_phys, _p(out))
         if rc != 0:
             raise RuntimeError("oracle rhs failed: %d" % rc)
+        if int(self.p.get("sponge_cells", 0)) > 0:
+            # relaxation toward the far-field state in the sponge layer
+            out -= self.sponge_strength(k)[None] * (q - qinf[:, None, None])
         return out
 
     def coupled_rhs(self, k, q_self, q_other):

@@ -39,7 +39,8 @@ class Params(ctypes.Structure):
                 ("omega_corner", ctypes.c_double), ("sigma_interface", ctypes.c_double),
                 ("sigma_physical", ctypes.c_double), ("cfl", ctypes.c_double), ("qinf", ctypes.c_double * 4),
                 ("order", ctypes.c_int), ("hist_len", ctypes.c_int), ("step_ratio", ctypes.c_int),
-                ("fast_mesh", ctypes.c_int), ("hole_cells", ctypes.c_double), ("scheme", ctypes.c_int)]
+                ("fast_mesh", ctypes.c_int), ("hole_cells", ctypes.c_double), ("scheme", ctypes.c_int),
+                ("sponge_cells", ctypes.c_int), ("sponge_strength", ctypes.c_double)]
 
 # MRAB orderings of Sec. 3.3 (sbp_mrab_scheme)
 SCHEMES = {"fastest_first": 0, "slowest_first": 1, "slowest_first_reextrapolate": 2}
@@ -215,6 +216,8 @@ class System:
         pr.fast_mesh = p["fast_mesh"]
         pr.hole_cells = hole_cells
         pr.scheme = SCHEMES[p.get("scheme", "fastest_first")]
+        pr.sponge_cells = int(p.get("sponge_cells", 0))
+        pr.sponge_strength = float(p.get("sponge_strength", 1.0))
         self.params = p
         h = ctypes.c_void_p()
         torch.cuda.init()

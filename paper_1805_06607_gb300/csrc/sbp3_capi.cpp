@@ -268,6 +268,7 @@ sbp_status sbp3_system_create(const sbp3_mesh_desc *meshes, int n_meshes, const 
   if (p.step_ratio < 1 || p.step_ratio > kMaxSets)
     return fail(SBP_ERR_ARG, "step_ratio must be in 1.." + std::to_string(kMaxSets));
   if (p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_ARG, "3D systems are fastest-first");
+  if (p.sponge_cells != 0) return fail(SBP_ERR_ARG, "3D systems have no sponge layer");
   auto *S = new sbp3_system_s();
   std::unique_ptr<sbp3_system_s> guard(S);
   S->p = p;

@@ -435,6 +435,7 @@ sbp_status sbp_rhs_eval_vjp(sbp_system_t S, int k, const void *q_self, const voi
   if (!S || k < 0 || k > 1 || !q_self || !q_other || !lam || !lq_self || !lq_other)
     return fail(SBP_ERR_ARG, "bad argument");
   if (S->p.dtype != SBP_F64) return fail(SBP_ERR_DTYPE, "the adjoint needs an SBP_F64 system");
+  if (S->p.sponge_cells > 0) return fail(SBP_ERR_ARG, "the adjoint does not cover the sponge layer");
   cudaStream_t s = (cudaStream_t)stream;
   CUDA_TRY(ensure_ws(S));
   CUDA_TRY(cudaMemsetAsync(lq_self, 0, S->state_elems(k) * 8, s));
@@ -454,6 +455,7 @@ sbp_status sbp_rhs_eval_jvp(sbp_system_t S, int k, const void *q_self, const voi
   if (!S || k < 0 || k > 1 || !q_self || !q_other || !dq_self || !dq_other || !drhs)
     return fail(SBP_ERR_ARG, "bad argument");
   if (S->p.dtype != SBP_F64) return fail(SBP_ERR_DTYPE, "the tangent needs an SBP_F64 system");
+  if (S->p.sponge_cells > 0) return fail(SBP_ERR_ARG, "the tangent does not cover the sponge layer");
   cudaStream_t s = (cudaStream_t)stream;
   CUDA_TRY(ensure_ws(S));
   CUDA_TRY(recv_values(S, k, (const double *)q_other, s));
@@ -496,6 +498,7 @@ sbp_status sbp_overset_interp_vjp(sbp_system_t S, int recv, const void *q_donor,
                                   const void *lfvhat, void *lq_donor, void *stream) {
   if (!S || recv < 0 || recv > 1 || !q_donor || !lqhat || !lq_donor) return fail(SBP_ERR_ARG, "bad argument");
   if (S->p.dtype != SBP_F64) return fail(SBP_ERR_DTYPE, "the adjoint needs an SBP_F64 system");
+  if (S->p.sponge_cells > 0) return fail(SBP_ERR_ARG, "the adjoint does not cover the sponge layer");
   cudaStream_t s = (cudaStream_t)stream;
   CUDA_TRY(ensure_ws(S));
   const size_t nr = S->mh[recv].recv_pt.size();
@@ -516,6 +519,7 @@ sbp_status sbp_adjoint_probe(sbp_system_t S, const sbp_adjoint_desc *desc, const
                              void *dJ_dq0_mesh1, double *dJ_dqinf, long *forward_steps, void *stream) {
   if (!S || !desc || !q0_mesh0 || !q0_mesh1) return fail(SBP_ERR_ARG, "bad argument");
   if (S->p.dtype != SBP_F64) return fail(SBP_ERR_DTYPE, "the adjoint needs an SBP_F64 system");
+  if (S->p.sponge_cells > 0) return fail(SBP_ERR_ARG, "the adjoint does not cover the sponge layer");
   if (S->p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_ARG, "the adjoint needs a fastest-first system");
   if (desc->n_steps < 0 || desc->n_snapshots < 0 || desc->n_probes < 1 || !desc->probe_xy || !(desc->H > 0.0))
     return fail(SBP_ERR_ARG, "descriptor: n_steps >= 0, n_snapshots >= 0, n_probes >= 1, probe_xy, H > 0");

@@ -39,6 +39,8 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
     return fail(SBP_ERR_ARG, "step_ratio must be in 1.." + std::to_string(kMaxSets));
   if (p.scheme < SBP_MRAB_FASTEST_FIRST || p.scheme > SBP_MRAB_SLOWEST_FIRST_REEXTRAPOLATE)
     return fail(SBP_ERR_ARG, "scheme");
+  if (p.sponge_cells < 0 || p.sponge_cells > 16 || !(p.sponge_strength >= 0.0))
+    return fail(SBP_ERR_ARG, "sponge_cells must be in 0..16 and sponge_strength >= 0");
   auto *S = new sbp_system_s();
   std::unique_ptr<sbp_system_s> guard(S);
   S->p = p;

@@ -453,6 +453,18 @@ __device__ void sat_terms(const RhsLaunch &a, int s, const T qp[4], const T mt[5
   }
 }
 
+// Sponge strength at (gi, gj): by the index distance to the nearest far-field face (0 outside
+// the layer). The layer's term -sigma (q - qinf) is added after the SAT terms.
+template <typename T>
+__device__ __forceinline__ T sponge_sigma(const KConst<T> &k, const DevMesh &m, int gi, int gj) {
+  int d = 1 << 30;
+  if (k.sponge_faces & 1) d = min(d, gi);
+  if (k.sponge_faces & 2) d = min(d, m.ni - 1 - gi);
+  if (k.sponge_faces & 4) d = min(d, gj);
+  if (k.sponge_faces & 8) d = min(d, m.nj - 1 - gj);
+  return d < k.sponge_d ? k.sponge_tab[d] : T(0);
+}
+
 // SAT entries of the CTA's rows: the tile lists are grouped by 32 x 8 tiles in column-major
 // tile order, so a 32 x TY block owns a contiguous range.
 // A block of fewer than 8 rows gets its 8-row group's range (a superset, searched by key).
@@ -640,6 +652,13 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
         if (lo < s1 && a.sat_ij[lo] == key) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) rhs[c] += satb[c * a.nsat + lo];
+        }
+      }
+      if (kc<T>(a).sponge_d > 0) {
+        const T sg = sponge_sigma(kc<T>(a), m, gi, gj);
+        if (sg != T(0)) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) rhs[c] = fma_rn(-sg, q[c * m.field + p] - kc<T>(a).qinf[c], rhs[c]);
         }
       }
     }

@@ -38,6 +38,10 @@ struct KConst {
   // row sum is the physical derivative d/dx or d/dy (rows as in the device table: closures
   // 0-3, interior 4, hole 5)
   T wx[6][4], wy[6][4];
+  // sponge layer: strength by index distance d < sponge_d to the nearest far-field face
+  // (sponge_faces: bit f set for a far-field face f = i-low, i-high, j-low, j-high)
+  int sponge_d, sponge_faces;
+  T sponge_tab[16];
 };
 
 // Right-hand side (+ optional MRAB update) of one mesh: k_flux then k_update.

@@ -359,6 +359,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
               for (int c = 0; c < 4; ++c) rhs[c] += satb[c * a.nsat + lo];
             }
           }
+          if (k.sponge_d > 0) {
+            const T sg = sponge_sigma(k, m, gi, gj);
+            if (sg != T(0)) {
+#pragma unroll
+              for (int c = 0; c < 4; ++c) rhs[c] = fma_rn(-sg, qr[c * kRing * PW + o] - k.qinf[c], rhs[c]);
+            }
+          }
         }
         T *out = static_cast<T *>(a.out);
         if (a.mode == 0) {

@@ -314,6 +314,15 @@ struct sbp_system_s {
     c.tw = (T)(p.twall / (g * (g - 1.0)));
     for (int v = 0; v < 4; ++v) c.qinf[v] = (T)p.qinf[v];
     const MeshHost &m = mh[k];
+    c.sponge_d = 0;
+    c.sponge_faces = 0;
+    for (int f = 0; f < 4; ++f)
+      if (m.bc[f] == SBP_BC_FARFIELD) c.sponge_faces |= 1 << f;
+    if (p.sponge_cells > 0 && c.sponge_faces) c.sponge_d = p.sponge_cells;
+    for (int d = 0; d < 16; ++d) {
+      const double r = d < p.sponge_cells ? (double)(p.sponge_cells - d) / p.sponge_cells : 0.0;
+      c.sponge_tab[d] = (T)(p.sponge_strength * r * r);
+    }
     if (m.cartesian) {
       c.mc[0] = (T)m.h[1];
       c.mc[1] = (T)0;

@@ -30,6 +30,7 @@ CASES = {
     "cylinder": lambda: W.cylinder_small(seed=32),
     "mms_viscous": lambda: W.mms_box_in_box(52, "viscous"),
     "cylinder_ragged": lambda: W.cylinder_small(seed=33, n_theta=72, n_r=20, bg_n=(90, 50), hist_len=4),
+    "cylinder_sponge": lambda: W.cylinder_small(seed=36, sponge_cells=6, sponge_strength=2.0),
 }
 SHAPES = [(64, 7), (64, 32), (64, 1), (64, 24), (64, 128), (64, 1000)]
 

@@ -36,6 +36,8 @@ CASES = {
     "cylinder": lambda: W.cylinder_small(seed=14),
     "cylinder_ab34": lambda: W.cylinder_small(seed=15, n_theta=72, n_r=20, bg_n=(90, 50), hist_len=4),
     "mms_viscous": lambda: W.mms_box_in_box(52, "viscous"),
+    # far-field sponge layer six points deep (Sec. 5.1)
+    "cylinder_sponge": lambda: W.cylinder_small(seed=20, sponge_cells=6, sponge_strength=2.0),
 }
 
 # The extended-history Adams-Bashforth family of Sec. 3.2 inside MRAB (order n, history m:
@@ -102,8 +104,8 @@ def test_interp_and_rhs_fp64(sbp, case):
     g.close()
 
 
-@pytest.mark.parametrize("case", ["vortex", "cylinder", "vortex_sr3_ab34", "cylinder_ab34", "vortex_sr1"]
-                         + sorted(AB_CASES))
+@pytest.mark.parametrize("case", ["vortex", "cylinder", "vortex_sr3_ab34", "cylinder_ab34", "vortex_sr1",
+                                  "cylinder_sponge"] + sorted(AB_CASES))
 def test_mrab_fp64(sbp, case):
     wl = {**CASES, **AB_CASES}[case]()
     ref = OracleSystem(wl)
@@ -166,7 +168,22 @@ def test_zero_steps_is_noop(sbp):
     g.close()
 
 
-@pytest.mark.parametrize("case", ["vortex", "cylinder"])
+def test_sponge_changes_the_state_and_is_refused_by_the_adjoint(sbp):
+    wl = CASES["cylinder_sponge"]()
+    wl0 = W.cylinder_small(seed=20)
+    g, g0 = sbp.System(wl), sbp.System(wl0)
+    qd = [g.to_device(k, wl["q0"][k]) for k in range(2)]
+    r = g.to_host(0, g.rhs_eval(0, qd[0], qd[1]))
+    r0 = g0.to_host(0, g0.rhs_eval(0, qd[0], qd[1]))
+    assert rel(r, r0) > 1e-3
+    lam = torch.zeros_like(qd[0])
+    with pytest.raises(sbp.SbpError):
+        g.rhs_eval_vjp(0, qd[0], qd[1], lam)
+    g.close()
+    g0.close()
+
+
+@pytest.mark.parametrize("case", ["vortex", "cylinder", "cylinder_sponge"])
 def test_fp32(sbp, case):
     """FP32 state and right-hand side with FP64 MRAB accumulation, against the FP64 oracle."""
     wl = CASES[case]()

@@ -131,7 +131,8 @@ def vortex_box_in_box(seed=0, n_bg=64, n_fine=41, bg_half=5.0, fine_half=1.0, om
 
 def cylinder_overset(seed=0, n_theta=512, n_r=128, r_in=0.5, stretch=1.05, s_bg=0.05,
                      bg_n=(1024, 512), bg_lo=(-12.8, -12.8), mach=0.2, re=200.0, pr=0.72,
-                     order=3, hist_len=None, step_ratio=4, cfl=0.5, amp=1e-3, twall=1.0):
+                     order=3, hist_len=None, step_ratio=4, cfl=0.5, amp=1e-3, twall=1.0,
+                     sponge_cells=0, sponge_strength=1.0):
     """2D Navier-Stokes cylinder in cross-flow: O-grid (wall inside, interface outside) on a
     Cartesian background with far-field faces. The first radial spacing is chosen so that the
     outermost O-grid spacing equals the background spacing."""
@@ -144,7 +145,8 @@ def cylinder_overset(seed=0, n_theta=512, n_r=128, r_in=0.5, stretch=1.05, s_bg=
     q_bg = noisy_uniform((bg_n[1], bg_n[0]), qinf, amp, rng)
     params = dict(physics="ns", gamma=GAMMA, mu=mach / re, pr=pr, order=order,
                   hist_len=hist_len or order, step_ratio=step_ratio, fast_mesh=1, cfl=cfl,
-                  qinf=qinf, twall=twall, omega_corner=1.0)
+                  qinf=qinf, twall=twall, omega_corner=1.0, sponge_cells=sponge_cells,
+                  sponge_strength=sponge_strength)
     return {"meshes": [bg, og], "q0": [q_bg, q_og], "params": params, "seed": seed}
 
 
