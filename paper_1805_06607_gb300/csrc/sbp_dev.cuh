@@ -699,21 +699,11 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
 template <typename T>
 __device__ __forceinline__ void set_state(const DonorLaunch &a, int set, size_t p, T out[4]) {
   const T *q = static_cast<const T *>(a.q);
-  const int nb = a.nb[set];
-  // every load first (one memory latency for the group), then the sums in history order
-  T qv[4], hv[kMaxHist][4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) qv[v] = q[v * a.d.field + p];
-#pragma unroll
-  for (int k = 0; k < kMaxHist; ++k)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) hv[k][v] = k < nb ? static_cast<const T *>(a.hist[k])[v * a.d.field + p] : T(0);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    double acc = (double)qv[v];
-#pragma unroll
-    for (int k = 0; k < kMaxHist; ++k)
-      if (k < nb) acc += a.beta[set][k] * (double)hv[k][v];
+    double acc = (double)q[v * a.d.field + p];
+    for (int k = 0; k < a.nb[set]; ++k)
+      acc += a.beta[set][k] * (double)static_cast<const T *>(a.hist[k])[v * a.d.field + p];
     out[v] = (T)acc;
   }
 }

@@ -23,21 +23,10 @@ namespace sbp {
 template <typename T>
 __device__ __forceinline__ void donor_state(const InterpLaunch &a, size_t p, T out[4]) {
   const T *q = static_cast<const T *>(a.q);
-  // every load first, then the sums in history order
-  T qv[4], hv[kMaxHist][4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) qv[v] = q[v * a.d.field + p];
-#pragma unroll
-  for (int k = 0; k < kMaxHist; ++k)
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-      hv[k][v] = k < a.nbeta ? static_cast<const T *>(a.hist[k])[v * a.d.field + p] : T(0);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    double acc = (double)qv[v];
-#pragma unroll
-    for (int k = 0; k < kMaxHist; ++k)
-      if (k < a.nbeta) acc += a.beta[k] * (double)hv[k][v];
+    double acc = (double)q[v * a.d.field + p];
+    for (int k = 0; k < a.nbeta; ++k) acc += a.beta[k] * (double)static_cast<const T *>(a.hist[k])[v * a.d.field + p];
     out[v] = (T)acc;
   }
 }
