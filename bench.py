@@ -271,6 +271,16 @@ class _Null:
         return False
 
 
+# DRAM bytes (read + write) per launch of a phase's kernels from one ncu capture of the current
+# kernels, for the kernel shape captured: the O-grid micro step of the cylinder workload in FP64
+# (flux kernel 8 rows + derivative kernel 8 rows per CTA; the mean over the four micro steps of a
+# macro step, serialised replay with a cold L2).
+MEASURED_TRAFFIC = {
+    ("f64", "rhs_fast"): {"shape": (32, 8, 8), "bytes": 16.96e6,
+                          "source": "ncu --set full, profiles/k_flux_update_cylinder_fp64.md"},
+}
+
+
 def _roofline(res, wl, dtype, hbm_peak, peak_kind):
     """Dominant kernel of the step (largest device time) against its bound."""
     evals, n_bg, n_og = _evals_per_step(wl)
@@ -301,6 +311,11 @@ def _roofline(res, wl, dtype, hbm_peak, peak_kind):
                      "peak_kind": peak_kind, "bytes_per_point": bpp})
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
+    t = MEASURED_TRAFFIC.get((dtype, phase))
+    og = res["tuning"]["ogrid"]
+    if t and (og["strip_width"], og["rows_per_cta"], og["rows_update"]) == t["shape"]:
+        roof["traffic"] = t["bytes"]
+        roof["traffic_source"] = t["source"]
     return roof
 
 
