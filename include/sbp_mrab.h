@@ -418,6 +418,12 @@ sbp_status sbp3_current_state(sbp3_system_t sys, int mesh, void **q);
 sbp_status sbp3_mrab_init(sbp3_system_t sys, double H, void *stream);
 sbp_status sbp3_mrab_step(sbp3_system_t sys, int n, void *stream);
 sbp_status sbp3_check(sbp3_system_t sys, void *stream);
+/* Right-hand-side kernels of one mesh (both give the same bits): kchunk > 0 marches along k
+ * (Navier-Stokes: primitives in a shared-memory ring, flux tiles staged one plane ahead), each
+ * CTA a 32 x 8 column tile and kchunk planes; kchunk = 0 (the default) takes the per-point
+ * kernels (primitives, fluxes, derivatives one point per thread). SBP_ERR_ARG for a bad mesh or
+ * kchunk outside 0..4096. */
+sbp_status sbp3_set_rhs_kernel(sbp3_system_t sys, int mesh, int kchunk);
 
 /* Synchronise the stream and report (then clear) the device error word. */
 sbp_status sbp_check(sbp_system_t sys, void *stream);

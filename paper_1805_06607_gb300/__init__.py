@@ -127,6 +127,7 @@ _SIGS.update({
     "sbp3_mrab_init": [_P, _D, _P],
     "sbp3_mrab_step": [_P, _I, _P],
     "sbp3_check": [_P, _P],
+    "sbp3_set_rhs_kernel": [_P, _I, _I],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -589,6 +590,10 @@ class System3D:
 
     def check(self, stream=None):
         _check(_lib.sbp3_check(self.h, _stream(stream)), "sbp3_check")
+
+    def set_rhs_kernel(self, mesh, kchunk):
+        """kchunk > 0: the k-marching right-hand side with kchunk planes per CTA; 0: per point."""
+        _check(_lib.sbp3_set_rhs_kernel(self.h, int(mesh), int(kchunk)), "sbp3_set_rhs_kernel")
 
 
 class Batch:

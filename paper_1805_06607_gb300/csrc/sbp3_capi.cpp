@@ -56,6 +56,7 @@ struct sbp3_system_s {
   unsigned long long *d_dt = nullptr;
   double H = 0.0, t = 0.0;
   bool initialised = false;
+  int kchunk[2] = {0, 0};  // k planes per CTA of the marching right-hand side (0: per-point kernels)
 
   ~sbp3_system_s() {
     for (auto &d : md) {
@@ -155,6 +156,7 @@ struct sbp3_system_s {
     a.dwt = d.dwt;
     a.ndv = d.ndv;
     a.nrecv = (int)mh[k].recv_pt.size();
+    a.kchunk = kchunk[k];
     a.err = d_err;
     return a;
   }
@@ -457,6 +459,12 @@ sbp_status sbp3_mrab_step(sbp3_system_t S, int n, void *stream) {
   if (!S || n < 0) return fail(SBP_ERR_ARG, "bad argument");
   if (!S->initialised) return fail(SBP_ERR_STATE, "sbp3_mrab_init has not run");
   for (int i = 0; i < n; ++i) CUDA_TRY(S->issue_step((cudaStream_t)stream));
+  return SBP_OK;
+}
+
+sbp_status sbp3_set_rhs_kernel(sbp3_system_t S, int mesh, int kchunk) {
+  if (!S || mesh < 0 || mesh > 1 || kchunk < 0 || kchunk > 4096) return fail(SBP_ERR_ARG, "bad argument");
+  S->kchunk[mesh] = kchunk;
   return SBP_OK;
 }
 

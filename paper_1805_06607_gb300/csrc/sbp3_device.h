@@ -48,6 +48,7 @@ struct Rhs3Launch {
   const int *didx;           // 64 per receiver
   const void *dwt;           // 12 per receiver, compute type
   int ndv, nrecv;
+  int kchunk;                // > 0: the k-marching kernels with chunks of kchunk planes; 0: per-point kernels
   int mode;                  // 0: out = dq/dt; 1: also qnext = q + sum alpha hold + alpha dq/dt
   void *out;
   void *qnext;

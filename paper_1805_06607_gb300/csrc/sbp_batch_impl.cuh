@@ -58,7 +58,7 @@ struct BatchSmem {
 };
 
 template <typename T, bool VISC, bool CURVF, int TY>
-__global__ void __launch_bounds__(kNT) k_batch_substep(const BatchSubstep b) {
+__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (VISC ? 3 : 4) : (VISC ? 1 : 2)) k_batch_substep(const BatchSubstep b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using F = FluxTile<T, VISC, TY>;
   T *prim = reinterpret_cast<T *>(smem_raw);

@@ -149,6 +149,45 @@ __device__ __forceinline__ bool wrap_index(int &g, int n, int per) {
   return (unsigned)g < (unsigned)n;
 }
 
+// Asynchronous global -> shared copies of N bytes (cp.async), their commit and wait.
+template <int N>
+__device__ __forceinline__ void cp_async_n(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(N));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Adams-Bashforth / MRAB update of one point's NV variables (Sec. 3.1 eq. (ab_general)):
+// qn = q + sum_h alpha[h] hold[h] + alpha[nold] rhs, accumulated in FP64 in that order. The
+// loads of one history slot's NV values are issued together, ahead of their products.
+template <typename T, int NV>
+__device__ __forceinline__ void ab_update(const T qv[NV], const void *const *hold, const double *alpha, int nold,
+                                          size_t field, size_t p, const T rhs[NV], T qn[NV]) {
+  double acc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) acc[c] = (double)qv[c];
+#pragma unroll
+  for (int h = 0; h < kMaxHist - 1; ++h) {
+    if (h < nold) {
+      const T *hp = static_cast<const T *>(hold[h]) + p;
+      T hv[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) hv[c] = hp[c * field];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) acc[c] += alpha[h] * (double)hv[c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    acc[c] += alpha[nold] * (double)rhs[c];
+    qn[c] = (T)acc[c];
+  }
+}
+
 // Products and fused multiply-adds with a fixed rounding (never re-associated or contracted
 // differently by the compiler), for expressions that several kernels must evaluate to the
 // same bits.
@@ -668,15 +707,13 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
       for (int c = 0; c < 4; ++c) out[c * m.field + p] = rhs[c];
     } else {
       T *qn = static_cast<T *>(a.qnext);
-      T qv[4];
+      T q0[4], qv[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) q0[c] = q[c * m.field + p];
+      ab_update<T, 4>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         out[c * m.field + p] = rhs[c];
-        double acc = (double)q[c * m.field + p];
-        for (int h = 0; h < a.nold; ++h)
-          acc += a.alpha[h] * (double)static_cast<const T *>(a.hold[h])[c * m.field + p];
-        acc += a.alpha[a.nold] * (double)rhs[c];
-        qv[c] = (T)acc;
         qn[c * m.field + p] = qv[c];
       }
       if (VISC && a.prim_out) {

@@ -35,17 +35,6 @@ struct March {
   static_assert(2 * R + 6 <= kRing && R + 6 <= kRing, "ring too short");
 };
 
-template <int N>
-__device__ __forceinline__ void cp_async_n(void *smem, const void *gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(N));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
 // SAT terms of every boundary / receiver point into a.sat, with the point's gradients from a
 // local copy of the primitives on its stencil cross (the arithmetic of flux_tile's SAT tail).
 template <typename T, bool VISC, bool CURV>
@@ -373,14 +362,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
           for (int c = 0; c < 4; ++c) out[c * m.field + p] = rhs[c];
         } else {
           T *qn = static_cast<T *>(a.qnext);
+          T q0[4], qv[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) q0[c] = qr[c * kRing * PW + o];
+          ab_update<T, 4>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             out[c * m.field + p] = rhs[c];
-            double acc = (double)qr[c * kRing * PW + o];
-            for (int h = 0; h < a.nold; ++h)
-              acc += a.alpha[h] * (double)static_cast<const T *>(a.hold[h])[c * m.field + p];
-            acc += a.alpha[a.nold] * (double)rhs[c];
-            qn[c * m.field + p] = (T)acc;
+            qn[c * m.field + p] = qv[c];
           }
         }
       }
