@@ -282,15 +282,23 @@ sbp_status sbp_profile_read(sbp_system_t sys, double *ms, int *launches, int res
  * Members must be initialised (sbp_mrab_init), share element type, physics and fine-mesh kind
  * (all Cartesian or all curvilinear) and have a Cartesian slow mesh; they stay usable on their
  * own (their states and ring positions follow the batch). The results equal stepping each
- * member alone. autotune != 0 picks the tile height (8 or 16 rows) by timing two macro steps
- * per candidate on a snapshot of every member's buffers (restored afterwards). */
+ * member alone. Euler batches may instead run the single-pass right-hand side: the launch's
+ * phases are then donor values, the SAT values of every boundary / receiver point, and 64-column
+ * strips of 32 or 64 rows (the marching kernel's body), with the same bits. autotune != 0 picks
+ * the work-item shape (tile pairs of 8 or 16 rows; for Euler also strips of 32 or 64 rows) by
+ * timing two macro steps per candidate on a snapshot of every member's buffers (restored
+ * afterwards). */
 typedef struct sbp_batch_s *sbp_batch_t;
 sbp_status sbp_batch_create(const sbp_system_t *systems, int n, int autotune, void *stream, sbp_batch_t *out);
 sbp_status sbp_batch_destroy(sbp_batch_t batch);
 /* n macro steps of every member (asynchronous). */
 sbp_status sbp_batch_step(sbp_batch_t batch, int n, void *stream);
-/* members, tile rows per CTA, cooperative grid size, number of ring phases (graphs). */
+/* members, rows per work item (8, 16: tile pairs of 32 columns; 32, 64: single-pass strips of
+ * 64 columns), cooperative grid size, number of ring phases (graphs). */
 sbp_status sbp_batch_info(sbp_batch_t batch, int *members, int *rows_per_cta, int *grid, int *period);
+/* Work-item shape (replaces the autotuner's choice; between steps): rows = 8 or 16 for tile
+ * pairs, 32, 64 or 128 for single-pass strips (Euler batches only); SBP_ERR_ARG otherwise. */
+sbp_status sbp_batch_set_shape(sbp_batch_t batch, int rows);
 /* Synchronise the stream and report (then clear) the batch's device error word. */
 sbp_status sbp_batch_check(sbp_batch_t batch, void *stream);
 

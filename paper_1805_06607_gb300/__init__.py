@@ -104,6 +104,7 @@ _SIGS.update({
     "sbp_batch_destroy": [_P],
     "sbp_batch_step": [_P, _I, _P],
     "sbp_batch_info": [_P, _P, _P, _P, _P],
+    "sbp_batch_set_shape": [_P, _I],
     "sbp_batch_check": [_P, _P],
 })
 _SIGS.update({
@@ -616,6 +617,10 @@ class Batch:
         _check(_lib.sbp_batch_info(self.h, *[ctypes.cast(ctypes.pointer(x), ctypes.c_void_p) for x in v]),
                "sbp_batch_info")
         return {"members": v[0].value, "rows_per_cta": v[1].value, "grid": v[2].value, "period": v[3].value}
+
+    def set_shape(self, rows):
+        """Work items of `rows` rows: 8, 16 (tile pairs) or, for Euler, 32, 64, 128 (strips)."""
+        _check(_lib.sbp_batch_set_shape(self.h, int(rows)), "sbp_batch_set_shape")
 
     def check(self, stream=None):
         _check(_lib.sbp_batch_check(self.h, _stream(stream)), "sbp_batch_check")

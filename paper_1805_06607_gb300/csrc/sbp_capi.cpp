@@ -525,13 +525,19 @@ struct sbp_batch_s {
       std::vector<std::vector<DonorLaunch>> dl(srmax);
       std::vector<std::vector<RhsLaunch>> rl(srmax);
       std::vector<std::vector<int4>> items(srmax);
+      std::vector<std::vector<int>> sat_off(srmax, std::vector<int>(1, 0)), rl_curv(srmax);
       auto add_rhs = [&](int j, sbp_system_s *S, int k, RhsLaunch a) {
         a.rows_per_cta = ty;
         int r = (int)rl[j].size();
         rl[j].push_back(a);
-        int ntx = (S->mh[k].ni + kTileX - 1) / kTileX, nty = (S->mh[k].nj + ty - 1) / ty;
+        sat_off[j].push_back(sat_off[j].back() + a.nsat);
+        const int curv = S->mh[k].cartesian ? 0 : 1;
+        rl_curv[j].push_back(curv);
+        // ty >= 32: single-pass strips of 64 columns and ty rows; else 32 x ty tiles
+        const int tw = ty >= 32 ? 64 : kTileX;
+        int ntx = (S->mh[k].ni + tw - 1) / tw, nty = (S->mh[k].nj + ty - 1) / ty;
         for (int by = 0; by < nty; ++by)
-          for (int bx = 0; bx < ntx; ++bx) items[j].push_back(make_int4(r, bx, by, S->mh[k].cartesian ? 0 : 1));
+          for (int bx = 0; bx < ntx; ++bx) items[j].push_back(make_int4(r, bx, by, curv));
       };
       for (auto *S : mem) {
         MemberBook b0 = save_book(S);
@@ -561,10 +567,14 @@ struct sbp_batch_s {
         if ((e = up(off, b.dl_off)) != cudaSuccess) return e;
         if ((e = up(rl[j], drl)) != cudaSuccess) return e;
         if ((e = up(items[j], b.items)) != cudaSuccess) return e;
+        if ((e = up(sat_off[j], b.sat_off)) != cudaSuccess) return e;
+        if ((e = up(rl_curv[j], b.rl_curv)) != cudaSuccess) return e;
         b.dl = ddl;
         b.rl = drl;
+        b.n_rl = (int)rl[j].size();
         b.n_dl = (int)dl[j].size();
         b.n_items = (int)items[j].size();
+        b.chunk = ty;
         b.bar_count = bar;
         b.bar_gen = bar + 1;
         b.err = err;
@@ -689,7 +699,9 @@ sbp_status sbp_batch_create(const sbp_system_t *systems, int n, int autotune, vo
     float best = 1e30f;
     int best_ty = 16;
     cudaError_t e = copy(true);
-    for (int ty : {8, 16}) {
+    std::vector<int> shapes = {8, 16};
+    if (!B->visc) shapes.insert(shapes.end(), {32, 64});  // single-pass strips (Euler)
+    for (int ty : shapes) {
       if (e != cudaSuccess) break;
       B->ty = ty;
       if ((e = B->build_plan()) != cudaSuccess) break;
@@ -739,6 +751,15 @@ sbp_status sbp_batch_info(sbp_batch_t B, int *members, int *rows_per_cta, int *g
   if (rows_per_cta) *rows_per_cta = B->ty;
   if (grid) *grid = B->grid;
   if (period) *period = B->period;
+  return SBP_OK;
+}
+
+sbp_status sbp_batch_set_shape(sbp_batch_t B, int rows) {
+  if (!B) return fail(SBP_ERR_ARG, "null batch");
+  if (!(rows == 8 || rows == 16 || ((rows == 32 || rows == 64 || rows == 128) && !B->visc)))
+    return fail(SBP_ERR_ARG, "rows must be 8 or 16 (tile pairs) or, for Euler batches, 32, 64 or 128 (strips)");
+  B->ty = rows;
+  CUDA_TRY(B->build_plan());
   return SBP_OK;
 }
 

@@ -135,9 +135,13 @@ struct BatchSubstep {
   const void *dl;     // DonorLaunch[n_dl] in device memory
   const int *dl_off;  // n_dl + 1 prefix sums of the (set, point) pairs per descriptor
   int n_dl;
-  const void *rl;     // RhsLaunch[] in device memory
-  const int4 *items;
+  const void *rl;     // RhsLaunch[n_rl] in device memory
+  int n_rl;
+  const int *sat_off; // n_rl + 1 prefix sums of the SAT points per descriptor (single-pass items)
+  const int *rl_curv; // per descriptor: curvilinear mesh
+  const int4 *items;  // (descriptor, tile column, tile row, curvilinear)
   int n_items;
+  int chunk;          // rows per item: 8, 16 = flux / derivative tile pair; >= 32 single-pass strips
   unsigned *bar_count;
   unsigned *bar_gen;
   int *err;

@@ -38,13 +38,11 @@ struct March {
 // SAT terms of every boundary / receiver point into a.sat, with the point's gradients from a
 // local copy of the primitives on its stencil cross (the arithmetic of flux_tile's SAT tail).
 template <typename T, bool VISC, bool CURV>
-__global__ void __launch_bounds__(128) k_sat(const RhsLaunch a) {
+__device__ __forceinline__ void sat_point(const RhsLaunch &a, int s) {
   const DevMesh &m = a.m;
   const KConst<T> &k = kc<T>(a);
   const T *q = static_cast<const T *>(a.q);
   T *satb = static_cast<T *>(a.sat);
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.nsat) return;
   uint32_t ij = a.sat_ij[s];
   int gi = (int)(ij & 0xFFFFu), gj = (int)(ij >> 16);
   size_t p = (size_t)gj * m.pitch + gi;
@@ -75,6 +73,12 @@ __global__ void __launch_bounds__(128) k_sat(const RhsLaunch a) {
   sat_terms<T, VISC>(a, s, qp, mt, Fv, Gv, acc);
 #pragma unroll
   for (int c = 0; c < 4; ++c) satb[c * a.nsat + s] = acc[c];
+}
+
+template <typename T, bool VISC, bool CURV>
+__global__ void __launch_bounds__(128) k_sat(const RhsLaunch a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < a.nsat) sat_point<T, VISC, CURV>(a, s);
 }
 
 // A thread's items of a window stage with `width` columns per row (R rows): row in the tick,
@@ -253,11 +257,12 @@ __device__ __forceinline__ void march_div_point(const KConst<T> &k, const T *fr,
   }
 }
 
+// One strip (bx) x chunk (by) of the mesh, by one CTA of 256 threads with M::bytes of shared
+// memory at smem_raw (the body of k_march, also run by the batched persistent kernel).
 template <typename T, bool VISC, bool CURV>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_march(const RhsLaunch a, int chunk) {
+__device__ __forceinline__ void march_tile(const RhsLaunch &a, int bx, int by, int chunk, unsigned char *smem_raw) {
   using M = March<T, VISC, CURV>;
   constexpr int W = M::W, R = M::R, PW = M::PW, FW = M::FW, NT = M::NT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *qr = reinterpret_cast<T *>(smem_raw);
   T *mr = qr + M::QR;
   T *prim = mr + M::MR;
@@ -266,8 +271,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
   const DevMesh &m = a.m;
   const KConst<T> &k = kc<T>(a);
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * W;
-  const int j0 = blockIdx.y * chunk, j1 = min(j0 + chunk, m.nj);
+  const int i0 = bx * W;
+  const int j0 = by * chunk, j1 = min(j0 + chunk, m.nj);
   const T *q = static_cast<const T *>(a.q);
   const T *satb = static_cast<const T *>(a.sat);
   const int nty8 = (m.nj + 7) / 8;
@@ -378,6 +383,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_ma
     march_store_cls<T, VISC, CURV>(pw, b + R, cr, cls);
   }
   cp_async_wait<0>();
+}
+
+template <typename T, bool VISC, bool CURV>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (CURV ? 2 : 3) : 1) k_march(const RhsLaunch a, int chunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  march_tile<T, VISC, CURV>(a, blockIdx.x, blockIdx.y, chunk, smem_raw);
 }
 
 template <typename T, bool VISC, bool CURV>

@@ -37,7 +37,7 @@ def test_batch_matches_single_systems(sbp, dtype):
     batched = _members(sbp, wls, dtype)
     b = sbp.Batch(batched, autotune=True)
     info = b.info()
-    assert info["members"] == 5 and info["rows_per_cta"] in (8, 16) and info["grid"] > 0
+    assert info["members"] == 5 and info["rows_per_cta"] in (8, 16, 32, 64) and info["grid"] > 0
     nsteps = 7
     b.step(nsteps)
     b.check()
@@ -52,6 +52,42 @@ def test_batch_matches_single_systems(sbp, dtype):
         assert gs.mrab_time() == gb.mrab_time()
     b.close()
     for g in single + batched:
+        g.close()
+
+
+@pytest.mark.parametrize("rows", [8, 16, 32, 64])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_shapes_match_single_systems(sbp, dtype, rows):
+    """Every work-item shape (tile pairs of 8 / 16 rows, single-pass strips of 32 / 64 rows)
+    reproduces each member stepped alone bit for bit, also after a change of shape between
+    steps (the plan is rebuilt from the members' current ring phase)."""
+    wls = W.batched_vortices(seed=6, n_systems=4, n_range=(40, 150), ratios=(1, 2, 4))
+    single = _members(sbp, wls, dtype)
+    batched = _members(sbp, wls, dtype)
+    b = sbp.Batch(batched, autotune=False)
+    b.step(2)
+    b.set_shape(rows)
+    assert b.info()["rows_per_cta"] == rows
+    b.step(5)
+    b.check()
+    for g in single:
+        g.mrab_step(7)
+        g.check()
+    for gs, gb in zip(single, batched):
+        for k in range(2):
+            assert np.array_equal(gs.to_host(k, gs.current_state(k)), gb.to_host(k, gb.current_state(k)))
+    b.close()
+    for g in single + batched:
+        g.close()
+
+
+def test_batch_shape_viscous_rejects_strips(sbp):
+    gs = _members(sbp, [W.cylinder_small(seed=3)], "f64")
+    b = sbp.Batch(gs, autotune=False)
+    with pytest.raises(sbp.SbpError):
+        b.set_shape(32)
+    b.close()
+    for g in gs:
         g.close()
 
 
