@@ -433,6 +433,11 @@ sbp_status sbp3_check(sbp3_system_t sys, void *stream);
  * kchunk outside 0..4096. */
 sbp_status sbp3_set_rhs_kernel(sbp3_system_t sys, int mesh, int kchunk);
 
+/* y[i] = x[i] widened from FP32 to FP64 (device buffers of n elements, asynchronous on stream),
+ * by the integer re-encoding that the FP32 forms use for their FP64 accumulations (the MRAB
+ * update and the slow-state extrapolation): exact, equal bit for bit to the hardware
+ * conversion for every input, without issuing to the FP64 pipe. */
+sbp_status sbp_f32_to_f64(const void *x, void *y, size_t n, void *stream);
 /* Synchronise the stream and report (then clear) the device error word. */
 sbp_status sbp_check(sbp_system_t sys, void *stream);
 

@@ -129,6 +129,7 @@ _SIGS.update({
     "sbp3_mrab_step": [_P, _I, _P],
     "sbp3_check": [_P, _P],
     "sbp3_set_rhs_kernel": [_P, _I, _I],
+    "sbp_f32_to_f64": [_P, _P, ctypes.c_size_t, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -635,6 +636,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def f32_to_f64(x, stream=None):
+    """Widen a contiguous FP32 CUDA tensor to FP64 with the library's integer re-encoding (the
+    conversion inside the FP32 forms' FP64 accumulations)."""
+    import torch
+    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("a contiguous float32 CUDA tensor is required")
+    y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    _check(_lib.sbp_f32_to_f64(_ptr(x), _ptr(y), x.numel(), _stream(stream)), "sbp_f32_to_f64")
+    return y
 
 
 def exported_symbols():

@@ -191,18 +191,29 @@ __device__ void visc3_at(const Dev3Mesh &m, const K3<T> &kk, const T *src, int i
   }
 }
 
-// A point whose derivative rows are the interior row in all three directions with all taps
-// inside the mesh (no periodic wrap): the taps are fixed offsets of the point's index.
-__device__ __forceinline__ bool central3(const Dev3Mesh &m, int i, int j, int k, unsigned code) {
-  return code == 0u && i >= 2 && i + 2 < m.ni && j >= 2 && j + 2 < m.nj && k >= 2 && k + 2 < m.nk;
+// Element offsets of the interior row's taps (-2, -1, +1, +2) along each direction at (i, j, k),
+// wrapped on periodic lines. Every point of class 0 takes them, so the warps of a mesh's interior
+// (periodic seams included) follow one path.
+__device__ __forceinline__ void central_offsets(const Dev3Mesh &m, int i, int j, int k, ptrdiff_t o[3][4]) {
+  const int c[3] = {i, j, k}, n[3] = {m.ni, m.nj, m.nk};
+  const ptrdiff_t st[3] = {1, (ptrdiff_t)m.pitch, (ptrdiff_t)m.pitch * m.nj};
+  const int off[4] = {-2, -1, 1, 2};
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int cc = c[d] + off[e];
+      wrap_index(cc, n[d], m.per[d]);
+      o[d][e] = (ptrdiff_t)(cc - c[d]) * st[d];
+    }
 }
 
-// The interior row applied to plane f at index p with element stride st.
+// The interior row applied to plane f at index p with the tap offsets o.
 template <typename T>
-__device__ __forceinline__ T csum3(const T *f, size_t p, ptrdiff_t st) {
+__device__ __forceinline__ T csum3(const T *f, size_t p, const ptrdiff_t o[4]) {
   T w[4];
   central_w(w);
-  return tap4(w, f[p - 2 * st], f[p - st], f[p + st], f[p + 2 * st]);
+  return tap4(w, f[p + o[0]], f[p + o[1]], f[p + o[2]], f[p + o[3]]);
 }
 
 // K^{side}_k dq through the eigen-decomposition of the 3D flux Jacobian along k: acoustic
@@ -276,12 +287,13 @@ __global__ void __launch_bounds__(256) k3_flux(const Rhs3Launch a) {
   T g[4][3], tau[3][3], vel[3];
   if (VISC) {
     const T *prim = static_cast<const T *>(a.prim);
-    if (central3(m, i, j, k, code)) {
-      const ptrdiff_t st[3] = {1, (ptrdiff_t)m.pitch, (ptrdiff_t)m.pitch * m.nj};
+    if (code == 0u) {
+      ptrdiff_t o[3][4];
+      central_offsets(m, i, j, k, o);
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int f = 0; f < 4; ++f) g[f][d] = mul_rn(kk.ih[d], csum3(prim + f * m.field, p, st[d]));
+        for (int f = 0; f < 4; ++f) g[f][d] = mul_rn(kk.ih[d], csum3(prim + f * m.field, p, o[d]));
     } else {
       grad3_at<T, false>(m, kk, prim, i, j, k, g);
     }
@@ -386,12 +398,13 @@ __global__ void __launch_bounds__(256) k3_update(const Rhs3Launch a) {
   if ((code & 15u) != 15u) {
     const T *fl = static_cast<const T *>(a.flux);
     T dsum[5] = {T(0), T(0), T(0), T(0), T(0)};
-    if (central3(m, i, j, k, code)) {
-      const ptrdiff_t st[3] = {1, (ptrdiff_t)m.pitch, (ptrdiff_t)m.pitch * m.nj};
+    if (code == 0u) {
+      ptrdiff_t o[3][4];
+      central_offsets(m, i, j, k, o);
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int v = 0; v < 5; ++v) dsum[v] = fma_rn(kk.ih[d], csum3(fl + (5 * d + v) * m.field, p, st[d]), dsum[v]);
+        for (int v = 0; v < 5; ++v) dsum[v] = fma_rn(kk.ih[d], csum3(fl + (5 * d + v) * m.field, p, o[d]), dsum[v]);
     } else {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -751,8 +764,8 @@ __device__ __forceinline__ void set_state3(const Donor3Launch &a, int set, size_
   const T *q = static_cast<const T *>(a.q);
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    double acc = (double)q[v * a.d.field + p];
-    for (int k = 0; k < a.nb[set]; ++k) acc += a.beta[set][k] * (double)static_cast<const T *>(a.hist[k])[v * a.d.field + p];
+    double acc = to_f64(q[v * a.d.field + p]);
+    for (int k = 0; k < a.nb[set]; ++k) acc += a.beta[set][k] * to_f64(static_cast<const T *>(a.hist[k])[v * a.d.field + p]);
     out[v] = (T)acc;
   }
 }

@@ -430,6 +430,12 @@ sbp_status sbp_profile_read(sbp_system_t S, double *ms, int *launches, int reset
   return SBP_OK;
 }
 
+sbp_status sbp_f32_to_f64(const void *x, void *y, size_t n, void *stream) {
+  if (n && (!x || !y)) return fail(SBP_ERR_ARG, "null buffer");
+  CUDA_TRY(launch_widen(static_cast<const float *>(x), static_cast<double *>(y), n, (cudaStream_t)stream));
+  return SBP_OK;
+}
+
 sbp_status sbp_check(sbp_system_t S, void *stream) {
   if (!S) return fail(SBP_ERR_ARG, "null system");
   cudaStream_t s = (cudaStream_t)stream;

@@ -161,6 +161,22 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+// Exact FP32 -> FP64 widening written from the IEEE 754 binary32 / binary64 layouts: the sign
+// kept, the exponent re-biased by 1023 - 127 = 896, the 23 fraction bits moved to the top of the
+// 52-bit fraction; zeros keep only their sign. Integer operations only, because GB300 issues the
+// hardware conversion to the FP64 pipe, which the FP64 accumulations of the FP32 forms (MRAB
+// update, slow-state extrapolation) already keep busy. Subnormal, infinite and NaN inputs take
+// the hardware conversion. Bit-identical to (double)x for every input.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned b = __float_as_uint(x), e = (b >> 23) & 0xFFu;
+  if (e - 1u < 254u)
+    return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu)), (int)(b << 29));
+  if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return (double)x;
+}
+__device__ __forceinline__ double to_f64(float x) { return widen(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+
 // Adams-Bashforth / MRAB update of one point's NV variables (Sec. 3.1 eq. (ab_general)):
 // qn = q + sum_h alpha[h] hold[h] + alpha[nold] rhs, accumulated in FP64 in that order. The
 // loads of one history slot's NV values are issued together, ahead of their products.
@@ -169,7 +185,7 @@ __device__ __forceinline__ void ab_update(const T qv[NV], const void *const *hol
                                           size_t field, size_t p, const T rhs[NV], T qn[NV]) {
   double acc[NV];
 #pragma unroll
-  for (int c = 0; c < NV; ++c) acc[c] = (double)qv[c];
+  for (int c = 0; c < NV; ++c) acc[c] = to_f64(qv[c]);
 #pragma unroll
   for (int h = 0; h < kMaxHist - 1; ++h) {
     if (h < nold) {
@@ -178,12 +194,12 @@ __device__ __forceinline__ void ab_update(const T qv[NV], const void *const *hol
 #pragma unroll
       for (int c = 0; c < NV; ++c) hv[c] = hp[c * field];
 #pragma unroll
-      for (int c = 0; c < NV; ++c) acc[c] += alpha[h] * (double)hv[c];
+      for (int c = 0; c < NV; ++c) acc[c] += alpha[h] * to_f64(hv[c]);
     }
   }
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
-    acc[c] += alpha[nold] * (double)rhs[c];
+    acc[c] += alpha[nold] * to_f64(rhs[c]);
     qn[c] = (T)acc[c];
   }
 }
@@ -738,9 +754,9 @@ __device__ __forceinline__ void set_state(const DonorLaunch &a, int set, size_t 
   const T *q = static_cast<const T *>(a.q);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    double acc = (double)q[v * a.d.field + p];
+    double acc = to_f64(q[v * a.d.field + p]);
     for (int k = 0; k < a.nb[set]; ++k)
-      acc += a.beta[set][k] * (double)static_cast<const T *>(a.hist[k])[v * a.d.field + p];
+      acc += a.beta[set][k] * to_f64(static_cast<const T *>(a.hist[k])[v * a.d.field + p]);
     out[v] = (T)acc;
   }
 }

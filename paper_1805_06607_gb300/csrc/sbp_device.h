@@ -253,6 +253,8 @@ cudaError_t launch_ab_combine(const void *q, const ABCombine &c, void *out, size
 // y_out = y + c1 k1 + c2 k2 (k2 may be NULL), FP64 accumulation, over n elements.
 cudaError_t launch_axpy(const void *y, const void *k1, double c1, const void *k2, double c2, void *y_out, size_t n,
                         int dtype, cudaStream_t s);
+// y = (double)x element by element through the integer widening of the FP32 forms.
+cudaError_t launch_widen(const float *x, double *y, size_t n, cudaStream_t s);
 // Interpolation + right-hand side with the receiver workspace in the library's fixed device
 // array (sbp_noalloc.cu); the qhat/fvhat pointers of the descriptors are replaced.
 cudaError_t rhs_eval_static_scratch(InterpLaunch ia, RhsLaunch ra, int dtype, bool viscous, size_t elem,

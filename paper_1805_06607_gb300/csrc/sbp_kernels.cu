@@ -25,8 +25,8 @@ __device__ __forceinline__ void donor_state(const InterpLaunch &a, size_t p, T o
   const T *q = static_cast<const T *>(a.q);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    double acc = (double)q[v * a.d.field + p];
-    for (int k = 0; k < a.nbeta; ++k) acc += a.beta[k] * (double)static_cast<const T *>(a.hist[k])[v * a.d.field + p];
+    double acc = to_f64(q[v * a.d.field + p]);
+    for (int k = 0; k < a.nbeta; ++k) acc += a.beta[k] * to_f64(static_cast<const T *>(a.hist[k])[v * a.d.field + p]);
     out[v] = (T)acc;
   }
 }
@@ -354,8 +354,8 @@ cudaError_t launch_metrics(const DevMesh &m, const double *x, const double *y, c
 template <typename T>
 __global__ void k_axpy(const T *y, const T *k1, double c1, const T *k2, double c2, T *yo, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    double acc = (double)y[t] + c1 * (double)k1[t];
-    if (k2) acc += c2 * (double)k2[t];
+    double acc = to_f64(y[t]) + c1 * to_f64(k1[t]);
+    if (k2) acc += c2 * to_f64(k2[t]);
     yo[t] = (T)acc;
   }
 }
@@ -374,14 +374,28 @@ cudaError_t launch_axpy(const void *y, const void *k1, double c1, const void *k2
 }
 
 
+// y = (double)x through widen() (the conversion of the FP32 forms' FP64 accumulations).
+__global__ void k_widen(const float *x, double *y, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = widen(x[t]);
+}
+
+cudaError_t launch_widen(const float *x, double *y, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_widen<<<blocks, 256, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
 // Adams-Bashforth state update without a new right-hand side (the slow step of the
 // slowest-first MRAB variants, whose newest history value already exists):
 // out = q + sum_k alpha_k hist_k in history order, FP64 accumulation.
 template <typename T>
 __global__ void k_ab_combine(const T *q, const ABCombine c, T *out, size_t n) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    double acc = (double)q[t];
-    for (int k = 0; k < c.nh; ++k) acc += c.alpha[k] * (double)static_cast<const T *>(c.hist[k])[t];
+    double acc = to_f64(q[t]);
+    for (int k = 0; k < c.nh; ++k) acc += c.alpha[k] * to_f64(static_cast<const T *>(c.hist[k])[t]);
     out[t] = (T)acc;
   }
 }
