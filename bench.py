@@ -284,7 +284,7 @@ class _Null:
 # (flux kernel 8 rows + derivative kernel 8 rows per CTA; the mean over the four micro steps of a
 # macro step, serialised replay with a cold L2).
 MEASURED_TRAFFIC = {
-    ("f64", "rhs_fast"): {"shape": (32, 8, 8), "bytes": 16.96e6,
+    ("f64", "rhs_fast"): {"shape": (32, 8, 8), "bytes": 16.94e6,
                           "source": "ncu --set full, profiles/k_flux_update_cylinder_fp64.md"},
 }
 
