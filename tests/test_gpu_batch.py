@@ -99,3 +99,25 @@ def test_batch_member_kinds_must_match(sbp):
         sbp.Batch(gs)
     for g in gs:
         g.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_full_size_batch_matches_single_systems(sbp, dtype):
+    """The benchmark's batch at full size (64 systems, backgrounds 128^2..512^2, step ratios 2, 4
+    and 8) with the autotuner's work-item shape: one macro step of the batch equals each member's
+    own macro step bit for bit."""
+    wls = W.batched_vortices(seed=0)
+    single = _members(sbp, wls, dtype)
+    batched = _members(sbp, wls, dtype)
+    b = sbp.Batch(batched, autotune=True)
+    b.step(1)
+    b.check()
+    for g in single:
+        g.mrab_step(1)
+        g.check()
+    for gs, gb in zip(single, batched):
+        for k in range(2):
+            assert np.array_equal(gs.to_host(k, gs.current_state(k)), gb.to_host(k, gb.current_state(k)))
+    b.close()
+    for g in single + batched:
+        g.close()

@@ -219,3 +219,26 @@ def test_full_size_cylinder_rhs(sbp):
         want = ref.coupled_rhs(k, wl["q0"][k], wl["q0"][1 - k])
         assert rel(got, want) < 1e-12, (k, rel(got, want))
     g.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_full_size_cylinder_mrab(sbp, dtype, tol):
+    """The benchmark's step at full size and in its launch configuration (autotuned kernel
+    shapes, CUDA-graph macro steps): the Runge-Kutta bootstrap and two MRAB macro steps against
+    the oracle's."""
+    wl = W.cylinder_overset(seed=1)
+    ref = OracleSystem(wl)
+    H = ref.macro_step_size(wl["q0"])
+    y, hf, hs = ref.bootstrap(wl["q0"], H)
+    want, _, _ = ref.mrab(y, hf, hs, H, 2)
+    g = sbp.System(wl, dtype=dtype)
+    g.bind(wl["q0"])
+    g.mrab_init()
+    g.mrab_step(2)
+    g.check()
+    for k in range(2):
+        act = ref.iblank[k] != 0
+        got = g.to_host(k, g.current_state(k))
+        e = rel(got[:, act], want[k][:, act])
+        assert e < tol, (dtype, k, e)
+    g.close()
