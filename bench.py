@@ -535,7 +535,7 @@ def _rhs_eval_large(hbm_peak, peak_kind, reps=10):
                 gbs = pts * bpp / (ms / 1e3) / 1e9
                 res[mesh] = {"points": pts, "ms": ms, "gpts_per_s": pts / (ms / 1e3) / 1e9, "bytes_per_point": bpp,
                              "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
-                             "kernel": ("single pass, 64-column strips, %d-row chunks" % inf.rows_per_cta
+                             "kernel": ("single pass, %d-column strips, %d-row chunks" % (inf.strip_width, inf.rows_per_cta)
                                         if inf.single_pass else "flux + derivative pair, %d / %d rows"
                                         % (inf.rows_per_cta, inf.rows_update))}
             g.check()

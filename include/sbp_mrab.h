@@ -218,7 +218,7 @@ sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
 /* Autotuner of the right-hand side's kernel and block shape. Two kernel designs compute the
  * same bits: a pair (contravariant fluxes of a 32 x rows tile with a halo-3 primitive tile in
  * shared memory, then derivatives + SAT + update from a halo-3 flux tile; 8, 16 or 32 rows per
- * CTA), and a single pass that marches a strip of 64 columns up a chunk of 16, 32, 64 or 128
+ * CTA), and a single pass that marches a strip of 58 columns up a chunk of 16, 32, 64 or 128
  * rows, 4 rows per step, with 16-row ring buffers of state, metrics, class bytes (copied one
  * step ahead with cp.async), primitives and fluxes in shared memory (state, metrics and result
  * cross HBM once). For each mesh the autotuner times every candidate on the bound state
@@ -283,7 +283,7 @@ sbp_status sbp_profile_read(sbp_system_t sys, double *ms, int *launches, int res
  * (all Cartesian or all curvilinear) and have a Cartesian slow mesh; they stay usable on their
  * own (their states and ring positions follow the batch). The results equal stepping each
  * member alone. Euler batches may instead run the single-pass right-hand side: the launch's
- * phases are then donor values, the SAT values of every boundary / receiver point, and 64-column
+ * phases are then donor values, the SAT values of every boundary / receiver point, and 58-column
  * strips of 32 or 64 rows (the marching kernel's body), with the same bits. autotune != 0 picks
  * the work-item shape (tile pairs of 8 or 16 rows; for Euler also strips of 32 or 64 rows) by
  * timing two macro steps per candidate on a snapshot of every member's buffers (restored
@@ -294,7 +294,7 @@ sbp_status sbp_batch_destroy(sbp_batch_t batch);
 /* n macro steps of every member (asynchronous). */
 sbp_status sbp_batch_step(sbp_batch_t batch, int n, void *stream);
 /* members, rows per work item (8, 16: tile pairs of 32 columns; 32, 64: single-pass strips of
- * 64 columns), cooperative grid size, number of ring phases (graphs). */
+ * 58 columns), cooperative grid size, number of ring phases (graphs). */
 sbp_status sbp_batch_info(sbp_batch_t batch, int *members, int *rows_per_cta, int *grid, int *period);
 /* Work-item shape (replaces the autotuner's choice; between steps): rows = 8 or 16 for tile
  * pairs, 32, 64 or 128 for single-pass strips (Euler batches only); SBP_ERR_ARG otherwise. */

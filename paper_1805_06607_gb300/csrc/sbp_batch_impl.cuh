@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (VISC ? 3 : 4) : (VISC ?
   }
 }
 
-// The same micro step with the single-pass right-hand side (march_tile, 64-column strips of
+// The same micro step with the single-pass right-hand side (march_tile, kMarchW-column strips of
 // b.chunk rows): donor values; SAT values of every boundary / receiver point of all meshes;
 // then the strips. The SAT phase replaces k_sat, the strips k_march.
 template <typename T, bool VISC, bool CURVF>

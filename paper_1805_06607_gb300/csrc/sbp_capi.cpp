@@ -346,7 +346,7 @@ sbp_status sbp_set_rhs_shape(sbp_system_t S, int k, int strip, int rows) {
     d.rows_per_cta = rf;
     d.rows_upd = ru;
   } else {
-    if (strip != 64) return fail(SBP_ERR_ARG, "the marching kernel takes strips of 64 columns");
+    if (strip != kMarchW) return fail(SBP_ERR_ARG, "the marching kernel takes strips of " + std::to_string(kMarchW) + " columns");
     if (rows < 1 || rows > 65535) return fail(SBP_ERR_ARG, "chunk rows out of range");
     d.strip = strip;
     d.chunk = rows;
@@ -539,8 +539,8 @@ struct sbp_batch_s {
         sat_off[j].push_back(sat_off[j].back() + a.nsat);
         const int curv = S->mh[k].cartesian ? 0 : 1;
         rl_curv[j].push_back(curv);
-        // ty >= 32: single-pass strips of 64 columns and ty rows; else 32 x ty tiles
-        const int tw = ty >= 32 ? 64 : kTileX;
+        // ty >= 32: single-pass strips of kMarchW columns and ty rows; else 32 x ty tiles
+        const int tw = ty >= 32 ? kMarchW : kTileX;
         int ntx = (S->mh[k].ni + tw - 1) / tw, nty = (S->mh[k].nj + ty - 1) / ty;
         for (int by = 0; by < nty; ++by)
           for (int bx = 0; bx < ntx; ++bx) items[j].push_back(make_int4(r, bx, by, curv));

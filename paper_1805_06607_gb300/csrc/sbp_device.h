@@ -57,8 +57,8 @@ struct RhsLaunch {
   const int *tile_sat;
   int rows_per_cta;  // 8, 16 or 32: rows per CTA of the split kernels' flux kernel
   int rows_upd;      // 4, 8, 16 or 32: rows per CTA of their update kernel (0: rows_per_cta)
-  // strip = 0: split kernels (k_flux, k_update); 64: the single-pass marching kernel (k_march)
-  // with strips of 64 columns and chunks of `chunk` rows per CTA
+  // strip = 0: split kernels (k_flux, k_update); kMarchW: the single-pass marching kernel
+  // (k_march) with strips of kMarchW columns and chunks of `chunk` rows per CTA
   int strip, chunk;
   void *flux;        // 8 planes: F^_xi (4 variables), F^_eta (4 variables)
   // Navier-Stokes primitives (u, v, T: 3 planes of the state's layout). prim_in: the flux
@@ -126,6 +126,9 @@ struct DonorLaunch {
 
 // Columns per CTA and threads per CTA of the right-hand-side kernels.
 constexpr int kTileX = 32;
+// Columns of a single-pass (marching) strip: 256 threads cover 4 rows of its 64-column flux
+// window (the strip plus a 3-point halo per side) in one pass.
+constexpr int kMarchW = 58;
 constexpr int kNT = 256;
 
 // One micro step of a batch of systems (a cooperative launch): donor values of the listed

@@ -1,4 +1,4 @@
-// Single-pass right-hand side of one mesh: a CTA owns a strip of W = 64 columns and a chunk of
+// Single-pass right-hand side of one mesh: a CTA owns a strip of W = kMarchW columns and a chunk of
 // rows and marches up the chunk R = 4 rows at a time, keeping the rows its stencils still need
 // in 16-row ring buffers in shared memory: the state, the metrics and the class bytes of the
 // window columns [i0 - 6, i0 + W + 6) (copied one tick ahead with cp.async, so the copies of the
@@ -23,7 +23,7 @@ constexpr unsigned kNoCls = 0x100u;  // "no class byte fetched" (outside the mes
 
 template <typename T, bool VISC, bool CURV>
 struct March {
-  static constexpr int W = 64, NT = 256, R = NT / W;
+  static constexpr int W = kMarchW, NT = 256, R = NT / W;
   static constexpr int PW = W + 12, FW = W + 6;
   static constexpr int QR = 4 * kRing * PW;                // state ring
   static constexpr int MR = CURV ? 5 * kRing * PW : 0;     // metric ring
@@ -325,7 +325,7 @@ __device__ __forceinline__ void march_tile(const RhsLaunch &a, int bx, int by, i
     {
       const int rr = tid / W, cc = tid - rr * W;
       const int gj = b - 6 + rr, gi = i0 + cc;
-      if (gj >= j0 && gj < j1 && gi < m.ni) {
+      if (rr < R && gj >= j0 && gj < j1 && gi < m.ni) {
         const size_t p = (size_t)gj * m.pitch + gi;
         const int o = (gj & (kRing - 1)) * PW + cc + 6;
         const unsigned code = cr[o];
@@ -414,7 +414,7 @@ static cudaError_t launch_march_vc(const RhsLaunch &a, cudaStream_t s) {
 
 template <typename T, bool VISC, bool CURV>
 static cudaError_t launch_march_w(const RhsLaunch &a, cudaStream_t s) {
-  if (a.strip != 64) return cudaErrorInvalidValue;
+  if (a.strip != kMarchW) return cudaErrorInvalidValue;
   return launch_march_vc<T, VISC, CURV>(a, s);
 }
 

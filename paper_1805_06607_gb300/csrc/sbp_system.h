@@ -648,14 +648,14 @@ struct sbp_system_s {
   // Autotuner of the right-hand side's kernel and block shape: for each mesh, time the
   // right-hand side (mode 0, into the state buffer the next step overwrites) on the bound state
   // with the split kernels at 8, 16 and 32 rows per CTA and with the marching kernel (strips of
-  // 64 columns) at chunks of 16, 32, 64 and 128 rows, and keep the fastest.
+  // kMarchW columns) at chunks of 16, 32, 64 and 128 rows, and keep the fastest.
   bool autotune_on = true;
   cudaError_t autotune(cudaStream_t s) {
     struct Cand {
       int strip, rows, rows_upd;
     };
     static const Cand cands[] = {{0, 8, 0},   {0, 8, 4},   {0, 16, 0},  {0, 16, 8},  {0, 16, 4}, {0, 32, 0},
-                                 {0, 32, 16}, {64, 16, 0}, {64, 32, 0}, {64, 64, 0}, {64, 128, 0}};
+                                 {0, 32, 16}, {kMarchW, 16, 0}, {kMarchW, 32, 0}, {kMarchW, 64, 0}, {kMarchW, 128, 0}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);

@@ -32,7 +32,7 @@ CASES = {
     "cylinder_ragged": lambda: W.cylinder_small(seed=33, n_theta=72, n_r=20, bg_n=(90, 50), hist_len=4),
     "cylinder_sponge": lambda: W.cylinder_small(seed=36, sponge_cells=6, sponge_strength=2.0),
 }
-SHAPES = [(64, 7), (64, 32), (64, 1), (64, 24), (64, 128), (64, 1000)]
+SHAPES = [(58, 7), (58, 32), (58, 1), (58, 24), (58, 128), (58, 1000)]
 
 
 def _rel(a, b):
@@ -58,7 +58,7 @@ def test_march_rhs_bit_identical(sbp, case, dtype):
     if dtype == "f64":
         o = OracleSystem(wl)
         for k in range(2):
-            g.set_rhs_shape(k, 64, 24)
+            g.set_rhs_shape(k, 58, 24)
             got = g.to_host(k, g.rhs_eval(k, q[k], q[1 - k]))
             want = o.coupled_rhs(k, wl["q0"][k], wl["q0"][1 - k])
             act = o.iblank[k] != 0
@@ -105,7 +105,7 @@ def test_pair_row_splits_bit_identical(sbp, case, dtype):
 def test_march_mrab_bit_identical(sbp, case, dtype):
     wl = CASES[case]()
     runs = []
-    for shape in [(0, 8), (64, 40), (64, 16)]:
+    for shape in [(0, 8), (58, 40), (58, 16)]:
         g = sbp.System(wl, dtype=dtype)
         g.autotune(False)
         for k in range(2):
@@ -129,7 +129,7 @@ def test_autotuner_reports_a_candidate(sbp):
     for k in range(2):
         info = g.mesh_info(k)
         if info.single_pass:
-            assert info.strip_width == 64 and info.rows_per_cta in (16, 32, 64, 128)
+            assert info.strip_width == 58 and info.rows_per_cta in (16, 32, 64, 128)
         else:
             assert info.strip_width == 32 and info.rows_per_cta in (8, 16, 32)
 
@@ -137,6 +137,6 @@ def test_autotuner_reports_a_candidate(sbp):
 def test_bad_shapes_rejected(sbp):
     wl = W.vortex_box_in_box(seed=35, n_bg=40, n_fine=25)
     g = sbp.System(wl)
-    for args in [(0, 12), (48, 32), (32, 32), (64, 0), (64, -3), (0, 16 | (12 << 8))]:
+    for args in [(0, 12), (48, 32), (32, 32), (64, 32), (58, 0), (58, -3), (0, 16 | (12 << 8))]:
         with pytest.raises(sbp.SbpError):
             g.set_rhs_shape(0, *args)
