@@ -123,7 +123,9 @@ typedef struct {
 /* Create a two-mesh overset system (mesh 0 = background, mesh 1 = the overset fine mesh) and
  * run its setup (Sec. 2.2 and Sec. 4.1): hole cut, SBP segment classes, metrics (computed on
  * the device by the derivative operator), SAT lists, donor search and Lagrange weights, and
- * the Adams-Bashforth / MRAB coefficient plan (Sec. 3.1-3.3). Synchronous. */
+ * the Adams-Bashforth / MRAB coefficient plan (Sec. 3.1-3.3). Synchronous. Each mesh needs
+ * 8..65535 points per direction (SBP_ERR_SHAPE otherwise: the closures need 8 points, and the
+ * point tables pack (i, j) into 16 bits each). */
 sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params,
                              sbp_system_t *out);
 sbp_status sbp_system_destroy(sbp_system_t sys);

@@ -21,6 +21,10 @@ sbp_status setup_mesh_basic(const sbp_mesh_desc &d, MeshHost &m, std::string &er
     err = "mesh needs at least 8 points per direction";
     return SBP_ERR_SHAPE;
   }
+  if (m.ni > 65535 || m.nj > 65535) {  // point tables pack (i, j) into 16 bits each
+    err = "mesh has more than 65535 points in a direction";
+    return SBP_ERR_SHAPE;
+  }
   m.pitch = round_up(m.ni, 32);
   for (int k = 0; k < 2; ++k) {
     m.per[k] = d.periodic[k] ? 1 : 0;

@@ -242,3 +242,15 @@ def test_full_size_cylinder_mrab(sbp, dtype, tol):
         e = rel(got[:, act], want[k][:, act])
         assert e < tol, (dtype, k, e)
     g.close()
+
+
+@pytest.mark.parametrize("n", [(7, 40), (40, 7), (65536, 8), (8, 65536)])
+def test_mesh_size_limits_rejected(sbp, n):
+    """Meshes below the closures' 8 points or above the 16-bit point tables' 65535 points per
+    direction are refused at creation (the fine patch is the same small one every time)."""
+    bg = W.cartesian_mesh("background", n, (-1.0, -1.0), (2.0 / n[0], 2.0 / n[1]), ("farfield",) * 4)
+    fine = W.cartesian_mesh("fine", (25, 25), (-0.2, -0.2), (0.4 / 24, 0.4 / 24), ("interface",) * 4)
+    wl = W.vortex_box_in_box(seed=1, n_bg=40, n_fine=25)
+    wl = dict(wl, meshes=[bg, fine], q0=[np.ones((4, n[1], n[0])), np.ones((4, 25, 25))])
+    with pytest.raises(sbp.SbpError):
+        sbp.System(wl)
