@@ -81,6 +81,31 @@ def test_batch_shapes_match_single_systems(sbp, dtype, rows):
         g.close()
 
 
+@pytest.mark.parametrize("rows", [16, 32])
+def test_batch_curvilinear_euler_shapes(sbp, rows):
+    """Euler systems with a curvilinear fine mesh (small cylinders at step ratios 2 and 3) in a
+    batch: tile pairs and single-pass strips on both mesh kinds reproduce the members."""
+    wls = []
+    for seed, sr in ((41, 2), (42, 3), (43, 2)):
+        wl = W.cylinder_small(seed=seed, step_ratio=sr)
+        wls.append(dict(wl, params=dict(wl["params"], physics="euler", mu=0.0)))
+    single = _members(sbp, wls, "f32")
+    batched = _members(sbp, wls, "f32")
+    b = sbp.Batch(batched, autotune=False)
+    b.set_shape(rows)
+    b.step(4)
+    b.check()
+    for g in single:
+        g.mrab_step(4)
+        g.check()
+    for gs, gb in zip(single, batched):
+        for k in range(2):
+            assert np.array_equal(gs.to_host(k, gs.current_state(k)), gb.to_host(k, gb.current_state(k)))
+    b.close()
+    for g in single + batched:
+        g.close()
+
+
 def test_batch_shape_viscous_rejects_strips(sbp):
     gs = _members(sbp, [W.cylinder_small(seed=3)], "f64")
     b = sbp.Batch(gs, autotune=False)

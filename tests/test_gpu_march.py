@@ -31,7 +31,13 @@ CASES = {
     "mms_viscous": lambda: W.mms_box_in_box(52, "viscous"),
     "cylinder_ragged": lambda: W.cylinder_small(seed=33, n_theta=72, n_r=20, bg_n=(90, 50), hist_len=4),
     "cylinder_sponge": lambda: W.cylinder_small(seed=36, sponge_cells=6, sponge_strength=2.0),
+    "cylinder_euler": lambda: _euler(W.cylinder_small(seed=37)),
 }
+
+
+def _euler(wl):
+    """The same meshes and state with the Euler equations (no viscous terms)."""
+    return dict(wl, params=dict(wl["params"], physics="euler", mu=0.0))
 SHAPES = [(58, 7), (58, 32), (58, 1), (58, 24), (58, 128), (58, 1000)]
 
 
