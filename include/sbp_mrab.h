@@ -220,11 +220,13 @@ sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
 /* Autotuner of the right-hand side's kernel and block shape. Two kernel designs compute the
  * same bits: a pair (contravariant fluxes of a 32 x rows tile with a halo-3 primitive tile in
  * shared memory, then derivatives + SAT + update from a halo-3 flux tile; 8, 16 or 32 rows per
- * CTA), and a single pass that marches a strip of 58 columns up a chunk of 16, 32, 64 or 128
+ * CTA), and a single pass that marches a strip of 58 columns up a chunk of 8, 16, 32, 64 or 128
  * rows, 4 rows per step, with 16-row ring buffers of state, metrics, class bytes (copied one
  * step ahead with cp.async), primitives and fluxes in shared memory (state, metrics and result
- * cross HBM once). For each mesh the autotuner times every candidate on the bound state
- * and keeps the fastest (reported by sbp_mesh_info_get). It runs at the end of sbp_mrab_init
+ * cross HBM once). For each mesh the autotuner times every candidate on the bound state, as
+ * the fused right-hand side + MRAB update of the next macro step (its outputs go to the state
+ * buffer that step overwrites; the history is only read), and keeps the fastest (reported by
+ * sbp_mesh_info_get). It runs at the end of sbp_mrab_init
  * while enabled (the default); enabling it on an initialised system runs it at once.
  * Synchronises the stream. */
 sbp_status sbp_autotune(sbp_system_t sys, int enable, void *stream);

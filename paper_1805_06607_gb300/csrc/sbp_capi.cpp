@@ -318,8 +318,7 @@ sbp_status sbp_mrab_init(sbp_system_t S, double H, void *stream) {
   S->initialised = true;
   S->clear_graphs();
   if (S->autotune_on) CUDA_TRY(S->autotune(s));
-  // slowest-first macro steps start with the slow history ending at the current time (after
-  // the autotuner, which uses the slot this push fills as scratch)
+  // slowest-first macro steps start with the slow history ending at the current time
   if (S->p.scheme != SBP_MRAB_FASTEST_FIRST) CUDA_TRY(S->slow_rhs_push(s));
   return SBP_OK;
 }

@@ -135,7 +135,7 @@ def test_autotuner_reports_a_candidate(sbp):
     for k in range(2):
         info = g.mesh_info(k)
         if info.single_pass:
-            assert info.strip_width == 58 and info.rows_per_cta in (16, 32, 64, 128)
+            assert info.strip_width == 58 and info.rows_per_cta in (8, 16, 32, 64, 128)
         else:
             assert info.strip_width == 32 and info.rows_per_cta in (8, 16, 32)
 
