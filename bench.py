@@ -192,7 +192,9 @@ def _run_gpu(wl, dtype, steps, warmup, world, local, sample_clocks=True):
     g.mrab_init()
     torch.cuda.synchronize()
     tuning = {name: {"strip_width": g.mesh_info(k).strip_width, "rows_per_cta": g.mesh_info(k).rows_per_cta,
-                     "rows_update": g.mesh_info(k).rows_update}
+                     "rows_update": g.mesh_info(k).rows_update,
+                     "rhs_eval": [g.mesh_info(k).eval_strip_width, g.mesh_info(k).eval_rows_per_cta,
+                                  g.mesh_info(k).eval_rows_update]}
               for k, name in enumerate(("background", "ogrid"))}
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -538,9 +540,10 @@ def _rhs_eval_large(hbm_peak, peak_kind, reps=10):
                 gbs = pts * bpp / (ms / 1e3) / 1e9
                 res[mesh] = {"points": pts, "ms": ms, "gpts_per_s": pts / (ms / 1e3) / 1e9, "bytes_per_point": bpp,
                              "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
-                             "kernel": ("single pass, %d-column strips, %d-row chunks" % (inf.strip_width, inf.rows_per_cta)
-                                        if inf.single_pass else "flux + derivative pair, %d / %d rows"
-                                        % (inf.rows_per_cta, inf.rows_update))}
+                             "kernel": ("single pass, %d-column strips, %d-row chunks"
+                                        % (inf.eval_strip_width, inf.eval_rows_per_cta)
+                                        if inf.eval_single_pass else "flux + derivative pair, %d / %d rows"
+                                        % (inf.eval_rows_per_cta, inf.eval_rows_update))}
             g.check()
             g.close()
             out["%s_%s" % (name, dtype)] = res

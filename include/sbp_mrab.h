@@ -118,6 +118,10 @@ typedef struct {
   int single_pass;      /* 1: the single-pass marching kernel (rows_per_cta = its chunk of rows);
                            0: the flux + derivative kernel pair */
   int rows_update;      /* kernel pair: rows per CTA of the derivative (update) kernel, 4..32 */
+  /* The four fields above describe the kernels of the fused right-hand side + MRAB update
+   * (sbp_mrab_step); these describe those of the right-hand side alone (sbp_rhs_eval,
+   * sbp_rhs_eval_noalloc, Runge-Kutta stages), which the autotuner chooses separately. */
+  int eval_strip_width, eval_rows_per_cta, eval_single_pass, eval_rows_update;
 } sbp_mesh_info;
 
 /* Create a two-mesh overset system (mesh 0 = background, mesh 1 = the overset fine mesh) and

@@ -52,7 +52,9 @@ class MeshInfo(ctypes.Structure):
                 ("hist_bytes", ctypes.c_size_t), ("nvar", ctypes.c_int), ("n_holes", ctypes.c_int),
                 ("n_receivers", ctypes.c_int), ("n_sat_points", ctypes.c_int), ("elem_size", ctypes.c_int),
                 ("strip_width", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("single_pass", ctypes.c_int),
-                ("rows_update", ctypes.c_int)]
+                ("rows_update", ctypes.c_int), ("eval_strip_width", ctypes.c_int),
+                ("eval_rows_per_cta", ctypes.c_int), ("eval_single_pass", ctypes.c_int),
+                ("eval_rows_update", ctypes.c_int)]
 
 
 class Mesh3Desc(ctypes.Structure):

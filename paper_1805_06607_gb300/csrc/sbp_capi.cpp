@@ -110,7 +110,7 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
     for (size_t t = 0; t + 1 < toff.size(); ++t) toff[t + 1] += toff[t];
     CUDA_TRY(upload(d.tile_sat, toff.data(), toff.size() * sizeof(int)));
     CUDA_TRY(cudaMalloc(&d.flux, 8 * field * S->esz));
-    d.rows_per_cta = 16;
+    d.rows_per_cta = d.e_rows = 16;
     if (p.physics == SBP_NS && k == p.fast_mesh) {
       CUDA_TRY(cudaMalloc(&d.prim, 3 * field * S->esz));
       CUDA_TRY(cudaMemset(d.prim, 0, 3 * field * S->esz));
@@ -165,6 +165,11 @@ sbp_status sbp_mesh_info_get(sbp_system_t S, int k, sbp_mesh_info *info) {
   info->rows_update = S->md[k].strip ? 0 : (S->md[k].rows_upd ? S->md[k].rows_upd : S->md[k].rows_per_cta);
   info->strip_width = S->md[k].strip ? S->md[k].strip : kTileX;
   info->single_pass = S->md[k].strip ? 1 : 0;
+  const MeshDev &d = S->md[k];
+  info->eval_rows_per_cta = d.e_strip ? d.e_chunk : d.e_rows;
+  info->eval_rows_update = d.e_strip ? 0 : (d.e_rows_upd ? d.e_rows_upd : d.e_rows);
+  info->eval_strip_width = d.e_strip ? d.e_strip : kTileX;
+  info->eval_single_pass = d.e_strip ? 1 : 0;
   return SBP_OK;
 }
 
@@ -235,7 +240,7 @@ sbp_status sbp_rhs_eval_noalloc(sbp_system_t S, int k, const void *q_self, const
   ia.nrecv = nrecv;
   ia.base = S->md[k].base;
   ia.w = S->md[k].w;
-  RhsLaunch ra = S->rhs_args(k, q_self);
+  RhsLaunch ra = S->rhs_args(k, q_self, true);
   ra.mode = 0;
   ra.out = rhs;
   CUDA_TRY(rhs_eval_static_scratch(ia, ra, S->p.dtype, S->viscous(), S->esz, (cudaStream_t)stream));
@@ -341,14 +346,14 @@ sbp_status sbp_set_rhs_shape(sbp_system_t S, int k, int strip, int rows) {
     if (rf != 8 && rf != 16 && rf != 32) return fail(SBP_ERR_ARG, "split kernels take 8, 16 or 32 rows per CTA");
     if (ru != 0 && ru != 4 && ru != 8 && ru != 16 && ru != 32)
       return fail(SBP_ERR_ARG, "the derivative kernel takes 4, 8, 16 or 32 rows per CTA");
-    d.strip = 0;
-    d.rows_per_cta = rf;
-    d.rows_upd = ru;
+    d.strip = d.e_strip = 0;
+    d.rows_per_cta = d.e_rows = rf;
+    d.rows_upd = d.e_rows_upd = ru;
   } else {
     if (strip != kMarchW) return fail(SBP_ERR_ARG, "the marching kernel takes strips of " + std::to_string(kMarchW) + " columns");
     if (rows < 1 || rows > 65535) return fail(SBP_ERR_ARG, "chunk rows out of range");
-    d.strip = strip;
-    d.chunk = rows;
+    d.strip = d.e_strip = strip;
+    d.chunk = d.e_chunk = rows;
   }
   S->clear_graphs();
   return SBP_OK;

@@ -65,6 +65,8 @@ struct MeshDev {
   int rows_per_cta = 16;
   int rows_upd = 0;           // rows per CTA of the update kernel (0: rows_per_cta)
   int strip = 0, chunk = 64;  // strip > 0: the single-pass marching kernel (see RhsLaunch)
+  // the same choice for right-hand sides without the update (rhs_eval, Runge-Kutta stages)
+  int e_strip = 0, e_chunk = 64, e_rows = 16, e_rows_upd = 0;
   void *prim = nullptr;       // Navier-Stokes fast mesh: primitives handed from micro step to micro step
   // bound integrator buffers
   void *q[2] = {nullptr, nullptr};
@@ -273,16 +275,18 @@ struct sbp_system_s {
     return launch_interp(a, p.dtype, viscous(), s);
   }
 
-  RhsLaunch rhs_args(int k, const void *q) const {
+  // Launch descriptor of mesh k's right-hand side at state q, with the kernel shape chosen for
+  // the fused right-hand side + update (eval = false) or for the right-hand side alone (true).
+  RhsLaunch rhs_args(int k, const void *q, bool eval = false) const {
     RhsLaunch a{};
     a.m = dev_mesh(k);
     a.g = gas();
     a.q = q;
     a.tile_sat = md[k].tile_sat;
-    a.rows_per_cta = md[k].rows_per_cta;
-    a.rows_upd = md[k].rows_upd;
-    a.strip = md[k].strip;
-    a.chunk = md[k].chunk;
+    a.rows_per_cta = eval ? md[k].e_rows : md[k].rows_per_cta;
+    a.rows_upd = eval ? md[k].e_rows_upd : md[k].rows_upd;
+    a.strip = eval ? md[k].e_strip : md[k].strip;
+    a.chunk = eval ? md[k].e_chunk : md[k].chunk;
     a.flux = md[k].flux;
     a.sat_ij = md[k].sat_ij;
     a.sat_code = md[k].sat_code;
@@ -347,7 +351,7 @@ struct sbp_system_s {
   cudaError_t rhs_plain(int k, const void *q_self, const void *q_other, void *out, cudaStream_t s) {
     cudaError_t e = interp(k, q_other, nullptr, nullptr, 0, s);
     if (e != cudaSuccess) return e;
-    RhsLaunch a = rhs_args(k, q_self);
+    RhsLaunch a = rhs_args(k, q_self, true);
     a.mode = 0;
     a.out = out;
     return launch_rhs(a, p.dtype, viscous(), s);
@@ -472,7 +476,7 @@ struct sbp_system_s {
   cudaError_t slow_rhs_at(const void *q, cudaStream_t s) {
     const int Sl = slow();
     const MeshDev &d = md[Sl];
-    RhsLaunch a = rhs_args(Sl, q);
+    RhsLaunch a = rhs_args(Sl, q, true);
     a.dv = d.dv;
     a.didx = d.didx;
     a.ndv = d.ndv;
@@ -645,10 +649,14 @@ struct sbp_system_s {
     t += H;
   }
 
-  // Autotuner of the right-hand side's kernel and block shape: for each mesh, time the fused
-  // right-hand side + MRAB update (into the state buffer the next step overwrites) on the bound
-  // state with the split kernels at 8, 16 and 32 rows per CTA and with the marching kernel (strips of
-  // kMarchW columns) at chunks of 8, 16, 32, 64 and 128 rows, and keep the fastest.
+  // Autotuner of the right-hand side's kernel and block shape: for each mesh and each use, time
+  // every candidate on the bound state and keep the fastest. The uses are the fused right-hand
+  // side + MRAB update of the macro step (a fast mesh's micro step 1, which takes the primitives
+  // handed over by micro step 0) and the right-hand side alone (rhs_eval, Runge-Kutta stages),
+  // both with their outputs in the state buffer the next step overwrites (each point's stores
+  // come from its own thread; the bound history is only read). Candidates: the split kernels at
+  // 8, 16 and 32 rows per CTA and the marching kernel (strips of kMarchW columns) at chunks of
+  // 8, 16, 32, 64 and 128 rows; each timed as the faster of two runs of three launches.
   bool autotune_on = true;
   cudaError_t autotune(cudaStream_t s) {
     struct Cand {
@@ -657,6 +665,7 @@ struct sbp_system_s {
     static const Cand cands[] = {{0, 8, 0},   {0, 8, 4},   {0, 16, 0},  {0, 16, 8},  {0, 16, 4}, {0, 32, 0},
                                  {0, 32, 16}, {kMarchW, 8, 0}, {kMarchW, 16, 0}, {kMarchW, 32, 0}, {kMarchW, 64, 0},
                                  {kMarchW, 128, 0}};
+    Cand step_shape[2] = {{0, 16, 0}, {0, 16, 0}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -664,42 +673,55 @@ struct sbp_system_s {
       MeshDev &d = md[k];
       if (!d.hist) continue;
       e = interp(k, md[1 - k].q[md[1 - k].cur], nullptr, nullptr, 0, s);
-      float best = 1e30f;
-      Cand best_c{d.strip, d.strip ? d.chunk : d.rows_per_cta, d.rows_upd};
-      for (const Cand &c : cands) {
-        if (e != cudaSuccess) continue;
-        if (c.strip == 0 && c.rows > mh[k].nj) continue;
-        if (c.strip > 0 && c.rows > 2 * mh[k].nj) continue;
-        d.strip = c.strip;
-        if (c.strip) d.chunk = c.rows;
-        else d.rows_per_cta = c.rows;
-        d.rows_upd = c.rows_upd;
-        // the fused right-hand side + update of the next step (a fast mesh's micro step 1, which
-        // takes the primitives handed over by micro step 0), with both of its outputs in the state
-        // buffer that the next step overwrites (each point's two stores come from its own
-        // thread); the bound history is only read
-        RhsLaunch a = fused_args(k, (k == fast() && plan.sr > 1) ? 1 : 0, k == fast() ? H / plan.sr : H);
-        a.out = a.qnext = d.q[1 - d.cur];
-        e = launch_rhs(a, p.dtype, viscous(), s);
-        float ms = 1e30f;
-        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the faster of two timings of 3
-          e = cudaEventRecord(e0, s);
-          for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_rhs(a, p.dtype, viscous(), s);
-          if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-          float t = 0.f;
-          if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-          if (e == cudaSuccess && t < ms) ms = t;
+      for (int use = 0; use < 2 && e == cudaSuccess; ++use) {  // 0: fused step, 1: rhs alone
+        float best = 1e30f;
+        Cand best_c{0, 16, 0};
+        for (const Cand &c : cands) {
+          if (e != cudaSuccess) continue;
+          if (c.strip == 0 && c.rows > mh[k].nj) continue;
+          if (c.strip > 0 && c.rows > 2 * mh[k].nj) continue;
+          d.strip = d.e_strip = c.strip;
+          if (c.strip) d.chunk = d.e_chunk = c.rows;
+          else d.rows_per_cta = d.e_rows = c.rows;
+          d.rows_upd = d.e_rows_upd = c.rows_upd;
+          RhsLaunch a;
+          if (use == 0) {
+            a = fused_args(k, (k == fast() && plan.sr > 1) ? 1 : 0, k == fast() ? H / plan.sr : H);
+            a.out = a.qnext = d.q[1 - d.cur];
+          } else {
+            a = rhs_args(k, d.q[d.cur], true);
+            a.mode = 0;
+            a.out = d.q[1 - d.cur];
+          }
+          e = launch_rhs(a, p.dtype, viscous(), s);
+          float ms = 1e30f;
+          for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_rhs(a, p.dtype, viscous(), s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && t < ms) ms = t;
+          }
+          if (e == cudaSuccess && ms < best) {
+            best = ms;
+            best_c = c;
+          }
         }
-        if (e == cudaSuccess && ms < best) {
-          best = ms;
-          best_c = c;
+        if (use == 0) {
+          step_shape[k] = best_c;
+        } else {
+          d.e_strip = best_c.strip;
+          if (best_c.strip) d.e_chunk = best_c.rows;
+          else d.e_rows = best_c.rows;
+          d.e_rows_upd = best_c.rows_upd;
         }
       }
-      d.strip = best_c.strip;
-      if (best_c.strip) d.chunk = best_c.rows;
-      else d.rows_per_cta = best_c.rows;
-      d.rows_upd = best_c.rows_upd;
+      d.strip = step_shape[k].strip;
+      if (step_shape[k].strip) d.chunk = step_shape[k].rows;
+      else d.rows_per_cta = step_shape[k].rows;
+      d.rows_upd = step_shape[k].rows_upd;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

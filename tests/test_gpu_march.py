@@ -134,10 +134,29 @@ def test_autotuner_reports_a_candidate(sbp):
     g.mrab_init()
     for k in range(2):
         info = g.mesh_info(k)
-        if info.single_pass:
-            assert info.strip_width == 58 and info.rows_per_cta in (8, 16, 32, 64, 128)
-        else:
-            assert info.strip_width == 32 and info.rows_per_cta in (8, 16, 32)
+        for sp, sw, rows in ((info.single_pass, info.strip_width, info.rows_per_cta),
+                             (info.eval_single_pass, info.eval_strip_width, info.eval_rows_per_cta)):
+            if sp:
+                assert sw == 58 and rows in (8, 16, 32, 64, 128)
+            else:
+                assert sw == 32 and rows in (8, 16, 32)
+    # the autotuner's choices give the same bits as any other shape: rhs_eval and a macro step
+    # against a fixed kernel pair
+    q = [g.to_device(k, wl["q0"][k]) for k in range(2)]
+    got = [g.rhs_eval(k, q[k], q[1 - k]).clone() for k in range(2)]
+    g2 = sbp.System(wl, dtype="f32")
+    g2.autotune(False)
+    for k in range(2):
+        g2.set_rhs_shape(k, 0, 16)
+        assert torch.equal(g2.rhs_eval(k, q[k], q[1 - k]), got[k])
+    g.mrab_step(2)
+    g2.bind(wl["q0"])
+    g2.mrab_init()
+    g2.mrab_step(2)
+    for k in range(2):
+        assert torch.equal(g.current_state(k), g2.current_state(k))
+    g.close()
+    g2.close()
 
 
 def test_bad_shapes_rejected(sbp):
