@@ -39,7 +39,7 @@ FLOP_PER_POINT_NS = 300.0      # algorithmic FLOPs of one 2D NS right-hand-side 
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
@@ -73,7 +73,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index, interval_ms=20):
+    def __init__(self, device_index, interval_ms=10):
         self.dev = device_index
         self.interval = interval_ms
         self.rows = []  # (host time, fields)
