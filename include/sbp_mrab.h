@@ -135,6 +135,24 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
 sbp_status sbp_system_destroy(sbp_system_t sys);
 sbp_status sbp_mesh_info_get(sbp_system_t sys, int mesh, sbp_mesh_info *info);
 
+/* The host part of sbp_system_create alone (no device calls, so it also runs on a machine
+ * without a GPU): the same argument checks, hole cut, SBP segment classes, SAT lists, donor
+ * search with Lagrange weights (Sec. 2.2) and the Adams-Bashforth / MRAB coefficient plan
+ * (Sec. 3.1-3.3), for inspection and tests. Errors as sbp_system_create. */
+typedef struct sbp_host_tables_s *sbp_host_tables_t;
+sbp_status sbp_host_tables_create(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                                  sbp_host_tables_t *out);
+sbp_status sbp_host_tables_destroy(sbp_host_tables_t tables);
+/* iblank (ni*nj bytes), receivers, donor_base, donor_w as in sbp_get_tables; n_receivers
+ * (host int) the receiver count. Any output pointer may be NULL. */
+sbp_status sbp_host_tables_get(sbp_host_tables_t tables, int mesh, signed char *iblank, int *receivers,
+                               int *donor_base, double *donor_w, int *n_receivers);
+/* The coefficient plan on unit steps: ab (m doubles) the weights of one Adams-Bashforth step
+ * over [0, 1] on the history nodes -(m-1)..0 (oldest first); ext (sr*m doubles, row j) the slow
+ * extrapolant's weights integrated over [0, j/sr] on the same nodes (row 0 zero); m, sr (host
+ * ints) the history length and step ratio. Any output pointer may be NULL. */
+sbp_status sbp_host_tables_plan(sbp_host_tables_t tables, double *ab, double *ext, int *m, int *sr);
+
 /* Setup tables copied to host memory, for inspection and tests.
  *  iblank: nj*ni bytes (1 active, 0 hole). metrics: 5*nj*ni doubles, planes
  *  (xi_x/J, xi_y/J, eta_x/J, eta_y/J, J). receivers: n_receivers point indices j*ni+i;

@@ -132,6 +132,10 @@ _SIGS.update({
     "sbp3_check": [_P, _P],
     "sbp3_set_rhs_kernel": [_P, _I, _I],
     "sbp_f32_to_f64": [_P, _P, ctypes.c_size_t, _P],
+    "sbp_host_tables_create": [ctypes.POINTER(MeshDesc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "sbp_host_tables_destroy": [_P],
+    "sbp_host_tables_get": [_P, _I, _P, _P, _P, _P, _P],
+    "sbp_host_tables_plan": [_P, _P, _P, _P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -170,6 +174,97 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _descriptors(wl, dtype, sigma_interface, sigma_physical, hole_cells):
+    """C descriptors (sbp_mesh_desc[2], sbp_params) of a workload dict, and the arrays they point
+    into (to be kept alive by the caller)."""
+    p = wl["params"]
+    descs = (MeshDesc * 2)()
+    keep = []
+    for k, m in enumerate(wl["meshes"]):
+        d = descs[k]
+        d.n[0], d.n[1] = m["n"]
+        d.periodic[0], d.periodic[1] = int(m["periodic"][0]), int(m["periodic"][1])
+        for f in range(4):
+            d.bc[f] = BC[m["bc"][f]]
+        d.cartesian = int(m["cartesian"])
+        d.lo[0], d.lo[1] = m["lo"]
+        d.h[0], d.h[1] = m["h"]
+        x = np.ascontiguousarray(m["x"], dtype=np.float64)
+        y = np.ascontiguousarray(m["y"], dtype=np.float64)
+        keep += [x, y]
+        d.x = x.ctypes.data
+        d.y = y.ctypes.data
+        sh = m["shift"]
+        d.shift[0], d.shift[1], d.shift[2], d.shift[3] = sh[0][0], sh[0][1], sh[1][0], sh[1][1]
+    pr = Params()
+    pr.physics = PHYSICS[p["physics"]]
+    pr.dtype = DTYPE[dtype]
+    pr.gamma = p["gamma"]
+    pr.mu = p["mu"]
+    pr.pr = p["pr"]
+    pr.twall = p["twall"]
+    pr.omega_corner = p["omega_corner"]
+    pr.sigma_interface = sigma_interface
+    pr.sigma_physical = sigma_physical
+    pr.cfl = p["cfl"]
+    for v in range(4):
+        pr.qinf[v] = float(p["qinf"][v])
+    pr.order = p["order"]
+    pr.hist_len = p["hist_len"]
+    pr.step_ratio = p["step_ratio"]
+    pr.fast_mesh = p["fast_mesh"]
+    pr.hole_cells = hole_cells
+    pr.scheme = SCHEMES[p.get("scheme", "fastest_first")]
+    pr.sponge_cells = int(p.get("sponge_cells", 0))
+    pr.sponge_strength = float(p.get("sponge_strength", 1.0))
+    return descs, pr, keep
+
+
+class HostTables:
+    """The host part of system creation alone (sbp_host_tables_*): setup tables and the MRAB
+    coefficient plan, without touching a GPU."""
+
+    def __init__(self, wl, hole_cells=4):
+        descs, pr, self._keep = _descriptors(wl, "f64", 0.5, 1.0, hole_cells)
+        h = ctypes.c_void_p()
+        _check(_lib.sbp_host_tables_create(descs, 2, ctypes.byref(pr), ctypes.byref(h)), "sbp_host_tables_create")
+        self.h = h
+        self.meshes = wl["meshes"]
+
+    def tables(self, k):
+        ni, nj = self.meshes[k]["n"]
+        nr = ctypes.c_int()
+        _check(_lib.sbp_host_tables_get(self.h, k, None, None, None, None, ctypes.byref(nr)), "sbp_host_tables_get")
+        nr = nr.value
+        ib = np.zeros(ni * nj, np.int8)
+        rec = np.zeros(max(nr, 1), np.int32)
+        base = np.zeros(max(2 * nr, 1), np.int32)
+        w = np.zeros(max(8 * nr, 1))
+        _check(_lib.sbp_host_tables_get(self.h, k, ib.ctypes.data, rec.ctypes.data, base.ctypes.data, w.ctypes.data,
+                                        None), "sbp_host_tables_get")
+        return {"iblank": ib.reshape(nj, ni), "receivers": rec[:nr], "base": base[:2 * nr].reshape(nr, 2),
+                "w": w[:8 * nr].reshape(nr, 8)}
+
+    def plan(self):
+        m, sr = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.sbp_host_tables_plan(self.h, None, None, ctypes.byref(m), ctypes.byref(sr)), "sbp_host_tables_plan")
+        ab = np.zeros(m.value)
+        ext = np.zeros((sr.value, m.value))
+        _check(_lib.sbp_host_tables_plan(self.h, ab.ctypes.data, ext.ctypes.data, None, None), "sbp_host_tables_plan")
+        return ab, ext
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp_host_tables_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class System:
     """A two-mesh overset system on the current CUDA device.
 
@@ -184,45 +279,7 @@ class System:
         self.tdtype = torch.float64 if dtype == "f64" else torch.float32
         self.meshes = wl["meshes"]
         p = wl["params"]
-        descs = (MeshDesc * 2)()
-        self._keep = []
-        for k, m in enumerate(self.meshes):
-            d = descs[k]
-            d.n[0], d.n[1] = m["n"]
-            d.periodic[0], d.periodic[1] = int(m["periodic"][0]), int(m["periodic"][1])
-            for f in range(4):
-                d.bc[f] = BC[m["bc"][f]]
-            d.cartesian = int(m["cartesian"])
-            d.lo[0], d.lo[1] = m["lo"]
-            d.h[0], d.h[1] = m["h"]
-            x = np.ascontiguousarray(m["x"], dtype=np.float64)
-            y = np.ascontiguousarray(m["y"], dtype=np.float64)
-            self._keep += [x, y]
-            d.x = x.ctypes.data
-            d.y = y.ctypes.data
-            sh = m["shift"]
-            d.shift[0], d.shift[1], d.shift[2], d.shift[3] = sh[0][0], sh[0][1], sh[1][0], sh[1][1]
-        pr = Params()
-        pr.physics = PHYSICS[p["physics"]]
-        pr.dtype = DTYPE[dtype]
-        pr.gamma = p["gamma"]
-        pr.mu = p["mu"]
-        pr.pr = p["pr"]
-        pr.twall = p["twall"]
-        pr.omega_corner = p["omega_corner"]
-        pr.sigma_interface = sigma_interface
-        pr.sigma_physical = sigma_physical
-        pr.cfl = p["cfl"]
-        for v in range(4):
-            pr.qinf[v] = float(p["qinf"][v])
-        pr.order = p["order"]
-        pr.hist_len = p["hist_len"]
-        pr.step_ratio = p["step_ratio"]
-        pr.fast_mesh = p["fast_mesh"]
-        pr.hole_cells = hole_cells
-        pr.scheme = SCHEMES[p.get("scheme", "fastest_first")]
-        pr.sponge_cells = int(p.get("sponge_cells", 0))
-        pr.sponge_strength = float(p.get("sponge_strength", 1.0))
+        descs, pr, self._keep = _descriptors(wl, dtype, sigma_interface, sigma_physical, hole_cells)
         self.params = p
         h = ctypes.c_void_p()
         torch.cuda.init()
@@ -234,6 +291,7 @@ class System:
             _check(_lib.sbp_mesh_info_get(self.h, k, ctypes.byref(inf)), "sbp_mesh_info_get")
             self.info.append(inf)
         self.bound = None
+
 
     def close(self):
         if getattr(self, "h", None):

@@ -25,10 +25,11 @@ const char *sbp_status_string(sbp_status s) {
 
 const char *sbp_last_error_message(void) { return g_msg.c_str(); }
 
-sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params,
-                             sbp_system_t *out) {
-  if (!meshes || !params || !out) return fail(SBP_ERR_ARG, "null argument");
-  *out = nullptr;
+// Host part of system creation (no device calls): argument checks, per-mesh setup, hole cut,
+// SBP segment classes, SAT lists, donor search and Lagrange weights, the coefficient plan.
+static sbp_status host_setup(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params, sbp_params &pout,
+                             MeshHost mh[2], CoeffPlan &plan) {
+  if (!meshes || !params) return fail(SBP_ERR_ARG, "null argument");
   if (n_meshes != 2) return fail(SBP_ERR_ARG, "exactly two meshes (background, fine) are supported");
   const sbp_params &p = *params;
   if (p.physics != SBP_EULER && p.physics != SBP_NS) return fail(SBP_ERR_ARG, "physics");
@@ -41,25 +42,87 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
     return fail(SBP_ERR_ARG, "scheme");
   if (p.sponge_cells < 0 || p.sponge_cells > 16 || !(p.sponge_strength >= 0.0))
     return fail(SBP_ERR_ARG, "sponge_cells must be in 0..16 and sponge_strength >= 0");
-  auto *S = new sbp_system_s();
-  std::unique_ptr<sbp_system_s> guard(S);
-  S->p = p;
-  if (S->p.hole_cells <= 0) S->p.hole_cells = 4;
-  S->esz = p.dtype == SBP_F64 ? 8 : 4;
+  pout = p;
+  if (pout.hole_cells <= 0) pout.hole_cells = 4;
   std::string err;
   sbp_status st;
   for (int k = 0; k < 2; ++k)
-    if ((st = setup_mesh_basic(meshes[k], S->mh[k], err)) != SBP_OK) return fail(st, err);
-  if (!S->mh[0].cartesian) return fail(SBP_ERR_ARG, "the background (mesh 0) must be Cartesian");
-  double margin = S->p.hole_cells * std::max(S->mh[0].h[0], S->mh[0].h[1]);
-  if ((st = setup_holes(S->mh[0], S->mh[1], margin, err)) != SBP_OK) return fail(st, err);
+    if ((st = setup_mesh_basic(meshes[k], mh[k], err)) != SBP_OK) return fail(st, err);
+  if (!mh[0].cartesian) return fail(SBP_ERR_ARG, "the background (mesh 0) must be Cartesian");
+  double margin = pout.hole_cells * std::max(mh[0].h[0], mh[0].h[1]);
+  if ((st = setup_holes(mh[0], mh[1], margin, err)) != SBP_OK) return fail(st, err);
   for (int k = 0; k < 2; ++k) {
-    if ((st = setup_classes(S->mh[k], err)) != SBP_OK) return fail(st, err);
-    if ((st = setup_sat(S->mh[k], p.omega_corner, err)) != SBP_OK) return fail(st, err);
+    if ((st = setup_classes(mh[k], err)) != SBP_OK) return fail(st, err);
+    if ((st = setup_sat(mh[k], p.omega_corner, err)) != SBP_OK) return fail(st, err);
   }
   for (int k = 0; k < 2; ++k)
-    if ((st = setup_donors(S->mh[k], S->mh[1 - k], err)) != SBP_OK) return fail(st, err);
-  if ((st = build_plan(p.order, p.hist_len, p.step_ratio, S->plan, err)) != SBP_OK) return fail(st, err);
+    if ((st = setup_donors(mh[k], mh[1 - k], err)) != SBP_OK) return fail(st, err);
+  if ((st = build_plan(p.order, p.hist_len, p.step_ratio, plan, err)) != SBP_OK) return fail(st, err);
+  return SBP_OK;
+}
+
+}  // extern "C"
+
+struct sbp_host_tables_s {
+  sbp_params p;
+  MeshHost mh[2];
+  CoeffPlan plan;
+};
+
+extern "C" {
+
+sbp_status sbp_host_tables_create(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                                  sbp_host_tables_t *out) {
+  if (!out) return fail(SBP_ERR_ARG, "null argument");
+  *out = nullptr;
+  auto *T = new sbp_host_tables_s();
+  std::unique_ptr<sbp_host_tables_s> guard(T);
+  sbp_status st = host_setup(meshes, n_meshes, params, T->p, T->mh, T->plan);
+  if (st != SBP_OK) return st;
+  *out = guard.release();
+  return SBP_OK;
+}
+
+sbp_status sbp_host_tables_destroy(sbp_host_tables_t T) {
+  delete T;
+  return SBP_OK;
+}
+
+sbp_status sbp_host_tables_get(sbp_host_tables_t T, int k, signed char *iblank, int *receivers, int *donor_base,
+                               double *donor_w, int *n_receivers) {
+  if (!T || k < 0 || k > 1) return fail(SBP_ERR_ARG, "bad argument");
+  const MeshHost &m = T->mh[k];
+  const size_t n = (size_t)m.ni * m.nj, nr = m.recv_pt.size();
+  if (iblank)
+    for (size_t q = 0; q < n; ++q) iblank[q] = m.active[q];
+  if (receivers) std::memcpy(receivers, m.recv_pt.data(), nr * sizeof(int));
+  if (donor_base) std::memcpy(donor_base, m.donor_base.data(), 2 * nr * sizeof(int));
+  if (donor_w) std::memcpy(donor_w, m.donor_w.data(), 8 * nr * sizeof(double));
+  if (n_receivers) *n_receivers = (int)nr;
+  return SBP_OK;
+}
+
+sbp_status sbp_host_tables_plan(sbp_host_tables_t T, double *ab, double *ext, int *m, int *sr) {
+  if (!T) return fail(SBP_ERR_ARG, "null argument");
+  const CoeffPlan &c = T->plan;
+  if (m) *m = c.m;
+  if (sr) *sr = c.sr;
+  if (ab) std::memcpy(ab, c.ab.data(), c.m * sizeof(double));
+  if (ext)
+    for (int j = 0; j < c.sr; ++j) std::memcpy(ext + (size_t)j * c.m, c.ext[j].data(), c.m * sizeof(double));
+  return SBP_OK;
+}
+
+sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                             sbp_system_t *out) {
+  if (!meshes || !params || !out) return fail(SBP_ERR_ARG, "null argument");
+  *out = nullptr;
+  auto *S = new sbp_system_s();
+  std::unique_ptr<sbp_system_s> guard(S);
+  sbp_status st = host_setup(meshes, n_meshes, params, S->p, S->mh, S->plan);
+  if (st != SBP_OK) return st;
+  const sbp_params &p = S->p;
+  S->esz = p.dtype == SBP_F64 ? 8 : 4;
 
   // device tables
   CUDA_TRY(cudaMalloc((void **)&S->d_err, sizeof(int)));
