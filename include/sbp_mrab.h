@@ -435,6 +435,15 @@ sbp_status sbp3_set_freestream(sbp3_system_t sys, const double *qinf);
  * (4 Lagrange weights along i, j, k) per receiver. */
 sbp_status sbp3_get_tables(sbp3_system_t sys, int mesh, signed char *iblank, long long *receivers, int *donor_base,
                            double *donor_w);
+/* The host part of sbp3_system_create alone (no device calls): argument checks, hole cut,
+ * segment classes, SAT lists, donor search and weights; tables as sbp3_get_tables, n_receivers
+ * (host int) the receiver count. Any output pointer may be NULL. */
+typedef struct sbp3_host_tables_s *sbp3_host_tables_t;
+sbp_status sbp3_host_tables_create(const sbp3_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                                   sbp3_host_tables_t *out);
+sbp_status sbp3_host_tables_destroy(sbp3_host_tables_t tables);
+sbp_status sbp3_host_tables_get(sbp3_host_tables_t tables, int mesh, signed char *iblank, long long *receivers,
+                                int *donor_base, double *donor_w, int *n_receivers);
 /* Interpolation to recv_mesh's receivers from the other mesh's state (device): qhat 5 x
  * n_receivers, fvhat 12 x n_receivers (Cartesian viscous fluxes F^V_x, F^V_y, F^V_z, each
  * momentum x, y, z and energy; NS only, may be NULL). */

@@ -136,6 +136,9 @@ _SIGS.update({
     "sbp_host_tables_destroy": [_P],
     "sbp_host_tables_get": [_P, _I, _P, _P, _P, _P, _P],
     "sbp_host_tables_plan": [_P, _P, _P, _P, _P],
+    "sbp3_host_tables_create": [ctypes.POINTER(Mesh3Desc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "sbp3_host_tables_destroy": [_P],
+    "sbp3_host_tables_get": [_P, _I, _P, _P, _P, _P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -511,6 +514,79 @@ class System:
         return out
 
 
+def _descriptors3(wl, dtype, sigma_interface, sigma_physical, hole_cells):
+    """C descriptors (sbp3_mesh_desc[2], sbp_params) of a 3D workload dict (qinf's first four
+    entries: rho, rho u, rho v, rho E; the full 5-component state goes through
+    sbp3_set_freestream)."""
+    p = wl["params"]
+    descs = (Mesh3Desc * 2)()
+    for k, m in enumerate(wl["meshes"]):
+        d = descs[k]
+        for a in range(3):
+            d.n[a] = m["n"][a]
+            d.periodic[a] = int(m["periodic"][a])
+            d.lo[a] = m["lo"][a]
+            d.h[a] = m["h"][a]
+        for f in range(6):
+            d.bc[f] = BC[m["bc"][f]]
+    pr = Params()
+    pr.physics = PHYSICS[p["physics"]]
+    pr.dtype = DTYPE[dtype]
+    pr.gamma = p["gamma"]
+    pr.mu = p["mu"]
+    pr.pr = p["pr"]
+    pr.twall = p["twall"]
+    pr.omega_corner = p["omega_corner"]
+    pr.sigma_interface = sigma_interface
+    pr.sigma_physical = sigma_physical
+    pr.cfl = p["cfl"]
+    qi = np.asarray(p["qinf"], dtype=np.float64)
+    for v, c in enumerate((0, 1, 2, 4)):
+        pr.qinf[v] = float(qi[c])
+    pr.order = p["order"]
+    pr.hist_len = p["hist_len"]
+    pr.step_ratio = p["step_ratio"]
+    pr.fast_mesh = p["fast_mesh"]
+    pr.hole_cells = hole_cells
+    return descs, pr
+
+
+class HostTables3D:
+    """The host part of 3D system creation alone (sbp3_host_tables_*), without a GPU."""
+
+    def __init__(self, wl, hole_cells=4):
+        descs, pr = _descriptors3(wl, "f64", 0.5, 1.0, hole_cells)
+        h = ctypes.c_void_p()
+        _check(_lib.sbp3_host_tables_create(descs, 2, ctypes.byref(pr), ctypes.byref(h)), "sbp3_host_tables_create")
+        self.h = h
+        self.meshes = wl["meshes"]
+
+    def tables(self, k):
+        ni, nj, nk = self.meshes[k]["n"]
+        nr = ctypes.c_int()
+        _check(_lib.sbp3_host_tables_get(self.h, k, None, None, None, None, ctypes.byref(nr)), "sbp3_host_tables_get")
+        nr = nr.value
+        ib = np.zeros(ni * nj * nk, np.int8)
+        rec = np.zeros(max(nr, 1), np.int64)
+        base = np.zeros(max(3 * nr, 1), np.int32)
+        w = np.zeros(max(12 * nr, 1))
+        _check(_lib.sbp3_host_tables_get(self.h, k, ib.ctypes.data, rec.ctypes.data, base.ctypes.data,
+                                         w.ctypes.data, None), "sbp3_host_tables_get")
+        return {"iblank": ib.reshape(nk, nj, ni), "receivers": rec[:nr], "base": base[:3 * nr].reshape(nr, 3),
+                "w": w[:12 * nr].reshape(nr, 12)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp3_host_tables_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class System3D:
     """A two-mesh 3D Cartesian overset system (C ABI sbp3_*). ``wl`` is a 3D workload dict
     (``workloads.taylor_green_box`` layout). States are numpy arrays (5, nk, nj, ni) or device
@@ -523,35 +599,8 @@ class System3D:
         self.tdtype = torch.float64 if dtype == "f64" else torch.float32
         self.meshes = wl["meshes"]
         p = wl["params"]
-        descs = (Mesh3Desc * 2)()
-        for k, m in enumerate(self.meshes):
-            d = descs[k]
-            for a in range(3):
-                d.n[a] = m["n"][a]
-                d.periodic[a] = int(m["periodic"][a])
-                d.lo[a] = m["lo"][a]
-                d.h[a] = m["h"][a]
-            for f in range(6):
-                d.bc[f] = BC[m["bc"][f]]
-        pr = Params()
-        pr.physics = PHYSICS[p["physics"]]
-        pr.dtype = DTYPE[dtype]
-        pr.gamma = p["gamma"]
-        pr.mu = p["mu"]
-        pr.pr = p["pr"]
-        pr.twall = p["twall"]
-        pr.omega_corner = p["omega_corner"]
-        pr.sigma_interface = sigma_interface
-        pr.sigma_physical = sigma_physical
-        pr.cfl = p["cfl"]
+        descs, pr = _descriptors3(wl, dtype, sigma_interface, sigma_physical, hole_cells)
         qi = np.asarray(p["qinf"], dtype=np.float64)
-        for v, c in enumerate((0, 1, 2, 4)):
-            pr.qinf[v] = float(qi[c])
-        pr.order = p["order"]
-        pr.hist_len = p["hist_len"]
-        pr.step_ratio = p["step_ratio"]
-        pr.fast_mesh = p["fast_mesh"]
-        pr.hole_cells = hole_cells
         self.params = p
         h = ctypes.c_void_p()
         torch.cuda.init()

@@ -257,10 +257,11 @@ struct sbp3_system_s {
 
 extern "C" {
 
-sbp_status sbp3_system_create(const sbp3_mesh_desc *meshes, int n_meshes, const sbp_params *params,
-                              sbp3_system_t *out) {
-  if (!meshes || !params || !out) return fail(SBP_ERR_ARG, "null argument");
-  *out = nullptr;
+// Host part of 3D system creation (no device calls): argument checks, per-mesh setup, hole
+// cut, SBP segment classes, SAT lists, donor search and Lagrange weights, the coefficient plan.
+static sbp_status host3_setup(const sbp3_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                              sbp_params &pout, Mesh3Host mh[2], CoeffPlan &plan) {
+  if (!meshes || !params) return fail(SBP_ERR_ARG, "null argument");
   if (n_meshes != 2) return fail(SBP_ERR_ARG, "exactly two meshes (background, fine box) are supported");
   const sbp_params &p = *params;
   if (p.physics != SBP_EULER && p.physics != SBP_NS) return fail(SBP_ERR_ARG, "physics");
@@ -271,29 +272,81 @@ sbp_status sbp3_system_create(const sbp3_mesh_desc *meshes, int n_meshes, const 
     return fail(SBP_ERR_ARG, "step_ratio must be in 1.." + std::to_string(kMaxSets));
   if (p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_ARG, "3D systems are fastest-first");
   if (p.sponge_cells != 0) return fail(SBP_ERR_ARG, "3D systems have no sponge layer");
+  pout = p;
+  if (pout.hole_cells <= 0) pout.hole_cells = 4;
+  std::string err;
+  sbp_status st;
+  for (int k = 0; k < 2; ++k)
+    if ((st = setup3_mesh(meshes[k], mh[k], err)) != SBP_OK) return fail(st, err);
+  double margin = pout.hole_cells * std::max({mh[0].h[0], mh[0].h[1], mh[0].h[2]});
+  if ((st = setup3_holes(mh[0], mh[1], margin, err)) != SBP_OK) return fail(st, err);
+  for (int k = 0; k < 2; ++k) {
+    if ((st = setup3_classes(mh[k], err)) != SBP_OK) return fail(st, err);
+    if ((st = setup3_sat(mh[k], p.omega_corner, err)) != SBP_OK) return fail(st, err);
+  }
+  for (int k = 0; k < 2; ++k)
+    if ((st = setup3_donors(mh[k], mh[1 - k], err)) != SBP_OK) return fail(st, err);
+  if ((st = build_plan(p.order, p.hist_len, p.step_ratio, plan, err)) != SBP_OK) return fail(st, err);
+  return SBP_OK;
+}
+
+}  // extern "C"
+
+struct sbp3_host_tables_s {
+  sbp_params p;
+  Mesh3Host mh[2];
+  CoeffPlan plan;
+};
+
+extern "C" {
+
+sbp_status sbp3_host_tables_create(const sbp3_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                                   sbp3_host_tables_t *out) {
+  if (!out) return fail(SBP_ERR_ARG, "null argument");
+  *out = nullptr;
+  auto *T = new sbp3_host_tables_s();
+  std::unique_ptr<sbp3_host_tables_s> guard(T);
+  sbp_status st = host3_setup(meshes, n_meshes, params, T->p, T->mh, T->plan);
+  if (st != SBP_OK) return st;
+  *out = guard.release();
+  return SBP_OK;
+}
+
+sbp_status sbp3_host_tables_destroy(sbp3_host_tables_t T) {
+  delete T;
+  return SBP_OK;
+}
+
+sbp_status sbp3_host_tables_get(sbp3_host_tables_t T, int k, signed char *iblank, long long *receivers,
+                                int *donor_base, double *donor_w, int *n_receivers) {
+  if (!T || k < 0 || k > 1) return fail(SBP_ERR_ARG, "bad argument");
+  const Mesh3Host &m = T->mh[k];
+  if (iblank)
+    for (size_t q = 0; q < m.points(); ++q) iblank[q] = m.active[q];
+  const size_t nr = m.recv_pt.size();
+  if (receivers)
+    for (size_t r = 0; r < nr; ++r) receivers[r] = (long long)m.recv_pt[r];
+  if (donor_base) std::memcpy(donor_base, m.donor_base.data(), 3 * nr * sizeof(int));
+  if (donor_w) std::memcpy(donor_w, m.donor_w.data(), 12 * nr * sizeof(double));
+  if (n_receivers) *n_receivers = (int)nr;
+  return SBP_OK;
+}
+
+sbp_status sbp3_system_create(const sbp3_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                              sbp3_system_t *out) {
+  if (!meshes || !params || !out) return fail(SBP_ERR_ARG, "null argument");
+  *out = nullptr;
   auto *S = new sbp3_system_s();
   std::unique_ptr<sbp3_system_s> guard(S);
-  S->p = p;
-  if (S->p.hole_cells <= 0) S->p.hole_cells = 4;
+  sbp_status st = host3_setup(meshes, n_meshes, params, S->p, S->mh, S->plan);
+  if (st != SBP_OK) return st;
+  const sbp_params &p = S->p;
   S->esz = p.dtype == SBP_F64 ? 8 : 4;
   S->qinf[0] = p.qinf[0];
   S->qinf[1] = p.qinf[1];
   S->qinf[2] = p.qinf[2];
   S->qinf[3] = 0.0;
   S->qinf[4] = p.qinf[3];
-  std::string err;
-  sbp_status st;
-  for (int k = 0; k < 2; ++k)
-    if ((st = setup3_mesh(meshes[k], S->mh[k], err)) != SBP_OK) return fail(st, err);
-  double margin = S->p.hole_cells * std::max({S->mh[0].h[0], S->mh[0].h[1], S->mh[0].h[2]});
-  if ((st = setup3_holes(S->mh[0], S->mh[1], margin, err)) != SBP_OK) return fail(st, err);
-  for (int k = 0; k < 2; ++k) {
-    if ((st = setup3_classes(S->mh[k], err)) != SBP_OK) return fail(st, err);
-    if ((st = setup3_sat(S->mh[k], p.omega_corner, err)) != SBP_OK) return fail(st, err);
-  }
-  for (int k = 0; k < 2; ++k)
-    if ((st = setup3_donors(S->mh[k], S->mh[1 - k], err)) != SBP_OK) return fail(st, err);
-  if ((st = build_plan(p.order, p.hist_len, p.step_ratio, S->plan, err)) != SBP_OK) return fail(st, err);
 
   CUDA_TRY(cudaMalloc((void **)&S->d_err, sizeof(int)));
   CUDA_TRY(cudaMemset(S->d_err, 0, sizeof(int)));

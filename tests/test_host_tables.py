@@ -79,3 +79,29 @@ def test_host_tables_reject_bad_input(sbp):
     bg = dict(wl["meshes"][0], n=(7, 40))
     with pytest.raises(sbp.SbpError):
         sbp.HostTables(dict(wl, meshes=[bg, wl["meshes"][1]]))
+
+
+CASES_3D = {
+    "tg_ns": (lambda: W.taylor_green_small(seed=41), 4),
+    "tg_sr3_ab34": (lambda: W.taylor_green_small(seed=43, step_ratio=3, hist_len=4, n_bg=20, n_fine=19), 4),
+    "extruded_z_vortex": (lambda: W.extrude_to_3d(W.vortex_box_in_box(seed=44, n_bg=40, n_fine=25), 8, 2.0, axis=2),
+                          2.5),
+    "extruded_y_mms": (lambda: W.extrude_to_3d(W.mms_box_in_box(40, "viscous"), 8, 0.4, axis=1), 3.7),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES_3D))
+def test_host_tables_3d_match_oracle(sbp, case):
+    from oracle import OracleSystem3D
+    mk, hc = CASES_3D[case]
+    wl = mk()
+    ref = OracleSystem3D(wl, hole_cells=hc)
+    h = sbp.HostTables3D(wl, hole_cells=hc)
+    for k in range(2):
+        t = h.tables(k)
+        assert np.array_equal(t["iblank"], ref.iblank[k])
+        assert np.array_equal(t["receivers"], ref.recv_pts[k])
+        if ref.recv_pts[k].size:
+            assert np.array_equal(t["base"], ref.base[k])
+            assert np.abs(t["w"] - ref.w[k]).max() < 1e-13
+    h.close()
