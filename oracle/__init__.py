@@ -85,10 +85,12 @@ def lib():
     return L
 
 
-from .system import (OracleSystem, ab_coefficients, mrab_macro_step, mrab_macro_step_slowest_first,  # noqa: E402
+from .system import (OracleSystem, ab_coefficients, mrab_macro_step, mrab_macro_step_multirate,  # noqa: E402
+                     mrab_macro_step_slowest_first,
                      mrab_macro_step_var, rk3_heun_step, rk4_step, srab_step, l2_norm)
 from .system3d import OracleSystem3D  # noqa: E402
 
 __all__ = ["build", "lib", "OracleSystem", "OracleSystem3D", "ab_coefficients", "mrab_macro_step",
+           "mrab_macro_step_multirate",
            "mrab_macro_step_slowest_first", "mrab_macro_step_var", "rk3_heun_step", "rk4_step", "srab_step",
            "l2_norm"]

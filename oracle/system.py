@@ -110,6 +110,58 @@ def mrab_macro_step(f, s, hist_f, hist_s, H, sr, order, rhs_fast, rhs_slow):
     return f, s, hist_f, hist_s
 
 
+def mrab_macro_step_multirate(ys, hists, H, ratios, order, rhs):
+    """One macro step [t, t+H] of fastest-first MRAB without re-extrapolation for any number
+    of rates. Sec. 3.3 notes that the two-rate scheme extends to any number of rates without
+    spelling the extension out; this is the reading: the two-rate recursion nested level by
+    level.
+
+    Components 0..R-1 run from slowest to fastest; component r steps with
+    h_r = H / (ratios[0] * ... * ratios[r-1]) (ratios: R-1 integers). hists[r] holds m
+    right-hand-side values of component r, oldest first, ending at t (nodes t-(m-1)h_r .. t).
+    To advance component r over [tau, tau + h_r], component r+1 first takes its ratios[r] steps
+    over the same interval; then y_r advances by the integral of its extrapolant (the polynomial
+    through hist_r), and its right-hand side at tau + h_r is evaluated with the faster components'
+    states (already at tau + h_r) and the slower ones extrapolated: the slower component's state
+    at the start of its current step plus the integral of its polynomial up to tau + h_r.
+    rhs(r, vals) evaluates component r's right-hand side from the values of all components.
+    Times are counted in steps of the fastest component, so that the extrapolation intervals are
+    exact ratios. For two rates this is mrab_macro_step operation for operation; with every
+    ratio 1 it is single-rate Adams-Bashforth (srab_step) on the whole system."""
+    R = len(ys)
+    if len(ratios) != R - 1 or len(hists) != R:
+        raise ValueError("one history per component and R - 1 step ratios")
+    m = len(hists[0])
+    nodes = np.arange(-(m - 1), 1, dtype=np.float64)
+    ticks = [1] * R                      # steps of the fastest component per step of component r
+    for r in range(R - 2, -1, -1):
+        ticks[r] = ticks[r + 1] * int(ratios[r])
+    h = [H]
+    for r in range(1, R):
+        h.append(h[-1] / ratios[r - 1])
+    alpha = [ab_coefficients(nodes, 0.0, 1.0, order) * h[r] for r in range(R)]
+    ys = list(ys)
+    hists = [list(x) for x in hists]
+    start = [0] * R                      # tick at which each component's current step began
+
+    def extrapolated(c, tick):
+        frac = (tick - start[c]) / ticks[c]
+        return _combine(ys[c], ab_coefficients(nodes, 0.0, frac, order) * h[c], hists[c])
+
+    def advance(r, tick0):
+        if r + 1 < R:
+            for j in range(int(ratios[r])):
+                advance(r + 1, tick0 + j * ticks[r + 1])
+        ys[r] = _combine(ys[r], alpha[r], hists[r])
+        tick1 = tick0 + ticks[r]
+        vals = [extrapolated(c, tick1) if c < r else ys[c] for c in range(R)]
+        hists[r] = hists[r][1:] + [rhs(r, vals)]
+        start[r] = tick1
+
+    advance(0, 0)
+    return ys, hists
+
+
 def mrab_macro_step_var(f, s, hist_f, times_f, hist_s, times_s, t, H, sr, order, rhs_fast, rhs_slow):
     """Fastest-first MRAB macro step [t, t+H] for histories at arbitrary past times (the macro
     step may change from one macro step to the next, Sec. 3.3 Step 1): every weight solves the
