@@ -1,0 +1,113 @@
+"""Plain FP64 CPU oracle: the flux divergence of the 3D compressible Navier-Stokes equations on
+one curvilinear structured mesh.
+
+TEST INFRASTRUCTURE ONLY. The GPU library never imports it; only tests may use it. No GPU path
+for 3D curvilinear meshes exists yet: this is the definition such a path will be checked against,
+pinned by tests/test_oracle_curv3d.py.
+
+What it computes (App. C.1's equations in curvilinear coordinates, Sec. 2.1's SBP operator):
+  * coordinate derivatives X_a = D_a X by the SBP 4-2 first derivative along each index
+    direction a (xi = i, eta = j, zeta = k), closures at both ends of every line (Sec. 2.1);
+  * metric terms xi_m,x_j / J in the symmetric conservative form of Thomas and Lombard (the
+    reading; the paper defers the metrics to other work): for (m, a, b) and (j, c, e) cyclic,
+        M[m][j] = D_b((X_c)_a X_e) - D_a((X_c)_b X_e),
+    which satisfies the discrete metric identity sum_m D_m M[m][j] = 0 because D_a and D_b act
+    on different index directions and commute;
+  * J^-1 = det(X_a) from the same coordinate derivatives;
+  * gradients d f / d x_j = J sum_m M[m][j] D_m f of (u, v, w, T) (the viscous term's first
+    application of D), stresses with Stokes' hypothesis, Fourier heat flux (App. C.1);
+  * dq/dt = -J sum_m D_m (sum_j M[m][j] (F_j - F^V_j)).
+No SAT penalties: this is the interior operator; boundary and interface terms are those of the
+Cartesian oracle with the metric vector in place of 1/h.
+
+Arrays are (nk, nj, ni) per variable, i fastest; q = (rho, rho u, rho v, rho w, rho E).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import lib
+
+
+def d_matrix(n):
+    """The SBP 4-2 first derivative on a line of n points with closures at both ends, as an
+    n x n matrix: columns are the oracle's pinned 1D operator (orc_apply_d1) applied to unit
+    vectors."""
+    if n < 8:
+        raise ValueError("a line needs at least 8 points")
+    cls = np.zeros(n, np.int8)
+    for r in range(4):
+        cls[r] = 1 + r          # closure row r at the low end
+        cls[n - 1 - r] = 5 + r  # closure row r counted from the high end
+    L = lib()
+    D = np.zeros((n, n))
+    out = np.zeros(n)
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = 1.0
+        L.orc_apply_d1(n, ctypes.c_void_p(cls.ctypes.data), ctypes.c_void_p(e.ctypes.data),
+                       ctypes.c_void_p(out.ctypes.data))
+        D[:, c] = out
+    return D
+
+
+class Curvilinear3D:
+    """One structured mesh with node coordinates x, y, z (each (nk, nj, ni)), non-periodic in
+    every direction."""
+
+    def __init__(self, x, y, z):
+        X = [np.asarray(v, dtype=np.float64) for v in (x, y, z)]
+        nk, nj, ni = X[0].shape
+        self.shape = (nk, nj, ni)
+        self.D = [d_matrix(ni), d_matrix(nj), d_matrix(nk)]
+        # derivative along index direction a (0: i, 1: j, 2: k) acts on array axis 2 - a
+        dX = [[self.deriv(X[c], a) for a in range(3)] for c in range(3)]   # dX[c][a] = D_a X_c
+        self.Jinv = (dX[0][0] * (dX[1][1] * dX[2][2] - dX[1][2] * dX[2][1])
+                     - dX[0][1] * (dX[1][0] * dX[2][2] - dX[1][2] * dX[2][0])
+                     + dX[0][2] * (dX[1][0] * dX[2][1] - dX[1][1] * dX[2][0]))
+        self.J = 1.0 / self.Jinv
+        cyc = [(0, 1, 2), (1, 2, 0), (2, 0, 1)]
+        self.M = [[None] * 3 for _ in range(3)]
+        for m, a, b in cyc:
+            for j, c, e in cyc:
+                self.M[m][j] = (self.deriv(dX[c][a] * X[e], b) - self.deriv(dX[c][b] * X[e], a))
+
+    def deriv(self, f, a):
+        """D_a f: the SBP derivative along index direction a (unit index spacing)."""
+        ax = 2 - a
+        g = np.tensordot(self.D[a], np.moveaxis(f, ax, 0), axes=(1, 0))
+        return np.moveaxis(g, 0, ax)
+
+    def gradient(self, f):
+        """(d f/dx, d f/dy, d f/dz) by the chain rule with the metric terms."""
+        Df = [self.deriv(f, m) for m in range(3)]
+        return [self.J * (self.M[0][j] * Df[0] + self.M[1][j] * Df[1] + self.M[2][j] * Df[2]) for j in range(3)]
+
+    def rhs(self, q, gamma, mu=0.0, pr=0.72):
+        """dq/dt = -J sum_m D_m F^_m (5 arrays), F^_m = sum_j M[m][j] (F_j - F^V_j)."""
+        rho = q[0]
+        vel = [q[1] / rho, q[2] / rho, q[3] / rho]
+        E = q[4]
+        p = (gamma - 1.0) * (E - 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2))
+        F = [[rho * vel[d]] + [rho * vel[d] * vel[c] + (p if c == d else 0.0) for c in range(3)]
+             + [(E + p) * vel[d]] for d in range(3)]
+        if mu > 0.0:
+            T = gamma * p / rho
+            g = [self.gradient(f) for f in vel + [T]]   # g[f][d]
+            div = g[0][0] + g[1][1] + g[2][2]
+            lam, kap = -2.0 / 3.0 * mu, mu / (pr * (gamma - 1.0))
+            for d in range(3):
+                tau = [mu * (g[d][c] + g[c][d]) + (lam * div if c == d else 0.0) for c in range(3)]
+                for c in range(3):
+                    F[d][1 + c] = F[d][1 + c] - tau[c]
+                F[d][4] = F[d][4] - (vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d])
+        out = []
+        for v in range(5):
+            s = 0.0
+            for m in range(3):
+                Fh = self.M[m][0] * F[0][v] + self.M[m][1] * F[1][v] + self.M[m][2] * F[2][v]
+                s = s + self.deriv(Fh, m)
+            out.append(-self.J * s)
+        return np.array(out)
