@@ -50,6 +50,7 @@ def _args():
     ap.add_argument("--no-rate-compare", action="store_true", help="skip MRAB vs single-rate at equal error")
     ap.add_argument("--no-large", action="store_true", help="skip rhs_eval on meshes larger than L2")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D Taylor-Green workload")
+    ap.add_argument("--no-curv3d", action="store_true", help="skip the 3D curvilinear operator")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-stability", action="store_true", help="skip the step-matrix stability study")
     ap.add_argument("--no-perf-model", action="store_true",
@@ -682,6 +683,51 @@ def _run_3d(steps, warmup, hbm_peak, peak_kind):
     return out
 
 
+def _run_curv3d(hbm_peak, peak_kind, n=192, reps=5):
+    """The 3D curvilinear operator (no configuration of its own): the Navier-Stokes flux
+    divergence on a warped n^3 mesh (each coordinate displaced by 0.02 sin sin of the other two),
+    FP32 and FP64, L2 flushed before every evaluation; state in + right-hand side out + the
+    10 metric planes read = 80 B/pt in FP32."""
+    import numpy as np
+    import torch
+    import paper_1805_06607_gb300 as sbp
+
+    t = np.linspace(0.0, 1.0, n)
+    Z, Y, X = np.meshgrid(t, t, t, indexing="ij")
+    s2 = 2 * np.pi
+    x = X + 0.02 * np.sin(s2 * Y) * np.sin(s2 * Z)
+    y = Y + 0.02 * np.sin(s2 * X) * np.sin(s2 * Z)
+    z = Z + 0.02 * np.sin(s2 * X) * np.sin(s2 * Y)
+    del X, Y
+    rho = 1.0 + 0.1 * np.sin(3 * x) * np.cos(2 * y)
+    q = np.array([rho, 0.3 * rho, -0.2 * rho, 0.1 * rho, 0.9 / 0.4 + 0.5 * rho * 0.14])
+    params = {"physics": "ns", "gamma": 1.4, "mu": 0.001, "pr": 0.72}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"workload": "Navier-Stokes flux divergence on a warped %d^3 curvilinear mesh" % n, "points": n ** 3}
+    for dtype in ("f32", "f64"):
+        g = sbp.Curvilinear3DMesh(x, y, z, params, dtype=dtype)
+        qd = torch.from_numpy(q.astype(np.float32 if dtype == "f32" else np.float64)).cuda()
+        r = g.rhs_eval(qd)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            g.rhs_eval(qd, r)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        es = 4 if dtype == "f32" else 8
+        gbs = n ** 3 * 20 * es / (ms / 1e3) / 1e9
+        out[dtype] = {"ms": ms, "gpts_per_s": n ** 3 / (ms / 1e3) / 1e9, "bytes_per_point": 20 * es,
+                      "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak, "peak_kind": peak_kind,
+                      "kernels": "per point: primitives, contravariant fluxes, derivatives"}
+        g.close()
+        del qd, r
+        torch.cuda.empty_cache()
+    return out
+
+
 def _run_adjoint(n_steps=500, n_snapshots=40):
     """The adjoint workload: the cylinder at half resolution (O-grid 256 x 64, background
     512 x 256), MRAB order 3, step ratio 4, FP64; objective J = H sum_n sum_p p_p(t_n)^2 over
@@ -1000,6 +1046,8 @@ def main():
         line["adjoint"] = _run_adjoint()
     if not args.no_3d and rank == 0:
         line["taylor_green_3d"] = _run_3d(min(args.steps, 10), 2, hbm_peak, peak_kind)
+    if not args.no_curv3d and rank == 0:
+        line["curvilinear_3d"] = _run_curv3d(hbm_peak, peak_kind)
     if not args.no_large and rank == 0:
         line["rhs_eval_large"] = _rhs_eval_large(hbm_peak, peak_kind)
     if not args.no_rate_compare and rank == 0:

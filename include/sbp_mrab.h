@@ -473,6 +473,29 @@ sbp_status sbp3_set_rhs_kernel(sbp3_system_t sys, int mesh, int kchunk);
  * update and the slow-state extrapolation): exact, equal bit for bit to the hardware
  * conversion for every input, without issuing to the FP64 pipe. */
 sbp_status sbp_f32_to_f64(const void *x, void *y, size_t n, void *stream);
+/* ---- 3D curvilinear operator -------------------------------------------------------------------
+ * The flux divergence of the 3D compressible Euler / Navier-Stokes equations (App. C.1) on one
+ * curvilinear structured mesh of n[0] x n[1] x n[2] points (i fastest), non-periodic in every
+ * direction, with the SBP 4-2 derivative (Sec. 2.1) and its closures at both ends of every line;
+ * no SAT penalties or interpolation (the interior operator of a 3D curvilinear mesh):
+ *   dq/dt = -J sum_m D_m (sum_j M[m][j] (F_j - F^V_j)),   M[m][j] = xi_m,x_j / J,
+ * with the metric terms in the symmetric conservative form of Thomas and Lombard (the paper defers
+ * the metrics to other work), M[m][j] = D_b((X_c)_a X_e) - D_a((X_c)_b X_e) over cyclic (m, a, b)
+ * and (j, c, e), J = 1 / det(D_a X_c) (computed in FP64 on the device at creation, stored in the
+ * element type); viscous gradients by d/dx_j = J sum_m M[m][j] D_m. A uniform state has zero
+ * divergence to rounding. params: physics, dtype, gamma, mu, pr are read. x, y, z: host arrays of
+ * n[0]*n[1]*n[2] doubles (copied). States and right-hand sides: 5 device planes of
+ * n[0]*n[1]*n[2] elements, unpitched, q = (rho, rho u, rho v, rho w, rho E). SBP_ERR_SHAPE for a
+ * direction outside 8..65535 points. */
+typedef struct sbp3c_mesh_s *sbp3c_mesh_t;
+sbp_status sbp3c_mesh_create(const int *n, const double *x, const double *y, const double *z,
+                             const sbp_params *params, sbp3c_mesh_t *out);
+sbp_status sbp3c_mesh_destroy(sbp3c_mesh_t mesh);
+/* metrics (host): 10 planes of n[0]*n[1]*n[2] doubles, M[m][j] m-major, then J. Synchronous. */
+sbp_status sbp3c_get_metrics(sbp3c_mesh_t mesh, double *metrics);
+/* rhs = dq/dt (device, asynchronous on stream). */
+sbp_status sbp3c_rhs_eval(sbp3c_mesh_t mesh, const void *q, void *rhs, void *stream);
+
 /* Synchronise the stream and report (then clear) the device error word. */
 sbp_status sbp_check(sbp_system_t sys, void *stream);
 

@@ -139,6 +139,10 @@ _SIGS.update({
     "sbp3_host_tables_create": [ctypes.POINTER(Mesh3Desc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "sbp3_host_tables_destroy": [_P],
     "sbp3_host_tables_get": [_P, _I, _P, _P, _P, _P, _P],
+    "sbp3c_mesh_create": [_P, _P, _P, _P, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "sbp3c_mesh_destroy": [_P],
+    "sbp3c_get_metrics": [_P, _P],
+    "sbp3c_rhs_eval": [_P, _P, _P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -756,6 +760,56 @@ def f32_to_f64(x, stream=None):
     y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
     _check(_lib.sbp_f32_to_f64(_ptr(x), _ptr(y), x.numel(), _stream(stream)), "sbp_f32_to_f64")
     return y
+
+
+class Curvilinear3DMesh:
+    """One 3D curvilinear structured mesh on the current CUDA device (C ABI sbp3c_*): device
+    metric terms and the flux divergence of a state. x, y, z: (nk, nj, ni) coordinate arrays;
+    params: a workload's params dict (physics, gamma, mu, pr)."""
+
+    def __init__(self, x, y, z, params, dtype="f64"):
+        import torch
+        self.torch = torch
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        X = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z)]
+        self.shape = X[0].shape
+        nk, nj, ni = self.shape
+        n = (ctypes.c_int * 3)(ni, nj, nk)
+        pr = Params()
+        pr.physics = PHYSICS[params["physics"]]
+        pr.dtype = DTYPE[dtype]
+        pr.gamma = params["gamma"]
+        pr.mu = params.get("mu", 0.0)
+        pr.pr = params.get("pr", 0.72)
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        _check(_lib.sbp3c_mesh_create(ctypes.cast(n, ctypes.c_void_p), X[0].ctypes.data, X[1].ctypes.data,
+                                      X[2].ctypes.data, ctypes.byref(pr), ctypes.byref(h)), "sbp3c_mesh_create")
+        self.h = h
+
+    def metrics(self):
+        out = np.zeros((10,) + self.shape)
+        _check(_lib.sbp3c_get_metrics(self.h, out.ctypes.data), "sbp3c_get_metrics")
+        return out
+
+    def rhs_eval(self, q, out=None, stream=None):
+        """q: (5, nk, nj, ni) device tensor of the mesh's element type."""
+        q = q.contiguous()
+        if out is None:
+            out = self.torch.empty_like(q)
+        _check(_lib.sbp3c_rhs_eval(self.h, _ptr(q), _ptr(out), _stream(stream)), "sbp3c_rhs_eval")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp3c_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def exported_symbols():

@@ -1,0 +1,104 @@
+// C ABI of the 3D curvilinear operator: a mesh object holding the device metric terms, and the
+// flux divergence of a state (App. C.1's equations in curvilinear coordinates, Sec. 2.1's SBP
+// 4-2 derivative with closures on every line; no SAT terms). Kernels: sbp3c_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "sbp3c_device.h"
+#include "sbp_system.h"
+
+using namespace sbp;
+
+struct sbp3c_mesh_s {
+  int n[3] = {0, 0, 0};
+  sbp_params p{};
+  size_t field = 0, esz = 8;
+  void *met = nullptr, *prim = nullptr, *flux = nullptr;
+  ~sbp3c_mesh_s() {
+    cudaFree(met);
+    cudaFree(prim);
+    cudaFree(flux);
+  }
+};
+
+extern "C" {
+
+sbp_status sbp3c_mesh_create(const int *n, const double *x, const double *y, const double *z,
+                             const sbp_params *params, sbp3c_mesh_t *out) {
+  if (!n || !x || !y || !z || !params || !out) return fail(SBP_ERR_ARG, "null argument");
+  *out = nullptr;
+  const sbp_params &p = *params;
+  if (p.physics != SBP_EULER && p.physics != SBP_NS) return fail(SBP_ERR_ARG, "physics");
+  if (p.dtype != SBP_F64 && p.dtype != SBP_F32) return fail(SBP_ERR_DTYPE, "dtype");
+  if (!(p.gamma > 1.0) || p.mu < 0.0 || !(p.pr > 0.0)) return fail(SBP_ERR_ARG, "gas constants");
+  for (int a = 0; a < 3; ++a)
+    if (n[a] < 8 || n[a] > 65535) return fail(SBP_ERR_SHAPE, "each direction needs 8..65535 points");
+  const long long N = (long long)n[0] * n[1] * n[2];
+  if (N > 2147483647LL / 16) return fail(SBP_ERR_SHAPE, "mesh too large");
+  auto *M = new sbp3c_mesh_s();
+  std::unique_ptr<sbp3c_mesh_s> guard(M);
+  std::memcpy(M->n, n, sizeof(M->n));
+  M->p = p;
+  M->field = (size_t)N;
+  M->esz = p.dtype == SBP_F64 ? 8 : 4;
+  double *dxyz = nullptr, *ddx = nullptr;
+  cudaError_t e = cudaMalloc((void **)&dxyz, 3 * M->field * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&ddx, 9 * M->field * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(dxyz, x, M->field * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dxyz + M->field, y, M->field * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dxyz + 2 * M->field, z, M->field * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&M->met, 10 * M->field * M->esz);
+  if (e == cudaSuccess) e = launch3c_metrics(n[0], n[1], n[2], dxyz, ddx, M->met, p.dtype, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(dxyz);
+  cudaFree(ddx);
+  CUDA_TRY(e);
+  if (p.physics == SBP_NS) CUDA_TRY(cudaMalloc(&M->prim, 4 * M->field * M->esz));
+  CUDA_TRY(cudaMalloc(&M->flux, 15 * M->field * M->esz));
+  *out = guard.release();
+  return SBP_OK;
+}
+
+sbp_status sbp3c_mesh_destroy(sbp3c_mesh_t M) {
+  delete M;
+  return SBP_OK;
+}
+
+sbp_status sbp3c_get_metrics(sbp3c_mesh_t M, double *metrics) {
+  if (!M || !metrics) return fail(SBP_ERR_ARG, "bad argument");
+  const size_t n = 10 * M->field;
+  if (M->esz == 8) {
+    CUDA_TRY(cudaMemcpy(metrics, M->met, n * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    std::unique_ptr<float[]> buf(new float[n]);
+    CUDA_TRY(cudaMemcpy(buf.get(), M->met, n * sizeof(float), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) metrics[i] = buf[i];
+  }
+  return SBP_OK;
+}
+
+sbp_status sbp3c_rhs_eval(sbp3c_mesh_t M, const void *q, void *rhs, void *stream) {
+  if (!M || !q || !rhs) return fail(SBP_ERR_ARG, "bad argument");
+  Curv3Launch a{};
+  a.ni = M->n[0];
+  a.nj = M->n[1];
+  a.nk = M->n[2];
+  a.field = M->field;
+  a.visc = M->p.physics == SBP_NS;
+  a.gam = M->p.gamma;
+  a.mu = a.visc ? M->p.mu : 0.0;
+  a.lam = -2.0 / 3.0 * a.mu;
+  a.kap = a.mu / (M->p.pr * (M->p.gamma - 1.0));
+  a.q = q;
+  a.out = rhs;
+  a.met = M->met;
+  a.prim = M->prim;
+  a.flux = M->flux;
+  CUDA_TRY(launch3c_rhs(a, M->p.dtype, (cudaStream_t)stream));
+  return SBP_OK;
+}
+
+}  // extern "C"

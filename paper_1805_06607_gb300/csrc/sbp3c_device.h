@@ -1,0 +1,29 @@
+// Launch descriptors of the 3D curvilinear operator (sbp3c_kernels.cu): one structured mesh,
+// non-periodic in every direction, arrays unpitched, point (i, j, k) at (k * nj + j) * ni + i.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace sbp {
+
+struct Curv3Launch {
+  int ni, nj, nk;
+  size_t field;          // ni * nj * nk
+  int visc;
+  double gam, mu, lam, kap;
+  const void *q;         // 5 planes
+  void *out;             // 5 planes
+  const void *met;       // 10 planes: M[m][j] = xi_m,x_j / J (m-major), then J
+  void *prim;            // 4 planes (u, v, w, T); Navier-Stokes only
+  void *flux;            // 15 planes: contravariant fluxes F^_m (5 variables each)
+};
+
+// Metric terms of the mesh with coordinates xyz (3 device planes, FP64) into met (10 planes of
+// the element type), using dx (9 device planes, FP64) as workspace.
+cudaError_t launch3c_metrics(int ni, int nj, int nk, const double *xyz, double *dx, void *met, int dtype,
+                             cudaStream_t s);
+cudaError_t launch3c_rhs(const Curv3Launch &a, int dtype, cudaStream_t s);
+
+}  // namespace sbp

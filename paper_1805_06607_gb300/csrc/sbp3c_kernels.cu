@@ -1,0 +1,195 @@
+// 3D curvilinear operator (App. C.1's equations in curvilinear coordinates with Sec. 2.1's SBP
+// 4-2 derivative): one structured mesh with closures at both ends of every line, no SAT terms.
+//   k3c_dx       coordinate derivatives D_a X_c (9 planes, FP64)
+//   k3c_metrics  metric terms M[m][j] = xi_m,x_j / J in the symmetric conservative form of
+//                Thomas and Lombard, M[m][j] = D_b((X_c)_a X_e) - D_a((X_c)_b X_e) over cyclic
+//                (m, a, b) and (j, c, e), and J = 1 / det(D_a X_c) (FP64 arithmetic, stored in
+//                the element type); D along different index directions commute, so
+//                sum_m D_m M[m][j] = 0 and a uniform state has zero divergence to rounding
+//   k3c_prim     primitives (u, v, w, T) (Navier-Stokes)
+//   k3c_flux     contravariant fluxes F^_m = sum_j M[m][j] (F_j - F^V_j), viscous gradients by
+//                the chain rule d/dx_j = J sum_m M[m][j] D_m
+//   k3c_update   dq/dt = -J sum_m D_m F^_m
+#include <cuda_runtime.h>
+
+#include "sbp3c_device.h"
+#include "sbp_dev.cuh"
+
+namespace sbp {
+
+// Stencil class of index c on a non-periodic line of n points: closure rows at both ends.
+__device__ __forceinline__ unsigned line_code(int c, int n) {
+  if (c < 4) return (unsigned)((kLeft << 2) | c);
+  if (c >= n - 4) return (unsigned)((kRight << 2) | (n - 1 - c));
+  return 0u;
+}
+
+// D_d f at point (i, j, k) of an unpitched plane f (unit index spacing).
+template <typename T, typename F>
+__device__ __forceinline__ T cderiv(const F &f, int i, int j, int k, int d, int ni, int nj, int nk) {
+  const int c[3] = {i, j, k}, n[3] = {ni, nj, nk};
+  const ptrdiff_t st[3] = {1, (ptrdiff_t)ni, (ptrdiff_t)ni * nj};
+  const Row<T> r = decode_row<T>(line_code(c[d], n[d]));
+  const ptrdiff_t p = ((ptrdiff_t)k * nj + j) * ni + i;
+  T acc = T(0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc += r.w[e] * f(p + (ptrdiff_t)r.off[e] * st[d]);
+  return r.neg ? -acc : acc;
+}
+
+__global__ void __launch_bounds__(256) k3c_dx(int ni, int nj, int nk, const double *xyz, double *dx) {
+  const size_t N = (size_t)ni * nj * nk;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int i = (int)(t % ni), j = (int)((t / ni) % nj), k = (int)(t / ((size_t)ni * nj));
+  for (int c = 0; c < 3; ++c) {
+    const double *X = xyz + c * N;
+    for (int a = 0; a < 3; ++a)
+      dx[(3 * c + a) * N + t] = cderiv<double>([&](ptrdiff_t q) { return X[q]; }, i, j, k, a, ni, nj, nk);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k3c_metrics(int ni, int nj, int nk, const double *xyz, const double *dx,
+                                                   T *met) {
+  const size_t N = (size_t)ni * nj * nk;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int i = (int)(t % ni), j = (int)((t / ni) % nj), k = (int)(t / ((size_t)ni * nj));
+  const int cyc[3][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}};
+  for (int mm = 0; mm < 3; ++mm) {
+    const int m = cyc[mm][0], a = cyc[mm][1], b = cyc[mm][2];
+    for (int jj = 0; jj < 3; ++jj) {
+      const int jc = cyc[jj][0], c = cyc[jj][1], e = cyc[jj][2];
+      const double *Xe = xyz + e * N, *Dca = dx + (3 * c + a) * N, *Dcb = dx + (3 * c + b) * N;
+      const double s1 = cderiv<double>([&](ptrdiff_t q) { return Dca[q] * Xe[q]; }, i, j, k, b, ni, nj, nk);
+      const double s2 = cderiv<double>([&](ptrdiff_t q) { return Dcb[q] * Xe[q]; }, i, j, k, a, ni, nj, nk);
+      met[(3 * m + jc) * N + t] = (T)(s1 - s2);
+    }
+  }
+  double D[3][3];
+  for (int c = 0; c < 3; ++c)
+    for (int a = 0; a < 3; ++a) D[c][a] = dx[(3 * c + a) * N + t];
+  const double jinv = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                      D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                      D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+  met[9 * N + t] = (T)(1.0 / jinv);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k3c_prim(const Curv3Launch a) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= a.field) return;
+  const T *q = static_cast<const T *>(a.q);
+  T *pr = static_cast<T *>(a.prim);
+  const T rho = q[t], u = q[a.field + t] / rho, v = q[2 * a.field + t] / rho, w = q[3 * a.field + t] / rho;
+  const T gam = (T)a.gam;
+  const T p = (gam - T(1)) * (q[4 * a.field + t] - T(0.5) * rho * (u * u + v * v + w * w));
+  pr[t] = u;
+  pr[a.field + t] = v;
+  pr[2 * a.field + t] = w;
+  pr[3 * a.field + t] = gam * p / rho;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k3c_flux(const Curv3Launch a) {
+  const size_t N = a.field;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int i = (int)(t % a.ni), j = (int)((t / a.ni) % a.nj), k = (int)(t / ((size_t)a.ni * a.nj));
+  const T *q = static_cast<const T *>(a.q);
+  const T *met = static_cast<const T *>(a.met);
+  T M[3][3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[m][c] = met[(3 * m + c) * N + t];
+  const T Jac = met[9 * N + t];
+  const T rho = q[t], vel[3] = {q[N + t] / rho, q[2 * N + t] / rho, q[3 * N + t] / rho}, E = q[4 * N + t];
+  const T gam = (T)a.gam;
+  const T p = (gam - T(1)) * (E - T(0.5) * rho * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]));
+  T F[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d][0] = rho * vel[d];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[d][1 + c] = rho * vel[d] * vel[c] + (c == d ? p : T(0));
+    F[d][4] = (E + p) * vel[d];
+  }
+  if (a.visc) {
+    const T *pr = static_cast<const T *>(a.prim);
+    T g[4][3];  // g[f][d] = d prim_f / d x_d
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T *pf = pr + f * N;
+      T Df[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+        Df[m] = cderiv<T>([&](ptrdiff_t s) { return pf[s]; }, i, j, k, m, a.ni, a.nj, a.nk);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[0] + M[1][d] * Df[1] + M[2][d] * Df[2]);
+    }
+    const T mu = (T)a.mu, lam = (T)a.lam, kap = (T)a.kap;
+    const T div = g[0][0] + g[1][1] + g[2][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T tau[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) tau[c] = mu * (g[d][c] + g[c][d]) + (c == d ? lam * div : T(0));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F[d][1 + c] -= tau[c];
+      F[d][4] -= vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d];
+    }
+  }
+  T *fl = static_cast<T *>(a.flux);
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fl[(5 * m + v) * N + t] = M[m][0] * F[0][v] + M[m][1] * F[1][v] + M[m][2] * F[2][v];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k3c_update(const Curv3Launch a) {
+  const size_t N = a.field;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int i = (int)(t % a.ni), j = (int)((t / a.ni) % a.nj), k = (int)(t / ((size_t)a.ni * a.nj));
+  const T *fl = static_cast<const T *>(a.flux);
+  const T Jac = static_cast<const T *>(a.met)[9 * N + t];
+  T *out = static_cast<T *>(a.out);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    T s = T(0);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const T *f = fl + (5 * m + v) * N;
+      s += cderiv<T>([&](ptrdiff_t q) { return f[q]; }, i, j, k, m, a.ni, a.nj, a.nk);
+    }
+    out[v * N + t] = -Jac * s;
+  }
+}
+
+cudaError_t launch3c_metrics(int ni, int nj, int nk, const double *xyz, double *dx, void *met, int dtype,
+                             cudaStream_t s) {
+  const size_t N = (size_t)ni * nj * nk;
+  const int blocks = (int)((N + 255) / 256);
+  k3c_dx<<<blocks, 256, 0, s>>>(ni, nj, nk, xyz, dx);
+  if (dtype == SBP_F64) k3c_metrics<double><<<blocks, 256, 0, s>>>(ni, nj, nk, xyz, dx, (double *)met);
+  else k3c_metrics<float><<<blocks, 256, 0, s>>>(ni, nj, nk, xyz, dx, (float *)met);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch3c_rhs_t(const Curv3Launch &a, cudaStream_t s) {
+  const int blocks = (int)((a.field + 255) / 256);
+  if (a.visc) k3c_prim<T><<<blocks, 256, 0, s>>>(a);
+  k3c_flux<T><<<blocks, 256, 0, s>>>(a);
+  k3c_update<T><<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch3c_rhs(const Curv3Launch &a, int dtype, cudaStream_t s) {
+  return dtype == SBP_F64 ? launch3c_rhs_t<double>(a, s) : launch3c_rhs_t<float>(a, s);
+}
+
+}  // namespace sbp

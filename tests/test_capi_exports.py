@@ -10,7 +10,7 @@ from conftest import ROOT, build_library
 def _declared():
     src = open(os.path.join(ROOT, "include", "sbp_mrab.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sbp3?_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sbp[0-9a-z]*_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_header_symbols():
