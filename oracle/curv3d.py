@@ -1,9 +1,9 @@
 """Plain FP64 CPU oracle: the flux divergence of the 3D compressible Navier-Stokes equations on
 one curvilinear structured mesh.
 
-TEST INFRASTRUCTURE ONLY. The GPU library never imports it; only tests may use it. No GPU path
-for 3D curvilinear meshes exists yet: this is the definition such a path will be checked against,
-pinned by tests/test_oracle_curv3d.py.
+TEST INFRASTRUCTURE ONLY. The GPU library never imports it; only tests may use it. It is the
+definition the GPU's curvilinear operator (sbp3c_*) is checked against, pinned by
+tests/test_oracle_curv3d.py.
 
 What it computes (App. C.1's equations in curvilinear coordinates, Sec. 2.1's SBP operator):
   * coordinate derivatives X_a = D_a X by the SBP 4-2 first derivative along each index
@@ -17,8 +17,13 @@ What it computes (App. C.1's equations in curvilinear coordinates, Sec. 2.1's SB
   * gradients d f / d x_j = J sum_m M[m][j] D_m f of (u, v, w, T) (the viscous term's first
     application of D), stresses with Stokes' hypothesis, Fourier heat flux (App. C.1);
   * dq/dt = -J sum_m D_m (sum_j M[m][j] (F_j - F^V_j)).
-No SAT penalties: this is the interior operator; boundary and interface terms are those of the
-Cartesian oracle with the metric vector in place of 1/h.
+Optionally (qinf given) the far-field SAT of Sec. 5.1 on all six faces (reading: the
+characteristic penalty of eq. (int) towards qinf with sigma, no viscous term, as for the 2D
+far field): at a point on the low (side +1) or high (side -1) face of index direction m,
+    dq/dt += -(sigma / p0) K^side_k (q - qinf),   k = grad xi_m = J M[m][:],
+summed over the directions whose face the point lies on (edges and corners), with K^side_k the
+characteristic splitting of the flux Jacobian along k (the Cartesian oracle's
+orc_penalty_matrix3d) and p0 = 17/48.
 
 Arrays are (nk, nj, ni) per variable, i fastest; q = (rho, rho u, rho v, rho w, rho E).
 """
@@ -85,8 +90,9 @@ class Curvilinear3D:
         Df = [self.deriv(f, m) for m in range(3)]
         return [self.J * (self.M[0][j] * Df[0] + self.M[1][j] * Df[1] + self.M[2][j] * Df[2]) for j in range(3)]
 
-    def rhs(self, q, gamma, mu=0.0, pr=0.72):
-        """dq/dt = -J sum_m D_m F^_m (5 arrays), F^_m = sum_j M[m][j] (F_j - F^V_j)."""
+    def rhs(self, q, gamma, mu=0.0, pr=0.72, qinf=None, sigma=1.0):
+        """dq/dt = -J sum_m D_m F^_m (5 arrays), F^_m = sum_j M[m][j] (F_j - F^V_j), plus the
+        far-field SAT on every face when qinf (5 values) is given."""
         rho = q[0]
         vel = [q[1] / rho, q[2] / rho, q[3] / rho]
         E = q[4]
@@ -110,4 +116,30 @@ class Curvilinear3D:
                 Fh = self.M[m][0] * F[0][v] + self.M[m][1] * F[1][v] + self.M[m][2] * F[2][v]
                 s = s + self.deriv(Fh, m)
             out.append(-self.J * s)
-        return np.array(out)
+        out = np.array(out)
+        if qinf is not None:
+            self._farfield(out, q, gamma, np.asarray(qinf, dtype=np.float64), sigma)
+        return out
+
+    def _farfield(self, out, q, gamma, qinf, sigma):
+        L = lib()
+        p0 = 17.0 / 48.0
+        nk, nj, ni = self.shape
+        n = (ni, nj, nk)
+        K = np.zeros((5, 5))
+        for k in range(nk):
+            for j in range(nj):
+                for i in range(ni):
+                    c = (i, j, k)
+                    for m in range(3):
+                        if c[m] == 0:
+                            side = 1
+                        elif c[m] == n[m] - 1:
+                            side = -1
+                        else:
+                            continue
+                        kv = [self.J[k, j, i] * self.M[m][jj][k, j, i] for jj in range(3)]
+                        qp = np.ascontiguousarray(q[:, k, j, i], dtype=np.float64)
+                        L.orc_penalty_matrix3d(ctypes.c_void_p(qp.ctypes.data), gamma, kv[0], kv[1], kv[2], side,
+                                               ctypes.c_void_p(K.ctypes.data))
+                        out[:, k, j, i] -= (sigma / p0) * (K @ (qp - qinf))
