@@ -477,7 +477,7 @@ sbp_status sbp_f32_to_f64(const void *x, void *y, size_t n, void *stream);
  * The flux divergence of the 3D compressible Euler / Navier-Stokes equations (App. C.1) on one
  * curvilinear structured mesh of n[0] x n[1] x n[2] points (i fastest), non-periodic in every
  * direction, with the SBP 4-2 derivative (Sec. 2.1) and its closures at both ends of every line;
- * no SAT penalties or interpolation (the interior operator of a 3D curvilinear mesh):
+ * no interpolation, and SAT penalties only for the optional far field (sbp3c_set_farfield):
  *   dq/dt = -J sum_m D_m (sum_j M[m][j] (F_j - F^V_j)),   M[m][j] = xi_m,x_j / J,
  * with the metric terms in the symmetric conservative form of Thomas and Lombard (the paper defers
  * the metrics to other work), M[m][j] = D_b((X_c)_a X_e) - D_a((X_c)_b X_e) over cyclic (m, a, b)
@@ -493,6 +493,14 @@ sbp_status sbp3c_mesh_create(const int *n, const double *x, const double *y, con
 sbp_status sbp3c_mesh_destroy(sbp3c_mesh_t mesh);
 /* metrics (host): 10 planes of n[0]*n[1]*n[2] doubles, M[m][j] m-major, then J. Synchronous. */
 sbp_status sbp3c_get_metrics(sbp3c_mesh_t mesh, double *metrics);
+/* Far-field SAT (Sec. 5.1's characteristic penalty, Sec. 2.2 eq. (int) towards a free stream) on
+ * all six faces: at a point on the low (side +1) or high (side -1) face of index direction m the
+ * right-hand side gains -(sigma / p0) K^side_k (q - qinf) with k = grad xi_m = J M[m][:] and
+ * p0 = 17/48, one term for each face the point lies on (edges and corners take two or three);
+ * no viscous penalty. qinf (host, 5 values, copied): the free stream's conserved variables;
+ * NULL turns the SAT off (the default at creation). SBP_ERR_ARG for sigma < 0 or a free stream
+ * without positive density and pressure. */
+sbp_status sbp3c_set_farfield(sbp3c_mesh_t mesh, const double *qinf, double sigma);
 /* rhs = dq/dt (device, asynchronous on stream). */
 sbp_status sbp3c_rhs_eval(sbp3c_mesh_t mesh, const void *q, void *rhs, void *stream);
 

@@ -143,6 +143,7 @@ _SIGS.update({
     "sbp3c_mesh_destroy": [_P],
     "sbp3c_get_metrics": [_P, _P],
     "sbp3c_rhs_eval": [_P, _P, _P, _P],
+    "sbp3c_set_farfield": [_P, _P, ctypes.c_double],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -791,6 +792,16 @@ class Curvilinear3DMesh:
         out = np.zeros((10,) + self.shape)
         _check(_lib.sbp3c_get_metrics(self.h, out.ctypes.data), "sbp3c_get_metrics")
         return out
+
+    def set_farfield(self, qinf, sigma=1.0):
+        """Far-field SAT towards qinf (5 conserved values) on every face; None turns it off."""
+        if qinf is None:
+            _check(_lib.sbp3c_set_farfield(self.h, None, 0.0), "sbp3c_set_farfield")
+            return
+        qi = np.ascontiguousarray(qinf, dtype=np.float64)
+        if qi.shape != (5,):
+            raise ValueError("qinf needs 5 values")
+        _check(_lib.sbp3c_set_farfield(self.h, qi.ctypes.data, float(sigma)), "sbp3c_set_farfield")
 
     def rhs_eval(self, q, out=None, stream=None):
         """q: (5, nk, nj, ni) device tensor of the mesh's element type."""

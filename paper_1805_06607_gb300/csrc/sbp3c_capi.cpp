@@ -1,6 +1,7 @@
 // C ABI of the 3D curvilinear operator: a mesh object holding the device metric terms, and the
 // flux divergence of a state (App. C.1's equations in curvilinear coordinates, Sec. 2.1's SBP
-// 4-2 derivative with closures on every line; no SAT terms). Kernels: sbp3c_kernels.cu.
+// 4-2 derivative with closures on every line; optionally the far-field SAT of Sec. 5.1 on every
+// face). Kernels: sbp3c_kernels.cu.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -17,6 +18,8 @@ struct sbp3c_mesh_s {
   sbp_params p{};
   size_t field = 0, esz = 8;
   void *met = nullptr, *prim = nullptr, *flux = nullptr;
+  int far = 0;
+  double sig = 0.0, qinf[5] = {0, 0, 0, 0, 0};
   ~sbp3c_mesh_s() {
     cudaFree(met);
     cudaFree(prim);
@@ -80,6 +83,21 @@ sbp_status sbp3c_get_metrics(sbp3c_mesh_t M, double *metrics) {
   return SBP_OK;
 }
 
+sbp_status sbp3c_set_farfield(sbp3c_mesh_t M, const double *qinf, double sigma) {
+  if (!M) return fail(SBP_ERR_ARG, "null mesh");
+  if (!qinf) {
+    M->far = 0;
+    return SBP_OK;
+  }
+  if (!(sigma >= 0.0) || !(qinf[0] > 0.0)) return fail(SBP_ERR_ARG, "far field: sigma >= 0 and rho > 0 required");
+  const double ke = 0.5 * (qinf[1] * qinf[1] + qinf[2] * qinf[2] + qinf[3] * qinf[3]) / qinf[0];
+  if (!((M->p.gamma - 1.0) * (qinf[4] - ke) > 0.0)) return fail(SBP_ERR_ARG, "far field: pressure must be positive");
+  M->far = 1;
+  M->sig = sigma;
+  std::memcpy(M->qinf, qinf, sizeof(M->qinf));
+  return SBP_OK;
+}
+
 sbp_status sbp3c_rhs_eval(sbp3c_mesh_t M, const void *q, void *rhs, void *stream) {
   if (!M || !q || !rhs) return fail(SBP_ERR_ARG, "bad argument");
   Curv3Launch a{};
@@ -97,6 +115,9 @@ sbp_status sbp3c_rhs_eval(sbp3c_mesh_t M, const void *q, void *rhs, void *stream
   a.met = M->met;
   a.prim = M->prim;
   a.flux = M->flux;
+  a.far = M->far;
+  a.sig = M->sig;
+  std::memcpy(a.qinf, M->qinf, sizeof(a.qinf));
   CUDA_TRY(launch3c_rhs(a, M->p.dtype, (cudaStream_t)stream));
   return SBP_OK;
 }

@@ -18,6 +18,8 @@ struct Curv3Launch {
   const void *met;       // 10 planes: M[m][j] = xi_m,x_j / J (m-major), then J
   void *prim;            // 4 planes (u, v, w, T); Navier-Stokes only
   void *flux;            // 15 planes: contravariant fluxes F^_m (5 variables each)
+  int far;               // far-field SAT on every face towards qinf with sigma
+  double sig, qinf[5];
 };
 
 // Metric terms of the mesh with coordinates xyz (3 device planes, FP64) into met (10 planes of

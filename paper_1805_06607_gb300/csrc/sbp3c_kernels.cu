@@ -10,8 +10,13 @@
 //   k3c_flux     contravariant fluxes F^_m = sum_j M[m][j] (F_j - F^V_j), viscous gradients by
 //                the chain rule d/dx_j = J sum_m M[m][j] D_m
 //   k3c_update   dq/dt = -J sum_m D_m F^_m
+//   k3c_far      (optional) the far-field SAT of Sec. 5.1 on every face: at a point on the low
+//                (side +1) or high (side -1) face of index direction m, -(sigma / p0)
+//                K^side_k (q - qinf) with k = grad xi_m = J M[m][:], one term for each face the
+//                point lies on
 #include <cuda_runtime.h>
 
+#include "sbp3_penalty.cuh"
 #include "sbp3c_device.h"
 #include "sbp_dev.cuh"
 
@@ -169,6 +174,65 @@ __global__ void __launch_bounds__(256) k3c_update(const Curv3Launch a) {
   }
 }
 
+// Number of distinct face points of the mesh, enumerated by k3c_far as: both i faces (all j, k),
+// then both j faces (interior i, all k), then both k faces (interior i and j).
+static size_t face_points(int ni, int nj, int nk) {
+  return 2 * ((size_t)nj * nk + (size_t)(ni - 2) * nk + (size_t)(ni - 2) * (nj - 2));
+}
+
+// Far-field SAT added to the right-hand side at each face point (one thread per point, all the
+// faces it lies on, in index-direction order), after k3c_update on the same stream. Kept apart
+// from k3c_update so that the penalty's registers do not cut the occupancy of every point.
+template <typename T>
+__global__ void __launch_bounds__(128) k3c_far(const Curv3Launch a, size_t nface) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= nface) return;
+  const int ni = a.ni, nj = a.nj, nk = a.nk;
+  const size_t fi = (size_t)nj * nk, fj = (size_t)(ni - 2) * nk, fk = (size_t)(ni - 2) * (nj - 2);
+  int i, j, k;
+  if (t < 2 * fi) {
+    const size_t r = t % fi;
+    i = t < fi ? 0 : ni - 1;
+    j = (int)(r % nj);
+    k = (int)(r / nj);
+  } else if (t < 2 * (fi + fj)) {
+    const size_t u = t - 2 * fi, r = u % fj;
+    j = u < fj ? 0 : nj - 1;
+    i = 1 + (int)(r % (ni - 2));
+    k = (int)(r / (ni - 2));
+  } else {
+    const size_t u = t - 2 * (fi + fj), r = u % fk;
+    k = u < fk ? 0 : nk - 1;
+    i = 1 + (int)(r % (ni - 2));
+    j = 1 + (int)(r / (ni - 2));
+  }
+  const size_t N = a.field, p = ((size_t)k * nj + j) * ni + i;
+  const T *q = static_cast<const T *>(a.q);
+  const T *met = static_cast<const T *>(a.met);
+  T *out = static_cast<T *>(a.out);
+  const T Jac = met[9 * N + p];
+  T qp[5], dq[5], r[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qp[v] = q[v * N + p];
+    dq[v] = qp[v] - (T)a.qinf[v];
+    r[v] = out[v * N + p];
+  }
+  const T sp = (T)a.sig * T(1.0 / SBP_P0);
+  const int c[3] = {i, j, k}, n[3] = {ni, nj, nk};
+  for (int m = 0; m < 3; ++m) {
+    const int side = c[m] == 0 ? 1 : (c[m] == n[m] - 1 ? -1 : 0);
+    if (!side) continue;
+    const T kv[3] = {Jac * met[(3 * m) * N + p], Jac * met[(3 * m + 1) * N + p], Jac * met[(3 * m + 2) * N + p]};
+    T kd[5];
+    penalty3(qp, (T)a.gam, kv, side, dq, kd);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) r[v] -= sp * kd[v];
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[v * N + p] = r[v];
+}
+
 cudaError_t launch3c_metrics(int ni, int nj, int nk, const double *xyz, double *dx, void *met, int dtype,
                              cudaStream_t s) {
   const size_t N = (size_t)ni * nj * nk;
@@ -185,6 +249,10 @@ static cudaError_t launch3c_rhs_t(const Curv3Launch &a, cudaStream_t s) {
   if (a.visc) k3c_prim<T><<<blocks, 256, 0, s>>>(a);
   k3c_flux<T><<<blocks, 256, 0, s>>>(a);
   k3c_update<T><<<blocks, 256, 0, s>>>(a);
+  if (a.far) {
+    const size_t nf = face_points(a.ni, a.nj, a.nk);
+    k3c_far<T><<<(unsigned)((nf + 127) / 128), 128, 0, s>>>(a, nf);
+  }
   return cudaGetLastError();
 }
 

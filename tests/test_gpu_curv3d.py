@@ -1,7 +1,8 @@
 """The 3D curvilinear operator on the GPU (sbp3c_*) against the oracle (oracle.curv3d): metric
 terms and flux divergences on warped meshes of uneven sizes, Euler and Navier-Stokes, FP64 to
 1e-12 relative (metrics to 1e-13), FP32 to the rounding bound of its fluxes; a uniform state
-keeps zero divergence (free-stream preservation)."""
+keeps zero divergence (free-stream preservation); the optional far-field SAT on every face
+against the oracle's, and zero at the free stream."""
 import numpy as np
 import pytest
 
@@ -108,3 +109,55 @@ def test_bad_sizes_rejected(sbp):
     x, y, z = _mesh(7, 10, 10)
     with pytest.raises(sbp.SbpError):
         sbp.Curvilinear3DMesh(x, y, z, PARAMS["euler"])
+
+
+QINF = np.array([1.0, 0.35, -0.1, 0.05, 0.9 / 0.4 + 0.5 * (0.35 ** 2 + 0.1 ** 2 + 0.05 ** 2)])
+
+
+@pytest.mark.parametrize("phys", ["euler", "ns"])
+@pytest.mark.parametrize("shape", [(20, 17, 13), (9, 8, 12)])
+def test_farfield_sat_matches_oracle(sbp, phys, shape):
+    """Far-field SAT on every face (edges and corners carry two or three terms)."""
+    x, y, z = _mesh(*shape)
+    o = Curvilinear3D(x, y, z)
+    q = _state(x, y, z, 13)
+    P = PARAMS[phys]
+    sigma = 1.3
+    want = o.rhs(q, P["gamma"], P["mu"], P["pr"], qinf=QINF, sigma=sigma)
+    plain = o.rhs(q, P["gamma"], P["mu"], P["pr"])
+    assert np.linalg.norm(want - plain) > 1e-3 * np.linalg.norm(want)
+    g = sbp.Curvilinear3DMesh(x, y, z, P)
+    g.set_farfield(QINF, sigma)
+    got = g.rhs_eval(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert _rel(got, want) < 1e-12, _rel(got, want)
+    g.set_farfield(None)
+    got0 = g.rhs_eval(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert _rel(got0, plain) < 1e-12, _rel(got0, plain)
+    g.close()
+    g32 = sbp.Curvilinear3DMesh(x, y, z, P, dtype="f32")
+    g32.set_farfield(QINF, sigma)
+    got32 = g32.rhs_eval(torch.from_numpy(q.astype(np.float32)).cuda()).cpu().numpy()
+    assert _rel(got32, want) < 2e-4, _rel(got32, want)
+    g32.close()
+
+
+def test_farfield_free_stream_preserved(sbp):
+    x, y, z = _mesh(24, 21, 19)
+    q = np.array([np.full(x.shape, c) for c in QINF])
+    g = sbp.Curvilinear3DMesh(x, y, z, PARAMS["ns"])
+    g.set_farfield(QINF, 1.0)
+    r = g.rhs_eval(torch.from_numpy(q).cuda()).cpu().numpy()
+    assert np.abs(r).max() < 1e-11, np.abs(r).max()
+    g.close()
+
+
+def test_farfield_bad_arguments_rejected(sbp):
+    x, y, z = _mesh(10, 10, 10)
+    g = sbp.Curvilinear3DMesh(x, y, z, PARAMS["euler"])
+    with pytest.raises(sbp.SbpError):
+        g.set_farfield(QINF, -1.0)
+    bad = QINF.copy()
+    bad[4] = 0.0   # negative pressure
+    with pytest.raises(sbp.SbpError):
+        g.set_farfield(bad, 1.0)
+    g.close()
