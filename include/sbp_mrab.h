@@ -270,6 +270,20 @@ sbp_status sbp_set_rhs_shape(sbp_system_t sys, int mesh, int strip, int rows);
  * (SBP_ERR_STATE otherwise). */
 sbp_status sbp_integrator_state(sbp_system_t sys, int mesh, void *q, void *hist, int set, void *stream);
 
+/* Checkpoint and resume of the whole integrator between macro steps (after sbp_mrab_init):
+ * both meshes' current states and history rings, the ring positions, the node times of the
+ * history entries, H, the elapsed time and the variable-step counter, in one host blob.
+ * sbp_checkpoint_save with blob NULL sets *size to the bytes needed; otherwise *size (in) is the
+ * buffer's capacity (SBP_ERR_ARG if too small) and (out) the bytes written. Synchronises the
+ * stream. sbp_checkpoint_load restores a blob into a system created with the same meshes and
+ * parameters and with bound buffers (SBP_ERR_STATE otherwise); it need not have run
+ * sbp_mrab_init. Macro steps after a load give the same bits as the steps after the save.
+ * SBP_ERR_ARG for a blob that is not a checkpoint, is truncated, or comes from a system with
+ * another element type, physics, scheme, history length or step ratio; SBP_ERR_SHAPE for other
+ * mesh sizes. The blob is in the host's byte order. Synchronises the stream. */
+sbp_status sbp_checkpoint_save(sbp_system_t sys, void *blob, size_t *size, void *stream);
+sbp_status sbp_checkpoint_load(sbp_system_t sys, const void *blob, size_t size, void *stream);
+
 /* n steps of the classical fourth-order Runge-Kutta method at step h on both meshes at one
  * rate, the single-rate baseline of Sec. 4.4 and 6.1 (eq. (perf_RK4): four right-hand sides
  * of every point per step). Each stage evaluates both meshes' right-hand sides with the overset

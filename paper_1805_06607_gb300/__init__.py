@@ -100,6 +100,8 @@ _SIGS = {
     "sbp_profile_read": [_P, _P, _P, _I],
     "sbp_set_rhs_shape": [_P, _I, _I, _I],
     "sbp_integrator_state": [_P, _I, _P, _P, _I, _P],
+    "sbp_checkpoint_save": [_P, _P, ctypes.POINTER(ctypes.c_size_t), _P],
+    "sbp_checkpoint_load": [_P, _P, ctypes.c_size_t, _P],
 }
 _SIGS.update({
     "sbp_batch_create": [ctypes.POINTER(_P), _I, _I, _P, ctypes.POINTER(_P)],
@@ -413,6 +415,21 @@ class System:
             q, h = state[k]
             _check(_lib.sbp_integrator_state(self.h, k, _ptr(q.contiguous()), _ptr(h.contiguous()), 1,
                                              _stream(stream)), "sbp_integrator_state")
+
+    def checkpoint_save(self, stream=None):
+        """The whole integrator (states, history rings, node times, H, t) as bytes."""
+        n = ctypes.c_size_t(0)
+        _check(_lib.sbp_checkpoint_save(self.h, None, ctypes.byref(n), _stream(stream)), "sbp_checkpoint_save")
+        buf = (ctypes.c_char * n.value)()
+        _check(_lib.sbp_checkpoint_save(self.h, ctypes.addressof(buf), ctypes.byref(n), _stream(stream)),
+               "sbp_checkpoint_save")
+        return bytes(buf)
+
+    def checkpoint_load(self, blob, stream=None):
+        """Restore the integrator from checkpoint_save's bytes (buffers must be bound)."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(_lib.sbp_checkpoint_load(self.h, ctypes.addressof(buf), len(blob), _stream(stream)),
+               "sbp_checkpoint_load")
 
     def mrab_time(self):
         H = ctypes.c_double()

@@ -369,6 +369,114 @@ sbp_status sbp_integrator_state(sbp_system_t S, int k, void *q, void *hist, int 
   return SBP_OK;
 }
 
+// Checkpoint blob: a fixed header, then per mesh the current state and the m history ring
+// slots in slot order (each state_elems * esz bytes).
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version, dtype, physics, scheme, m, sr;
+  int64_t state_elems[2];
+  int32_t cur[2], head[2], count[2], var_left;
+  double H, t;
+  double tnode[2][kMaxHist];
+};
+constexpr char kCkptMagic[8] = {'S', 'B', 'P', 'C', 'K', 'P', 'T', '1'};
+
+size_t ckpt_bytes(const sbp_system_s *S) {
+  size_t b = sizeof(CkptHeader);
+  for (int k = 0; k < 2; ++k) b += (size_t)(1 + S->plan.m) * S->state_elems(k) * S->esz;
+  return b;
+}
+}  // namespace
+
+sbp_status sbp_checkpoint_save(sbp_system_t S, void *blob, size_t *size, void *stream) {
+  if (!S || !size) return fail(SBP_ERR_ARG, "bad argument");
+  if (!S->initialised) return fail(SBP_ERR_STATE, "sbp_mrab_init has not run");
+  const size_t need = ckpt_bytes(S);
+  if (!blob) {
+    *size = need;
+    return SBP_OK;
+  }
+  if (*size < need) return fail(SBP_ERR_ARG, "checkpoint buffer too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+  h.version = 1;
+  h.dtype = S->p.dtype;
+  h.physics = S->p.physics;
+  h.scheme = S->p.scheme;
+  h.m = S->plan.m;
+  h.sr = S->plan.sr;
+  for (int k = 0; k < 2; ++k) {
+    h.state_elems[k] = (int64_t)S->state_elems(k);
+    h.cur[k] = S->md[k].cur;
+    h.head[k] = S->md[k].head;
+    h.count[k] = S->md[k].count;
+  }
+  h.var_left = S->var_left;
+  h.H = S->H;
+  h.t = S->t;
+  std::memcpy(h.tnode, S->tnode, sizeof(h.tnode));
+  char *out = static_cast<char *>(blob);
+  std::memcpy(out, &h, sizeof(h));
+  size_t off = sizeof(h);
+  for (int k = 0; k < 2; ++k) {
+    const size_t b = S->state_elems(k) * S->esz;
+    CUDA_TRY(cudaMemcpyAsync(out + off, S->md[k].q[S->md[k].cur], b, cudaMemcpyDeviceToHost, s));
+    off += b;
+    CUDA_TRY(cudaMemcpyAsync(out + off, S->md[k].hist, (size_t)S->plan.m * b, cudaMemcpyDeviceToHost, s));
+    off += (size_t)S->plan.m * b;
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *size = need;
+  return SBP_OK;
+}
+
+sbp_status sbp_checkpoint_load(sbp_system_t S, const void *blob, size_t size, void *stream) {
+  if (!S || !blob) return fail(SBP_ERR_ARG, "bad argument");
+  for (int k = 0; k < 2; ++k)
+    if (!S->md[k].hist) return fail(SBP_ERR_STATE, "buffers not bound");
+  if (size < sizeof(CkptHeader)) return fail(SBP_ERR_ARG, "checkpoint too short");
+  CkptHeader h;
+  std::memcpy(&h, blob, sizeof(h));
+  if (std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0 || h.version != 1)
+    return fail(SBP_ERR_ARG, "not a checkpoint of this library");
+  if (h.dtype != S->p.dtype || h.physics != S->p.physics || h.scheme != S->p.scheme || h.m != S->plan.m ||
+      h.sr != S->plan.sr)
+    return fail(SBP_ERR_ARG, "checkpoint of a system with another dtype, physics, scheme, history or ratio");
+  for (int k = 0; k < 2; ++k) {
+    if (h.state_elems[k] != (int64_t)S->state_elems(k)) return fail(SBP_ERR_SHAPE, "checkpoint of other meshes");
+    if (h.cur[k] < 0 || h.cur[k] > 1 || h.head[k] < 0 || h.head[k] >= h.m || h.count[k] < 0)
+      return fail(SBP_ERR_ARG, "corrupt checkpoint header");
+  }
+  if (!(h.H > 0.0) || !std::isfinite(h.H) || !std::isfinite(h.t) || h.var_left < 0 || h.var_left > h.m)
+    return fail(SBP_ERR_ARG, "corrupt checkpoint header");
+  if (size < ckpt_bytes(S)) return fail(SBP_ERR_ARG, "checkpoint too short");
+  cudaStream_t s = (cudaStream_t)stream;
+  const char *in = static_cast<const char *>(blob);
+  size_t off = sizeof(h);
+  for (int k = 0; k < 2; ++k) {
+    const size_t b = S->state_elems(k) * S->esz;
+    CUDA_TRY(cudaMemcpyAsync(S->md[k].q[h.cur[k]], in + off, b, cudaMemcpyHostToDevice, s));
+    off += b;
+    CUDA_TRY(cudaMemcpyAsync(S->md[k].hist, in + off, (size_t)h.m * b, cudaMemcpyHostToDevice, s));
+    off += (size_t)h.m * b;
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < 2; ++k) {
+    S->md[k].cur = h.cur[k];
+    S->md[k].head = h.head[k];
+    S->md[k].count = h.count[k];
+  }
+  S->var_left = h.var_left;
+  S->H = h.H;
+  S->t = h.t;
+  std::memcpy(S->tnode, h.tnode, sizeof(S->tnode));
+  S->initialised = true;
+  S->clear_graphs();
+  return SBP_OK;
+}
+
 sbp_status sbp_mrab_init(sbp_system_t S, double H, void *stream) {
   if (!S) return fail(SBP_ERR_ARG, "null system");
   for (int k = 0; k < 2; ++k)

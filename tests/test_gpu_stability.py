@@ -131,3 +131,45 @@ def test_spectral_radius_brackets_stability(sbp):
         g.close()
     assert rho[0.3] <= 1.0 + 1e-3, rho
     assert rho[1.0] > 1.05, rho
+
+
+def test_checkpoint_blob_resume_is_bit_identical(sbp):
+    """sbp_checkpoint_save / _load: steps after a load give the bits of the steps after the
+    save, in the same system and in a fresh one (whose right-hand-side shapes were never tuned:
+    the kernel designs give the same bits); a checkpoint of another system, a truncated blob
+    and a foreign blob are refused."""
+    wl = _small()
+    g = sbp.System(wl)
+    g.bind(wl["q0"])
+    g.mrab_init()
+    g.mrab_step(3)
+    g.mrab_set_step(g.mrab_time()[0] * 0.9)   # a variable-step transition in flight
+    g.mrab_step(1)
+    blob = g.checkpoint_save()
+    t0 = g.mrab_time()
+    g.mrab_step(4)
+    a = [g.current_state(k).clone() for k in range(2)]
+    ta = g.mrab_time()
+    g.checkpoint_load(blob)
+    assert g.mrab_time() == t0
+    g.mrab_step(4)
+    b = [g.current_state(k).clone() for k in range(2)]
+    assert g.mrab_time() == ta
+    for k in range(2):
+        assert torch.equal(a[k], b[k])
+    fresh = sbp.System(wl)
+    fresh.bind(wl["q0"])
+    fresh.checkpoint_load(blob)
+    fresh.mrab_step(4)
+    for k in range(2):
+        assert torch.equal(a[k], fresh.current_state(k))
+    h32 = sbp.System(wl, dtype="f32")
+    h32.bind(wl["q0"])
+    with pytest.raises(sbp.SbpError):
+        h32.checkpoint_load(blob)
+    with pytest.raises(sbp.SbpError):
+        fresh.checkpoint_load(blob[:-8])
+    with pytest.raises(sbp.SbpError):
+        fresh.checkpoint_load(b"x" * len(blob))
+    for s in (g, fresh, h32):
+        s.close()
