@@ -25,6 +25,12 @@ summed over the directions whose face the point lies on (edges and corners), wit
 characteristic splitting of the flux Jacobian along k (the Cartesian oracle's
 orc_penalty_matrix3d) and p0 = 17/48.
 
+Donor search (Sec. 2.2's donor-receiver pairing and Lagrange interpolation, in 3D as the 2D
+oracle's orc_donors2d does it): for a point p, computational coordinates (s, r, t) on the mesh
+with X(s, r, t) = p, X the mesh map interpolated by the 4 x 4 x 4 Lagrange basis on the stencil
+starting at (floor(s) - 1, ...) clamped into the mesh; Newton from the nearest node until three
+consecutive steps are below 1e-10; the weights are that basis at the solution.
+
 Arrays are (nk, nj, ni) per variable, i fastest; q = (rho, rho u, rho v, rho w, rho E).
 """
 from __future__ import annotations
@@ -143,3 +149,78 @@ class Curvilinear3D:
                         L.orc_penalty_matrix3d(ctypes.c_void_p(qp.ctypes.data), gamma, kv[0], kv[1], kv[2], side,
                                                ctypes.c_void_p(K.ctypes.data))
                         out[:, k, j, i] -= (sigma / p0) * (K @ (qp - qinf))
+
+
+def lagrange4(s):
+    """Cubic Lagrange basis on nodes 0, 1, 2, 3 at s, and its derivative."""
+    d = [s - 0.0, s - 1.0, s - 2.0, s - 3.0]
+    den = [-6.0, 2.0, -2.0, 6.0]
+    l, dl = [], []
+    for a in range(4):
+        o = [d[b] for b in range(4) if b != a]
+        l.append(o[0] * o[1] * o[2] / den[a])
+        dl.append((o[1] * o[2] + o[0] * o[2] + o[0] * o[1]) / den[a])
+    return np.array(l), np.array(dl)
+
+
+def _start(s, n):
+    return int(min(max(np.floor(s) - 1, 0), n - 4))
+
+
+class DonorError(ValueError):
+    pass
+
+
+def donors(x, y, z, points, iblank=None):
+    """Donor stencils on a curvilinear mesh (coordinates (nk, nj, ni)) for points (npts, 3):
+    base (npts, 3) ints (i0, j0, k0), weights (npts, 12) (4 along i, 4 along j, 4 along k) and
+    computational coordinates (npts, 3). Raises DonorError(index) for the first point with no
+    valid stencil (outside the mesh, no convergence, or an inactive point in the stencil)."""
+    X = np.stack([np.asarray(v, dtype=np.float64) for v in (x, y, z)])
+    nk, nj, ni = X.shape[1:]
+    n = (ni, nj, nk)
+    act = np.ones((nk, nj, ni), bool) if iblank is None else np.asarray(iblank) != 0
+    P = np.asarray(points, dtype=np.float64).reshape(-1, 3)
+    base = np.zeros((len(P), 3), np.int64)
+    w = np.zeros((len(P), 12))
+    xi = np.zeros((len(P), 3))
+    for t, p in enumerate(P):
+        d2 = ((X - p[:, None, None, None]) ** 2).sum(axis=0)
+        k, j, i = np.unravel_index(np.argmin(d2), d2.shape)
+        c = np.array([i, j, k], dtype=np.float64)
+        small = 0
+        for _ in range(100):
+            b0 = [_start(c[a], n[a]) for a in range(3)]
+            L = [lagrange4(c[a] - b0[a]) for a in range(3)]
+            cube = X[:, b0[2]:b0[2] + 4, b0[1]:b0[1] + 4, b0[0]:b0[0] + 4]   # (3, 4k, 4j, 4i)
+            val = np.einsum("xkji,i,j,k->x", cube, L[0][0], L[1][0], L[2][0])
+            jac = np.stack([np.einsum("xkji,i,j,k->x", cube, L[0][0 if a != 0 else 1], L[1][0 if a != 1 else 1],
+                                      L[2][0 if a != 2 else 1]) for a in range(3)], axis=1)
+            try:
+                step = np.linalg.solve(jac, val - p)
+            except np.linalg.LinAlgError:
+                break
+            c = c - step
+            small = small + 1 if np.all(np.abs(step) < 1e-10) else 0
+            if small == 3:
+                break
+        if small < 3 or any(c[a] < -1e-9 or c[a] > n[a] - 1 + 1e-9 for a in range(3)):
+            raise DonorError(t)
+        b0 = [_start(c[a], n[a]) for a in range(3)]
+        if not act[b0[2]:b0[2] + 4, b0[1]:b0[1] + 4, b0[0]:b0[0] + 4].all():
+            raise DonorError(t)
+        base[t] = b0
+        for a in range(3):
+            w[t, 4 * a:4 * a + 4] = lagrange4(c[a] - b0[a])[0]
+        xi[t] = c
+    return base, w, xi
+
+
+def interpolate(f, base, w):
+    """sum over the 4 x 4 x 4 stencil of wi wj wk f, for fields f (nf, nk, nj, ni)."""
+    out = np.zeros((f.shape[0], len(base)))
+    for t in range(len(base)):
+        i0, j0, k0 = base[t]
+        cube = f[:, k0:k0 + 4, j0:j0 + 4, i0:i0 + 4]
+        out[:, t] = np.einsum("fkji,i,j,k->f", cube, w[t, 0:4], w[t, 4:8], w[t, 8:12])
+    return out
