@@ -515,6 +515,22 @@ sbp_status sbp3c_get_metrics(sbp3c_mesh_t mesh, double *metrics);
  * NULL turns the SAT off (the default at creation). SBP_ERR_ARG for sigma < 0 or a free stream
  * without positive density and pressure. */
 sbp_status sbp3c_set_farfield(sbp3c_mesh_t mesh, const double *qinf, double sigma);
+/* Donor search on a curvilinear mesh (Sec. 2.2: donor-receiver pairing; weights from the
+ * Lagrange shape functions). Host only, no device calls. For each of the npts points
+ * pts[3 t .. 3 t + 2] = (x, y, z): computational coordinates (s, r, t) (index units) with
+ * X(s, r, t) = p, X the mesh map interpolated by the 4 x 4 x 4 Lagrange basis on the stencil
+ * that starts at floor(.) - 1 clamped into the mesh, found by Newton's method from a nearby
+ * node (the nearest of a coarse subset of nodes, refined locally; the nearest of all nodes if
+ * that start fails) until three consecutive steps stay below 1e-10. Outputs (host, caller
+ * owned): base 3 ints per point (i0, j0, k0), w 12 doubles per point (the 4 basis values along
+ * i, then j, then k: the value at the point is sum wi[a] wj[b] wk[c] f(i0 + a, j0 + b, k0 + c)),
+ * xi 3 doubles per point (NULL to skip). n, x, y, z as for sbp3c_mesh_create; iblank
+ * (n[0]*n[1]*n[2] bytes, NULL: all active) marks active points. SBP_ERR_DONOR for the first
+ * point with no valid stencil (outside the mesh, no convergence, or an inactive point in its
+ * stencil), its index in *first_failed (NULL to skip; -1 when all succeed). */
+sbp_status sbp3c_donor_search(const int *n, const double *x, const double *y, const double *z,
+                              const signed char *iblank, int npts, const double *pts, int *base, double *w,
+                              double *xi, int *first_failed);
 /* rhs = dq/dt (device, asynchronous on stream). */
 sbp_status sbp3c_rhs_eval(sbp3c_mesh_t mesh, const void *q, void *rhs, void *stream);
 

@@ -146,6 +146,7 @@ _SIGS.update({
     "sbp3c_get_metrics": [_P, _P],
     "sbp3c_rhs_eval": [_P, _P, _P, _P],
     "sbp3c_set_farfield": [_P, _P, ctypes.c_double],
+    "sbp3c_donor_search": [_P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -838,6 +839,28 @@ class Curvilinear3DMesh:
             self.close()
         except Exception:
             pass
+
+
+def donor_search_3d(x, y, z, points, iblank=None):
+    """Donor stencils on a curvilinear mesh (host, no device calls; C ABI sbp3c_donor_search).
+    x, y, z: (nk, nj, ni) coordinates; points (npts, 3). Returns base (npts, 3) int32,
+    weights (npts, 12), computational coordinates (npts, 3); raises SbpError (status
+    SBP_ERR_DONOR) naming the first point without a valid stencil."""
+    X = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z)]
+    nk, nj, ni = X[0].shape
+    n = (ctypes.c_int * 3)(ni, nj, nk)
+    P = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    npts = len(P)
+    base = np.zeros((npts, 3), np.int32)
+    w = np.zeros((npts, 12))
+    xi = np.zeros((npts, 3))
+    ib = None if iblank is None else np.ascontiguousarray(iblank, dtype=np.int8)
+    failed = ctypes.c_int(-1)
+    _check(_lib.sbp3c_donor_search(ctypes.cast(n, ctypes.c_void_p), X[0].ctypes.data, X[1].ctypes.data,
+                                   X[2].ctypes.data, None if ib is None else ib.ctypes.data, npts,
+                                   P.ctypes.data, base.ctypes.data, w.ctypes.data, xi.ctypes.data,
+                                   ctypes.byref(failed)), "sbp3c_donor_search")
+    return base, w, xi
 
 
 def exported_symbols():
