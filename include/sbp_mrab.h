@@ -531,6 +531,15 @@ sbp_status sbp3c_set_farfield(sbp3c_mesh_t mesh, const double *qinf, double sigm
 sbp_status sbp3c_donor_search(const int *n, const double *x, const double *y, const double *z,
                               const signed char *iblank, int npts, const double *pts, int *base, double *w,
                               double *xi, int *first_failed);
+/* Overset gather on the mesh (Sec. 2.2 interpolation): out[v * nrecv + r] = sum over a, b, c in
+ * 0..3 of w[12 r + a] w[12 r + 4 + b] w[12 r + 8 + c] q_v(base[3 r] + a, base[3 r + 1] + b,
+ * base[3 r + 2] + c) for the 5 variables v. q: a state (5 device planes); base (3 ints per
+ * receiver) and w (12 doubles per receiver) as sbp3c_donor_search writes them, copied to the
+ * device by the caller; out: 5 planes of nrecv elements of the mesh's element type (device).
+ * The weights are applied in the element type. Stencils must lie inside the mesh (the search
+ * guarantees it; nothing checks it here). Asynchronous on stream. */
+sbp_status sbp3c_interp(sbp3c_mesh_t mesh, const void *q, int nrecv, const int *base, const double *w, void *out,
+                        void *stream);
 /* rhs = dq/dt (device, asynchronous on stream). */
 sbp_status sbp3c_rhs_eval(sbp3c_mesh_t mesh, const void *q, void *rhs, void *stream);
 

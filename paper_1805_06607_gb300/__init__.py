@@ -147,6 +147,7 @@ _SIGS.update({
     "sbp3c_rhs_eval": [_P, _P, _P, _P],
     "sbp3c_set_farfield": [_P, _P, ctypes.c_double],
     "sbp3c_donor_search": [_P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P],
+    "sbp3c_interp": [_P, _P, _I, _P, _P, _P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -820,6 +821,20 @@ class Curvilinear3DMesh:
         if qi.shape != (5,):
             raise ValueError("qinf needs 5 values")
         _check(_lib.sbp3c_set_farfield(self.h, qi.ctypes.data, float(sigma)), "sbp3c_set_farfield")
+
+    def interp(self, q, base, w, stream=None):
+        """Overset gather of q (5, nk, nj, ni) at stencils (base (n, 3) ints, w (n, 12)), as
+        donor_search_3d returns them: a (5, n) device tensor."""
+        torch = self.torch
+        b = torch.as_tensor(np.ascontiguousarray(base, dtype=np.int32)).cuda()
+        wt = torch.as_tensor(np.ascontiguousarray(w, dtype=np.float64)).cuda()
+        n = int(b.shape[0])
+        if b.shape != (n, 3) or wt.shape != (n, 12):
+            raise ValueError("base (n, 3) and w (n, 12) expected")
+        q = q.contiguous()
+        out = torch.empty((5, n), dtype=self.tdtype, device="cuda")
+        _check(_lib.sbp3c_interp(self.h, _ptr(q), n, _ptr(b), _ptr(wt), _ptr(out), _stream(stream)), "sbp3c_interp")
+        return out
 
     def rhs_eval(self, q, out=None, stream=None):
         """q: (5, nk, nj, ni) device tensor of the mesh's element type."""

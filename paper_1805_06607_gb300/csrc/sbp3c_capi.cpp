@@ -98,6 +98,13 @@ sbp_status sbp3c_set_farfield(sbp3c_mesh_t M, const double *qinf, double sigma) 
   return SBP_OK;
 }
 
+sbp_status sbp3c_interp(sbp3c_mesh_t M, const void *q, int nrecv, const int *base, const double *w, void *out,
+                        void *stream) {
+  if (!M || nrecv < 0 || (nrecv > 0 && (!q || !base || !w || !out))) return fail(SBP_ERR_ARG, "bad argument");
+  CUDA_TRY(launch3c_interp(M->n[0], M->n[1], M->field, q, nrecv, base, w, out, M->p.dtype, (cudaStream_t)stream));
+  return SBP_OK;
+}
+
 sbp_status sbp3c_rhs_eval(sbp3c_mesh_t M, const void *q, void *rhs, void *stream) {
   if (!M || !q || !rhs) return fail(SBP_ERR_ARG, "bad argument");
   Curv3Launch a{};

@@ -27,5 +27,9 @@ struct Curv3Launch {
 cudaError_t launch3c_metrics(int ni, int nj, int nk, const double *xyz, double *dx, void *met, int dtype,
                              cudaStream_t s);
 cudaError_t launch3c_rhs(const Curv3Launch &a, int dtype, cudaStream_t s);
+// out (5 planes of nrecv) = the 4 x 4 x 4 Lagrange gather of q's 5 planes at each receiver's
+// stencil (base: 3 ints, w: 12 doubles per receiver; device).
+cudaError_t launch3c_interp(int ni, int nj, size_t field, const void *q, int nrecv, const int *base, const double *w,
+                            void *out, int dtype, cudaStream_t s);
 
 }  // namespace sbp

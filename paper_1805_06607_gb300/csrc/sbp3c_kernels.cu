@@ -10,6 +10,7 @@
 //   k3c_flux     contravariant fluxes F^_m = sum_j M[m][j] (F_j - F^V_j), viscous gradients by
 //                the chain rule d/dx_j = J sum_m M[m][j] D_m
 //   k3c_update   dq/dt = -J sum_m D_m F^_m
+//   k3c_interp   overset gather of the 5 variables at receivers with given donor stencils
 //   k3c_far      (optional) the far-field SAT of Sec. 5.1 on every face: at a point on the low
 //                (side +1) or high (side -1) face of index direction m, -(sigma / p0)
 //                K^side_k (q - qinf) with k = grad xi_m = J M[m][:], one term for each face the
@@ -231,6 +232,48 @@ __global__ void __launch_bounds__(128) k3c_far(const Curv3Launch a, size_t nface
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v) out[v * N + p] = r[v];
+}
+
+// Overset gather (Sec. 2.2 interpolation): out[v][r] = sum over the 4 x 4 x 4 stencil at base[r]
+// of wi wj wk q[v], weights (FP64) taken in the element type, one thread per receiver.
+template <typename T>
+__global__ void __launch_bounds__(128) k3c_interp(int ni, int nj, size_t field, const T *q, int nrecv,
+                                                  const int *base, const double *w, T *out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrecv) return;
+  const int i0 = base[3 * r], j0 = base[3 * r + 1], k0 = base[3 * r + 2];
+  T wi[4], wj[4], wk[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    wi[a] = (T)w[12 * (size_t)r + a];
+    wj[a] = (T)w[12 * (size_t)r + 4 + a];
+    wk[a] = (T)w[12 * (size_t)r + 8 + a];
+  }
+  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
+  for (int c = 0; c < 4; ++c)
+    for (int b = 0; b < 4; ++b) {
+      const size_t p = ((size_t)(k0 + c) * nj + (j0 + b)) * ni + i0;
+      const T wjk = wj[b] * wk[c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const T wt = wi[a] * wjk;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) acc[v] += wt * q[v * field + p + a];
+      }
+    }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[(size_t)v * nrecv + r] = acc[v];
+}
+
+cudaError_t launch3c_interp(int ni, int nj, size_t field, const void *q, int nrecv, const int *base, const double *w,
+                            void *out, int dtype, cudaStream_t s) {
+  if (nrecv <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((nrecv + 127) / 128);
+  if (dtype == SBP_F64)
+    k3c_interp<double><<<blocks, 128, 0, s>>>(ni, nj, field, (const double *)q, nrecv, base, w, (double *)out);
+  else
+    k3c_interp<float><<<blocks, 128, 0, s>>>(ni, nj, field, (const float *)q, nrecv, base, w, (float *)out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch3c_metrics(int ni, int nj, int nk, const double *xyz, double *dx, void *met, int dtype,

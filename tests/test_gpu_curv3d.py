@@ -161,3 +161,28 @@ def test_farfield_bad_arguments_rejected(sbp):
     with pytest.raises(sbp.SbpError):
         g.set_farfield(bad, 1.0)
     g.close()
+
+
+@pytest.mark.parametrize("shape", [(20, 17, 13), (8, 19, 12)])
+def test_overset_gather_matches_oracle(sbp, shape):
+    """sbp3c_interp with stencils from the library's donor search against the oracle's gather:
+    FP64 to 1e-14 relative, FP32 to its rounding."""
+    from oracle.curv3d import interpolate
+    x, y, z = _mesh(*shape)
+    rng = np.random.default_rng(21)
+    nk, nj, ni = x.shape
+    cells = np.stack([rng.integers(1, n - 2, 70) for n in (ni, nj, nk)], axis=1)
+    frac = rng.uniform(0, 1, (70, 3))
+    pts = np.array([[(1 - f[0]) * v[k, j, i] + f[0] * v[k, j, i + 1] for v in (x, y, z)]
+                    for (i, j, k), f in zip(cells, frac)])
+    base, w, _ = sbp.donor_search_3d(x, y, z, pts)
+    q = _state(x, y, z, 5)
+    want = interpolate(q, base, w)
+    g = sbp.Curvilinear3DMesh(x, y, z, PARAMS["euler"])
+    got = g.interp(torch.from_numpy(q).cuda(), base, w).cpu().numpy()
+    assert _rel(got, want) < 1e-14, _rel(got, want)
+    g.close()
+    g32 = sbp.Curvilinear3DMesh(x, y, z, PARAMS["euler"], dtype="f32")
+    got32 = g32.interp(torch.from_numpy(q.astype(np.float32)).cuda(), base, w).cpu().numpy()
+    assert _rel(got32, want) < 1e-6, _rel(got32, want)
+    g32.close()
