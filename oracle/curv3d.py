@@ -25,6 +25,9 @@ summed over the directions whose face the point lies on (edges and corners), wit
 characteristic splitting of the flux Jacobian along k (the Cartesian oracle's
 orc_penalty_matrix3d) and p0 = 17/48.
 
+Optionally interface SAT terms (Sec. 2.2 eq. (int)) at receiver points with given donor values,
+the Cartesian oracle's interface term with the normal k = J M[m][:] (see _interface).
+
 Donor search (Sec. 2.2's donor-receiver pairing and Lagrange interpolation, in 3D as the 2D
 oracle's orc_donors2d does it): for a point p, computational coordinates (s, r, t) on the mesh
 with X(s, r, t) = p, X the mesh map interpolated by the 4 x 4 x 4 Lagrange basis on the stencil
@@ -96,25 +99,29 @@ class Curvilinear3D:
         Df = [self.deriv(f, m) for m in range(3)]
         return [self.J * (self.M[0][j] * Df[0] + self.M[1][j] * Df[1] + self.M[2][j] * Df[2]) for j in range(3)]
 
-    def rhs(self, q, gamma, mu=0.0, pr=0.72, qinf=None, sigma=1.0):
+    def rhs(self, q, gamma, mu=0.0, pr=0.72, qinf=None, sigma=1.0, interface=None):
         """dq/dt = -J sum_m D_m F^_m (5 arrays), F^_m = sum_j M[m][j] (F_j - F^V_j), plus the
-        far-field SAT on every face when qinf (5 values) is given."""
+        far-field SAT on every face when qinf (5 values) is given, plus interface SAT terms when
+        `interface` is given (see _interface)."""
         rho = q[0]
         vel = [q[1] / rho, q[2] / rho, q[3] / rho]
         E = q[4]
         p = (gamma - 1.0) * (E - 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2))
         F = [[rho * vel[d]] + [rho * vel[d] * vel[c] + (p if c == d else 0.0) for c in range(3)]
              + [(E + p) * vel[d]] for d in range(3)]
+        Fv = None
         if mu > 0.0:
             T = gamma * p / rho
             g = [self.gradient(f) for f in vel + [T]]   # g[f][d]
             div = g[0][0] + g[1][1] + g[2][2]
             lam, kap = -2.0 / 3.0 * mu, mu / (pr * (gamma - 1.0))
+            Fv = []
             for d in range(3):
                 tau = [mu * (g[d][c] + g[c][d]) + (lam * div if c == d else 0.0) for c in range(3)]
+                Fv.append(tau + [vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d]])
                 for c in range(3):
                     F[d][1 + c] = F[d][1 + c] - tau[c]
-                F[d][4] = F[d][4] - (vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d])
+                F[d][4] = F[d][4] - Fv[d][3]
         out = []
         for v in range(5):
             s = 0.0
@@ -125,7 +132,38 @@ class Curvilinear3D:
         out = np.array(out)
         if qinf is not None:
             self._farfield(out, q, gamma, np.asarray(qinf, dtype=np.float64), sigma)
+        if interface is not None:
+            self._interface(out, q, gamma, mu, Fv, **interface)
         return out
+
+    def _interface(self, out, q, gamma, mu, Fv, terms, qhat, fvhat=None, sigma=0.5):
+        """Interface SAT of Sec. 2.2 eq. (int) at receiver points, with the metric normal in place
+        of the Cartesian one: for each term (i, j, k, m, side, r, scale) -- receiver point
+        (i, j, k), normal index direction m, side +1 (low face) or -1 (high face), donor values
+        column r of qhat (5, nrecv) and of fvhat (12, nrecv: F^V_d's 4 components (momentum x,
+        y, z, energy) for d = x, y, z, Cartesian, interpolated from the donor mesh; Navier-Stokes
+        only) --
+            dq/dt += scale * (-(1/p0) [(sigma K^side_k + sigma1 I)(q - qhat)
+                                      - side/2 (F^V_k - F^V_k hat)]),
+        k = grad xi_m = J M[m][:], sigma1 = mu |k|^2 / 2 (0 for Euler), F^V_k = sum_d k_d F^V_d
+        (momentum and energy rows)."""
+        L = lib()
+        p0 = 17.0 / 48.0
+        K = np.zeros((5, 5))
+        for (i, j, k, m, side, r, scale) in terms:
+            kv = [self.J[k, j, i] * self.M[m][jj][k, j, i] for jj in range(3)]
+            qp = np.ascontiguousarray(q[:, k, j, i], dtype=np.float64)
+            L.orc_penalty_matrix3d(ctypes.c_void_p(qp.ctypes.data), gamma, kv[0], kv[1], kv[2], side,
+                                   ctypes.c_void_p(K.ctypes.data))
+            dq = qp - qhat[:, r]
+            sig1 = 0.5 * mu * (kv[0] ** 2 + kv[1] ** 2 + kv[2] ** 2) if mu > 0.0 else 0.0
+            sat = -(sigma * (K @ dq) + sig1 * dq) / p0
+            if mu > 0.0:
+                for c in range(4):
+                    own = sum(kv[d] * Fv[d][c][k, j, i] for d in range(3))
+                    hat = sum(kv[d] * fvhat[4 * d + c, r] for d in range(3))
+                    sat[1 + c] += 0.5 * side * (own - hat) / p0
+            out[:, k, j, i] += scale * sat
 
     def _farfield(self, out, q, gamma, qinf, sigma):
         L = lib()

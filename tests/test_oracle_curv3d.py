@@ -9,7 +9,9 @@
 * on a warped mesh it converges to the exact divergence of the Euler and Navier-Stokes fluxes
   of a smooth manufactured state at fourth order away from the boundary closures;
 * the far-field SAT on a rotated uniform mesh is the Cartesian oracle's far-field SAT turned
-  by the same rotation, and it vanishes at the free stream."""
+  by the same rotation, and it vanishes at the free stream;
+* interface SAT terms (with donor values and donor viscous fluxes) on a rotated uniform mesh are
+  the Cartesian oracle's interface terms turned by the same rotation."""
 import ctypes
 
 import numpy as np
@@ -234,3 +236,65 @@ def test_farfield_sat_vanishes_at_free_stream_and_damps_deviation():
     sat = g.rhs(q, GAMMA, qinf=qinf) - g.rhs(q, GAMMA)
     assert np.abs(sat[:, 1:-1, 1:-1, 1:-1]).max() == 0.0
     assert np.abs(sat).max() > 1e-3
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.02])
+def test_interface_sat_on_rotated_mesh_equals_cartesian_oracle(mu):
+    """Interface SAT terms (receiver points on faces, edges and a corner, with donor values and,
+    for Navier-Stokes, donor viscous fluxes) on a uniform mesh turned by R equal the Cartesian
+    oracle's interface terms (kind 1 of orc_rhs3d) with every vector and the viscous-flux tensor
+    turned alike, the result's momentum turned back. A wrong face side, a transposed metric
+    index or a dropped viscous-flux jump fails it."""
+    ni, nj, nk = 11, 9, 10
+    h = (0.1, 0.07, 0.13)
+    R = _rotation()
+    Z, Y, X = np.meshgrid(np.arange(nk) * h[2], np.arange(nj) * h[1], np.arange(ni) * h[0], indexing="ij")
+    g = Curvilinear3D(*np.einsum("ab,b...->a...", R, np.stack([X, Y, Z])))
+    rng = np.random.default_rng(17)
+    q = _uniform_state(X.shape) * (1.0 + 0.05 * rng.standard_normal((5,) + X.shape))
+    # (i, j, k, normal direction, side, receiver column, scale)
+    terms = [(0, 3, 4, 0, 1, 0, 1.0), (ni - 1, 5, 2, 0, -1, 1, 1.0), (4, 0, 6, 1, 1, 2, 1.0),
+             (6, nj - 1, 3, 1, -1, 3, 1.0), (5, 4, 0, 2, 1, 4, 1.0), (3, 2, nk - 1, 2, -1, 5, 1.0),
+             (0, 0, 5, 0, 1, 6, 0.7), (0, 0, 5, 1, 1, 6, 0.7),                      # an edge, weighted
+             (ni - 1, nj - 1, nk - 1, 0, -1, 7, 1.0), (ni - 1, nj - 1, nk - 1, 2, -1, 7, 1.0)]
+    nrecv = 8
+    qhat = np.array([q[:, t[2], t[1], t[0]] for t in sorted({(x[0], x[1], x[2], x[5]) for x in terms},
+                                                             key=lambda x: x[3])]).T
+    qhat = qhat * (1.0 + 0.03 * rng.standard_normal(qhat.shape))
+    fvhat = 0.05 * rng.standard_normal((12, nrecv))
+    sigma = 0.5
+    # Cartesian oracle
+    L = oracle.lib()
+    p = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+    iblank = np.ones((nk, nj, ni), np.int8)
+    ci, cj, ck = (np.zeros((nk, nj, ni), np.int8) for _ in range(3))
+    assert L.orc_classes3d(ni, nj, nk, 0, 0, 0, p(iblank), p(ci), p(cj), p(ck)) >= 0
+    t_pt = np.array([(t[2] * nj + t[1]) * ni + t[0] for t in terms], np.int64)
+    t_dir = np.array([t[3] for t in terms], np.int32)
+    t_side = np.array([t[4] for t in terms], np.int32)
+    t_kind = np.ones(len(terms), np.int32)
+    t_recv = np.array([t[5] for t in terms], np.int32)
+    t_scale = np.array([t[6] for t in terms])
+    want = np.zeros((5, nk, nj, ni))
+    qc, qh, fh = (np.ascontiguousarray(a) for a in (q, qhat, fvhat))
+    rc = L.orc_rhs3d(ni, nj, nk, p(ci), p(cj), p(ck), ctypes.c_double(h[0]), ctypes.c_double(h[1]),
+                     ctypes.c_double(h[2]), p(qc), int(mu > 0), ctypes.c_double(GAMMA), ctypes.c_double(mu),
+                     ctypes.c_double(0.72), len(terms), p(t_pt), p(t_dir), p(t_side), p(t_kind), p(t_recv),
+                     p(t_scale), nrecv, p(qh), p(fh) if mu > 0 else None, p(np.zeros(5)), ctypes.c_double(sigma),
+                     ctypes.c_double(1.0), p(want))
+    assert rc == 0
+    # the same terms on the turned mesh
+    turn = lambda a: np.einsum("ab,b...->a...", R, a)  # noqa: E731
+    qr, qhr = q.copy(), qhat.copy()
+    qr[1:4], qhr[1:4] = turn(q[1:4]), turn(qhat[1:4])
+    F = fvhat.reshape(3, 4, nrecv)                       # F[d][c]
+    Fr = np.empty_like(F)
+    Fr[:, :3] = np.einsum("da,cb,abr->dcr", R, R, F[:, :3])
+    Fr[:, 3] = turn(F[:, 3])
+    got = g.rhs(qr, GAMMA, mu, interface=dict(terms=terms, qhat=qhr, fvhat=Fr.reshape(12, nrecv), sigma=sigma))
+    got[1:4] = np.einsum("ba,b...->a...", R, got[1:4])
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < 1e-12, err
+    plain = g.rhs(qr, GAMMA, mu)
+    plain[1:4] = np.einsum("ba,b...->a...", R, plain[1:4])
+    assert np.linalg.norm(got - plain) > 1e-3 * np.linalg.norm(want)
