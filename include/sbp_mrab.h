@@ -540,6 +540,25 @@ sbp_status sbp3c_donor_search(const int *n, const double *x, const double *y, co
  * guarantees it; nothing checks it here). Asynchronous on stream. */
 sbp_status sbp3c_interp(sbp3c_mesh_t mesh, const void *q, int nrecv, const int *base, const double *w, void *out,
                         void *stream);
+/* Interface SAT terms at receiver points (Sec. 2.2 eq. (int), the normal of index direction m
+ * being k = grad xi_m = J M[m][:]). sbp3c_set_interface stores nterms terms (host, copied):
+ * terms[6 e ..] = (i, j, k, m, side, r): receiver point (i, j, k), normal direction m (0..2),
+ * side +1 (the domain lies towards higher index) or -1, donor column r (0 <= r < nrecv); scale
+ * (NULL: all 1) weights each term (corner weights); sigma is the interface penalty. Terms are
+ * grouped by point and keep their order within a point. SBP_ERR_ARG for a point outside the
+ * mesh, a bad direction, side or column, or sigma < 0. sbp3c_interface_sat adds, at each
+ * receiver point, sum over its terms of
+ *   scale * (-(1/p0) [(sigma K^side_k + sigma1 I)(q - qhat_r) - side/2 (F^V_k - F^V_k hat_r)])
+ * to rhs (device, the mesh's element type), with sigma1 = mu |k|^2 / 2 and F^V_k =
+ * sum_d k_d F^V_d (momentum and energy rows; Navier-Stokes only): the receiver's own viscous
+ * fluxes come from chain-rule gradients of q. qhat: 5 x nrecv donor states (device, plane v at
+ * qhat + v * nrecv); fvhat: 12 x nrecv donor viscous fluxes, the 4 components (momentum x, y,
+ * z, energy) of F^V_x, then F^V_y, then F^V_z (Cartesian; required for Navier-Stokes, else
+ * ignored). Deterministic (one thread per point). Asynchronous on stream. */
+sbp_status sbp3c_set_interface(sbp3c_mesh_t mesh, int nterms, const int *terms, const double *scale, int nrecv,
+                               double sigma);
+sbp_status sbp3c_interface_sat(sbp3c_mesh_t mesh, const void *q, const void *qhat, const void *fvhat, void *rhs,
+                               void *stream);
 /* rhs = dq/dt (device, asynchronous on stream). */
 sbp_status sbp3c_rhs_eval(sbp3c_mesh_t mesh, const void *q, void *rhs, void *stream);
 

@@ -148,6 +148,8 @@ _SIGS.update({
     "sbp3c_set_farfield": [_P, _P, ctypes.c_double],
     "sbp3c_donor_search": [_P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P],
     "sbp3c_interp": [_P, _P, _I, _P, _P, _P, _P],
+    "sbp3c_set_interface": [_P, _I, _P, _P, _I, ctypes.c_double],
+    "sbp3c_interface_sat": [_P, _P, _P, _P, _P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -821,6 +823,23 @@ class Curvilinear3DMesh:
         if qi.shape != (5,):
             raise ValueError("qinf needs 5 values")
         _check(_lib.sbp3c_set_farfield(self.h, qi.ctypes.data, float(sigma)), "sbp3c_set_farfield")
+
+    def set_interface(self, terms, nrecv, sigma=0.5):
+        """Interface SAT terms: a list of (i, j, k, m, side, r, scale)."""
+        t = np.ascontiguousarray([x[:6] for x in terms], dtype=np.int32).reshape(-1, 6)
+        sc = np.ascontiguousarray([x[6] for x in terms], dtype=np.float64)
+        _check(_lib.sbp3c_set_interface(self.h, len(t), t.ctypes.data if len(t) else None,
+                                        sc.ctypes.data if len(t) else None, int(nrecv), float(sigma)),
+               "sbp3c_set_interface")
+
+    def interface_sat(self, q, qhat, rhs, fvhat=None, stream=None):
+        """rhs += the interface SAT terms at state q (device tensors; qhat (5, nrecv), fvhat
+        (12, nrecv) for Navier-Stokes)."""
+        q, qhat = q.contiguous(), qhat.contiguous()
+        fv = None if fvhat is None else fvhat.contiguous()
+        _check(_lib.sbp3c_interface_sat(self.h, _ptr(q), _ptr(qhat), None if fv is None else _ptr(fv), _ptr(rhs),
+                                        _stream(stream)), "sbp3c_interface_sat")
+        return rhs
 
     def interp(self, q, base, w, stream=None):
         """Overset gather of q (5, nk, nj, ni) at stencils (base (n, 3) ints, w (n, 12)), as

@@ -4,9 +4,12 @@
 // face). Kernels: sbp3c_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "sbp3c_device.h"
 #include "sbp_system.h"
@@ -20,10 +23,27 @@ struct sbp3c_mesh_s {
   void *met = nullptr, *prim = nullptr, *flux = nullptr;
   int far = 0;
   double sig = 0.0, qinf[5] = {0, 0, 0, 0, 0};
+  // interface SAT terms grouped by receiver point (device)
+  int i_npt = 0, i_nrecv = 0;
+  double i_sig = 0.0;
+  long long *i_pt = nullptr;
+  int *i_off = nullptr, *i_term = nullptr;
+  double *i_scale = nullptr;
+  void free_interface() {
+    cudaFree(i_pt);
+    cudaFree(i_off);
+    cudaFree(i_term);
+    cudaFree(i_scale);
+    i_pt = nullptr;
+    i_off = i_term = nullptr;
+    i_scale = nullptr;
+    i_npt = i_nrecv = 0;
+  }
   ~sbp3c_mesh_s() {
     cudaFree(met);
     cudaFree(prim);
     cudaFree(flux);
+    free_interface();
   }
 };
 
@@ -102,6 +122,87 @@ sbp_status sbp3c_interp(sbp3c_mesh_t M, const void *q, int nrecv, const int *bas
                         void *stream) {
   if (!M || nrecv < 0 || (nrecv > 0 && (!q || !base || !w || !out))) return fail(SBP_ERR_ARG, "bad argument");
   CUDA_TRY(launch3c_interp(M->n[0], M->n[1], M->field, q, nrecv, base, w, out, M->p.dtype, (cudaStream_t)stream));
+  return SBP_OK;
+}
+
+sbp_status sbp3c_set_interface(sbp3c_mesh_t M, int nterms, const int *terms, const double *scale, int nrecv,
+                               double sigma) {
+  if (!M || nterms < 0 || nrecv < 0 || (nterms > 0 && !terms) || !(sigma >= 0.0))
+    return fail(SBP_ERR_ARG, "bad argument");
+  std::vector<std::pair<long long, int>> order;  // (point, term) sorted by point, stable
+  order.reserve(nterms);
+  for (int e = 0; e < nterms; ++e) {
+    const int *t = terms + 6 * (size_t)e;
+    if (t[0] < 0 || t[0] >= M->n[0] || t[1] < 0 || t[1] >= M->n[1] || t[2] < 0 || t[2] >= M->n[2])
+      return fail(SBP_ERR_ARG, "interface term " + std::to_string(e) + ": point outside the mesh");
+    if (t[3] < 0 || t[3] > 2 || (t[4] != 1 && t[4] != -1) || t[5] < 0 || t[5] >= nrecv)
+      return fail(SBP_ERR_ARG, "interface term " + std::to_string(e) + ": direction, side or receiver column");
+    order.emplace_back(((long long)t[2] * M->n[1] + t[1]) * M->n[0] + t[0], e);
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<long long, int> &x, const std::pair<long long, int> &y) { return x.first < y.first; });
+  std::vector<long long> pt;
+  std::vector<int> off, term;
+  std::vector<double> sc;
+  for (size_t u = 0; u < order.size(); ++u) {
+    if (u == 0 || order[u].first != order[u - 1].first) {
+      pt.push_back(order[u].first);
+      off.push_back((int)u);
+    }
+    const int *t = terms + 6 * (size_t)order[u].second;
+    term.insert(term.end(), {t[3], t[4], t[5]});
+    sc.push_back(scale ? scale[order[u].second] : 1.0);
+  }
+  off.push_back((int)order.size());
+  M->free_interface();
+  CUDA_TRY(upload(M->i_pt, pt.data(), pt.size() * sizeof(long long)));
+  CUDA_TRY(upload(M->i_off, off.data(), off.size() * sizeof(int)));
+  CUDA_TRY(upload(M->i_term, term.data(), term.size() * sizeof(int)));
+  CUDA_TRY(upload(M->i_scale, sc.data(), sc.size() * sizeof(double)));
+  M->i_npt = (int)pt.size();
+  M->i_nrecv = nrecv;
+  M->i_sig = sigma;
+  return SBP_OK;
+}
+
+static Curv3Launch curv_args(sbp3c_mesh_t M, const void *q, void *rhs) {
+  Curv3Launch a{};
+  a.ni = M->n[0];
+  a.nj = M->n[1];
+  a.nk = M->n[2];
+  a.field = M->field;
+  a.visc = M->p.physics == SBP_NS;
+  a.gam = M->p.gamma;
+  a.mu = a.visc ? M->p.mu : 0.0;
+  a.lam = -2.0 / 3.0 * a.mu;
+  a.kap = a.mu / (M->p.pr * (M->p.gamma - 1.0));
+  a.q = q;
+  a.out = rhs;
+  a.met = M->met;
+  a.prim = M->prim;
+  a.flux = M->flux;
+  a.far = M->far;
+  a.sig = M->sig;
+  std::memcpy(a.qinf, M->qinf, sizeof(a.qinf));
+  return a;
+}
+
+sbp_status sbp3c_interface_sat(sbp3c_mesh_t M, const void *q, const void *qhat, const void *fvhat, void *rhs,
+                               void *stream) {
+  if (!M || !q || !rhs || (M->i_npt > 0 && !qhat)) return fail(SBP_ERR_ARG, "bad argument");
+  if (M->p.physics == SBP_NS && M->i_npt > 0 && !fvhat)
+    return fail(SBP_ERR_ARG, "Navier-Stokes interface terms need the donor viscous fluxes");
+  Curv3Sat sat{};
+  sat.npt = M->i_npt;
+  sat.nrecv = M->i_nrecv;
+  sat.pt = M->i_pt;
+  sat.off = M->i_off;
+  sat.term = M->i_term;
+  sat.scale = M->i_scale;
+  sat.qhat = qhat;
+  sat.fvhat = fvhat;
+  sat.sig = M->i_sig;
+  CUDA_TRY(launch3c_isat(curv_args(M, q, rhs), sat, M->p.dtype, (cudaStream_t)stream));
   return SBP_OK;
 }
 

@@ -10,6 +10,7 @@
 //   k3c_flux     contravariant fluxes F^_m = sum_j M[m][j] (F_j - F^V_j), viscous gradients by
 //                the chain rule d/dx_j = J sum_m M[m][j] D_m
 //   k3c_update   dq/dt = -J sum_m D_m F^_m
+//   k3c_isat     interface SAT at receiver points with given donor values (added to a rhs)
 //   k3c_interp   overset gather of the 5 variables at receivers with given donor stencils
 //   k3c_far      (optional) the far-field SAT of Sec. 5.1 on every face: at a point on the low
 //                (side +1) or high (side -1) face of index direction m, -(sigma / p0)
@@ -263,6 +264,98 @@ __global__ void __launch_bounds__(128) k3c_interp(int ni, int nj, size_t field, 
     }
 #pragma unroll
   for (int v = 0; v < 5; ++v) out[(size_t)v * nrecv + r] = acc[v];
+}
+
+// Interface SAT (Sec. 2.2 eq. (int)) at receiver points, one thread per distinct point adding its
+// terms in order: for term (m, side, r, scale), k = J M[m][:],
+//   rhs += scale * (-(1/p0) [(sigma K^side_k + sigma1 I)(q - qhat_r) - side/2 (F^V_k - F^V_k hat_r)])
+// with sigma1 = mu |k|^2 / 2 and F^V_k = sum_d k_d F^V_d (Navier-Stokes), the receiver's own
+// viscous fluxes from chain-rule gradients of primitives taken from q at the stencil taps.
+template <typename T>
+__global__ void __launch_bounds__(64) k3c_isat(const Curv3Launch a, Curv3Sat s) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s.npt) return;
+  const size_t N = a.field;
+  const long long pl = s.pt[t];
+  const int i = (int)(pl % a.ni), j = (int)((pl / a.ni) % a.nj), k = (int)(pl / ((long long)a.ni * a.nj));
+  const size_t p = (size_t)pl;
+  const T *q = static_cast<const T *>(a.q);
+  const T *met = static_cast<const T *>(a.met);
+  const T gam = (T)a.gam;
+  const T Jac = met[9 * N + p];
+  T qp[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qp[v] = q[v * N + p];
+  T Fv[3][4] = {};
+  if (a.visc) {
+    T M[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) M[m][c] = met[(3 * m + c) * N + p];
+    auto prim = [&](ptrdiff_t x, int f) {
+      const T rho = q[x], u = q[N + x] / rho, v = q[2 * N + x] / rho, w = q[3 * N + x] / rho;
+      if (f == 0) return u;
+      if (f == 1) return v;
+      if (f == 2) return w;
+      const T pr = (gam - T(1)) * (q[4 * N + x] - T(0.5) * rho * (u * u + v * v + w * w));
+      return gam * pr / rho;
+    };
+    T g[4][3];
+    for (int f = 0; f < 4; ++f) {
+      T Df[3];
+      for (int m = 0; m < 3; ++m) Df[m] = cderiv<T>([&](ptrdiff_t x) { return prim(x, f); }, i, j, k, m, a.ni, a.nj, a.nk);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[0] + M[1][d] * Df[1] + M[2][d] * Df[2]);
+    }
+    const T mu = (T)a.mu, lam = (T)a.lam, kap = (T)a.kap;
+    const T div = g[0][0] + g[1][1] + g[2][2];
+    const T vel[3] = {qp[1] / qp[0], qp[2] / qp[0], qp[3] / qp[0]};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Fv[d][c] = mu * (g[d][c] + g[c][d]) + (c == d ? lam * div : T(0));
+      Fv[d][3] = vel[0] * Fv[d][0] + vel[1] * Fv[d][1] + vel[2] * Fv[d][2] + kap * g[3][d];
+    }
+  }
+  const T *qh = static_cast<const T *>(s.qhat);
+  const T *fh = static_cast<const T *>(s.fvhat);
+  T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
+  for (int e = s.off[t]; e < s.off[t + 1]; ++e) {
+    const int m = s.term[3 * e], side = s.term[3 * e + 1], r = s.term[3 * e + 2];
+    const T kv[3] = {Jac * met[(3 * m) * N + p], Jac * met[(3 * m + 1) * N + p], Jac * met[(3 * m + 2) * N + p]};
+    T dq[5], kd[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dq[v] = qp[v] - qh[(size_t)v * s.nrecv + r];
+    penalty3(qp, gam, kv, side, dq, kd);
+    const T sig1 = a.visc ? T(0.5) * (T)a.mu * (kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]) : T(0);
+    T sat[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sat[v] = -((T)s.sig * kd[v] + sig1 * dq[v]) * T(1.0 / SBP_P0);
+    if (a.visc) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const T own = kv[0] * Fv[0][c] + kv[1] * Fv[1][c] + kv[2] * Fv[2][c];
+        const T hat = kv[0] * fh[(size_t)c * s.nrecv + r] + kv[1] * fh[(size_t)(4 + c) * s.nrecv + r] +
+                      kv[2] * fh[(size_t)(8 + c) * s.nrecv + r];
+        sat[1 + c] += T(0.5) * T(side) * (own - hat) * T(1.0 / SBP_P0);
+      }
+    }
+    const T sc = (T)s.scale[e];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] += sc * sat[v];
+  }
+  T *out = static_cast<T *>(a.out);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[v * N + p] += acc[v];
+}
+
+cudaError_t launch3c_isat(const Curv3Launch &a, const Curv3Sat &s, int dtype, cudaStream_t st) {
+  if (s.npt <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((s.npt + 63) / 64);
+  if (dtype == SBP_F64) k3c_isat<double><<<blocks, 64, 0, st>>>(a, s);
+  else k3c_isat<float><<<blocks, 64, 0, st>>>(a, s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch3c_interp(int ni, int nj, size_t field, const void *q, int nrecv, const int *base, const double *w,

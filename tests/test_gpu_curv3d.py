@@ -186,3 +186,51 @@ def test_overset_gather_matches_oracle(sbp, shape):
     got32 = g32.interp(torch.from_numpy(q.astype(np.float32)).cuda(), base, w).cpu().numpy()
     assert _rel(got32, want) < 1e-6, _rel(got32, want)
     g32.close()
+
+
+@pytest.mark.parametrize("phys", ["euler", "ns"])
+def test_interface_sat_matches_oracle(sbp, phys):
+    """sbp3c_interface_sat after sbp3c_rhs_eval against the oracle's right-hand side with the same
+    interface terms: receivers on all six faces, a weighted edge, a corner and a point inside
+    the mesh (a hole-boundary receiver), donor states and viscous fluxes given."""
+    x, y, z = _mesh(13, 11, 12)
+    nk, nj, ni = x.shape
+    o = Curvilinear3D(x, y, z)
+    q = _state(x, y, z, 31)
+    P = PARAMS[phys]
+    terms = [(0, 3, 4, 0, 1, 0, 1.0), (ni - 1, 5, 2, 0, -1, 1, 1.0), (4, 0, 6, 1, 1, 2, 1.0),
+             (6, nj - 1, 3, 1, -1, 3, 1.0), (5, 4, 0, 2, 1, 4, 1.0), (3, 2, nk - 1, 2, -1, 5, 1.0),
+             (0, 0, 5, 0, 1, 6, 0.7), (0, 0, 5, 1, 1, 6, 0.7),
+             (ni - 1, nj - 1, nk - 1, 0, -1, 7, 1.0), (ni - 1, nj - 1, nk - 1, 2, -1, 7, 1.0),
+             (6, 5, 6, 0, -1, 8, 1.0)]
+    nrecv = 9
+    rng = np.random.default_rng(3)
+    cols = {t[5]: (t[0], t[1], t[2]) for t in terms}
+    qhat = np.array([q[:, cols[r][2], cols[r][1], cols[r][0]] for r in range(nrecv)]).T
+    qhat = qhat * (1.0 + 0.03 * rng.standard_normal(qhat.shape))
+    fvhat = 0.05 * rng.standard_normal((12, nrecv))
+    sigma = 0.5
+    want = o.rhs(q, P["gamma"], P["mu"], P["pr"], interface=dict(terms=terms, qhat=qhat, fvhat=fvhat, sigma=sigma))
+    plain = o.rhs(q, P["gamma"], P["mu"], P["pr"])
+    assert np.linalg.norm(want - plain) > 1e-3 * np.linalg.norm(want)
+    for dtype, tol in (("f64", 1e-12), ("f32", 2e-4)):
+        nd = np.float64 if dtype == "f64" else np.float32
+        g = sbp.Curvilinear3DMesh(x, y, z, P, dtype=dtype)
+        g.set_interface(terms, nrecv, sigma)
+        qd = torch.from_numpy(q.astype(nd)).cuda()
+        r = g.rhs_eval(qd)
+        g.interface_sat(qd, torch.from_numpy(qhat.astype(nd)).cuda(), r,
+                        fvhat=torch.from_numpy(fvhat.astype(nd)).cuda() if phys == "ns" else None)
+        got = r.cpu().numpy()
+        assert _rel(got, want) < tol, (dtype, _rel(got, want))
+        g.close()
+
+
+def test_interface_terms_rejected(sbp):
+    x, y, z = _mesh(10, 10, 10)
+    g = sbp.Curvilinear3DMesh(x, y, z, PARAMS["euler"])
+    for bad in ([(10, 0, 0, 0, 1, 0, 1.0)], [(0, 0, 0, 3, 1, 0, 1.0)], [(0, 0, 0, 0, 0, 0, 1.0)],
+                [(0, 0, 0, 0, 1, 2, 1.0)]):
+        with pytest.raises(sbp.SbpError):
+            g.set_interface(bad, 2)
+    g.close()
