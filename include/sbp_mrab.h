@@ -531,6 +531,14 @@ sbp_status sbp3c_set_farfield(sbp3c_mesh_t mesh, const double *qinf, double sigm
 sbp_status sbp3c_donor_search(const int *n, const double *x, const double *y, const double *z,
                               const signed char *iblank, int npts, const double *pts, int *base, double *w,
                               double *xi, int *first_failed);
+/* Hole cut against a curvilinear mesh (Sec. 2.2 hole cutting; reading, as for the Cartesian 3D
+ * systems in the overlapping mesh's index units). Host only, no device calls. For each of the
+ * npts points pts[3 t ..] (e.g. another mesh's nodes) the inverse map of the mesh (as in
+ * sbp3c_donor_search) is sought; a point found inside the mesh with every index coordinate more
+ * than margin (>= 0) from the faces (margin < s < n[a] - 1 - margin) is a hole: iblank[t] = 0.
+ * Other entries of iblank (host, npts bytes) are left as they are. */
+sbp_status sbp3c_hole_cut(const int *n, const double *x, const double *y, const double *z, int npts,
+                          const double *pts, double margin, signed char *iblank);
 /* Overset gather on the mesh (Sec. 2.2 interpolation): out[v * nrecv + r] = sum over a, b, c in
  * 0..3 of w[12 r + a] w[12 r + 4 + b] w[12 r + 8 + c] q_v(base[3 r] + a, base[3 r + 1] + b,
  * base[3 r + 2] + c) for the 5 variables v. q: a state (5 device planes); base (3 ints per

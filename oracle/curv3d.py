@@ -209,6 +209,51 @@ class DonorError(ValueError):
     pass
 
 
+def _invert(X, p):
+    """Index coordinates c with the Lagrange-interpolated map X(c) = p (Newton from the nearest
+    node, three consecutive steps below 1e-10), or None (no convergence, or outside the mesh)."""
+    nk, nj, ni = X.shape[1:]
+    n = (ni, nj, nk)
+    d2 = ((X - p[:, None, None, None]) ** 2).sum(axis=0)
+    k, j, i = np.unravel_index(np.argmin(d2), d2.shape)
+    c = np.array([i, j, k], dtype=np.float64)
+    small = 0
+    for _ in range(100):
+        b0 = [_start(c[a], n[a]) for a in range(3)]
+        L = [lagrange4(c[a] - b0[a]) for a in range(3)]
+        cube = X[:, b0[2]:b0[2] + 4, b0[1]:b0[1] + 4, b0[0]:b0[0] + 4]   # (3, 4k, 4j, 4i)
+        val = np.einsum("xkji,i,j,k->x", cube, L[0][0], L[1][0], L[2][0])
+        jac = np.stack([np.einsum("xkji,i,j,k->x", cube, L[0][0 if a != 0 else 1], L[1][0 if a != 1 else 1],
+                                  L[2][0 if a != 2 else 1]) for a in range(3)], axis=1)
+        try:
+            step = np.linalg.solve(jac, val - p)
+        except np.linalg.LinAlgError:
+            return None
+        c = c - step
+        if not np.all(np.abs(c) < 1e7):
+            return None
+        small = small + 1 if np.all(np.abs(step) < 1e-10) else 0
+        if small == 3:
+            break
+    if small < 3 or any(c[a] < -1e-9 or c[a] > n[a] - 1 + 1e-9 for a in range(3)):
+        return None
+    return c
+
+
+def hole_cut(x, y, z, points, margin):
+    """Hole cut against a curvilinear mesh (Sec. 2.2; reading, as for the Cartesian 3D hole cut
+    with the overlapping mesh's index units): a point is a hole when it lies inside the mesh at
+    index coordinates more than `margin` from each of the mesh's faces. Returns a bool array."""
+    X = np.stack([np.asarray(v, dtype=np.float64) for v in (x, y, z)])
+    nk, nj, ni = X.shape[1:]
+    n = (ni, nj, nk)
+    out = []
+    for p in np.asarray(points, dtype=np.float64).reshape(-1, 3):
+        c = _invert(X, p)
+        out.append(c is not None and all(margin < c[a] < n[a] - 1 - margin for a in range(3)))
+    return np.array(out, bool)
+
+
 def donors(x, y, z, points, iblank=None):
     """Donor stencils on a curvilinear mesh (coordinates (nk, nj, ni)) for points (npts, 3):
     base (npts, 3) ints (i0, j0, k0), weights (npts, 12) (4 along i, 4 along j, 4 along k) and
@@ -223,26 +268,8 @@ def donors(x, y, z, points, iblank=None):
     w = np.zeros((len(P), 12))
     xi = np.zeros((len(P), 3))
     for t, p in enumerate(P):
-        d2 = ((X - p[:, None, None, None]) ** 2).sum(axis=0)
-        k, j, i = np.unravel_index(np.argmin(d2), d2.shape)
-        c = np.array([i, j, k], dtype=np.float64)
-        small = 0
-        for _ in range(100):
-            b0 = [_start(c[a], n[a]) for a in range(3)]
-            L = [lagrange4(c[a] - b0[a]) for a in range(3)]
-            cube = X[:, b0[2]:b0[2] + 4, b0[1]:b0[1] + 4, b0[0]:b0[0] + 4]   # (3, 4k, 4j, 4i)
-            val = np.einsum("xkji,i,j,k->x", cube, L[0][0], L[1][0], L[2][0])
-            jac = np.stack([np.einsum("xkji,i,j,k->x", cube, L[0][0 if a != 0 else 1], L[1][0 if a != 1 else 1],
-                                      L[2][0 if a != 2 else 1]) for a in range(3)], axis=1)
-            try:
-                step = np.linalg.solve(jac, val - p)
-            except np.linalg.LinAlgError:
-                break
-            c = c - step
-            small = small + 1 if np.all(np.abs(step) < 1e-10) else 0
-            if small == 3:
-                break
-        if small < 3 or any(c[a] < -1e-9 or c[a] > n[a] - 1 + 1e-9 for a in range(3)):
+        c = _invert(X, p)
+        if c is None:
             raise DonorError(t)
         b0 = [_start(c[a], n[a]) for a in range(3)]
         if not act[b0[2]:b0[2] + 4, b0[1]:b0[1] + 4, b0[0]:b0[0] + 4].all():

@@ -148,6 +148,7 @@ _SIGS.update({
     "sbp3c_set_farfield": [_P, _P, ctypes.c_double],
     "sbp3c_donor_search": [_P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P],
     "sbp3c_interp": [_P, _P, _I, _P, _P, _P, _P],
+    "sbp3c_hole_cut": [_P, _P, _P, _P, _I, _P, ctypes.c_double, _P],
     "sbp3c_set_interface": [_P, _I, _P, _P, _I, ctypes.c_double],
     "sbp3c_interface_sat": [_P, _P, _P, _P, _P, _P],
 })
@@ -895,6 +896,19 @@ def donor_search_3d(x, y, z, points, iblank=None):
                                    P.ctypes.data, base.ctypes.data, w.ctypes.data, xi.ctypes.data,
                                    ctypes.byref(failed)), "sbp3c_donor_search")
     return base, w, xi
+
+
+def hole_cut_3d(x, y, z, points, margin):
+    """Points (npts, 3) that are holes of the curvilinear mesh x, y, z (host, no device calls;
+    C ABI sbp3c_hole_cut): a bool array."""
+    X = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z)]
+    nk, nj, ni = X[0].shape
+    n = (ctypes.c_int * 3)(ni, nj, nk)
+    P = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    ib = np.ones(len(P), np.int8)
+    _check(_lib.sbp3c_hole_cut(ctypes.cast(n, ctypes.c_void_p), X[0].ctypes.data, X[1].ctypes.data, X[2].ctypes.data,
+                               len(P), P.ctypes.data, float(margin), ib.ctypes.data), "sbp3c_hole_cut")
+    return ib == 0
 
 
 def exported_symbols():

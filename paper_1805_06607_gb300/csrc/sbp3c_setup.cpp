@@ -2,7 +2,9 @@
 // Lagrange shape functions): for each point, computational coordinates (s, r, t) with
 // X(s, r, t) = p, X the mesh map interpolated by the 4 x 4 x 4 Lagrange basis on the stencil
 // starting at floor(.) - 1 clamped into the mesh, by Newton's method from a nearby node; the
-// weights are that basis at the solution. Host only: no device calls.
+// weights are that basis at the solution. Hole cut (reading, as for the Cartesian 3D hole cut
+// with the overlapping mesh's index units): a point inside the mesh more than a margin of index
+// units from each of its faces is a hole. Host only: no device calls.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -165,6 +167,31 @@ extern "C" sbp_status sbp3c_donor_search(const int *n, const double *x, const do
       for (int d = 0; d < 4; ++d) w[12 * (size_t)t + 4 * a + d] = l[d];
       if (xi) xi[3 * (size_t)t + a] = s[a];
     }
+  }
+  return SBP_OK;
+}
+
+extern "C" sbp_status sbp3c_hole_cut(const int *n, const double *x, const double *y, const double *z, int npts,
+                                     const double *pts, double margin, signed char *iblank) {
+  if (!n || !x || !y || !z || npts < 0 || (npts > 0 && (!pts || !iblank)) || !(margin >= 0.0))
+    return sbp::fail(SBP_ERR_ARG, "bad argument");
+  for (int a = 0; a < 3; ++a)
+    if (n[a] < 8 || n[a] > 65535) return sbp::fail(SBP_ERR_SHAPE, "each direction needs 8..65535 points");
+  const Grid3 g{{n[0], n[1], n[2]}, {x, y, z}};
+  const int stride = std::max(1, std::min({n[0], n[1], n[2]}) / 8);
+  for (int t = 0; t < npts; ++t) {
+    const double *q = pts + 3 * (size_t)t;
+    int c[3];
+    near_node(g, q, stride, c);
+    double s[3] = {(double)c[0], (double)c[1], (double)c[2]};
+    bool ok = newton(g, q, s);
+    if (!ok && stride > 1) {
+      near_node(g, q, 1, c);
+      for (int a = 0; a < 3; ++a) s[a] = c[a];
+      ok = newton(g, q, s);
+    }
+    for (int a = 0; ok && a < 3; ++a) ok = s[a] > margin && s[a] < n[a] - 1 - margin;
+    if (ok) iblank[t] = 0;
   }
   return SBP_OK;
 }

@@ -72,3 +72,17 @@ def test_donor_search_failures_match_oracle(sbp):
         donors(x, y, z, pts, iblank=ib)
     with pytest.raises(sbp.SbpError, match="point %d " % e.value.args[0]):
         sbp.donor_search_3d(x, y, z, pts, iblank=ib)
+
+
+def test_hole_cut_matches_oracle(sbp):
+    """sbp3c_hole_cut against oracle.curv3d.hole_cut: the nodes of a background box around a
+    warped mesh, margin 2 index units."""
+    from oracle.curv3d import hole_cut
+    x, y, z = _mesh(20, 17, 14)
+    t = [np.linspace(-0.2, 1.3, 16), np.linspace(-0.2, 1.1, 13), np.linspace(-0.2, 1.5, 17)]
+    Zb, Yb, Xb = np.meshgrid(t[2], t[1], t[0], indexing="ij")
+    pts = np.stack([Xb.ravel(), Yb.ravel(), Zb.ravel()], axis=1)
+    want = hole_cut(x, y, z, pts, 2.0)
+    got = sbp.hole_cut_3d(x, y, z, pts, 2.0)
+    assert want.sum() > 100 and (~want).sum() > 1000
+    assert np.array_equal(got, want)

@@ -89,3 +89,21 @@ def test_outside_points_and_inactive_stencils_refused():
     ib[:] = 1
     ib[0, 0, 0] = 0    # outside its stencil
     donors(*X, inside, iblank=ib)
+
+
+def test_hole_cut_on_affine_mesh_is_the_index_box():
+    """Hole cut against a mesh affine in its index coordinates: a point is a hole exactly when the
+    inverse map's closed form puts it more than `margin` index units inside every face."""
+    from oracle.curv3d import hole_cut
+    K, J, I = _index_grid()
+    A = np.array([[0.1, 0.02, -0.01], [0.015, 0.09, 0.02], [-0.02, 0.01, 0.11]])
+    b = np.array([0.3, -0.2, 1.0])
+    X = np.einsum("ab,bkji->akji", A, np.stack([I, J, K])) + b[:, None, None, None]
+    rng = np.random.default_rng(9)
+    xs = rng.uniform([-2, -2, -2], [NI + 1, NJ + 1, NK + 1], (300, 3))
+    pts = xs @ A.T + b
+    margin = 2.5
+    want = np.all((xs > margin) & (xs < np.array([NI, NJ, NK]) - 1 - margin), axis=1)
+    got = hole_cut(*X, pts, margin)
+    assert want.sum() >= 10 and (~want).sum() > 100
+    assert np.array_equal(got, want)
