@@ -491,7 +491,8 @@ sbp_status sbp_f32_to_f64(const void *x, void *y, size_t n, void *stream);
  * The flux divergence of the 3D compressible Euler / Navier-Stokes equations (App. C.1) on one
  * curvilinear structured mesh of n[0] x n[1] x n[2] points (i fastest), non-periodic in every
  * direction, with the SBP 4-2 derivative (Sec. 2.1) and its closures at both ends of every line;
- * no interpolation, and SAT penalties only for the optional far field (sbp3c_set_farfield):
+ * plus the optional far-field SAT (sbp3c_set_farfield) and, for overset coupling, the host hole
+ * cut and donor search, the device gather and the interface SAT at given receivers:
  *   dq/dt = -J sum_m D_m (sum_j M[m][j] (F_j - F^V_j)),   M[m][j] = xi_m,x_j / J,
  * with the metric terms in the symmetric conservative form of Thomas and Lombard (the paper defers
  * the metrics to other work), M[m][j] = D_b((X_c)_a X_e) - D_a((X_c)_b X_e) over cyclic (m, a, b)

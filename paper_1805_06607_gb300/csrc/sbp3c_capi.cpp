@@ -1,7 +1,8 @@
 // C ABI of the 3D curvilinear operator: a mesh object holding the device metric terms, and the
 // flux divergence of a state (App. C.1's equations in curvilinear coordinates, Sec. 2.1's SBP
 // 4-2 derivative with closures on every line; optionally the far-field SAT of Sec. 5.1 on every
-// face). Kernels: sbp3c_kernels.cu.
+// face), the interface SAT at given receivers and the overset gather. Kernels: sbp3c_kernels.cu;
+// host donor search and hole cut: sbp3c_setup.cpp.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,5 +1,6 @@
 // 3D curvilinear operator (App. C.1's equations in curvilinear coordinates with Sec. 2.1's SBP
-// 4-2 derivative): one structured mesh with closures at both ends of every line, no SAT terms.
+// 4-2 derivative): one structured mesh with closures at both ends of every line; far-field and
+// interface SAT terms and the overset gather as separate kernels.
 //   k3c_dx       coordinate derivatives D_a X_c (9 planes, FP64)
 //   k3c_metrics  metric terms M[m][j] = xi_m,x_j / J in the symmetric conservative form of
 //                Thomas and Lombard, M[m][j] = D_b((X_c)_a X_e) - D_a((X_c)_b X_e) over cyclic
