@@ -846,7 +846,11 @@ class Curvilinear3DMesh:
         """Overset gather of q (5, nk, nj, ni) at stencils (base (n, 3) ints, w (n, 12)), as
         donor_search_3d returns them: a (5, n) device tensor."""
         torch = self.torch
-        b = torch.as_tensor(np.ascontiguousarray(base, dtype=np.int32)).cuda()
+        bh = np.ascontiguousarray(base, dtype=np.int32).reshape(-1, 3)
+        nk, nj, ni = self.shape
+        if len(bh) and ((bh.min(axis=0) < 0).any() or (bh.max(axis=0) > np.array([ni, nj, nk]) - 4).any()):
+            raise ValueError("donor stencil outside the mesh")
+        b = torch.as_tensor(bh).cuda()
         wt = torch.as_tensor(np.ascontiguousarray(w, dtype=np.float64)).cuda()
         n = int(b.shape[0])
         if b.shape != (n, 3) or wt.shape != (n, 12):
