@@ -58,6 +58,30 @@ def _args():
     return ap.parse_args()
 
 
+def _fp64_peak(iters=4000, reps=5):
+    """FP64 rate of this GPU, measured: the library's FMA probe (8 independent chains per
+    thread, 8 CTAs of 256 threads per SM), best of reps launches timed with CUDA events."""
+    import torch
+    import paper_1805_06607_gb300 as sbp
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    grid, block = 8 * sms, 256
+    out = torch.empty(grid * block, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sbp.fp64_rate_probe(out, grid, block, 100)
+    best, flops = float("inf"), 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = sbp.fp64_rate_probe(out, grid, block, iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return {"tflops": flops / best / 1e12, "ms": best * 1e3, "grid": grid, "block": block,
+            "how": "sbp_fp64_rate_probe: %d FP64 FMAs per thread in 8 independent chains, %d x %d threads, "
+                   "best of %d launches (CUDA events)" % (8 * iters, grid, block, reps)}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -211,6 +235,9 @@ def _run_gpu(wl, dtype, steps, warmup, world, local, sample_clocks=True):
             sampler.wait_first()
         _barrier(world)
         torch.cuda.synchronize()
+        if sample_clocks:
+            # an ncu run with --profile-from-start off captures the timed steps only
+            torch.cuda.profiler.start()
         t0 = time.perf_counter()
         for k in range(steps):
             flush.zero_()                       # evict the working set (< L2) between steps
@@ -219,6 +246,8 @@ def _run_gpu(wl, dtype, steps, warmup, world, local, sample_clocks=True):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
+        if sample_clocks:
+            torch.cuda.profiler.stop()
         if sample_clocks:
             # the same steps, untimed, for a few more clock samples under this load
             while time.perf_counter() - t1 < 0.4:
@@ -341,7 +370,7 @@ MEASURED_TRAFFIC = {
 }
 
 
-def _roofline(res, wl, dtype, hbm_peak, peak_kind):
+def _roofline(res, wl, dtype, hbm_peak, peak_kind, fp64=None):
     """Dominant kernel of the step (largest device time) against its bound."""
     evals, n_bg, n_og = _evals_per_step(wl)
     prof = res["prof"]
@@ -361,8 +390,11 @@ def _roofline(res, wl, dtype, hbm_peak, peak_kind):
     roof = {"kernel": phase, "launches": n, "avg_launch_ms": avg_s * 1e3}
     if dtype == "f64" and phase.startswith("rhs"):
         flops = FLOP_PER_POINT_NS * pts
-        roof.update({"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "peak_kind": "nominal FP64 (derived: 152 SMs x 2 DFMA/clk x 2 x 2.06 GHz)",
+        peak = fp64["tflops"] if fp64 else FP64_PEAK_TFLOPS
+        kind = ("measured FP64 FMA rate of this GPU (%s)" % fp64["how"]) if fp64 else \
+            "nominal FP64 (derived: 152 SMs x 2 DFMA/clk x 2 x 2.06 GHz)"
+        roof.update({"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak,
+                     "unit": "TFLOP/s", "peak_kind": kind,
                      "hbm_achieved_gbs": bpp * pts / avg_s / 1e9, "bytes_per_point": bpp,
                      "flop_per_point": FLOP_PER_POINT_NS})
         roof["frac"] = roof["achieved"] / roof["peak"]
@@ -1007,6 +1039,7 @@ def main():
     wl = W.cylinder_overset(seed=rank)
     evals, n_bg, n_og = _evals_per_step(wl)
     hbm_peak, peak_kind = _peaks()
+    fp64 = _fp64_peak()
     res = _run_gpu(wl, args.dtype, args.steps, args.warmup, world, local)
     step_ms = _max_over_ranks(world, res["step_ms"])
     e2e_ms = _max_over_ranks(world, res["e2e_ms"])
@@ -1027,7 +1060,8 @@ def main():
                        "steps' compute",
                 "serial_value": _job_rate(world, evals, _max_over_ranks(world, res["e2e_serial_ms"]))},
         "gpu_launches": res["launches_per_step"] * args.steps,
-        "roofline": _roofline(res, wl, args.dtype, hbm_peak, peak_kind),
+        "roofline": _roofline(res, wl, args.dtype, hbm_peak, peak_kind, fp64),
+        "fp64_peak": fp64,
         "phases_ms_per_step": {p: v[0] / args.steps for p, v in res["prof"].items()},
         "phases_note": "kernel-by-kernel launches with CUDA events (the timed step replays a CUDA graph)",
         "wall_s_timed_region": res["wall_s"],
@@ -1038,7 +1072,7 @@ def main():
         r2 = _run_gpu(wl, other, args.steps, args.warmup, world, local, sample_clocks=False)
         ms2 = _max_over_ranks(world, r2["step_ms"])
         line["variants"] = {other: {"value": _job_rate(world, evals, ms2), "ms_per_step": ms2,
-                                    "roofline": _roofline(r2, wl, other, hbm_peak, peak_kind),
+                                    "roofline": _roofline(r2, wl, other, hbm_peak, peak_kind, fp64),
                                     "autotuned_blocks": r2["tuning"],
                                     "phases_ms_per_step": {p: v[0] / args.steps for p, v in r2["prof"].items()}}}
     if not args.no_stability and rank == 0:

@@ -487,6 +487,13 @@ sbp_status sbp3_set_rhs_kernel(sbp3_system_t sys, int mesh, int kchunk);
  * update and the slow-state extrapolation): exact, equal bit for bit to the hardware
  * conversion for every input, without issuing to the FP64 pipe. */
 sbp_status sbp_f32_to_f64(const void *x, void *y, size_t n, void *stream);
+/* Measurement utility (the paper has no counterpart: it is the denominator of the FP64 roofline
+ * that the benchmark reports). Launches one kernel of grid x block threads on stream in which
+ * every thread runs 8 independent chains of iters FP64 fused multiply-adds and writes one double
+ * to out (device, grid * block doubles, caller-owned); *flops (host, may be NULL) receives the
+ * FP64 operations it performs (2 per FMA). Time it with events on the same stream. SBP_ERR_ARG
+ * for a null out, non-positive sizes or a block that is not a multiple of 32 up to 1024. */
+sbp_status sbp_fp64_rate_probe(void *out, int grid, int block, long iters, double *flops, void *stream);
 /* ---- 3D curvilinear operator -------------------------------------------------------------------
  * The flux divergence of the 3D compressible Euler / Navier-Stokes equations (App. C.1) on one
  * curvilinear structured mesh of n[0] x n[1] x n[2] points (i fastest), non-periodic in every

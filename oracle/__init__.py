@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
         return _SO
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
     tmp = _SO + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                            *_SRC, "-o", tmp, "-lm"])
     os.replace(tmp, _SO)
     return _SO
@@ -47,6 +47,8 @@ def lib():
     I = ctypes.c_int
     D = ctypes.c_double
     Lg = ctypes.c_long
+    L.orc_set_threads.argtypes = [I]
+    L.orc_set_threads.restype = I
     L.orc_classes2d.argtypes = [I, I, I, I, P, P, P]
     L.orc_classes2d.restype = I
     L.orc_metrics2d.argtypes = [I, I, P, P, P, P, P, P]

@@ -21,6 +21,11 @@
  * Points where the paper is silent follow the readings listed in the design
  * notes; each is repeated next to the code that takes it.
  *
+ * The per-point loops run under OpenMP (orc_set_threads picks the thread
+ * count): every point's arithmetic is independent of the others and of the
+ * thread count, so the results are the same bits for any number of threads.
+ * Accumulations into one point (the SAT terms) stay sequential.
+ *
  * Array layout: every field is (nvar, nj, ni) with i fastest; a point index
  * is p = j*ni + i.
  */
@@ -29,6 +34,21 @@
 #include <string.h>
 
 #include "orc_sbp.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the per-point loops (n <= 0: the OpenMP default); returns the count in use. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* iblank: in/out active mask (1 active, 0 hole).  ci/cj: class along i and along j.
  * Returns the number of hole-growing passes, or -1 if a whole line became inactive
@@ -112,6 +132,7 @@ int orc_viscflux2d(int ni, int nj, int per_i, int per_j, const signed char *ci, 
   long N = (long)ni * nj;
   double *prim = (double *)malloc(sizeof(double) * 3 * N); /* u, v, T */
   if (!prim) return -1;
+#pragma omp parallel for schedule(static)
   for (long p = 0; p < N; ++p) {
     double rho = q[p], u = q[N + p] / rho, v = q[2 * N + p] / rho;
     double pr_ = (gamma - 1.0) * (q[3 * N + p] - 0.5 * rho * (u * u + v * v));
@@ -120,6 +141,7 @@ int orc_viscflux2d(int ni, int nj, int per_i, int per_j, const signed char *ci, 
   (void)per_i;
   double lam = -2.0 / 3.0 * mu;
   double kap = mu / (pr * (gamma - 1.0));
+#pragma omp parallel for schedule(static)
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i < ni; ++i) {
       long p = (long)j * ni + i;
@@ -227,6 +249,7 @@ int orc_rhs2d(int ni, int nj, int per_i, int per_j, const signed char *ci, const
   if (!fl || (viscous && !fv)) { free(fl); free(fv); return -1; }
   if (viscous) orc_viscflux2d(ni, nj, per_i, per_j, ci, cj, met, q, gamma, mu, pr, fv);
 
+#pragma omp parallel for schedule(static)
   for (long p = 0; p < N; ++p) {
     double qp[4] = {q[p], q[N + p], q[2 * N + p], q[3 * N + p]};
     double F[4], G[4];
@@ -241,6 +264,7 @@ int orc_rhs2d(int ni, int nj, int per_i, int per_j, const signed char *ci, const
       fl[(4 + v) * N + p] = met[2 * N + p] * (F[v] - Fv[v]) + met[3 * N + p] * (G[v] - Gv[v]);
     }
   }
+#pragma omp parallel for schedule(static)
   for (int j = 0; j < nj; ++j)
     for (int i = 0; i < ni; ++i) {
       long p = (long)j * ni + i;
@@ -305,6 +329,7 @@ int orc_rhs2d(int ni, int nj, int per_i, int per_j, const signed char *ci, const
 int orc_interp2d(int ni, int nj, int nf, const double *field, int nrecv, const int *base,
                  const double *w, double *out) {
   long N = (long)ni * nj;
+#pragma omp parallel for schedule(static)
   for (int r = 0; r < nrecv; ++r) {
     for (int f = 0; f < nf; ++f) {
       double acc = 0.0;

@@ -134,6 +134,7 @@ _SIGS.update({
     "sbp3_check": [_P, _P],
     "sbp3_set_rhs_kernel": [_P, _I, _I],
     "sbp_f32_to_f64": [_P, _P, ctypes.c_size_t, _P],
+    "sbp_fp64_rate_probe": [_P, _I, _I, ctypes.c_long, ctypes.POINTER(_D), _P],
     "sbp_host_tables_create": [ctypes.POINTER(MeshDesc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "sbp_host_tables_destroy": [_P],
     "sbp_host_tables_get": [_P, _I, _P, _P, _P, _P, _P],
@@ -783,6 +784,19 @@ def f32_to_f64(x, stream=None):
     y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
     _check(_lib.sbp_f32_to_f64(_ptr(x), _ptr(y), x.numel(), _stream(stream)), "sbp_f32_to_f64")
     return y
+
+
+def fp64_rate_probe(out, grid, block, iters, stream=None):
+    """Launch the FP64 fused multiply-add probe (grid x block threads, 8 chains of iters FMAs
+    each) on stream; out is a float64 CUDA tensor of at least grid * block elements. Returns the
+    FP64 operations the launch performs."""
+    import torch
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < grid * block:
+        raise ValueError("a float64 CUDA tensor of grid * block elements is required")
+    flops = ctypes.c_double(0.0)
+    _check(_lib.sbp_fp64_rate_probe(_ptr(out), int(grid), int(block), int(iters), ctypes.byref(flops),
+                                    _stream(stream)), "sbp_fp64_rate_probe")
+    return flops.value
 
 
 class Curvilinear3DMesh:
