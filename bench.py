@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -411,7 +412,7 @@ def _roofline(res, wl, dtype, hbm_peak, peak_kind, fp64=None):
     return roof
 
 
-def _run_batch(dtype, steps, warmup, seed=0):
+def _run_batch(dtype, steps, warmup, hbm_peak, peak_kind, seed=0):
     """64 independent 2D Euler vortex systems (backgrounds 128^2..512^2, fine patches at ratio
     2, 4 or 8 = their MRAB step ratio), one cooperative persistent launch per micro step."""
     import torch
@@ -448,8 +449,19 @@ def _run_batch(dtype, steps, warmup, seed=0):
     b.close()
     for g in members:
         g.close()
+    esz = 8 if dtype == "f64" else 4
+    m = wls[0]["params"]["hist_len"]
+    # per point evaluation of the fused right-hand side + MRAB update (Euler, Cartesian): state in
+    # and out, new history slot out, m - 1 older slots in (4 variables each), the class byte
+    bpp = 4 * esz * (3 + (m - 1)) + 1
+    achieved = evals * bpp / (ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "peak_kind": peak_kind, "bytes_per_point": bpp, "traffic": None,
+            "note": "whole macro step of all members (donor values, SAT and right-hand sides with the MRAB "
+                    "update in each cooperative launch), algorithmic bytes of the fused update per point "
+                    "evaluation"}
     return {"value": evals / (ms / 1e3), "unit": "point-evals/s", "ms_per_step": ms, "dtype": dtype,
-            "systems": len(wls), "points": points, "evals_per_step": evals,
+            "roofline": roof, "systems": len(wls), "points": points, "evals_per_step": evals,
             "step": "one macro step of every member = max(step ratio) cooperative launches (CUDA graph)",
             "l2": "working set (%.1f GB) larger than L2" % (points * 4 * (8 if dtype == "f64" else 4) * 5 / 1e9),
             "rows_per_cta": info["rows_per_cta"], "grid": info["grid"], "setup_s": setup_s}
@@ -576,7 +588,7 @@ def _mrab_variants(name, wl, k_slow, ref_factor=10):
 
 
 def _rhs_eval_large(hbm_peak, peak_kind, reps=10):
-    """sbp_rhs_eval alone on meshes larger than L2 (SURVEY's K2 on enlarged workloads): the
+    """sbp_rhs_eval alone on meshes larger than L2 (the right-hand-side kernels alone, on enlarged workloads): the
     cylinder at 4x resolution (Navier-Stokes; O-grid 2048 x 512, background 4096 x 2048) and
     the vortex pair at 32x resolution (Euler; background 2048^2, patch 821^2), FP32 and FP64,
     kernel shape from the autotuner. Algorithmic bytes per point: state in + right-hand side out
@@ -964,11 +976,31 @@ def _run_perf_model(ratios=(1, 2, 3, 4), order=3, hist_len=4, rel_tol=3e-3, t_rk
             "wall_s": time.perf_counter() - t0}
 
 
-def _cpu_baseline(wl, seconds):
-    """The oracle, as it stands, on the host: whole MRAB macro steps of the same workload."""
+def _cpu_model():
+    """The host CPU's name as the kernel reports it (x86 'model name', Arm implementer / part)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return platform.processor() or "unknown"
+    for key in ("model name", "Model Name", "Hardware"):
+        for line in info.splitlines():
+            if line.split(":")[0].strip() == key:
+                return line.split(":", 1)[1].strip()
+    parts = {line.split(":")[0].strip(): line.split(":", 1)[1].strip()
+             for line in info.splitlines() if ":" in line}
+    if "CPU implementer" in parts:
+        return "Arm implementer %s part %s" % (parts["CPU implementer"], parts.get("CPU part", "?"))
+    return platform.processor() or "unknown"
+
+
+def _oracle_macro_steps(wl, seconds, threads):
+    """Whole oracle MRAB macro steps of the workload for about `seconds`, the oracle's per-point
+    loops on `threads` OpenMP threads (the assembly and the updates are numpy on one thread)."""
     import numpy as np
+    import oracle
     from oracle import OracleSystem
 
+    used = oracle.lib().orc_set_threads(threads)
     ref = OracleSystem(wl)
     q = wl["q0"]
     H = ref.macro_step_size(q)
@@ -978,27 +1010,41 @@ def _cpu_baseline(wl, seconds):
     hs = [a[ref.slow]] * m
     evals, _, _ = _evals_per_step(wl)
     n = 0
-    t0 = time.perf_counter()
     y = [np.array(v) for v in q]
+    t0 = time.perf_counter()
     while True:
         y, hf, hs = ref.mrab(y, hf, hs, H, 1)
         n += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": n * evals / el, "unit": "point-evals/s", "cores": 1, "kind": "oracle",
-            "sample": "%d MRAB macro steps of the full workload (histories seeded with the initial "
-                      "right-hand side), %.1f s, single-threaded C + numpy" % (n, el)}
+    return n * evals / el, n, el, used
+
+
+def _cpu_baseline(wl, seconds):
+    """The oracle, as it stands, on the host: whole MRAB macro steps of the same workload, on one
+    thread and on all cores (OpenMP over the points of its per-point loops)."""
+    cores = os.cpu_count() or 1
+    v1, n1, e1, _ = _oracle_macro_steps(wl, 0.3 * seconds, 1)
+    va, na, ea, used = _oracle_macro_steps(wl, 0.7 * seconds, cores)
+    return {"value": va, "unit": "point-evals/s", "cores": used, "kind": "oracle",
+            "sample": "%d MRAB macro steps of the full workload (histories seeded with the initial right-hand "
+                      "side), %.1f s, C per-point loops on %d OpenMP threads + numpy" % (na, ea, used),
+            "single_thread": {"value": v1, "sample": "%d macro steps, %.1f s, 1 thread" % (n1, e1)},
+            "os_cpu_count": cores, "cpu_model": _cpu_model()}
 
 
 def _reference(args):
-    world, rank, _ = (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    world, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import numpy as np
+    import oracle
     import workloads as W
     from oracle import OracleSystem
 
+    cores = os.cpu_count() or 1
+    used = oracle.lib().orc_set_threads(cores)
     wl = W.cylinder_overset(seed=0)
     evals, _, _ = _evals_per_step(wl)
     ref = OracleSystem(wl)
@@ -1021,9 +1067,11 @@ def _reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "points": sum(mm["n"][0] * mm["n"][1] for mm in wl["meshes"]),
                        "evals_per_step": evals},
-            "cpu_baseline": {"value": v, "unit": "point-evals/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d timed MRAB macro steps of the full workload after %d warm-up steps"
-                                       % (args.steps, args.warmup)},
+            "cpu_baseline": {"value": v, "unit": "point-evals/s", "cores": used, "kind": "oracle",
+                             "sample": "%d timed MRAB macro steps of the full workload after %d warm-up steps, "
+                                       "C per-point loops on %d OpenMP threads + numpy"
+                                       % (args.steps, args.warmup, used),
+                             "os_cpu_count": cores, "cpu_model": _cpu_model()},
             "e2e": {"value": v, "unit": "point-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -1099,7 +1147,8 @@ def main():
         }
         line["mrab_orderings"] = _mrab_variants(WORKLOAD, W2.cylinder_overset(seed=0), 20)
     if not args.no_batch:
-        line["batched"] = {dt: _run_batch(dt, args.steps, args.warmup, seed=rank) for dt in ("f64", "f32")}
+        line["batched"] = {dt: _run_batch(dt, args.steps, args.warmup, hbm_peak, peak_kind, seed=rank)
+                           for dt in ("f64", "f32")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:

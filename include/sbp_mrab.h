@@ -178,9 +178,10 @@ sbp_status sbp_rhs_eval(sbp_system_t sys, int mesh, const void *q_self, const vo
                         void *stream);
 
 /* sbp_rhs_eval for callers that cannot have device memory allocated for them while they run:
- * code that evaluates the right-hand side inside a CUDA stream capture in global mode (where
- * cudaMalloc is illegal), or in a process whose device memory is all reserved up front by
- * another allocator. The paper has no counterpart; the result equals sbp_rhs_eval's. The
+ * a process whose device memory is all reserved up front by another allocator (a framework's
+ * caching pool), or a latency-critical loop in which the device-wide synchronisation that
+ * cudaMalloc and cudaFree imply is not acceptable. The paper has no counterpart; the result
+ * equals sbp_rhs_eval's. The
  * receiver workspace (interpolated states and viscous fluxes) lives in one fixed device array
  * of SBP_NOALLOC_MAX_RECEIVERS * 10 doubles (640 KiB) that the library defines and that every
  * GPU loading the library keeps until the process exits; the call allocates and frees nothing.
@@ -528,8 +529,10 @@ sbp_status sbp3c_set_farfield(sbp3c_mesh_t mesh, const double *qinf, double sigm
  * pts[3 t .. 3 t + 2] = (x, y, z): computational coordinates (s, r, t) (index units) with
  * X(s, r, t) = p, X the mesh map interpolated by the 4 x 4 x 4 Lagrange basis on the stencil
  * that starts at floor(.) - 1 clamped into the mesh, found by Newton's method from a nearby
- * node (the nearest of a coarse subset of nodes, refined locally; the nearest of all nodes if
- * that start fails) until three consecutive steps stay below 1e-10. Outputs (host, caller
+ * node (the nearest of a coarse subset of nodes, refined locally by halving the stride; the
+ * nearest of all nodes if that start fails) until three consecutive steps stay below 1e-10.
+ * Points outside the nodes' bounding box padded by the longest edge between neighbouring nodes
+ * are outside the mesh without a search. Outputs (host, caller
  * owned): base 3 ints per point (i0, j0, k0), w 12 doubles per point (the 4 basis values along
  * i, then j, then k: the value at the point is sum wi[a] wj[b] wk[c] f(i0 + a, j0 + b, k0 + c)),
  * xi 3 doubles per point (NULL to skip). n, x, y, z as for sbp3c_mesh_create; iblank

@@ -18,8 +18,8 @@
  *   - hole cutting and donor search (Sec. 2.2);
  *   - the inviscid/viscous time-step estimate of Sec. 4.1 eqs. (ts_inv),
  *     (ts_visc), (ts_overall).
- * Points where the paper is silent follow the readings listed in the design
- * notes; each is repeated next to the code that takes it.
+ * Where the paper is silent, the reading taken is stated next to the code
+ * that takes it.
  *
  * The per-point loops run under OpenMP (orc_set_threads picks the thread
  * count): every point's arithmetic is independent of the others and of the

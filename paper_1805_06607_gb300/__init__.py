@@ -808,6 +808,8 @@ class Curvilinear3DMesh:
         import torch
         self.torch = torch
         self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        self.viscous = params["physics"] == "ns"
+        self.nrecv = None
         X = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z)]
         self.shape = X[0].shape
         nk, nj, ni = self.shape
@@ -823,6 +825,18 @@ class Curvilinear3DMesh:
         _check(_lib.sbp3c_mesh_create(ctypes.cast(n, ctypes.c_void_p), X[0].ctypes.data, X[1].ctypes.data,
                                       X[2].ctypes.data, ctypes.byref(pr), ctypes.byref(h)), "sbp3c_mesh_create")
         self.h = h
+
+    def _field(self, t, name, shape):
+        """t as a contiguous device tensor of the mesh's element type and the given shape; the
+        kernels index it by the mesh's sizes, so anything else is refused before the call."""
+        torch = self.torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.dtype != self.tdtype:
+            raise ValueError("%s must be %s, got %s" % (name, self.tdtype, t.dtype))
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+        return t.contiguous()
 
     def metrics(self):
         out = np.zeros((10,) + self.shape)
@@ -846,12 +860,24 @@ class Curvilinear3DMesh:
         _check(_lib.sbp3c_set_interface(self.h, len(t), t.ctypes.data if len(t) else None,
                                         sc.ctypes.data if len(t) else None, int(nrecv), float(sigma)),
                "sbp3c_set_interface")
+        self.nrecv = int(nrecv)
 
     def interface_sat(self, q, qhat, rhs, fvhat=None, stream=None):
-        """rhs += the interface SAT terms at state q (device tensors; qhat (5, nrecv), fvhat
-        (12, nrecv) for Navier-Stokes)."""
-        q, qhat = q.contiguous(), qhat.contiguous()
-        fv = None if fvhat is None else fvhat.contiguous()
+        """rhs += the interface SAT terms at state q (device tensors of the mesh's element type:
+        q and rhs (5, nk, nj, ni), qhat (5, nrecv), fvhat (12, nrecv) for Navier-Stokes, with
+        nrecv as given to set_interface)."""
+        if self.nrecv is None:
+            raise ValueError("set_interface first")
+        q = self._field(q, "q", (5,) + self.shape)
+        if not rhs.is_contiguous():
+            raise ValueError("rhs must be contiguous")
+        self._field(rhs, "rhs", (5,) + self.shape)
+        qhat = self._field(qhat, "qhat", (5, self.nrecv))
+        fv = None
+        if self.viscous:
+            if fvhat is None:
+                raise ValueError("fvhat (12, nrecv) is required for Navier-Stokes")
+            fv = self._field(fvhat, "fvhat", (12, self.nrecv))
         _check(_lib.sbp3c_interface_sat(self.h, _ptr(q), _ptr(qhat), None if fv is None else _ptr(fv), _ptr(rhs),
                                         _stream(stream)), "sbp3c_interface_sat")
         return rhs
@@ -860,6 +886,7 @@ class Curvilinear3DMesh:
         """Overset gather of q (5, nk, nj, ni) at stencils (base (n, 3) ints, w (n, 12)), as
         donor_search_3d returns them: a (5, n) device tensor."""
         torch = self.torch
+        q = self._field(q, "q", (5,) + self.shape)
         bh = np.ascontiguousarray(base, dtype=np.int32).reshape(-1, 3)
         nk, nj, ni = self.shape
         if len(bh) and ((bh.min(axis=0) < 0).any() or (bh.max(axis=0) > np.array([ni, nj, nk]) - 4).any()):
@@ -869,16 +896,19 @@ class Curvilinear3DMesh:
         n = int(b.shape[0])
         if b.shape != (n, 3) or wt.shape != (n, 12):
             raise ValueError("base (n, 3) and w (n, 12) expected")
-        q = q.contiguous()
         out = torch.empty((5, n), dtype=self.tdtype, device="cuda")
         _check(_lib.sbp3c_interp(self.h, _ptr(q), n, _ptr(b), _ptr(wt), _ptr(out), _stream(stream)), "sbp3c_interp")
         return out
 
     def rhs_eval(self, q, out=None, stream=None):
         """q: (5, nk, nj, ni) device tensor of the mesh's element type."""
-        q = q.contiguous()
+        q = self._field(q, "q", (5,) + self.shape)
         if out is None:
             out = self.torch.empty_like(q)
+        elif not out.is_contiguous():
+            raise ValueError("out must be contiguous")
+        else:
+            self._field(out, "out", (5,) + self.shape)
         _check(_lib.sbp3c_rhs_eval(self.h, _ptr(q), _ptr(out), _stream(stream)), "sbp3c_rhs_eval")
         return out
 

@@ -1,7 +1,8 @@
 // Donor search on a 3D curvilinear mesh (Sec. 2.2: donor-receiver pairing, weights from the
 // Lagrange shape functions): for each point, computational coordinates (s, r, t) with
 // X(s, r, t) = p, X the mesh map interpolated by the 4 x 4 x 4 Lagrange basis on the stencil
-// starting at floor(.) - 1 clamped into the mesh, by Newton's method from a nearby node; the
+// starting at floor(.) - 1 clamped into the mesh, by Newton's method from a nearby node (points
+// outside the mesh's padded bounding box are refused without a search); the
 // weights are that basis at the solution. Hole cut (reading, as for the Cartesian 3D hole cut
 // with the overlapping mesh's index units): a point inside the mesh more than a margin of index
 // units from each of its faces is a hole. Host only: no device calls.
@@ -38,8 +39,9 @@ struct Grid3 {
   }
 };
 
-// Nearest node to q among every stride-th node of each line (and the last), then among the
-// nodes within stride of that one.
+// A node near q: the nearest among every stride-th node of each line (and the last), then,
+// halving the stride, the nearest within the previous stride of the node found, down to stride 1.
+// (With stride 1 from the start, the nearest of all nodes.)
 void near_node(const Grid3 &g, const double *q, int stride, int c[3]) {
   double best = INFINITY;
   auto scan = [&](int lo0, int hi0, int lo1, int hi1, int lo2, int hi2, int st) {
@@ -61,14 +63,59 @@ void near_node(const Grid3 &g, const double *q, int stride, int c[3]) {
   };
   c[0] = c[1] = c[2] = 0;
   scan(0, g.n[0] - 1, 0, g.n[1] - 1, 0, g.n[2] - 1, stride);
-  if (stride > 1) {
+  while (stride > 1) {
+    const int next = std::max(1, stride / 2);
     int lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
       lo[a] = std::max(0, c[a] - stride);
       hi[a] = std::min(g.n[a] - 1, c[a] + stride);
     }
-    scan(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], 1);
+    scan(lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], next);
+    stride = next;
   }
+}
+
+// Axis-aligned box of all nodes, padded by the longest edge between neighbouring nodes: the
+// Lagrange-interpolated mesh map does not reach beyond it on meshes whose cells are not folded,
+// so a point outside it is outside the mesh and needs no search.
+struct Box {
+  double lo[3], hi[3];
+  bool contains(const double *q) const {
+    for (int a = 0; a < 3; ++a)
+      if (!(q[a] >= lo[a] && q[a] <= hi[a])) return false;
+    return true;
+  }
+};
+
+Box padded_box(const Grid3 &g) {
+  Box b;
+  for (int a = 0; a < 3; ++a) {
+    b.lo[a] = INFINITY;
+    b.hi[a] = -INFINITY;
+  }
+  double edge2 = 0.0;
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        const size_t p = g.at(i, j, k);
+        for (int a = 0; a < 3; ++a) {
+          b.lo[a] = std::min(b.lo[a], g.X[a][p]);
+          b.hi[a] = std::max(b.hi[a], g.X[a][p]);
+        }
+        const int nb[3][3] = {{i + 1, j, k}, {i, j + 1, k}, {i, j, k + 1}};
+        for (int d = 0; d < 3; ++d) {
+          if (nb[d][d] >= g.n[d]) continue;
+          const size_t r = g.at(nb[d][0], nb[d][1], nb[d][2]);
+          const double q[3] = {g.X[0][r], g.X[1][r], g.X[2][r]};
+          edge2 = std::max(edge2, g.dist2(p, q));
+        }
+      }
+  const double pad = std::sqrt(edge2);
+  for (int a = 0; a < 3; ++a) {
+    b.lo[a] -= pad;
+    b.hi[a] += pad;
+  }
+  return b;
 }
 
 // Newton's method on the interpolated map from s; true when three consecutive steps stay below
@@ -125,6 +172,20 @@ bool newton(const Grid3 &g, const double *q, double s[3]) {
   return true;
 }
 
+// Computational coordinates of q by Newton's method from a nearby node, retried from the nearest
+// of all nodes; false for points outside the padded box without any search.
+bool locate(const Grid3 &g, const Box &box, int stride, const double *q, double s[3]) {
+  if (!box.contains(q)) return false;
+  int c[3];
+  near_node(g, q, stride, c);
+  for (int a = 0; a < 3; ++a) s[a] = c[a];
+  if (newton(g, q, s)) return true;
+  if (stride == 1) return false;
+  near_node(g, q, 1, c);
+  for (int a = 0; a < 3; ++a) s[a] = c[a];
+  return newton(g, q, s);
+}
+
 }  // namespace
 
 extern "C" sbp_status sbp3c_donor_search(const int *n, const double *x, const double *y, const double *z,
@@ -137,17 +198,11 @@ extern "C" sbp_status sbp3c_donor_search(const int *n, const double *x, const do
     if (n[a] < 8 || n[a] > 65535) return sbp::fail(SBP_ERR_SHAPE, "each direction needs 8..65535 points");
   const Grid3 g{{n[0], n[1], n[2]}, {x, y, z}};
   const int stride = std::max(1, std::min({n[0], n[1], n[2]}) / 8);
+  const Box box = padded_box(g);
   for (int t = 0; t < npts; ++t) {
     const double *q = pts + 3 * (size_t)t;
-    int c[3];
-    near_node(g, q, stride, c);
-    double s[3] = {(double)c[0], (double)c[1], (double)c[2]};
-    bool ok = newton(g, q, s);
-    if (!ok && stride > 1) {  // retry from the nearest of all nodes
-      near_node(g, q, 1, c);
-      for (int a = 0; a < 3; ++a) s[a] = c[a];
-      ok = newton(g, q, s);
-    }
+    double s[3];
+    bool ok = locate(g, box, stride, q, s);
     int b[3] = {0, 0, 0};
     for (int a = 0; ok && a < 3; ++a) b[a] = first_node(s[a], n[a]);
     for (int cc = 0; ok && iblank && cc < 4; ++cc)
@@ -179,17 +234,11 @@ extern "C" sbp_status sbp3c_hole_cut(const int *n, const double *x, const double
     if (n[a] < 8 || n[a] > 65535) return sbp::fail(SBP_ERR_SHAPE, "each direction needs 8..65535 points");
   const Grid3 g{{n[0], n[1], n[2]}, {x, y, z}};
   const int stride = std::max(1, std::min({n[0], n[1], n[2]}) / 8);
+  const Box box = padded_box(g);
   for (int t = 0; t < npts; ++t) {
     const double *q = pts + 3 * (size_t)t;
-    int c[3];
-    near_node(g, q, stride, c);
-    double s[3] = {(double)c[0], (double)c[1], (double)c[2]};
-    bool ok = newton(g, q, s);
-    if (!ok && stride > 1) {
-      near_node(g, q, 1, c);
-      for (int a = 0; a < 3; ++a) s[a] = c[a];
-      ok = newton(g, q, s);
-    }
+    double s[3];
+    bool ok = locate(g, box, stride, q, s);
     for (int a = 0; ok && a < 3; ++a) ok = s[a] > margin && s[a] < n[a] - 1 - margin;
     if (ok) iblank[t] = 0;
   }

@@ -1,6 +1,8 @@
 // Right-hand-side evaluation whose receiver workspace lives in a fixed device array, for
 // sbp_rhs_eval_noalloc: callers that must not have the library allocate device memory at call
-// time use it (see include/sbp_mrab.h).
+// time (device memory reserved up front by another allocator, or loops that cannot afford the
+// synchronisation of cudaMalloc / cudaFree) use it. The first call on a device looks the array's
+// address up; it should come before any stream capture.
 #include <cuda_runtime.h>
 
 #include <mutex>

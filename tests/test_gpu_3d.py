@@ -1,14 +1,16 @@
 """3D Cartesian GPU path against the 3D oracle through the C ABI (sbp3_*).
 
 FP64: setup tables exact (hole cut, receivers) or to rounding (donor weights), right-hand side,
-interpolation and whole MRAB runs to 1e-12 relative L2; FP32 state with FP64 update arithmetic
-within 1e-5 of the FP64 oracle after the bootstrap and several macro steps."""
+interpolation and whole MRAB runs to 1e-12 relative L2 (states and increments); FP32 state with
+FP64 update arithmetic within 1e-5 of the FP64 oracle after the bootstrap and several macro
+steps, its increments within the derived FP32 bound."""
 import numpy as np
 import pytest
 
 import workloads as W
 from conftest import build_library
 from oracle import OracleSystem3D
+from tolerances import U32, U64, fp32_rhs_tol_3d, increment_tol, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -23,9 +25,7 @@ def sbp():
     return mod
 
 
-def _rel(a, b):
-    nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+_rel = rel
 
 
 CASES = {
@@ -74,24 +74,27 @@ def test_rhs_and_interp_3d_fp64(sbp, case):
                 assert _rel(fh.cpu().numpy(), o.interp(k, o.viscflux(1 - k, wl["q0"][1 - k]))) < 1e-12
 
 
-def _oracle_run(o, q0, H, n):
-    qs, hf, hs = o.bootstrap(q0, H)
-    qs, hf, hs = o.mrab(qs, hf, hs, H, n)
-    return qs
-
-
 @pytest.mark.parametrize("case", ["tg_ns", "tg_sr3_ab34", "extruded_y_mms"])
 def test_mrab_3d(sbp, case):
+    """Bootstrap + 3 macro steps against the oracle: the states (FP64 1e-12, FP32 1e-5) and the
+    increments over the 3 macro steps, each side from its own start (FP64 1e-12; FP32 the
+    derived FP32 right-hand-side bound), with the stored state's rounding floor added."""
     mk, hc = CASES[case]
     wl = mk()
     o = OracleSystem3D(wl, hole_cells=hc)
     H = o.macro_step_size(wl["q0"])
     n = 3
-    want = _oracle_run(o, wl["q0"], H, n)
+    y, hf, hs = o.bootstrap(wl["q0"], H)
+    want, _, _ = o.mrab(y, hf, hs, H, n)
+    sr = wl["params"]["step_ratio"]
+    q0 = wl["q0"]
+    fp32_bar = max(fp32_rhs_tol_3d(q0[j], wl["meshes"][j]["h"], o.iblank[j] != 0,
+                                   o.coupled_rhs(j, q0[j], q0[1 - j])) for j in range(2))
     for dtype, tol in (("f64", 1e-12), ("f32", 1e-5)):
         g = sbp.System3D(wl, dtype=dtype, hole_cells=hc)
         g.bind(wl["q0"])
         g.mrab_init(H)
+        start = [g.to_host(k, g.current_state(k)) for k in range(2)]
         g.mrab_step(n)
         g.check()
         for k in range(2):
@@ -99,6 +102,10 @@ def test_mrab_3d(sbp, case):
             act = o.iblank[k] != 0
             err = _rel(got[:, act], want[k][:, act])
             assert err < tol, (dtype, k, err)
+            ei = _rel(got[:, act] - start[k][:, act], want[k][:, act] - y[k][:, act])
+            itol = increment_tol(1e-12 if dtype == "f64" else fp32_bar, y[k][:, act], want[k][:, act], n * sr,
+                                 U64 if dtype == "f64" else U32)
+            assert ei < itol, (dtype, k, ei, itol)
         g.close()
 
 

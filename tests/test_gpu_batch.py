@@ -1,11 +1,14 @@
 """Batched persistent stepping (one cooperative launch per micro step over all member systems)
-against stepping each member alone: the same kernels' arithmetic, so the states must agree
-bit for bit, over more macro steps than the ring-phase period."""
+against the oracle (each member's bootstrap and macro steps against OracleSystem's, on states and
+increments), and against stepping each member alone: the same kernels' arithmetic, so the states
+must agree bit for bit, over more macro steps than the ring-phase period."""
 import numpy as np
 import pytest
 
 import workloads as W
 from conftest import build_library
+from oracle import OracleSystem
+from tolerances import U32, U64, fp32_rhs_tol, increment_tol, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -28,6 +31,47 @@ def _members(sbp, wls, dtype):
         g.mrab_init()
         out.append(g)
     return out
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batch_matches_oracle(sbp, dtype):
+    """Four small members with step ratios 2, 4, 8 and 2 (backgrounds 96..128 points a side with a
+    hole under the patch, patch spacing ratio = step ratio), stepped together: each member's states against the oracle's
+    bootstrap + macro steps, FP64 to 1e-12 on states and increments; FP32 states to 1e-5 and
+    increments within the derived FP32 right-hand-side bound."""
+    spec = [(96, 2, 101), (104, 4, 102), (128, 8, 103), (112, 2, 104)]
+    wls = [W.vortex_box_in_box(seed=s, n_bg=n, n_fine=int(round(n * r / 8.0)) + 1, bg_half=5.0,
+                               fine_half=5.0 / 8.0, step_ratio=r, jitter=0.3) for n, r, s in spec]
+    members = _members(sbp, wls, dtype)
+    b = sbp.Batch(members, autotune=True)
+    start = [[g.to_host(k, g.current_state(k)) for k in range(2)] for g in members]
+    nsteps = 3
+    b.step(nsteps)
+    b.check()
+    for wl, g, st in zip(wls, members, start):
+        ref = OracleSystem(wl)
+        H = ref.macro_step_size(wl["q0"])
+        Hg, _ = g.mrab_time()
+        assert abs(Hg - H) <= 1e-14 * H
+        y, hf, hs = ref.bootstrap(wl["q0"], H)
+        want, _, _ = ref.mrab(y, hf, hs, H, nsteps)
+        q0, sr = wl["q0"], wl["params"]["step_ratio"]
+        if dtype == "f64":
+            bar, unit, stol = 1e-12, U64, 1e-12
+        else:
+            bar = max(fp32_rhs_tol(ref.met[j], q0[j], ref.iblank[j] != 0, ref.coupled_rhs(j, q0[j], q0[1 - j]))
+                      for j in range(2))
+            unit, stol = U32, 1e-5
+        for k in range(2):
+            act = ref.iblank[k] != 0
+            got = g.to_host(k, g.current_state(k))[:, act]
+            assert rel(got, want[k][:, act]) < stol, (sr, k)
+            ei = rel(got - st[k][:, act], want[k][:, act] - y[k][:, act])
+            tol = increment_tol(bar, y[k][:, act], want[k][:, act], nsteps * sr, unit)
+            assert ei < tol, (dtype, sr, k, ei, tol)
+    b.close()
+    for g in members:
+        g.close()
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

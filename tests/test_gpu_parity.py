@@ -1,15 +1,19 @@
 """GPU path against the oracle, element by element, through the C ABI.
 
 FP64 bar: 1e-12 relative L2 (setup tables bit-exact where the computation is integer or
-follows the same operation order). FP32 bar: 1e-5 relative L2 on states after time steps; the
-FP32 right-hand side is reported against the FP64 oracle with a bound derived from the
-cancellation in its flux differences (see the design notes)."""
+follows the same operation order); time steps are compared on their increments (the state at
+the end minus the state at the start of the tested steps, on each side), with the stored
+state's own rounding added where it is a larger fraction of the increment. FP32: states after
+time steps within 1e-5 relative L2 of the FP64 oracle's; right-hand sides and increments within
+the bound derived from FP32 rounding and the cancellation in the flux differences
+(tests/tolerances.py)."""
 import numpy as np
 import pytest
 
 import workloads as W
 from conftest import build_library
 from oracle import OracleSystem
+from tolerances import U32, U64, fp32_rhs_tol, increment_tol, rel, rel_increment
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -24,9 +28,9 @@ def sbp():
     return mod
 
 
-def rel(a, b):
-    nb = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+def _omega(wl, omega):
+    wl["params"]["omega_corner"] = omega
+    return wl
 
 
 CASES = {
@@ -38,6 +42,8 @@ CASES = {
     "mms_viscous": lambda: W.mms_box_in_box(52, "viscous"),
     # far-field sponge layer six points deep (Sec. 5.1)
     "cylinder_sponge": lambda: W.cylinder_small(seed=20, sponge_cells=6, sponge_strength=2.0),
+    # corner interface points weighted by Omega = 1/2 (Sec. 4.2 eq. (penalty_interp))
+    "vortex_omega": lambda: _omega(W.vortex_box_in_box(seed=21, n_bg=48, n_fine=33), 0.5),
 }
 
 # The extended-history Adams-Bashforth family of Sec. 3.2 inside MRAB (order n, history m:
@@ -105,7 +111,7 @@ def test_interp_and_rhs_fp64(sbp, case):
 
 
 @pytest.mark.parametrize("case", ["vortex", "cylinder", "vortex_sr3_ab34", "cylinder_ab34", "vortex_sr1",
-                                  "cylinder_sponge"] + sorted(AB_CASES))
+                                  "cylinder_sponge", "vortex_omega"] + sorted(AB_CASES))
 def test_mrab_fp64(sbp, case):
     wl = {**CASES, **AB_CASES}[case]()
     ref = OracleSystem(wl)
@@ -120,18 +126,24 @@ def test_mrab_fp64(sbp, case):
     y, hf, hs = ref.bootstrap(wl["q0"], H_ref)
     g.bind(wl["q0"])
     g.mrab_init()
+    sr, m = wl["params"]["step_ratio"], wl["params"]["hist_len"]
+    start = []
     for k in range(2):
-        assert rel(g.to_host(k, g.current_state(k)), y[k]) < 1e-12, "bootstrap state"
+        got = g.to_host(k, g.current_state(k))
+        tol = increment_tol(1e-12, wl["q0"][k], y[k], (m - 1) * sr, U64)
+        assert rel_increment(got, y[k], wl["q0"][k]) < tol, "bootstrap increment"
+        start.append(got)
     nsteps = 3
     want, _, _ = ref.mrab(y, hf, hs, H_ref, nsteps)
     g.mrab_step(nsteps)
     g.check()
     for k in range(2):
         got = g.to_host(k, g.current_state(k))
-        e = rel(got, want[k])
-        assert e < 1e-12, (k, e)
-        # the state moved: the comparison is not trivially between two copies of q0
-        assert rel(want[k], wl["q0"][k]) > 1e-9
+        assert rel(got, want[k]) < 1e-12, (k, rel(got, want[k]))
+        # the increment over the tested steps, each side from its own start
+        e = rel(got - start[k], want[k] - y[k])
+        tol = increment_tol(1e-12, y[k], want[k], nsteps * sr, U64)
+        assert e < tol, (k, e, tol)
     Hg, t = g.mrab_time()
     assert t == pytest.approx(nsteps * Hg)
     g.close()
@@ -183,49 +195,73 @@ def test_sponge_changes_the_state_and_is_refused_by_the_adjoint(sbp):
     g0.close()
 
 
-@pytest.mark.parametrize("case", ["vortex", "cylinder", "cylinder_sponge"])
+@pytest.mark.parametrize("case", ["vortex", "cylinder", "cylinder_sponge", "vortex_omega"])
 def test_fp32(sbp, case):
     """FP32 state and right-hand side with FP64 MRAB accumulation, against the FP64 oracle."""
     wl = CASES[case]()
     ref = OracleSystem(wl)
     g = sbp.System(wl, dtype="f32")
     qd = [g.to_device(k, wl["q0"][k]) for k in range(2)]
+    rhs_tol = []
     for k in range(2):
+        act = ref.iblank[k] != 0
         got = g.to_host(k, g.rhs_eval(k, qd[k], qd[1 - k]))
         want = ref.coupled_rhs(k, wl["q0"][k], wl["q0"][1 - k])
-        # FP32 flux rounding (~6e-8 |F|) over the derivative stencil, relative to |dq/dt|
-        assert rel(got, want) < (2e-5 if case == "vortex" else 2e-3), rel(got, want)
+        tol = fp32_rhs_tol(ref.met[k], wl["q0"][k], act, want)
+        e = rel(got[:, act], want[:, act])
+        print("fp32 rhs", case, k, "error %.3e bound %.3e" % (e, tol))
+        assert e < tol, (k, e, tol)
+        rhs_tol.append(tol)
     H_ref = ref.macro_step_size(wl["q0"])
     y, hf, hs = ref.bootstrap(wl["q0"], H_ref)
-    want, _, _ = ref.mrab(y, hf, hs, H_ref, 3)
+    nsteps = 3
+    want, _, _ = ref.mrab(y, hf, hs, H_ref, nsteps)
     g.bind(wl["q0"])
     g.mrab_init()
-    g.mrab_step(3)
+    start = [g.to_host(k, g.current_state(k)) for k in range(2)]
+    g.mrab_step(nsteps)
     g.check()
+    sr = wl["params"]["step_ratio"]
     for k in range(2):
-        e = rel(g.to_host(k, g.current_state(k)), want[k])
+        act = ref.iblank[k] != 0
+        got = g.to_host(k, g.current_state(k))
+        e = rel(got[:, act], want[k][:, act])
         assert e < 1e-5, (k, e)
+        # the increment is as accurate as the FP32 right-hand sides it integrates
+        ei = rel(got[:, act] - start[k][:, act], want[k][:, act] - y[k][:, act])
+        tol = increment_tol(max(rhs_tol), y[k][:, act], want[k][:, act], nsteps * sr, U32)
+        print("fp32 increment", case, k, "error %.3e bound %.3e" % (ei, tol))
+        assert ei < tol, (k, ei, tol)
     g.close()
 
 
 def test_full_size_cylinder_rhs(sbp):
-    """The benchmark's workload at full size (O-grid 512x128, background 1024x512)."""
+    """The benchmark's workload at full size (O-grid 512x128, background 1024x512): FP64 within
+    1e-12, FP32 within its derived bound."""
     wl = W.cylinder_overset(seed=0)
     ref = OracleSystem(wl)
-    g = sbp.System(wl)
-    qd = [g.to_device(k, wl["q0"][k]) for k in range(2)]
-    for k in range(2):
-        got = g.to_host(k, g.rhs_eval(k, qd[k], qd[1 - k]))
-        want = ref.coupled_rhs(k, wl["q0"][k], wl["q0"][1 - k])
-        assert rel(got, want) < 1e-12, (k, rel(got, want))
-    g.close()
+    want = [ref.coupled_rhs(k, wl["q0"][k], wl["q0"][1 - k]) for k in range(2)]
+    for dtype in ("f64", "f32"):
+        g = sbp.System(wl, dtype=dtype)
+        qd = [g.to_device(k, wl["q0"][k]) for k in range(2)]
+        for k in range(2):
+            act = ref.iblank[k] != 0
+            got = g.to_host(k, g.rhs_eval(k, qd[k], qd[1 - k]))
+            tol = 1e-12 if dtype == "f64" else fp32_rhs_tol(ref.met[k], wl["q0"][k], act, want[k])
+            e = rel(got[:, act], want[k][:, act])
+            print("full-size rhs", dtype, k, "error %.3e bound %.3e" % (e, tol))
+            assert e < tol, (dtype, k, e, tol)
+        g.close()
 
 
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
 def test_full_size_cylinder_mrab(sbp, dtype, tol):
     """The benchmark's step at full size and in its launch configuration (autotuned kernel
     shapes, CUDA-graph macro steps): the Runge-Kutta bootstrap and two MRAB macro steps against
-    the oracle's."""
+    the oracle's, on the states and on the increments over the two macro steps. In FP32 the
+    background's increment over two macro steps (4e-7 of the state) is below the FP32 state's
+    own rounding, so only the O-grid's increment is compared there; the full-size FP32
+    right-hand side is checked in test_full_size_cylinder_rhs."""
     wl = W.cylinder_overset(seed=1)
     ref = OracleSystem(wl)
     H = ref.macro_step_size(wl["q0"])
@@ -234,13 +270,22 @@ def test_full_size_cylinder_mrab(sbp, dtype, tol):
     g = sbp.System(wl, dtype=dtype)
     g.bind(wl["q0"])
     g.mrab_init()
+    start = [g.to_host(k, g.current_state(k)) for k in range(2)]
     g.mrab_step(2)
     g.check()
+    sr = wl["params"]["step_ratio"]
     for k in range(2):
         act = ref.iblank[k] != 0
         got = g.to_host(k, g.current_state(k))
         e = rel(got[:, act], want[k][:, act])
         assert e < tol, (dtype, k, e)
+        if dtype == "f32" and k == 0:
+            continue
+        bar = tol if dtype == "f64" else fp32_rhs_tol(ref.met[k], y[k], act, hs[-1] if k == ref.slow else hf[-1])
+        itol = increment_tol(bar, y[k][:, act], want[k][:, act], 2 * sr, U64 if dtype == "f64" else U32)
+        ei = rel(got[:, act] - start[k][:, act], want[k][:, act] - y[k][:, act])
+        print("full-size increment", dtype, k, "error %.3e bound %.3e" % (ei, itol))
+        assert ei < itol, (dtype, k, ei, itol)
     g.close()
 
 

@@ -1,0 +1,74 @@
+"""Comparison helpers and the tolerances the parity tests derive from the arithmetic.
+
+* Increments, not states: a time step is checked on y_end - y_start, where y_start is the state
+  at the start of the tested steps on both sides, so that a state that did not advance fails
+  (its increment error is 100 %). The bar applies to the increment, except where the rounding of
+  the stored state itself (one half unit in the last place per stored update, growing like the
+  square root of the number of updates) is a larger fraction of the increment; that floor is
+  added to the bar.
+* FP32 right-hand sides against the FP64 oracle: every flux value carries the rounding of the
+  ~12 FP32 operations that form it and the derivative stencil adds its own four, so the
+  absolute error of dq/dt is at most (12 + 4) u32 sum_k |c_k| J (|F_xi| + |F_eta|) with
+  u32 = 2^-24 and sum_k |c_k| = 3/2 for the interior row; relative to |dq/dt| this is large
+  where the flux differences cancel (a nearly uniform flow), which the bound measures case by
+  case from the oracle's state and metrics.
+"""
+import math
+
+import numpy as np
+
+U32 = 2.0 ** -24
+U64 = 2.0 ** -53
+GAMMA = 1.4
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def rel_increment(got, want, start):
+    """Relative L2 error of the increment got - start against want - start."""
+    return rel(np.asarray(got) - start, np.asarray(want) - start)
+
+
+def increment_tol(bar, start, want, n_updates, unit):
+    """bar plus the rounding floor of the stored state: 2 sqrt(n_updates) unit |q| / |dq|.
+    Asserts that the comparison is not vacuous (the floor well below the increment)."""
+    dq = np.linalg.norm(np.asarray(want) - start)
+    floor = 2.0 * math.sqrt(max(n_updates, 1)) * unit * np.linalg.norm(start) / max(dq, 1e-300)
+    assert floor < 0.1, "the increment is below the state's own rounding: run more steps"
+    return bar + floor
+
+
+def fp32_rhs_bound(met, q, act):
+    """Numerator of the derived FP32 bound (module docstring): 16 u32 (3/2) |J (|F_xi| +
+    |F_eta|)| over the active points, from the state q (4, nj, ni) and the metric planes met
+    (xi_x/J, xi_y/J, eta_x/J, eta_y/J, J)."""
+    rho, mx, my, E = q
+    u, v = mx / rho, my / rho
+    p = (GAMMA - 1.0) * (E - 0.5 * rho * (u * u + v * v))
+    F = np.stack([mx, mx * u + p, mx * v, (E + p) * u])
+    G = np.stack([my, my * u, my * v + p, (E + p) * v])
+    fx = np.abs(met[0] * F + met[1] * G)
+    fe = np.abs(met[2] * F + met[3] * G)
+    return 16.0 * U32 * 1.5 * float(np.linalg.norm((met[4] * (fx + fe))[:, act]))
+
+
+def fp32_rhs_tol(met, q, act, rhs_ref):
+    """The derived FP32 bound relative to the oracle's right-hand side rhs_ref."""
+    return fp32_rhs_bound(met, q, act) / float(np.linalg.norm(rhs_ref[:, act]))
+
+
+def fp32_rhs_tol_3d(q, h, act, rhs_ref):
+    """The same bound on a 3D Cartesian mesh of spacings h = (hx, hy, hz): 16 u32 (3/2)
+    |(|F|/hx + |G|/hy + |H|/hz)| / |dq/dt| over the active points, q = (rho, rho u, rho v,
+    rho w, rho E)."""
+    rho, mx, my, mz, E = q
+    u, v, w = mx / rho, my / rho, mz / rho
+    p = (GAMMA - 1.0) * (E - 0.5 * rho * (u * u + v * v + w * w))
+    F = np.stack([mx, mx * u + p, mx * v, mx * w, (E + p) * u])
+    G = np.stack([my, my * u, my * v + p, my * w, (E + p) * v])
+    H = np.stack([mz, mz * u, mz * v, mz * w + p, (E + p) * w])
+    s = np.abs(F) / h[0] + np.abs(G) / h[1] + np.abs(H) / h[2]
+    return 16.0 * U32 * 1.5 * float(np.linalg.norm(s[:, act])) / float(np.linalg.norm(rhs_ref[:, act]))

@@ -19,8 +19,8 @@ The index i (the xi direction) runs fastest in every array. States are
 
 The workloads follow the paper's test problems: the convecting isentropic
 vortex of App. C.2 on a box-in-box pair, and a cylinder in cross-flow on an
-O-grid inside a Cartesian background (Sec. 5.1), with the sizes listed in
-the DESIGN notes.
+O-grid inside a Cartesian background (Sec. 5.1); each function states its
+sizes.
 """
 from __future__ import annotations
 
