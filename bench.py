@@ -34,7 +34,10 @@ WORKLOAD = ("cylinder overset Navier-Stokes: O-grid 512x128 + Cartesian 1024x512
             "MRAB order 3, step ratio 4")
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_TFLOPS = 1.25        # nominal dense FP64 rate of GB300 (no FP64 tensor path)
-FLOP_PER_POINT_NS = 300.0      # algorithmic FLOPs of one 2D NS right-hand-side point + update
+# FLOPs per active point of one coupled right-hand side + MRAB update (order 3) as the oracle
+# writes it (python oracle/flops.py: every +, -, *, /, sqrt of its per-point arithmetic counted;
+# it computes zero metric terms on Cartesian meshes and divisions as one operation)
+ORACLE_FLOP_PER_POINT = {"background": 442.2, "ogrid": 456.4}
 
 
 def _args():
@@ -54,6 +57,9 @@ def _args():
     ap.add_argument("--no-curv3d", action="store_true", help="skip the 3D curvilinear operator")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-stability", action="store_true", help="skip the step-matrix stability study")
+    ap.add_argument("--profile-shapes", action="store_true",
+                    help="profiling aid: one eager macro step of the cylinder per kernel shape, the CUDA "
+                         "profiler started around each (ncu --profile-from-start off), then exit")
     ap.add_argument("--no-perf-model", action="store_true",
                     help="skip the performance model (RK4 vs MRAB at their largest stable steps)")
     return ap.parse_args()
@@ -358,16 +364,30 @@ class _Null:
         return False
 
 
-# DRAM bytes (read + write) per launch of a phase's kernels from ncu captures of the current
-# kernels, for the kernel shapes captured (strip, flux rows, derivative rows): the O-grid micro
-# step of the cylinder workload in FP64 (the mean over the four micro steps of a macro step,
-# serialised replay with a cold L2).
-MEASURED_TRAFFIC = {
-    ("f64", "rhs_fast"): [
-        {"shape": (32, 8, 8), "bytes": 16.94e6, "source": "ncu --set full, profiles/k_flux_update_cylinder_fp64.md"},
-        {"shape": (32, 16, 4), "bytes": 16.95e6,
-         "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, profiles/k_flux_update_cylinder_fp64.md"},
-    ],
+# FP64 operations executed (dadd + dmul + 2 dfma) and DRAM bytes (read + write) per right-hand
+# side + MRAB update of the cylinder workload, counted by ncu for every kernel shape the
+# autotuner offers (kernel pair: (0, flux rows, derivative rows); marching kernel: (58, chunk,
+# 0)): (background per launch, O-grid per micro step averaged over a macro step, background
+# DRAM bytes, O-grid DRAM bytes per micro step). Serialised launches with a cold L2; the command
+# and the per-shape table are in profiles/fp64_ops_cylinder.md.
+FP64_COUNTS = {
+(0, 8, 4): (126749752, 18413760, 1.116e+08, 1.694e+07),
+    (0, 8, 8): (126749752, 18413760, 1.101e+08, 1.694e+07),
+    (0, 8, 16): (126749752, 18413760, 1.092e+08, 1.696e+07),
+    (0, 8, 32): (126749752, 18413760, 1.088e+08, 1.699e+07),
+    (0, 16, 4): (121579064, 18210496, 1.117e+08, 1.695e+07),
+    (0, 16, 8): (121579064, 18210496, 1.104e+08, 1.695e+07),
+    (0, 16, 16): (121579064, 18210496, 1.089e+08, 1.697e+07),
+    (0, 16, 32): (121579064, 18210496, 1.098e+08, 1.699e+07),
+    (0, 32, 4): (118993720, 18133440, 1.121e+08, 1.697e+07),
+    (0, 32, 8): (118993720, 18133440, 1.097e+08, 1.697e+07),
+    (0, 32, 16): (118993720, 18133440, 1.097e+08, 1.699e+07),
+    (0, 32, 32): (118993720, 18133440, 1.089e+08, 1.701e+07),
+    (58, 8, 0): (170707384, 27947744, 5.595e+07, 9.506e+06),
+    (58, 16, 0): (142303648, 22987232, 5.535e+07, 9.506e+06),
+    (58, 32, 0): (128101444, 20506976, 5.472e+07, 9.509e+06),
+    (58, 64, 0): (121002034, 19266848, 5.426e+07, 9.508e+06),
+    (58, 128, 0): (117452482, 18646784, 5.455e+07, 9.506e+06),
 }
 
 
@@ -389,26 +409,37 @@ def _roofline(res, wl, dtype, hbm_peak, peak_kind, fp64=None):
     else:
         bpp = 0.0
     roof = {"kernel": phase, "launches": n, "avg_launch_ms": avg_s * 1e3}
+    mesh = "background" if phase.endswith("slow") else "ogrid"
+    tn = res["tuning"][mesh]
+    shape = (0 if tn["strip_width"] == 32 else tn["strip_width"], tn["rows_per_cta"],
+             tn["rows_update"] if tn["strip_width"] == 32 else 0)
+    counts = FP64_COUNTS.get(shape) if phase.startswith("rhs") else None
     if dtype == "f64" and phase.startswith("rhs"):
-        flops = FLOP_PER_POINT_NS * pts
         peak = fp64["tflops"] if fp64 else FP64_PEAK_TFLOPS
         kind = ("measured FP64 FMA rate of this GPU (%s)" % fp64["how"]) if fp64 else \
             "nominal FP64 (derived: 152 SMs x 2 DFMA/clk x 2 x 2.06 GHz)"
-        roof.update({"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak,
-                     "unit": "TFLOP/s", "peak_kind": kind,
+        roof.update({"bound": "alu", "unit": "TFLOP/s", "peak": peak, "peak_kind": kind,
                      "hbm_achieved_gbs": bpp * pts / avg_s / 1e9, "bytes_per_point": bpp,
-                     "flop_per_point": FLOP_PER_POINT_NS})
-        roof["frac"] = roof["achieved"] / roof["peak"]
+                     "kernel_shape": list(shape)})
+        if counts is not None:
+            flops = counts[0] if mesh == "background" else counts[1]
+            roof.update({"achieved": flops / avg_s / 1e12, "frac": flops / avg_s / 1e12 / peak,
+                         "flop_per_launch": flops, "flop_per_point_executed": flops / pts,
+                         "flop_per_point_oracle": ORACLE_FLOP_PER_POINT[mesh],
+                         "flop_source": "FP64 operations executed by this kernel shape, counted by ncu "
+                                        "(profiles/fp64_ops_cylinder.md); the oracle's formulation of the "
+                                        "same right-hand side and update counts flop_per_point_oracle"})
+        else:
+            roof.update({"achieved": None, "frac": None,
+                         "flop_source": "no ncu count for the autotuned shape %s" % (shape,)})
     else:
         roof.update({"bound": "hbm", "achieved": bpp * pts / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                      "peak_kind": peak_kind, "bytes_per_point": bpp})
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
-    og = res["tuning"]["ogrid"]
-    for t in MEASURED_TRAFFIC.get((dtype, phase), []):
-        if (og["strip_width"], og["rows_per_cta"], og["rows_update"]) == t["shape"]:
-            roof["traffic"] = t["bytes"]
-            roof["traffic_source"] = t["source"]
+    if dtype == "f64" and counts is not None:
+        roof["traffic"] = counts[2] if mesh == "background" else counts[3]
+        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/fp64_ops_cylinder.md"
     return roof
 
 
@@ -1077,10 +1108,43 @@ def _reference(args):
     return 0
 
 
+def _profile_shapes(dtype):
+    """One macro step of the cylinder workload per kernel shape the autotuner offers (both meshes
+    on the same shape, kernel-by-kernel launches), each bracketed by the CUDA profiler's start
+    and stop, so that an ncu run with --profile-from-start off captures exactly those launches:
+    10 per shape (1 slow + 4 fast right-hand sides, 2 kernels each)."""
+    import torch
+    import paper_1805_06607_gb300 as sbp
+    import workloads as W
+
+    wl = W.cylinder_overset(seed=0)
+    g = sbp.System(wl, dtype=dtype)
+    g.bind(wl["q0"])
+    g.mrab_init()
+    g.autotune(False)
+    g.use_graphs(False)
+    shapes = [(0, r, u) for r in (8, 16, 32) for u in (4, 8, 16, 32)] + [(58, c, 0) for c in (8, 16, 32, 64, 128)]
+    for strip, rows, ru in shapes:
+        for k in range(2):
+            g.set_rhs_shape(k, strip, rows, ru)
+        g.mrab_step(1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        g.mrab_step(1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("shape", strip, rows, ru, flush=True)
+    g.check()
+    g.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return _reference(args)
+    if args.profile_shapes:
+        return _profile_shapes(args.dtype)
     import workloads as W
 
     world, rank, local = _setup_dist(args)

@@ -495,6 +495,16 @@ sbp_status sbp_f32_to_f64(const void *x, void *y, size_t n, void *stream);
  * FP64 operations it performs (2 per FMA). Time it with events on the same stream. SBP_ERR_ARG
  * for a null out, non-positive sizes or a block that is not a multiple of 32 up to 1024. */
 sbp_status sbp_fp64_rate_probe(void *out, int grid, int block, long iters, double *flops, void *stream);
+/* Failure-detection self-test (the paper has no counterpart): the bounded wait of the grid
+ * barrier that separates the phases of a batch launch (sbp_batch_step), run on `grid` CTAs of 32
+ * threads that wait for `arrivals` arrivals with at most max_spins polls of 256 ns each. With
+ * arrivals > grid no CTA can pass: each gives up after its poll limit, records SBP_ERR_TIMEOUT in
+ * the launch's error word and returns, so the context stays usable. *status (host) receives
+ * that error word (0 when the barrier opened), *passed (host) the CTAs that passed. Allocates a
+ * 16-byte device word set and synchronises the stream. SBP_ERR_ARG for grid outside 1..8,
+ * arrivals < 1 or max_spins outside 1..65536 (a limit of at most ~17 ms). */
+sbp_status sbp_barrier_selftest(int grid, int arrivals, unsigned max_spins, int *status, int *passed,
+                                void *stream);
 /* ---- 3D curvilinear operator -------------------------------------------------------------------
  * The flux divergence of the 3D compressible Euler / Navier-Stokes equations (App. C.1) on one
  * curvilinear structured mesh of n[0] x n[1] x n[2] points (i fastest), non-periodic in every

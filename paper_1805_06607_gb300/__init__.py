@@ -135,6 +135,7 @@ _SIGS.update({
     "sbp3_set_rhs_kernel": [_P, _I, _I],
     "sbp_f32_to_f64": [_P, _P, ctypes.c_size_t, _P],
     "sbp_fp64_rate_probe": [_P, _I, _I, ctypes.c_long, ctypes.POINTER(_D), _P],
+    "sbp_barrier_selftest": [_I, _I, ctypes.c_uint, ctypes.POINTER(_I), ctypes.POINTER(_I), _P],
     "sbp_host_tables_create": [ctypes.POINTER(MeshDesc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "sbp_host_tables_destroy": [_P],
     "sbp_host_tables_get": [_P, _I, _P, _P, _P, _P, _P],
@@ -784,6 +785,15 @@ def f32_to_f64(x, stream=None):
     y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
     _check(_lib.sbp_f32_to_f64(_ptr(x), _ptr(y), x.numel(), _stream(stream)), "sbp_f32_to_f64")
     return y
+
+
+def barrier_selftest(grid, arrivals, max_spins, stream=None):
+    """The batch launch's bounded grid barrier on `grid` CTAs waiting for `arrivals` arrivals
+    (C ABI sbp_barrier_selftest): returns (error word, CTAs that passed)."""
+    st, npass = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib.sbp_barrier_selftest(int(grid), int(arrivals), int(max_spins), ctypes.byref(st),
+                                     ctypes.byref(npass), _stream(stream)), "sbp_barrier_selftest")
+    return st.value, npass.value
 
 
 def fp64_rate_probe(out, grid, block, iters, stream=None):

@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(256) k3_update(const Rhs3Launch a) {
     T q0[5], qv[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) q0[v] = q[v * m.field + p];
-    ab_update<T, 5>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv);
+    ab_update<T, 5>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv, (code & 15u) != 15u ? a.err : nullptr);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       out[v * m.field + p] = rhs[v];
@@ -713,7 +713,7 @@ __global__ void __launch_bounds__(256) k3_updm(const Rhs3Launch a, int chunk) {
       T q0[5], qv[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) q0[v] = q[v * m.field + p];
-      ab_update<T, 5>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv);
+      ab_update<T, 5>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv, (code & 15u) != 15u ? a.err : nullptr);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         out[v * m.field + p] = rhs[v];

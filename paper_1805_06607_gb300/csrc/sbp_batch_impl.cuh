@@ -23,7 +23,8 @@ namespace sbp {
 // so a broken launch ends instead of hanging the device.
 constexpr unsigned kBarrierSpins = 4u << 20;  // with 256 ns sleeps: about one second
 
-static __device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned nblocks, int *err) {
+static __device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned nblocks, int *err,
+                                    unsigned max_spins = kBarrierSpins) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -37,7 +38,7 @@ static __device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, uns
     } else {
       unsigned spins = 0;
       while (*gen == g) {
-        if (++spins > kBarrierSpins || *(volatile int *)err) {
+        if (++spins > max_spins || *(volatile int *)err) {
           atomicCAS(err, 0, (int)SBP_ERR_TIMEOUT);
           ok = 0;
           break;
@@ -88,11 +89,12 @@ __device__ __forceinline__ void batch_donor_phase(const BatchSubstep &b) {
         const int set = pair / a.npts, d = pair - set * a.npts;
         const uint32_t ij = a.pts[d];
         const size_t p = (size_t)(ij >> 16) * a.d.pitch + (ij & 0xFFFFu);
-        T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * a.npts;
+        const int sd = a.stride ? a.stride : a.npts;
+        T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * sd;
         T st[4];
         set_state(a, set, p, st);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) dv[v * a.npts + d] = st[v];
+        for (int v = 0; v < 4; ++v) dv[v * sd + d] = st[v];
       }
     }
   }

@@ -709,6 +709,7 @@ struct sbp_batch_s {
       std::vector<std::vector<int>> sat_off(srmax, std::vector<int>(1, 0)), rl_curv(srmax);
       auto add_rhs = [&](int j, sbp_system_s *S, int k, RhsLaunch a) {
         a.rows_per_cta = ty;
+        a.err = err;  // failures inside the batch launch are reported by sbp_batch_check
         int r = (int)rl[j].size();
         rl[j].push_back(a);
         sat_off[j].push_back(sat_off[j].back() + a.nsat);

@@ -177,12 +177,31 @@ __device__ __forceinline__ double widen(float x) {
 __device__ __forceinline__ double to_f64(float x) { return widen(x); }
 __device__ __forceinline__ double to_f64(double x) { return x; }
 
+// Failure detection: true when a value is infinite or NaN (exponent field all ones), tested on
+// the bits (integer operations, nothing issued to the FP64 pipe).
+__device__ __forceinline__ bool not_finite(float x) { return (__float_as_uint(x) & 0x7F800000u) == 0x7F800000u; }
+__device__ __forceinline__ bool not_finite(double x) {
+  return (__double_as_longlong(x) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
+}
+
+// Records SBP_ERR_NONFINITE in the device error word (first error wins) when a new state has a
+// non-finite value or a density that is not positive: the state cannot be stepped further.
+template <typename T, int NV>
+__device__ __forceinline__ void flag_bad_state(const T qn[NV], int *err) {
+  bool bad = !(qn[0] > T(0));
+#pragma unroll
+  for (int c = 1; c < NV; ++c) bad |= not_finite(qn[c]);
+  if (bad && err) atomicCAS(err, 0, (int)SBP_ERR_NONFINITE);
+}
+
 // Adams-Bashforth / MRAB update of one point's NV variables (Sec. 3.1 eq. (ab_general)):
 // qn = q + sum_h alpha[h] hold[h] + alpha[nold] rhs, accumulated in FP64 in that order. The
-// loads of one history slot's NV values are issued together, ahead of their products.
+// loads of one history slot's NV values are issued together, ahead of their products. A new
+// state that is not finite or has a non-positive density is flagged in *err (callers pass err
+// for active points only: hole points carry no state).
 template <typename T, int NV>
 __device__ __forceinline__ void ab_update(const T qv[NV], const void *const *hold, const double *alpha, int nold,
-                                          size_t field, size_t p, const T rhs[NV], T qn[NV]) {
+                                          size_t field, size_t p, const T rhs[NV], T qn[NV], int *err) {
   double acc[NV];
 #pragma unroll
   for (int c = 0; c < NV; ++c) acc[c] = to_f64(qv[c]);
@@ -202,6 +221,7 @@ __device__ __forceinline__ void ab_update(const T qv[NV], const void *const *hol
     acc[c] += alpha[nold] * to_f64(rhs[c]);
     qn[c] = (T)acc[c];
   }
+  flag_bad_state<T, NV>(qn, err);
 }
 
 // Products and fused multiply-adds with a fixed rounding (never re-associated or contracted
@@ -726,7 +746,7 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
       T q0[4], qv[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) q0[c] = q[c * m.field + p];
-      ab_update<T, 4>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv);
+      ab_update<T, 4>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv, (code & 15u) != 15u ? a.err : nullptr);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         out[c * m.field + p] = rhs[c];
@@ -822,9 +842,10 @@ __device__ __forceinline__ void donor_group(const DonorLaunch &a, int pair, bool
       }
     }
     if (valid && l == 0) {
-      T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * a.npts;
+      const int st = a.stride ? a.stride : a.npts;
+      T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * st;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) dv[v * a.npts + d] = s[v];
+      for (int v = 0; v < 4; ++v) dv[v * st + d] = s[v];
       const T mu = (T)a.g.mu, kap = (T)(a.g.mu / (a.g.pr * (a.g.gamma - 1.0)));
       T mt[5];
       if (CURV) {
@@ -845,8 +866,8 @@ __device__ __forceinline__ void donor_group(const DonorLaunch &a, int pair, bool
       viscous_flux(pr[0], pr[1], gr, mu, kap, Fv, Gv);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        dv[(4 + c) * a.npts + d] = Fv[c];
-        dv[(7 + c) * a.npts + d] = Gv[c];
+        dv[(4 + c) * st + d] = Fv[c];
+        dv[(7 + c) * st + d] = Gv[c];
       }
     }
   }

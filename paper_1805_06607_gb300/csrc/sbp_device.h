@@ -109,7 +109,7 @@ struct InterpLaunch {
 
 // Values at the distinct donor points of one receiving mesh, for `nsets` extrapolation sets:
 // set s holds q + sum_k beta[s][k] hist[k] (nb[s] terms) and, for Navier-Stokes, the Cartesian
-// viscous fluxes of that state. Output dv[(s * 10 + c) * npts + d].
+// viscous fluxes of that state. Output dv[(s * 10 + c) * S + d], S = stride (npts when 0).
 constexpr int kMaxSets = 16;
 struct DonorLaunch {
   DevMesh d;
@@ -122,6 +122,9 @@ struct DonorLaunch {
   int npts;
   const uint32_t *pts;  // i | j << 16
   void *dv;
+  // plane stride of dv in elements (0: npts), so that several launches can fill the segments
+  // of one receiving mesh's donor values that come from different donor meshes
+  int stride;
 };
 
 // Columns per CTA and threads per CTA of the right-hand-side kernels.

@@ -165,11 +165,12 @@ __global__ void __launch_bounds__(128) k_donor_vals(const DonorLaunch a) {
     const int set = t / a.npts, d = t - set * a.npts;
     const uint32_t ij = a.pts[d];
     const size_t p = (size_t)(ij >> 16) * a.d.pitch + (ij & 0xFFFFu);
-    T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * a.npts;
+    const int st = a.stride ? a.stride : a.npts;
+    T *dv = static_cast<T *>(a.dv) + (size_t)set * 10 * st;
     T s[4];
     set_state(a, set, p, s);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) dv[v * a.npts + d] = s[v];
+    for (int v = 0; v < 4; ++v) dv[v * st + d] = s[v];
   }
 }
 

@@ -370,7 +370,7 @@ __device__ __forceinline__ void march_tile(const RhsLaunch &a, int bx, int by, i
           T q0[4], qv[4];
 #pragma unroll
           for (int c = 0; c < 4; ++c) q0[c] = qr[c * kRing * PW + o];
-          ab_update<T, 4>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv);
+          ab_update<T, 4>(q0, a.hold, a.alpha, a.nold, m.field, p, rhs, qv, (code & 15u) != 15u ? a.err : nullptr);
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             out[c * m.field + p] = rhs[c];

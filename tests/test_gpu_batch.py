@@ -52,14 +52,17 @@ def test_batch_matches_oracle(sbp, dtype):
         ref = OracleSystem(wl)
         H = ref.macro_step_size(wl["q0"])
         Hg, _ = g.mrab_time()
-        assert abs(Hg - H) <= 1e-14 * H
+        # the FP32 form takes its step from its FP32 state; the oracle then runs with that step
+        assert abs(Hg - H) <= (1e-14 if dtype == "f64" else 1e-6) * H
+        H = Hg
         y, hf, hs = ref.bootstrap(wl["q0"], H)
         want, _, _ = ref.mrab(y, hf, hs, H, nsteps)
         q0, sr = wl["q0"], wl["params"]["step_ratio"]
         if dtype == "f64":
             bar, unit, stol = 1e-12, U64, 1e-12
         else:
-            bar = max(fp32_rhs_tol(ref.met[j], q0[j], ref.iblank[j] != 0, ref.coupled_rhs(j, q0[j], q0[1 - j]))
+            bar = max(fp32_rhs_tol(ref.met[j], q0[j], ref.iblank[j] != 0, ref.coupled_rhs(j, q0[j], q0[1 - j]),
+                               ref.mu, ref.pr)
                       for j in range(2))
             unit, stol = U32, 1e-5
         for k in range(2):

@@ -77,7 +77,8 @@ def test_variant_fp32(sbp, scheme):
     g.mrab_step(3)
     g.check()
     q0 = wl["q0"]
-    bar = max(fp32_rhs_tol(ref.met[j], q0[j], ref.iblank[j] != 0, ref.coupled_rhs(j, q0[j], q0[1 - j]))
+    bar = max(fp32_rhs_tol(ref.met[j], q0[j], ref.iblank[j] != 0, ref.coupled_rhs(j, q0[j], q0[1 - j]),
+                               ref.mu, ref.pr)
               for j in range(2))
     sr = wl["params"]["step_ratio"]
     for k in range(2):

@@ -207,7 +207,7 @@ def test_fp32(sbp, case):
         act = ref.iblank[k] != 0
         got = g.to_host(k, g.rhs_eval(k, qd[k], qd[1 - k]))
         want = ref.coupled_rhs(k, wl["q0"][k], wl["q0"][1 - k])
-        tol = fp32_rhs_tol(ref.met[k], wl["q0"][k], act, want)
+        tol = fp32_rhs_tol(ref.met[k], wl["q0"][k], act, want, ref.mu, ref.pr)
         e = rel(got[:, act], want[:, act])
         print("fp32 rhs", case, k, "error %.3e bound %.3e" % (e, tol))
         assert e < tol, (k, e, tol)
@@ -247,7 +247,8 @@ def test_full_size_cylinder_rhs(sbp):
         for k in range(2):
             act = ref.iblank[k] != 0
             got = g.to_host(k, g.rhs_eval(k, qd[k], qd[1 - k]))
-            tol = 1e-12 if dtype == "f64" else fp32_rhs_tol(ref.met[k], wl["q0"][k], act, want[k])
+            tol = 1e-12 if dtype == "f64" else fp32_rhs_tol(ref.met[k], wl["q0"][k], act, want[k],
+                                                                 ref.mu, ref.pr)
             e = rel(got[:, act], want[k][:, act])
             print("full-size rhs", dtype, k, "error %.3e bound %.3e" % (e, tol))
             assert e < tol, (dtype, k, e, tol)
@@ -281,7 +282,8 @@ def test_full_size_cylinder_mrab(sbp, dtype, tol):
         assert e < tol, (dtype, k, e)
         if dtype == "f32" and k == 0:
             continue
-        bar = tol if dtype == "f64" else fp32_rhs_tol(ref.met[k], y[k], act, hs[-1] if k == ref.slow else hf[-1])
+        bar = tol if dtype == "f64" else fp32_rhs_tol(ref.met[k], y[k], act, hs[-1] if k == ref.slow else hf[-1],
+                                                              ref.mu, ref.pr)
         itol = increment_tol(bar, y[k][:, act], want[k][:, act], 2 * sr, U64 if dtype == "f64" else U32)
         ei = rel(got[:, act] - start[k][:, act], want[k][:, act] - y[k][:, act])
         print("full-size increment", dtype, k, "error %.3e bound %.3e" % (ei, itol))

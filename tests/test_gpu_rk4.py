@@ -59,7 +59,8 @@ def test_rk4_matches_oracle(sbp, case, dtype):
         if dtype == "f64":
             bar, unit = 1e-12, U64
         else:
-            bar = max(fp32_rhs_tol(ref.met[j], q0[j], ref.iblank[j] != 0, ref.coupled_rhs(j, q0[j], q0[1 - j]))
+            bar = max(fp32_rhs_tol(ref.met[j], q0[j], ref.iblank[j] != 0, ref.coupled_rhs(j, q0[j], q0[1 - j]),
+                               ref.mu, ref.pr)
                       for j in range(2))
             unit = U32
         ei = rel(got - q0[k][:, act], want[k][:, act] - q0[k][:, act])

@@ -11,7 +11,9 @@
   absolute error of dq/dt is at most (12 + 4) u32 sum_k |c_k| J (|F_xi| + |F_eta|) with
   u32 = 2^-24 and sum_k |c_k| = 3/2 for the interior row; relative to |dq/dt| this is large
   where the flux differences cancel (a nearly uniform flow), which the bound measures case by
-  case from the oracle's state and metrics.
+  case from the oracle's state and metrics. Navier-Stokes adds the rounding of the primitives
+  taken through two derivatives (the gradient, then the divergence of the viscous flux), which
+  grows like |grad xi|^2: large on the finely stretched cells of a wall-resolving mesh.
 """
 import math
 
@@ -41,10 +43,13 @@ def increment_tol(bar, start, want, n_updates, unit):
     return bar + floor
 
 
-def fp32_rhs_bound(met, q, act):
-    """Numerator of the derived FP32 bound (module docstring): 16 u32 (3/2) |J (|F_xi| +
-    |F_eta|)| over the active points, from the state q (4, nj, ni) and the metric planes met
-    (xi_x/J, xi_y/J, eta_x/J, eta_y/J, J)."""
+def fp32_rhs_bound(met, q, act, mu=0.0, pr=0.72):
+    """Numerator of the derived FP32 bound (module docstring), from the state q (4, nj, ni) and
+    the metric planes met (xi_x/J, xi_y/J, eta_x/J, eta_y/J, J), over the active points:
+    the flux term 16 u32 (3/2) J (|F_xi| + |F_eta|), plus, for Navier-Stokes (mu > 0), the
+    rounding of the primitives carried through two derivatives: 16 u32 (3/2)^2
+    (|grad xi| + |grad eta|)^2 mu (4/3 (|u| + |v|)(1 + |u| + |v|) + |T| / (Pr (gamma - 1))), the
+    largest of the momentum and energy viscous terms."""
     rho, mx, my, E = q
     u, v = mx / rho, my / rho
     p = (GAMMA - 1.0) * (E - 0.5 * rho * (u * u + v * v))
@@ -52,12 +57,19 @@ def fp32_rhs_bound(met, q, act):
     G = np.stack([my, my * u, my * v + p, (E + p) * v])
     fx = np.abs(met[0] * F + met[1] * G)
     fe = np.abs(met[2] * F + met[3] * G)
-    return 16.0 * U32 * 1.5 * float(np.linalg.norm((met[4] * (fx + fe))[:, act]))
+    b = 16.0 * U32 * 1.5 * met[4] * (fx + fe)
+    if mu > 0.0:
+        gk = met[4] * (np.hypot(met[0], met[1]) + np.hypot(met[2], met[3]))
+        T = GAMMA * p / rho
+        au, av = np.abs(u), np.abs(v)
+        visc = mu * (4.0 / 3.0 * (au + av) * (1.0 + au + av) + np.abs(T) / (pr * (GAMMA - 1.0)))
+        b = b + 16.0 * U32 * 2.25 * gk * gk * visc
+    return float(np.linalg.norm(b[:, act]))
 
 
-def fp32_rhs_tol(met, q, act, rhs_ref):
+def fp32_rhs_tol(met, q, act, rhs_ref, mu=0.0, pr=0.72):
     """The derived FP32 bound relative to the oracle's right-hand side rhs_ref."""
-    return fp32_rhs_bound(met, q, act) / float(np.linalg.norm(rhs_ref[:, act]))
+    return fp32_rhs_bound(met, q, act, mu, pr) / float(np.linalg.norm(rhs_ref[:, act]))
 
 
 def fp32_rhs_tol_3d(q, h, act, rhs_ref):

@@ -129,6 +129,34 @@ def vortex_box_in_box(seed=0, n_bg=64, n_fine=41, bg_half=5.0, fine_half=1.0, om
     return {"meshes": [bg, fine], "q0": q, "params": params, "vortex": vort, "seed": seed}
 
 
+def vortex_chain(seed=0, n_bg=48, ratios=(2, 2), halves=(5.0, 2.2, 0.9), omega=5.0, phi=1.0, mach=0.5, order=3,
+                 hist_len=None, cfl=0.5, jitter=0.3):
+    """2D Euler vortex on a chain of nested overset meshes, one step ratio per level: a periodic
+    n_bg^2 background on [-halves[0], halves[0]]^2 and boxes [-halves[r], halves[r]]^2 (interface
+    faces) whose spacing is the enclosing mesh's divided by ratios[r-1]; mesh r steps ratios[r-1]
+    times per step of mesh r-1."""
+    rng = np.random.default_rng(seed)
+    hb = 2.0 * halves[0] / n_bg
+    meshes = [cartesian_mesh("background", (n_bg, n_bg), (-halves[0], -halves[0]), (hb, hb), ("periodic",) * 4,
+                             periodic=(True, True))]
+    h = hb
+    for r, ratio in enumerate(ratios, start=1):
+        h = h / ratio
+        n = int(round(2.0 * halves[r] / h)) + 1
+        hr = 2.0 * halves[r] / (n - 1)
+        meshes.append(cartesian_mesh("level%d" % r, (n, n), (-halves[r], -halves[r]), (hr, hr), ("interface",) * 4))
+    c0 = math.sqrt(GAMMA)
+    x0, y0 = rng.uniform(-jitter, jitter, 2)
+    vort = dict(x0=float(x0), y0=float(y0), u0=mach * c0, v0=0.0, omega=omega, phi=phi)
+    q = [vortex_state(m["x"], m["y"], 0.0, gamma=GAMMA, **vort) for m in meshes]
+    params = dict(physics="euler", gamma=GAMMA, mu=0.0, pr=0.72, order=order, hist_len=hist_len or order,
+                  step_ratio=int(ratios[0]), fast_mesh=1, cfl=cfl,
+                  qinf=np.array([1.0, vort["u0"], 0.0, 1.0 / (GAMMA - 1.0) + 0.5 * vort["u0"] ** 2]),
+                  twall=1.0, omega_corner=1.0)
+    return {"meshes": meshes, "q0": q, "params": params, "ratios": [int(r) for r in ratios], "vortex": vort,
+            "seed": seed}
+
+
 def cylinder_overset(seed=0, n_theta=512, n_r=128, r_in=0.5, stretch=1.05, s_bg=0.05,
                      bg_n=(1024, 512), bg_lo=(-12.8, -12.8), mach=0.2, re=200.0, pr=0.72,
                      order=3, hist_len=None, step_ratio=4, cfl=0.5, amp=1e-3, twall=1.0,
