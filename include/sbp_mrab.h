@@ -488,6 +488,54 @@ sbp_status sbp3_set_rhs_kernel(sbp3_system_t sys, int mesh, int kchunk);
  * update and the slow-state extrapolation): exact, equal bit for bit to the hardware
  * conversion for every input, without issuing to the FP64 pipe. */
 sbp_status sbp_f32_to_f64(const void *x, void *y, size_t n, void *stream);
+/* ---- Chains of nested overset meshes, one rate per mesh --------------------------------------
+ * Sec. 3.3: the multi-rate scheme extends to any number of rates (read as the two-rate
+ * fastest-first recursion nested level by level); Sec. 2.2's overset coupling at every level.
+ * meshes[0] is the outermost mesh; meshes[r] (r >= 1) lies inside meshes[r - 1] and cuts a hole
+ * into it (points inside its outer boundary and more than hole_cells spacings of mesh r - 1 from
+ * it). Mesh r's receivers are its interface faces, interpolated from mesh r - 1, and the segment
+ * ends next to the hole mesh r + 1 cuts, interpolated from mesh r + 1 (4 x 4 Lagrange stencils,
+ * interface SAT of eq. (int)). Every mesh but the innermost must be Cartesian; the outermost has
+ * no interface faces. ratios[r] (n_meshes - 1 of them, 1..16, product <= 2^20) is the step of
+ * mesh r over the step of mesh r + 1: with macro step H, mesh r steps H / (ratios[0] ...
+ * ratios[r - 1]). params as for sbp_system_create (step_ratio and fast_mesh are not read; no
+ * sponge layer). Host tables and device tables are owned by the chain. SBP_ERR_SHAPE for a
+ * receiver next to both its outer face and a hole, or an interface face without an enclosing
+ * mesh; SBP_ERR_DONOR for a receiver without a valid stencil. */
+typedef struct sbp_chain_s *sbp_chain_t;
+sbp_status sbp_chain_create(const sbp_mesh_desc *meshes, int n_meshes, const int *ratios, const sbp_params *params,
+                            sbp_chain_t *out);
+sbp_status sbp_chain_destroy(sbp_chain_t chain);
+/* Sizes and layout of mesh r (as sbp_mesh_info_get; hist_bytes for hist_len states). */
+sbp_status sbp_chain_mesh_info(sbp_chain_t chain, int mesh, sbp_mesh_info *info);
+/* Host copies of mesh r's setup (any pointer may be NULL): iblank (ni*nj), receivers (point
+ * index j*ni+i, ascending), donor_mesh (the mesh each receiver reads), donor_base (2 ints) and
+ * donor_w (8 doubles) per receiver, as sbp_get_tables. */
+sbp_status sbp_chain_tables(sbp_chain_t chain, int mesh, signed char *iblank, int *receivers, int *donor_mesh,
+                            int *donor_base, double *donor_w);
+/* dq/dt of mesh r (device, the state layout) with its receivers fed from the states q_all[0..n-1]
+ * (one device state per mesh) as they are. Asynchronous on stream. */
+sbp_status sbp_chain_rhs_eval(sbp_chain_t chain, int mesh, const void *const *q_all, void *rhs, void *stream);
+/* Sec. 4.1's stable step of every mesh without the CFL factor (dt_mesh[n], host) and the macro
+ * step H = min over r of cfl dt_r (ratios[0] ... ratios[r - 1]) (host): every mesh's own step
+ * respects the CFL limit. Synchronises the stream. */
+sbp_status sbp_chain_timestep(sbp_chain_t chain, const void *const *q_all, double *dt_mesh, double *H, void *stream);
+/* Integrator buffers of mesh r (device, caller-owned): two states and a ring of hist_len states. */
+sbp_status sbp_chain_bind(sbp_chain_t chain, int mesh, void *q_a, void *q_b, void *hist);
+sbp_status sbp_chain_current_state(sbp_chain_t chain, int mesh, void **q);
+/* Bootstrap (Heun's RK3 at the innermost step for (hist_len - 1) macro steps of mesh 0, recording
+ * each mesh's right-hand side at its own step) with macro step H (<= 0: from sbp_chain_timestep).
+ * Synchronises the stream. */
+sbp_status sbp_chain_mrab_init(sbp_chain_t chain, double H, void *stream);
+/* n macro steps: for mesh r at the start tau of each of its steps, the donor values (mesh r - 1
+ * extrapolated to tau by the polynomial through its history from the start of its current
+ * step, mesh r + 1 at tau), the right-hand side at tau fused with the Adams-Bashforth update
+ * (FP64 accumulation), then mesh r + 1's steps over the same interval. Asynchronous. */
+sbp_status sbp_chain_mrab_step(sbp_chain_t chain, int n, void *stream);
+sbp_status sbp_chain_mrab_time(sbp_chain_t chain, double *H, double *t);
+/* Synchronise the stream and report (then clear) the chain's device error word. */
+sbp_status sbp_chain_check(sbp_chain_t chain, void *stream);
+
 /* Measurement utility (the paper has no counterpart: it is the denominator of the FP64 roofline
  * that the benchmark reports). Launches one kernel of grid x block threads on stream in which
  * every thread runs 8 independent chains of iters FP64 fused multiply-adds and writes one double

@@ -136,6 +136,18 @@ _SIGS.update({
     "sbp_f32_to_f64": [_P, _P, ctypes.c_size_t, _P],
     "sbp_fp64_rate_probe": [_P, _I, _I, ctypes.c_long, ctypes.POINTER(_D), _P],
     "sbp_barrier_selftest": [_I, _I, ctypes.c_uint, ctypes.POINTER(_I), ctypes.POINTER(_I), _P],
+    "sbp_chain_create": [ctypes.POINTER(MeshDesc), _I, _P, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "sbp_chain_destroy": [_P],
+    "sbp_chain_mesh_info": [_P, _I, ctypes.POINTER(MeshInfo)],
+    "sbp_chain_tables": [_P, _I, _P, _P, _P, _P, _P],
+    "sbp_chain_rhs_eval": [_P, _I, _P, _P, _P],
+    "sbp_chain_timestep": [_P, _P, _P, _P, _P],
+    "sbp_chain_bind": [_P, _I, _P, _P, _P],
+    "sbp_chain_current_state": [_P, _I, ctypes.POINTER(_P)],
+    "sbp_chain_mrab_init": [_P, _D, _P],
+    "sbp_chain_mrab_step": [_P, _I, _P],
+    "sbp_chain_mrab_time": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "sbp_chain_check": [_P, _P],
     "sbp_host_tables_create": [ctypes.POINTER(MeshDesc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "sbp_host_tables_destroy": [_P],
     "sbp_host_tables_get": [_P, _I, _P, _P, _P, _P, _P],
@@ -192,10 +204,10 @@ def _ptr(t):
 
 
 def _descriptors(wl, dtype, sigma_interface, sigma_physical, hole_cells):
-    """C descriptors (sbp_mesh_desc[2], sbp_params) of a workload dict, and the arrays they point
+    """C descriptors (sbp_mesh_desc[n], sbp_params) of a workload dict, and the arrays they point
     into (to be kept alive by the caller)."""
     p = wl["params"]
-    descs = (MeshDesc * 2)()
+    descs = (MeshDesc * len(wl["meshes"]))()
     keep = []
     for k, m in enumerate(wl["meshes"]):
         d = descs[k]
@@ -785,6 +797,108 @@ def f32_to_f64(x, stream=None):
     y = torch.empty(x.shape, dtype=torch.float64, device=x.device)
     _check(_lib.sbp_f32_to_f64(_ptr(x), _ptr(y), x.numel(), _stream(stream)), "sbp_f32_to_f64")
     return y
+
+
+class Chain:
+    """A chain of nested overset meshes, each at its own rate (C ABI sbp_chain_*). ``wl`` is a
+    workload dict with meshes (outermost first), params and ratios (``workloads.vortex_chain``
+    layout). States are numpy arrays (4, nj, ni) or device tensors in the pitched layout."""
+
+    def __init__(self, wl, dtype="f64", sigma_interface=0.5, sigma_physical=1.0, hole_cells=4):
+        import torch
+        self.torch = torch
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        self.params = wl["params"]
+        self.R = len(wl["meshes"])
+        descs, pr, self._keep = _descriptors(wl, dtype, sigma_interface, sigma_physical, hole_cells)
+        ratios = (ctypes.c_int * max(self.R - 1, 1))(*[int(r) for r in wl["ratios"]])
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        _check(_lib.sbp_chain_create(descs, self.R, ctypes.cast(ratios, ctypes.c_void_p), ctypes.byref(pr),
+                                     ctypes.byref(h)), "sbp_chain_create")
+        self.h = h
+        self.info = []
+        for k in range(self.R):
+            inf = MeshInfo()
+            _check(_lib.sbp_chain_mesh_info(self.h, k, ctypes.byref(inf)), "sbp_chain_mesh_info")
+            self.info.append(inf)
+        self.bound = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp_chain_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    empty_state = System.empty_state
+    to_device = System.to_device
+    to_host = System.to_host
+
+    def tables(self, k):
+        inf = self.info[k]
+        n, nr = inf.ni * inf.nj, inf.n_receivers
+        ib = np.zeros(n, np.int8)
+        rec = np.zeros(max(nr, 1), np.int32)
+        src = np.zeros(max(nr, 1), np.int32)
+        base = np.zeros(max(2 * nr, 1), np.int32)
+        w = np.zeros(max(8 * nr, 1))
+        _check(_lib.sbp_chain_tables(self.h, k, ib.ctypes.data, rec.ctypes.data, src.ctypes.data, base.ctypes.data,
+                                     w.ctypes.data), "sbp_chain_tables")
+        return {"iblank": ib.reshape(inf.nj, inf.ni), "receivers": rec[:nr], "donor_mesh": src[:nr],
+                "base": base[:2 * nr].reshape(nr, 2), "w": w[:8 * nr].reshape(nr, 8)}
+
+    def _ptrs(self, qs):
+        return (ctypes.c_void_p * self.R)(*[t.data_ptr() for t in qs])
+
+    def rhs_eval(self, k, qs, out=None, stream=None):
+        if out is None:
+            out = self.empty_state(k)
+        _check(_lib.sbp_chain_rhs_eval(self.h, k, ctypes.cast(self._ptrs(qs), ctypes.c_void_p), _ptr(out),
+                                       _stream(stream)), "sbp_chain_rhs_eval")
+        return out
+
+    def timestep(self, qs, stream=None):
+        dt = (ctypes.c_double * self.R)()
+        H = ctypes.c_double()
+        _check(_lib.sbp_chain_timestep(self.h, ctypes.cast(self._ptrs(qs), ctypes.c_void_p),
+                                       ctypes.cast(dt, ctypes.c_void_p), ctypes.cast(ctypes.pointer(H), ctypes.c_void_p),
+                                       _stream(stream)), "sbp_chain_timestep")
+        return list(dt), H.value
+
+    def bind(self, q_host):
+        self.bound = []
+        for k in range(self.R):
+            qa = self.to_device(k, q_host[k])
+            qb = self.empty_state(k)
+            hist = self.empty_state(k, n=self.params["hist_len"]) if self.params["hist_len"] > 1 else \
+                self.empty_state(k)[None]
+            _check(_lib.sbp_chain_bind(self.h, k, _ptr(qa), _ptr(qb), _ptr(hist)), "sbp_chain_bind")
+            self.bound.append((qa, qb, hist))
+
+    def current_state(self, k):
+        p = ctypes.c_void_p()
+        _check(_lib.sbp_chain_current_state(self.h, k, ctypes.byref(p)), "sbp_chain_current_state")
+        qa, qb, _ = self.bound[k]
+        return qa if p.value == qa.data_ptr() else qb
+
+    def mrab_init(self, H=0.0, stream=None):
+        _check(_lib.sbp_chain_mrab_init(self.h, float(H), _stream(stream)), "sbp_chain_mrab_init")
+
+    def mrab_step(self, n=1, stream=None):
+        _check(_lib.sbp_chain_mrab_step(self.h, int(n), _stream(stream)), "sbp_chain_mrab_step")
+
+    def mrab_time(self):
+        H, t = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.sbp_chain_mrab_time(self.h, ctypes.byref(H), ctypes.byref(t)), "sbp_chain_mrab_time")
+        return H.value, t.value
+
+    def check(self, stream=None):
+        _check(_lib.sbp_chain_check(self.h, _stream(stream)), "sbp_chain_check")
 
 
 def barrier_selftest(grid, arrivals, max_spins, stream=None):

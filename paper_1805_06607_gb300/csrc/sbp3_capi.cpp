@@ -219,7 +219,11 @@ struct sbp3_system_s {
       if (e == cudaSuccess) e = cudaMalloc(&ystage[k], b);
       if (e == cudaSuccess) e = cudaMalloc(&k1tmp[k], b);
       if (e == cudaSuccess) e = cudaMalloc(&k23[k], b);
+      // zeroed: the right-hand sides leave the padding columns unwritten, and the stage updates
+      // run over the whole pitched arrays
       if (e == cudaSuccess) e = cudaMemsetAsync(ystage[k], 0, b, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(k1tmp[k], 0, b, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(k23[k], 0, b, s);
       md[k].head = -1;
     }
     const int nsteps = (m - 1) * sr;
@@ -361,10 +365,15 @@ sbp_status sbp3_system_create(const sbp3_mesh_desc *meshes, int n_meshes, const 
       for (int j = 0; j < nj; ++j)
         std::memcpy(&cls[((size_t)kk * nj + j) * m.pitch], &m.cls[((size_t)kk * nj + j) * ni], ni * sizeof(uint16_t));
     CUDA_TRY(up3(d.cls, cls.data(), fld * sizeof(uint16_t)));
-    if (S->viscous()) CUDA_TRY(cudaMalloc(&d.prim, 4 * fld * S->esz));
+    if (S->viscous()) {
+      CUDA_TRY(cudaMalloc(&d.prim, 4 * fld * S->esz));
+      CUDA_TRY(cudaMemset(d.prim, 0, 4 * fld * S->esz));
+    }
     CUDA_TRY(cudaMalloc(&d.flux, 15 * fld * S->esz));
+    CUDA_TRY(cudaMemset(d.flux, 0, 15 * fld * S->esz));
     const size_t ns = m.sat_pt.size(), nr = m.recv_pt.size();
     CUDA_TRY(cudaMalloc(&d.sat, (5 * ns + 1) * S->esz));
+    CUDA_TRY(cudaMemset(d.sat, 0, (5 * ns + 1) * S->esz));
     CUDA_TRY(up3(d.sat_pt, m.sat_pt.data(), ns * sizeof(int64_t)));
     CUDA_TRY(up3(d.sat_code, m.sat_code.data(), ns * sizeof(uint32_t)));
     CUDA_TRY(up3(d.sat_recv, m.sat_recv.data(), ns * sizeof(int)));
@@ -384,6 +393,7 @@ sbp_status sbp3_system_create(const sbp3_mesh_desc *meshes, int n_meshes, const 
       CUDA_TRY(up3(d.dwt, wf.data(), wf.size() * sizeof(float)));
     }
     CUDA_TRY(cudaMalloc(&d.dv, ((size_t)d.dv_sets * kRv3 * d.ndv + 1) * S->esz));
+    CUDA_TRY(cudaMemset(d.dv, 0, ((size_t)d.dv_sets * kRv3 * d.ndv + 1) * S->esz));
   }
   CUDA_TRY(cudaDeviceSynchronize());
   *out = guard.release();

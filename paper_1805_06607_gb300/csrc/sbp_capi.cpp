@@ -113,6 +113,95 @@ sbp_status sbp_host_tables_plan(sbp_host_tables_t T, double *ab, double *ext, in
   return SBP_OK;
 }
 
+}  // extern "C"
+
+// Device tables of mesh k of a system (class map, metrics, SAT lists by tile, donor tables and
+// workspaces) from its host setup; used by system creation and by the chains of nested meshes.
+sbp_status sbp::upload_mesh_tables(sbp_system_s *S, int k) {
+  const sbp_params &p = S->p;
+  MeshHost &m = S->mh[k];
+  MeshDev &d = S->md[k];
+  size_t field = (size_t)m.pitch * m.nj;
+  std::vector<uint8_t> cls(field, 0xFF);
+  for (int j = 0; j < m.nj; ++j)
+    std::memcpy(&cls[(size_t)j * m.pitch], &m.cls[(size_t)j * m.ni], m.ni);
+  CUDA_TRY(upload(d.cls, cls.data(), field));
+  if (!m.cartesian) {
+    CUDA_TRY(cudaMalloc(&d.met, 5 * field * S->esz));
+    CUDA_TRY(cudaMemset(d.met, 0, 5 * field * S->esz));
+    double *dx = nullptr, *dy = nullptr;
+    CUDA_TRY(upload(dx, m.x.data(), m.x.size() * sizeof(double)));
+    CUDA_TRY(upload(dy, m.y.data(), m.y.size() * sizeof(double)));
+    DevMesh dm = S->dev_mesh(k);
+    cudaError_t e = launch_metrics(dm, dx, dy, m.shift, d.met, p.dtype, 0);
+    cudaError_t e2 = cudaDeviceSynchronize();
+    cudaFree(dx);
+    cudaFree(dy);
+    CUDA_TRY(e);
+    CUDA_TRY(e2);
+  }
+  // SAT points grouped by 32 x 8 tile, tiles in column-major order so that the tiles of a
+  // taller CTA (16 or 32 rows) are contiguous
+  const int ntx = (m.ni + kTileX - 1) / kTileX, nty8 = (m.nj + 7) / 8;
+  size_t ns = m.sat_pt.size();
+  std::vector<int> order(ns);
+  for (size_t s = 0; s < ns; ++s) order[s] = (int)s;
+  auto tile_of = [&](int pt) { return ((pt % m.ni) / kTileX) * nty8 + (pt / m.ni) / 8; };
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return tile_of(m.sat_pt[a]) < tile_of(m.sat_pt[b]); });
+  std::vector<int> toff((size_t)ntx * nty8 + 1, 0);
+  std::vector<uint32_t> ij(ns), code(ns);
+  std::vector<int> recv(ns);
+  std::vector<double> scale(ns);
+  for (size_t s = 0; s < ns; ++s) {
+    int o = order[s], pt = m.sat_pt[o];
+    toff[tile_of(pt) + 1]++;
+    ij[s] = (uint32_t)(pt % m.ni) | ((uint32_t)(pt / m.ni) << 16);
+    code[s] = m.sat_code[o];
+    recv[s] = m.sat_recv[o];
+    scale[s] = m.sat_scale[o];
+  }
+  for (size_t t = 0; t + 1 < toff.size(); ++t) toff[t + 1] += toff[t];
+  CUDA_TRY(upload(d.tile_sat, toff.data(), toff.size() * sizeof(int)));
+  // workspaces start zeroed: entries no kernel writes (padding columns, holes) never carry stale
+  // device memory into a result
+  CUDA_TRY(cudaMalloc(&d.flux, 8 * field * S->esz));
+  CUDA_TRY(cudaMemset(d.flux, 0, 8 * field * S->esz));
+  d.rows_per_cta = d.e_rows = 16;
+  if (p.physics == SBP_NS && k == p.fast_mesh) {
+    CUDA_TRY(cudaMalloc(&d.prim, 3 * field * S->esz));
+    CUDA_TRY(cudaMemset(d.prim, 0, 3 * field * S->esz));
+  }
+  CUDA_TRY(upload(d.sat_ij, ij.data(), ns * sizeof(uint32_t)));
+  CUDA_TRY(upload(d.sat_code, code.data(), ns * sizeof(uint32_t)));
+  CUDA_TRY(upload(d.sat_recv, recv.data(), ns * sizeof(int)));
+  CUDA_TRY(upload(d.sat_scale, scale.data(), ns * sizeof(double)));
+  size_t nr = m.recv_pt.size();
+  CUDA_TRY(upload(d.base, m.donor_base.data(), 2 * nr * sizeof(int)));
+  CUDA_TRY(upload(d.w, m.donor_w.data(), 8 * nr * sizeof(double)));
+  if (p.dtype == SBP_F64) {
+    CUDA_TRY(upload(d.wt, m.donor_w.data(), 8 * nr * sizeof(double)));
+  } else {
+    std::vector<float> wf(m.donor_w.begin(), m.donor_w.end());
+    CUDA_TRY(upload(d.wt, wf.data(), wf.size() * sizeof(float)));
+  }
+  CUDA_TRY(cudaMalloc(&d.sat, (4 * ns + 1) * S->esz));
+  CUDA_TRY(cudaMemset(d.sat, 0, (4 * ns + 1) * S->esz));
+  CUDA_TRY(cudaMalloc(&d.qhat, (4 * nr + 1) * S->esz));
+  CUDA_TRY(cudaMemset(d.qhat, 0, (4 * nr + 1) * S->esz));
+  CUDA_TRY(cudaMalloc(&d.fvhat, (6 * nr + 1) * S->esz));
+  CUDA_TRY(cudaMemset(d.fvhat, 0, (6 * nr + 1) * S->esz));
+  d.ndv = (int)m.donor_pts.size();
+  d.dv_sets = k == p.fast_mesh ? p.step_ratio : 1;
+  CUDA_TRY(upload(d.dpts, m.donor_pts.data(), m.donor_pts.size() * sizeof(uint32_t)));
+  CUDA_TRY(upload(d.didx, m.donor_idx.data(), m.donor_idx.size() * sizeof(int)));
+  CUDA_TRY(cudaMalloc(&d.dv, ((size_t)d.dv_sets * 10 * d.ndv + 1) * S->esz));
+  CUDA_TRY(cudaMemset(d.dv, 0, ((size_t)d.dv_sets * 10 * d.ndv + 1) * S->esz));
+  return SBP_OK;
+}
+
+extern "C" {
+
 sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sbp_params *params,
                              sbp_system_t *out) {
   if (!meshes || !params || !out) return fail(SBP_ERR_ARG, "null argument");
@@ -129,76 +218,8 @@ sbp_status sbp_system_create(const sbp_mesh_desc *meshes, int n_meshes, const sb
   CUDA_TRY(cudaMemset(S->d_err, 0, sizeof(int)));
   CUDA_TRY(cudaMalloc((void **)&S->d_dt, 2 * sizeof(unsigned long long)));
   for (int k = 0; k < 2; ++k) {
-    MeshHost &m = S->mh[k];
-    MeshDev &d = S->md[k];
-    size_t field = (size_t)m.pitch * m.nj;
-    std::vector<uint8_t> cls(field, 0xFF);
-    for (int j = 0; j < m.nj; ++j)
-      std::memcpy(&cls[(size_t)j * m.pitch], &m.cls[(size_t)j * m.ni], m.ni);
-    CUDA_TRY(upload(d.cls, cls.data(), field));
-    if (!m.cartesian) {
-      CUDA_TRY(cudaMalloc(&d.met, 5 * field * S->esz));
-      double *dx = nullptr, *dy = nullptr;
-      CUDA_TRY(upload(dx, m.x.data(), m.x.size() * sizeof(double)));
-      CUDA_TRY(upload(dy, m.y.data(), m.y.size() * sizeof(double)));
-      DevMesh dm = S->dev_mesh(k);
-      cudaError_t e = launch_metrics(dm, dx, dy, m.shift, d.met, p.dtype, 0);
-      cudaError_t e2 = cudaDeviceSynchronize();
-      cudaFree(dx);
-      cudaFree(dy);
-      CUDA_TRY(e);
-      CUDA_TRY(e2);
-    }
-    // SAT points grouped by 32 x 8 tile, tiles in column-major order so that the tiles of a
-    // taller CTA (16 or 32 rows) are contiguous
-    const int ntx = (m.ni + kTileX - 1) / kTileX, nty8 = (m.nj + 7) / 8;
-    size_t ns = m.sat_pt.size();
-    std::vector<int> order(ns);
-    for (size_t s = 0; s < ns; ++s) order[s] = (int)s;
-    auto tile_of = [&](int pt) { return ((pt % m.ni) / kTileX) * nty8 + (pt / m.ni) / 8; };
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return tile_of(m.sat_pt[a]) < tile_of(m.sat_pt[b]); });
-    std::vector<int> toff((size_t)ntx * nty8 + 1, 0);
-    std::vector<uint32_t> ij(ns), code(ns);
-    std::vector<int> recv(ns);
-    std::vector<double> scale(ns);
-    for (size_t s = 0; s < ns; ++s) {
-      int o = order[s], pt = m.sat_pt[o];
-      toff[tile_of(pt) + 1]++;
-      ij[s] = (uint32_t)(pt % m.ni) | ((uint32_t)(pt / m.ni) << 16);
-      code[s] = m.sat_code[o];
-      recv[s] = m.sat_recv[o];
-      scale[s] = m.sat_scale[o];
-    }
-    for (size_t t = 0; t + 1 < toff.size(); ++t) toff[t + 1] += toff[t];
-    CUDA_TRY(upload(d.tile_sat, toff.data(), toff.size() * sizeof(int)));
-    CUDA_TRY(cudaMalloc(&d.flux, 8 * field * S->esz));
-    d.rows_per_cta = d.e_rows = 16;
-    if (p.physics == SBP_NS && k == p.fast_mesh) {
-      CUDA_TRY(cudaMalloc(&d.prim, 3 * field * S->esz));
-      CUDA_TRY(cudaMemset(d.prim, 0, 3 * field * S->esz));
-    }
-    CUDA_TRY(upload(d.sat_ij, ij.data(), ns * sizeof(uint32_t)));
-    CUDA_TRY(upload(d.sat_code, code.data(), ns * sizeof(uint32_t)));
-    CUDA_TRY(upload(d.sat_recv, recv.data(), ns * sizeof(int)));
-    CUDA_TRY(upload(d.sat_scale, scale.data(), ns * sizeof(double)));
-    size_t nr = m.recv_pt.size();
-    CUDA_TRY(upload(d.base, m.donor_base.data(), 2 * nr * sizeof(int)));
-    CUDA_TRY(upload(d.w, m.donor_w.data(), 8 * nr * sizeof(double)));
-    if (p.dtype == SBP_F64) {
-      CUDA_TRY(upload(d.wt, m.donor_w.data(), 8 * nr * sizeof(double)));
-    } else {
-      std::vector<float> wf(m.donor_w.begin(), m.donor_w.end());
-      CUDA_TRY(upload(d.wt, wf.data(), wf.size() * sizeof(float)));
-    }
-    CUDA_TRY(cudaMalloc(&d.sat, (4 * ns + 1) * S->esz));
-    CUDA_TRY(cudaMalloc(&d.qhat, (4 * nr + 1) * S->esz));
-    CUDA_TRY(cudaMalloc(&d.fvhat, (6 * nr + 1) * S->esz));
-    d.ndv = (int)m.donor_pts.size();
-    d.dv_sets = k == p.fast_mesh ? p.step_ratio : 1;
-    CUDA_TRY(upload(d.dpts, m.donor_pts.data(), m.donor_pts.size() * sizeof(uint32_t)));
-    CUDA_TRY(upload(d.didx, m.donor_idx.data(), m.donor_idx.size() * sizeof(int)));
-    CUDA_TRY(cudaMalloc(&d.dv, ((size_t)d.dv_sets * 10 * d.ndv + 1) * S->esz));
+    sbp_status st2 = upload_mesh_tables(S, k);
+    if (st2 != SBP_OK) return st2;
   }
   CUDA_TRY(cudaDeviceSynchronize());
   *out = guard.release();

@@ -745,7 +745,11 @@ struct sbp_system_s {
       if (e == cudaSuccess) e = cudaMalloc(&ystage[k], b);
       if (e == cudaSuccess) e = cudaMalloc(&k1tmp[k], b);
       if (e == cudaSuccess) e = cudaMalloc(&k23[k], b);
+      // zeroed: the right-hand sides leave the padding columns unwritten, and the stage updates
+      // run over the whole pitched arrays
       if (e == cudaSuccess) e = cudaMemsetAsync(ystage[k], 0, b, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(k1tmp[k], 0, b, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(k23[k], 0, b, s);
       md[k].head = -1;
       md[k].count = 0;
     }
@@ -889,3 +893,8 @@ struct sbp_system_s {
     return cudaGraphLaunch(it->second, s);
   }
 };
+
+namespace sbp {
+// Device tables of mesh k of S from its host setup (sbp_capi.cpp).
+sbp_status upload_mesh_tables(sbp_system_s *S, int k);
+}  // namespace sbp
