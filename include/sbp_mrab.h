@@ -240,13 +240,15 @@ sbp_status sbp_mrab_set_step(sbp_system_t sys, double H);
  * (sbp_profile_enable) force the kernel-by-kernel mode while they are on. */
 sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
 
-/* Autotuner of the right-hand side's kernel and block shape. Two kernel designs compute the
+/* Autotuner of the right-hand side's kernel and block shape. Three kernel designs compute the
  * same bits: a pair (contravariant fluxes of a 32 x rows tile with a halo-3 primitive tile in
- * shared memory, then derivatives + SAT + update from a halo-3 flux tile; 8, 16 or 32 rows per
- * CTA), and a single pass that marches a strip of 58 columns up a chunk of 8, 16, 32, 64 or 128
+ * shared memory, then derivatives + SAT + update from a halo-3 flux tile; 4, 8, 16 or 32 rows per
+ * CTA); a single pass that marches a strip of 58 columns up a chunk of 8, 16, 32, 64 or 128
  * rows, 4 rows per step, with 16-row ring buffers of state, metrics, class bytes (copied one
  * step ahead with cp.async), primitives and fluxes in shared memory (state, metrics and result
- * cross HBM once). For each mesh the autotuner times every candidate on the bound state, as
+ * cross HBM once); and a column-marching single pass (one mesh column per thread, strips of 116
+ * or 244 columns, chunks of 32 to 256 rows, one row per step, the j-direction stencil taps in
+ * per-thread register windows and one shared-memory row per stage for the i-direction ones). For each mesh the autotuner times every candidate on the bound state, as
  * the fused right-hand side + MRAB update of the next macro step (its outputs go to the state
  * buffer that step overwrites; the history is only read), and keeps the fastest (reported by
  * sbp_mesh_info_get). It runs at the end of sbp_mrab_init
@@ -255,9 +257,12 @@ sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
 sbp_status sbp_autotune(sbp_system_t sys, int enable, void *stream);
 
 /* Choose the right-hand-side kernel of `mesh` by hand (the autotuner's choice otherwise): strip
- * = 0 selects the kernel pair with rows & 0xFF = 8, 16 or 32 rows per CTA of the flux kernel
- * and rows >> 8 = 4, 8, 16 or 32 rows of the derivative kernel (0: the same); strip = 64 the single-pass
- * marching kernel with chunks of `rows` rows (1..65535). Both give the same bits.
+ * = 0 selects the kernel pair with rows & 0xFF = 4, 8, 16 or 32 rows per CTA of the flux kernel
+ * and rows >> 8 = 4, 8, 16 or 32 rows of the derivative kernel (0: the same); strip = 58 the
+ * single-pass marching kernel with chunks of `rows` rows (1..65535); strip = 116 or 244 the
+ * column-marching kernel (one column per thread, CTAs of 128 or 256 threads, the j-direction
+ * stencils from per-thread register windows; meshes at least 128 or 256 points wide) with chunks
+ * of `rows` rows. All give the same bits.
  * Later autotuner runs (sbp_mrab_init, sbp_autotune) override the choice; disable the
  * autotuner (sbp_autotune(sys, 0, stream)) to keep it. */
 sbp_status sbp_set_rhs_shape(sbp_system_t sys, int mesh, int strip, int rows);

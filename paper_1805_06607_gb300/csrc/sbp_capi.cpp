@@ -535,14 +535,20 @@ sbp_status sbp_set_rhs_shape(sbp_system_t S, int k, int strip, int rows) {
   MeshDev &d = S->md[k];
   if (strip == 0) {
     const int rf = rows & 0xFF, ru = rows >> 8;
-    if (rf != 8 && rf != 16 && rf != 32) return fail(SBP_ERR_ARG, "split kernels take 8, 16 or 32 rows per CTA");
+    if (rf != 4 && rf != 8 && rf != 16 && rf != 32)
+      return fail(SBP_ERR_ARG, "split kernels take 4, 8, 16 or 32 rows per CTA");
     if (ru != 0 && ru != 4 && ru != 8 && ru != 16 && ru != 32)
       return fail(SBP_ERR_ARG, "the derivative kernel takes 4, 8, 16 or 32 rows per CTA");
     d.strip = d.e_strip = 0;
     d.rows_per_cta = d.e_rows = rf;
     d.rows_upd = d.e_rows_upd = ru;
   } else {
-    if (strip != kMarchW) return fail(SBP_ERR_ARG, "the marching kernel takes strips of " + std::to_string(kMarchW) + " columns");
+    if (strip != kMarchW && strip != kColW128 && strip != kColW256)
+      return fail(SBP_ERR_ARG, "single-pass strips are " + std::to_string(kMarchW) + " (marching kernel), " +
+                                   std::to_string(kColW128) + " or " + std::to_string(kColW256) +
+                                   " (column-marching kernel) columns wide");
+    if (strip != kMarchW && S->mh[k].ni < strip + 12)
+      return fail(SBP_ERR_ARG, "the column-marching kernel needs a mesh at least as wide as its CTA");
     if (rows < 1 || rows > 65535) return fail(SBP_ERR_ARG, "chunk rows out of range");
     d.strip = d.e_strip = strip;
     d.chunk = d.e_chunk = rows;

@@ -554,7 +554,8 @@ __device__ __forceinline__ void tile_sat_range(const RhsLaunch &a, int bx, int b
 
 template <typename T, bool VISC, int TY>
 struct FluxTile {
-  static constexpr int TX = kTileX, NT = kNT, PPT = TX * TY / NT;
+  // one point per thread up to 8 rows (128 threads for 4-row tiles), kNT threads beyond
+  static constexpr int TX = kTileX, NT = TX * TY < kNT ? TX * TY : kNT, PPT = TX * TY / NT;
   static constexpr int H = VISC ? 3 : 0, RX = TX + 2 * H, RY = TY + 2 * H, RN = RX * RY;
 };
 
@@ -641,6 +642,8 @@ __device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T 
   for (int s = s0 + tid; s < s1; s += NT) {
     uint32_t ij = a.sat_ij[s];
     int gi = (int)(ij & 0xFFFFu), gj = (int)(ij >> 16);
+    // tiles of fewer than 8 rows share their 8-row group's SAT range: each takes its own rows
+    if (TY < 8 && (gj < j0 || gj >= j0 + TY)) continue;
     size_t p = (size_t)gj * m.pitch + gi;
     T qp[4] = {q[p], q[m.field + p], q[2 * m.field + p], q[3 * m.field + p]};
     T mt[5];

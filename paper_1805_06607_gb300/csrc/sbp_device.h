@@ -132,6 +132,9 @@ constexpr int kTileX = 32;
 // Columns of a single-pass (marching) strip: 256 threads cover 4 rows of its 64-column flux
 // window (the strip plus a 3-point halo per side) in one pass.
 constexpr int kMarchW = 58;
+// Output columns of the column-marching kernel's strips (CTAs of 128 or 256 threads, one column
+// per thread, 6 halo columns per side); it needs meshes at least as wide as its CTA.
+constexpr int kColW128 = 128 - 12, kColW256 = 256 - 12;
 constexpr int kNT = 256;
 
 // One micro step of a batch of systems (a cooperative launch): donor values of the listed

@@ -9,13 +9,15 @@
 
 #include "sbp_dev.cuh"
 #include "sbp_march_impl.cuh"
+#include "sbp_col_impl.cuh"
 
 namespace sbp {
 
 // At least 4 (FP32) / 3 (FP64) resident CTAs per SM: caps the registers that the SAT tail
 // (taken by boundary tiles only) would otherwise claim for the whole kernel.
 template <typename T, bool VISC, bool CURV, int TY>
-__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 4 : 3) k_flux(const RhsLaunch a) {
+__global__ void __launch_bounds__(FluxTile<T, VISC, TY>::NT, (sizeof(T) == 4 ? 4 : 3) * kNT / FluxTile<T, VISC, TY>::NT)
+    k_flux(const RhsLaunch a) {
   using F = FluxTile<T, VISC, TY>;
   __shared__ T prim[VISC ? 3 * F::RN : 1];
   __shared__ uint8_t scls[VISC ? F::RN : 1];
@@ -31,7 +33,7 @@ __global__ void __launch_bounds__(UpdTile<T, TY>::NT) k_update(const RhsLaunch a
 template <typename T, bool VISC, bool CURV, int TY>
 static cudaError_t launch_flux_t(const RhsLaunch &a, cudaStream_t s) {
   dim3 grid((a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
-  k_flux<T, VISC, CURV, TY><<<grid, kNT, 0, s>>>(a);
+  k_flux<T, VISC, CURV, TY><<<grid, FluxTile<T, VISC, TY>::NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -50,12 +52,13 @@ static cudaError_t launch_update_t(const RhsLaunch &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// The flux kernel with rows_per_cta (8, 16, 32) rows per CTA, then the update kernel with
+// The flux kernel with rows_per_cta (4, 8, 16, 32) rows per CTA, then the update kernel with
 // rows_upd (4, 8, 16, 32; 0: the same).
 template <typename T, bool VISC, bool CURV>
 static cudaError_t launch_rhs_ty(const RhsLaunch &a, cudaStream_t s) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (a.rows_per_cta) {
+    case 4: e = launch_flux_t<T, VISC, CURV, 4>(a, s); break;
     case 8: e = launch_flux_t<T, VISC, CURV, 8>(a, s); break;
     case 16: e = launch_flux_t<T, VISC, CURV, 16>(a, s); break;
     case 32: e = launch_flux_t<T, VISC, CURV, 32>(a, s); break;
@@ -74,6 +77,10 @@ static cudaError_t launch_rhs_ty(const RhsLaunch &a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_rhs_typed(const RhsLaunch &a, bool viscous, cudaStream_t s) {
   bool curv = !a.m.cart;
+  if (a.strip == kColW128 || a.strip == kColW256) {
+    if (viscous) return curv ? launch_col_w<T, true, true>(a, s) : launch_col_w<T, true, false>(a, s);
+    return curv ? launch_col_w<T, false, true>(a, s) : launch_col_w<T, false, false>(a, s);
+  }
   if (a.strip) {
     if (viscous) return curv ? launch_march_w<T, true, true>(a, s) : launch_march_w<T, true, false>(a, s);
     return curv ? launch_march_w<T, false, true>(a, s) : launch_march_w<T, false, false>(a, s);

@@ -80,7 +80,7 @@ def test_pair_row_splits_bit_identical(sbp, case, dtype):
     wl = CASES[case]()
     g = sbp.System(wl, dtype=dtype)
     q = [g.to_device(k, wl["q0"][k]) for k in range(2)]
-    splits = [(8, 4), (16, 4), (16, 8), (32, 16), (32, 4)]
+    splits = [(8, 4), (16, 4), (16, 8), (32, 16), (32, 4), (4, 4), (4, 8)]
     for k in range(2):
         g.set_rhs_shape(k, 0, 16)
         ref = g.rhs_eval(k, q[k], q[1 - k]).clone()
@@ -139,7 +139,7 @@ def test_autotuner_reports_a_candidate(sbp):
             if sp:
                 assert sw == 58 and rows in (8, 16, 32, 64, 128)
             else:
-                assert sw == 32 and rows in (8, 16, 32)
+                assert sw == 32 and rows in (4, 8, 16, 32)
     # the autotuner's choices give the same bits as any other shape: rhs_eval and a macro step
     # against a fixed kernel pair
     q = [g.to_device(k, wl["q0"][k]) for k in range(2)]
@@ -165,3 +165,65 @@ def test_bad_shapes_rejected(sbp):
     for args in [(0, 12), (48, 32), (32, 32), (64, 32), (58, 0), (58, -3), (0, 16 | (12 << 8))]:
         with pytest.raises(sbp.SbpError):
             g.set_rhs_shape(0, *args)
+
+
+COL_CASES = {
+    "vortex_wide": lambda: W.vortex_box_in_box(seed=38, n_bg=160, n_fine=130),
+    "cylinder_wide": lambda: W.cylinder_small(seed=39, n_theta=256, n_r=40, bg_n=(270, 150), s_bg=0.04),
+    "cylinder_wide_euler": lambda: _euler(W.cylinder_small(seed=40, n_theta=256, n_r=40, bg_n=(270, 150), s_bg=0.04)),
+    "mms_viscous_wide": lambda: W.mms_box_in_box(260, "viscous"),
+}
+
+
+@pytest.mark.parametrize("case", sorted(COL_CASES))
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_column_kernel_bit_identical(sbp, case, dtype):
+    """The column-marching kernel (128- and 256-thread CTAs, chunks that are and are not
+    multiples of 8 rows, chunks taller than the mesh) against the kernel pair, bit for bit, on
+    right-hand sides and on MRAB runs; FP64 also against the oracle."""
+    wl = COL_CASES[case]()
+    g = sbp.System(wl, dtype=dtype)
+    g.autotune(False)
+    q = [g.to_device(k, wl["q0"][k]) for k in range(2)]
+    shapes = [(116, 32), (116, 45), (244, 64), (244, 1000)]
+    tried = 0
+    for k in range(2):
+        g.set_rhs_shape(k, 0, 16)
+        ref = g.rhs_eval(k, q[k], q[1 - k]).clone()
+        for strip, rows in shapes:
+            if g.info[k].ni < strip + 12:
+                with pytest.raises(sbp.SbpError):
+                    g.set_rhs_shape(k, strip, rows)
+                continue
+            g.set_rhs_shape(k, strip, rows)
+            info = g.mesh_info(k)
+            assert info.single_pass == 1 and info.strip_width == strip
+            assert torch.equal(g.rhs_eval(k, q[k], q[1 - k]), ref), (k, strip, rows)
+            tried += 1
+    assert tried >= 2
+    if dtype == "f64":
+        o = OracleSystem(wl)
+        for k in range(2):
+            if g.info[k].ni >= 128:
+                g.set_rhs_shape(k, 116, 40)
+            got = g.to_host(k, g.rhs_eval(k, q[k], q[1 - k]))
+            want = o.coupled_rhs(k, wl["q0"][k], wl["q0"][1 - k])
+            act = o.iblank[k] != 0
+            assert _rel(got[:, act], want[:, act]) < 1e-12
+    g.close()
+    runs = []
+    for shape in [(0, 16), (116, 40), (244, 64)]:
+        g = sbp.System(wl, dtype=dtype)
+        g.autotune(False)
+        for k in range(2):
+            if shape[0] == 0 or g.info[k].ni >= shape[0] + 12:
+                g.set_rhs_shape(k, *shape)
+        g.bind(wl["q0"])
+        g.mrab_init()
+        g.mrab_step(5)
+        g.check()
+        runs.append([g.current_state(k).clone() for k in range(2)])
+        g.close()
+    for r in runs[1:]:
+        for k in range(2):
+            assert torch.equal(r[k], runs[0][k])

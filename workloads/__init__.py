@@ -160,10 +160,12 @@ def vortex_chain(seed=0, n_bg=48, ratios=(2, 2), halves=(5.0, 2.2, 0.9), omega=5
 def cylinder_overset(seed=0, n_theta=512, n_r=128, r_in=0.5, stretch=1.05, s_bg=0.05,
                      bg_n=(1024, 512), bg_lo=(-12.8, -12.8), mach=0.2, re=200.0, pr=0.72,
                      order=3, hist_len=None, step_ratio=4, cfl=0.5, amp=1e-3, twall=1.0,
-                     sponge_cells=0, sponge_strength=1.0):
+                     sponge_cells=0, sponge_strength=1.0, pulse_amp=0.0, pulse_at=(-1.2, 0.3), pulse_width=0.4):
     """2D Navier-Stokes cylinder in cross-flow: O-grid (wall inside, interface outside) on a
     Cartesian background with far-field faces. The first radial spacing is chosen so that the
-    outermost O-grid spacing equals the background spacing."""
+    outermost O-grid spacing equals the background spacing. The state is the free stream plus
+    amp N(0,1) noise per point, plus (pulse_amp > 0) a smooth pressure pulse
+    p (1 + pulse_amp exp(-|x - pulse_at|^2 / pulse_width^2)) at fixed density."""
     rng = np.random.default_rng(seed)
     dr0 = s_bg / stretch ** (n_r - 2)
     og = ogrid_mesh("ogrid", n_theta, n_r, r_in, dr0, stretch)
@@ -171,6 +173,11 @@ def cylinder_overset(seed=0, n_theta=512, n_r=128, r_in=0.5, stretch=1.05, s_bg=
     qinf = freestream(mach)
     q_og = noisy_uniform((n_r, n_theta), qinf, amp, rng)
     q_bg = noisy_uniform((bg_n[1], bg_n[0]), qinf, amp, rng)
+    if pulse_amp > 0.0:
+        p_inf = (GAMMA - 1.0) * (qinf[3] - 0.5 * (qinf[1] ** 2 + qinf[2] ** 2) / qinf[0])
+        for m, q in ((og, q_og), (bg, q_bg)):
+            r2 = (m["x"] - pulse_at[0]) ** 2 + (m["y"] - pulse_at[1]) ** 2
+            q[3] += p_inf * pulse_amp * np.exp(-r2 / pulse_width ** 2) / (GAMMA - 1.0)
     params = dict(physics="ns", gamma=GAMMA, mu=mach / re, pr=pr, order=order,
                   hist_len=hist_len or order, step_ratio=step_ratio, fast_mesh=1, cfl=cfl,
                   qinf=qinf, twall=twall, omega_corner=1.0, sponge_cells=sponge_cells,
