@@ -69,13 +69,22 @@ def d_matrix(n):
 
 class Curvilinear3D:
     """One structured mesh with node coordinates x, y, z (each (nk, nj, ni)), non-periodic in
-    every direction."""
+    every direction.
 
-    def __init__(self, x, y, z):
+    With an iblank (nonzero: active), the flux divergence and the viscous gradients take every
+    maximal active run along a line as one SBP segment with closures at both of its ends (Sec.
+    2.2 hole cutting; the Cartesian oracle's stencil classes, orc_classes3d, which also makes
+    runs shorter than 8 points inactive, so the mask in ``self.iblank`` may have grown), and
+    the right-hand side is 0 at inactive points. The metric terms always take whole lines: the
+    mesh map is defined at every node, holes included (reading)."""
+
+    def __init__(self, x, y, z, iblank=None):
         X = [np.asarray(v, dtype=np.float64) for v in (x, y, z)]
         nk, nj, ni = X[0].shape
         self.shape = (nk, nj, ni)
         self.D = [d_matrix(ni), d_matrix(nj), d_matrix(nk)]
+        self.cls = None
+        self.iblank = None
         # derivative along index direction a (0: i, 1: j, 2: k) acts on array axis 2 - a
         dX = [[self.deriv(X[c], a) for a in range(3)] for c in range(3)]   # dX[c][a] = D_a X_c
         self.Jinv = (dX[0][0] * (dX[1][1] * dX[2][2] - dX[1][2] * dX[2][1])
@@ -87,12 +96,52 @@ class Curvilinear3D:
         for m, a, b in cyc:
             for j, c, e in cyc:
                 self.M[m][j] = (self.deriv(dX[c][a] * X[e], b) - self.deriv(dX[c][b] * X[e], a))
+        if iblank is not None:
+            ib = np.ascontiguousarray(np.asarray(iblank) != 0, dtype=np.int8).copy()
+            cls = [np.zeros(self.shape, np.int8) for _ in range(3)]
+            rc = lib().orc_classes3d(ni, nj, nk, 0, 0, 0, ctypes.c_void_p(ib.ctypes.data),
+                                     *[ctypes.c_void_p(c.ctypes.data) for c in cls])
+            if rc < 0:
+                raise RuntimeError("hole growing did not converge")
+            self.iblank = ib
+            self.cls = cls
+            self._lines = {}
 
     def deriv(self, f, a):
-        """D_a f: the SBP derivative along index direction a (unit index spacing)."""
+        """D_a f: the SBP derivative along index direction a (unit index spacing); on a mesh with
+        holes, per active segment (0 at inactive points)."""
         ax = 2 - a
-        g = np.tensordot(self.D[a], np.moveaxis(f, ax, 0), axes=(1, 0))
-        return np.moveaxis(g, 0, ax)
+        if self.cls is None:
+            g = np.tensordot(self.D[a], np.moveaxis(f, ax, 0), axes=(1, 0))
+            return np.moveaxis(g, 0, ax)
+        cl = np.moveaxis(self.cls[a], ax, -1)
+        fl = np.moveaxis(np.asarray(f, dtype=np.float64), ax, -1)
+        n = cl.shape[-1]
+        lines, vals = cl.reshape(-1, n), fl.reshape(-1, n)
+        out = np.zeros_like(vals)
+        pats, which = np.unique(lines, axis=0, return_inverse=True)
+        for u, pat in enumerate(pats):
+            sel = which.reshape(-1) == u
+            out[sel] = vals[sel] @ self._line_matrix(pat).T
+        return np.moveaxis(out.reshape(fl.shape), -1, ax)
+
+    def _line_matrix(self, pat):
+        """The derivative on one line with stencil classes pat, as a matrix: the pinned 1D
+        operator (orc_apply_d1) applied to unit vectors."""
+        key = pat.tobytes()
+        if key not in self._lines:
+            n = pat.size
+            cls = np.ascontiguousarray(pat, dtype=np.int8)
+            D = np.zeros((n, n))
+            out = np.zeros(n)
+            for c in range(n):
+                e = np.zeros(n)
+                e[c] = 1.0
+                lib().orc_apply_d1(n, ctypes.c_void_p(cls.ctypes.data), ctypes.c_void_p(e.ctypes.data),
+                                   ctypes.c_void_p(out.ctypes.data))
+                D[:, c] = out
+            self._lines[key] = D
+        return self._lines[key]
 
     def gradient(self, f):
         """(d f/dx, d f/dy, d f/dz) by the chain rule with the metric terms."""
@@ -111,16 +160,10 @@ class Curvilinear3D:
              + [(E + p) * vel[d]] for d in range(3)]
         Fv = None
         if mu > 0.0:
-            T = gamma * p / rho
-            g = [self.gradient(f) for f in vel + [T]]   # g[f][d]
-            div = g[0][0] + g[1][1] + g[2][2]
-            lam, kap = -2.0 / 3.0 * mu, mu / (pr * (gamma - 1.0))
-            Fv = []
+            Fv = self._viscous(q, gamma, mu, pr)
             for d in range(3):
-                tau = [mu * (g[d][c] + g[c][d]) + (lam * div if c == d else 0.0) for c in range(3)]
-                Fv.append(tau + [vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d]])
                 for c in range(3):
-                    F[d][1 + c] = F[d][1 + c] - tau[c]
+                    F[d][1 + c] = F[d][1 + c] - Fv[d][c]
                 F[d][4] = F[d][4] - Fv[d][3]
         out = []
         for v in range(5):
@@ -130,10 +173,38 @@ class Curvilinear3D:
                 s = s + self.deriv(Fh, m)
             out.append(-self.J * s)
         out = np.array(out)
+        if self.iblank is not None:
+            out[:, self.iblank == 0] = 0.0
         if qinf is not None:
             self._farfield(out, q, gamma, np.asarray(qinf, dtype=np.float64), sigma)
         if interface is not None:
             self._interface(out, q, gamma, mu, Fv, **interface)
+        return out
+
+    def _viscous(self, q, gamma, mu, pr):
+        """Cartesian viscous fluxes Fv[d] = (tau_d0, tau_d1, tau_d2, u . tau_d + kappa T_d) for
+        d = x, y, z (App. C.1: Stokes' hypothesis, Fourier heat flux, T = gamma p / rho), with
+        the gradients of (u, v, w, T) by the chain rule."""
+        rho = q[0]
+        vel = [q[1] / rho, q[2] / rho, q[3] / rho]
+        p = (gamma - 1.0) * (q[4] - 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2))
+        T = gamma * p / rho
+        g = [self.gradient(f) for f in vel + [T]]   # g[f][d]
+        div = g[0][0] + g[1][1] + g[2][2]
+        lam, kap = -2.0 / 3.0 * mu, mu / (pr * (gamma - 1.0))
+        Fv = []
+        for d in range(3):
+            tau = [mu * (g[d][c] + g[c][d]) + (lam * div if c == d else 0.0) for c in range(3)]
+            Fv.append(tau + [vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d]])
+        return Fv
+
+    def viscous_fluxes(self, q, gamma, mu, pr):
+        """The 12 planes (F^V_x, F^V_y, F^V_z; each momentum x, y, z and energy) of the Cartesian
+        viscous fluxes, 0 at inactive points: the donor values of Navier-Stokes receivers."""
+        Fv = self._viscous(np.asarray(q, dtype=np.float64), gamma, mu, pr)
+        out = np.array([Fv[d][c] for d in range(3) for c in range(4)])
+        if self.iblank is not None:
+            out[:, self.iblank == 0] = 0.0
         return out
 
     def _interface(self, out, q, gamma, mu, Fv, terms, qhat, fvhat=None, sigma=0.5):
@@ -247,8 +318,17 @@ def hole_cut(x, y, z, points, margin):
     X = np.stack([np.asarray(v, dtype=np.float64) for v in (x, y, z)])
     nk, nj, ni = X.shape[1:]
     n = (ni, nj, nk)
+    # points outside the nodes' bounding box padded by the longest edge between neighbouring
+    # nodes are outside the mesh (the interpolated map of a mesh whose cells are not folded
+    # does not reach there): no search
+    edge = max(float(np.sqrt((np.diff(X, axis=ax) ** 2).sum(axis=0)).max()) for ax in (1, 2, 3))
+    lo = X.reshape(3, -1).min(axis=1) - edge
+    hi = X.reshape(3, -1).max(axis=1) + edge
     out = []
     for p in np.asarray(points, dtype=np.float64).reshape(-1, 3):
+        if np.any(p < lo) or np.any(p > hi):
+            out.append(False)
+            continue
         c = _invert(X, p)
         out.append(c is not None and all(margin < c[a] < n[a] - 1 - margin for a in range(3)))
     return np.array(out, bool)

@@ -345,3 +345,79 @@ def extrude_to_3d(wl, nk, lz, axis=2):
     p["qinf"] = (np.array([qi[0], qi[1], qi[2], 0.0, qi[3]]) if axis == 2
                  else np.array([qi[0], qi[1], 0.0, qi[2], qi[3]]))
     return {"meshes": meshes, "q0": qs, "params": p}
+
+
+# --------------------------------------------------------------------------------------------
+# 3D curvilinear overset pair
+# --------------------------------------------------------------------------------------------
+
+def curvilinear_mesh3d(name, x, y, z):
+    """A 3D curvilinear mesh (non-periodic in every direction) from node coordinates, each
+    (nk, nj, ni) with i fastest."""
+    x, y, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z))
+    nk, nj, ni = x.shape
+    return {"name": name, "dim": 3, "n": (ni, nj, nk), "curvilinear": True, "x": x, "y": y, "z": z}
+
+
+def rotation3d(angles):
+    """The rotation Rz(c) Ry(b) Rx(a) for angles (a, b, c) in radians, as a 3 x 3 array."""
+    a, b, c = angles
+    rx = np.array([[1, 0, 0], [0, math.cos(a), -math.sin(a)], [0, math.sin(a), math.cos(a)]])
+    ry = np.array([[math.cos(b), 0, math.sin(b)], [0, 1, 0], [-math.sin(b), 0, math.cos(b)]])
+    rz = np.array([[math.cos(c), -math.sin(c), 0], [math.sin(c), math.cos(c), 0], [0, 0, 1]])
+    return rz @ ry @ rx
+
+
+def curvilinear_pair(seed=0, n_bg=24, n_fine=25, ratio=2, eps_bg=0.03, eps_fine=0.02, angles=(0.25, -0.15, 0.35),
+                     hole_cells=7, physics="euler", mach=0.3, re=200.0, pr=0.72, pulse_amp=0.05, order=3,
+                     hist_len=None, step_ratio=2, cfl=0.5, omega_corner=1.0):
+    """A 3D curvilinear overset pair. Mesh 0: n_bg^3 points over [-1, 1]^3, each coordinate
+    displaced by eps_bg sin(2 pi s) sin(2 pi t) of the other two index fractions s, t (far
+    field on all six faces). Mesh 1: an n_fine^3 box at 1/ratio of the background spacing,
+    displaced the same way by eps_fine times its width, turned by rotation3d(angles) and
+    centred near the origin (jittered by the seed; interface on all six faces). Background
+    points more than hole_cells index units of mesh 1 inside it are holes. Initial state: a
+    uniform stream of Mach `mach` (rho = 1, p = 1 / gamma) along a seeded direction, plus a
+    Gaussian bump of relative amplitude pulse_amp and width 4 spacings of mesh 1 at its centre
+    in pressure and density, and a swirl about the z axis through the centre of the same
+    width. Navier-Stokes: mu = mach / re. The defaults (13,824 + 15,625 points, 125 holes) are
+    the parity-test size; the overset box must stay inside the background, and a hole wider
+    than n_bg - 16 background points along a line grows (segments shorter than 8 points become
+    holes) until the setup finds no donors."""
+    rng = np.random.default_rng(seed)
+    t = np.linspace(0.0, 1.0, n_bg)
+    T3, T2, T1 = np.meshgrid(t, t, t, indexing="ij")
+    s2 = 2.0 * math.pi
+    xb = -1.0 + 2.0 * T1 + eps_bg * np.sin(s2 * T2) * np.sin(s2 * T3)
+    yb = -1.0 + 2.0 * T2 + eps_bg * np.sin(s2 * T1) * np.sin(s2 * T3)
+    zb = -1.0 + 2.0 * T3 + eps_bg * np.sin(s2 * T1) * np.sin(s2 * T2)
+    hf = 2.0 / (n_bg - 1) / ratio
+    width = (n_fine - 1) * hf
+    t = np.linspace(0.0, 1.0, n_fine)
+    T3, T2, T1 = np.meshgrid(t, t, t, indexing="ij")
+    loc = np.stack([(T1 - 0.5) * width + eps_fine * width * np.sin(s2 * T2) * np.sin(s2 * T3),
+                    (T2 - 0.5) * width + eps_fine * width * np.sin(s2 * T1) * np.sin(s2 * T3),
+                    (T3 - 0.5) * width + eps_fine * width * np.sin(s2 * T1) * np.sin(s2 * T2)])
+    R = rotation3d(angles)
+    centre = rng.uniform(-0.5, 0.5, 3) * hf
+    xf, yf, zf = (centre[a] + sum(R[a, b] * loc[b] for b in range(3)) for a in range(3))
+    meshes = [curvilinear_mesh3d("background", xb, yb, zb), curvilinear_mesh3d("overset", xf, yf, zf)]
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    w = 4.0 * hf
+    qs = []
+    for m in meshes:
+        x, y, z = m["x"], m["y"], m["z"]
+        G = np.exp(-((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2) / (w * w))
+        rho = 1.0 + 0.5 * pulse_amp * G
+        p = (1.0 + pulse_amp * G) / GAMMA
+        u = mach * d[0] - pulse_amp * (y - centre[1]) / w * G
+        v = mach * d[1] + pulse_amp * (x - centre[0]) / w * G
+        wz = np.full_like(G, mach * d[2])
+        E = p / (GAMMA - 1.0) + 0.5 * rho * (u * u + v * v + wz * wz)
+        qs.append(np.stack([rho, rho * u, rho * v, rho * wz, E]))
+    qinf = np.array([1.0, mach * d[0], mach * d[1], mach * d[2], 1.0 / (GAMMA * (GAMMA - 1.0)) + 0.5 * mach * mach])
+    params = dict(physics=physics, gamma=GAMMA, mu=(mach / re if physics == "ns" else 0.0), pr=pr, order=order,
+                  hist_len=hist_len or order, step_ratio=step_ratio, fast_mesh=1, cfl=cfl, qinf=qinf, twall=1.0,
+                  omega_corner=omega_corner, hole_cells=hole_cells)
+    return {"meshes": meshes, "q0": qs, "params": params, "seed": seed}
