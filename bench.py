@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--no-large", action="store_true", help="skip rhs_eval on meshes larger than L2")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D Taylor-Green workload")
     ap.add_argument("--no-curv3d", action="store_true", help="skip the 3D curvilinear operator")
+    ap.add_argument("--no-curv-pair", action="store_true", help="skip the 3D curvilinear overset pair")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-stability", action="store_true", help="skip the step-matrix stability study")
     ap.add_argument("--profile-shapes", action="store_true",
@@ -807,6 +808,52 @@ def _run_curv3d(hbm_peak, peak_kind, n=192, reps=5):
     return out
 
 
+def _run_curv_pair(hbm_peak, peak_kind, n_bg=128, n_fine=97, steps=10, warmup=3):
+    """The 3D curvilinear overset pair (no configuration of its own): a warped n_bg^3 background
+    with far field on its faces and a warped, turned n_fine^3 box at half its spacing (interface
+    on its faces; workloads.curvilinear_pair with hole margin 8), Navier-Stokes, MRAB order 3,
+    step ratio 2, FP64 and FP32; `steps` macro steps after `warmup`, device-timed with events (the
+    working set, about 1 GB in FP64, is far above L2). Throughput in point-evaluations per
+    second (one slow and two fast right-hand sides per macro step). Algorithmic bytes per
+    point-evaluation of a fused step: the state, the 10 metric planes and the 2 older history
+    values read, the right-hand side and the new state written: 35 values."""
+    import numpy as np
+    import torch
+    import paper_1805_06607_gb300 as sbp
+    import workloads as W
+
+    wl = W.curvilinear_pair(seed=0, n_bg=n_bg, n_fine=n_fine, hole_cells=8, physics="ns")
+    sr = wl["params"]["step_ratio"]
+    n0, n1 = n_bg ** 3, n_fine ** 3
+    out = {"workload": "Navier-Stokes curvilinear overset pair: warped %d^3 background + turned %d^3 box at half "
+                       "spacing, MRAB 3, SR %d" % (n_bg, n_fine, sr), "points": n0 + n1}
+    stream = torch.cuda.current_stream()
+    for dtype in ("f64", "f32"):
+        t0 = time.perf_counter()
+        g = sbp.CurvilinearPair(wl, dtype=dtype)
+        setup_s = time.perf_counter() - t0
+        evals = n0 - g.info[0].n_holes + sr * n1
+        g.bind(wl["q0"])
+        g.mrab_init()
+        g.mrab_step(warmup)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.mrab_step(steps)
+        b.record(stream)
+        g.check()
+        ms = a.elapsed_time(b) / steps
+        es = 4 if dtype == "f32" else 8
+        gbs = evals * 35 * es / (ms / 1e3) / 1e9
+        out[dtype] = {"ms_per_macro_step": ms, "gpt_evals_per_s": evals / (ms / 1e3) / 1e9,
+                      "point_evals_per_step": evals, "bytes_per_point_eval": 35 * es, "achieved_gbs": gbs,
+                      "hbm_frac": gbs / hbm_peak, "peak_kind": peak_kind, "host_setup_s": setup_s,
+                      "holes": g.info[0].n_holes, "receivers": [g.info[k].n_receivers for k in range(2)]}
+        g.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def _run_adjoint(n_steps=500, n_snapshots=40):
     """The adjoint workload: the cylinder at half resolution (O-grid 256 x 64, background
     512 x 256), MRAB order 3, step ratio 4, FP64; objective J = H sum_n sum_p p_p(t_n)^2 over
@@ -1200,6 +1247,8 @@ def main():
         line["taylor_green_3d"] = _run_3d(min(args.steps, 10), 2, hbm_peak, peak_kind)
     if not args.no_curv3d and rank == 0:
         line["curvilinear_3d"] = _run_curv3d(hbm_peak, peak_kind)
+    if not args.no_curv_pair and rank == 0:
+        line["curvilinear_pair_3d"] = _run_curv_pair(hbm_peak, peak_kind)
     if not args.no_large and rank == 0:
         line["rhs_eval_large"] = _rhs_eval_large(hbm_peak, peak_kind)
     if not args.no_rate_compare and rank == 0:

@@ -593,7 +593,9 @@ sbp_status sbp3c_set_farfield(sbp3c_mesh_t mesh, const double *qinf, double sigm
  * X(s, r, t) = p, X the mesh map interpolated by the 4 x 4 x 4 Lagrange basis on the stencil
  * that starts at floor(.) - 1 clamped into the mesh, found by Newton's method from a nearby
  * node (the nearest of a coarse subset of nodes, refined locally by halving the stride; the
- * nearest of all nodes if that start fails) until three consecutive steps stay below 1e-10.
+ * nearest of all nodes if the iteration from there fails to converge inside the index range)
+ * until three consecutive steps stay below 1e-10; a point it converges to outside the index
+ * range, or fails on more than a cell outside it, is outside the mesh.
  * Points outside the nodes' bounding box padded by the longest edge between neighbouring nodes
  * are outside the mesh without a search. Outputs (host, caller
  * owned): base 3 ints per point (i0, j0, k0), w 12 doubles per point (the 4 basis values along
@@ -643,6 +645,85 @@ sbp_status sbp3c_interface_sat(sbp3c_mesh_t mesh, const void *q, const void *qha
                                void *stream);
 /* rhs = dq/dt (device, asynchronous on stream). */
 sbp_status sbp3c_rhs_eval(sbp3c_mesh_t mesh, const void *q, void *rhs, void *stream);
+
+/* ---- 3D curvilinear overset pairs ---------------------------------------------------------------
+ * Two curvilinear meshes stepped together (Sec. 2.2 overset coupling, Sec. 3.1-3.3 MRAB): mesh 0,
+ * the background, with the far-field SAT (sbp3c_set_farfield's form, sigma = sigma_physical) on
+ * all six faces; mesh 1, the overset mesh, with interface SAT terms (eq. (int), sigma =
+ * sigma_interface) on all six faces. Setup: the hole cut of the background by the overset mesh
+ * (sbp3c_hole_cut with margin = params.hole_cells index units of the overset mesh; <= 0: 4),
+ * every maximal active run along a line an SBP segment of at least 8 points (shorter runs
+ * become holes), receivers at the overset mesh's faces and at the background's active points
+ * next to a hole, one interface term per normal direction and side (corner weight Omega =
+ * omega_corner where a point has several), donor stencils by sbp3c_donor_search (no hole in a
+ * stencil; SBP_ERR_DONOR otherwise), the coefficient plan of the 2D systems. Right-hand sides:
+ * the 3D curvilinear operator per active segment (metric terms on whole lines), 0 at holes; the
+ * receivers' donor values are the other mesh's state and, for Navier-Stokes, its Cartesian
+ * viscous fluxes, gathered with the stencils' weights. Time step (the 2D curvilinear form over
+ * three directions): per active point 1 / (sum_m |u . k_m| + c |K| + 2 nu |K|^2), k_m = grad
+ * xi_m, |K|^2 = sum_m |k_m|^2, nu = max(mu, gamma mu / Pr) / rho; H = min(cfl dt_slow, SR cfl
+ * dt_fast). Integrator: fastest-first MRAB of order `order` with `hist_len` values and step
+ * ratio `step_ratio`, mesh `fast_mesh` at the micro step, bootstrapped by Heun's RK3 at the
+ * micro step, as sbp_mrab_init / sbp_mrab_step. States and right-hand sides: 5 device planes of
+ * n[0]*n[1]*n[2] elements, unpitched, q = (rho, rho u, rho v, rho w, rho E); the element type
+ * is params.dtype. x, y, z: host arrays of n[0]*n[1]*n[2] doubles, i fastest (copied). */
+typedef struct {
+  int n[3];
+  const double *x, *y, *z;
+} sbp3c_mesh_desc;
+typedef struct sbp3c_system_s *sbp3c_system_t;
+/* Synchronous. SBP_ERR_ARG, SBP_ERR_SHAPE, SBP_ERR_DTYPE for bad parameters or sizes (8..65535
+ * points per direction), SBP_ERR_DONOR when a receiver has no valid stencil (message names it),
+ * SBP_ERR_CUDA on a failed allocation. The far-field state starts as params.qinf (rho, rho u,
+ * rho v, rho E) with rho w = 0; sbp3c_system_set_freestream sets all five. */
+sbp_status sbp3c_system_create(const sbp3c_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                               sbp3c_system_t *out);
+sbp_status sbp3c_system_destroy(sbp3c_system_t sys);
+/* ni, nj, nk, pitch (= ni), field_elems, state_bytes, n_holes, n_receivers, n_sat_points (points
+ * with SAT terms of any kind), elem_size of one mesh. */
+sbp_status sbp3c_system_info(sbp3c_system_t sys, int mesh, sbp3_mesh_info *info);
+/* qinf[5] (host): the far-field state. SBP_ERR_ARG without positive density and pressure. */
+sbp_status sbp3c_system_set_freestream(sbp3c_system_t sys, const double *qinf);
+/* Setup tables (host, any pointer may be NULL): iblank n[0]*n[1]*n[2] bytes (1 active, 0 hole,
+ * after hole growth); receivers n_receivers linear indices (k n[1] + j) n[0] + i, sorted;
+ * donor_base 3 ints (i0, j0, k0) and donor_w 12 doubles (Lagrange weights along i, j, k) per
+ * receiver, on the other mesh. */
+sbp_status sbp3c_system_tables(sbp3c_system_t sys, int mesh, signed char *iblank, long long *receivers,
+                               int *donor_base, double *donor_w);
+/* The host part of sbp3c_system_create alone (no device calls); errors as sbp3c_system_create,
+ * tables as sbp3c_system_tables, n_receivers (host int) the receiver count. */
+typedef struct sbp3c_host_tables_s *sbp3c_host_tables_t;
+sbp_status sbp3c_host_tables_create(const sbp3c_mesh_desc *meshes, int n_meshes, const sbp_params *params,
+                                    sbp3c_host_tables_t *out);
+sbp_status sbp3c_host_tables_destroy(sbp3c_host_tables_t tables);
+sbp_status sbp3c_host_tables_get(sbp3c_host_tables_t tables, int mesh, signed char *iblank, long long *receivers,
+                                 int *donor_base, double *donor_w, int *n_receivers);
+/* Donor values at recv_mesh's receivers from the other mesh's state q_donor (device): qhat 5 x
+ * n_receivers, fvhat 12 x n_receivers (F^V_x, F^V_y, F^V_z, each momentum x, y, z and energy;
+ * Navier-Stokes only, may be NULL). Asynchronous on stream. */
+sbp_status sbp3c_system_interp(sbp3c_system_t sys, int recv_mesh, const void *q_donor, void *qhat, void *fvhat,
+                               void *stream);
+/* Right-hand side of one mesh with its receivers fed from q_other (device). Asynchronous. */
+sbp_status sbp3c_system_rhs_eval(sbp3c_system_t sys, int mesh, const void *q_self, const void *q_other, void *rhs,
+                                 void *stream);
+/* Time step per mesh (without the CFL factor; dt_mesh: 2 doubles, may be NULL) and the macro step
+ * H (host, may be NULL). Synchronises the stream. */
+sbp_status sbp3c_system_timestep(sbp3c_system_t sys, const void *q0, const void *q1, double *dt_mesh, double *H,
+                                 void *stream);
+/* Integrator buffers (device, caller-owned): two states and hist_len right-hand sides per mesh,
+ * as sbp_bind; the state to start from is q_a. */
+sbp_status sbp3c_system_bind(sbp3c_system_t sys, int mesh, void *q_a, void *q_b, void *hist);
+sbp_status sbp3c_system_current_state(sbp3c_system_t sys, int mesh, void **q);
+/* Bootstrap with macro step H (H <= 0: from sbp3c_system_timestep at the bound states); allocates
+ * and frees its stage buffers, synchronises the stream. SBP_ERR_STATE before sbp3c_system_bind. */
+sbp_status sbp3c_system_mrab_init(sbp3c_system_t sys, double H, void *stream);
+/* n macro steps, asynchronous on stream. SBP_ERR_STATE before sbp3c_system_mrab_init. */
+sbp_status sbp3c_system_mrab_step(sbp3c_system_t sys, int n, void *stream);
+/* The macro step and the time reached since sbp3c_system_mrab_init (host). */
+sbp_status sbp3c_system_mrab_time(sbp3c_system_t sys, double *H, double *t);
+/* Synchronise the stream and report (then clear) the device error word (SBP_ERR_NONFINITE: a
+ * step produced a non-finite or non-positive-density state at an active point). */
+sbp_status sbp3c_system_check(sbp3c_system_t sys, void *stream);
 
 /* Synchronise the stream and report (then clear) the device error word. */
 sbp_status sbp_check(sbp_system_t sys, void *stream);

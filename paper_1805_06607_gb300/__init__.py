@@ -69,6 +69,10 @@ class Mesh3Info(ctypes.Structure):
                 ("elem_size", ctypes.c_int)]
 
 
+class Mesh3cDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p)]
+
+
 class AdjointDesc(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int), ("n_snapshots", ctypes.c_int), ("n_probes", ctypes.c_int),
                 ("probe_xy", ctypes.c_void_p), ("H", ctypes.c_double)]
@@ -165,6 +169,23 @@ _SIGS.update({
     "sbp3c_hole_cut": [_P, _P, _P, _P, _I, _P, ctypes.c_double, _P],
     "sbp3c_set_interface": [_P, _I, _P, _P, _I, ctypes.c_double],
     "sbp3c_interface_sat": [_P, _P, _P, _P, _P, _P],
+    "sbp3c_system_create": [ctypes.POINTER(Mesh3cDesc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "sbp3c_system_destroy": [_P],
+    "sbp3c_system_info": [_P, _I, ctypes.POINTER(Mesh3Info)],
+    "sbp3c_system_set_freestream": [_P, _P],
+    "sbp3c_system_tables": [_P, _I, _P, _P, _P, _P],
+    "sbp3c_host_tables_create": [ctypes.POINTER(Mesh3cDesc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
+    "sbp3c_host_tables_destroy": [_P],
+    "sbp3c_host_tables_get": [_P, _I, _P, _P, _P, _P, _P],
+    "sbp3c_system_interp": [_P, _I, _P, _P, _P, _P],
+    "sbp3c_system_rhs_eval": [_P, _I, _P, _P, _P, _P],
+    "sbp3c_system_timestep": [_P, _P, _P, _P, _P, _P],
+    "sbp3c_system_bind": [_P, _I, _P, _P, _P],
+    "sbp3c_system_current_state": [_P, _I, ctypes.POINTER(_P)],
+    "sbp3c_system_mrab_init": [_P, _D, _P],
+    "sbp3c_system_mrab_step": [_P, _I, _P],
+    "sbp3c_system_mrab_time": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "sbp3c_system_check": [_P, _P],
 })
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -1046,6 +1067,206 @@ class Curvilinear3DMesh:
             self.close()
         except Exception:
             pass
+
+
+def _descriptors_curv(wl, dtype, sigma_interface, sigma_physical):
+    """C descriptors (sbp3c_mesh_desc[2], sbp_params) of a curvilinear pair workload
+    (``workloads.curvilinear_pair`` layout) and the coordinate arrays they point to (keep them
+    alive for the call)."""
+    p = wl["params"]
+    descs = (Mesh3cDesc * 2)()
+    keep = []
+    for k, m in enumerate(wl["meshes"]):
+        X = [np.ascontiguousarray(m[c], dtype=np.float64) for c in ("x", "y", "z")]
+        nk, nj, ni = X[0].shape
+        if tuple(m["n"]) != (ni, nj, nk) or any(v.shape != X[0].shape for v in X):
+            raise ValueError("mesh %d: coordinates must be (nk, nj, ni) arrays matching n" % k)
+        keep.extend(X)
+        d = descs[k]
+        for a, v in enumerate((ni, nj, nk)):
+            d.n[a] = v
+        d.x, d.y, d.z = (v.ctypes.data for v in X)
+    pr = Params()
+    pr.physics = PHYSICS[p["physics"]]
+    pr.dtype = DTYPE[dtype]
+    pr.gamma = p["gamma"]
+    pr.mu = p["mu"]
+    pr.pr = p["pr"]
+    pr.twall = p.get("twall", 1.0)
+    pr.omega_corner = p["omega_corner"]
+    pr.sigma_interface = sigma_interface
+    pr.sigma_physical = sigma_physical
+    pr.cfl = p["cfl"]
+    qi = np.asarray(p["qinf"], dtype=np.float64)
+    for v, c in enumerate((0, 1, 2, 4)):
+        pr.qinf[v] = float(qi[c])
+    pr.order = p["order"]
+    pr.hist_len = p["hist_len"]
+    pr.step_ratio = p["step_ratio"]
+    pr.fast_mesh = p["fast_mesh"]
+    pr.hole_cells = float(p["hole_cells"])
+    return descs, pr, keep
+
+
+def _tables3(getter, where, handle, k, shape, nr):
+    """iblank, receivers, donor bases and weights of mesh k by a table getter of the C ABI."""
+    nk, nj, ni = shape
+    ib = np.zeros(ni * nj * nk, np.int8)
+    rec = np.zeros(max(nr, 1), np.int64)
+    base = np.zeros(max(3 * nr, 1), np.int32)
+    w = np.zeros(max(12 * nr, 1))
+    _check(getter(handle, k, ib.ctypes.data, rec.ctypes.data, base.ctypes.data, w.ctypes.data), where)
+    return {"iblank": ib.reshape(nk, nj, ni), "receivers": rec[:nr], "base": base[:3 * nr].reshape(nr, 3),
+            "w": w[:12 * nr].reshape(nr, 12)}
+
+
+class HostTablesCurvilinearPair:
+    """The host part of curvilinear pair creation alone (sbp3c_host_tables_*), without a GPU."""
+
+    def __init__(self, wl, sigma_interface=0.5, sigma_physical=1.0):
+        descs, pr, keep = _descriptors_curv(wl, "f64", sigma_interface, sigma_physical)
+        h = ctypes.c_void_p()
+        _check(_lib.sbp3c_host_tables_create(descs, 2, ctypes.byref(pr), ctypes.byref(h)), "sbp3c_host_tables_create")
+        del keep
+        self.h = h
+        self.shapes = [m["x"].shape for m in wl["meshes"]]
+
+    def tables(self, k):
+        nr = ctypes.c_int()
+        _check(_lib.sbp3c_host_tables_get(self.h, k, None, None, None, None, ctypes.byref(nr)), "sbp3c_host_tables_get")
+        return _tables3(lambda h, kk, a, b, c, d: _lib.sbp3c_host_tables_get(h, kk, a, b, c, d, None),
+                        "sbp3c_host_tables_get", self.h, k, self.shapes[k], nr.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp3c_host_tables_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CurvilinearPair:
+    """A 3D curvilinear overset pair on the current CUDA device (C ABI sbp3c_system_*): mesh 0 the
+    background (far field on its faces), mesh 1 the overset mesh (interface on its faces).
+    ``wl`` is a ``workloads.curvilinear_pair`` dict. States are numpy arrays or device tensors
+    (5, nk, nj, ni) of the pair's element type."""
+
+    def __init__(self, wl, dtype="f64", sigma_interface=0.5, sigma_physical=1.0):
+        import torch
+        self.torch = torch
+        self.dtype = dtype
+        self.tdtype = torch.float64 if dtype == "f64" else torch.float32
+        self.params = wl["params"]
+        self.viscous = self.params["physics"] == "ns"
+        self.shapes = [m["x"].shape for m in wl["meshes"]]
+        descs, pr, keep = _descriptors_curv(wl, dtype, sigma_interface, sigma_physical)
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        _check(_lib.sbp3c_system_create(descs, 2, ctypes.byref(pr), ctypes.byref(h)), "sbp3c_system_create")
+        del keep
+        self.h = h
+        qi = np.ascontiguousarray(self.params["qinf"], dtype=np.float64)
+        _check(_lib.sbp3c_system_set_freestream(self.h, qi.ctypes.data), "sbp3c_system_set_freestream")
+        self.info = []
+        for k in range(2):
+            inf = Mesh3Info()
+            _check(_lib.sbp3c_system_info(self.h, k, ctypes.byref(inf)), "sbp3c_system_info")
+            self.info.append(inf)
+        self.bound = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.sbp3c_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _state(self, k, t, name):
+        torch = self.torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != self.tdtype or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CUDA tensor of %s" % (name, self.tdtype))
+        if tuple(t.shape) != (5,) + tuple(self.shapes[k]):
+            raise ValueError("%s must have shape %s" % (name, (5,) + tuple(self.shapes[k])))
+        return t
+
+    def empty_state(self, k, n=1):
+        t = self.torch.zeros((n, 5) + tuple(self.shapes[k]), dtype=self.tdtype, device="cuda")
+        return t if n > 1 else t[0]
+
+    def to_device(self, k, q):
+        return self.torch.from_numpy(np.ascontiguousarray(q)).to(self.tdtype).cuda().contiguous()
+
+    def to_host(self, k, t):
+        return t.double().cpu().numpy()
+
+    def tables(self, k):
+        return _tables3(_lib.sbp3c_system_tables, "sbp3c_system_tables", self.h, k, self.shapes[k],
+                        self.info[k].n_receivers)
+
+    def overset_interp(self, recv, q_donor, stream=None):
+        """(qhat (5, n_receivers), fvhat (12, n_receivers)) at mesh recv's receivers."""
+        nr = self.info[recv].n_receivers
+        q_donor = self._state(1 - recv, q_donor, "q_donor")
+        qhat = self.torch.zeros((5, max(nr, 1)), dtype=self.tdtype, device="cuda")
+        fvhat = self.torch.zeros((12, max(nr, 1)), dtype=self.tdtype, device="cuda")
+        _check(_lib.sbp3c_system_interp(self.h, recv, _ptr(q_donor), _ptr(qhat), _ptr(fvhat), _stream(stream)),
+               "sbp3c_system_interp")
+        return qhat[:, :nr], fvhat[:, :nr]
+
+    def rhs_eval(self, k, q_self, q_other, out=None, stream=None):
+        q_self = self._state(k, q_self, "q_self")
+        q_other = self._state(1 - k, q_other, "q_other")
+        out = self.empty_state(k) if out is None else self._state(k, out, "out")
+        _check(_lib.sbp3c_system_rhs_eval(self.h, k, _ptr(q_self), _ptr(q_other), _ptr(out), _stream(stream)),
+               "sbp3c_system_rhs_eval")
+        return out
+
+    def timestep(self, q0, q1, stream=None):
+        q0, q1 = self._state(0, q0, "q0"), self._state(1, q1, "q1")
+        dt = (ctypes.c_double * 2)()
+        H = ctypes.c_double()
+        _check(_lib.sbp3c_system_timestep(self.h, _ptr(q0), _ptr(q1), ctypes.cast(dt, ctypes.c_void_p),
+                                          ctypes.cast(ctypes.pointer(H), ctypes.c_void_p), _stream(stream)),
+               "sbp3c_system_timestep")
+        return [dt[0], dt[1]], H.value
+
+    def bind(self, q_host):
+        self.bound = []
+        m = int(self.params["hist_len"])
+        for k in range(2):
+            qa = self.to_device(k, q_host[k])
+            qb = self.empty_state(k)
+            hist = self.empty_state(k, n=m) if m > 1 else self.empty_state(k)[None]
+            _check(_lib.sbp3c_system_bind(self.h, k, _ptr(qa), _ptr(qb), _ptr(hist)), "sbp3c_system_bind")
+            self.bound.append((qa, qb, hist))
+
+    def current_state(self, k):
+        p = ctypes.c_void_p()
+        _check(_lib.sbp3c_system_current_state(self.h, k, ctypes.byref(p)), "sbp3c_system_current_state")
+        qa, qb, _ = self.bound[k]
+        return qa if p.value == qa.data_ptr() else qb
+
+    def mrab_init(self, H=0.0, stream=None):
+        _check(_lib.sbp3c_system_mrab_init(self.h, float(H), _stream(stream)), "sbp3c_system_mrab_init")
+
+    def mrab_step(self, n=1, stream=None):
+        _check(_lib.sbp3c_system_mrab_step(self.h, int(n), _stream(stream)), "sbp3c_system_mrab_step")
+
+    def mrab_time(self):
+        H, t = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.sbp3c_system_mrab_time(self.h, ctypes.byref(H), ctypes.byref(t)), "sbp3c_system_mrab_time")
+        return H.value, t.value
+
+    def check(self, stream=None):
+        _check(_lib.sbp3c_system_check(self.h, _stream(stream)), "sbp3c_system_check")
 
 
 def donor_search_3d(x, y, z, points, iblank=None):

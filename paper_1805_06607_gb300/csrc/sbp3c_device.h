@@ -5,12 +5,19 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <cstdint>
+
+#include "sbp_device.h"
 
 namespace sbp {
 
 struct Curv3Launch {
   int ni, nj, nk;
   size_t field;          // ni * nj * nk
+  // stencil classes, 4 bits per direction (i, j, k), 0xFFF for a hole (the 3D Cartesian
+  // systems' codes): every maximal active run along a line is one SBP segment; NULL: whole
+  // lines (no holes)
+  const uint16_t *cls;
   int visc;
   double gam, mu, lam, kap;
   const void *q;         // 5 planes
@@ -46,5 +53,42 @@ cudaError_t launch3c_isat(const Curv3Launch &a, const Curv3Sat &s, int dtype, cu
 // stencil (base: 3 ints, w: 12 doubles per receiver; device).
 cudaError_t launch3c_interp(int ni, int nj, size_t field, const void *q, int nrecv, const int *base, const double *w,
                             void *out, int dtype, cudaStream_t s);
+
+// Donor values of a curvilinear mesh for another mesh's receivers (Sec. 2.2 interpolation with
+// Sec. 3.3 Step 2's extrapolation in time): one thread per (extrapolation set, distinct donor
+// point) writes the state q + sum_k beta[set][k] hist[k] (FP64 accumulation) and, for
+// Navier-Stokes, the Cartesian viscous fluxes of that state by the mesh's own SBP derivatives
+// and metric terms, to dv[(set * 17 + c) * npts + point] (c: 5 state values, then F^V_x,
+// F^V_y, F^V_z, each momentum x, y, z and energy).
+struct Curv3Donor {
+  Curv3Launch m;                       // the donor mesh (q, met, cls, gas constants)
+  const void *hist[kMaxHist];
+  double beta[kMaxSets][kMaxHist];
+  int nb[kMaxSets];
+  int nsets, npts;
+  const long long *pts;                // linear indices (k nj + j) ni + i on the donor mesh
+  void *dv;
+};
+cudaError_t launch3c_donor(const Curv3Donor &a, int dtype, cudaStream_t s);
+
+// Adams-Bashforth combine (Sec. 3.1-3.3) over the whole mesh: qn = q + sum_{h < nold} alpha[h]
+// hold[h] + alpha[nold] rhs (FP64 accumulation); a non-finite or non-positive-density result at
+// an active point raises SBP_ERR_NONFINITE in *err.
+struct Curv3Ab {
+  size_t field;
+  const uint16_t *cls;                 // NULL: every point active
+  const void *q, *rhs;
+  const void *hold[kMaxHist];
+  double alpha[kMaxHist];
+  int nold;
+  void *qn;
+  int *err;
+};
+cudaError_t launch3c_ab(const Curv3Ab &a, int dtype, cudaStream_t s);
+
+// Time step of the curvilinear mesh at state q (active points): min over points of
+// 1 / (sum_m |u . k_m| + c |K| + 2 nu |K|^2), k_m = J M[m][:], |K|^2 = sum_m |k_m|^2,
+// nu = max(mu, gamma mu / Pr) / rho, as the bits of a positive double min-reduced into *out.
+cudaError_t launch3c_dt(const Curv3Launch &a, double pr, unsigned long long *out, cudaStream_t s, int dtype);
 
 }  // namespace sbp

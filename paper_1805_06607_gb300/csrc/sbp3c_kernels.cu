@@ -1,6 +1,8 @@
 // 3D curvilinear operator (App. C.1's equations in curvilinear coordinates with Sec. 2.1's SBP
-// 4-2 derivative): one structured mesh with closures at both ends of every line; far-field and
-// interface SAT terms and the overset gather as separate kernels.
+// 4-2 derivative): one structured mesh with closures at both ends of every line, or, with a
+// class map (overset pairs with a hole cut), at both ends of every active segment; far-field
+// and interface SAT terms and the overset gather as separate kernels; for overset pairs also
+// the donor values, the Adams-Bashforth combine and the time step.
 //   k3c_dx       coordinate derivatives D_a X_c (9 planes, FP64)
 //   k3c_metrics  metric terms M[m][j] = xi_m,x_j / J in the symmetric conservative form of
 //                Thomas and Lombard, M[m][j] = D_b((X_c)_a X_e) - D_a((X_c)_b X_e) over cyclic
@@ -17,7 +19,13 @@
 //                (side +1) or high (side -1) face of index direction m, -(sigma / p0)
 //                K^side_k (q - qinf) with k = grad xi_m = J M[m][:], one term for each face the
 //                point lies on
+//   k3c_donor    donor-point states (slow extrapolation of Sec. 3.3) and viscous fluxes
+//   k3c_ab       qn = q + sum alpha_h hist_h (Sec. 3.1-3.3), non-finite states flagged
+//   k3c_dt       time step, min-reduced
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
 
 #include "sbp3_penalty.cuh"
 #include "sbp3c_device.h"
@@ -32,17 +40,37 @@ __device__ __forceinline__ unsigned line_code(int c, int n) {
   return 0u;
 }
 
-// D_d f at point (i, j, k) of an unpitched plane f (unit index spacing).
+// The derivative row of stencil class `code` applied at linear index p of a line with stride st.
+template <typename T, typename F>
+__device__ __forceinline__ T dtap(const F &f, ptrdiff_t p, ptrdiff_t st, unsigned code) {
+  const Row<T> r = decode_row<T>(code);
+  T acc = T(0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc += r.w[e] * f(p + (ptrdiff_t)r.off[e] * st);
+  return r.neg ? -acc : acc;
+}
+
+// D_d f at point (i, j, k) of an unpitched plane f (unit index spacing), whole lines.
 template <typename T, typename F>
 __device__ __forceinline__ T cderiv(const F &f, int i, int j, int k, int d, int ni, int nj, int nk) {
   const int c[3] = {i, j, k}, n[3] = {ni, nj, nk};
   const ptrdiff_t st[3] = {1, (ptrdiff_t)ni, (ptrdiff_t)ni * nj};
-  const Row<T> r = decode_row<T>(line_code(c[d], n[d]));
-  const ptrdiff_t p = ((ptrdiff_t)k * nj + j) * ni + i;
-  T acc = T(0);
-#pragma unroll
-  for (int e = 0; e < 4; ++e) acc += r.w[e] * f(p + (ptrdiff_t)r.off[e] * st[d]);
-  return r.neg ? -acc : acc;
+  return dtap<T>(f, ((ptrdiff_t)k * nj + j) * ni + i, st[d], line_code(c[d], n[d]));
+}
+
+// Stencil class of point p = (i, j, k) along direction d: from the class map, else whole lines.
+__device__ __forceinline__ unsigned pcode(const Curv3Launch &a, size_t p, int i, int j, int k, int d) {
+  if (a.cls) return (a.cls[p] >> (4 * d)) & 15u;
+  return line_code(d == 0 ? i : (d == 1 ? j : k), d == 0 ? a.ni : (d == 1 ? a.nj : a.nk));
+}
+
+__device__ __forceinline__ bool is_hole(const Curv3Launch &a, size_t p) { return a.cls && (a.cls[p] & 15u) == 15u; }
+
+// D_d f at point (i, j, k) of the mesh of a (per segment with a class map).
+template <typename T, typename F>
+__device__ __forceinline__ T mderiv(const Curv3Launch &a, const F &f, size_t p, int i, int j, int k, int d) {
+  const ptrdiff_t st = d == 0 ? 1 : (d == 1 ? (ptrdiff_t)a.ni : (ptrdiff_t)a.ni * a.nj);
+  return dtap<T>(f, (ptrdiff_t)p, st, pcode(a, p, i, j, k, d));
 }
 
 __global__ void __launch_bounds__(256) k3c_dx(int ni, int nj, int nk, const double *xyz, double *dx) {
@@ -87,7 +115,7 @@ __global__ void __launch_bounds__(256) k3c_metrics(int ni, int nj, int nk, const
 template <typename T>
 __global__ void __launch_bounds__(256) k3c_prim(const Curv3Launch a) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= a.field) return;
+  if (t >= a.field || is_hole(a, t)) return;
   const T *q = static_cast<const T *>(a.q);
   T *pr = static_cast<T *>(a.prim);
   const T rho = q[t], u = q[a.field + t] / rho, v = q[2 * a.field + t] / rho, w = q[3 * a.field + t] / rho;
@@ -105,6 +133,11 @@ __global__ void __launch_bounds__(256) k3c_flux(const Curv3Launch a) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= N) return;
   const int i = (int)(t % a.ni), j = (int)((t / a.ni) % a.nj), k = (int)(t / ((size_t)a.ni * a.nj));
+  T *fl = static_cast<T *>(a.flux);
+  if (is_hole(a, t)) {
+    for (int c = 0; c < 15; ++c) fl[c * N + t] = T(0);
+    return;
+  }
   const T *q = static_cast<const T *>(a.q);
   const T *met = static_cast<const T *>(a.met);
   T M[3][3];
@@ -132,8 +165,7 @@ __global__ void __launch_bounds__(256) k3c_flux(const Curv3Launch a) {
       const T *pf = pr + f * N;
       T Df[3];
 #pragma unroll
-      for (int m = 0; m < 3; ++m)
-        Df[m] = cderiv<T>([&](ptrdiff_t s) { return pf[s]; }, i, j, k, m, a.ni, a.nj, a.nk);
+      for (int m = 0; m < 3; ++m) Df[m] = mderiv<T>(a, [&](ptrdiff_t s) { return pf[s]; }, t, i, j, k, m);
 #pragma unroll
       for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[0] + M[1][d] * Df[1] + M[2][d] * Df[2]);
     }
@@ -149,7 +181,6 @@ __global__ void __launch_bounds__(256) k3c_flux(const Curv3Launch a) {
       F[d][4] -= vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d];
     }
   }
-  T *fl = static_cast<T *>(a.flux);
 #pragma unroll
   for (int m = 0; m < 3; ++m)
 #pragma unroll
@@ -162,16 +193,25 @@ __global__ void __launch_bounds__(256) k3c_update(const Curv3Launch a) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= N) return;
   const int i = (int)(t % a.ni), j = (int)((t / a.ni) % a.nj), k = (int)(t / ((size_t)a.ni * a.nj));
+  T *out = static_cast<T *>(a.out);
+  if (is_hole(a, t)) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v * N + t] = T(0);
+    return;
+  }
   const T *fl = static_cast<const T *>(a.flux);
   const T Jac = static_cast<const T *>(a.met)[9 * N + t];
-  T *out = static_cast<T *>(a.out);
+  unsigned code[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) code[m] = pcode(a, t, i, j, k, m);
+  const ptrdiff_t st[3] = {1, (ptrdiff_t)a.ni, (ptrdiff_t)a.ni * a.nj};
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     T s = T(0);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const T *f = fl + (5 * m + v) * N;
-      s += cderiv<T>([&](ptrdiff_t q) { return f[q]; }, i, j, k, m, a.ni, a.nj, a.nk);
+      s += dtap<T>([&](ptrdiff_t q) { return f[q]; }, (ptrdiff_t)t, st[m], code[m]);
     }
     out[v * N + t] = -Jac * s;
   }
@@ -210,6 +250,7 @@ __global__ void __launch_bounds__(128) k3c_far(const Curv3Launch a, size_t nface
     j = 1 + (int)(r / (ni - 2));
   }
   const size_t N = a.field, p = ((size_t)k * nj + j) * ni + i;
+  if (is_hole(a, p)) return;
   const T *q = static_cast<const T *>(a.q);
   const T *met = static_cast<const T *>(a.met);
   T *out = static_cast<T *>(a.out);
@@ -305,7 +346,7 @@ __global__ void __launch_bounds__(64) k3c_isat(const Curv3Launch a, Curv3Sat s) 
     T g[4][3];
     for (int f = 0; f < 4; ++f) {
       T Df[3];
-      for (int m = 0; m < 3; ++m) Df[m] = cderiv<T>([&](ptrdiff_t x) { return prim(x, f); }, i, j, k, m, a.ni, a.nj, a.nk);
+      for (int m = 0; m < 3; ++m) Df[m] = mderiv<T>(a, [&](ptrdiff_t x) { return prim(x, f); }, p, i, j, k, m);
 #pragma unroll
       for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[0] + M[1][d] * Df[1] + M[2][d] * Df[2]);
     }
@@ -377,6 +418,168 @@ cudaError_t launch3c_metrics(int ni, int nj, int nk, const double *xyz, double *
   k3c_dx<<<blocks, 256, 0, s>>>(ni, nj, nk, xyz, dx);
   if (dtype == SBP_F64) k3c_metrics<double><<<blocks, 256, 0, s>>>(ni, nj, nk, xyz, dx, (double *)met);
   else k3c_metrics<float><<<blocks, 256, 0, s>>>(ni, nj, nk, xyz, dx, (float *)met);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Overset pairs of curvilinear meshes: donor values, the Adams-Bashforth combine, the time step.
+
+template <typename T>
+__device__ __forceinline__ void donor_state(const Curv3Donor &a, int set, size_t p, T out[5]) {
+  const T *q = static_cast<const T *>(a.m.q);
+  const size_t N = a.m.field;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    double acc = to_f64(q[v * N + p]);
+    for (int k = 0; k < a.nb[set]; ++k) acc += a.beta[set][k] * to_f64(static_cast<const T *>(a.hist[k])[v * N + p]);
+    out[v] = (T)acc;
+  }
+}
+
+// (u, v, w, T = gamma p / rho) of a conserved state.
+template <typename T>
+__device__ __forceinline__ void prim_of(const T s[5], T gam, T out[4]) {
+  const T rho = s[0], u = s[1] / rho, v = s[2] / rho, w = s[3] / rho;
+  const T pr = (gam - T(1)) * (s[4] - T(0.5) * rho * (u * u + v * v + w * w));
+  out[0] = u;
+  out[1] = v;
+  out[2] = w;
+  out[3] = gam * pr / rho;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k3c_donor(const Curv3Donor a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nsets * a.npts) return;
+  const int set = t / a.npts, dp = t - set * a.npts;
+  const Curv3Launch &m = a.m;
+  const size_t N = m.field;
+  const long long pl = a.pts[dp];
+  const int i = (int)(pl % m.ni), j = (int)((pl / m.ni) % m.nj), k = (int)(pl / ((long long)m.ni * m.nj));
+  const size_t p = (size_t)pl;
+  T s[5];
+  donor_state(a, set, p, s);
+  T *dv = static_cast<T *>(a.dv) + (size_t)set * 17 * a.npts;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) dv[(size_t)v * a.npts + dp] = s[v];
+  if (!m.visc) return;
+  const T gam = (T)m.gam;
+  const T *met = static_cast<const T *>(m.met);
+  // derivatives along each index direction of the primitives of the (extrapolated) state
+  T Df[3][4];
+  const ptrdiff_t st[3] = {1, (ptrdiff_t)m.ni, (ptrdiff_t)m.ni * m.nj};
+  for (int d = 0; d < 3; ++d) {
+    const Row<T> r = decode_row<T>(pcode(m, p, i, j, k, d));
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int e = 0; e < 4; ++e) {
+      T sn[5], pn[4];
+      donor_state(a, set, (size_t)((ptrdiff_t)p + (ptrdiff_t)r.off[e] * st[d]), sn);
+      prim_of(sn, gam, pn);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) acc[f] += r.w[e] * pn[f];
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) Df[d][f] = r.neg ? -acc[f] : acc[f];
+  }
+  T M[3][3];
+#pragma unroll
+  for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[mm][c] = met[(3 * mm + c) * N + p];
+  const T Jac = met[9 * N + p];
+  T g[4][3];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[0][f] + M[1][d] * Df[1][f] + M[2][d] * Df[2][f]);
+  const T mu = (T)m.mu, lam = (T)m.lam, kap = (T)m.kap;
+  const T div = g[0][0] + g[1][1] + g[2][2];
+  const T vel[3] = {s[1] / s[0], s[2] / s[0], s[3] / s[0]};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T tau[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tau[c] = mu * (g[d][c] + g[c][d]) + (c == d ? lam * div : T(0));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dv[(size_t)(5 + 4 * d + c) * a.npts + dp] = tau[c];
+    dv[(size_t)(5 + 4 * d + 3) * a.npts + dp] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k3c_ab(const Curv3Ab a) {
+  const T *q = static_cast<const T *>(a.q);
+  const T *rhs = static_cast<const T *>(a.rhs);
+  T *qn = static_cast<T *>(a.qn);
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < a.field; t += (size_t)gridDim.x * blockDim.x) {
+    T q0[5], r[5], qv[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      q0[v] = q[v * a.field + t];
+      r[v] = rhs[v * a.field + t];
+    }
+    const bool active = !a.cls || (a.cls[t] & 15u) != 15u;
+    ab_update<T, 5>(q0, a.hold, a.alpha, a.nold, a.field, t, r, qv, active ? a.err : nullptr);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qn[v * a.field + t] = qv[v];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k3c_dt(const Curv3Launch a, double pr, unsigned long long *out) {
+  const T *q = static_cast<const T *>(a.q);
+  const T *met = static_cast<const T *>(a.met);
+  const size_t N = a.field;
+  double best = DBL_MAX;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < N; t += (size_t)gridDim.x * blockDim.x) {
+    if (is_hole(a, t)) continue;
+    const double rho = q[t];
+    const double u[3] = {q[N + t] / rho, q[2 * N + t] / rho, q[3 * N + t] / rho};
+    const double pres = (a.gam - 1.0) * ((double)q[4 * N + t] - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    const double c = sqrt(a.gam * pres / rho);
+    const double Jac = met[9 * N + t];
+    double conv = 0.0, g2 = 0.0;
+    for (int m = 0; m < 3; ++m) {
+      const double kv[3] = {Jac * (double)met[(3 * m) * N + t], Jac * (double)met[(3 * m + 1) * N + t],
+                            Jac * (double)met[(3 * m + 2) * N + t]};
+      conv += fabs(u[0] * kv[0] + u[1] * kv[1] + u[2] * kv[2]);
+      g2 += kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+    }
+    const double nu = fmax(a.mu, a.gam * a.mu / pr) / rho;
+    best = fmin(best, 1.0 / (conv + c * sqrt(g2) + 2.0 * nu * g2));
+  }
+  for (int off = 16; off > 0; off >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, off));
+  __shared__ double wmin[8];
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = fmin(best, wmin[w]);
+    atomicMin(out, (unsigned long long)__double_as_longlong(best));
+  }
+}
+
+cudaError_t launch3c_donor(const Curv3Donor &a, int dtype, cudaStream_t s) {
+  const int n = a.nsets * a.npts;
+  if (n <= 0) return cudaSuccess;
+  if (dtype == SBP_F64) k3c_donor<double><<<(n + 127) / 128, 128, 0, s>>>(a);
+  else k3c_donor<float><<<(n + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch3c_ab(const Curv3Ab &a, int dtype, cudaStream_t s) {
+  const int blocks = (int)std::min<size_t>((a.field + 255) / 256, 152 * 16);
+  if (dtype == SBP_F64) k3c_ab<double><<<blocks, 256, 0, s>>>(a);
+  else k3c_ab<float><<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch3c_dt(const Curv3Launch &a, double pr, unsigned long long *out, cudaStream_t s, int dtype) {
+  // 0x7F in every byte: a positive double near 1.4e306, above any time step (the min's start)
+  cudaError_t e = cudaMemsetAsync(out, 0x7F, sizeof(*out), s);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)std::min<size_t>((a.field + 255) / 256, 152 * 8);
+  if (dtype == SBP_F64) k3c_dt<double><<<blocks, 256, 0, s>>>(a, pr, out);
+  else k3c_dt<float><<<blocks, 256, 0, s>>>(a, pr, out);
   return cudaGetLastError();
 }
 

@@ -2,7 +2,8 @@
 // Lagrange shape functions): for each point, computational coordinates (s, r, t) with
 // X(s, r, t) = p, X the mesh map interpolated by the 4 x 4 x 4 Lagrange basis on the stencil
 // starting at floor(.) - 1 clamped into the mesh, by Newton's method from a nearby node (points
-// outside the mesh's padded bounding box are refused without a search); the
+// outside the mesh's padded bounding box are refused without a search, points the iteration
+// places outside the mesh without a second search); the
 // weights are that basis at the solution. Hole cut (reading, as for the Cartesian 3D hole cut
 // with the overlapping mesh's index units): a point inside the mesh more than a margin of index
 // units from each of its faces is a hole. Host only: no device calls.
@@ -118,9 +119,20 @@ Box padded_box(const Grid3 &g) {
   return b;
 }
 
-// Newton's method on the interpolated map from s; true when three consecutive steps stay below
-// 1e-10 (the rounding floor follows two steps after the first small one) inside the mesh.
-bool newton(const Grid3 &g, const double *q, double s[3]) {
+// The verdict on an iteration that did not converge at s: 0 (outside the mesh) when the iterate
+// has left the index range by more than one cell, else -1 (retry from another start).
+int failed_at(const Grid3 &g, const double s[3]) {
+  for (int a = 0; a < 3; ++a)
+    if (!(s[a] >= -1.0 && s[a] <= g.n[a])) return 0;
+  return -1;
+}
+
+// Newton's method on the interpolated map from s: 1 when three consecutive steps stay below
+// 1e-10 (the rounding floor follows two steps after the first small one) inside the mesh, 0
+// when they do so outside it, or when the iteration fails (a singular Jacobian, divergence, no
+// convergence in 100 steps) with the iterate more than a cell outside (the point is outside
+// the mesh), -1 when it fails inside.
+int newton(const Grid3 &g, const double *q, double s[3]) {
   int small = 0;
   for (int it = 0; it < 100 && small < 3; ++it) {
     int b[3];
@@ -148,7 +160,7 @@ bool newton(const Grid3 &g, const double *q, double s[3]) {
     const double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) -
                        Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +
                        Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
-    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return failed_at(g, s);
     double step[3];
     for (int a = 0; a < 3; ++a) {
       double M[3][3];
@@ -161,29 +173,32 @@ bool newton(const Grid3 &g, const double *q, double s[3]) {
     bool tiny = true;
     for (int a = 0; a < 3; ++a) {
       s[a] -= step[a];
-      if (!(std::fabs(s[a]) < 1e7)) return false;  // diverged (or not finite): far outside any mesh
+      if (!(std::fabs(s[a]) < 1e7)) return 0;  // diverged (or not finite): far outside the mesh
       tiny = tiny && std::fabs(step[a]) < 1e-10;
     }
     small = tiny ? small + 1 : 0;
   }
-  if (small < 3) return false;
+  if (small < 3) return failed_at(g, s);
   for (int a = 0; a < 3; ++a)
-    if (s[a] < -1e-9 || s[a] > g.n[a] - 1 + 1e-9) return false;
-  return true;
+    if (s[a] < -1e-9 || s[a] > g.n[a] - 1 + 1e-9) return 0;
+  return 1;
 }
 
-// Computational coordinates of q by Newton's method from a nearby node, retried from the nearest
-// of all nodes; false for points outside the padded box without any search.
+// Computational coordinates of q by Newton's method from a nearby node; false for points
+// outside the padded box without any search, and for points the iteration places outside the
+// mesh. Only when the iteration fails inside the mesh is it retried, from the nearest of all
+// nodes.
 bool locate(const Grid3 &g, const Box &box, int stride, const double *q, double s[3]) {
   if (!box.contains(q)) return false;
   int c[3];
   near_node(g, q, stride, c);
   for (int a = 0; a < 3; ++a) s[a] = c[a];
-  if (newton(g, q, s)) return true;
+  const int r = newton(g, q, s);
+  if (r >= 0) return r == 1;
   if (stride == 1) return false;
   near_node(g, q, 1, c);
   for (int a = 0; a < 3; ++a) s[a] = c[a];
-  return newton(g, q, s);
+  return newton(g, q, s) == 1;
 }
 
 }  // namespace

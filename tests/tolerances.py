@@ -84,3 +84,44 @@ def fp32_rhs_tol_3d(q, h, act, rhs_ref):
     H = np.stack([mz, mz * u, mz * v, mz * w + p, (E + p) * w])
     s = np.abs(F) / h[0] + np.abs(G) / h[1] + np.abs(H) / h[2]
     return 16.0 * U32 * 1.5 * float(np.linalg.norm(s[:, act])) / float(np.linalg.norm(rhs_ref[:, act]))
+
+
+def fp32_rhs_tol_curv(q, op, act, rhs_ref, mu=0.0, pr=0.72, unit=U32):
+    """The same bound on a 3D curvilinear mesh (op: an oracle.curv3d.Curvilinear3D): the flux term
+    16 u (3/2) J sum_m |F^_m| with the contravariant fluxes F^_m = sum_j M[m][j] F_j, plus,
+    for Navier-Stokes, 16 u (3/2)^2 (sum_m |grad xi_m|)^2 mu (4/3 |u|_1 (1 + |u|_1) + |T| /
+    (Pr (gamma - 1))) with |u|_1 = |u| + |v| + |w|; relative to the oracle's right-hand side
+    over the active points. u = u32 by default; with unit = U64 it is the FP64 rounding bound,
+    which exceeds 1e-12 where a nearly uniform stream makes the flux differences cancel."""
+    rho, mx, my, mz, E = q
+    u, v, w = mx / rho, my / rho, mz / rho
+    p = (GAMMA - 1.0) * (E - 0.5 * rho * (u * u + v * v + w * w))
+    F = [np.stack([mx, mx * u + p, mx * v, mx * w, (E + p) * u]),
+         np.stack([my, my * u, my * v + p, my * w, (E + p) * v]),
+         np.stack([mz, mz * u, mz * v, mz * w + p, (E + p) * w])]
+    s = 0.0
+    for m in range(3):
+        s = s + np.abs(op.M[m][0] * F[0] + op.M[m][1] * F[1] + op.M[m][2] * F[2])
+    b = 16.0 * unit * 1.5 * op.J * s
+    if mu > 0.0:
+        gk = sum(op.J * np.sqrt(op.M[m][0] ** 2 + op.M[m][1] ** 2 + op.M[m][2] ** 2) for m in range(3))
+        T = GAMMA * p / rho
+        a1 = np.abs(u) + np.abs(v) + np.abs(w)
+        visc = mu * (4.0 / 3.0 * a1 * (1.0 + a1) + np.abs(T) / (pr * (GAMMA - 1.0)))
+        b = b + 16.0 * unit * 2.25 * gk * gk * visc
+    return float(np.linalg.norm(b[:, act])) / float(np.linalg.norm(rhs_ref[:, act]))
+
+
+def viscous_flux_rounding_curv(q, op, act, mu, pr=0.72, unit=U64):
+    """Largest absolute rounding of the Cartesian viscous fluxes on a 3D curvilinear mesh over its
+    active points: the primitives' rounding carried through the gradient (the derivative's row,
+    sum |c| = 3/2, times |grad xi| summed over the three directions) into the stress and the heat
+    flux, 16 u (3/2) (sum_m |grad xi_m|) mu (4/3 |u|_1 (1 + |u|_1) + |T| / (Pr (gamma - 1)))."""
+    rho, mx, my, mz, E = q
+    u, v, w = mx / rho, my / rho, mz / rho
+    p = (GAMMA - 1.0) * (E - 0.5 * rho * (u * u + v * v + w * w))
+    gk = sum(op.J * np.sqrt(op.M[m][0] ** 2 + op.M[m][1] ** 2 + op.M[m][2] ** 2) for m in range(3))
+    a1 = np.abs(u) + np.abs(v) + np.abs(w)
+    T = GAMMA * p / rho
+    b = 16.0 * unit * 1.5 * gk * mu * (4.0 / 3.0 * a1 * (1.0 + a1) + np.abs(T) / (pr * (GAMMA - 1.0)))
+    return float(b[act].max())
