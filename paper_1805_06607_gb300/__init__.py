@@ -197,6 +197,10 @@ _lib.sbp_last_error_message.argtypes = []
 _lib.sbp_last_error_message.restype = ctypes.c_char_p
 
 
+# Flag in the marching kernel's chunk rows (set_rhs_shape): TMA tensor-copy staging.
+STAGE_TMA = 0x10000
+
+
 class SbpError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -489,7 +493,8 @@ class System:
 
     def set_rhs_shape(self, k, strip, rows, rows_update=0):
         """strip 0: kernel pair with `rows` rows per CTA of the flux kernel and `rows_update`
-        (0: the same) of the derivative kernel; 64: marching kernel, chunks of `rows`."""
+        (0: the same) of the derivative kernel; 58: marching kernel, chunks of `rows` (| STAGE_TMA:
+        rows staged by TMA tensor copies); 116 / 244: column-marching kernel, chunks of `rows`."""
         code = int(rows) | (int(rows_update) << 8) if int(strip) == 0 else int(rows)
         _check(_lib.sbp_set_rhs_shape(self.h, k, int(strip), code), "sbp_set_rhs_shape")
         self.info[k] = self.mesh_info(k)

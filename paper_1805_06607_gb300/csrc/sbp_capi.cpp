@@ -549,7 +549,9 @@ sbp_status sbp_set_rhs_shape(sbp_system_t S, int k, int strip, int rows) {
                                    " (column-marching kernel) columns wide");
     if (strip != kMarchW && S->mh[k].ni < strip + 12)
       return fail(SBP_ERR_ARG, "the column-marching kernel needs a mesh at least as wide as its CTA");
-    if (rows < 1 || rows > 65535) return fail(SBP_ERR_ARG, "chunk rows out of range");
+    const int chunk = rows & (kStageTma - 1), staging = rows >> 16;
+    if (chunk < 1 || staging < 0 || staging > 1) return fail(SBP_ERR_ARG, "chunk rows out of range");
+    if (staging && strip != kMarchW) return fail(SBP_ERR_ARG, "TMA staging is the marching kernel's");
     d.strip = d.e_strip = strip;
     d.chunk = d.e_chunk = rows;
   }

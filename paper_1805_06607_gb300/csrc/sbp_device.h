@@ -132,6 +132,10 @@ constexpr int kTileX = 32;
 // Columns of a single-pass (marching) strip: 256 threads cover 4 rows of its 64-column flux
 // window (the strip plus a 3-point halo per side) in one pass.
 constexpr int kMarchW = 58;
+// Flag in the marching kernel's chunk (RhsLaunch::chunk; the rows of sbp_set_rhs_shape for strips
+// of kMarchW columns): stage the state and metric rows by TMA tensor copies (k_march_tma)
+// instead of per-thread cp.async (k_march); both give the same bits.
+constexpr int kStageTma = 0x10000;
 // Output columns of the column-marching kernel's strips (CTAs of 128 or 256 threads, one column
 // per thread, 6 halo columns per side); it needs meshes at least as wide as its CTA.
 constexpr int kColW128 = 128 - 12, kColW256 = 256 - 12;

@@ -142,21 +142,23 @@ __device__ __forceinline__ void march_store_cls(const WinItem wi[2], int r0, uin
 }
 
 // Contravariant fluxes of one point (ring row `row`, window column pc) into the flux ring;
-// INT: the point is interior in both directions (central stencil as constants).
-template <typename T, bool VISC, bool CURV, bool INT>
+// INT: the point is interior in both directions (central stencil as constants). The state and
+// metric rings have QW columns per row with the window's column 0 at ring column qsh (QW = PW,
+// qsh = 0 for the cp.async-staged kernel); the primitive ring has PW.
+template <typename T, bool VISC, bool CURV, bool INT, int QW = March<T, VISC, CURV>::PW>
 __device__ __forceinline__ void march_flux_point(const RhsLaunch &a, const T *qr, const T *mr, const T *prim, T *fr,
-                                                 int row, int pc, unsigned code) {
+                                                 int row, int pc, unsigned code, int qsh = 0) {
   using M = March<T, VISC, CURV>;
   constexpr int PW = M::PW, FW = M::FW;
   const KConst<T> &k = kc<T>(a);
-  const int sl = row & (kRing - 1), o = sl * PW + pc;
+  const int sl = row & (kRing - 1), o = sl * PW + pc, qo = sl * QW + pc + qsh;
   T qp[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) qp[v] = qr[v * kRing * PW + o];
+  for (int v = 0; v < 4; ++v) qp[v] = qr[v * kRing * QW + qo];
   T mt[5];
   if (CURV) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) mt[c] = mr[c * kRing * PW + o];
+    for (int c = 0; c < 5; ++c) mt[c] = mr[c * kRing * QW + qo];
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c) mt[c] = k.mc[c];

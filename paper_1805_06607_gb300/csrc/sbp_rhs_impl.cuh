@@ -9,6 +9,7 @@
 
 #include "sbp_dev.cuh"
 #include "sbp_march_impl.cuh"
+#include "sbp_march_tma.cuh"
 #include "sbp_col_impl.cuh"
 
 namespace sbp {
@@ -80,6 +81,11 @@ cudaError_t launch_rhs_typed(const RhsLaunch &a, bool viscous, cudaStream_t s) {
   if (a.strip == kColW128 || a.strip == kColW256) {
     if (viscous) return curv ? launch_col_w<T, true, true>(a, s) : launch_col_w<T, true, false>(a, s);
     return curv ? launch_col_w<T, false, true>(a, s) : launch_col_w<T, false, false>(a, s);
+  }
+  if (a.strip && (a.chunk & kStageTma)) {
+    if (a.strip != kMarchW) return cudaErrorInvalidValue;
+    if (viscous) return curv ? launch_march_tma<T, true, true>(a, s) : launch_march_tma<T, true, false>(a, s);
+    return curv ? launch_march_tma<T, false, true>(a, s) : launch_march_tma<T, false, false>(a, s);
   }
   if (a.strip) {
     if (viscous) return curv ? launch_march_w<T, true, true>(a, s) : launch_march_w<T, true, false>(a, s);

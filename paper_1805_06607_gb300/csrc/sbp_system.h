@@ -656,7 +656,8 @@ struct sbp_system_s {
   // both with their outputs in the state buffer the next step overwrites (each point's stores
   // come from its own thread; the bound history is only read). Candidates: the split kernels at
   // 4, 8, 16 and 32 rows per CTA, the marching kernel (strips of kMarchW columns) at chunks of
-  // 8, 16, 32, 64 and 128 rows and the column-marching kernel (CTAs of 128 or 256 threads, on
+  // 8, 16, 32, 64 and 128 rows, staged by cp.async or (chunks of 16 to 128) by TMA tensor
+  // copies, and the column-marching kernel (CTAs of 128 or 256 threads, on
   // meshes at least that wide) at chunks of 32 to 256 rows; each timed as the faster of two runs
   // of three launches.
   bool autotune_on = true;
@@ -666,7 +667,9 @@ struct sbp_system_s {
     };
     static const Cand cands[] = {{0, 4, 0},   {0, 8, 0},   {0, 8, 4},   {0, 16, 0},  {0, 16, 8},  {0, 16, 4}, {0, 32, 0},
                                  {0, 32, 16}, {kMarchW, 8, 0}, {kMarchW, 16, 0}, {kMarchW, 32, 0}, {kMarchW, 64, 0},
-                                 {kMarchW, 128, 0}, {kColW128, 32, 0}, {kColW128, 64, 0}, {kColW128, 128, 0},
+                                 {kMarchW, 128, 0}, {kMarchW, 16 | kStageTma, 0}, {kMarchW, 32 | kStageTma, 0},
+                                 {kMarchW, 64 | kStageTma, 0}, {kMarchW, 128 | kStageTma, 0},
+                                 {kColW128, 32, 0}, {kColW128, 64, 0}, {kColW128, 128, 0},
                                  {kColW256, 64, 0}, {kColW256, 128, 0}, {kColW256, 256, 0}};
     Cand step_shape[2] = {{0, 16, 0}, {0, 16, 0}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -682,7 +685,7 @@ struct sbp_system_s {
         for (const Cand &c : cands) {
           if (e != cudaSuccess) continue;
           if (c.strip == 0 && c.rows > mh[k].nj) continue;
-          if (c.strip > 0 && c.rows > 2 * mh[k].nj) continue;
+          if (c.strip > 0 && (c.rows & (kStageTma - 1)) > 2 * mh[k].nj) continue;
           if (c.strip > kMarchW && mh[k].ni < c.strip + 12) continue;  // column marching: a CTA's width
           d.strip = d.e_strip = c.strip;
           if (c.strip) d.chunk = d.e_chunk = c.rows;

@@ -1,4 +1,5 @@
-"""The single-pass marching right-hand-side kernel against the kernel pair and the oracle.
+"""The single-pass marching right-hand-side kernel (rows staged by per-thread cp.async, or by
+TMA tensor copies) against the kernel pair and the oracle.
 
 Both designs perform the same floating-point operations per point in the same order, so the
 right-hand side and whole MRAB runs must agree bit for bit, for every chunk height (chunks that are
@@ -38,7 +39,9 @@ CASES = {
 def _euler(wl):
     """The same meshes and state with the Euler equations (no viscous terms)."""
     return dict(wl, params=dict(wl["params"], physics="euler", mu=0.0))
-SHAPES = [(58, 7), (58, 32), (58, 1), (58, 24), (58, 128), (58, 1000)]
+TMA = 0x10000   # chunk flag: rows staged by TMA tensor copies (k_march_tma)
+SHAPES = [(58, 7), (58, 32), (58, 1), (58, 24), (58, 128), (58, 1000),
+          (58, 7 | TMA), (58, 32 | TMA), (58, 1 | TMA), (58, 128 | TMA), (58, 1000 | TMA)]
 
 
 def _rel(a, b):
@@ -111,7 +114,7 @@ def test_pair_row_splits_bit_identical(sbp, case, dtype):
 def test_march_mrab_bit_identical(sbp, case, dtype):
     wl = CASES[case]()
     runs = []
-    for shape in [(0, 8), (58, 40), (58, 16)]:
+    for shape in [(0, 8), (58, 40), (58, 16), (58, 16 | TMA), (58, 40 | TMA)]:
         g = sbp.System(wl, dtype=dtype)
         g.autotune(False)
         for k in range(2):
@@ -162,7 +165,8 @@ def test_autotuner_reports_a_candidate(sbp):
 def test_bad_shapes_rejected(sbp):
     wl = W.vortex_box_in_box(seed=35, n_bg=40, n_fine=25)
     g = sbp.System(wl)
-    for args in [(0, 12), (48, 32), (32, 32), (64, 32), (58, 0), (58, -3), (0, 16 | (12 << 8))]:
+    for args in [(0, 12), (48, 32), (32, 32), (64, 32), (58, 0), (58, -3), (0, 16 | (12 << 8)), (58, TMA),
+                 (58, 16 | (2 << 16))]:
         with pytest.raises(sbp.SbpError):
             g.set_rhs_shape(0, *args)
 
