@@ -245,10 +245,12 @@ sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
  * shared memory, then derivatives + SAT + update from a halo-3 flux tile; 4, 8, 16 or 32 rows per
  * CTA); a single pass that marches a strip of 58 columns up a chunk of 8, 16, 32, 64 or 128
  * rows, 4 rows per step, with 16-row ring buffers of state, metrics, class bytes (copied one
- * step ahead with cp.async), primitives and fluxes in shared memory (state, metrics and result
- * cross HBM once); and a column-marching single pass (one mesh column per thread, strips of 116
- * or 244 columns, chunks of 32 to 256 rows, one row per step, the j-direction stencil taps in
- * per-thread register windows and one shared-memory row per stage for the i-direction ones). For each mesh the autotuner times every candidate on the bound state, as
+ * step ahead with cp.async, or, at chunks of 16 to 128 rows, the state and metrics by TMA
+ * tensor copies), primitives and fluxes in shared memory (state, metrics and result cross HBM
+ * once); and a column-marching single pass (one mesh column per thread, strips of 116 or 244
+ * columns, chunks of 32 to 256 rows, one row per step, the j-direction stencil taps in
+ * per-thread register windows and one shared-memory row per stage for the i-direction ones).
+ * For each mesh the autotuner times every candidate on the bound state, as
  * the fused right-hand side + MRAB update of the next macro step (its outputs go to the state
  * buffer that step overwrites; the history is only read), and keeps the fastest (reported by
  * sbp_mesh_info_get). It runs at the end of sbp_mrab_init
@@ -259,12 +261,16 @@ sbp_status sbp_autotune(sbp_system_t sys, int enable, void *stream);
 /* Choose the right-hand-side kernel of `mesh` by hand (the autotuner's choice otherwise): strip
  * = 0 selects the kernel pair with rows & 0xFF = 4, 8, 16 or 32 rows per CTA of the flux kernel
  * and rows >> 8 = 4, 8, 16 or 32 rows of the derivative kernel (0: the same); strip = 58 the
- * single-pass marching kernel with chunks of `rows` rows (1..65535); strip = 116 or 244 the
+ * single-pass marching kernel with chunks of rows & 0xFFFF rows (1..65535), its state and metric
+ * rows copied into the shared-memory rings by per-thread cp.async, or, with rows | SBP_STAGE_TMA,
+ * by TMA tensor copies (one thread issues 72 x 4 boxes that complete on an mbarrier; a wait
+ * that runs out after about a second records SBP_ERR_TIMEOUT for sbp_check); strip = 116 or 244 the
  * column-marching kernel (one column per thread, CTAs of 128 or 256 threads, the j-direction
  * stencils from per-thread register windows; meshes at least 128 or 256 points wide) with chunks
  * of `rows` rows. All give the same bits.
  * Later autotuner runs (sbp_mrab_init, sbp_autotune) override the choice; disable the
  * autotuner (sbp_autotune(sys, 0, stream)) to keep it. */
+#define SBP_STAGE_TMA 0x10000
 sbp_status sbp_set_rhs_shape(sbp_system_t sys, int mesh, int strip, int rows);
 
 /* The integrator state of `mesh` between macro steps (after sbp_mrab_init): its current state
