@@ -58,19 +58,24 @@ __device__ __forceinline__ T cderiv(const F &f, int i, int j, int k, int d, int 
   return dtap<T>(f, ((ptrdiff_t)k * nj + j) * ni + i, st[d], line_code(c[d], n[d]));
 }
 
-// Stencil class of point p = (i, j, k) along direction d: from the class map, else whole lines.
+// Stencil class of point p = (i, j, k) along direction d: from the class map (SEG: the kernels'
+// overset-pair instances, a.cls set), else whole lines. A compile-time choice, so that the
+// whole-line kernels carry no class-map registers.
+template <bool SEG>
 __device__ __forceinline__ unsigned pcode(const Curv3Launch &a, size_t p, int i, int j, int k, int d) {
-  if (a.cls) return (a.cls[p] >> (4 * d)) & 15u;
+  if (SEG) return (a.cls[p] >> (4 * d)) & 15u;
   return line_code(d == 0 ? i : (d == 1 ? j : k), d == 0 ? a.ni : (d == 1 ? a.nj : a.nk));
 }
 
-__device__ __forceinline__ bool is_hole(const Curv3Launch &a, size_t p) { return a.cls && (a.cls[p] & 15u) == 15u; }
+template <bool SEG>
+__device__ __forceinline__ bool is_hole(const Curv3Launch &a, size_t p) { return SEG && (a.cls[p] & 15u) == 15u; }
 
 // D_d f at point (i, j, k) of the mesh of a (per segment with a class map).
-template <typename T, typename F>
+template <typename T, bool SEG, typename F>
 __device__ __forceinline__ T mderiv(const Curv3Launch &a, const F &f, size_t p, int i, int j, int k, int d) {
+  if (!SEG) return cderiv<T>(f, i, j, k, d, a.ni, a.nj, a.nk);
   const ptrdiff_t st = d == 0 ? 1 : (d == 1 ? (ptrdiff_t)a.ni : (ptrdiff_t)a.ni * a.nj);
-  return dtap<T>(f, (ptrdiff_t)p, st, pcode(a, p, i, j, k, d));
+  return dtap<T>(f, (ptrdiff_t)p, st, pcode<SEG>(a, p, i, j, k, d));
 }
 
 __global__ void __launch_bounds__(256) k3c_dx(int ni, int nj, int nk, const double *xyz, double *dx) {
@@ -112,10 +117,10 @@ __global__ void __launch_bounds__(256) k3c_metrics(int ni, int nj, int nk, const
   met[9 * N + t] = (T)(1.0 / jinv);
 }
 
-template <typename T>
+template <typename T, bool SEG>
 __global__ void __launch_bounds__(256) k3c_prim(const Curv3Launch a) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (t >= a.field || is_hole(a, t)) return;
+  if (t >= a.field || is_hole<SEG>(a, t)) return;
   const T *q = static_cast<const T *>(a.q);
   T *pr = static_cast<T *>(a.prim);
   const T rho = q[t], u = q[a.field + t] / rho, v = q[2 * a.field + t] / rho, w = q[3 * a.field + t] / rho;
@@ -127,14 +132,14 @@ __global__ void __launch_bounds__(256) k3c_prim(const Curv3Launch a) {
   pr[3 * a.field + t] = gam * p / rho;
 }
 
-template <typename T>
+template <typename T, bool SEG>
 __global__ void __launch_bounds__(256) k3c_flux(const Curv3Launch a) {
   const size_t N = a.field;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= N) return;
   const int i = (int)(t % a.ni), j = (int)((t / a.ni) % a.nj), k = (int)(t / ((size_t)a.ni * a.nj));
   T *fl = static_cast<T *>(a.flux);
-  if (is_hole(a, t)) {
+  if (is_hole<SEG>(a, t)) {
     for (int c = 0; c < 15; ++c) fl[c * N + t] = T(0);
     return;
   }
@@ -165,7 +170,7 @@ __global__ void __launch_bounds__(256) k3c_flux(const Curv3Launch a) {
       const T *pf = pr + f * N;
       T Df[3];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) Df[m] = mderiv<T>(a, [&](ptrdiff_t s) { return pf[s]; }, t, i, j, k, m);
+      for (int m = 0; m < 3; ++m) Df[m] = mderiv<T, SEG>(a, [&](ptrdiff_t s) { return pf[s]; }, t, i, j, k, m);
 #pragma unroll
       for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[0] + M[1][d] * Df[1] + M[2][d] * Df[2]);
     }
@@ -187,31 +192,27 @@ __global__ void __launch_bounds__(256) k3c_flux(const Curv3Launch a) {
     for (int v = 0; v < 5; ++v) fl[(5 * m + v) * N + t] = M[m][0] * F[0][v] + M[m][1] * F[1][v] + M[m][2] * F[2][v];
 }
 
-template <typename T>
+template <typename T, bool SEG>
 __global__ void __launch_bounds__(256) k3c_update(const Curv3Launch a) {
   const size_t N = a.field;
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= N) return;
   const int i = (int)(t % a.ni), j = (int)((t / a.ni) % a.nj), k = (int)(t / ((size_t)a.ni * a.nj));
   T *out = static_cast<T *>(a.out);
-  if (is_hole(a, t)) {
+  if (is_hole<SEG>(a, t)) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[v * N + t] = T(0);
     return;
   }
   const T *fl = static_cast<const T *>(a.flux);
   const T Jac = static_cast<const T *>(a.met)[9 * N + t];
-  unsigned code[3];
-#pragma unroll
-  for (int m = 0; m < 3; ++m) code[m] = pcode(a, t, i, j, k, m);
-  const ptrdiff_t st[3] = {1, (ptrdiff_t)a.ni, (ptrdiff_t)a.ni * a.nj};
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     T s = T(0);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const T *f = fl + (5 * m + v) * N;
-      s += dtap<T>([&](ptrdiff_t q) { return f[q]; }, (ptrdiff_t)t, st[m], code[m]);
+      s += mderiv<T, SEG>(a, [&](ptrdiff_t q) { return f[q]; }, t, i, j, k, m);
     }
     out[v * N + t] = -Jac * s;
   }
@@ -226,7 +227,7 @@ static size_t face_points(int ni, int nj, int nk) {
 // Far-field SAT added to the right-hand side at each face point (one thread per point, all the
 // faces it lies on, in index-direction order), after k3c_update on the same stream. Kept apart
 // from k3c_update so that the penalty's registers do not cut the occupancy of every point.
-template <typename T>
+template <typename T, bool SEG>
 __global__ void __launch_bounds__(128) k3c_far(const Curv3Launch a, size_t nface) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= nface) return;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(128) k3c_far(const Curv3Launch a, size_t nface
     j = 1 + (int)(r / (ni - 2));
   }
   const size_t N = a.field, p = ((size_t)k * nj + j) * ni + i;
-  if (is_hole(a, p)) return;
+  if (is_hole<SEG>(a, p)) return;
   const T *q = static_cast<const T *>(a.q);
   const T *met = static_cast<const T *>(a.met);
   T *out = static_cast<T *>(a.out);
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(128) k3c_interp(int ni, int nj, size_t field, 
 //   rhs += scale * (-(1/p0) [(sigma K^side_k + sigma1 I)(q - qhat_r) - side/2 (F^V_k - F^V_k hat_r)])
 // with sigma1 = mu |k|^2 / 2 and F^V_k = sum_d k_d F^V_d (Navier-Stokes), the receiver's own
 // viscous fluxes from chain-rule gradients of primitives taken from q at the stencil taps.
-template <typename T>
+template <typename T, bool SEG>
 __global__ void __launch_bounds__(64) k3c_isat(const Curv3Launch a, Curv3Sat s) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= s.npt) return;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(64) k3c_isat(const Curv3Launch a, Curv3Sat s) 
     T g[4][3];
     for (int f = 0; f < 4; ++f) {
       T Df[3];
-      for (int m = 0; m < 3; ++m) Df[m] = mderiv<T>(a, [&](ptrdiff_t x) { return prim(x, f); }, p, i, j, k, m);
+      for (int m = 0; m < 3; ++m) Df[m] = mderiv<T, SEG>(a, [&](ptrdiff_t x) { return prim(x, f); }, p, i, j, k, m);
 #pragma unroll
       for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[0] + M[1][d] * Df[1] + M[2][d] * Df[2]);
     }
@@ -395,8 +396,13 @@ __global__ void __launch_bounds__(64) k3c_isat(const Curv3Launch a, Curv3Sat s) 
 cudaError_t launch3c_isat(const Curv3Launch &a, const Curv3Sat &s, int dtype, cudaStream_t st) {
   if (s.npt <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((s.npt + 63) / 64);
-  if (dtype == SBP_F64) k3c_isat<double><<<blocks, 64, 0, st>>>(a, s);
-  else k3c_isat<float><<<blocks, 64, 0, st>>>(a, s);
+  if (a.cls) {
+    if (dtype == SBP_F64) k3c_isat<double, true><<<blocks, 64, 0, st>>>(a, s);
+    else k3c_isat<float, true><<<blocks, 64, 0, st>>>(a, s);
+  } else {
+    if (dtype == SBP_F64) k3c_isat<double, false><<<blocks, 64, 0, st>>>(a, s);
+    else k3c_isat<float, false><<<blocks, 64, 0, st>>>(a, s);
+  }
   return cudaGetLastError();
 }
 
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(128) k3c_donor(const Curv3Donor a) {
   T Df[3][4];
   const ptrdiff_t st[3] = {1, (ptrdiff_t)m.ni, (ptrdiff_t)m.ni * m.nj};
   for (int d = 0; d < 3; ++d) {
-    const Row<T> r = decode_row<T>(pcode(m, p, i, j, k, d));
+    const Row<T> r = decode_row<T>(pcode<true>(m, p, i, j, k, d));
     T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int e = 0; e < 4; ++e) {
       T sn[5], pn[4];
@@ -525,14 +531,14 @@ __global__ void __launch_bounds__(256) k3c_ab(const Curv3Ab a) {
   }
 }
 
-template <typename T>
+template <typename T, bool SEG>
 __global__ void __launch_bounds__(256) k3c_dt(const Curv3Launch a, double pr, unsigned long long *out) {
   const T *q = static_cast<const T *>(a.q);
   const T *met = static_cast<const T *>(a.met);
   const size_t N = a.field;
   double best = DBL_MAX;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < N; t += (size_t)gridDim.x * blockDim.x) {
-    if (is_hole(a, t)) continue;
+    if (is_hole<SEG>(a, t)) continue;
     const double rho = q[t];
     const double u[3] = {q[N + t] / rho, q[2 * N + t] / rho, q[3 * N + t] / rho};
     const double pres = (a.gam - 1.0) * ((double)q[4 * N + t] - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
@@ -578,26 +584,32 @@ cudaError_t launch3c_dt(const Curv3Launch &a, double pr, unsigned long long *out
   cudaError_t e = cudaMemsetAsync(out, 0x7F, sizeof(*out), s);
   if (e != cudaSuccess) return e;
   const int blocks = (int)std::min<size_t>((a.field + 255) / 256, 152 * 8);
-  if (dtype == SBP_F64) k3c_dt<double><<<blocks, 256, 0, s>>>(a, pr, out);
-  else k3c_dt<float><<<blocks, 256, 0, s>>>(a, pr, out);
+  if (a.cls) {
+    if (dtype == SBP_F64) k3c_dt<double, true><<<blocks, 256, 0, s>>>(a, pr, out);
+    else k3c_dt<float, true><<<blocks, 256, 0, s>>>(a, pr, out);
+  } else {
+    if (dtype == SBP_F64) k3c_dt<double, false><<<blocks, 256, 0, s>>>(a, pr, out);
+    else k3c_dt<float, false><<<blocks, 256, 0, s>>>(a, pr, out);
+  }
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool SEG>
 static cudaError_t launch3c_rhs_t(const Curv3Launch &a, cudaStream_t s) {
   const int blocks = (int)((a.field + 255) / 256);
-  if (a.visc) k3c_prim<T><<<blocks, 256, 0, s>>>(a);
-  k3c_flux<T><<<blocks, 256, 0, s>>>(a);
-  k3c_update<T><<<blocks, 256, 0, s>>>(a);
+  if (a.visc) k3c_prim<T, SEG><<<blocks, 256, 0, s>>>(a);
+  k3c_flux<T, SEG><<<blocks, 256, 0, s>>>(a);
+  k3c_update<T, SEG><<<blocks, 256, 0, s>>>(a);
   if (a.far) {
     const size_t nf = face_points(a.ni, a.nj, a.nk);
-    k3c_far<T><<<(unsigned)((nf + 127) / 128), 128, 0, s>>>(a, nf);
+    k3c_far<T, SEG><<<(unsigned)((nf + 127) / 128), 128, 0, s>>>(a, nf);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch3c_rhs(const Curv3Launch &a, int dtype, cudaStream_t s) {
-  return dtype == SBP_F64 ? launch3c_rhs_t<double>(a, s) : launch3c_rhs_t<float>(a, s);
+  if (a.cls) return dtype == SBP_F64 ? launch3c_rhs_t<double, true>(a, s) : launch3c_rhs_t<float, true>(a, s);
+  return dtype == SBP_F64 ? launch3c_rhs_t<double, false>(a, s) : launch3c_rhs_t<float, false>(a, s);
 }
 
 }  // namespace sbp
