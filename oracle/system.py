@@ -11,6 +11,10 @@
   hole cut, stencil classes, metrics, SAT terms, donors (Sec. 2.2), the
   coupled right-hand side, the time step of Sec. 4.1 and the error norm of
   App. C eq. (l2error).
+
+Parity unpinned: the shape of the sponge profile inside the layer
+(``OracleSystem.sponge_strength``, a reading; its depth, its relaxation toward
+the free stream and its decay away from the face are pinned).
 """
 from __future__ import annotations
 
