@@ -434,12 +434,23 @@ template <typename T>
 __device__ __forceinline__ void donor_state(const Curv3Donor &a, int set, size_t p, T out[5]) {
   const T *q = static_cast<const T *>(a.m.q);
   const size_t N = a.m.field;
+  double acc[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    double acc = to_f64(q[v * N + p]);
-    for (int k = 0; k < a.nb[set]; ++k) acc += a.beta[set][k] * to_f64(static_cast<const T *>(a.hist[k])[v * N + p]);
-    out[v] = (T)acc;
+  for (int v = 0; v < 5; ++v) acc[v] = to_f64(q[v * N + p]);
+  // each history slot's five values loaded together (the same sums in the same order)
+#pragma unroll
+  for (int k = 0; k < kMaxHist; ++k) {
+    if (k < a.nb[set]) {
+      const T *h = static_cast<const T *>(a.hist[k]) + p;
+      T hv[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) hv[v] = h[v * N];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] += a.beta[set][k] * to_f64(hv[v]);
+    }
   }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[v] = (T)acc[v];
 }
 
 // (u, v, w, T = gamma p / rho) of a conserved state.

@@ -775,13 +775,23 @@ __device__ __forceinline__ void update_tile(const RhsLaunch &a, int bx, int by, 
 template <typename T>
 __device__ __forceinline__ void set_state(const DonorLaunch &a, int set, size_t p, T out[4]) {
   const T *q = static_cast<const T *>(a.q);
+  double acc[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    double acc = to_f64(q[v * a.d.field + p]);
-    for (int k = 0; k < a.nb[set]; ++k)
-      acc += a.beta[set][k] * to_f64(static_cast<const T *>(a.hist[k])[v * a.d.field + p]);
-    out[v] = (T)acc;
+  for (int v = 0; v < 4; ++v) acc[v] = to_f64(q[v * a.d.field + p]);
+  // each history slot's four values loaded together (the same sums in the same order)
+#pragma unroll
+  for (int k = 0; k < kMaxHist; ++k) {
+    if (k < a.nb[set]) {
+      const T *h = static_cast<const T *>(a.hist[k]) + p;
+      T hv[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) hv[v] = h[v * a.d.field];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v] += a.beta[set][k] * to_f64(hv[v]);
+    }
   }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) out[v] = (T)acc[v];
 }
 
 template <typename T>
