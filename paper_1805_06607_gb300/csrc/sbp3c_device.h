@@ -58,8 +58,10 @@ cudaError_t launch3c_interp(int ni, int nj, size_t field, const void *q, int nre
 // Sec. 3.3 Step 2's extrapolation in time): one thread per (extrapolation set, distinct donor
 // point) writes the state q + sum_k beta[set][k] hist[k] (FP64 accumulation) and, for
 // Navier-Stokes, the Cartesian viscous fluxes of that state by the mesh's own SBP derivatives
-// and metric terms, to dv[(set * 17 + c) * npts + point] (c: 5 state values, then F^V_x,
-// F^V_y, F^V_z, each momentum x, y, z and energy).
+// and metric terms, point-major: dv[(set * npts + point) * kDvPitch + c] (c: 5 state values,
+// then F^V_x, F^V_y, F^V_z, each momentum x, y, z and energy; kDvPitch elements per point so
+// that a point's values are read by 16-byte loads).
+constexpr int kDvPitch = 20;
 struct Curv3Donor {
   Curv3Launch m;                       // the donor mesh (q, met, cls, gas constants)
   const void *hist[kMaxHist];
@@ -70,6 +72,19 @@ struct Curv3Donor {
   void *dv;
 };
 cudaError_t launch3c_donor(const Curv3Donor &a, int dtype, cudaStream_t s);
+
+// Receiver values of one donor-value set: out_c[r] = sum over the 64 stencil points of
+// wi wj wk dv[didx][c] (dv point-major as k3c_donor writes it; didx 64 and dwt 12 (element
+// type) per receiver), c < 5 into qhat (5 x nrecv), c >= 5 into fvhat (12 x nrecv; nval = 17
+// for Navier-Stokes, else 5). One thread per receiver.
+struct Curv3Gather {
+  const void *dv;
+  const int *didx;
+  const void *dwt;
+  int nrecv, nval;
+  void *qhat, *fvhat;
+};
+cudaError_t launch3c_gather(const Curv3Gather &a, int dtype, cudaStream_t s);
 
 // Adams-Bashforth combine (Sec. 3.1-3.3) over the whole mesh: qn = q + sum_{h < nold} alpha[h]
 // hold[h] + alpha[nold] rhs (FP64 accumulation); a non-finite or non-positive-density result at

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cfloat>
+#include <type_traits>
 
 #include "sbp3_penalty.cuh"
 #include "sbp3c_device.h"
@@ -336,21 +337,32 @@ __global__ void __launch_bounds__(64) k3c_isat(const Curv3Launch a, Curv3Sat s) 
     for (int m = 0; m < 3; ++m)
 #pragma unroll
       for (int c = 0; c < 3; ++c) M[m][c] = met[(3 * m + c) * N + p];
-    auto prim = [&](ptrdiff_t x, int f) {
-      const T rho = q[x], u = q[N + x] / rho, v = q[2 * N + x] / rho, w = q[3 * N + x] / rho;
-      if (f == 0) return u;
-      if (f == 1) return v;
-      if (f == 2) return w;
-      const T pr = (gam - T(1)) * (q[4 * N + x] - T(0.5) * rho * (u * u + v * v + w * w));
-      return gam * pr / rho;
-    };
-    T g[4][3];
-    for (int f = 0; f < 4; ++f) {
-      T Df[3];
-      for (int m = 0; m < 3; ++m) Df[m] = mderiv<T, SEG>(a, [&](ptrdiff_t x) { return prim(x, f); }, p, i, j, k, m);
+    // derivatives of the primitives (u, v, w, T) along each index direction: each stencil tap's
+    // primitives formed once for all four (the operations of k3c_prim)
+    T Df[4][3];
+    const ptrdiff_t st[3] = {1, (ptrdiff_t)a.ni, (ptrdiff_t)a.ni * a.nj};
 #pragma unroll
-      for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[0] + M[1][d] * Df[1] + M[2][d] * Df[2]);
+    for (int m = 0; m < 3; ++m) {
+      const Row<T> r = decode_row<T>(SEG ? pcode<SEG>(a, p, i, j, k, m)
+                                         : line_code(m == 0 ? i : (m == 1 ? j : k), m == 0 ? a.ni : (m == 1 ? a.nj : a.nk)));
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const ptrdiff_t x = (ptrdiff_t)p + (ptrdiff_t)r.off[e] * st[m];
+        const T rho = q[x], u = q[N + x] / rho, v = q[2 * N + x] / rho, w = q[3 * N + x] / rho;
+        const T pr = (gam - T(1)) * (q[4 * N + x] - T(0.5) * rho * (u * u + v * v + w * w));
+        const T pv[4] = {u, v, w, gam * pr / rho};
+#pragma unroll
+        for (int f = 0; f < 4; ++f) acc[f] += r.w[e] * pv[f];
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) Df[f][m] = r.neg ? -acc[f] : acc[f];
     }
+    T g[4][3];
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) g[f][d] = Jac * (M[0][d] * Df[f][0] + M[1][d] * Df[f][1] + M[2][d] * Df[f][2]);
     const T mu = (T)a.mu, lam = (T)a.lam, kap = (T)a.kap;
     const T div = g[0][0] + g[1][1] + g[2][2];
     const T vel[3] = {qp[1] / qp[0], qp[2] / qp[0], qp[3] / qp[0]};
@@ -476,9 +488,9 @@ __global__ void __launch_bounds__(128) k3c_donor(const Curv3Donor a) {
   const size_t p = (size_t)pl;
   T s[5];
   donor_state(a, set, p, s);
-  T *dv = static_cast<T *>(a.dv) + (size_t)set * 17 * a.npts;
+  T *dv = static_cast<T *>(a.dv) + ((size_t)set * a.npts + dp) * kDvPitch;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) dv[(size_t)v * a.npts + dp] = s[v];
+  for (int v = 0; v < 5; ++v) dv[v] = s[v];
   if (!m.visc) return;
   const T gam = (T)m.gam;
   const T *met = static_cast<const T *>(m.met);
@@ -518,9 +530,73 @@ __global__ void __launch_bounds__(128) k3c_donor(const Curv3Donor a) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) tau[c] = mu * (g[d][c] + g[c][d]) + (c == d ? lam * div : T(0));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dv[(size_t)(5 + 4 * d + c) * a.npts + dp] = tau[c];
-    dv[(size_t)(5 + 4 * d + 3) * a.npts + dp] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d];
+    for (int c = 0; c < 3; ++c) dv[5 + 4 * d + c] = tau[c];
+    dv[5 + 4 * d + 3] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + kap * g[3][d];
   }
+}
+
+// Receiver values of one donor-value set (the pair's right-hand side), one thread per receiver:
+// each of the 64 stencil points' values read by 16-byte loads from the point-major donor
+// values, accumulated in the stencil order (c, b, a) with the weight wi wj wk.
+template <typename T, int NV>
+__global__ void __launch_bounds__(128) k3c_gather(const Curv3Gather a) {
+  constexpr int VW = 16 / (int)sizeof(T), NL = (NV + VW - 1) / VW;
+  static_assert(NL * VW <= kDvPitch && kDvPitch % VW == 0, "16-byte loads within a point's values");
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.nrecv) return;
+  const T *dv = static_cast<const T *>(a.dv);
+  const T *w = static_cast<const T *>(a.dwt) + 12 * (size_t)r;
+  const int *idx = a.didx + 64 * (size_t)r;
+  T wi[4], wj[4], wk[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    wi[e] = w[e];
+    wj[e] = w[4 + e];
+    wk[e] = w[8 + e];
+  }
+  T acc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int c3 = 0; c3 < 4; ++c3)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int d[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[e] = idx[(c3 * 4 + b) * 4 + e];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const T wt = wi[e] * wj[b] * wk[c3];
+        const V *pv = reinterpret_cast<const V *>(dv + (size_t)d[e] * kDvPitch);
+        T v[NL * VW];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) *reinterpret_cast<V *>(v + l * VW) = pv[l];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc[c] += wt * v[c];
+      }
+    }
+  T *qh = static_cast<T *>(a.qhat);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) qh[(size_t)c * a.nrecv + r] = acc[c];
+  if (NV > 5) {
+    T *fh = static_cast<T *>(a.fvhat);
+#pragma unroll
+    for (int c = 5; c < NV; ++c) fh[(size_t)(c - 5) * a.nrecv + r] = acc[c];
+  }
+}
+
+cudaError_t launch3c_gather(const Curv3Gather &a, int dtype, cudaStream_t s) {
+  if (a.nrecv <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((a.nrecv + 127) / 128);
+  if (a.nval == 17) {
+    if (dtype == SBP_F64) k3c_gather<double, 17><<<blocks, 128, 0, s>>>(a);
+    else k3c_gather<float, 17><<<blocks, 128, 0, s>>>(a);
+  } else {
+    if (dtype == SBP_F64) k3c_gather<double, 5><<<blocks, 128, 0, s>>>(a);
+    else k3c_gather<float, 5><<<blocks, 128, 0, s>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 template <typename T>

@@ -7,7 +7,7 @@
 //    every receiver by the curvilinear donor search (sbp3c_donor_search), the coefficient plan;
 //  * right-hand side of mesh k: donor values on the other mesh (k3c_donor: state, extrapolated
 //    in time for the fast mesh's micro steps, and viscous fluxes at the distinct donor points),
-//    their Lagrange gather at the receivers (k3_gather), the curvilinear flux divergence per
+//    their Lagrange gather at the receivers (k3c_gather), the curvilinear flux divergence per
 //    active segment with the far-field SAT (k3c_prim / k3c_flux / k3c_update / k3c_far), and
 //    the interface SAT at the receivers (k3c_isat);
 //  * MRAB step: the right-hand side into the history ring and the Adams-Bashforth combine
@@ -277,21 +277,20 @@ struct sbp3c_system_s {
     a.nsets = nsets;
     a.npts = md[recv].ndv;
     a.pts = md[recv].dpts;
-    a.dv = (char *)md[recv].dv + (size_t)set0 * 17 * md[recv].ndv * esz;
+    a.dv = (char *)md[recv].dv + (size_t)set0 * kDvPitch * md[recv].ndv * esz;
     return launch3c_donor(a, p.dtype, s);
   }
 
   cudaError_t gather(int k, int set, void *qhat, void *fvhat, cudaStream_t s) const {
-    Gather3Launch g{};
-    g.dv = (const char *)md[k].dv + (size_t)set * 17 * md[k].ndv * esz;
+    Curv3Gather g{};
+    g.dv = (const char *)md[k].dv + (size_t)set * kDvPitch * md[k].ndv * esz;
     g.didx = md[k].didx;
     g.dwt = md[k].dwt;
-    g.ndv = md[k].ndv;
     g.nrecv = md[k].nrecv;
-    g.nval = viscous() ? 17 : 5;
+    g.nval = (viscous() && fvhat) ? 17 : 5;  // no viscous fluxes without a place for them
     g.qhat = qhat;
     g.fvhat = viscous() ? fvhat : nullptr;
-    return launch3_gather(g, p.dtype, s);
+    return launch3c_gather(g, p.dtype, s);
   }
 
   // out = dq/dt of mesh k at q_self with the receiver values of donor set `set`.
@@ -515,8 +514,8 @@ sbp_status sbp3c_system_create(const sbp3c_mesh_desc *meshes, int n_meshes, cons
       CUDA_TRY(upload(d.dwt, wf.data(), wf.size() * sizeof(float)));
     }
     const size_t sets = k == p.fast_mesh ? (size_t)p.step_ratio : 1;
-    CUDA_TRY(cudaMalloc(&d.dv, (sets * 17 * d.ndv + 1) * esz));
-    CUDA_TRY(cudaMemset(d.dv, 0, (sets * 17 * d.ndv + 1) * esz));
+    CUDA_TRY(cudaMalloc(&d.dv, (sets * kDvPitch * d.ndv + 1) * esz));
+    CUDA_TRY(cudaMemset(d.dv, 0, (sets * kDvPitch * d.ndv + 1) * esz));
     CUDA_TRY(cudaMalloc(&d.qhat, (5 * (size_t)d.nrecv + 1) * esz));
     CUDA_TRY(cudaMemset(d.qhat, 0, (5 * (size_t)d.nrecv + 1) * esz));
     CUDA_TRY(cudaMalloc(&d.fvhat, (12 * (size_t)d.nrecv + 1) * esz));
