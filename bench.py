@@ -838,9 +838,12 @@ def _run_curv_pair(hbm_peak, peak_kind, n_bg=128, n_fine=97, steps=10, warmup=3)
         g.mrab_step(warmup)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.profiler.start()  # an ncu run with --profile-from-start off captures these steps
         a.record(stream)
         g.mrab_step(steps)
         b.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         g.check()
         ms = a.elapsed_time(b) / steps
         es = 4 if dtype == "f32" else 8

@@ -253,8 +253,8 @@ __device__ __forceinline__ void col_tick(const RhsLaunch &a, ColWin<T> &w, int L
             const T deta = CURV ? central_taps(tp) : central_taps_w(tp, k.wy[4]);
             const T dxi = w.gi[F4][f];
             if (CURV) {
-              gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
-              gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
+              gr[2 * f] = grad_x<T, true>(mt, dxi, deta);
+              gr[2 * f + 1] = grad_y<T, true>(mt, dxi, deta);
             } else {
               gr[2 * f] = dxi;
               gr[2 * f + 1] = deta;
@@ -270,8 +270,8 @@ __device__ __forceinline__ void col_tick(const RhsLaunch &a, ColWin<T> &w, int L
             const T deta = taps_sum(rj, tp);
             const T dxi = w.gi[F4][f];
             if (CURV) {
-              gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
-              gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
+              gr[2 * f] = grad_x<T, true>(mt, dxi, deta);
+              gr[2 * f + 1] = grad_y<T, true>(mt, dxi, deta);
             } else {
               gr[2 * f] = dxi;
               gr[2 * f + 1] = deta;
@@ -280,21 +280,15 @@ __device__ __forceinline__ void col_tick(const RhsLaunch &a, ColWin<T> &w, int L
         }
         T Fv[3], Gv[3];
         visc_flux_k(k, u, v, gr, Fv, Gv);
-        Fx[0] = qp[1];
-        Fx[1] = qp[1] * u + pr - Fv[0];
-        Fx[2] = qp[2] * u - Fv[1];
-        Fx[3] = (qp[3] + pr) * u - Fv[2];
-        Gx[0] = qp[2];
-        Gx[1] = qp[1] * v - Gv[0];
-        Gx[2] = qp[2] * v + pr - Gv[1];
-        Gx[3] = (qp[3] + pr) * v - Gv[2];
+        ns_flux_x(qp, u, pr, Fv, Fx);
+        ns_flux_y(qp, v, pr, Gv, Gx);
       } else {
         inviscid_flux(qp, k.gam, Fx, Gx, u, v, pr);
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        fx[c] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : Fx[c];
-        fy[c] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : Gx[c];
+        fx[c] = CURV ? dot2_rn(mt[0], Fx[c], mt[1], Gx[c]) : Fx[c];
+        fy[c] = CURV ? dot2_rn(mt[2], Fx[c], mt[3], Gx[c]) : Gx[c];
       }
     }
 #pragma unroll

@@ -232,6 +232,46 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// a b + c d and a b + c d + e f with one fixed rounding order (fma(a, b, c d), fma(a, b,
+// fma(c, d, e f))): the viscous and contravariant fluxes and the metric chain rule that every
+// right-hand-side design evaluates, so that they give the same bits whatever the compiler does.
+template <typename T>
+__device__ __forceinline__ T dot2_rn(T a, T b, T c, T d) {
+  return fma_rn(a, b, mul_rn(c, d));
+}
+template <typename T>
+__device__ __forceinline__ T dot3_rn(T a, T b, T c, T d, T e, T f) {
+  return fma_rn(a, b, fma_rn(c, d, mul_rn(e, f)));
+}
+
+// d/dx and d/dy of a field from its index-direction derivatives (chain rule with the metrics on
+// curvilinear meshes; Cartesian meshes take rows already scaled by 1/h).
+template <typename T, bool CURV>
+__device__ __forceinline__ T grad_x(const T mt[5], T dxi, T deta) {
+  return CURV ? mul_rn(mt[4], dot2_rn(mt[0], dxi, mt[2], deta)) : dxi;
+}
+template <typename T, bool CURV>
+__device__ __forceinline__ T grad_y(const T mt[5], T dxi, T deta) {
+  return CURV ? mul_rn(mt[4], dot2_rn(mt[1], dxi, mt[3], deta)) : deta;
+}
+
+// F - F^V and G - G^V of the Navier-Stokes equations at a point: state qp, velocity (u, v),
+// pressure pr, Cartesian viscous fluxes Fv, Gv (momentum x, momentum y, energy).
+template <typename T>
+__device__ __forceinline__ void ns_flux_x(const T qp[4], T u, T pr, const T Fv[3], T Fx[4]) {
+  Fx[0] = qp[1];
+  Fx[1] = fma_rn(qp[1], u, pr) - Fv[0];
+  Fx[2] = fma_rn(qp[2], u, -Fv[1]);
+  Fx[3] = fma_rn(qp[3] + pr, u, -Fv[2]);
+}
+template <typename T>
+__device__ __forceinline__ void ns_flux_y(const T qp[4], T v, T pr, const T Gv[3], T Gx[4]) {
+  Gx[0] = qp[2];
+  Gx[1] = fma_rn(qp[1], v, -Gv[0]);
+  Gx[2] = fma_rn(qp[2], v, pr) - Gv[1];
+  Gx[3] = fma_rn(qp[3] + pr, v, -Gv[2]);
+}
+
 // p = (gamma - 1)(rho E - (rho u u + rho v v) / 2).
 template <typename T>
 __device__ __forceinline__ T pressure_of(T gam, T rE, T ru, T rv, T u, T v) {
@@ -264,15 +304,16 @@ template <typename T>
 __device__ __forceinline__ void viscous_flux(T u, T v, const T gr[6], T mu, T kap, T Fv[3], T Gv[3]) {
   // gr = (u_x, u_y, v_x, v_y, T_x, T_y)
   T div = gr[0] + gr[3];
-  T txx = mu * (T(2) * gr[0]) - T(2.0 / 3.0) * mu * div;
-  T tyy = mu * (T(2) * gr[3]) - T(2.0 / 3.0) * mu * div;
+  T m23 = T(2.0 / 3.0) * mu;
+  T txx = dot2_rn(mu, T(2) * gr[0], -m23, div);
+  T tyy = dot2_rn(mu, T(2) * gr[3], -m23, div);
   T txy = mu * (gr[1] + gr[2]);
   Fv[0] = txx;
   Fv[1] = txy;
-  Fv[2] = u * txx + v * txy + kap * gr[4];
+  Fv[2] = dot3_rn(u, txx, v, txy, kap, gr[4]);
   Gv[0] = txy;
   Gv[1] = tyy;
-  Gv[2] = u * txy + v * tyy + kap * gr[5];
+  Gv[2] = dot3_rn(u, txy, v, tyy, kap, gr[5]);
 }
 
 // K^{+/-}_k (q - target) of eq. (int), applied through the eigen-decomposition of the flux
@@ -374,8 +415,8 @@ __device__ void visc_at_point(const DevMesh &m, const T *q, int i, int j, T gam,
   T gr[6];
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
-    gr[2 * f] = mt[4] * (mt[0] * dxi[f] + mt[2] * deta[f]);
-    gr[2 * f + 1] = mt[4] * (mt[1] * dxi[f] + mt[3] * deta[f]);
+    gr[2 * f] = grad_x<T, true>(mt, dxi[f], deta[f]);
+    gr[2 * f + 1] = grad_y<T, true>(mt, dxi[f], deta[f]);
   }
   T pc[3];
   prim_at(q, m.field, p, gam, pc);
@@ -409,16 +450,25 @@ __device__ __forceinline__ void load_met(const RhsLaunch &a, int gi, int gj, T m
 
 // Cartesian viscous fluxes from gradients (u_x, u_y, v_x, v_y, T_x, T_y), Stokes hypothesis.
 template <typename T>
-__device__ __forceinline__ void visc_flux_k(const KConst<T> &k, T u, T v, const T gr[6], T Fv[3], T Gv[3]) {
-  T txx = k.mu43 * gr[0] - k.mu23 * gr[3];
-  T tyy = k.mu43 * gr[3] - k.mu23 * gr[0];
+__device__ __forceinline__ void visc_flux_kx(const KConst<T> &k, T u, T v, const T gr[6], T Fv[3]) {
+  T txx = dot2_rn(k.mu43, gr[0], -k.mu23, gr[3]);
   T txy = k.mu * (gr[1] + gr[2]);
   Fv[0] = txx;
   Fv[1] = txy;
-  Fv[2] = u * txx + v * txy + k.kap * gr[4];
+  Fv[2] = dot3_rn(u, txx, v, txy, k.kap, gr[4]);
+}
+template <typename T>
+__device__ __forceinline__ void visc_flux_ky(const KConst<T> &k, T u, T v, const T gr[6], T Gv[3]) {
+  T tyy = dot2_rn(k.mu43, gr[3], -k.mu23, gr[0]);
+  T txy = k.mu * (gr[1] + gr[2]);
   Gv[0] = txy;
   Gv[1] = tyy;
-  Gv[2] = u * txy + v * tyy + k.kap * gr[5];
+  Gv[2] = dot3_rn(u, txy, v, tyy, k.kap, gr[5]);
+}
+template <typename T>
+__device__ __forceinline__ void visc_flux_k(const KConst<T> &k, T u, T v, const T gr[6], T Fv[3], T Gv[3]) {
+  visc_flux_kx(k, u, v, gr, Fv);
+  visc_flux_ky(k, u, v, gr, Gv);
 }
 
 // Gradients of (u, v, T) at smem index r of the primitive planes (row stride rx), chain rule
@@ -438,13 +488,8 @@ __device__ __forceinline__ void smem_grads(const RhsLaunch &a, const T *prim, in
   for (int f = 0; f < 3; ++f) {
     T dxi = row_sum(ri, pi, f * rn);
     T deta = row_sum(rj, pj, f * rn);
-    if (CURV) {
-      gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
-      gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
-    } else {
-      gr[2 * f] = dxi;
-      gr[2 * f + 1] = deta;
-    }
+    gr[2 * f] = grad_x<T, CURV>(mt, dxi, deta);
+    gr[2 * f + 1] = grad_y<T, CURV>(mt, dxi, deta);
   }
 }
 
@@ -616,14 +661,8 @@ __device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T 
       smem_grads<T, CURV>(a, prim, RN, r, RX, scls[r], mt, gr);
       T Fv[3], Gv[3];
       visc_flux_k(k, u, v, gr, Fv, Gv);
-      Fx[0] = qp[1];
-      Fx[1] = qp[1] * u + pr - Fv[0];
-      Fx[2] = qp[2] * u - Fv[1];
-      Fx[3] = (qp[3] + pr) * u - Fv[2];
-      Gx[0] = qp[2];
-      Gx[1] = qp[1] * v - Gv[0];
-      Gx[2] = qp[2] * v + pr - Gv[1];
-      Gx[3] = (qp[3] + pr) * v - Gv[2];
+      ns_flux_x(qp, u, pr, Fv, Fx);
+      ns_flux_y(qp, v, pr, Gv, Gx);
     } else {
       inviscid_flux(qp, k.gam, Fx, Gx, u, v, pr);
     }
@@ -631,8 +670,8 @@ __device__ __forceinline__ void flux_tile(const RhsLaunch &a, int bx, int by, T 
     // scaled rows give d/dx, d/dy)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      fl[c * m.field + p] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : Fx[c];
-      fl[(4 + c) * m.field + p] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : Gx[c];
+      fl[c * m.field + p] = CURV ? dot2_rn(mt[0], Fx[c], mt[1], Gx[c]) : Fx[c];
+      fl[(4 + c) * m.field + p] = CURV ? dot2_rn(mt[2], Fx[c], mt[3], Gx[c]) : Gx[c];
     }
   }
   // SAT terms of this tile's boundary / receiver points (one thread per point)
@@ -872,8 +911,8 @@ __device__ __forceinline__ void donor_group(const DonorLaunch &a, int pair, bool
       T gr[6];
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
-        gr[2 * f] = mt[4] * (mt[0] * cx[f] + mt[2] * cy[f]);
-        gr[2 * f + 1] = mt[4] * (mt[1] * cx[f] + mt[3] * cy[f]);
+        gr[2 * f] = grad_x<T, true>(mt, cx[f], cy[f]);
+        gr[2 * f + 1] = grad_y<T, true>(mt, cx[f], cy[f]);
       }
       T Fv[3], Gv[3];
       viscous_flux(pr[0], pr[1], gr, mu, kap, Fv, Gv);

@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(256) k_interp(const InterpLaunch a) {
       T gr[6];
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
-        gr[2 * f] = mt[4] * (mt[0] * dxi[f] + mt[2] * deta[f]);
-        gr[2 * f + 1] = mt[4] * (mt[1] * dxi[f] + mt[3] * deta[f]);
+        gr[2 * f] = grad_x<T, true>(mt, dxi[f], deta[f]);
+        gr[2 * f + 1] = grad_y<T, true>(mt, dxi[f], deta[f]);
       }
       T pc[3];
       donor_prim(a, ii, jj, gam, pc);

@@ -193,8 +193,8 @@ __device__ __forceinline__ void march_flux_point(const RhsLaunch &a, const T *qr
       if (CURV) {
         T dxi = INT ? central_sum(pi, f * kRing * PW) : row_sum(ri, pi, f * kRing * PW);
         T deta = INT ? central_sum(pj, f * kRing * PW) : row_sum(rj, pj, f * kRing * PW);
-        gr[2 * f] = mt[4] * (mt[0] * dxi + mt[2] * deta);
-        gr[2 * f + 1] = mt[4] * (mt[1] * dxi + mt[3] * deta);
+        gr[2 * f] = grad_x<T, true>(mt, dxi, deta);
+        gr[2 * f + 1] = grad_y<T, true>(mt, dxi, deta);
       } else {
         gr[2 * f] = INT ? central_sum_w(pi, f * kRing * PW, k.wx[4]) : row_sum(ri, pi, f * kRing * PW);
         gr[2 * f + 1] = INT ? central_sum_w(pj, f * kRing * PW, k.wy[4]) : row_sum(rj, pj, f * kRing * PW);
@@ -202,22 +202,16 @@ __device__ __forceinline__ void march_flux_point(const RhsLaunch &a, const T *qr
     }
     T Fv[3], Gv[3];
     visc_flux_k(k, u, v, gr, Fv, Gv);
-    Fx[0] = qp[1];
-    Fx[1] = qp[1] * u + pr - Fv[0];
-    Fx[2] = qp[2] * u - Fv[1];
-    Fx[3] = (qp[3] + pr) * u - Fv[2];
-    Gx[0] = qp[2];
-    Gx[1] = qp[1] * v - Gv[0];
-    Gx[2] = qp[2] * v + pr - Gv[1];
-    Gx[3] = (qp[3] + pr) * v - Gv[2];
+    ns_flux_x(qp, u, pr, Fv, Fx);
+    ns_flux_y(qp, v, pr, Gv, Gx);
   } else {
     inviscid_flux(qp, k.gam, Fx, Gx, u, v, pr);
   }
   const int fo = sl * FW + pc - 3;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    fr[c * kRing * FW + fo] = CURV ? mt[0] * Fx[c] + mt[1] * Gx[c] : Fx[c];
-    fr[(4 + c) * kRing * FW + fo] = CURV ? mt[2] * Fx[c] + mt[3] * Gx[c] : Gx[c];
+    fr[c * kRing * FW + fo] = CURV ? dot2_rn(mt[0], Fx[c], mt[1], Gx[c]) : Fx[c];
+    fr[(4 + c) * kRing * FW + fo] = CURV ? dot2_rn(mt[2], Fx[c], mt[3], Gx[c]) : Gx[c];
   }
 }
 
