@@ -626,10 +626,14 @@ sbp_status sbp3c_hole_cut(const int *n, const double *x, const double *y, const 
  * base[3 r + 2] + c) for the 5 variables v. q: a state (5 device planes); base (3 ints per
  * receiver) and w (12 doubles per receiver) as sbp3c_donor_search writes them, copied to the
  * device by the caller; out: 5 planes of nrecv elements of the mesh's element type (device).
- * The weights are applied in the element type. Stencils must lie inside the mesh (the search
- * guarantees it; nothing checks it here). Asynchronous on stream. */
+ * The weights are applied in the element type. A stencil that does not lie inside the mesh
+ * (base outside 0 .. n[a] - 4 in some direction) gives zeros for that receiver and records
+ * SBP_ERR_BOUNDS in the mesh's device error word (read by sbp3c_mesh_check), without reading out
+ * of range. Asynchronous on stream. */
 sbp_status sbp3c_interp(sbp3c_mesh_t mesh, const void *q, int nrecv, const int *base, const double *w, void *out,
                         void *stream);
+/* Synchronise the stream and report (then clear) the mesh's device error word. */
+sbp_status sbp3c_mesh_check(sbp3c_mesh_t mesh, void *stream);
 /* Interface SAT terms at receiver points (Sec. 2.2 eq. (int), the normal of index direction m
  * being k = grad xi_m = J M[m][:]). sbp3c_set_interface stores nterms terms (host, copied):
  * terms[6 e ..] = (i, j, k, m, side, r): receiver point (i, j, k), normal direction m (0..2),
@@ -733,6 +737,13 @@ sbp_status sbp3c_system_check(sbp3c_system_t sys, void *stream);
 
 /* Synchronise the stream and report (then clear) the device error word. */
 sbp_status sbp_check(sbp_system_t sys, void *stream);
+
+/* Bounds checks. The gathers that follow tables built by the library's setup (donor indices into
+ * the distinct donor points) check their indices in builds compiled with SBP_BOUNDS_CHECK
+ * defined (paper_1805_06607_gb300/build.py: build(bounds_check=True), into _build_checked/): an
+ * index out of range is replaced by a valid one and recorded as SBP_ERR_BOUNDS in the system's
+ * device error word, read by the system's check call. Indices the caller supplies
+ * (sbp3c_interp's stencil bases) are checked in every build. */
 
 const char *sbp_status_string(sbp_status s);
 const char *sbp_last_error_message(void);

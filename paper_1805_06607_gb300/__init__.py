@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsbpmrab.so")
+# SBP_MRAB_LIBRARY may name another build of the library (e.g. the bounds-checked one of
+# build.build(bounds_check=True)); the default is the in-tree build
+LIB_PATH = os.environ.get("SBP_MRAB_LIBRARY") or os.path.join(_HERE, "_build", "libsbpmrab.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libsbpmrab.so is not built: run paper_1805_06607_gb300.build.build() "
@@ -169,6 +171,7 @@ _SIGS.update({
     "sbp3c_hole_cut": [_P, _P, _P, _P, _I, _P, ctypes.c_double, _P],
     "sbp3c_set_interface": [_P, _I, _P, _P, _I, ctypes.c_double],
     "sbp3c_interface_sat": [_P, _P, _P, _P, _P, _P],
+    "sbp3c_mesh_check": [_P, _P],
     "sbp3c_system_create": [ctypes.POINTER(Mesh3cDesc), _I, ctypes.POINTER(Params), ctypes.POINTER(_P)],
     "sbp3c_system_destroy": [_P],
     "sbp3c_system_info": [_P, _I, ctypes.POINTER(Mesh3Info)],
@@ -1049,6 +1052,10 @@ class Curvilinear3DMesh:
         out = torch.empty((5, n), dtype=self.tdtype, device="cuda")
         _check(_lib.sbp3c_interp(self.h, _ptr(q), n, _ptr(b), _ptr(wt), _ptr(out), _stream(stream)), "sbp3c_interp")
         return out
+
+    def check(self, stream=None):
+        """Synchronise and report the mesh's device error word (SBP_ERR_BOUNDS from interp)."""
+        _check(_lib.sbp3c_mesh_check(self.h, _stream(stream)), "sbp3c_mesh_check")
 
     def rhs_eval(self, q, out=None, stream=None):
         """q: (5, nk, nj, ni) device tensor of the mesh's element type."""

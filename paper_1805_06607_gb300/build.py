@@ -1,5 +1,7 @@
 """Build the library in-tree: nvcc for sm_103a, one object per source compiled in parallel,
-linked into paper_1805_06607_gb300/_build/libsbpmrab.so (CUDA runtime linked statically)."""
+linked into paper_1805_06607_gb300/_build/libsbpmrab.so (CUDA runtime linked statically); with
+bounds_check=True, a build with SBP_BOUNDS_CHECK defined (the gathers check the table indices
+they follow) into _build_checked/, loaded when SBP_MRAB_LIBRARY names it."""
 from __future__ import annotations
 
 import os
@@ -26,28 +28,34 @@ def _nvcc():
     return "nvcc"
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _paths(bounds_check):
+    out = os.path.join(HERE, "_build_checked") if bounds_check else OUT_DIR
+    return out, os.path.join(out, "libsbpmrab.so")
+
+
+def _stale(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "sbp_mrab.h"),
                                                                   os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
+    out_dir, lib = _paths(bounds_check)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     # host code without floating-point contraction, so that its arithmetic (coordinates, donor
     # search, Adams-Bashforth weights) is the same on x86 and Arm hosts
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-              "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+              "-I", os.path.join(ROOT, "include"), "-I", CSRC] + (["-DSBP_BOUNDS_CHECK"] if bounds_check else [])
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(OUT_DIR, src + ".o")
+        obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
         cmd = [nvcc, *ARCH, *common, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
@@ -59,12 +67,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(out.decode(errors="replace"))
         if pr.returncode:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds_check="--bounds-check" in sys.argv))

@@ -455,6 +455,7 @@ sbp_status sbp3_overset_interp(sbp3_system_t S, int recv, const void *q_donor, v
   g.nval = S->viscous() ? kRv3 : 5;
   g.qhat = qhat;
   g.fvhat = S->viscous() ? fvhat : nullptr;
+  g.err = S->d_err;
   CUDA_TRY(launch3_gather(g, S->p.dtype, s));
   return SBP_OK;
 }

@@ -80,6 +80,7 @@ struct Gather3Launch {
   int ndv, nrecv, nval;
   void *qhat;
   void *fvhat;
+  int *err;   // SBP_BOUNDS_CHECK builds: where an out-of-range donor index is recorded (may be null)
 };
 
 cudaError_t launch3_rhs(const Rhs3Launch &a, int dtype, cudaStream_t s);

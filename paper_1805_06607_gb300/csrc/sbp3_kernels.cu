@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(32) k3_sat(const Rhs3Launch a) {
     for (int t = 0; t < 64; ++t) {  // donor point (c3 * 4 + b) * 4 + e
       const int e = t & 3, b = (t >> 2) & 3, c3 = t >> 4;
       const T wt = w[e] * w[4 + b] * w[8 + c3];
-      const int d = a.didx[64 * recv + t];
+      const int d = checked_index(a.didx[64 * recv + t], a.ndv, a.err);
 #pragma unroll
       for (int c = 0; c < NRV; ++c) rv[c] += wt * dv[c * a.ndv + d];
     }
@@ -805,7 +805,7 @@ __global__ void __launch_bounds__(128) k3_gather(const Gather3Launch a) {
     for (int b = 0; b < 4; ++b)
       for (int e = 0; e < 4; ++e) {
         const T wt = w[e] * w[4 + b] * w[8 + c3];
-        const int d = a.didx[64 * r + (c3 * 4 + b) * 4 + e];
+        const int d = checked_index(a.didx[64 * r + (c3 * 4 + b) * 4 + e], a.ndv, a.err);
         for (int c = 0; c < a.nval; ++c) acc[c] += wt * dv[c * a.ndv + d];
       }
   T *qh = static_cast<T *>(a.qhat);

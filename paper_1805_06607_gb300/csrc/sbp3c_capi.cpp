@@ -22,6 +22,7 @@ struct sbp3c_mesh_s {
   sbp_params p{};
   size_t field = 0, esz = 8;
   void *met = nullptr, *prim = nullptr, *flux = nullptr;
+  int *d_err = nullptr;  // device error word (SBP_ERR_BOUNDS from the gather)
   int far = 0;
   double sig = 0.0, qinf[5] = {0, 0, 0, 0, 0};
   // interface SAT terms grouped by receiver point (device)
@@ -41,6 +42,7 @@ struct sbp3c_mesh_s {
     i_npt = i_nrecv = 0;
   }
   ~sbp3c_mesh_s() {
+    cudaFree(d_err);
     cudaFree(met);
     cudaFree(prim);
     cudaFree(flux);
@@ -82,7 +84,19 @@ sbp_status sbp3c_mesh_create(const int *n, const double *x, const double *y, con
   CUDA_TRY(e);
   if (p.physics == SBP_NS) CUDA_TRY(cudaMalloc(&M->prim, 4 * M->field * M->esz));
   CUDA_TRY(cudaMalloc(&M->flux, 15 * M->field * M->esz));
+  CUDA_TRY(cudaMalloc((void **)&M->d_err, sizeof(int)));
+  CUDA_TRY(cudaMemset(M->d_err, 0, sizeof(int)));
   *out = guard.release();
+  return SBP_OK;
+}
+
+sbp_status sbp3c_mesh_check(sbp3c_mesh_t M, void *stream) {
+  if (!M) return fail(SBP_ERR_ARG, "null mesh");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int e = 0;
+  CUDA_TRY(cudaMemcpy(&e, M->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(M->d_err, 0, sizeof(int)));
+  if (e) return fail((sbp_status)e, "device error word set");
   return SBP_OK;
 }
 
@@ -122,7 +136,8 @@ sbp_status sbp3c_set_farfield(sbp3c_mesh_t M, const double *qinf, double sigma) 
 sbp_status sbp3c_interp(sbp3c_mesh_t M, const void *q, int nrecv, const int *base, const double *w, void *out,
                         void *stream) {
   if (!M || nrecv < 0 || (nrecv > 0 && (!q || !base || !w || !out))) return fail(SBP_ERR_ARG, "bad argument");
-  CUDA_TRY(launch3c_interp(M->n[0], M->n[1], M->field, q, nrecv, base, w, out, M->p.dtype, (cudaStream_t)stream));
+  CUDA_TRY(launch3c_interp(M->n[0], M->n[1], M->n[2], q, nrecv, base, w, out, M->d_err, M->p.dtype,
+                           (cudaStream_t)stream));
   return SBP_OK;
 }
 

@@ -50,9 +50,11 @@ cudaError_t launch3c_rhs(const Curv3Launch &a, int dtype, cudaStream_t s);
 // a.out += the interface SAT terms of s at state a.q (a.met, gas constants as for rhs).
 cudaError_t launch3c_isat(const Curv3Launch &a, const Curv3Sat &s, int dtype, cudaStream_t st);
 // out (5 planes of nrecv) = the 4 x 4 x 4 Lagrange gather of q's 5 planes at each receiver's
-// stencil (base: 3 ints, w: 12 doubles per receiver; device).
-cudaError_t launch3c_interp(int ni, int nj, size_t field, const void *q, int nrecv, const int *base, const double *w,
-                            void *out, int dtype, cudaStream_t s);
+// stencil (base: 3 ints, w: 12 doubles per receiver; device). The bases come from the caller:
+// a stencil that does not lie inside the ni x nj x nk mesh records SBP_ERR_BOUNDS in *err and
+// gives zeros, without reading out of range.
+cudaError_t launch3c_interp(int ni, int nj, int nk, const void *q, int nrecv, const int *base, const double *w,
+                            void *out, int *err, int dtype, cudaStream_t s);
 
 // Donor values of a curvilinear mesh for another mesh's receivers (Sec. 2.2 interpolation with
 // Sec. 3.3 Step 2's extrapolation in time): one thread per (extrapolation set, distinct donor
@@ -81,8 +83,9 @@ struct Curv3Gather {
   const void *dv;
   const int *didx;
   const void *dwt;
-  int nrecv, nval;
+  int nrecv, nval, ndv;
   void *qhat, *fvhat;
+  int *err;   // SBP_BOUNDS_CHECK builds: where an out-of-range donor index is recorded
 };
 cudaError_t launch3c_gather(const Curv3Gather &a, int dtype, cudaStream_t s);
 

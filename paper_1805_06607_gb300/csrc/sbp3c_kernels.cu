@@ -282,11 +282,19 @@ __global__ void __launch_bounds__(128) k3c_far(const Curv3Launch a, size_t nface
 // Overset gather (Sec. 2.2 interpolation): out[v][r] = sum over the 4 x 4 x 4 stencil at base[r]
 // of wi wj wk q[v], weights (FP64) taken in the element type, one thread per receiver.
 template <typename T>
-__global__ void __launch_bounds__(128) k3c_interp(int ni, int nj, size_t field, const T *q, int nrecv,
-                                                  const int *base, const double *w, T *out) {
+__global__ void __launch_bounds__(128) k3c_interp(int ni, int nj, int nk, const T *q, int nrecv,
+                                                  const int *base, const double *w, T *out, int *err) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrecv) return;
+  const size_t field = (size_t)ni * nj * nk;
   const int i0 = base[3 * r], j0 = base[3 * r + 1], k0 = base[3 * r + 2];
+  if (i0 < 0 || j0 < 0 || k0 < 0 || i0 > ni - 4 || j0 > nj - 4 || k0 > nk - 4) {
+    // a stencil outside the mesh (the caller's bases): record it, give zeros, read nothing
+    if (err) atomicCAS(err, 0, (int)SBP_ERR_BOUNDS);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[(size_t)v * nrecv + r] = T(0);
+    return;
+  }
   T wi[4], wj[4], wk[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -418,14 +426,14 @@ cudaError_t launch3c_isat(const Curv3Launch &a, const Curv3Sat &s, int dtype, cu
   return cudaGetLastError();
 }
 
-cudaError_t launch3c_interp(int ni, int nj, size_t field, const void *q, int nrecv, const int *base, const double *w,
-                            void *out, int dtype, cudaStream_t s) {
+cudaError_t launch3c_interp(int ni, int nj, int nk, const void *q, int nrecv, const int *base, const double *w,
+                            void *out, int *err, int dtype, cudaStream_t s) {
   if (nrecv <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((nrecv + 127) / 128);
   if (dtype == SBP_F64)
-    k3c_interp<double><<<blocks, 128, 0, s>>>(ni, nj, field, (const double *)q, nrecv, base, w, (double *)out);
+    k3c_interp<double><<<blocks, 128, 0, s>>>(ni, nj, nk, (const double *)q, nrecv, base, w, (double *)out, err);
   else
-    k3c_interp<float><<<blocks, 128, 0, s>>>(ni, nj, field, (const float *)q, nrecv, base, w, (float *)out);
+    k3c_interp<float><<<blocks, 128, 0, s>>>(ni, nj, nk, (const float *)q, nrecv, base, w, (float *)out, err);
   return cudaGetLastError();
 }
 
@@ -564,7 +572,7 @@ __global__ void __launch_bounds__(128) k3c_gather(const Curv3Gather a) {
     for (int b = 0; b < 4; ++b) {
       int d[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) d[e] = idx[(c3 * 4 + b) * 4 + e];
+      for (int e = 0; e < 4; ++e) d[e] = checked_index(idx[(c3 * 4 + b) * 4 + e], a.ndv, a.err);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const T wt = wi[e] * wj[b] * wk[c3];

@@ -287,6 +287,8 @@ struct sbp3c_system_s {
     g.didx = md[k].didx;
     g.dwt = md[k].dwt;
     g.nrecv = md[k].nrecv;
+    g.ndv = md[k].ndv;
+    g.err = d_err;
     g.nval = (viscous() && fvhat) ? 17 : 5;  // no viscous fluxes without a place for them
     g.qhat = qhat;
     g.fvhat = viscous() ? fvhat : nullptr;

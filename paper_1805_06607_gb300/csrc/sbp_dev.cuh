@@ -232,6 +232,22 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Index checks of the tables the gathers follow, in builds with SBP_BOUNDS_CHECK defined: an
+// index outside [0, n) records SBP_ERR_BOUNDS in *err (when given) and is replaced by 0, a valid
+// entry, so that the kernel neither reads out of range nor stops. Without the flag, the indices
+// are used as they are (the setup builds them in range, and the tests check the tables).
+#ifdef SBP_BOUNDS_CHECK
+__device__ __forceinline__ int checked_index(int d, int n, int *err) {
+  if ((unsigned)d >= (unsigned)n) {
+    if (err) atomicCAS(err, 0, (int)SBP_ERR_BOUNDS);
+    return 0;
+  }
+  return d;
+}
+#else
+__device__ __forceinline__ int checked_index(int d, int, int *) { return d; }
+#endif
+
 // a b + c d and a b + c d + e f with one fixed rounding order (fma(a, b, c d), fma(a, b,
 // fma(c, d, e f))): the viscous and contravariant fluxes and the metric chain rule that every
 // right-hand-side design evaluates, so that they give the same bits whatever the compiler does.
@@ -514,7 +530,7 @@ __device__ void sat_terms(const RhsLaunch &a, int s, const T qp[4], const T mt[5
       const T *dv = static_cast<const T *>(a.dv);
       for (int e = 0; e < 16; ++e) {
         T w = dw[8 * recv + (e & 3)] * dw[8 * recv + 4 + (e >> 2)];
-        int d = a.didx[16 * recv + e];
+        int d = checked_index(a.didx[16 * recv + e], a.ndv, a.err);
 #pragma unroll
         for (int c = 0; c < NRV; ++c) rv[c] += w * dv[c * a.ndv + d];
       }
