@@ -200,7 +200,6 @@ void orc_penalty_matrix2d(const double q[4], double gamma, double kx, double ky,
   memset(K, 0, sizeof(double) * 16);
   for (int a = 0; a < 3; ++a) {
     double fl = 0.5 * (fabs(lam[a]) + side * lam[a]);
-    if (fl == 0.0) continue;
     /* P = prod_{b != a} (A - lam_b I)/(lam_a - lam_b) */
     double P[4][4], T[4][4];
     for (int r = 0; r < 4; ++r)

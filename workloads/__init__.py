@@ -217,6 +217,31 @@ def mms_box_in_box(n, kind="inviscid", gamma=GAMMA, mu=1.0):
     return {"meshes": [bg, fine], "q0": qs, "params": params}
 
 
+def corner_box_in_box(omega_corner=1.0, n_bg=31, n_fine=41, bg_half=4.0, fine_half=2.0, gamma=GAMMA,
+                      order=3, hist_len=4):
+    """Box-in-box pair of the corner-penalty study (Sec. 4.2): periodic background [-4,4]^2 with
+    31 x 31 points, inner box [-2,2]^2 with 41 x 41 points (all faces interface), inviscid. The
+    state is effectively one-dimensional: rho = 1, rho u = 1.25 - 0.01 |x|, rho v = 0 and
+    constant pressure 1/gamma (the paper gives the momentum alone; density and pressure follow
+    the unit-density, unit-sound-speed convention of the other cases). omega_corner weights the
+    interface penalty at fringe points with more than one interface term (eq. (penalty_interp))."""
+    hb = 2.0 * bg_half / n_bg
+    bg = cartesian_mesh("background", (n_bg, n_bg), (-bg_half, -bg_half), (hb, hb), ("periodic",) * 4,
+                        periodic=(True, True))
+    hf = 2.0 * fine_half / (n_fine - 1)
+    fine = cartesian_mesh("fine", (n_fine, n_fine), (-fine_half, -fine_half), (hf, hf), ("interface",) * 4)
+    qs = []
+    for m in (bg, fine):
+        rho = np.ones_like(m["x"])
+        mom = 1.25 - 0.01 * np.abs(m["x"])
+        p = np.full_like(m["x"], 1.0 / gamma)
+        qs.append(np.stack([rho, mom, np.zeros_like(mom), p / (gamma - 1.0) + 0.5 * mom * mom / rho]))
+    params = dict(physics="euler", gamma=gamma, mu=0.0, pr=0.72, order=order, hist_len=hist_len, step_ratio=1,
+                  fast_mesh=1, cfl=1.0, qinf=np.array([1.0, 1.25, 0.0, 1.0 / (gamma * (gamma - 1.0)) + 0.5 * 1.25 ** 2]),
+                  twall=1.0, omega_corner=float(omega_corner))
+    return {"meshes": [bg, fine], "q0": qs, "params": params}
+
+
 def batched_vortices(seed=0, n_systems=64, n_range=(128, 512), ratios=(2, 4, 8), bg_half=5.0, omega=5.0,
                      mach=0.5, order=3, cfl=0.5):
     """Many independent 2D Euler vortex systems: background N x N periodic on [-bg_half, bg_half]^2
