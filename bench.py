@@ -58,6 +58,9 @@ def _args():
     ap.add_argument("--no-curv-pair", action="store_true", help="skip the 3D curvilinear overset pair")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-stability", action="store_true", help="skip the step-matrix stability study")
+    ap.add_argument("--no-corner", action="store_true", help="skip the corner-penalty spectrum study")
+    ap.add_argument("--corner-sigmas", default="0.5,1.0",
+                    help="interface penalties of the corner-penalty study (comma separated)")
     ap.add_argument("--profile-shapes", action="store_true",
                     help="profiling aid: one eager macro step of the cylinder per kernel shape, the CUDA "
                          "profiler started around each (ncu --profile-from-start off), then exit")
@@ -974,6 +977,114 @@ def _run_stability(ratios=(1, 2, 3, 4), rel_tol=3e-3):
     return out
 
 
+def _run_corner_study(sigmas=(0.5, 1.0), omegas=(1.0, 0.5)):
+    """Corner-penalty spectrum study (Sec. 4.2, eq. (penalty_interp)) on the paper's box-in-box case
+    (periodic 31^2 background on [-4,4]^2, 41^2 box on [-2,2]^2, rho u = 1.25 - 0.01 |x|, Euler):
+    for each interface penalty sigma and corner weight Omega, the Jacobian of the coupled right-hand
+    side from the library's forward-mode derivative (one GPU derivative per unknown), all its
+    eigenvalues (dense eigensolver on the host, split by the mirror symmetry y -> -y), and for the
+    classical Runge-Kutta method, AB3 and AB34 the largest step with every dt * lambda inside the
+    approximate stability region (amplification <= 2^(1/100), the appendix's 100-step test), with
+    the eigenvalue that limits it. Where an eigenvector is reported, its weight on the inner box's
+    corner points (within 2 points of a corner) comes from inverse iteration on the host."""
+    import numpy as np
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    import torch
+    import paper_1805_06607_gb300 as sbp
+    from paper_1805_06607_gb300 import stability as S
+    import workloads as W
+
+    t0 = time.perf_counter()
+    ab = {}
+    for hl in (3, 4):
+        h = sbp.HostTables(W.corner_box_in_box(1.0, hist_len=hl))
+        ab[hl] = h.plan()[0]
+        h.close()
+    schemes = {"RK4": (S.rk4_amplification, 4), "AB3": (lambda z: S.ab_amplification(ab[3], z), 1),
+               "AB34": (lambda z: S.ab_amplification(ab[4], z), 1)}
+    out = {"workload": "box-in-box corner case: periodic 31x31 background on [-4,4]^2, 41x41 box on [-2,2]^2 "
+                       "(all faces interface), Euler, rho = 1, rho u = 1.25 - 0.01|x|, rho v = 0, p = 1/gamma",
+           "rows": [], "moved": []}
+    spectra = {}
+    for sig in sigmas:
+        for om in omegas:
+            wl = W.corner_box_in_box(om)
+            g = sbp.System(wl, sigma_interface=sig)
+            g.bind(wl["q0"])
+            q = [g.current_state(k) for k in range(2)]
+            dts, _ = g.timestep(q[0], q[1])
+            torch.cuda.synchronize()
+            tj = time.perf_counter()
+            Jm, host = S.coupled_jacobian(g, q)
+            torch.cuda.synchronize()
+            t_jac = time.perf_counter() - tj
+            mirror = S.mirror_permutation(g, host, axis=1)
+            A = Jm.cpu().numpy()
+            del Jm
+            g.close()
+            te = time.perf_counter()
+            lam = S.operator_spectrum(A, mirror)
+            t_eig = time.perf_counter() - te
+            spectra[(sig, om)] = lam
+            As = sp.csc_matrix(A)
+            n_fine = wl["meshes"][1]["n"]
+            corner = np.array([k == 1 and min(i, n_fine[0] - 1 - i) <= 2 and min(j, n_fine[1] - 1 - j) <= 2
+                               for (k, v, i, j) in host])
+
+            def corner_weight(mu):
+                mu = mu + 1e-9 * np.abs(lam).max()  # beside the eigenvalue: a regular shifted matrix
+                lu = sla.splu((As - mu * sp.identity(As.shape[0], format="csc")).astype(np.complex128).tocsc())
+                v = np.random.default_rng(0).standard_normal(As.shape[0]).astype(np.complex128)
+                for _ in range(8):
+                    v = lu.solve(v)
+                    v /= np.linalg.norm(v)
+                return float(np.sum(np.abs(v[corner]) ** 2))
+
+            i_ab = int(np.argmax(lam.real))
+            i_lo = int(np.argmin(lam.real))
+            real = lam[np.abs(lam.imag) <= 1e-9 * np.abs(lam).max()]
+            row = {"sigma_interface": sig, "omega": om, "unknowns": int(A.shape[0]),
+                   "mirror_split": mirror is not None, "jacobian_s": t_jac, "eig_s": t_eig,
+                   "dt_eq_ts_overall": min(dts),
+                   "abscissa": [lam[i_ab].real, lam[i_ab].imag],
+                   "abscissa_corner_weight": corner_weight(lam[i_ab]),
+                   "min_real": [lam[i_lo].real, lam[i_lo].imag],
+                   "min_real_corner_weight": corner_weight(lam[i_lo]),
+                   "most_negative_real_eigenvalue": float(real.real.min()) if real.size else None,
+                   "most_negative_real_corner_weight": corner_weight(real.real.min()) if real.size else None,
+                   "max_abs_imag": float(np.abs(lam.imag).max()), "steps": {}}
+            for name, (amp, evals) in schemes.items():
+                dt, lim = S.largest_stable_step(amp, lam, 0.5)
+                row["steps"][name] = {"dt_max": dt, "dt_max_per_rhs_eval": dt / evals,
+                                      "dt_max_over_dt_eq_ts_overall": dt / min(dts),
+                                      "limiting_eigenvalue": None if lim is None else [lim.real, lim.imag]}
+            out["rows"].append(row)
+        if len(omegas) == 2:
+            from scipy.spatial import cKDTree
+            a, b = spectra[(sig, omegas[0])], spectra[(sig, omegas[1])]
+            tol = 1e-2 * np.abs(a).max()
+            d, _ = cKDTree(np.c_[b.real, b.imag]).query(np.c_[a.real, a.imag])
+            mv = a[d > tol]
+            top = mv[np.argmax(np.abs(mv))] if mv.size else None
+            left = mv[np.argmin(mv.real)] if mv.size else None
+            out["moved"].append({"sigma_interface": sig, "omegas": list(omegas), "tolerance": tol,
+                                 "count": int(mv.size),
+                                 "largest_magnitude": None if top is None else [top.real, top.imag],
+                                 "most_negative_real": None if left is None else [left.real, left.imag]})
+            if left is not None:
+                # where the corner eigenvalue lands at each scheme's largest stable step
+                for row in out["rows"]:
+                    if row["sigma_interface"] != sig or row["omega"] != omegas[0]:
+                        continue
+                    for name, (amp, _) in schemes.items():
+                        z = row["steps"][name]["dt_max"] * left
+                        row["steps"][name]["corner_z"] = [z.real, z.imag]
+                        row["steps"][name]["corner_amplification"] = float(amp(z)[0])
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def _run_perf_model(ratios=(1, 2, 3, 4), order=3, hist_len=4, rel_tol=3e-3, t_rk4_steps=40):
     """The performance model of Sec. 6.1 against measured GPU time (Tables perfmodelthird and
     perfthird), on a small viscous cylinder shaped like the paper's guiding case (O-grid 96 x 24
@@ -1242,6 +1353,8 @@ def main():
                                     "phases_ms_per_step": {p: v[0] / args.steps for p, v in r2["prof"].items()}}}
     if not args.no_stability and rank == 0:
         line["stability"] = _run_stability()
+    if not args.no_corner and rank == 0:
+        line["corner_study"] = _run_corner_study(tuple(float(x) for x in args.corner_sigmas.split(",")))
     if not args.no_perf_model and rank == 0:
         line["performance_model"] = _run_perf_model()
     if not args.no_adjoint and rank == 0:

@@ -37,7 +37,13 @@ __device__ __forceinline__ Dd sqrt(Dd a) {
   double r = ::sqrt(a.v);
   return Dd(r, a.d / (2.0 * r));
 }
-__device__ __forceinline__ Dd fmax(Dd a, Dd b) { return a.v >= b.v ? a : b; }
+// max(a, b) on the branch the values select; at a tie (the kink) the derivative is the mean of
+// the two one-sided slopes, so that the characteristic splitting (positive part of a wave speed
+// minus the positive part of its negative) still differentiates to the wave speed's derivative
+// when the speed is exactly zero.
+__device__ __forceinline__ Dd fmax(Dd a, Dd b) {
+  return a.v > b.v ? a : (a.v < b.v ? b : Dd(a.v, 0.5 * (a.d + b.d)));
+}
 
 // ---------------------------------------------------------------------------------------------
 // Pointwise functions of the forward kernels, on a generic scalar S (double or Dd).
