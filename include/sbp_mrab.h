@@ -236,7 +236,10 @@ sbp_status sbp_mrab_set_step(sbp_system_t sys, double H);
  * With graphs, each macro step is one graph launch on the caller's stream: the graph is
  * captured once per ring/buffer phase (at most 4 hist_len^2 of them, on first use) and runs
  * the slow right-hand side and the first fast micro step on parallel branches, which both
- * depend only on the states at t. Results are identical in both modes. The phase timers
+ * depend only on the states at t; where the fast receivers' donor points cover at most a
+ * quarter of the slow mesh (split kernels, no periodic wrap of that region), only the slow
+ * mesh's tiles around them precede the fast micro steps, and the rest of the slow right-hand
+ * side runs on a third, low-priority branch beside them. Results are identical in both modes. The phase timers
  * (sbp_profile_enable) force the kernel-by-kernel mode while they are on. */
 sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
 

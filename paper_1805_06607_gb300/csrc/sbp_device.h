@@ -44,10 +44,19 @@ struct KConst {
   T sponge_tab[16];
 };
 
+// A rectangle of tiles [x0, x1) x [y0, y1) of the split kernels' grid (x in kTileX columns, y in
+// the kernel's rows per CTA). mode 0: every tile; 1: the rectangle's tiles only (the grid is the
+// rectangle); 2: every tile outside the rectangle.
+struct TileBox {
+  int mode, x0, x1, y0, y1;
+};
+
 // Right-hand side (+ optional MRAB update) of one mesh: k_flux then k_update.
 struct RhsLaunch {
   DevMesh m;
   Gas g;
+  // tiles of the flux and the update kernel this launch covers (split kernels only)
+  TileBox fbox, ubox;
   KConst<float> cf;
   KConst<double> cd;
   const void *q;

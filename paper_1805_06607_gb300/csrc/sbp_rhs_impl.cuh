@@ -16,24 +16,46 @@ namespace sbp {
 
 // At least 4 (FP32) / 3 (FP64) resident CTAs per SM: caps the registers that the SAT tail
 // (taken by boundary tiles only) would otherwise claim for the whole kernel.
+// The tile of this CTA under the launch's tile box; false: the CTA has no tile (mode 2, inside).
+__device__ __forceinline__ bool box_tile(const TileBox &b, int &bx, int &by) {
+  bx = blockIdx.x;
+  by = blockIdx.y;
+  if (b.mode == 1) {
+    bx += b.x0;
+    by += b.y0;
+  } else if (b.mode == 2) {
+    return !(bx >= b.x0 && bx < b.x1 && by >= b.y0 && by < b.y1);
+  }
+  return true;
+}
+
+// The grid of a launch over a tile box of a full grid nx x ny.
+static inline dim3 box_grid(const TileBox &b, int nx, int ny) {
+  return b.mode == 1 ? dim3((unsigned)(b.x1 - b.x0), (unsigned)(b.y1 - b.y0)) : dim3((unsigned)nx, (unsigned)ny);
+}
+
 template <typename T, bool VISC, bool CURV, int TY>
 __global__ void __launch_bounds__(FluxTile<T, VISC, TY>::NT, (sizeof(T) == 4 ? 4 : 3) * kNT / FluxTile<T, VISC, TY>::NT)
     k_flux(const RhsLaunch a) {
   using F = FluxTile<T, VISC, TY>;
   __shared__ T prim[VISC ? 3 * F::RN : 1];
   __shared__ uint8_t scls[VISC ? F::RN : 1];
-  flux_tile<T, VISC, CURV, TY>(a, blockIdx.x, blockIdx.y, prim, scls);
+  int bx, by;
+  if (!box_tile(a.fbox, bx, by)) return;
+  flux_tile<T, VISC, CURV, TY>(a, bx, by, prim, scls);
 }
 
 template <typename T, bool VISC, bool CURV, int TY>
 __global__ void __launch_bounds__(UpdTile<T, TY>::NT) k_update(const RhsLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  update_tile<T, VISC, CURV, TY>(a, blockIdx.x, blockIdx.y, reinterpret_cast<T *>(smem_raw));
+  int bx, by;
+  if (!box_tile(a.ubox, bx, by)) return;
+  update_tile<T, VISC, CURV, TY>(a, bx, by, reinterpret_cast<T *>(smem_raw));
 }
 
 template <typename T, bool VISC, bool CURV, int TY>
 static cudaError_t launch_flux_t(const RhsLaunch &a, cudaStream_t s) {
-  dim3 grid((a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
+  dim3 grid = box_grid(a.fbox, (a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
   k_flux<T, VISC, CURV, TY><<<grid, FluxTile<T, VISC, TY>::NT, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -48,7 +70,7 @@ static cudaError_t launch_update_t(const RhsLaunch &a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
+  dim3 grid = box_grid(a.ubox, (a.m.ni + kTileX - 1) / kTileX, (a.m.nj + TY - 1) / TY);
   ku<<<grid, U::NT, U::bytes, s>>>(a);
   return cudaGetLastError();
 }

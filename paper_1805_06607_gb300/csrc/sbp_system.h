@@ -112,7 +112,9 @@ struct sbp_system_s {
   // phase), captured on internal streams with the slow RHS and the first fast micro step on
   // parallel branches.
   bool use_graph = true;
-  cudaStream_t cap = nullptr, side = nullptr;
+  // cap, side: the fast chain (high priority); side2: the slow right-hand side's tiles away from
+  // the fast receivers' donors (low priority), beside the fast micro steps
+  cudaStream_t cap = nullptr, side = nullptr, side2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_a = nullptr, ev_b = nullptr;
   std::map<uint64_t, cudaGraphExec_t> graphs;
   // FP64 workspace of the adjoint and tangent calls, per mesh (allocated on first use):
@@ -209,6 +211,7 @@ struct sbp_system_s {
     clear_graphs();
     if (cap) cudaStreamDestroy(cap);
     if (side) cudaStreamDestroy(side);
+    if (side2) cudaStreamDestroy(side2);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (ev_a) cudaEventDestroy(ev_a);
@@ -460,8 +463,11 @@ struct sbp_system_s {
   cudaError_t ensure_capture_streams() {
     cudaError_t e = cudaSuccess;
     if (!cap) {
-      if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
-      if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+      int least = 0, greatest = 0;
+      if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess) return e;
+      if ((e = cudaStreamCreateWithPriority(&cap, cudaStreamNonBlocking, greatest)) != cudaSuccess) return e;
+      if ((e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, greatest)) != cudaSuccess) return e;
+      if ((e = cudaStreamCreateWithPriority(&side2, cudaStreamNonBlocking, least)) != cudaSuccess) return e;
       if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
       if ((e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming)) != cudaSuccess) return e;
       if ((e = cudaEventCreateWithFlags(&ev_a, cudaEventDisableTiming)) != cudaSuccess) return e;
@@ -583,9 +589,55 @@ struct sbp_system_s {
     return e;
   }
 
+  // The slow mesh's tiles that the fast receivers' donor values depend on: the update tiles
+  // (rows ty_u) holding the distinct donor points and their derivative taps (3 points either
+  // way), and the flux tiles (rows ty_f) holding the update tiles' 3-point halos. False (no
+  // split) when the split kernels are not the slow mesh's design, the region reaches across a
+  // periodic edge, or it covers more than a quarter of the update tiles.
+  bool slow_core_boxes(TileBox &fb, TileBox &ub) const {
+    const int F = fast(), Sl = slow();
+    const MeshDev &d = md[Sl];
+    const MeshHost &m = mh[Sl];
+    const std::vector<uint32_t> &pts = mh[F].donor_pts;
+    if (d.strip != 0 || pts.empty()) return false;
+    const int ty_f = d.rows_per_cta, ty_u = d.rows_upd ? d.rows_upd : d.rows_per_cta;
+    int i0 = m.ni, i1 = -1, j0 = m.nj, j1 = -1;
+    for (uint32_t ij : pts) {
+      const int i = (int)(ij & 0xFFFFu), j = (int)(ij >> 16);
+      i0 = std::min(i0, i);
+      i1 = std::max(i1, i);
+      j0 = std::min(j0, j);
+      j1 = std::max(j1, j);
+    }
+    // a point range widened by w on each side: clamped at the ends, refused across a periodic edge
+    auto widen = [](int &a, int &b, int w, int n, int per) {
+      a -= w;
+      b += w;
+      if (a < 0 || b > n - 1) {
+        if (per) return false;
+        a = std::max(a, 0);
+        b = std::min(b, n - 1);
+      }
+      return true;
+    };
+    if (!widen(i0, i1, 3, m.ni, m.per[0]) || !widen(j0, j1, 3, m.nj, m.per[1])) return false;
+    const int nx = (m.ni + kTileX - 1) / kTileX, nyu = (m.nj + ty_u - 1) / ty_u;
+    ub = {1, i0 / kTileX, i1 / kTileX + 1, j0 / ty_u, j1 / ty_u + 1};
+    if (4L * (ub.x1 - ub.x0) * (ub.y1 - ub.y0) > (long)nx * nyu) return false;
+    int fi0 = ub.x0 * kTileX, fi1 = std::min(ub.x1 * kTileX, m.ni) - 1;
+    int fj0 = ub.y0 * ty_u, fj1 = std::min(ub.y1 * ty_u, m.nj) - 1;
+    if (!widen(fi0, fi1, 3, m.ni, m.per[0]) || !widen(fj0, fj1, 3, m.nj, m.per[1])) return false;
+    fb = {1, fi0 / kTileX, fi1 / kTileX + 1, fj0 / ty_f, fj1 / ty_f + 1};
+    return true;
+  }
+
   // Enqueue one macro step (Sec. 3.3) for the current ring heads and state buffers, without
   // changing them. With `side` set, the slow right-hand side and the first fast micro step
   // (which needs only s(t) and f(t)) run on two streams joined before the second micro step.
+  // With side2 as well (graph capture), the slow right-hand side is split: the tiles that the
+  // fast receivers' extrapolated donor values read (slow_core_boxes) stay on the critical path,
+  // and the rest of the mesh runs on side2 beside the fast micro steps (the same kernels and
+  // arithmetic on fewer tiles: the same bits), joined at the end of the macro step.
   // frec (eager mode only): the fast state before micro step j is copied to frec[j].
   cudaError_t issue_step(cudaStream_t s, cudaStream_t sd, void *const *frec = nullptr, const StepCoef *cf = nullptr) {
     if (p.scheme != SBP_MRAB_FASTEST_FIRST) return issue_step_sf(s, sd);
@@ -605,7 +657,22 @@ struct sbp_system_s {
     }
     // slow: receivers from f(t), fused RHS + update into the other buffer
     run(timed(SBP_PHASE_INTERP_SLOW, s, [&] { return donor_vals(Sl, md[F].q[md[F].cur], 0, 1, false, H, s); }));
-    run(timed(SBP_PHASE_RHS_SLOW, s, [&] { return fused(Sl, 0, H, s, cf ? cf->as : nullptr); }));
+    TileBox fb{}, ub{};
+    const bool split = sd && side2 && sd != side2 && sr > 1 && slow_core_boxes(fb, ub);
+    if (split) {
+      RhsLaunch a = fused_args(Sl, 0, H, cf ? cf->as : nullptr);
+      a.fbox = fb;
+      a.ubox = ub;
+      run(launch_rhs(a, p.dtype, viscous(), s));
+      run(cudaEventRecord(ev_a, s));
+      run(cudaStreamWaitEvent(side2, ev_a, 0));
+      a.fbox.mode = 2;
+      a.ubox.mode = 2;
+      run(launch_rhs(a, p.dtype, viscous(), side2));
+      run(cudaEventRecord(ev_b, side2));
+    } else {
+      run(timed(SBP_PHASE_RHS_SLOW, s, [&] { return fused(Sl, 0, H, s, cf ? cf->as : nullptr); }));
+    }
     md[Sl].head = (md[Sl].head + 1) % plan.m;
     // fast receivers for the micro steps that need the slow extrapolant (a_s(t) is now in the ring)
     int first = sd ? 1 : 0;
@@ -630,6 +697,7 @@ struct sbp_system_s {
       md[F].head = (md[F].head + 1) % plan.m;
       md[F].cur ^= 1;
     }
+    if (split) run(cudaStreamWaitEvent(s, ev_b, 0));
     md[Sl] = saved_s;
     md[F] = saved_f;
     return e;
@@ -892,7 +960,8 @@ struct sbp_system_s {
       }
       if (e != cudaSuccess) return e;
       cudaGraphExec_t ex = nullptr;
-      e = cudaGraphInstantiate(&ex, g, 0);
+      // kernel nodes keep the priorities of the streams they were captured on
+      e = cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return e;
       it = graphs.emplace(key, ex).first;
