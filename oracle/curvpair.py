@@ -21,6 +21,11 @@ of ``curv3d``:
     point 1 / (sum_m |u . k_m| + c |K| + 2 nu |K|^2), k_m = grad xi_m = J M[m][:],
     |K|^2 = sum_m |k_m|^2, nu = max(mu, gamma mu / Pr) / rho; the mesh's time step is the
     minimum. On a Cartesian mesh this is orc_dt3d's.
+  * sponge layer (Sec. 5.1; the 2D systems' reading carried to three directions): with
+    ``params["sponge_cells"]`` = D > 0, the background's right-hand side gains -sigma (q - qinf)
+    after its SAT terms, sigma = A ((D - d) / D)^2 for the index distance d < D to the nearest of
+    its six far-field faces (A = ``params["sponge_strength"]``), 0 elsewhere and at holes; the
+    overset mesh has no far-field face and no sponge.
 Time integration (bootstrap, fastest-first MRAB) is inherited from the 2D class: it needs only
 the coupled right-hand side and the time step.
 """
@@ -108,12 +113,31 @@ class OracleCurvPair(OracleSystem):
     def interp(self, k, field):
         return interpolate(np.asarray(field, dtype=np.float64), self.base[k], self.w[k])
 
+    def sponge_strength(self, k):
+        """sigma per point of mesh k (nk, nj, ni): A ((D - d) / D)^2 for the index distance d < D
+        to the nearest far-field face (the background's six faces), 0 elsewhere, at holes and on
+        the overset mesh."""
+        shape = self.meshes[k]["x"].shape
+        D = int(self.p.get("sponge_cells", 0))
+        if k != 0 or D <= 0:
+            return np.zeros(shape)
+        A = float(self.p.get("sponge_strength", 1.0))
+        nk, nj, ni = shape
+        kk, jj, ii = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")
+        d = np.minimum.reduce([ii, ni - 1 - ii, jj, nj - 1 - jj, kk, nk - 1 - kk])
+        sig = np.where(d < D, A * ((D - d) / D) ** 2, 0.0)
+        return np.where(self.iblank[k] != 0, sig, 0.0)
+
     def rhs(self, k, q, qhat, fvhat=None):
         """dq/dt on mesh k given the interpolated donor values at its receivers."""
         q = np.asarray(q, dtype=np.float64)
         qinf = np.asarray(self.p["qinf"], dtype=np.float64) if k == 0 else None
         iface = dict(terms=self.terms[k], qhat=np.asarray(qhat), fvhat=fvhat, sigma=self.sig_int)
-        return self.ops[k].rhs(q, self.gamma, self.mu, self.pr, qinf=qinf, sigma=self.sig_phys, interface=iface)
+        out = self.ops[k].rhs(q, self.gamma, self.mu, self.pr, qinf=qinf, sigma=self.sig_phys, interface=iface)
+        if k == 0 and int(self.p.get("sponge_cells", 0)) > 0:
+            # relaxation toward the far-field state in the sponge layer, after the SAT terms
+            out = out - self.sponge_strength(k)[None] * (q - qinf[:, None, None, None])
+        return out
 
     def dt_mesh(self, k, q):
         op = self.ops[k]

@@ -14,7 +14,11 @@
 * on a warped background with holes and a warped, turned overset mesh, the coupled right-hand
   sides converge to the exact divergence of a smooth Euler state (EOC 2.4 under refinement by
   1.5, the 4-2 operator's closures showing in the L2 norm); with the donor weights of one
-  direction applied in reverse (planted) they do not."""
+  direction applied in reverse (planted) they do not;
+* sponge layer (Sec. 5.1, six points deep) on the background: on a uniform state offset from the
+  free stream it adds -sigma (q - qinf) alone, at one rate for all five variables, decaying away
+  from the faces to zero at the sixth point, zero at holes and on the overset mesh (its profile
+  inside the layer is a reading: parity unpinned for its shape)."""
 import numpy as np
 import pytest
 
@@ -234,3 +238,37 @@ def test_convergence_fails_planted_donor_weight_order(tmp_path):
                                 "e1 = T.coupled_rhs_error(36, 37, 10.5)\n"
                                 "print(np.log(e0 / e1) / np.log(35.0 / 23.0))\n")
     assert float(out) < 1.0
+
+
+def test_sponge_layer_on_the_background():
+    """Sec. 5.1's sponge (six points deep) on the pair's background, on a uniform state offset from
+    the free stream: it adds -sigma (q - qinf) and nothing else, with the same rate for every
+    variable, zero from the sixth point inside the faces on, at holes and on the overset mesh, and a
+    rate that decreases away from the faces (the background Cartesian, as in the free-stream pin, so
+    that the uniform state's flux divergence vanishes on its hole segments too)."""
+    base = dict(eps_bg=0.0)
+    wl = W.curvilinear_pair(sponge_cells=6, sponge_strength=2.0, **base)
+    qinf = np.asarray(wl["params"]["qinf"])
+    off = np.array([0.01, 0.02, -0.01, 0.015, 0.03])
+    qs = [np.broadcast_to((qinf + off)[:, None, None, None], (5,) + m["x"].shape).copy() for m in wl["meshes"]]
+    o = OracleCurvPair(wl)
+    plain = OracleCurvPair(W.curvilinear_pair(**base))
+    sig = o.sponge_strength(0)
+    r = [o.coupled_rhs(k, qs[k], qs[1 - k]) for k in range(2)]
+    p = [plain.coupled_rhs(k, qs[k], qs[1 - k]) for k in range(2)]
+    scale = np.abs(p[0]).max()
+    assert np.abs((r[0] - p[0]) + sig[None] * off[:, None, None, None]).max() <= 1e-13 * scale
+    assert np.array_equal(r[1], p[1])
+    nk, nj, ni = sig.shape
+    kk, jj, ii = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")
+    d = np.minimum.reduce([ii, ni - 1 - ii, jj, nj - 1 - jj, kk, nk - 1 - kk])
+    act = o.iblank[0] != 0
+    assert np.all(sig[d >= 6] == 0.0) and np.all(sig[~act] == 0.0)
+    assert np.all(sig[(d < 6) & act] > 0.0)
+    prof = [sig[(d == e) & act].max() for e in range(6)]
+    assert all(prof[e] == sig[(d == e) & act].min() for e in range(6))  # a function of d alone
+    assert all(prof[e + 1] < prof[e] for e in range(5))
+    # away from the faces the uniform state's right-hand side is the sponge term alone
+    inner = (d >= 1) & (d < 6) & act
+    rate = -r[0][:, inner] / off[:, None]
+    assert np.abs(rate - sig[inner][None]).max() <= 1e-9 * prof[0]

@@ -395,7 +395,7 @@ def rotation3d(angles):
 
 def curvilinear_pair(seed=0, n_bg=24, n_fine=25, ratio=2, eps_bg=0.03, eps_fine=0.02, angles=(0.25, -0.15, 0.35),
                      hole_cells=7, physics="euler", mach=0.3, re=200.0, pr=0.72, pulse_amp=0.05, order=3,
-                     hist_len=None, step_ratio=2, cfl=0.5, omega_corner=1.0):
+                     hist_len=None, step_ratio=2, cfl=0.5, omega_corner=1.0, sponge_cells=0, sponge_strength=1.0):
     """A 3D curvilinear overset pair. Mesh 0: n_bg^3 points over [-1, 1]^3, each coordinate
     displaced by eps_bg sin(2 pi s) sin(2 pi t) of the other two index fractions s, t (far
     field on all six faces). Mesh 1: an n_fine^3 box at 1/ratio of the background spacing,
@@ -444,5 +444,6 @@ def curvilinear_pair(seed=0, n_bg=24, n_fine=25, ratio=2, eps_bg=0.03, eps_fine=
     qinf = np.array([1.0, mach * d[0], mach * d[1], mach * d[2], 1.0 / (GAMMA * (GAMMA - 1.0)) + 0.5 * mach * mach])
     params = dict(physics=physics, gamma=GAMMA, mu=(mach / re if physics == "ns" else 0.0), pr=pr, order=order,
                   hist_len=hist_len or order, step_ratio=step_ratio, fast_mesh=1, cfl=cfl, qinf=qinf, twall=1.0,
-                  omega_corner=omega_corner, hole_cells=hole_cells)
+                  omega_corner=omega_corner, hole_cells=hole_cells, sponge_cells=sponge_cells,
+                  sponge_strength=sponge_strength)
     return {"meshes": meshes, "q0": qs, "params": params, "seed": seed}
