@@ -85,7 +85,8 @@ typedef struct {
    * the form is cited, not printed). Within sponge_cells (0: off, at most 16) points of a
    * far-field face the right-hand side gains -sigma (q - qinf), sigma = sponge_strength
    * ((D - d) / D)^2 for the index distance d < D = sponge_cells to the nearest far-field face.
-   * Forward paths only: the adjoint calls reject a system with a sponge. */
+   * 2D systems and chains, and the background of a 3D curvilinear pair; 3D Cartesian systems
+   * reject it. Forward paths only: the adjoint calls reject a system with a sponge. */
   int sponge_cells;
   double sponge_strength;
 } sbp_params;
@@ -672,7 +673,9 @@ sbp_status sbp3c_rhs_eval(sbp3c_mesh_t mesh, const void *q, void *rhs, void *str
  * stencil; SBP_ERR_DONOR otherwise), the coefficient plan of the 2D systems. Right-hand sides:
  * the 3D curvilinear operator per active segment (metric terms on whole lines), 0 at holes; the
  * receivers' donor values are the other mesh's state and, for Navier-Stokes, its Cartesian
- * viscous fluxes, gathered with the stencils' weights. Time step (the 2D curvilinear form over
+ * viscous fluxes, gathered with the stencils' weights; with sponge_cells > 0 the background's
+ * right-hand side gains the sponge term of sbp_params after its SAT terms (the index distance to
+ * the nearest of its six far-field faces; 0 at holes; the overset mesh has none). Time step (the 2D curvilinear form over
  * three directions): per active point 1 / (sum_m |u . k_m| + c |K| + 2 nu |K|^2), k_m = grad
  * xi_m, |K|^2 = sum_m |k_m|^2, nu = max(mu, gamma mu / Pr) / rho; H = min(cfl dt_slow, SR cfl
  * dt_fast). Integrator: fastest-first MRAB of order `order` with `hist_len` values and step

@@ -104,6 +104,15 @@ struct Curv3Ab {
 };
 cudaError_t launch3c_ab(const Curv3Ab &a, int dtype, cudaStream_t s);
 
+// Sponge layer (Sec. 5.1) of a mesh whose six faces are far field: a.out -= sigma (a.q - a.qinf)
+// at the active points within d < depth index points of the nearest face, sigma = tab[d]
+// (A ((depth - d) / depth)^2, computed on the host); after the SAT terms.
+struct Curv3Sponge {
+  int depth;        // 1..16
+  double tab[16];
+};
+cudaError_t launch3c_sponge(const Curv3Launch &a, const Curv3Sponge &sp, int dtype, cudaStream_t s);
+
 // Time step of the curvilinear mesh at state q (active points): min over points of
 // 1 / (sum_m |u . k_m| + c |K| + 2 nu |K|^2), k_m = J M[m][:], |K|^2 = sum_m |k_m|^2,
 // nu = max(mu, gamma mu / Pr) / rho, as the bits of a positive double min-reduced into *out.

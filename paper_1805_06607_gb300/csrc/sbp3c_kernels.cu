@@ -667,6 +667,29 @@ cudaError_t launch3c_donor(const Curv3Donor &a, int dtype, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One thread per point: the sponge term at the active points within sp.depth of a face.
+template <typename T>
+__global__ void __launch_bounds__(256) k3c_sponge(const Curv3Launch a, const Curv3Sponge sp) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.field) return;
+  const int i = (int)(p % a.ni), j = (int)((p / a.ni) % a.nj), k = (int)(p / ((size_t)a.ni * a.nj));
+  const int d = min(min(min(i, a.ni - 1 - i), min(j, a.nj - 1 - j)), min(k, a.nk - 1 - k));
+  if (d >= sp.depth || (a.cls && a.cls[p] == 0xFFFu)) return;
+  const T sg = (T)sp.tab[d];
+  const T *q = static_cast<const T *>(a.q);
+  T *out = static_cast<T *>(a.out);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[v * a.field + p] = fma_rn(-sg, q[v * a.field + p] - (T)a.qinf[v], out[v * a.field + p]);
+}
+
+cudaError_t launch3c_sponge(const Curv3Launch &a, const Curv3Sponge &sp, int dtype, cudaStream_t s) {
+  if (sp.depth <= 0 || a.field == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((a.field + 255) / 256);
+  if (dtype == SBP_F64) k3c_sponge<double><<<blocks, 256, 0, s>>>(a, sp);
+  else k3c_sponge<float><<<blocks, 256, 0, s>>>(a, sp);
+  return cudaGetLastError();
+}
+
 cudaError_t launch3c_ab(const Curv3Ab &a, int dtype, cudaStream_t s) {
   const int blocks = (int)std::min<size_t>((a.field + 255) / 256, 152 * 16);
   if (dtype == SBP_F64) k3c_ab<double><<<blocks, 256, 0, s>>>(a);

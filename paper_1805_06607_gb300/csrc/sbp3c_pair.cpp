@@ -92,7 +92,8 @@ sbp_status pair_setup(const sbp3c_mesh_desc *meshes, int n_meshes, const sbp_par
   if (p.step_ratio < 1 || p.step_ratio > kMaxSets)
     return fail(SBP_ERR_ARG, "step_ratio must be in 1.." + std::to_string(kMaxSets));
   if (p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_ARG, "curvilinear pairs are fastest-first");
-  if (p.sponge_cells != 0) return fail(SBP_ERR_ARG, "curvilinear pairs have no sponge layer");
+  if (p.sponge_cells < 0 || p.sponge_cells > 16 || !(p.sponge_strength >= 0.0))
+    return fail(SBP_ERR_ARG, "sponge_cells must be in 0..16 and sponge_strength >= 0");
   if (!(p.sigma_interface >= 0.0) || !(p.sigma_physical >= 0.0)) return fail(SBP_ERR_ARG, "penalties");
   pout = p;
   if (!(pout.hole_cells > 0.0)) pout.hole_cells = 4.0;
@@ -312,7 +313,16 @@ struct sbp3c_system_s {
     sat.qhat = md[k].qhat;
     sat.fvhat = md[k].fvhat;
     sat.sig = p.sigma_interface;
-    return launch3c_isat(a, sat, p.dtype, s);
+    e = launch3c_isat(a, sat, p.dtype, s);
+    if (e != cudaSuccess || k != 0 || p.sponge_cells <= 0) return e;
+    // the background's sponge layer (all six faces far field), after its SAT terms
+    Curv3Sponge sp{};
+    sp.depth = p.sponge_cells;
+    for (int d = 0; d < p.sponge_cells; ++d) {
+      const double r = (double)(p.sponge_cells - d) / p.sponge_cells;
+      sp.tab[d] = p.sponge_strength * r * r;
+    }
+    return launch3c_sponge(a, sp, p.dtype, s);
   }
 
   cudaError_t rhs_plain(int k, const void *q_self, const void *q_other, void *out, cudaStream_t s) const {

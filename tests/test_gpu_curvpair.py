@@ -11,7 +11,9 @@ holes, a warped and turned 25^3 overset box), Euler and Navier-Stokes:
 * the time step of each mesh and the macro step: FP64 to 1e-13;
 * bootstrap + 3 MRAB macro steps: increments over the 3 macro steps to the FP64 bar above and
   to the derived FP32 right-hand-side bound (FP32), each with the stored state's rounding floor;
-* a non-finite state planted on the host is reported by the step's check as SBP_ERR_NONFINITE."""
+* a non-finite state planted on the host is reported by the step's check as SBP_ERR_NONFINITE;
+* with the sponge layer on the background (Navier-Stokes, six points deep, strength 2) the same
+  right-hand-side and MRAB bars, and a depth beyond 16 refused."""
 import numpy as np
 import pytest
 
@@ -37,7 +39,10 @@ def sbp():
 
 def case(phys):
     if phys not in _CACHE:
-        wl = W.curvilinear_pair(seed=3, physics=phys)
+        if phys == "ns_sponge":
+            wl = W.curvilinear_pair(seed=3, physics="ns", sponge_cells=6, sponge_strength=2.0)
+        else:
+            wl = W.curvilinear_pair(seed=3, physics=phys)
         _CACHE[phys] = (wl, OracleCurvPair(wl))
     return _CACHE[phys]
 
@@ -56,11 +61,11 @@ def test_tables(sbp, phys):
     g.close()
 
 
-@pytest.mark.parametrize("phys", ["euler", "ns"])
+@pytest.mark.parametrize("phys", ["euler", "ns", "ns_sponge"])
 def test_rhs_and_donor_values(sbp, phys):
     wl, o = case(phys)
     q = wl["q0"]
-    mu = wl["params"]["mu"] if phys == "ns" else 0.0
+    mu = wl["params"]["mu"]
     for dtype in ("f64", "f32"):
         g = sbp.CurvilinearPair(wl, dtype=dtype)
         qd = [g.to_device(k, q[k]) for k in range(2)]
@@ -75,7 +80,7 @@ def test_rhs_and_donor_values(sbp, phys):
             if dtype == "f64":
                 qh, fh = g.overset_interp(k, qd[1 - k])
                 assert rel(qh.cpu().numpy(), o.interp(k, q[1 - k])) < 1e-12, k
-                if phys == "ns":
+                if phys != "euler":
                     # the donor mesh's viscous fluxes are small where its stream is nearly
                     # uniform: 1e-12 relative, or their derived absolute rounding
                     fw = o.interp(k, o.viscflux(1 - k, q[1 - k]))
@@ -97,13 +102,13 @@ def test_timestep(sbp):
     g.close()
 
 
-@pytest.mark.parametrize("phys", ["euler", "ns"])
+@pytest.mark.parametrize("phys", ["euler", "ns", "ns_sponge"])
 def test_mrab(sbp, phys):
     """Bootstrap + 3 macro steps: increments over the 3 macro steps, each side from its own
     start."""
     wl, o = case(phys)
     q0 = wl["q0"]
-    mu = wl["params"]["mu"] if phys == "ns" else 0.0
+    mu = wl["params"]["mu"]
     H = o.macro_step_size(q0)
     n = 3
     y, hf, hs = o.bootstrap(q0, H)
@@ -144,3 +149,22 @@ def test_nonfinite_state_reported(sbp):
         g.check()
     assert e.value.status == -5
     g.close()
+
+
+def test_sponge_changes_the_background_and_bad_depth_is_refused(sbp):
+    wl, o = case("ns_sponge")
+    wl0, _ = case("ns")
+    g, g0 = sbp.CurvilinearPair(wl), sbp.CurvilinearPair(wl0)
+    q = [g.to_device(k, wl["q0"][k]) for k in range(2)]
+    r = [g.to_host(k, g.rhs_eval(k, q[k], q[1 - k])) for k in range(2)]
+    r0 = [g0.to_host(k, g0.rhs_eval(k, q[k], q[1 - k])) for k in range(2)]
+    sig = o.sponge_strength(0)
+    qinf = np.asarray(wl["params"]["qinf"])
+    want = -sig[None] * (wl["q0"][0] - qinf[:, None, None, None])
+    assert np.abs((r[0] - r0[0]) - want).max() <= 1e-12 * np.abs(r0[0]).max()
+    assert np.array_equal(r[1], r0[1])
+    g.close()
+    g0.close()
+    bad = dict(wl, params=dict(wl["params"], sponge_cells=17))
+    with pytest.raises(sbp.SbpError):
+        sbp.CurvilinearPair(bad)
