@@ -354,8 +354,9 @@ def _run_gpu(wl, dtype, steps, warmup, world, local, sample_clocks=True):
     bytes_io = sum(h.numel() * h.element_size() for h in host_in)
     out = {"step_ms": step_ms, "wall_s": wall, "prof": prof, "clocks": clk,
            "e2e_ms": e2e_ms, "e2e_serial_ms": e2e_serial_ms, "h2d": bytes_io, "d2h": bytes_io, "info": inf,
-           # 3 donor-value launches + (flux, update) per right-hand side (1 slow + SR fast)
-           "launches_per_step": 3 + 2 * (1 + wl["params"]["step_ratio"]), "tuning": tuning}
+           # the kernel nodes of the replayed macro-step graph, counted by the library (3 donor-value
+           # launches + flux and update per right-hand side, the slow one in two parts when split)
+           "launches_per_step": g.graph_launches(), "tuning": tuning}
     g.close()
     return out
 

@@ -243,6 +243,10 @@ sbp_status sbp_mrab_set_step(sbp_system_t sys, double H);
  * side runs on a third, low-priority branch beside them. Results are identical in both modes. The phase timers
  * (sbp_profile_enable) force the kernel-by-kernel mode while they are on. */
 sbp_status sbp_use_graphs(sbp_system_t sys, int enable);
+/* Kernel launches in one macro step's CUDA graph: the kernel nodes of the graph that
+ * sbp_mrab_step replayed last (host int; 0 before the first replay). A count of this library's
+ * own launches per macro step, for reports; no counterpart in the paper. */
+sbp_status sbp_graph_launches(sbp_system_t sys, int *kernels);
 
 /* Autotuner of the right-hand side's kernel and block shape. Three kernel designs compute the
  * same bits: a pair (contravariant fluxes of a 32 x rows tile with a halo-3 primitive tile in

@@ -102,6 +102,7 @@ _SIGS = {
     "sbp_check": [_P, _P],
     "sbp_profile_enable": [_P, _I],
     "sbp_use_graphs": [_P, _I],
+    "sbp_graph_launches": [_P, _P],
     "sbp_autotune": [_P, _I, _P],
     "sbp_profile_read": [_P, _P, _P, _I],
     "sbp_set_rhs_shape": [_P, _I, _I, _I],
@@ -504,6 +505,12 @@ class System:
 
     def use_graphs(self, on=True):
         _check(_lib.sbp_use_graphs(self.h, int(bool(on))), "sbp_use_graphs")
+
+    def graph_launches(self):
+        """Kernel launches in the macro-step graph replayed last (0 before the first replay)."""
+        n = ctypes.c_int(0)
+        _check(_lib.sbp_graph_launches(self.h, ctypes.byref(n)), "sbp_graph_launches")
+        return n.value
 
     def profile_enable(self, on=True):
         _check(_lib.sbp_profile_enable(self.h, int(bool(on))), "sbp_profile_enable")

@@ -614,6 +614,12 @@ sbp_status sbp_use_graphs(sbp_system_t S, int enable) {
   return SBP_OK;
 }
 
+sbp_status sbp_graph_launches(sbp_system_t S, int *kernels) {
+  if (!S || !kernels) return fail(SBP_ERR_ARG, "null argument");
+  *kernels = S->last_graph_kernels;
+  return SBP_OK;
+}
+
 sbp_status sbp_profile_enable(sbp_system_t S, int enable) {
   if (!S) return fail(SBP_ERR_ARG, "null system");
   S->prof = enable != 0;

@@ -117,6 +117,8 @@ struct sbp_system_s {
   cudaStream_t cap = nullptr, side = nullptr, side2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_a = nullptr, ev_b = nullptr;
   std::map<uint64_t, cudaGraphExec_t> graphs;
+  std::map<uint64_t, int> graph_kernels;  // kernel nodes of each phase's graph
+  int last_graph_kernels = 0;             // of the graph launched last
   // FP64 workspace of the adjoint and tangent calls, per mesh (allocated on first use):
   // mu 8 planes, ld 6 planes, lp 3 planes, receiver values rv and their adjoint lrv (10 per
   // receiver), far-field adjoint per SAT point (4), donor-point adjoint ldv (10 per point)
@@ -139,6 +141,7 @@ struct sbp_system_s {
   void clear_graphs() {
     for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
+    graph_kernels.clear();
     if (rk_graph) cudaGraphExecDestroy(rk_graph);
     rk_graph = nullptr;
   }
@@ -959,6 +962,24 @@ struct sbp_system_s {
         return ei;
       }
       if (e != cudaSuccess) return e;
+      // count the kernel nodes (the macro step's launches of this library)
+      size_t nn = 0;
+      int nk = 0;
+      e = cudaGraphGetNodes(g, nullptr, &nn);
+      if (e == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        e = cudaGraphGetNodes(g, nodes.data(), &nn);
+        for (size_t i = 0; i < nn && e == cudaSuccess; ++i) {
+          cudaGraphNodeType t;
+          e = cudaGraphNodeGetType(nodes[i], &t);
+          if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+        }
+      }
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return e;
+      }
+      graph_kernels[key] = nk;
       cudaGraphExec_t ex = nullptr;
       // kernel nodes keep the priorities of the streams they were captured on
       e = cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority);
@@ -966,6 +987,7 @@ struct sbp_system_s {
       if (e != cudaSuccess) return e;
       it = graphs.emplace(key, ex).first;
     }
+    last_graph_kernels = graph_kernels[key];
     return cudaGraphLaunch(it->second, s);
   }
 };

@@ -183,6 +183,8 @@ def test_graph_replay_matches_eager_full_size(sbp, dtype):
         g.mrab_step(8)
         g.check()
         out.append([g.to_host(k, g.current_state(k)) for k in range(2)])
+        # donor values 3, the O-grid's 4 micro steps 2 each, the background's right-hand side 2 x 2
+        assert g.graph_launches() == (15 if graphs else 0)
         g.close()
     for k in range(2):
         assert np.array_equal(out[0][k], out[1][k])
