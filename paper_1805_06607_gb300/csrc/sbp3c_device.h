@@ -72,6 +72,14 @@ struct Curv3Donor {
   int nsets, npts;
   const long long *pts;                // linear indices (k nj + j) ni + i on the donor mesh
   void *dv;
+  // Navier-Stokes: the distinct points the donor points' derivative stencils read (ntap linear
+  // indices), 13 indices into them per donor point (the point, then the 4 taps along i, j and
+  // k), and a workspace of 4 values (u, v, w, T of the extrapolated state) per set and tap point,
+  // so that each tap's extrapolated primitives are formed once; NULL tpts: formed per use
+  const long long *tpts;
+  const int *tidx;
+  int ntap;
+  void *tv;
 };
 cudaError_t launch3c_donor(const Curv3Donor &a, int dtype, cudaStream_t s);
 

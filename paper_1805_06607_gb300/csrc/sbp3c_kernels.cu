@@ -505,13 +505,21 @@ __global__ void __launch_bounds__(128) k3c_donor(const Curv3Donor a) {
   // derivatives along each index direction of the primitives of the (extrapolated) state
   T Df[3][4];
   const ptrdiff_t st[3] = {1, (ptrdiff_t)m.ni, (ptrdiff_t)m.ni * m.nj};
+  const T *tvs = a.tpts ? static_cast<const T *>(a.tv) + (size_t)set * a.ntap * 4 : nullptr;
   for (int d = 0; d < 3; ++d) {
     const Row<T> r = decode_row<T>(pcode<true>(m, p, i, j, k, d));
     T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int e = 0; e < 4; ++e) {
-      T sn[5], pn[4];
-      donor_state(a, set, (size_t)((ptrdiff_t)p + (ptrdiff_t)r.off[e] * st[d]), sn);
-      prim_of(sn, gam, pn);
+      T pn[4];
+      if (tvs) {
+        const T *tp = tvs + (size_t)a.tidx[(size_t)dp * 13 + 1 + 4 * d + e] * 4;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) pn[f] = tp[f];
+      } else {
+        T sn[5];
+        donor_state(a, set, (size_t)((ptrdiff_t)p + (ptrdiff_t)r.off[e] * st[d]), sn);
+        prim_of(sn, gam, pn);
+      }
 #pragma unroll
       for (int f = 0; f < 4; ++f) acc[f] += r.w[e] * pn[f];
     }
@@ -659,9 +667,28 @@ __global__ void __launch_bounds__(256) k3c_dt(const Curv3Launch a, double pr, un
   }
 }
 
+// Extrapolated primitives (u, v, w, T) of every tap point of a donor-value launch, per set.
+template <typename T>
+__global__ void __launch_bounds__(128) k3c_tapvals(const Curv3Donor a) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)a.nsets * a.ntap) return;
+  const int set = (int)(t / a.ntap), tp = (int)(t - (long long)set * a.ntap);
+  T sn[5], pn[4];
+  donor_state(a, set, (size_t)a.tpts[tp], sn);
+  prim_of(sn, (T)a.m.gam, pn);
+  T *out = static_cast<T *>(a.tv) + ((size_t)set * a.ntap + tp) * 4;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) out[f] = pn[f];
+}
+
 cudaError_t launch3c_donor(const Curv3Donor &a, int dtype, cudaStream_t s) {
   const int n = a.nsets * a.npts;
   if (n <= 0) return cudaSuccess;
+  if (a.m.visc && a.tpts && a.ntap > 0) {
+    const unsigned b = (unsigned)(((long long)a.nsets * a.ntap + 127) / 128);
+    if (dtype == SBP_F64) k3c_tapvals<double><<<b, 128, 0, s>>>(a);
+    else k3c_tapvals<float><<<b, 128, 0, s>>>(a);
+  }
   if (dtype == SBP_F64) k3c_donor<double><<<(n + 127) / 128, 128, 0, s>>>(a);
   else k3c_donor<float><<<(n + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError();

@@ -43,6 +43,10 @@ struct PairHost {
   std::vector<double> donor_w;        // 12 per receiver
   std::vector<long long> donor_pts;   // distinct donor points (linear index on the other mesh)
   std::vector<int> donor_idx;         // 64 per receiver: (c * 4 + b) * 4 + a -> index in donor_pts
+  // Navier-Stokes: distinct points of the donor points' derivative stencils on the other mesh,
+  // and 13 indices into them per donor point (the point, then 4 taps along i, j, k)
+  std::vector<long long> tap_pts;
+  std::vector<int> tap_idx;
   size_t points() const { return (size_t)n[0] * n[1] * n[2]; }
 };
 
@@ -54,6 +58,10 @@ struct PairDev {
   double *iscale = nullptr;
   long long *dpts = nullptr;
   int *didx = nullptr;
+  long long *tpts = nullptr;  // Navier-Stokes tap points of the donor values (PairHost::tap_pts)
+  int *tidx = nullptr;
+  void *tv = nullptr;         // their extrapolated primitives, 4 per set and tap point
+  int ntap = 0;
   void *dwt = nullptr;
   void *dv = nullptr;
   void *qhat = nullptr, *fvhat = nullptr;
@@ -72,6 +80,9 @@ struct PairDev {
     cudaFree(iscale);
     cudaFree(dpts);
     cudaFree(didx);
+    cudaFree(tpts);
+    cudaFree(tidx);
+    cudaFree(tv);
     cudaFree(dwt);
     cudaFree(dv);
     cudaFree(qhat);
@@ -208,6 +219,32 @@ sbp_status pair_setup(const sbp3c_mesh_desc *meshes, int n_meshes, const sbp_par
     m.donor_idx.assign(all.size(), 0);
     for (size_t t = 0; t < all.size(); ++t)
       m.donor_idx[t] = (int)(std::lower_bound(m.donor_pts.begin(), m.donor_pts.end(), all[t]) - m.donor_pts.begin());
+    if (p.physics == SBP_NS) {
+      // the taps of each donor point's derivative rows (the class codes and offsets the
+      // kernels decode), so that every tap's extrapolated primitives are formed once per set
+      static const int off[6][4] = SBP_ROW_OFFSETS;
+      const long long st[3] = {1, (long long)o.n[0], (long long)o.n[0] * o.n[1]};
+      std::vector<long long> taps(13 * m.donor_pts.size());
+      for (size_t q = 0; q < m.donor_pts.size(); ++q) {
+        const long long pnt = m.donor_pts[q];
+        taps[13 * q] = pnt;
+        for (int d = 0; d < 3; ++d) {
+          const unsigned code = ((unsigned)o.m3.cls[(size_t)pnt] >> (4 * d)) & 15u, kind = code >> 2;
+          const int row = kind == kInterior ? 4 : kind == kHole ? 5 : (int)(code & 3u);
+          const int sgn = kind == kRight ? -1 : 1;
+          for (int e = 0; e < 4; ++e) taps[13 * q + 1 + 4 * d + e] = pnt + (long long)sgn * off[row][e] * st[d];
+        }
+      }
+      m.tap_pts = taps;
+      std::sort(m.tap_pts.begin(), m.tap_pts.end());
+      m.tap_pts.erase(std::unique(m.tap_pts.begin(), m.tap_pts.end()), m.tap_pts.end());
+      const long long npo = (long long)o.points();
+      if (!m.tap_pts.empty() && (m.tap_pts.front() < 0 || m.tap_pts.back() >= npo))
+        return fail(SBP_ERR_DONOR, "a donor point's derivative stencil leaves mesh " + std::to_string(1 - k));
+      m.tap_idx.assign(taps.size(), 0);
+      for (size_t t = 0; t < taps.size(); ++t)
+        m.tap_idx[t] = (int)(std::lower_bound(m.tap_pts.begin(), m.tap_pts.end(), taps[t]) - m.tap_pts.begin());
+    }
   }
   if ((st = build_plan(p.order, p.hist_len, p.step_ratio, plan, err)) != SBP_OK) return fail(st, err);
   return SBP_OK;
@@ -279,6 +316,12 @@ struct sbp3c_system_s {
     a.npts = md[recv].ndv;
     a.pts = md[recv].dpts;
     a.dv = (char *)md[recv].dv + (size_t)set0 * kDvPitch * md[recv].ndv * esz;
+    if (md[recv].tpts) {
+      a.tpts = md[recv].tpts;
+      a.tidx = md[recv].tidx;
+      a.ntap = md[recv].ntap;
+      a.tv = md[recv].tv;  // sets of this launch from the workspace's start
+    }
     return launch3c_donor(a, p.dtype, s);
   }
 
@@ -526,6 +569,12 @@ sbp_status sbp3c_system_create(const sbp3c_mesh_desc *meshes, int n_meshes, cons
       CUDA_TRY(upload(d.dwt, wf.data(), wf.size() * sizeof(float)));
     }
     const size_t sets = k == p.fast_mesh ? (size_t)p.step_ratio : 1;
+    if (!m.tap_pts.empty()) {
+      d.ntap = (int)m.tap_pts.size();
+      CUDA_TRY(upload(d.tpts, m.tap_pts.data(), m.tap_pts.size() * sizeof(long long)));
+      CUDA_TRY(upload(d.tidx, m.tap_idx.data(), m.tap_idx.size() * sizeof(int)));
+      CUDA_TRY(cudaMalloc(&d.tv, sets * 4 * (size_t)d.ntap * esz));
+    }
     CUDA_TRY(cudaMalloc(&d.dv, (sets * kDvPitch * d.ndv + 1) * esz));
     CUDA_TRY(cudaMemset(d.dv, 0, (sets * kDvPitch * d.ndv + 1) * esz));
     CUDA_TRY(cudaMalloc(&d.qhat, (5 * (size_t)d.nrecv + 1) * esz));

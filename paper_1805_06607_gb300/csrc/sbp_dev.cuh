@@ -19,8 +19,7 @@ namespace sbp {
 // H = diag(17/48, 59/48, 43/48, 49/48, 1, ...), row 4 the interior fourth-order central row,
 // row 5 a hole (all zero). A closure counted from a segment's high end uses the same row with
 // the offsets and the result negated.
-static __constant__ int8_t c_off[6][4] = {{0, 1, 2, 3}, {-1, 1, 0, 0}, {-2, -1, 1, 2}, {-3, -1, 1, 2}, {-2, -1, 1, 2},
-                                   {0, 0, 0, 0}};
+static __constant__ int8_t c_off[6][4] = SBP_ROW_OFFSETS;
 static __constant__ double c_w64[6][4] = {{-24.0 / 17.0, 59.0 / 34.0, -4.0 / 17.0, -3.0 / 34.0},
                                    {-0.5, 0.5, 0.0, 0.0},
                                    {4.0 / 43.0, -59.0 / 86.0, 59.0 / 86.0, -4.0 / 43.0},

@@ -137,6 +137,10 @@ struct DonorLaunch {
 };
 
 // Columns per CTA and threads per CTA of the right-hand-side kernels.
+// Offsets of the four (offset, weight) pairs of each SBP 4-2 derivative row (rows 0..3 the
+// boundary closures, 4 the interior row, 5 a hole), for the device table and host set-up.
+#define SBP_ROW_OFFSETS {{0, 1, 2, 3}, {-1, 1, 0, 0}, {-2, -1, 1, 2}, {-3, -1, 1, 2}, {-2, -1, 1, 2}, {0, 0, 0, 0}}
+
 constexpr int kTileX = 32;
 // Columns of a single-pass (marching) strip: 256 threads cover 4 rows of its 64-column flux
 // window (the strip plus a 3-point halo per side) in one pass.
