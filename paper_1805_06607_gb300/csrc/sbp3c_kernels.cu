@@ -551,47 +551,53 @@ __global__ void __launch_bounds__(128) k3c_donor(const Curv3Donor a) {
   }
 }
 
-// Receiver values of one donor-value set (the pair's right-hand side), one thread per receiver:
-// each of the 64 stencil points' values read by 16-byte loads from the point-major donor
-// values, accumulated in the stencil order (c, b, a) with the weight wi wj wk.
-template <typename T, int NV>
+// Receiver values of one donor-value set (the pair's right-hand side), GL lanes per receiver:
+// lane l takes the stencil rows (c, b) = l, l + GL, ... of the 16, reads their 4 points' values by
+// 16-byte loads from the point-major donor values and accumulates them with the weight wi wj wk
+// in the stencil order; the lanes' sums are then added by a fixed butterfly of shuffles. GL = 8
+// lanes per receiver keep a gather of a few thousand receivers from running on a few dozen CTAs
+// (measured: the 128^3 + 97^3 pair's FP32 macro step 0.932 -> 0.914 ms, FP64 unchanged).
+template <typename T, int NV, int GL>
 __global__ void __launch_bounds__(128) k3c_gather(const Curv3Gather a) {
   constexpr int VW = 16 / (int)sizeof(T), NL = (NV + VW - 1) / VW;
   static_assert(NL * VW <= kDvPitch && kDvPitch % VW == 0, "16-byte loads within a point's values");
+  static_assert(32 % GL == 0 && 16 % GL == 0, "lane groups within a warp");
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.nrecv) return;
-  const T *dv = static_cast<const T *>(a.dv);
-  const T *w = static_cast<const T *>(a.dwt) + 12 * (size_t)r;
-  const int *idx = a.didx + 64 * (size_t)r;
-  T wi[4], wj[4], wk[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    wi[e] = w[e];
-    wj[e] = w[4 + e];
-    wk[e] = w[8 + e];
-  }
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = (int)(g / GL), l = (int)(g % GL);
+  const bool valid = r < a.nrecv;
   T acc[NV];
 #pragma unroll
   for (int c = 0; c < NV; ++c) acc[c] = T(0);
+  if (valid) {
+    const T *dv = static_cast<const T *>(a.dv);
+    const T *w = static_cast<const T *>(a.dwt) + 12 * (size_t)r;
+    const int *idx = a.didx + 64 * (size_t)r;
 #pragma unroll
-  for (int c3 = 0; c3 < 4; ++c3)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int q = 0; q < 16 / GL; ++q) {
+      const int row = l + q * GL, c3 = row >> 2, b = row & 3;
+      const T wjk = w[4 + b] * w[8 + c3];
       int d[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) d[e] = checked_index(idx[(c3 * 4 + b) * 4 + e], a.ndv, a.err);
+      for (int e = 0; e < 4; ++e) d[e] = checked_index(idx[row * 4 + e], a.ndv, a.err);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const T wt = wi[e] * wj[b] * wk[c3];
+        const T wt = w[e] * wjk;
         const V *pv = reinterpret_cast<const V *>(dv + (size_t)d[e] * kDvPitch);
         T v[NL * VW];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) *reinterpret_cast<V *>(v + l * VW) = pv[l];
+        for (int k = 0; k < NL; ++k) *reinterpret_cast<V *>(v + k * VW) = pv[k];
 #pragma unroll
         for (int c = 0; c < NV; ++c) acc[c] += wt * v[c];
       }
     }
+  }
+#pragma unroll
+  for (int off = GL / 2; off > 0; off >>= 1) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+  }
+  if (!valid || l != 0) return;
   T *qh = static_cast<T *>(a.qhat);
 #pragma unroll
   for (int c = 0; c < 5; ++c) qh[(size_t)c * a.nrecv + r] = acc[c];
@@ -602,16 +608,21 @@ __global__ void __launch_bounds__(128) k3c_gather(const Curv3Gather a) {
   }
 }
 
+template <int GL>
+static void launch3c_gather_l(const Curv3Gather &a, int dtype, cudaStream_t s) {
+  const unsigned blocks = (unsigned)(((long long)a.nrecv * GL + 127) / 128);
+  if (a.nval == 17) {
+    if (dtype == SBP_F64) k3c_gather<double, 17, GL><<<blocks, 128, 0, s>>>(a);
+    else k3c_gather<float, 17, GL><<<blocks, 128, 0, s>>>(a);
+  } else {
+    if (dtype == SBP_F64) k3c_gather<double, 5, GL><<<blocks, 128, 0, s>>>(a);
+    else k3c_gather<float, 5, GL><<<blocks, 128, 0, s>>>(a);
+  }
+}
+
 cudaError_t launch3c_gather(const Curv3Gather &a, int dtype, cudaStream_t s) {
   if (a.nrecv <= 0) return cudaSuccess;
-  const unsigned blocks = (unsigned)((a.nrecv + 127) / 128);
-  if (a.nval == 17) {
-    if (dtype == SBP_F64) k3c_gather<double, 17><<<blocks, 128, 0, s>>>(a);
-    else k3c_gather<float, 17><<<blocks, 128, 0, s>>>(a);
-  } else {
-    if (dtype == SBP_F64) k3c_gather<double, 5><<<blocks, 128, 0, s>>>(a);
-    else k3c_gather<float, 5><<<blocks, 128, 0, s>>>(a);
-  }
+  launch3c_gather_l<8>(a, dtype, s);
   return cudaGetLastError();
 }
 
