@@ -227,7 +227,27 @@ class OracleSystem3D(OracleSystem):
                          self.sig_int, self.sig_phys, _p(out))
         if rc != 0:
             raise RuntimeError("oracle rhs failed: %d" % rc)
+        if int(self.p.get("sponge_cells", 0)) > 0:
+            # relaxation toward the far-field state in the sponge layer, after the SAT terms
+            out -= self.sponge_strength(k)[None] * (q - qinf[:, None, None, None])
         return out
+
+    def sponge_strength(self, k):
+        """The sponge layer of Sec. 5.1 in three directions (the 2D reading): sigma = A ((D - d) /
+        D)^2 for the index distance d < D to the nearest far-field face, the largest over the
+        faces, A = `sponge_strength`, D = `sponge_cells`; 0 elsewhere and at holes."""
+        m = self.meshes[k]
+        ni, nj, nk = m["n"]
+        D = int(self.p.get("sponge_cells", 0))
+        sig = np.zeros((nk, nj, ni))
+        if D <= 0:
+            return sig
+        A = float(self.p.get("sponge_strength", 1.0))
+        kk, jj, ii = np.meshgrid(np.arange(nk), np.arange(nj), np.arange(ni), indexing="ij")
+        for face, d in zip(m["bc"], (ii, ni - 1 - ii, jj, nj - 1 - jj, kk, nk - 1 - kk)):
+            if face == "farfield":
+                sig = np.maximum(sig, np.where(d < D, A * ((D - d) / D) ** 2, 0.0))
+        return np.where(self.iblank[k] != 0, sig, 0.0)
 
     def dt_mesh(self, k, q):
         L = lib()

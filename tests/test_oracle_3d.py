@@ -10,6 +10,7 @@
 - A uniform state is steady (free-stream preservation, interface jumps zero).
 - Tensor-product Lagrange interpolation reproduces tricubic fields; the time step matches its
   closed form on a uniform state.
+- The sponge layer reduces to the pinned 2D one on an extruded pair with far-field faces.
 """
 import ctypes
 
@@ -138,3 +139,38 @@ def test_dt3d_closed_form():
     nu = max(mu, g * mu / pr) / rho
     want = 1.0 / (inv + 2 * nu * np.sum(1 / h ** 2))
     assert abs(o.dt_mesh(0, state) - want) < 1e-14 * want
+
+
+def _sponge_vortex():
+    """The vortex pair with a far-field background (not periodic) and a sponge six points deep."""
+    wl = W.vortex_box_in_box(seed=3, n_bg=40, n_fine=25)
+    bg = wl["meshes"][0]
+    far = W.cartesian_mesh("background", bg["n"], bg["lo"], bg["h"], ("farfield",) * 4)
+    params = dict(wl["params"], sponge_cells=6, sponge_strength=2.0)
+    return dict(wl, meshes=[far, wl["meshes"][1]], params=params)
+
+
+@pytest.mark.parametrize("axis", [2, 1])
+def test_extruded_sponge_equals_2d(axis):
+    """The sponge layer (Sec. 5.1) in three directions reduces to the pinned 2D one: on the vortex
+    pair with far-field background faces extruded along a periodic direction (no far-field face
+    there), the 3D right-hand side equals the 2D oracle's slice by slice, and without the sponge
+    it does not."""
+    wl2 = _sponge_vortex()
+    o2 = OracleSystem(wl2, hole_cells=2.5)
+    r2 = o2.rhs_all(wl2["q0"])
+    wl3 = W.extrude_to_3d(wl2, nk=6, lz=6 * max(wl2["meshes"][0]["h"]), axis=axis)
+    o3 = OracleSystem3D(wl3, hole_cells=2.5)
+    r3 = o3.rhs_all(wl3["q0"])
+    plain = OracleSystem3D(dict(wl3, params=dict(wl3["params"], sponge_cells=0)), hole_cells=2.5)
+    r3p = plain.rhs_all(wl3["q0"])
+    for s in range(6):
+        if axis == 2:
+            want = np.stack([r2[0][0], r2[0][1], r2[0][2], np.zeros_like(r2[0][0]), r2[0][3]])
+            got, nosp = r3[0][:, s], r3p[0][:, s]
+        else:
+            want = np.stack([r2[0][0], r2[0][1], np.zeros_like(r2[0][0]), r2[0][2], r2[0][3]])
+            got, nosp = r3[0][:, :, s, :], r3p[0][:, :, s, :]
+        assert _rel(got, want) < 1e-12, s
+        assert _rel(nosp, want) > 1e-3, s
+    assert np.abs(o3.sponge_strength(1)).max() == 0.0  # the fine box has no far-field face
