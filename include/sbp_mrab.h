@@ -85,8 +85,9 @@ typedef struct {
    * the form is cited, not printed). Within sponge_cells (0: off, at most 16) points of a
    * far-field face the right-hand side gains -sigma (q - qinf), sigma = sponge_strength
    * ((D - d) / D)^2 for the index distance d < D = sponge_cells to the nearest far-field face.
-   * 2D systems and chains, and the background of a 3D curvilinear pair; 3D Cartesian systems
-   * reject it. Forward paths only: the adjoint calls reject a system with a sponge. */
+   * 2D systems and chains, 3D Cartesian systems (distance to the nearest of their far-field
+   * faces) and the background of a 3D curvilinear pair. Forward paths only: the adjoint calls
+   * reject a system with a sponge. */
   int sponge_cells;
   double sponge_strength;
 } sbp_params;

@@ -625,6 +625,8 @@ def _descriptors3(wl, dtype, sigma_interface, sigma_physical, hole_cells):
     pr.step_ratio = p["step_ratio"]
     pr.fast_mesh = p["fast_mesh"]
     pr.hole_cells = hole_cells
+    pr.sponge_cells = int(p.get("sponge_cells", 0))
+    pr.sponge_strength = float(p.get("sponge_strength", 1.0))
     return descs, pr
 
 

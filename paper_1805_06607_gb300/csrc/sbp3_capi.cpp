@@ -110,6 +110,15 @@ struct sbp3_system_s {
     c.sig_phys = (T)p.sigma_physical;
     for (int v = 0; v < 5; ++v) c.qinf[v] = (T)qinf[v];
     for (int a = 0; a < 3; ++a) c.ih[a] = (T)(1.0 / mh[k].h[a]);
+    c.sponge_d = 0;
+    c.sponge_faces = 0;
+    for (int f = 0; f < 6; ++f)
+      if (mh[k].bc[f] == SBP_BC_FARFIELD) c.sponge_faces |= 1 << f;
+    if (p.sponge_cells > 0 && c.sponge_faces) c.sponge_d = p.sponge_cells;
+    for (int d = 0; d < 16; ++d) {
+      const double r = d < p.sponge_cells ? (double)(p.sponge_cells - d) / p.sponge_cells : 0.0;
+      c.sponge_tab[d] = (T)(p.sponge_strength * r * r);
+    }
     return c;
   }
 
@@ -275,7 +284,8 @@ static sbp_status host3_setup(const sbp3_mesh_desc *meshes, int n_meshes, const 
   if (p.step_ratio < 1 || p.step_ratio > kMaxSets)
     return fail(SBP_ERR_ARG, "step_ratio must be in 1.." + std::to_string(kMaxSets));
   if (p.scheme != SBP_MRAB_FASTEST_FIRST) return fail(SBP_ERR_ARG, "3D systems are fastest-first");
-  if (p.sponge_cells != 0) return fail(SBP_ERR_ARG, "3D systems have no sponge layer");
+  if (p.sponge_cells < 0 || p.sponge_cells > 16 || !(p.sponge_strength >= 0.0))
+    return fail(SBP_ERR_ARG, "sponge_cells must be in 0..16 and sponge_strength >= 0");
   pout = p;
   if (pout.hole_cells <= 0) pout.hole_cells = 4;
   std::string err;

@@ -25,6 +25,10 @@ struct K3 {
   T sig_int, sig_phys;
   T qinf[5];
   T ih[3];               // 1 / h per direction
+  // sponge layer: strength by index distance d < sponge_d to the nearest far-field face
+  // (sponge_faces: bit f for a far-field face f = i-low, i-high, j-low, j-high, k-low, k-high)
+  int sponge_d, sponge_faces;
+  T sponge_tab[16];
 };
 
 constexpr int kRv3 = 17;  // receiver values: state (5), F^V_x, F^V_y, F^V_z (4 each)

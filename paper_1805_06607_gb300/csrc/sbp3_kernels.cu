@@ -352,6 +352,28 @@ __global__ void __launch_bounds__(32) k3_sat(const Rhs3Launch a) {
   for (int v = 0; v < 5; ++v) satb[v * a.nsat + s] = acc[v];
 }
 
+// Sponge layer (Sec. 5.1) at point (i, j, k), after the SAT terms: rhs -= sigma (q - qinf) with
+// sigma = sponge_tab[d] for the index distance d < sponge_d to the nearest far-field face.
+template <typename T>
+__device__ __forceinline__ void sponge3(const Rhs3Launch &a, const K3<T> &kk, int i, int j, int k, size_t p,
+                                        T rhs[5]) {
+  if (kk.sponge_d <= 0) return;
+  const Dev3Mesh &m = a.m;
+  int d = 1 << 30;
+  if (kk.sponge_faces & 1) d = min(d, i);
+  if (kk.sponge_faces & 2) d = min(d, m.ni - 1 - i);
+  if (kk.sponge_faces & 4) d = min(d, j);
+  if (kk.sponge_faces & 8) d = min(d, m.nj - 1 - j);
+  if (kk.sponge_faces & 16) d = min(d, k);
+  if (kk.sponge_faces & 32) d = min(d, m.nk - 1 - k);
+  if (d >= kk.sponge_d) return;
+  const T sg = kk.sponge_tab[d];
+  if (sg == T(0)) return;
+  const T *q = static_cast<const T *>(a.q);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) rhs[v] = fma_rn(-sg, q[v * m.field + p] - kk.qinf[v], rhs[v]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k3_update(const Rhs3Launch a) {
   const Dev3Mesh &m = a.m;
@@ -398,6 +420,7 @@ __global__ void __launch_bounds__(256) k3_update(const Rhs3Launch a) {
         for (int v = 0; v < 5; ++v) rhs[v] += satb[v * a.nsat + lo];
       }
     }
+    sponge3(a, kk, i, j, k, p, rhs);
   }
   T *out = static_cast<T *>(a.out);
   if (a.mode == 0) {
@@ -702,6 +725,7 @@ __global__ void __launch_bounds__(256) k3_updm(const Rhs3Launch a, int chunk) {
           for (int v = 0; v < 5; ++v) rhs[v] += satb[v * a.nsat + lo];
         }
       }
+      sponge3(a, kk, gi, gj, kq, p, rhs);
     }
     T *out = static_cast<T *>(a.out);
     if (a.mode == 0) {

@@ -28,8 +28,19 @@ def sbp():
 _rel = rel
 
 
+def _sponge_vortex_y():
+    """The vortex pair with far-field background faces and a sponge six points deep, extruded
+    along y (the far-field faces along i and k)."""
+    wl = W.vortex_box_in_box(seed=45, n_bg=40, n_fine=25)
+    bg = wl["meshes"][0]
+    far = W.cartesian_mesh("background", bg["n"], bg["lo"], bg["h"], ("farfield",) * 4)
+    wl = dict(wl, meshes=[far, wl["meshes"][1]], params=dict(wl["params"], sponge_cells=6, sponge_strength=2.0))
+    return W.extrude_to_3d(wl, 8, 8 * bg["h"][0], axis=1)
+
+
 CASES = {
     "tg_ns": (lambda: W.taylor_green_small(seed=41), 4),
+    "extruded_y_sponge": (_sponge_vortex_y, 2.5),
     "tg_euler": (lambda: W.taylor_green_small(seed=42, physics="euler", n_bg=20, n_fine=17), 4),
     "tg_sr3_ab34": (lambda: W.taylor_green_small(seed=43, step_ratio=3, hist_len=4, n_bg=20, n_fine=19), 4),
     "extruded_z_vortex": (lambda: W.extrude_to_3d(W.vortex_box_in_box(seed=44, n_bg=40, n_fine=25), 8, 2.0, axis=2),
@@ -74,7 +85,7 @@ def test_rhs_and_interp_3d_fp64(sbp, case):
                 assert _rel(fh.cpu().numpy(), o.interp(k, o.viscflux(1 - k, wl["q0"][1 - k]))) < 1e-12
 
 
-@pytest.mark.parametrize("case", ["tg_ns", "tg_sr3_ab34", "extruded_y_mms"])
+@pytest.mark.parametrize("case", ["tg_ns", "tg_sr3_ab34", "extruded_y_mms", "extruded_y_sponge"])
 def test_mrab_3d(sbp, case):
     """Bootstrap + 3 macro steps against the oracle: the states (FP64 1e-12, FP32 1e-5) and the
     increments over the 3 macro steps, each side from its own start (FP64 1e-12; FP32 the
