@@ -860,8 +860,21 @@ __device__ __forceinline__ void set_prim(const DonorLaunch &a, int set, int i, i
   pr[2] = gam * p * ri;
 }
 
+// Primitives (u, v, T) of an extrapolated donor state with one fixed rounding order, so that
+// the single-system kernel and the batched persistent kernel give the same bits whatever the
+// compiler contracts.
+template <typename T>
+__device__ __forceinline__ void donor_prims(const T s[4], T gam, T pr[3]) {
+  const T ri = T(1) / s[0];
+  pr[0] = mul_rn(s[1], ri);
+  pr[1] = mul_rn(s[2], ri);
+  const T ke = fma_rn(s[1], s[1], mul_rn(s[2], s[2]));
+  pr[2] = mul_rn(mul_rn(mul_rn(gam, gam - T(1)), fma_rn(mul_rn(T(-0.5), ke), ri, s[3])), ri);
+}
+
 // Navier-Stokes donor values of one (set, donor point) pair by a 16-lane group; every lane of
-// the warp must call this (shuffles), with valid = false for lanes past the end.
+// the warp must call this (shuffles), with valid = false for lanes past the end. The weighted
+// taps are rounded products, so the butterfly's sums take no contraction either.
 template <typename T, bool CURV>
 __device__ __forceinline__ void donor_group(const DonorLaunch &a, int pair, bool valid);
 
@@ -892,13 +905,13 @@ __device__ __forceinline__ void donor_group(const DonorLaunch &a, int pair, bool
     const bool act = valid && (l == 0 || w != T(0));
     T s[4] = {T(1), T(0), T(0), T(2.5)};
     if (act) set_state(a, set, (size_t)pj * a.d.pitch + pi, s);
-    const T ri = T(1) / s[0];
-    const T pr[3] = {s[1] * ri, s[2] * ri, gam * (gam - T(1)) * (s[3] - T(0.5) * (s[1] * s[1] + s[2] * s[2]) * ri) * ri};
+    T pr[3];
+    donor_prims(s, gam, pr);
     T cx[3], cy[3];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      cx[f] = (act && dir == 0) ? w * pr[f] : T(0);
-      cy[f] = (act && dir == 1) ? w * pr[f] : T(0);
+      cx[f] = (act && dir == 0) ? mul_rn(w, pr[f]) : T(0);
+      cy[f] = (act && dir == 1) ? mul_rn(w, pr[f]) : T(0);
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) {
