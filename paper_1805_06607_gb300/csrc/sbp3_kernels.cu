@@ -353,7 +353,9 @@ __global__ void __launch_bounds__(32) k3_sat(const Rhs3Launch a) {
 }
 
 // Sponge layer (Sec. 5.1) at point (i, j, k), after the SAT terms: rhs -= sigma (q - qinf) with
-// sigma = sponge_tab[d] for the index distance d < sponge_d to the nearest far-field face.
+// sigma = sponge_tab[d] for the index distance d < sponge_d to the nearest far-field face. The
+// update kernels take it behind a template switch, so meshes without a sponge (the periodic
+// boxes) run code without it.
 template <typename T>
 __device__ __forceinline__ void sponge3(const Rhs3Launch &a, const K3<T> &kk, int i, int j, int k, size_t p,
                                         T rhs[5]) {
@@ -374,7 +376,7 @@ __device__ __forceinline__ void sponge3(const Rhs3Launch &a, const K3<T> &kk, in
   for (int v = 0; v < 5; ++v) rhs[v] = fma_rn(-sg, q[v * m.field + p] - kk.qinf[v], rhs[v]);
 }
 
-template <typename T>
+template <typename T, bool SPONGE>
 __global__ void __launch_bounds__(256) k3_update(const Rhs3Launch a) {
   const Dev3Mesh &m = a.m;
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(256) k3_update(const Rhs3Launch a) {
         for (int v = 0; v < 5; ++v) rhs[v] += satb[v * a.nsat + lo];
       }
     }
-    sponge3(a, kk, i, j, k, p, rhs);
+    if constexpr (SPONGE) sponge3(a, kk, i, j, k, p, rhs);
   }
   T *out = static_cast<T *>(a.out);
   if (a.mode == 0) {
@@ -597,7 +599,7 @@ struct Upd3M {
   static constexpr size_t bytes = (size_t)(2 * BUF + kM3Ring * 5 * HN) * sizeof(T);
 };
 
-template <typename T>
+template <typename T, bool SPONGE>
 __global__ void __launch_bounds__(256) k3_updm(const Rhs3Launch a, int chunk) {
   using U = Upd3M<T>;
   constexpr int FX = U::FX, FN = U::FN, GN = U::GN, HN = U::HN, BUF = U::BUF;
@@ -725,7 +727,7 @@ __global__ void __launch_bounds__(256) k3_updm(const Rhs3Launch a, int chunk) {
           for (int v = 0; v < 5; ++v) rhs[v] += satb[v * a.nsat + lo];
         }
       }
-      sponge3(a, kk, gi, gj, kq, p, rhs);
+      if constexpr (SPONGE) sponge3(a, kk, gi, gj, kq, p, rhs);
     }
     T *out = static_cast<T *>(a.out);
     if (a.mode == 0) {
@@ -877,7 +879,9 @@ static cudaError_t march3_attrs() {
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k3_fluxm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Flux3M<T>::bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k3_updm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Upd3M<T>::bytes);
+    e = cudaFuncSetAttribute(k3_updm<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Upd3M<T>::bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k3_updm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Upd3M<T>::bytes);
   done = e == cudaSuccess;
   return e;
 }
@@ -905,8 +909,11 @@ static cudaError_t launch3_rhs_t(const Rhs3Launch &a, cudaStream_t s) {
     else if (a.visc) k3_sat<T, true, false><<<blocks, 32, 0, s>>>(a);
     else k3_sat<T, false, false><<<blocks, 32, 0, s>>>(a);
   }
-  if (march) k3_updm<T><<<mgrid, 256, Upd3M<T>::bytes, s>>>(a, a.kchunk);
-  else k3_update<T><<<grid, blk, 0, s>>>(a);
+  const bool sponge = (sizeof(T) == 4 ? a.cf.sponge_d : a.cd.sponge_d) > 0;
+  if (march && sponge) k3_updm<T, true><<<mgrid, 256, Upd3M<T>::bytes, s>>>(a, a.kchunk);
+  else if (march) k3_updm<T, false><<<mgrid, 256, Upd3M<T>::bytes, s>>>(a, a.kchunk);
+  else if (sponge) k3_update<T, true><<<grid, blk, 0, s>>>(a);
+  else k3_update<T, false><<<grid, blk, 0, s>>>(a);
   return cudaGetLastError();
 }
 
