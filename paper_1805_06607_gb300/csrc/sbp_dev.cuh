@@ -399,45 +399,6 @@ __device__ __forceinline__ void prim_at(const T *q, size_t field, size_t p, T ga
   prim4(q[p], q[field + p], q[2 * field + p], q[3 * field + p], gam, pr);
 }
 
-// Cartesian viscous fluxes at one point from the state in global memory (used at SAT points).
-template <typename T, bool CURV>
-__device__ void visc_at_point(const DevMesh &m, const T *q, int i, int j, T gam, T mu, T kap, T Fv[3], T Gv[3]) {
-  size_t p = (size_t)j * m.pitch + i;
-  unsigned code = m.cls[p];
-  T dxi[3] = {0, 0, 0}, deta[3] = {0, 0, 0};
-  for (int dir = 0; dir < 2; ++dir) {
-    int row, sgn;
-    row_of(dir == 0 ? (code & 15u) : (code >> 4), row, sgn);
-    for (int e = 0; e < 4; ++e) {
-      T we = wgt<T>(row, e);
-      if (we == T(0)) continue;
-      int ii = i, jj = j;
-      if (dir == 0) ii += sgn * c_off[row][e];
-      else jj += sgn * c_off[row][e];
-      wrap_index(ii, m.ni, m.per_i);
-      wrap_index(jj, m.nj, m.per_j);
-      T pr[3];
-      prim_at(q, m.field, (size_t)jj * m.pitch + ii, gam, pr);
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        if (dir == 0) dxi[f] += T(sgn) * we * pr[f];
-        else deta[f] += T(sgn) * we * pr[f];
-      }
-    }
-  }
-  T mt[5];
-  point_metrics<T, CURV>(m, i, j, mt);
-  T gr[6];
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    gr[2 * f] = grad_x<T, true>(mt, dxi[f], deta[f]);
-    gr[2 * f + 1] = grad_y<T, true>(mt, dxi[f], deta[f]);
-  }
-  T pc[3];
-  prim_at(q, m.field, p, gam, pc);
-  viscous_flux(pc[0], pc[1], gr, mu, kap, Fv, Gv);
-}
-
 // Kernel constants in the compute type.
 template <typename T>
 __device__ __forceinline__ const KConst<T> &kc(const RhsLaunch &a);
@@ -846,18 +807,6 @@ __device__ __forceinline__ void set_state(const DonorLaunch &a, int set, size_t 
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) out[v] = (T)acc[v];
-}
-
-template <typename T>
-__device__ __forceinline__ void set_prim(const DonorLaunch &a, int set, int i, int j, T gam, T pr[3]) {
-  T s[4];
-  set_state(a, set, (size_t)j * a.d.pitch + i, s);
-  T ri = T(1) / s[0];
-  T u = s[1] * ri, v = s[2] * ri;
-  T p = (gam - T(1)) * (s[3] - T(0.5) * (s[1] * u + s[2] * v));
-  pr[0] = u;
-  pr[1] = v;
-  pr[2] = gam * p * ri;
 }
 
 // Primitives (u, v, T) of an extrapolated donor state with one fixed rounding order, so that
