@@ -376,7 +376,7 @@ class _Null:
 # DRAM bytes, O-grid DRAM bytes per micro step). Serialised launches with a cold L2; the command
 # and the per-shape table are in profiles/fp64_ops_cylinder.md.
 FP64_COUNTS = {
-(0, 8, 4): (126749752, 18413760, 1.116e+08, 1.694e+07),
+    (0, 8, 4): (126749752, 18413760, 1.116e+08, 1.694e+07),
     (0, 8, 8): (126749752, 18413760, 1.101e+08, 1.694e+07),
     (0, 8, 16): (126749752, 18413760, 1.092e+08, 1.696e+07),
     (0, 8, 32): (126749752, 18413760, 1.088e+08, 1.699e+07),
