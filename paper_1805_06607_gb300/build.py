@@ -17,7 +17,7 @@ SOURCES = ["sbp_batch_f64.cu", "sbp_batch_f32.cu", "sbp_rhs_f64.cu", "sbp_rhs_f3
            "sbp_capi.cpp", "sbp_adjoint_capi.cpp", "sbp_setup.cpp", "sbp_noalloc.cu", "sbp3_setup.cpp",
            "sbp3_kernels.cu", "sbp3_capi.cpp", "sbp3c_kernels.cu", "sbp3c_capi.cpp", "sbp3c_setup.cpp", "sbp_probe.cu", "sbp_faults.cu", "sbp_chain.cpp",
            "sbp3c_pair.cpp"]
-HEADERS = ["sbp_internal.h", "sbp_device.h", "sbp_dev.cuh", "sbp_system.h", "sbp_rhs_impl.cuh", "sbp_march_impl.cuh", "sbp_march_tma.cuh", "sbp_col_impl.cuh", "sbp_batch_impl.cuh", "sbp3_device.h", "sbp3c_device.h", "sbp3_penalty.cuh"]
+HEADERS = ["sbp_internal.h", "sbp_device.h", "sbp_dev.cuh", "sbp_system.h", "sbp_rhs_impl.cuh", "sbp_march_impl.cuh", "sbp_march_tma.cuh", "sbp_col_impl.cuh", "sbp_batch_impl.cuh", "sbp3_device.h", "sbp3c_device.h", "sbp3_penalty.cuh", "sbp_tune.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -13,6 +13,7 @@
 
 #include "sbp_device.h"
 #include "sbp_internal.h"
+#include "sbp_tune.h"
 
 using namespace sbp;
 
@@ -730,26 +731,19 @@ struct sbp_system_s {
   // 8, 16, 32, 64 and 128 rows, staged by cp.async or (chunks of 16 to 128) by TMA tensor
   // copies, and the column-marching kernel (CTAs of 128 or 256 threads, on
   // meshes at least that wide) at chunks of 32 to 256 rows; each timed as the faster of two runs
-  // of three launches. The fast mesh's fused step (micro steps that follow one another on the
-  // critical path while the slow right-hand side runs beside them) takes only shapes whose
-  // launches give every SM a CTA (or the most CTAs any shape gives) and, for Navier-Stokes, flux
-  // tiles of at least 8 rows (a 4-row tile loads its two 3-row halos of primitives for every 4
-  // rows), and of those within 3 % of the fastest the one with the most CTAs over its launches.
-  // Timed alone, shapes of fewer, larger CTAs can win by a few percent and then lose in the
-  // macro step, where the slow mesh's CTAs share the SMs: on the cylinder's O-grid, 16-row flux
-  // tiles time within 2 % of 8-row ones alone, but the FP64 macro step takes 0.357 ms with them,
-  // 0.335 ms with 8-row flux and derivative tiles and 0.322 ms with 4-row derivative tiles.
+  // of three launches. A fast mesh's fused step follows the rules of sbp_tune.h (tune_eligible,
+  // tune_pick: every SM a CTA, Navier-Stokes flux tiles of at least 8 rows, the most CTAs among
+  // the candidates within 3 % of the fastest). Timed alone, shapes of fewer, larger CTAs can win
+  // by a few percent and then lose in the macro step, where the slow mesh's CTAs share the SMs:
+  // on the cylinder's O-grid, 16-row flux tiles time within 2 % of 8-row ones alone, but the
+  // FP64 macro step takes 0.357 ms with them, 0.335 ms with 8-row flux and derivative tiles and
+  // 0.322 ms with 4-row derivative tiles.
   bool autotune_on = true;
   cudaError_t autotune(cudaStream_t s) {
-    struct Cand {
-      int strip, rows, rows_upd;
-    };
-    static const Cand cands[] = {{0, 4, 0},   {0, 8, 0},   {0, 8, 4},   {0, 16, 0},  {0, 16, 8},  {0, 16, 4}, {0, 32, 0},
-                                 {0, 32, 16}, {kMarchW, 8, 0}, {kMarchW, 16, 0}, {kMarchW, 32, 0}, {kMarchW, 64, 0},
-                                 {kMarchW, 128, 0}, {kMarchW, 16 | kStageTma, 0}, {kMarchW, 32 | kStageTma, 0},
-                                 {kMarchW, 64 | kStageTma, 0}, {kMarchW, 128 | kStageTma, 0},
-                                 {kColW128, 32, 0}, {kColW128, 64, 0}, {kColW128, 128, 0},
-                                 {kColW256, 64, 0}, {kColW256, 128, 0}, {kColW256, 256, 0}};
+    using Cand = TuneCand;
+    static const std::vector<Cand> cand_list = tune_candidates(kMarchW, kColW128, kColW256, kStageTma);
+    const Cand *cands = cand_list.data();
+    const int ncand = (int)cand_list.size();
     Cand step_shape[2] = {{0, 16, 0}, {0, 16, 0}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
@@ -757,48 +751,18 @@ struct sbp_system_s {
     int n_sm = 1, dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    // CTAs of a candidate's launches on mesh m: the smaller grid of the pair (total = false) or
-    // the sum of its grids (total = true)
-    auto ctas = [](const Cand &c, const MeshHost &m, bool total = false) {
-      if (c.strip == 0) {
-        const long nx = (m.ni + kTileX - 1) / kTileX, ru = c.rows_upd ? c.rows_upd : c.rows;
-        const long gf = nx * ((m.nj + c.rows - 1) / c.rows), gu = nx * ((m.nj + ru - 1) / ru);
-        return total ? gf + gu : std::min(gf, gu);
-      }
-      const long ch = c.rows & (kStageTma - 1);
-      return (long)((m.ni + c.strip - 1) / c.strip) * ((m.nj + ch - 1) / ch);
-    };
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
       MeshDev &d = md[k];
       if (!d.hist) continue;
       e = interp(k, md[1 - k].q[md[1 - k].cur], nullptr, nullptr, 0, s);
       for (int use = 0; use < 2 && e == cudaSuccess; ++use) {  // 0: fused step, 1: rhs alone
-        float best = 1e30f;
         Cand best_c{0, 16, 0};
-        auto usable = [&](const Cand &c) {
-          if (c.strip == 0 && c.rows > mh[k].nj) return false;
-          if (c.strip > 0 && (c.rows & (kStageTma - 1)) > 2 * mh[k].nj) return false;
-          if (c.strip > kMarchW && mh[k].ni < c.strip + 12) return false;  // column marching: a CTA's width
-          return true;
-        };
         const bool critical = use == 0 && k == fast() && plan.sr > 1;
-        auto preferred = [&](const Cand &c) {
-          return usable(c) && !(critical && viscous() && c.strip == 0 && c.rows < 8);
-        };
-        bool any_preferred = false;
-        for (const Cand &c : cands) any_preferred = any_preferred || preferred(c);
-        auto allowed = [&](const Cand &c) { return any_preferred ? preferred(c) : usable(c); };
-        long min_ctas = 0;
-        if (critical) {
-          long most = 0;
-          for (const Cand &c : cands)
-            if (allowed(c)) most = std::max(most, ctas(c, mh[k]));
-          min_ctas = std::min((long)n_sm, most);
-        }
-        std::vector<std::pair<float, Cand>> timed;
-        for (const Cand &c : cands) {
+        const TuneMesh tm{mh[k].ni, mh[k].nj, viscous(), kTileX, kStageTma, kMarchW};
+        std::vector<std::pair<float, int>> timed;
+        for (int ci : tune_eligible(cands, ncand, tm, critical, n_sm)) {
+          const Cand &c = cands[ci];
           if (e != cudaSuccess) continue;
-          if (!allowed(c) || ctas(c, mh[k]) < min_ctas) continue;
           d.strip = d.e_strip = c.strip;
           if (c.strip) d.chunk = d.e_chunk = c.rows;
           else d.rows_per_cta = d.e_rows = c.rows;
@@ -826,20 +790,10 @@ struct sbp_system_s {
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
             if (e == cudaSuccess && t < ms) ms = t;
           }
-          if (e == cudaSuccess) timed.push_back({ms, c});
-          if (e == cudaSuccess && ms < best) {
-            best = ms;
-            best_c = c;
-          }
+          if (e == cudaSuccess) timed.push_back({ms, ci});
         }
-        if (critical) {
-          long most = ctas(best_c, mh[k], true);
-          for (const auto &tc : timed)
-            if (tc.first <= 1.03f * best && ctas(tc.second, mh[k], true) > most) {
-              most = ctas(tc.second, mh[k], true);
-              best_c = tc.second;
-            }
-        }
+        const int pick = tune_pick(cands, timed, tm, critical);
+        if (pick >= 0) best_c = cands[pick];
         if (use == 0) {
           step_shape[k] = best_c;
         } else {
